@@ -1,0 +1,233 @@
+/*
+ * corutv.h -- C ABI of libcorutv, a GB300 (sm_103a) implementation of the
+ * hot path of Compressed Randomized UTV (CoR-UTV):
+ *
+ *   M. F. Kaloorazi and R. C. de Lamare, "Compressed Randomized UTV
+ *   Decompositions for Low-Rank Approximations and Big Data Applications",
+ *   arXiv:1810.07323.  Citations below name its sections, equations and
+ *   algorithms.
+ *
+ * Problem (Sec. III, Alg. 2 and Alg. 3): given A (m x n), integers
+ * k <= l < min(m, n), q >= 0 and a Gaussian test matrix Psi (n x l, passed in
+ * by the caller), compute A ~ U T V^T with U (m x l) and V (n x l) having
+ * orthonormal columns and T (l x l) triangular.
+ *
+ * Conventions shared by every call
+ *   - Matrices are ROW-MAJOR with an explicit leading dimension (elements).
+ *   - Unless stated otherwise pointers are DEVICE pointers owned by the
+ *     caller; the library never frees them.  Inputs are read-only.
+ *   - `stream` arguments are cudaStream_t values passed as void*.  Work is
+ *     enqueued asynchronously on that stream; a call returns once the work is
+ *     enqueued.  Argument checks happen first and, on failure, nothing is
+ *     enqueued and the call returns the error code.
+ *   - "Skinny transposed" (ST) layout: an (len x l) block held as its
+ *     transpose, l rows of `len` contiguous elements, leading dimension
+ *     ld >= len, ld a multiple of 4 and the base 16-byte aligned.  The
+ *     building-block calls below read and write sketches in this layout.
+ *   - Device-side conditions (a bounded wait that expired, a Cholesky
+ *     breakdown that was repaired) are recorded in the handle's status words
+ *     and returned by corutv_info_wait().
+ *   - A handle must not be used from two host threads at once.
+ */
+#ifndef CORUTV_H
+#define CORUTV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CORUTV_ABI_VERSION 1
+
+typedef enum {
+  CORUTV_OK = 0,
+  CORUTV_ERR_INVALID_ARG = 1,   /* null pointer, bad enum, k/l/q out of range */
+  CORUTV_ERR_SHAPE = 2,         /* l >= min(m, n), leading dimension too small, l beyond the kernel limit */
+  CORUTV_ERR_ALIGN = 3,         /* base not 16-byte aligned or row pitch not a multiple of 16 bytes */
+  CORUTV_ERR_OOM = 4,           /* workspace allocation failed or caller workspace too small */
+  CORUTV_ERR_CUDA = 5,          /* a CUDA runtime/driver call failed */
+  CORUTV_ERR_TIMEOUT = 6,       /* a device-side bounded wait expired (reported by corutv_info_wait) */
+  CORUTV_ERR_CHOL_BREAKDOWN = 7,/* reserved: breakdowns are repaired, never returned by this version */
+  CORUTV_ERR_BUSY = 8,          /* serving queue full */
+  CORUTV_PENDING = 9,           /* serving request not finished */
+  CORUTV_ERR_UNSUPPORTED = 10   /* combination not built (e.g. a dtype on a path that lacks it) */
+} corutv_status;
+
+typedef enum { CORUTV_SIDE_RIGHT = 0, CORUTV_SIDE_LEFT = 1 } corutv_side;
+typedef enum { CORUTV_CORE_EXACT = 0, CORUTV_CORE_SKETCH = 1 } corutv_core;
+typedef enum { CORUTV_ORTH_STABILISED = 0 } corutv_orth;
+typedef enum { CORUTV_F64 = 0, CORUTV_F32 = 1, CORUTV_BF16 = 2, CORUTV_FP8_E4M3 = 3 } corutv_dtype;
+typedef enum {
+  CORUTV_MMA_AUTO = 0,   /* F32 A: tcgen05 TF32; F64 A: SIMT FP64 */
+  CORUTV_MMA_TF32 = 1,   /* tcgen05 kind::tf32, one product per tile */
+  CORUTV_MMA_TF32X3 = 2, /* tcgen05 kind::tf32, split hi/lo operands, FP32-faithful products */
+  CORUTV_MMA_SIMT = 3    /* CUDA-core FMA in the storage precision */
+} corutv_mma;
+
+typedef enum { CORUTV_DIR_AX = 0, CORUTV_DIR_ATY = 1 } corutv_dir;
+
+/* Parameters of one solve (Alg. 2 / Alg. 3). */
+typedef struct {
+  int64_t m, n;          /* shape of A */
+  int32_t k;             /* target rank: validated (1 <= k <= l) and used for the rank-k readout */
+  int32_t l;             /* sample size l, k <= l < min(m, n); l <= 128 (F32) or l <= 112 (F64) */
+  int32_t q;             /* power steps, q >= 0 (q = 0 is Alg. 2) */
+  int32_t side;          /* corutv_side: RIGHT = Alg. 2/3 (Psi is n x l, T upper);
+                            LEFT = the m < n modification of Sec. III: Alg. 2/3 on A^T with
+                            Psi m x l (sketch A^T Psi first), T lower (ULV form) */
+  int32_t core;          /* corutv_core: EXACT = one more pass, D = Q1^T (A Q2) (Alg. 2 step 5);
+                            SKETCH = D = (A^T Q1)^T Q2 from the last sketch, no extra pass */
+  int32_t orth;          /* corutv_orth: STABILISED (orthonormalise every sketch) */
+  int32_t a_dtype;       /* corutv_dtype of A (and of Psi, U, V: F64 for F64, F32 otherwise) */
+  int32_t mma;           /* corutv_mma for the passes over A */
+  int32_t want_fro2;     /* 1: also compute ||A||_F^2 (one extra read of A) into the info */
+  int32_t reserved[7];   /* must be zero */
+} corutv_params;
+
+/* Device-side outcome of the last solve on a handle. */
+typedef struct {
+  int32_t status;          /* corutv_status of the device work (OK or ERR_TIMEOUT) */
+  int32_t passes_over_A;   /* streaming passes over A enqueued by the solve */
+  int32_t chol_fallbacks;  /* sketch columns found numerically dependent and replaced */
+  int32_t reserved0;
+  double chol_shift_rel;   /* shift of the first CholeskyQR pass, relative to trace(C^T C) */
+  double fro2_A;           /* ||A||_F^2 if want_fro2, else NaN */
+  double fro2_T;           /* ||T||_F^2 */
+  double fro2_Tk;          /* ||T(1:k, :)||_F^2 */
+} corutv_info;
+
+typedef struct corutv_handle corutv_handle;
+
+/* ABI version (CORUTV_ABI_VERSION). */
+int corutv_version(void);
+
+/* Human-readable name of a status code (static storage). */
+const char* corutv_status_string(int status);
+
+/* Create a handle bound to `stream` (a cudaStream_t, may be NULL for the
+ * legacy default stream) on the current device.  The handle owns no user
+ * data; it lazily owns a device workspace unless one is set.  */
+int corutv_create(corutv_handle** out, void* stream);
+
+/* Synchronise the handle's stream and free what the handle owns. */
+int corutv_destroy(corutv_handle* h);
+
+/* Rebind the handle to another stream (work already enqueued stays where it is). */
+int corutv_set_stream(corutv_handle* h, void* stream);
+
+/* Bytes of device workspace a solve with parameters `p` needs (sketches
+ * C1 (m x l) and C2 (n x l) in ST layout, the core pass product, split-K
+ * partials, Gram partials, l x l factors and status words). */
+int corutv_workspace_size(const corutv_params* p, size_t* bytes);
+
+/* Use caller-owned device memory [dptr, dptr + bytes) as workspace (256-byte
+ * aligned).  Passing NULL returns the handle to lazy self-allocation.  The
+ * memory must stay valid until the handle's stream has finished the solves
+ * that use it. */
+int corutv_set_workspace(corutv_handle* h, void* dptr, size_t bytes);
+
+/*
+ * corutv_solve -- one CoR-UTV factorisation (Alg. 2 for q = 0, Alg. 3 for q >= 1).
+ *
+ *   A      device, m x n row-major, leading dimension lda >= n, dtype a_dtype;
+ *          base 16-byte aligned and lda * sizeof(dtype) a multiple of 16 (TMA rows).
+ *   a_tile_scales  FP8 only: ceil(m/128) x ceil(n/128) float scales (row-major); else NULL.
+ *   Phi    device, the Gaussian test matrix Psi (Sec. III): n x l (RIGHT) or m x l
+ *          (LEFT) row-major, ldphi >= l, F64 for a_dtype F64 else F32.
+ *   U      device out, m x l row-major (ldu >= l), same dtype as Phi.
+ *   T      device out, l x l row-major FP64 (ldt >= l): upper triangular (RIGHT,
+ *          URV) or lower triangular (LEFT, ULV); diag(T) >= 0, non-increasing.
+ *   V      device out, n x l row-major (ldv >= l), same dtype as Phi.
+ *   perm   device out, int32[l]: the QRCP pivots of the core (Sec. III, Eq. (D = Q~ R~ P~^T)).
+ *          RIGHT: V[:, j] = Q2[:, perm[j]]; LEFT: U[:, j] is the permuted basis.
+ *
+ * Range finding is stabilised: every sketch is orthonormalised (Sec. III,
+ * QR of C1 and C2) before the next product, which in exact arithmetic
+ * yields the same Q1, Q2 as the literal loop of Alg. 3.  The orthonormalisation
+ * is shifted CholeskyQR3 with an FP64 reduction of FP32 Gram partials.
+ * Returns a validation error synchronously; device conditions via corutv_info_wait.
+ */
+int corutv_solve(corutv_handle* h, const corutv_params* p,
+                 const void* A, int64_t lda, const float* a_tile_scales,
+                 const void* Phi, int64_t ldphi,
+                 void* U, int64_t ldu, double* T, int64_t ldt,
+                 void* V, int64_t ldv, int32_t* perm);
+
+/* Synchronise the handle's stream and return the outcome of the last solve. */
+int corutv_info_wait(corutv_handle* h, corutv_info* out);
+
+/* Per-phase device time accumulated since the last corutv_trace_read (tracing
+ * records a CUDA event pair around every phase of every solve on the handle's
+ * stream; it costs a few microseconds per solve). */
+typedef struct {
+  int32_t solves;          /* solves traced */
+  int32_t pass_launches;   /* streaming passes over A */
+  int64_t launches;        /* library kernels launched (all phases) */
+  double pass_ms;          /* device time inside the passes (including split-tile reduction) */
+  double pass_bytes;       /* algorithmic bytes of those passes: A + skinny operand + result */
+  double orth_ms;          /* CholeskyQR orthonormalisation */
+  double core_ms;          /* core reduction (D = Q1^T E or C2^T Q2) */
+  double qrcp_ms;          /* QRCP of D */
+  double assembly_ms;      /* U = Q1 Q~, V = Q2 P~ and staging of Psi */
+  double fro2_ms;          /* ||A||_F^2 */
+} corutv_trace;
+
+/* Enable (1) or disable (0) tracing on the handle. */
+int corutv_set_tracing(corutv_handle* h, int enable);
+
+/* Synchronise, return and reset the accumulated trace. */
+int corutv_trace_read(corutv_handle* h, corutv_trace* out);
+
+/* ------------------------------------------------------------------------
+ * Building blocks (the steps of the hot path, exported for testing and for
+ * callers that drive their own schedule).  All take the handle for its
+ * stream and workspace.
+ * ---------------------------------------------------------------------- */
+
+/*
+ * One streaming pass over A (Sec. III: C1 = A Psi, C2 = A^T C1; Alg. 3 steps 3-4).
+ *   dir = AX : Ct (l x m, ST) = (A X)^T    with Xt (l x n, ST) = X^T
+ *   dir = ATY: Ct (l x n, ST) = (A^T Y)^T  with Xt (l x m, ST) = Y^T
+ * A: m x n row-major (lda), dtype a_dtype (F64 needs mma SIMT or AUTO).
+ * Rows l..(ST rows) of Xt are ignored.
+ */
+int corutv_pass(corutv_handle* h, int dir, int a_dtype, int mma,
+                const void* A, int64_t lda, int64_t m, int64_t n, const float* a_tile_scales,
+                const void* Xt, int64_t ldx, int32_t l, void* Ct, int64_t ldc);
+
+/*
+ * Orthonormalise a tall-skinny block in place (Sec. III: C = Q R), ST layout:
+ * Ct is l x len (ldc), F32 or F64 (dtype F32/F64).  Shifted CholeskyQR3:
+ * R from the Cholesky factor of the FP64-reduced Gram matrix, Q = C R^-1,
+ * three times, the first with a diagonal shift.  If R_out != NULL it
+ * receives the l x l upper-triangular R (row-major FP64, ld l) with C = Q R.
+ */
+int corutv_orthonormalize(corutv_handle* h, int dtype, void* Ct, int64_t ldc,
+                          int64_t len, int32_t l, double* R_out);
+
+/* G (l x l, FP64 row-major, ld l) = X Y^T for ST blocks Xt, Yt (l x len):
+ * the Gram matrix C^T C of CholeskyQR, or Q1^T E for the core. */
+int corutv_gram(corutv_handle* h, int dtype, const void* Xt, int64_t ldx,
+                const void* Yt, int64_t ldy, int64_t len, int32_t l, double* G);
+
+/*
+ * QRCP of the l x l core D (FP64 row-major, ldd): D P = Q R (Sec. III,
+ * Eq. (D = Q~ R~ P~^T); Alg. 2 step 6).  Householder with Businger-Golub
+ * pivoting, column norms recomputed exactly each step, lowest index wins a
+ * tie, diag(R) >= 0.  Arithmetic in `dtype` (F32 or F64).  Outputs
+ * Q (l x l FP64), R (l x l FP64, upper), perm (int32[l], (D P)[:, j] = D[:, perm[j]]),
+ * fro2 (FP64[2]: ||R||_F^2 and ||R(1:k,:)||_F^2) -- fro2 may be NULL.
+ */
+int corutv_qrcp(corutv_handle* h, int dtype, const double* D, int64_t ldd, int32_t l, int32_t k,
+                double* Q, double* R, int32_t* perm, double* fro2);
+
+/* ||A||_F^2 of an m x n row-major A (dtype, lda) into *out (device FP64). */
+int corutv_fro2(corutv_handle* h, int a_dtype, const void* A, int64_t lda,
+                int64_t m, int64_t n, const float* a_tile_scales, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CORUTV_H */

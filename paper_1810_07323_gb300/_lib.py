@@ -1,0 +1,346 @@
+"""ctypes binding of libcorutv (argument marshalling only).
+
+Every step of the computation runs in the library's CUDA kernels; this module
+only checks tensor placement, allocates outputs with torch (device memory
+plumbing) and forwards raw pointers, sizes and the current CUDA stream to the
+C ABI declared in include/corutv.h.  If the shared library is missing the
+import fails: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from dataclasses import dataclass
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libcorutv.so")
+
+# status codes (include/corutv.h)
+OK, ERR_INVALID_ARG, ERR_SHAPE, ERR_ALIGN, ERR_OOM, ERR_CUDA, ERR_TIMEOUT = 0, 1, 2, 3, 4, 5, 6
+ERR_CHOL_BREAKDOWN, ERR_BUSY, PENDING, ERR_UNSUPPORTED = 7, 8, 9, 10
+SIDE = {"right": 0, "left": 1}
+CORE = {"exact": 0, "sketch": 1}
+DTYPE = {"f64": 0, "f32": 1, "bf16": 2, "fp8": 3}
+MMA = {"auto": 0, "tf32": 1, "tf32x3": 2, "simt": 3}
+DIR = {"ax": 0, "aty": 1}
+
+
+class CorutvError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {status_string(status)} (status {status})")
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("k", ctypes.c_int32), ("l", ctypes.c_int32),
+                ("q", ctypes.c_int32), ("side", ctypes.c_int32), ("core", ctypes.c_int32),
+                ("orth", ctypes.c_int32), ("a_dtype", ctypes.c_int32), ("mma", ctypes.c_int32),
+                ("want_fro2", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("passes_over_A", ctypes.c_int32),
+                ("chol_fallbacks", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("chol_shift_rel", ctypes.c_double), ("fro2_A", ctypes.c_double),
+                ("fro2_T", ctypes.c_double), ("fro2_Tk", ctypes.c_double)]
+
+
+class Trace(ctypes.Structure):
+    _fields_ = [("solves", ctypes.c_int32), ("pass_launches", ctypes.c_int32), ("launches", ctypes.c_int64),
+                ("pass_ms", ctypes.c_double), ("pass_bytes", ctypes.c_double), ("orth_ms", ctypes.c_double),
+                ("core_ms", ctypes.c_double), ("qrcp_ms", ctypes.c_double), ("assembly_ms", ctypes.c_double),
+                ("fro2_ms", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+
+# every entry point declared in include/corutv.h
+EXPORTS = ("corutv_version", "corutv_status_string", "corutv_create", "corutv_destroy", "corutv_set_stream",
+           "corutv_workspace_size", "corutv_set_workspace", "corutv_solve", "corutv_info_wait",
+           "corutv_set_tracing", "corutv_trace_read", "corutv_pass", "corutv_orthonormalize", "corutv_gram",
+           "corutv_qrcp", "corutv_fro2")
+
+
+def load() -> ctypes.CDLL:
+    """Load libcorutv.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with paper_1810_07323_gb300.build.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I64, I32, D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+    lib.corutv_version.restype = ctypes.c_int
+    lib.corutv_status_string.restype = ctypes.c_char_p
+    lib.corutv_status_string.argtypes = [ctypes.c_int]
+    lib.corutv_create.argtypes = [ctypes.POINTER(P), P]
+    lib.corutv_destroy.argtypes = [P]
+    lib.corutv_set_stream.argtypes = [P, P]
+    lib.corutv_workspace_size.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_size_t)]
+    lib.corutv_set_workspace.argtypes = [P, P, ctypes.c_size_t]
+    lib.corutv_solve.argtypes = [P, ctypes.POINTER(Params), P, I64, P, P, I64, P, I64, P, I64, P, I64, P]
+    lib.corutv_info_wait.argtypes = [P, ctypes.POINTER(Info)]
+    lib.corutv_pass.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, I64, I64, I64, P, P, I64, I32, P,
+                                I64]
+    lib.corutv_orthonormalize.argtypes = [P, ctypes.c_int, P, I64, I64, I32, P]
+    lib.corutv_gram.argtypes = [P, ctypes.c_int, P, I64, P, I64, I64, I32, P]
+    lib.corutv_qrcp.argtypes = [P, ctypes.c_int, P, I64, I32, I32, P, P, P, P]
+    lib.corutv_fro2.argtypes = [P, ctypes.c_int, P, I64, I64, I64, P, P]
+    lib.corutv_set_tracing.argtypes = [P, ctypes.c_int]
+    lib.corutv_trace_read.argtypes = [P, ctypes.POINTER(Trace)]
+    for name in ("corutv_set_tracing", "corutv_trace_read", "corutv_create", "corutv_destroy", "corutv_set_stream", "corutv_workspace_size",
+                 "corutv_set_workspace", "corutv_solve", "corutv_info_wait", "corutv_pass",
+                 "corutv_orthonormalize", "corutv_gram", "corutv_qrcp", "corutv_fro2"):
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def status_string(status: int) -> str:
+    return load().corutv_status_string(int(status)).decode()
+
+
+def version() -> int:
+    return load().corutv_version()
+
+
+def _check(rc: int, what: str):
+    if rc != OK:
+        raise CorutvError(rc, what)
+
+
+# ------------------------------------------------------------------ handles
+class Handle:
+    """A libcorutv handle bound to one CUDA stream (its own lazily grown workspace)."""
+
+    def __init__(self, stream=None):
+        import torch
+        self._torch = torch
+        lib = load()
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = ctypes.c_void_p()
+        _check(lib.corutv_create(ctypes.byref(h), ctypes.c_void_p(stream.cuda_stream)), "corutv_create")
+        self.h = h
+
+    def close(self):
+        if self.h:
+            load().corutv_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_tracing(self, enable: bool = True):
+        _check(load().corutv_set_tracing(self.h, 1 if enable else 0), "corutv_set_tracing")
+
+    def trace_read(self) -> Trace:
+        t = Trace()
+        _check(load().corutv_trace_read(self.h, ctypes.byref(t)), "corutv_trace_read")
+        return t
+
+    def set_workspace(self, tensor):
+        """Use a caller-owned device tensor as workspace (None: self-allocate)."""
+        ptr = 0 if tensor is None else tensor.data_ptr()
+        nbytes = 0 if tensor is None else tensor.numel() * tensor.element_size()
+        _check(load().corutv_set_workspace(self.h, ctypes.c_void_p(ptr), nbytes), "corutv_set_workspace")
+
+
+_handles: dict = {}
+
+
+def handle_for(stream=None) -> Handle:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    key = (stream.device.index if stream.device.index is not None else torch.cuda.current_device(),
+           stream.cuda_stream)
+    h = _handles.get(key)
+    if h is None:
+        h = Handle(stream)
+        _handles[key] = h
+    return h
+
+
+# ------------------------------------------------------------------ helpers
+def _dt_code(t) -> int:
+    import torch
+    m = {torch.float64: 0, torch.float32: 1, torch.bfloat16: 2}
+    if t.dtype in m:
+        return m[t.dtype]
+    if t.dtype == getattr(torch, "float8_e4m3fn", None):
+        return 3
+    raise TypeError(f"unsupported dtype {t.dtype}")
+
+
+def _need_cuda(*ts):
+    for t in ts:
+        if t is not None and not t.is_cuda:
+            raise ValueError("libcorutv takes device tensors (no CPU path)")
+
+
+def _rowmajor_ld(t) -> int:
+    if t.dim() != 2 or t.stride(1) != 1:
+        raise ValueError("expected a 2-D row-major tensor with unit column stride")
+    return t.stride(0)
+
+
+def ld_for(length: int) -> int:
+    """Leading dimension the library uses for skinny-transposed buffers."""
+    return max(64, (length + 63) // 64 * 64)
+
+
+@dataclass
+class SolveResult:
+    U: object
+    T: object
+    V: object
+    perm: object
+    info: Info | None
+
+
+def workspace_size(m, n, k, l, q=0, side="right", core="exact", a_dtype="f32", mma="auto") -> int:
+    p = _params(m, n, k, l, q, side, core, DTYPE[a_dtype], mma, False)
+    out = ctypes.c_size_t()
+    _check(load().corutv_workspace_size(ctypes.byref(p), ctypes.byref(out)), "corutv_workspace_size")
+    return out.value
+
+
+def _params(m, n, k, l, q, side, core, a_dtype_code, mma, want_fro2) -> Params:
+    p = Params()
+    p.m, p.n, p.k, p.l, p.q = int(m), int(n), int(k), int(l), int(q)
+    p.side, p.core, p.orth = SIDE[side], CORE[core], 0
+    p.a_dtype, p.mma, p.want_fro2 = a_dtype_code, MMA[mma], 1 if want_fro2 else 0
+    return p
+
+
+def solve(A, Phi, k: int, l: int, q: int = 0, side: str = "right", core: str = "exact", mma: str = "auto",
+          a_tile_scales=None, want_fro2: bool = False, out=None, wait: bool = True, handle: Handle | None = None):
+    """CoR-UTV of a device matrix A (Alg. 2 / Alg. 3): returns U, T, V, perm.
+
+    A: (m, n) row-major float64 / float32 / bfloat16 / float8_e4m3fn (with
+    a_tile_scales); Phi: (n, l) for side="right", (m, l) for side="left",
+    float64 if A is float64 else float32.  T is float64.
+    out: optional (U, T, V, perm) preallocated outputs.  wait=True
+    synchronises and returns the device info; wait=False leaves the work
+    enqueued on the current stream (info is None).
+    """
+    import torch
+    _need_cuda(A, Phi, a_tile_scales)
+    h = handle or handle_for()
+    m, n = A.shape
+    code = _dt_code(A)
+    fdt = torch.float64 if code == 0 else torch.float32
+    if Phi.dtype != fdt:
+        raise TypeError(f"Phi must be {fdt}")
+    p = _params(m, n, k, l, q, side, core, code, mma, want_fro2)
+    if out is None:
+        dev = A.device
+        U = torch.empty((m, l), dtype=fdt, device=dev)
+        T = torch.empty((l, l), dtype=torch.float64, device=dev)
+        V = torch.empty((n, l), dtype=fdt, device=dev)
+        perm = torch.empty((l,), dtype=torch.int32, device=dev)
+    else:
+        U, T, V, perm = out
+    sc = a_tile_scales.data_ptr() if a_tile_scales is not None else 0
+    rc = load().corutv_solve(h.h, ctypes.byref(p), ctypes.c_void_p(A.data_ptr()), _rowmajor_ld(A),
+                             ctypes.c_void_p(sc), ctypes.c_void_p(Phi.data_ptr()), _rowmajor_ld(Phi),
+                             ctypes.c_void_p(U.data_ptr()), _rowmajor_ld(U), ctypes.c_void_p(T.data_ptr()),
+                             _rowmajor_ld(T), ctypes.c_void_p(V.data_ptr()), _rowmajor_ld(V),
+                             ctypes.c_void_p(perm.data_ptr()))
+    _check(rc, "corutv_solve")
+    info = info_wait(h) if wait else None
+    return SolveResult(U, T, V, perm, info)
+
+
+def info_wait(h: Handle | None = None) -> Info:
+    h = h or handle_for()
+    info = Info()
+    _check(load().corutv_info_wait(h.h, ctypes.byref(info)), "corutv_info_wait")
+    return info
+
+
+def skinny_pass(direction: str, A, Xt, l: int, mma: str = "auto", a_tile_scales=None, out=None,
+                handle: Handle | None = None):
+    """One streaming pass: direction "ax": Ct (l x m) = (A X)^T from Xt (l x n);
+    "aty": Ct (l x n) = (A^T Y)^T from Xt (l x m).  Skinny-transposed buffers."""
+    import torch
+    _need_cuda(A, Xt, a_tile_scales)
+    h = handle or handle_for()
+    m, n = A.shape
+    code = _dt_code(A)
+    fdt = torch.float64 if code == 0 else torch.float32
+    olen = m if direction == "ax" else n
+    if out is None:
+        out = torch.zeros((l, ld_for(olen)), dtype=fdt, device=A.device)
+    sc = a_tile_scales.data_ptr() if a_tile_scales is not None else 0
+    rc = load().corutv_pass(h.h, DIR[direction], code, MMA[mma], ctypes.c_void_p(A.data_ptr()), _rowmajor_ld(A),
+                            m, n, ctypes.c_void_p(sc), ctypes.c_void_p(Xt.data_ptr()), _rowmajor_ld(Xt), int(l),
+                            ctypes.c_void_p(out.data_ptr()), _rowmajor_ld(out))
+    _check(rc, "corutv_pass")
+    return out
+
+
+def orthonormalize(Ct, length: int, l: int, want_R: bool = False, handle: Handle | None = None):
+    """Shifted CholeskyQR3 of a skinny-transposed block in place; returns R if asked."""
+    import torch
+    _need_cuda(Ct)
+    h = handle or handle_for()
+    code = _dt_code(Ct)
+    R = torch.empty((l, l), dtype=torch.float64, device=Ct.device) if want_R else None
+    rc = load().corutv_orthonormalize(h.h, code, ctypes.c_void_p(Ct.data_ptr()), _rowmajor_ld(Ct), int(length),
+                                      int(l), ctypes.c_void_p(R.data_ptr() if R is not None else 0))
+    _check(rc, "corutv_orthonormalize")
+    return R
+
+
+def gram(Xt, Yt, length: int, l: int, handle: Handle | None = None):
+    """G = X Y^T (float64, l x l) of two skinny-transposed blocks."""
+    import torch
+    _need_cuda(Xt, Yt)
+    h = handle or handle_for()
+    G = torch.empty((l, l), dtype=torch.float64, device=Xt.device)
+    rc = load().corutv_gram(h.h, _dt_code(Xt), ctypes.c_void_p(Xt.data_ptr()), _rowmajor_ld(Xt),
+                            ctypes.c_void_p(Yt.data_ptr()), _rowmajor_ld(Yt), int(length), int(l),
+                            ctypes.c_void_p(G.data_ptr()))
+    _check(rc, "corutv_gram")
+    return G
+
+
+def qrcp(D, k: int | None = None, dtype: str = "f64", handle: Handle | None = None):
+    """QRCP of a float64 square device matrix: returns Q, R, perm, fro2 (||R||^2, ||R(:k)||^2)."""
+    import torch
+    _need_cuda(D)
+    h = handle or handle_for()
+    l = D.shape[0]
+    Q = torch.empty((l, l), dtype=torch.float64, device=D.device)
+    R = torch.empty((l, l), dtype=torch.float64, device=D.device)
+    perm = torch.empty((l,), dtype=torch.int32, device=D.device)
+    fro2 = torch.empty((2,), dtype=torch.float64, device=D.device)
+    rc = load().corutv_qrcp(h.h, DTYPE[dtype], ctypes.c_void_p(D.data_ptr()), _rowmajor_ld(D), int(l),
+                            int(l if k is None else k), ctypes.c_void_p(Q.data_ptr()), ctypes.c_void_p(R.data_ptr()),
+                            ctypes.c_void_p(perm.data_ptr()), ctypes.c_void_p(fro2.data_ptr()))
+    _check(rc, "corutv_qrcp")
+    return Q, R, perm, fro2
+
+
+def fro2(A, a_tile_scales=None, handle: Handle | None = None):
+    """||A||_F^2 (float64 device scalar)."""
+    import torch
+    _need_cuda(A, a_tile_scales)
+    h = handle or handle_for()
+    out = torch.empty((1,), dtype=torch.float64, device=A.device)
+    sc = a_tile_scales.data_ptr() if a_tile_scales is not None else 0
+    m, n = A.shape
+    rc = load().corutv_fro2(h.h, _dt_code(A), ctypes.c_void_p(A.data_ptr()), _rowmajor_ld(A), m, n,
+                            ctypes.c_void_p(sc), ctypes.c_void_p(out.data_ptr()))
+    _check(rc, "corutv_fro2")
+    return out

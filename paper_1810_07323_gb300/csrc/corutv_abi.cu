@@ -1,0 +1,636 @@
+// C-ABI front end of libcorutv: argument checks, workspace planning, and the
+// schedule of one CoR-UTV solve (Alg. 2 / Alg. 3 of the paper, stabilised
+// range finding) enqueued on the handle's stream.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "../../include/corutv.h"
+#include "common.cuh"
+#include "internal.h"
+
+using namespace corutv;
+
+namespace corutv {
+int64_t& launch_counter() {
+  static thread_local int64_t n = 0;
+  return n;
+}
+}  // namespace corutv
+
+enum Phase { kPhPass = 0, kPhOrth, kPhCore, kPhQrcp, kPhAsm, kPhFro2, kNumPh };
+
+struct TraceRec {
+  int phase;
+  cudaEvent_t a, b;
+  double bytes;
+};
+
+struct corutv_handle {
+  cudaStream_t stream = nullptr;
+  bool tracing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<TraceRec> recs;
+  corutv_trace acc{};
+  int64_t launches = 0;
+  int device = 0;
+  int sms = 0;
+  void* ws = nullptr;          // workspace base (owned if own_ws)
+  size_t ws_bytes = 0;
+  bool own_ws = false;
+  DevStatus* status = nullptr; // inside the workspace
+  corutv_params last{};
+  int last_passes = 0;
+  double last_shift = 0.0;
+  bool have_last = false;
+};
+
+namespace {
+
+// ---------------------------------------------------------------- sizes
+constexpr double kShiftRel32 = 1e-5;    // first CholeskyQR pass, FP32 arithmetic
+constexpr double kShiftRel64 = 1e-12;   // first CholeskyQR pass, FP64 arithmetic
+constexpr double kTolRel32 = 1e-7;      // dependent-column threshold, FP32
+constexpr double kTolRel64 = 1e-14;     // dependent-column threshold, FP64
+constexpr int64_t kAlign = 256;
+
+inline int64_t ld_for(int64_t len) { return round_up(len < 1 ? 1 : len, 64); }
+inline int elem_bytes(int dt) { return dt == CORUTV_F64 ? 8 : (dt == CORUTV_F32 ? 4 : (dt == CORUTV_BF16 ? 2 : 1)); }
+inline int tc_bytes(int dt) { return dt == CORUTV_F64 ? 8 : 4; }   // sketch / compute precision
+
+struct Carve {
+  char* base;
+  size_t off = 0;
+  explicit Carve(void* b) : base(static_cast<char*>(b)) {}
+  void* take(size_t bytes) {
+    off = (size_t)round_up((int64_t)off, kAlign);
+    void* p = base ? base + off : nullptr;
+    off += bytes;
+    return p;
+  }
+};
+
+// Workspace of one solve.
+struct Plan {
+  int64_t len1, len2;       // lengths of the first (C1) and second (C2) sketch
+  int64_t ld1, ld2, ld3;
+  int LP;                   // rows of every ST buffer (>= l, 128 on the tensor-core path)
+  size_t pass_partials;
+  int gparts;
+  int fparts;
+  // carved pointers
+  DevStatus* status;
+  void *P1, *P2, *P3;
+  void* partials;
+  void* gram_parts;
+  double *G, *D, *Qt, *fro_parts;
+  void *R, *Rinv;
+  int* defic;
+};
+
+size_t plan_layout(Plan& pl, void* base) {
+  Carve c(base);
+  pl.status = static_cast<DevStatus*>(c.take(sizeof(DevStatus)));
+  const int tb = 8;  // sized for the wider of the two compute types
+  pl.P1 = c.take((size_t)pl.LP * pl.ld1 * tb);
+  pl.P2 = c.take((size_t)pl.LP * pl.ld2 * tb);
+  pl.P3 = c.take((size_t)pl.LP * pl.ld3 * tb);
+  pl.partials = c.take(pl.pass_partials);
+  pl.gram_parts = c.take((size_t)pl.gparts * kMaxL * kMaxL * tb);
+  pl.G = static_cast<double*>(c.take(sizeof(double) * kMaxL * kMaxL));
+  pl.D = static_cast<double*>(c.take(sizeof(double) * kMaxL * kMaxL));
+  pl.Qt = static_cast<double*>(c.take(sizeof(double) * kMaxL * kMaxL));
+  pl.R = c.take((size_t)kMaxL * kMaxL * tb);
+  pl.Rinv = c.take((size_t)kMaxL * kMaxL * tb);
+  pl.defic = static_cast<int*>(c.take(sizeof(int) * kMaxL));
+  pl.fro_parts = static_cast<double*>(c.take(sizeof(double) * pl.fparts));
+  return (size_t)round_up((int64_t)c.off, kAlign);
+}
+
+int device_sms(int* sms_out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return CORUTV_ERR_CUDA;
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return CORUTV_ERR_CUDA;
+  *sms_out = sms;
+  return CORUTV_OK;
+}
+
+size_t pass_partial_bytes(int64_t m, int64_t n, int l, int a_dtype, int sms) {
+  size_t b = 0;
+  // both directions, both engines (the plan does not depend on the engine chosen later)
+  b = std::max(b, simt_pass_partial_bytes(m, n, l, tc_bytes(a_dtype), sms));
+  b = std::max(b, simt_pass_partial_bytes(n, m, l, tc_bytes(a_dtype), sms));
+  if (a_dtype != CORUTV_F64) {
+    b = std::max(b, tc_pass_partial_bytes(m, n, sms));
+    b = std::max(b, tc_pass_partial_bytes(n, m, sms));
+  }
+  return b;
+}
+
+void make_plan(const corutv_params* p, int sms, Plan& pl) {
+  const bool right = p->side == CORUTV_SIDE_RIGHT;
+  pl.len1 = right ? p->m : p->n;   // C1 = A Psi (right) or A^T Psi (left)
+  pl.len2 = right ? p->n : p->m;
+  pl.ld1 = ld_for(pl.len1);
+  pl.ld2 = ld_for(pl.len2);
+  pl.ld3 = std::max(pl.ld1, pl.ld2);
+  pl.LP = kMaxL;
+  pl.pass_partials = pass_partial_bytes(p->m, p->n, p->l, p->a_dtype, sms);
+  pl.gparts = std::max(gram_parts(pl.len1, sms), gram_parts(pl.len2, sms));
+  pl.fparts = fro2_parts(sms);
+}
+
+int check_params(const corutv_params* p) {
+  if (!p) return CORUTV_ERR_INVALID_ARG;
+  for (int r : p->reserved)
+    if (r != 0) return CORUTV_ERR_INVALID_ARG;
+  if (p->a_dtype < CORUTV_F64 || p->a_dtype > CORUTV_FP8_E4M3) return CORUTV_ERR_INVALID_ARG;
+  if (p->side != CORUTV_SIDE_RIGHT && p->side != CORUTV_SIDE_LEFT) return CORUTV_ERR_INVALID_ARG;
+  if (p->core != CORUTV_CORE_EXACT && p->core != CORUTV_CORE_SKETCH) return CORUTV_ERR_INVALID_ARG;
+  if (p->orth != CORUTV_ORTH_STABILISED) return CORUTV_ERR_INVALID_ARG;
+  if (p->mma < CORUTV_MMA_AUTO || p->mma > CORUTV_MMA_SIMT) return CORUTV_ERR_INVALID_ARG;
+  if (p->m <= 0 || p->n <= 0) return CORUTV_ERR_SHAPE;
+  if (p->k < 1 || p->k > p->l) return CORUTV_ERR_INVALID_ARG;      // 1 <= k <= l (Sec. III)
+  if (p->q < 0) return CORUTV_ERR_INVALID_ARG;
+  if (p->l >= std::min(p->m, p->n)) return CORUTV_ERR_SHAPE;      // l < min(m, n) (Sec. III)
+  if (p->l > (p->a_dtype == CORUTV_F64 ? kMaxL64 : kMaxL)) return CORUTV_ERR_SHAPE;
+  if (p->a_dtype == CORUTV_F64 && (p->mma == CORUTV_MMA_TF32 || p->mma == CORUTV_MMA_TF32X3))
+    return CORUTV_ERR_UNSUPPORTED;
+  return CORUTV_OK;
+}
+
+inline bool aligned16(const void* ptr) { return ((uintptr_t)ptr & 15u) == 0; }
+
+int ensure_workspace(corutv_handle* h, size_t need) {
+  if (h->ws && h->ws_bytes >= need) return CORUTV_OK;
+  if (h->ws && !h->own_ws) return CORUTV_ERR_OOM;   // caller workspace too small
+  if (h->ws) {
+    cudaStreamSynchronize(h->stream);
+    cudaFree(h->ws);
+    h->ws = nullptr;
+    h->ws_bytes = 0;
+  }
+  void* p = nullptr;
+  if (cudaMalloc(&p, need) != cudaSuccess) {
+    cudaGetLastError();
+    return CORUTV_ERR_OOM;
+  }
+  // zero once: rows >= l of the sketch buffers are read (never used) by the tensor-core passes
+  if (cudaMemsetAsync(p, 0, need, h->stream) != cudaSuccess) {
+    cudaFree(p);
+    return CORUTV_ERR_CUDA;
+  }
+  h->ws = p;
+  h->ws_bytes = need;
+  h->own_ws = true;
+  return CORUTV_OK;
+}
+
+cudaEvent_t ev_get(corutv_handle* h) {
+  if (!h->ev_pool.empty()) {
+    cudaEvent_t e = h->ev_pool.back();
+    h->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// RAII phase timer: records an event pair on the handle's stream when tracing.
+struct PhaseTimer {
+  corutv_handle* h;
+  int phase;
+  double bytes;
+  cudaEvent_t a = nullptr;
+  PhaseTimer(corutv_handle* h_, int ph, double by = 0.0) : h(h_), phase(ph), bytes(by) {
+    if (h->tracing) {
+      a = ev_get(h);
+      cudaEventRecord(a, h->stream);
+    }
+  }
+  ~PhaseTimer() {
+    if (h->tracing && a) {
+      cudaEvent_t b = ev_get(h);
+      cudaEventRecord(b, h->stream);
+      h->recs.push_back(TraceRec{phase, a, b, bytes});
+    }
+  }
+};
+
+#define CU(x)                                   \
+  do {                                          \
+    cudaError_t e_ = (x);                       \
+    if (e_ != cudaSuccess) {                    \
+      fprintf(stderr, "corutv: %s (%s:%d)\n", cudaGetErrorString(e_), __FILE__, __LINE__); \
+      return CORUTV_ERR_CUDA;                   \
+    }                                           \
+  } while (0)
+
+// engine choice for a pass
+int pick_mma(int a_dtype, int mma) {
+  if (a_dtype == CORUTV_F64) return CORUTV_MMA_SIMT;
+  if (mma == CORUTV_MMA_AUTO) return CORUTV_MMA_TF32;
+  return mma;
+}
+
+int run_pass(corutv_handle* h, int dir, int a_dtype, int mma, const void* A, int64_t lda, int64_t m, int64_t n,
+             const float* scales, const void* Xt, int64_t ldx, int l, void* Ct, int64_t ldc, void* partials) {
+  PassArgs a{};
+  a.A = A;
+  a.lda = lda;
+  a.m = m;
+  a.n = n;
+  a.scales = scales;
+  a.scale_ld = cdiv(n, 128);
+  a.Xt = Xt;
+  a.ldx = ldx;
+  a.l = l;
+  a.Ct = Ct;
+  a.ldc = ldc;
+  a.partials = partials;
+  a.len_out = dir == CORUTV_DIR_AX ? m : n;
+  a.K = dir == CORUTV_DIR_AX ? n : m;
+  const int eng = pick_mma(a_dtype, mma);
+  const double bytes = (double)m * n * elem_bytes(a_dtype) + (double)l * (a.K + a.len_out) * tc_bytes(a_dtype);
+  PhaseTimer tm(h, kPhPass, bytes);
+  if (eng == CORUTV_MMA_SIMT) {
+    CU(launch_pass_simt(a, dir, a_dtype, h->sms, h->stream));
+  } else {
+    if (!tc_pass_supported(dir, a_dtype, eng, l)) return CORUTV_ERR_UNSUPPORTED;
+    CU(launch_pass_tc(a, dir, a_dtype, eng, h->sms, h->status, h->stream));
+  }
+  return CORUTV_OK;
+}
+
+// shifted CholeskyQR3 on an ST block (in place)
+template <typename TC>
+int orth_st(corutv_handle* h, TC* Ct, int64_t ldc, int64_t len, int l, const Plan& pl, double* Rout_last) {
+  const bool f64 = sizeof(TC) == 8;
+  PhaseTimer tm(h, kPhOrth);
+  for (int pass = 0; pass < 3; ++pass) {
+    CU(launch_gram<TC>(Ct, ldc, Ct, ldc, len, l, static_cast<TC*>(pl.gram_parts), gram_parts(len, h->sms), pl.G,
+                       kMaxL, h->stream));
+    const double shift = pass == 0 ? (f64 ? kShiftRel64 : kShiftRel32) : 0.0;
+    const double tol = f64 ? kTolRel64 : kTolRel32;
+    CU(launch_cholinv<TC>(pl.G, kMaxL, l, shift, tol, static_cast<TC*>(pl.R), static_cast<TC*>(pl.Rinv), pl.defic,
+                          pl.status, pass == 2 ? Rout_last : nullptr, h->stream));
+    CU(launch_lmul<TC>(Ct, ldc, len, l, static_cast<const TC*>(pl.Rinv), kMaxL, Ct, ldc, false, h->stream));
+    CU(launch_fill_deficient<TC>(Ct, ldc, len, l, pl.defic, pass, h->stream));
+  }
+  return CORUTV_OK;
+}
+
+template <typename TC>
+int solve_impl(corutv_handle* h, const corutv_params* p, const Plan& pl, const void* A, int64_t lda,
+               const float* scales, const void* Phi, int64_t ldphi, void* U, int64_t ldu, double* T, int64_t ldt,
+               void* V, int64_t ldv, int32_t* perm) {
+  const bool right = p->side == CORUTV_SIDE_RIGHT;
+  const int l = p->l;
+  // RIGHT: first product A X (dir AX), second A^T Q1 (dir ATY); LEFT: swapped.
+  const int dir1 = right ? CORUTV_DIR_AX : CORUTV_DIR_ATY;
+  const int dir2 = right ? CORUTV_DIR_ATY : CORUTV_DIR_AX;
+  TC* P1 = static_cast<TC*>(pl.P1);
+  TC* P2 = static_cast<TC*>(pl.P2);
+  TC* P3 = static_cast<TC*>(pl.P3);
+  int passes = 0;
+
+  CU(cudaMemsetAsync(pl.status, 0, sizeof(DevStatus), h->stream));
+  {
+    // S0: stage Psi^T into P2 (the "X" of the first product)
+    PhaseTimer tm(h, kPhAsm);
+    CU(launch_stage_transpose<TC>(static_cast<const TC*>(Phi), ldphi, pl.len2, l, P2, pl.ld2, h->stream));
+  }
+  for (int it = 0; it <= p->q; ++it) {
+    // S1: C1 = A X  (Alg. 3 step 3)
+    int rc = run_pass(h, dir1, p->a_dtype, p->mma, A, lda, p->m, p->n, scales, P2, pl.ld2, l, P1, pl.ld1,
+                      pl.partials);
+    if (rc) return rc;
+    ++passes;
+    // S2: orth(C1)
+    rc = orth_st<TC>(h, P1, pl.ld1, pl.len1, l, pl, nullptr);
+    if (rc) return rc;
+    // S3: C2 = A^T Q1  (Alg. 3 step 4)
+    rc = run_pass(h, dir2, p->a_dtype, p->mma, A, lda, p->m, p->n, scales, P1, pl.ld1, l, P2, pl.ld2,
+                  pl.partials);
+    if (rc) return rc;
+    ++passes;
+    if (it == p->q && p->core == CORUTV_CORE_SKETCH)
+      CU(cudaMemcpy2DAsync(P3, pl.ld3 * sizeof(TC), P2, pl.ld2 * sizeof(TC), pl.len2 * sizeof(TC), l,
+                           cudaMemcpyDeviceToDevice, h->stream));
+    // S4: orth(C2)
+    rc = orth_st<TC>(h, P2, pl.ld2, pl.len2, l, pl, nullptr);
+    if (rc) return rc;
+  }
+  // S5: core D = Q1^T A Q2 (Alg. 2 step 5)
+  if (p->core == CORUTV_CORE_EXACT) {
+    int rc = run_pass(h, dir1, p->a_dtype, p->mma, A, lda, p->m, p->n, scales, P2, pl.ld2, l, P3, pl.ld3,
+                      pl.partials);   // E = A Q2 (ST, len1)
+    if (rc) return rc;
+    ++passes;
+    PhaseTimer tm(h, kPhCore);
+    CU(launch_gram<TC>(P1, pl.ld1, P3, pl.ld3, pl.len1, l, static_cast<TC*>(pl.gram_parts),
+                       gram_parts(pl.len1, h->sms), pl.D, kMaxL, h->stream));   // D = Q1^T E
+  } else {
+    PhaseTimer tm(h, kPhCore);
+    // D = Q1^T A Q2 = (A^T Q1)^T Q2 = C2^T Q2 with the saved C2 (ST, len2)
+    CU(launch_gram<TC>(P3, pl.ld3, P2, pl.ld2, pl.len2, l, static_cast<TC*>(pl.gram_parts),
+                       gram_parts(pl.len2, h->sms), pl.D, kMaxL, h->stream));
+  }
+  {
+    // S6: QRCP of D (Alg. 2 step 6); T = R~ (RIGHT) or R~^T (LEFT)
+    PhaseTimer tm(h, kPhQrcp);
+    CU(launch_qrcp<TC>(pl.D, kMaxL, l, p->k, pl.Qt, kMaxL, T, ldt, !right, perm, nullptr, pl.status, h->stream));
+  }
+  // S7: assembly (Alg. 2 step 7): Q1 Q~ and Q2 P~
+  PhaseTimer tm_asm(h, kPhAsm);
+  if (right) {
+    CU(launch_lmul_f64s<TC>(P1, pl.ld1, pl.len1, l, pl.Qt, kMaxL, static_cast<TC*>(U), ldu, true, h->stream));
+    CU(launch_gather_cols<TC>(P2, pl.ld2, pl.len2, l, perm, static_cast<TC*>(V), ldv, h->stream));
+  } else {
+    CU(launch_lmul_f64s<TC>(P1, pl.ld1, pl.len1, l, pl.Qt, kMaxL, static_cast<TC*>(V), ldv, true, h->stream));
+    CU(launch_gather_cols<TC>(P2, pl.ld2, pl.len2, l, perm, static_cast<TC*>(U), ldu, h->stream));
+  }
+  // S9: ||A||_F^2 on request
+  if (p->want_fro2) {
+    PhaseTimer tm(h, kPhFro2, (double)p->m * p->n * elem_bytes(p->a_dtype));
+    CU(launch_fro2(p->a_dtype, A, lda, p->m, p->n, scales, cdiv(p->n, 128), pl.fro_parts, pl.fparts,
+                   &pl.status->fro2_A, h->stream));
+    ++passes;
+  }
+  h->last_passes = passes;
+  h->last_shift = sizeof(TC) == 8 ? kShiftRel64 : kShiftRel32;
+  return CORUTV_OK;
+}
+
+}  // namespace
+
+// =============================================================================== exported
+extern "C" {
+
+int corutv_version(void) { return CORUTV_ABI_VERSION; }
+
+const char* corutv_status_string(int s) {
+  switch (s) {
+    case CORUTV_OK: return "ok";
+    case CORUTV_ERR_INVALID_ARG: return "invalid argument";
+    case CORUTV_ERR_SHAPE: return "invalid shape";
+    case CORUTV_ERR_ALIGN: return "misaligned pointer or row pitch";
+    case CORUTV_ERR_OOM: return "out of device memory / workspace too small";
+    case CORUTV_ERR_CUDA: return "CUDA error";
+    case CORUTV_ERR_TIMEOUT: return "device wait timed out";
+    case CORUTV_ERR_CHOL_BREAKDOWN: return "Cholesky breakdown";
+    case CORUTV_ERR_BUSY: return "busy";
+    case CORUTV_PENDING: return "pending";
+    case CORUTV_ERR_UNSUPPORTED: return "unsupported combination";
+    default: return "unknown status";
+  }
+}
+
+int corutv_create(corutv_handle** out, void* stream) {
+  if (!out) return CORUTV_ERR_INVALID_ARG;
+  *out = nullptr;
+  corutv_handle* h = new (std::nothrow) corutv_handle();
+  if (!h) return CORUTV_ERR_OOM;
+  h->stream = static_cast<cudaStream_t>(stream);
+  if (cudaGetDevice(&h->device) != cudaSuccess || device_sms(&h->sms) != CORUTV_OK) {
+    delete h;
+    return CORUTV_ERR_CUDA;
+  }
+  *out = h;
+  return CORUTV_OK;
+}
+
+int corutv_destroy(corutv_handle* h) {
+  if (!h) return CORUTV_ERR_INVALID_ARG;
+  cudaStreamSynchronize(h->stream);
+  if (h->own_ws && h->ws) cudaFree(h->ws);
+  for (const TraceRec& r : h->recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+  delete h;
+  return CORUTV_OK;
+}
+
+int corutv_set_stream(corutv_handle* h, void* stream) {
+  if (!h) return CORUTV_ERR_INVALID_ARG;
+  h->stream = static_cast<cudaStream_t>(stream);
+  return CORUTV_OK;
+}
+
+int corutv_workspace_size(const corutv_params* p, size_t* bytes) {
+  if (!bytes) return CORUTV_ERR_INVALID_ARG;
+  int rc = check_params(p);
+  if (rc) return rc;
+  int sms = 0;
+  rc = device_sms(&sms);
+  if (rc) return rc;
+  Plan pl{};
+  make_plan(p, sms, pl);
+  *bytes = plan_layout(pl, nullptr);
+  return CORUTV_OK;
+}
+
+int corutv_set_workspace(corutv_handle* h, void* dptr, size_t bytes) {
+  if (!h) return CORUTV_ERR_INVALID_ARG;
+  if (dptr && ((uintptr_t)dptr % kAlign)) return CORUTV_ERR_ALIGN;
+  cudaStreamSynchronize(h->stream);
+  if (h->own_ws && h->ws) cudaFree(h->ws);
+  h->ws = dptr;
+  h->ws_bytes = dptr ? bytes : 0;
+  h->own_ws = false;
+  if (dptr && cudaMemsetAsync(dptr, 0, bytes, h->stream) != cudaSuccess) return CORUTV_ERR_CUDA;
+  return CORUTV_OK;
+}
+
+int corutv_solve(corutv_handle* h, const corutv_params* p, const void* A, int64_t lda, const float* a_tile_scales,
+                 const void* Phi, int64_t ldphi, void* U, int64_t ldu, double* T, int64_t ldt, void* V, int64_t ldv,
+                 int32_t* perm) {
+  if (!h) return CORUTV_ERR_INVALID_ARG;
+  int rc = check_params(p);
+  if (rc) return rc;
+  if (!A || !Phi || !U || !T || !V || !perm) return CORUTV_ERR_INVALID_ARG;
+  if (p->a_dtype == CORUTV_FP8_E4M3 && !a_tile_scales) return CORUTV_ERR_INVALID_ARG;
+  const int l = p->l;
+  if (lda < p->n || ldphi < l || ldu < l || ldt < l || ldv < l) return CORUTV_ERR_SHAPE;
+  if (!aligned16(A) || (lda * elem_bytes(p->a_dtype)) % 16) return CORUTV_ERR_ALIGN;
+  Plan pl{};
+  make_plan(p, h->sms, pl);
+  const size_t need = plan_layout(pl, nullptr);
+  rc = ensure_workspace(h, need);
+  if (rc) return rc;
+  plan_layout(pl, h->ws);
+  h->status = pl.status;
+  h->last = *p;
+  h->have_last = true;
+  const int64_t l0 = launch_counter();
+  if (p->a_dtype == CORUTV_F64)
+    rc = solve_impl<double>(h, p, pl, A, lda, a_tile_scales, Phi, ldphi, U, ldu, T, ldt, V, ldv, perm);
+  else
+    rc = solve_impl<float>(h, p, pl, A, lda, a_tile_scales, Phi, ldphi, U, ldu, T, ldt, V, ldv, perm);
+  h->launches += launch_counter() - l0;
+  if (h->tracing) h->acc.solves += 1;
+  return rc;
+}
+
+int corutv_info_wait(corutv_handle* h, corutv_info* out) {
+  if (!h || !out) return CORUTV_ERR_INVALID_ARG;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return CORUTV_ERR_CUDA;
+  memset(out, 0, sizeof(*out));
+  if (!h->have_last || !h->status) return CORUTV_ERR_INVALID_ARG;
+  DevStatus st{};
+  if (cudaMemcpy(&st, h->status, sizeof(st), cudaMemcpyDeviceToHost) != cudaSuccess) return CORUTV_ERR_CUDA;
+  out->status = (st.flags & kStatTimeout) ? CORUTV_ERR_TIMEOUT : CORUTV_OK;
+  out->passes_over_A = h->last_passes;
+  out->chol_fallbacks = st.chol_fallbacks;
+  out->chol_shift_rel = h->last_shift;
+  out->fro2_A = h->last.want_fro2 ? st.fro2_A : NAN;
+  out->fro2_T = st.fro2_T;
+  out->fro2_Tk = st.fro2_Tk;
+  return CORUTV_OK;
+}
+
+int corutv_set_tracing(corutv_handle* h, int enable) {
+  if (!h) return CORUTV_ERR_INVALID_ARG;
+  h->tracing = enable != 0;
+  return CORUTV_OK;
+}
+
+int corutv_trace_read(corutv_handle* h, corutv_trace* out) {
+  if (!h || !out) return CORUTV_ERR_INVALID_ARG;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return CORUTV_ERR_CUDA;
+  corutv_trace t = h->acc;
+  for (const TraceRec& r : h->recs) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, r.a, r.b);
+    switch (r.phase) {
+      case kPhPass: t.pass_ms += ms; t.pass_bytes += r.bytes; t.pass_launches += 1; break;
+      case kPhOrth: t.orth_ms += ms; break;
+      case kPhCore: t.core_ms += ms; break;
+      case kPhQrcp: t.qrcp_ms += ms; break;
+      case kPhAsm: t.assembly_ms += ms; break;
+      case kPhFro2: t.fro2_ms += ms; break;
+      default: break;
+    }
+    h->ev_pool.push_back(r.a);
+    h->ev_pool.push_back(r.b);
+  }
+  h->recs.clear();
+  t.launches = h->launches;
+  *out = t;
+  h->acc = corutv_trace{};
+  h->launches = 0;
+  return CORUTV_OK;
+}
+
+// ------------------------------------------------------------------ building blocks
+static int block_ws(corutv_handle* h, int64_t m, int64_t n, int l, int a_dtype, Plan& pl) {
+  corutv_params p{};
+  p.m = m;
+  p.n = n;
+  p.k = 1;
+  p.l = l;
+  p.a_dtype = a_dtype;
+  make_plan(&p, h->sms, pl);
+  pl.len1 = std::max(m, n);
+  pl.len2 = pl.len1;
+  pl.ld1 = pl.ld2 = pl.ld3 = 64;   // sketch buffers unused by the building blocks
+  pl.gparts = gram_parts(std::max(m, n), h->sms);
+  const size_t need = plan_layout(pl, nullptr);
+  int rc = ensure_workspace(h, need);
+  if (rc) return rc;
+  plan_layout(pl, h->ws);
+  h->status = pl.status;
+  return CORUTV_OK;
+}
+
+int corutv_pass(corutv_handle* h, int dir, int a_dtype, int mma, const void* A, int64_t lda, int64_t m, int64_t n,
+                const float* a_tile_scales, const void* Xt, int64_t ldx, int32_t l, void* Ct, int64_t ldc) {
+  if (!h || !A || !Xt || !Ct) return CORUTV_ERR_INVALID_ARG;
+  if (dir != CORUTV_DIR_AX && dir != CORUTV_DIR_ATY) return CORUTV_ERR_INVALID_ARG;
+  if (a_dtype < CORUTV_F64 || a_dtype > CORUTV_FP8_E4M3 || mma < 0 || mma > CORUTV_MMA_SIMT)
+    return CORUTV_ERR_INVALID_ARG;
+  if (a_dtype == CORUTV_F64 && (mma == CORUTV_MMA_TF32 || mma == CORUTV_MMA_TF32X3)) return CORUTV_ERR_UNSUPPORTED;
+  if (a_dtype == CORUTV_FP8_E4M3 && !a_tile_scales) return CORUTV_ERR_INVALID_ARG;
+  if (m <= 0 || n <= 0 || l < 1 || l > kMaxL || lda < n) return CORUTV_ERR_SHAPE;
+  const int64_t klen = dir == CORUTV_DIR_AX ? n : m, olen = dir == CORUTV_DIR_AX ? m : n;
+  if (ldx < klen || ldc < olen) return CORUTV_ERR_SHAPE;
+  if (!aligned16(A) || (lda * elem_bytes(a_dtype)) % 16) return CORUTV_ERR_ALIGN;
+  if (!aligned16(Xt) || (ldx * tc_bytes(a_dtype)) % 16) return CORUTV_ERR_ALIGN;
+  if (!aligned16(Ct) || (ldc * tc_bytes(a_dtype)) % 16) return CORUTV_ERR_ALIGN;
+  Plan pl{};
+  int rc = block_ws(h, m, n, l, a_dtype, pl);
+  if (rc) return rc;
+  CU(cudaMemsetAsync(pl.status, 0, sizeof(DevStatus), h->stream));
+  const int64_t l0 = launch_counter();
+  rc = run_pass(h, dir, a_dtype, mma, A, lda, m, n, a_tile_scales, Xt, ldx, l, Ct, ldc, pl.partials);
+  h->launches += launch_counter() - l0;
+  h->have_last = true;
+  h->last = corutv_params{};
+  return rc;
+}
+
+int corutv_orthonormalize(corutv_handle* h, int dtype, void* Ct, int64_t ldc, int64_t len, int32_t l,
+                          double* R_out) {
+  if (!h || !Ct) return CORUTV_ERR_INVALID_ARG;
+  if (dtype != CORUTV_F32 && dtype != CORUTV_F64) return CORUTV_ERR_INVALID_ARG;
+  if (l < 1 || l > (dtype == CORUTV_F64 ? kMaxL64 : kMaxL) || len < l || ldc < len) return CORUTV_ERR_SHAPE;
+  Plan pl{};
+  int rc = block_ws(h, len, len, l, dtype, pl);
+  if (rc) return rc;
+  CU(cudaMemsetAsync(pl.status, 0, sizeof(DevStatus), h->stream));
+  if (dtype == CORUTV_F64) return orth_st<double>(h, static_cast<double*>(Ct), ldc, len, l, pl, R_out);
+  return orth_st<float>(h, static_cast<float*>(Ct), ldc, len, l, pl, R_out);
+}
+
+int corutv_gram(corutv_handle* h, int dtype, const void* Xt, int64_t ldx, const void* Yt, int64_t ldy, int64_t len,
+                int32_t l, double* G) {
+  if (!h || !Xt || !Yt || !G) return CORUTV_ERR_INVALID_ARG;
+  if (dtype != CORUTV_F32 && dtype != CORUTV_F64) return CORUTV_ERR_INVALID_ARG;
+  if (l < 1 || l > kMaxL || len < 1 || ldx < len || ldy < len) return CORUTV_ERR_SHAPE;
+  Plan pl{};
+  int rc = block_ws(h, len, len, l, dtype, pl);
+  if (rc) return rc;
+  if (dtype == CORUTV_F64)
+    CU(launch_gram<double>(static_cast<const double*>(Xt), ldx, static_cast<const double*>(Yt), ldy, len, l,
+                           static_cast<double*>(pl.gram_parts), gram_parts(len, h->sms), G, l, h->stream));
+  else
+    CU(launch_gram<float>(static_cast<const float*>(Xt), ldx, static_cast<const float*>(Yt), ldy, len, l,
+                          static_cast<float*>(pl.gram_parts), gram_parts(len, h->sms), G, l, h->stream));
+  return CORUTV_OK;
+}
+
+int corutv_qrcp(corutv_handle* h, int dtype, const double* D, int64_t ldd, int32_t l, int32_t k, double* Q,
+                double* R, int32_t* perm, double* fro2) {
+  if (!h || !D || !Q || !R || !perm) return CORUTV_ERR_INVALID_ARG;
+  if (dtype != CORUTV_F32 && dtype != CORUTV_F64) return CORUTV_ERR_INVALID_ARG;
+  if (l < 1 || l > (dtype == CORUTV_F64 ? kMaxL64 : kMaxL) || ldd < l || k < 0 || k > l) return CORUTV_ERR_SHAPE;
+  if (dtype == CORUTV_F64)
+    CU(launch_qrcp<double>(D, ldd, l, k, Q, l, R, l, false, perm, fro2, nullptr, h->stream));
+  else
+    CU(launch_qrcp<float>(D, ldd, l, k, Q, l, R, l, false, perm, fro2, nullptr, h->stream));
+  return CORUTV_OK;
+}
+
+int corutv_fro2(corutv_handle* h, int a_dtype, const void* A, int64_t lda, int64_t m, int64_t n,
+                const float* a_tile_scales, double* out) {
+  if (!h || !A || !out) return CORUTV_ERR_INVALID_ARG;
+  if (a_dtype < CORUTV_F64 || a_dtype > CORUTV_FP8_E4M3) return CORUTV_ERR_INVALID_ARG;
+  if (a_dtype == CORUTV_FP8_E4M3 && !a_tile_scales) return CORUTV_ERR_INVALID_ARG;
+  if (m <= 0 || n <= 0 || lda < n) return CORUTV_ERR_SHAPE;
+  Plan pl{};
+  int rc = block_ws(h, m, n, 1, a_dtype, pl);
+  if (rc) return rc;
+  CU(launch_fro2(a_dtype, A, lda, m, n, a_tile_scales, cdiv(n, 128), pl.fro_parts, pl.fparts, out, h->stream));
+  return CORUTV_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,76 @@
+// Internal launch interface between the C-ABI front end and the kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace corutv {
+
+// Kernels launched by this host thread (read around a solve for its launch count).
+int64_t& launch_counter();
+#define CORUTV_COUNT_LAUNCH() (++::corutv::launch_counter())
+
+// One streaming pass over A: dir 0 (AX): Ct (l x m) = (A X)^T with Xt (l x n);
+// dir 1 (ATY): Ct (l x n) = (A^T Y)^T with Xt (l x m).
+struct PassArgs {
+  const void* A;
+  int64_t lda;
+  int64_t m, n;
+  const float* scales;   // FP8 tile scales (ceil(m/128) x ceil(n/128)) or null
+  int64_t scale_ld;      // ceil(n/128)
+  const void* Xt;
+  int64_t ldx;
+  int l;
+  void* Ct;
+  int64_t ldc;
+  void* partials;        // Stream-K partial slots
+  int64_t len_out, K;    // AX: (m, n); ATY: (n, m)
+};
+
+// pass_simt.cu
+int64_t simt_pass_grid(int64_t len, int64_t K, int sms);
+size_t simt_pass_partial_bytes(int64_t len, int64_t K, int l, int elem_bytes, int sms);
+cudaError_t launch_pass_simt(const PassArgs& a, int dir, int a_dtype, int sms, cudaStream_t st);
+
+cudaError_t launch_streamk_reduce_f32(float* Ct, int64_t ldc, const float* P, int l, int LP, int BN, int64_t len,
+                                      int64_t KB, int64_t G, cudaStream_t st);
+
+// pass_tc.cu (tcgen05 + TMA, FP32/BF16/FP8 A)
+size_t tc_pass_partial_bytes(int64_t len, int64_t K, int sms);
+bool tc_pass_supported(int dir, int a_dtype, int mma, int l);
+cudaError_t launch_pass_tc(const PassArgs& a, int dir, int a_dtype, int mma, int sms, DevStatus* status,
+                           cudaStream_t st);
+
+// small.cu
+template <typename TC>
+cudaError_t launch_gram(const TC* Xt, int64_t ldx, const TC* Yt, int64_t ldy, int64_t len, int l, TC* parts,
+                        int gparts, double* G, int64_t ldg, cudaStream_t st);
+int gram_parts(int64_t len, int sms);
+template <typename TC>
+cudaError_t launch_cholinv(const double* G, int64_t ldg, int l, double shift_rel, double tol_rel, TC* R, TC* Rinv,
+                           int* defic, DevStatus* status, double* Rout, cudaStream_t st);
+template <typename TC>
+cudaError_t launch_lmul(const TC* In, int64_t ldi, int64_t len, int l, const TC* S, int64_t lds, TC* Out,
+                        int64_t ldo, bool out_rowmajor, cudaStream_t st);
+template <typename TC>
+cudaError_t launch_lmul_f64s(const TC* In, int64_t ldi, int64_t len, int l, const double* S, int64_t lds, TC* Out,
+                             int64_t ldo, bool out_rowmajor, cudaStream_t st);
+template <typename TC>
+cudaError_t launch_fill_deficient(TC* Ct, int64_t ldc, int64_t len, int l, const int* defic, int pass,
+                                  cudaStream_t st);
+template <typename TC>
+cudaError_t launch_gather_cols(const TC* St, int64_t lds, int64_t len, int l, const int32_t* perm, TC* Out,
+                               int64_t ldo, cudaStream_t st);
+template <typename TC>
+cudaError_t launch_stage_transpose(const TC* Phi, int64_t ldphi, int64_t len, int l, TC* Xt, int64_t ldx,
+                                   cudaStream_t st);
+template <typename TC>
+cudaError_t launch_qrcp(const double* D, int64_t ldd, int l, int k, double* Q, int64_t ldq, double* R, int64_t ldr,
+                        bool r_transposed, int32_t* perm, double* fro2, DevStatus* status, cudaStream_t st);
+cudaError_t launch_fro2(int a_dtype, const void* A, int64_t lda, int64_t m, int64_t n, const float* scales,
+                        int64_t sld, double* parts, int nparts, double* out, cudaStream_t st);
+int fro2_parts(int sms);
+
+}  // namespace corutv

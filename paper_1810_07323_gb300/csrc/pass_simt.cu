@@ -1,0 +1,194 @@
+// CUDA-core (SIMT) streaming passes over A, the products of Sec. III
+// (C1 = A Psi, C2 = A^T C1) and of Alg. 3 steps 3-4, in the storage
+// precision (FP64 for FP64 data; FP32 accumulation otherwise), plus the
+// ordered reduction of Stream-K partial tiles shared with the tensor-core
+// passes.
+//
+// Layout: the skinny operand and the result are "skinny transposed": l rows
+// of `len` contiguous elements.  dir AX: Ct[j][i] = sum_k Xt[j][k] A[i][k];
+// dir ATY: Ct[j][c] = sum_r Xt[j][r] A[r][c].
+#include "common.cuh"
+#include "elem.cuh"
+#include "internal.h"
+
+namespace corutv {
+
+namespace {
+
+constexpr int kBN = 64;   // output positions per tile
+constexpr int kBK = 32;   // reduction depth per shared-memory stage
+
+template <typename TA, int DIR, int JPT>
+__global__ void __launch_bounds__(256) pass_simt_kernel(PassArgs args) {
+  using TC = typename Elem<TA>::acc;
+  constexpr int LP = 16 * JPT;
+  __shared__ TC As[kBN][kBK + 1];
+  __shared__ TC Xs[LP][kBK + 1];
+
+  const TA* A = static_cast<const TA*>(args.A);
+  const TC* Xt = static_cast<const TC*>(args.Xt);
+  TC* Ct = static_cast<TC*>(args.Ct);
+  TC* P = static_cast<TC*>(args.partials);
+  const int64_t len = args.len_out, K = args.K;
+  const int64_t KB = cdiv_d(K, kBK);
+  StreamK sk(cdiv_d(len, kBN), KB, gridDim.x);
+  const int64_t s = sk.start(blockIdx.x), e = sk.start(blockIdx.x + 1);
+  const int tid = threadIdx.x, ti = tid & 15, tj = tid >> 4;
+  const int l = args.l;
+  const int64_t sld = args.scale_ld;
+
+  int64_t it = s;
+  while (it < e) {
+    const int64_t t = it / KB;
+    const int64_t kb0 = it - t * KB;
+    const int64_t kb1 = (e - t * KB < KB) ? (e - t * KB) : KB;
+    const int64_t i0 = t * kBN;
+    TC acc[JPT][4];
+#pragma unroll
+    for (int v = 0; v < JPT; ++v)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc[v][u] = TC(0);
+
+    for (int64_t kb = kb0; kb < kb1; ++kb) {
+      const int64_t k0 = kb * kBK;
+      // stage A tile into As[i][kk]
+      for (int x = tid; x < kBN * kBK; x += 256) {
+        int ii, kk;
+        if (DIR == 0) { ii = x / kBK; kk = x % kBK; }   // coalesced along k (A rows)
+        else          { kk = x / kBN; ii = x % kBN; }   // coalesced along i (A columns)
+        const int64_t gi = i0 + ii, gk = k0 + kk;
+        TC val = TC(0);
+        if (gi < len && gk < K)
+          val = (DIR == 0) ? Elem<TA>::load(A, gi, gk, args.lda, args.scales, sld)
+                           : Elem<TA>::load(A, gk, gi, args.lda, args.scales, sld);
+        As[ii][kk] = val;
+      }
+      for (int x = tid; x < LP * kBK; x += 256) {
+        const int jj = x / kBK, kk = x % kBK;
+        const int64_t gk = k0 + kk;
+        Xs[jj][kk] = (jj < l && gk < K) ? Xt[jj * args.ldx + gk] : TC(0);
+      }
+      __syncthreads();
+#pragma unroll 8
+      for (int kk = 0; kk < kBK; ++kk) {
+        TC a[4], xv[JPT];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) a[u] = As[ti + 16 * u][kk];
+#pragma unroll
+        for (int v = 0; v < JPT; ++v) xv[v] = Xs[tj + 16 * v][kk];
+#pragma unroll
+        for (int v = 0; v < JPT; ++v)
+#pragma unroll
+          for (int u = 0; u < 4; ++u) acc[v][u] = fma(xv[v], a[u], acc[v][u]);
+      }
+      __syncthreads();
+    }
+
+    const bool complete = (kb0 == 0 && kb1 == KB);
+    if (complete) {
+#pragma unroll
+      for (int v = 0; v < JPT; ++v) {
+        const int j = tj + 16 * v;
+        if (j >= l) continue;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int64_t gi = i0 + ti + 16 * u;
+          if (gi < len) Ct[j * args.ldc + gi] = acc[v][u];
+        }
+      }
+    } else {
+      TC* slot = P + (int64_t)sk.slot(blockIdx.x, t) * LP * kBN;
+#pragma unroll
+      for (int v = 0; v < JPT; ++v)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) slot[(tj + 16 * v) * kBN + ti + 16 * u] = acc[v][u];
+    }
+    it = t * KB + kb1;
+  }
+}
+
+}  // namespace
+
+// Ordered sum of Stream-K partial tiles: tile t (BN output positions, LP rows)
+// split across workers cf..cl is the sum of their slots in worker order.
+template <typename TC>
+__global__ void streamk_reduce_kernel(TC* __restrict__ Ct, int64_t ldc, const TC* __restrict__ P, int l, int LP,
+                                      int BN, int64_t len, int64_t KB, int64_t G) {
+  StreamK sk((len + BN - 1) / BN, KB, G);
+  const int64_t t = blockIdx.x;
+  const int64_t cf = sk.owner(t * KB), cl = sk.owner(t * KB + KB - 1);
+  if (cf == cl) return;  // written directly by its only worker
+  for (int x = threadIdx.x; x < l * BN; x += blockDim.x) {
+    const int j = x / BN, ii = x % BN;
+    const int64_t gi = t * BN + ii;
+    if (gi >= len) continue;
+    TC sum = TC(0);
+    for (int64_t c = cf; c <= cl; ++c) sum += P[((int64_t)sk.slot(c, t) * LP + j) * BN + ii];
+    Ct[j * ldc + gi] = sum;
+  }
+}
+
+template __global__ void streamk_reduce_kernel<float>(float*, int64_t, const float*, int, int, int, int64_t, int64_t,
+                                                      int64_t);
+template __global__ void streamk_reduce_kernel<double>(double*, int64_t, const double*, int, int, int, int64_t,
+                                                       int64_t, int64_t);
+
+cudaError_t launch_streamk_reduce_f32(float* Ct, int64_t ldc, const float* P, int l, int LP, int BN, int64_t len,
+                                      int64_t KB, int64_t G, cudaStream_t st) {
+  const int64_t tiles = cdiv(len, BN);
+  if (tiles > 0) { streamk_reduce_kernel<float><<<(unsigned)tiles, 256, 0, st>>>(Ct, ldc, P, l, LP, BN, len, KB, G); CORUTV_COUNT_LAUNCH(); }
+  return cudaGetLastError();
+}
+
+int64_t simt_pass_grid(int64_t len, int64_t K, int sms) {
+  const int64_t work = cdiv(len, kBN) * cdiv(K, kBK);
+  int64_t G = (int64_t)sms * 4;
+  return G < work ? G : work;
+}
+
+size_t simt_pass_partial_bytes(int64_t len, int64_t K, int l, int elem_bytes, int sms) {
+  const int LP = l <= 32 ? 32 : (l <= 64 ? 64 : 128);
+  return (size_t)2 * simt_pass_grid(len, K, sms) * LP * kBN * elem_bytes;
+}
+
+template <typename TA, int DIR>
+static cudaError_t launch_jpt(const PassArgs& a, int64_t G, cudaStream_t st) {
+  if (a.l <= 32) { pass_simt_kernel<TA, DIR, 2><<<(unsigned)G, 256, 0, st>>>(a); CORUTV_COUNT_LAUNCH(); }
+  else if (a.l <= 64) { pass_simt_kernel<TA, DIR, 4><<<(unsigned)G, 256, 0, st>>>(a); CORUTV_COUNT_LAUNCH(); }
+  else { pass_simt_kernel<TA, DIR, 8><<<(unsigned)G, 256, 0, st>>>(a); CORUTV_COUNT_LAUNCH(); }
+  return cudaGetLastError();
+}
+
+template <typename TA>
+static cudaError_t launch_dir(const PassArgs& a, int dir, int64_t G, cudaStream_t st) {
+  return dir == 0 ? launch_jpt<TA, 0>(a, G, st) : launch_jpt<TA, 1>(a, G, st);
+}
+
+cudaError_t launch_pass_simt(const PassArgs& a, int dir, int a_dtype, int sms, cudaStream_t st) {
+  const int64_t G = simt_pass_grid(a.len_out, a.K, sms);
+  if (G <= 0) return cudaSuccess;
+  cudaError_t err;
+  switch (a_dtype) {
+    case 0: err = launch_dir<double>(a, dir, G, st); break;
+    case 1: err = launch_dir<float>(a, dir, G, st); break;
+    case 2: err = launch_dir<__nv_bfloat16>(a, dir, G, st); break;
+    case 3: err = launch_dir<__nv_fp8_e4m3>(a, dir, G, st); break;
+    default: return cudaErrorInvalidValue;
+  }
+  if (err != cudaSuccess) return err;
+  const int LP = a.l <= 32 ? 32 : (a.l <= 64 ? 64 : 128);
+  const int64_t tiles = cdiv(a.len_out, kBN), KB = cdiv(a.K, kBK);
+  if (a_dtype == 0) {
+    streamk_reduce_kernel<double><<<(unsigned)tiles, 256, 0, st>>>(static_cast<double*>(a.Ct), a.ldc,
+                                                                   static_cast<const double*>(a.partials), a.l, LP,
+                                                                   kBN, a.len_out, KB, G);
+  } else {
+    streamk_reduce_kernel<float><<<(unsigned)tiles, 256, 0, st>>>(static_cast<float*>(a.Ct), a.ldc,
+                                                                  static_cast<const float*>(a.partials), a.l, LP,
+                                                                  kBN, a.len_out, KB, G);
+  }
+  CORUTV_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
+
+}  // namespace corutv

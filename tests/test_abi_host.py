@@ -1,0 +1,80 @@
+"""Host-only checks of the C ABI: the library loads, exports every entry
+point include/corutv.h declares, and rejects invalid arguments before touching
+a device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1810_07323_gb300 import corutv
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "corutv.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(corutv_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported():
+    lib = corutv.load()
+    names = _declared()
+    assert len(names) >= 16
+    for name in names:
+        assert hasattr(lib, name), f"{name} declared in corutv.h but not exported"
+    assert sorted(corutv.EXPORTS) == names
+
+
+def test_version_and_status_strings():
+    assert corutv.version() == 1
+    assert corutv.status_string(0) == "ok"
+    assert "timed out" in corutv.status_string(6)
+    assert corutv.status_string(999) == "unknown status"
+
+
+def _ws(**kw):
+    args = dict(m=100, n=80, k=5, l=10, q=0, side="right", core="exact", a_dtype="f32", mma="auto")
+    args.update(kw)
+    return corutv.workspace_size(**args)
+
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(k=0), corutv.ERR_INVALID_ARG),           # 1 <= k
+    (dict(k=11), corutv.ERR_INVALID_ARG),          # k <= l
+    (dict(q=-1), corutv.ERR_INVALID_ARG),          # q >= 0
+    (dict(l=80), corutv.ERR_SHAPE),                # l < min(m, n)
+    (dict(m=1000, n=1000, l=129), corutv.ERR_SHAPE),            # l beyond the FP32 kernels
+    (dict(m=1000, n=1000, l=113, a_dtype="f64"), corutv.ERR_SHAPE),  # l beyond the FP64 kernels
+    (dict(a_dtype="f64", mma="tf32"), corutv.ERR_UNSUPPORTED),
+    (dict(m=0), corutv.ERR_SHAPE),
+])
+def test_invalid_parameters_rejected_on_host(kw, status):
+    with pytest.raises(corutv.CorutvError) as e:
+        _ws(**kw)
+    assert e.value.status == status
+
+
+def test_null_pointers_rejected():
+    lib = corutv.load()
+    assert lib.corutv_create(None, None) == corutv.ERR_INVALID_ARG
+    assert lib.corutv_destroy(None) == corutv.ERR_INVALID_ARG
+    assert lib.corutv_info_wait(None, None) == corutv.ERR_INVALID_ARG
+    assert lib.corutv_workspace_size(None, None) == corutv.ERR_INVALID_ARG
+    p = corutv.Params()
+    assert lib.corutv_solve(None, ctypes.byref(p), None, 0, None, None, 0, None, 0, None, 0, None, 0,
+                            None) == corutv.ERR_INVALID_ARG
+
+
+def test_reserved_fields_must_be_zero():
+    p = corutv._params(100, 80, 5, 10, 0, "right", "exact", 1, "auto", False)
+    p.reserved[3] = 1
+    out = ctypes.c_size_t()
+    assert corutv.load().corutv_workspace_size(ctypes.byref(p), ctypes.byref(out)) == corutv.ERR_INVALID_ARG
+
+
+def test_device_tensors_required():
+    import torch
+    with pytest.raises(ValueError):
+        corutv.solve(torch.zeros(10, 8), torch.zeros(8, 2), 1, 2)

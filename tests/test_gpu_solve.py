@@ -1,0 +1,208 @@
+"""End-to-end GPU parity of corutv_solve (through the C ABI) with the FP64
+oracle run on the same inputs (the storage-dtype A and Psi promoted to FP64).
+
+Primary parity measure (pivot- and sign-invariant, Sec. III: A ~ U T V^T):
+    rho = ||U T V^T - U_o T_o V_o^T||_F / ||U_o T_o V_o^T||_F
+Tolerances, derived from the arithmetic of each engine:
+  FP64 (SIMT, FP64 factorisations):     rho <= 1e-10
+  FP32 SIMT products, FP32 factorisations: rho <= 1e-4
+  TF32 tensor-core products (operands keep 10 mantissa bits, products
+  truncated toward zero: up to ~2^-10 relative per product, a systematic
+  shrink of ~3.5e-4 on average): rho <= 5e-3
+Structure is checked exactly where the method fixes it (T triangular,
+diag(T) >= 0 non-increasing, perm a permutation, V = Q2 P~ up to FP error).
+"""
+import numpy as np
+import pytest
+
+from oracle import corutv_oracle as O
+from synth import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if torch.cuda.is_available():
+    from paper_1810_07323_gb300 import corutv
+
+TOL = {"f64": 1e-10, "simt": 1e-4, "tf32": 5e-3}
+
+
+def _run(A, phi, k, l, q, dt, mma="auto", side="right", core="exact", want_fro2=False):
+    Ad = torch.tensor(A, dtype=torch.float64, device="cuda").to(dt)
+    Pd = torch.tensor(phi, dtype=torch.float64, device="cuda").to(dt)
+    r = corutv.solve(Ad, Pd, k, l, q, side=side, core=core, mma=mma, want_fro2=want_fro2)
+    assert r.info.status == 0, corutv.status_string(r.info.status)
+    A64 = Ad.double().cpu().numpy()
+    P64 = Pd.double().cpu().numpy()
+    return r, A64, P64
+
+
+def _np(r):
+    return r.U.double().cpu().numpy(), r.T.cpu().numpy(), r.V.double().cpu().numpy(), r.perm.cpu().numpy()
+
+
+def _structure(U, T, V, perm, l, side="right", orth_tol=1e-12):
+    tri = np.tril(T, -1) if side == "right" else np.triu(T, 1)
+    assert np.abs(tri).max() == 0.0
+    d = np.diag(T)
+    assert np.all(d >= 0) and np.all(np.diff(d) <= 1e-12 * max(d[0], 1e-300))
+    assert sorted(perm) == list(range(l))
+    assert O.orthonormality_error(U) < orth_tol
+    assert O.orthonormality_error(V) < orth_tol
+
+
+@pytest.fixture(scope="module")
+def cfg1():
+    return W.config1()
+
+
+@pytest.mark.parametrize("q", [0, 1, 2])
+@pytest.mark.parametrize("core", ["exact", "sketch"])
+def test_config1_fp64_parity(cfg1, q, core):
+    r, A, phi = _run(cfg1.A, W.phi(1500, 30), 20, 30, q, torch.float64, core=core, want_fro2=True)
+    U, T, V, perm = _np(r)
+    ref = O.corutv(A, phi, 20, 30, q)
+    rho = O.factor_distance(U, T, V, ref["U"], ref["T"], ref["V"])
+    assert rho < TOL["f64"], rho
+    _structure(U, T, V, perm, 30)
+    assert np.array_equal(perm, ref["perm"])
+    assert np.abs(T - ref["T"]).max() < 1e-10
+    # S9: ||A - U T V^T||_F^2 = ||A||_F^2 - ||T||_F^2 from the device readouts
+    a2 = np.sum(A ** 2)
+    assert abs(r.info.fro2_A - a2) < 1e-12 * a2
+    assert abs(r.info.fro2_T - np.sum(T ** 2)) < 1e-12 * a2
+    e2 = O.fro_residual(A, U, T, V) ** 2
+    assert abs((r.info.fro2_A - r.info.fro2_T) - e2) < 1e-10 * a2
+    assert r.info.passes_over_A == 2 * q + (3 if core == "exact" else 2) + 1
+
+
+def test_config1_exact_rank_recovery():
+    d = W.config1(exact_rank=True)
+    r, A, phi = _run(d.A, W.phi(1500, 30), 20, 30, 0, torch.float64)
+    U, T, V, perm = _np(r)
+    assert O.fro_residual(A, U, T, V) / np.linalg.norm(A) < 1e-12
+    sT = O.jacobi_svd(T)
+    assert np.abs(sT[:20] - d.sigma[:20]).max() < 1e-12
+    _structure(U, T, V, perm, 30)
+
+
+def test_config1_side_left_ulv(cfg1):
+    r, A, phi = _run(cfg1.A, W.phi(2000, 30), 20, 30, 1, torch.float64, side="left")
+    U, T, V, perm = _np(r)
+    ref = O.corutv(A, phi, 20, 30, 1, side="left")
+    assert O.factor_distance(U, T, V, ref["U"], ref["T"], ref["V"]) < TOL["f64"]
+    _structure(U, T, V, perm, 30, side="left")
+
+
+@pytest.fixture(scope="module")
+def slice2():
+    """4000 x 4000 slice of the 20000 x 20000 workload (same generator, same indices)."""
+    g = W.config2()
+    return g.block(0, 4000, 0, 4000), W.phi(20000, 120)[:4000]
+
+
+@pytest.mark.parametrize("mma", ["tf32", "simt"])
+@pytest.mark.parametrize("q", [0, 1, 2])
+def test_config2_slice_fp32_parity(slice2, mma, q):
+    A, phi = slice2
+    r, A32, P32 = _run(A, phi, 100, 120, q, torch.float32, mma=mma)
+    U, T, V, perm = _np(r)
+    ref = O.corutv(A32, P32, 100, 120, q)
+    rho = O.factor_distance(U, T, V, ref["U"], ref["T"], ref["V"])
+    print(f"config2 slice mma={mma} q={q}: rho={rho:.3e}")
+    assert rho < TOL[mma], rho
+    _structure(U, T, V, perm, 120, orth_tol=5e-5)
+    # rank-k error at most 1.05 x the oracle's (plus the engine's rounding floor)
+    ek = O.fro_residual(A32, U, T, V, k=100)
+    ek_ref = O.fro_residual(A32, ref["U"], ref["T"], ref["V"], k=100)
+    floor = (2.0 ** -10 if mma == "tf32" else 1e-6) * np.linalg.norm(A32)
+    assert ek <= 1.05 * ek_ref + floor
+
+
+@pytest.mark.parametrize("m,n,k,l,q,side", [
+    (1001, 777, 10, 37, 1, "right"),      # ragged everywhere
+    (200, 900, 5, 12, 1, "left"),          # m < n: ULV form
+    (130, 129, 128, 128, 0, "right"),      # l = k = 128 = min(m, n) - 1
+    (65, 64, 3, 3, 2, "right"),            # tiny
+])
+@pytest.mark.parametrize("mma", ["tf32", "simt"])
+def test_shapes_and_degenerate_cases(m, n, k, l, q, side, mma):
+    A = (W.gaussian(m + 1, m, 40) * np.exp(-np.arange(40) / 5.0)) @ W.gaussian(n + 2, 40, n) / 10
+    phi = W.gaussian(7, m if side == "left" else n, l)
+    r, A32, P32 = _run(A, phi, k, l, q, torch.float32, mma=mma, side=side)
+    U, T, V, perm = _np(r)
+    ref = O.corutv(A32, P32, k, l, q, side=side)
+    rho = O.factor_distance(U, T, V, ref["U"], ref["T"], ref["V"])
+    assert rho < TOL[mma], rho
+    _structure(U, T, V, perm, l, side=side, orth_tol=5e-5)
+
+
+def test_solve_deterministic(slice2):
+    A, phi = slice2
+    Ad = torch.tensor(A, dtype=torch.float32, device="cuda")
+    Pd = torch.tensor(phi, dtype=torch.float32, device="cuda")
+    r1 = corutv.solve(Ad, Pd, 100, 120, 1)
+    U1, T1, V1 = r1.U.clone(), r1.T.clone(), r1.V.clone()
+    r2 = corutv.solve(Ad, Pd, 100, 120, 1)
+    assert torch.equal(U1, r2.U) and torch.equal(T1, r2.T) and torch.equal(V1, r2.V)
+
+
+def test_invalid_arguments_enqueue_nothing():
+    A = torch.zeros((100, 80), device="cuda")
+    phi = torch.zeros((80, 10), device="cuda")
+    with pytest.raises(corutv.CorutvError) as e:
+        corutv.solve(A, phi, 11, 10)
+    assert e.value.status == corutv.ERR_INVALID_ARG
+    with pytest.raises(corutv.CorutvError) as e:
+        corutv.solve(A, torch.zeros((80, 80), device="cuda"), 5, 80)
+    assert e.value.status == corutv.ERR_SHAPE
+
+
+@pytest.mark.slow
+def test_config2_full_size_properties():
+    """The 20000 x 20000 FP32 workload in the launch configuration the
+    benchmark times: sampled rows of the first pass against the oracle,
+    structure, the exact-core Pythagorean identity, and diag(T) against the
+    closed-form spectrum sigma_j(G1 S G2^T) = sigma_j(R1 S R2^T)."""
+    g = W.config2()
+    A = g.block_t(0, g.m, 0, g.n, device="cuda", dtype=torch.float32)
+    phi_d = W.phi_t(g.n, 120, device="cuda").float()
+    # sampled rows of C1 = A Psi through the building-block pass
+    Xt = torch.zeros((120, corutv.ld_for(g.n)), device="cuda")
+    Xt[:, :g.n] = phi_d.T
+    C1t = corutv.skinny_pass("ax", A, Xt, 120, mma="tf32")
+    rows = np.random.default_rng(0).choice(g.m, 64, replace=False)
+    A_rows = A[rows].double().cpu().numpy()
+    P64 = phi_d.double().cpu().numpy()
+    ref = A_rows @ P64
+    got = C1t[:, rows].double().cpu().numpy().T
+    assert np.all(np.abs(got - ref) <= 2.5 * 2.0 ** -10 * (np.abs(A_rows) @ np.abs(P64)))
+    # the solve
+    r = corutv.solve(A, phi_d, 100, 120, 1, want_fro2=True)
+    assert r.info.status == 0
+    U, T, V = r.U, r.T, r.V
+    assert (U.T.double() @ U.double() - torch.eye(120, device="cuda", dtype=torch.float64)).abs().max() < 5e-5
+    assert (V.T.double() @ V.double() - torch.eye(120, device="cuda", dtype=torch.float64)).abs().max() < 5e-5
+    Th = T.cpu().numpy()
+    assert np.abs(np.tril(Th, -1)).max() == 0
+    # exact core: ||A - U T V^T||^2 = ||A||^2 - ||T||^2 (to the TF32 level of the passes)
+    res2 = 0.0
+    for a in range(0, g.m, 2000):
+        blk = A[a:a + 2000].double() - (U[a:a + 2000].double() @ T) @ V.double().T
+        res2 += float((blk * blk).sum())
+    a2 = r.info.fro2_A
+    assert abs((a2 - r.info.fro2_T) - res2) < 2e-3 * a2
+    # closed-form spectrum of the noise-free part: Eckart-Young floor and near-optimality
+    R1 = O.householder_qr(g.g1(0, g.m))[1]
+    R2 = O.householder_qr(g.g2(0, g.n))[1]
+    sig = O.jacobi_svd((R1 * g.sigma[None, :]) @ R2.T)
+    assert Th[0, 0] <= sig[0] * (1 + 1e-3)               # max column norm of D <= sigma_1(D) <= sigma_1(A)
+    ek2 = 0.0
+    Uk, Tk, Vd = U[:, :100].double(), T[:100].double(), V.double()
+    for a in range(0, g.m, 2000):
+        blk = A[a:a + 2000].double() - (Uk[a:a + 2000] @ Tk) @ Vd.T
+        ek2 += float((blk * blk).sum())
+    floor2 = float(np.sum(sig[100:] ** 2))
+    print(f"full size: e_k^2 = {ek2:.4e}, optimal {floor2:.4e}")
+    assert ek2 >= floor2 * (1 - 1e-3)
+    assert ek2 <= 4.0 * floor2
