@@ -60,10 +60,13 @@ typedef enum { CORUTV_CORE_EXACT = 0, CORUTV_CORE_SKETCH = 1 } corutv_core;
 typedef enum { CORUTV_ORTH_STABILISED = 0 } corutv_orth;
 typedef enum { CORUTV_F64 = 0, CORUTV_F32 = 1, CORUTV_BF16 = 2, CORUTV_FP8_E4M3 = 3 } corutv_dtype;
 typedef enum {
-  CORUTV_MMA_AUTO = 0,   /* F32 A: tcgen05 TF32; F64 A: SIMT FP64 */
-  CORUTV_MMA_TF32 = 1,   /* tcgen05 kind::tf32, one product per tile */
-  CORUTV_MMA_TF32X3 = 2, /* tcgen05 kind::tf32, split hi/lo operands, FP32-faithful products */
-  CORUTV_MMA_SIMT = 3    /* CUDA-core FMA in the storage precision */
+  CORUTV_MMA_AUTO = 0,       /* F32 A: TF32 (rounded); other dtypes: SIMT */
+  CORUTV_MMA_TF32 = 1,       /* tcgen05 kind::tf32 with both operands rounded to nearest TF32
+                                (A tile by tile in shared memory): unbiased products */
+  CORUTV_MMA_TF32X3 = 2,     /* reserved (split-operand FP32-faithful products): returns UNSUPPORTED */
+  CORUTV_MMA_SIMT = 3,       /* CUDA-core FMA in the storage precision (FP32 or FP64 products) */
+  CORUTV_MMA_TF32_TRUNC = 4  /* tcgen05 kind::tf32 reading raw FP32 (the tensor core drops the low
+                                13 mantissa bits: products shrink by ~3.5e-4 on average) */
 } corutv_mma;
 
 typedef enum { CORUTV_DIR_AX = 0, CORUTV_DIR_ATY = 1 } corutv_dir;
@@ -82,7 +85,8 @@ typedef struct {
   int32_t orth;          /* corutv_orth: STABILISED (orthonormalise every sketch) */
   int32_t a_dtype;       /* corutv_dtype of A (and of Psi, U, V: F64 for F64, F32 otherwise) */
   int32_t mma;           /* corutv_mma for the passes over A */
-  int32_t want_fro2;     /* 1: also compute ||A||_F^2 (one extra read of A) into the info */
+  int32_t want_fro2;     /* 1: also compute ||A||_F^2 into the info (fused into the first pass on the
+                            tensor-core engine, one extra read of A otherwise) */
   int32_t reserved[7];   /* must be zero */
 } corutv_params;
 
@@ -131,8 +135,10 @@ int corutv_set_workspace(corutv_handle* h, void* dptr, size_t bytes);
 /*
  * corutv_solve -- one CoR-UTV factorisation (Alg. 2 for q = 0, Alg. 3 for q >= 1).
  *
- *   A      device, m x n row-major, leading dimension lda >= n, dtype a_dtype;
- *          base 16-byte aligned and lda * sizeof(dtype) a multiple of 16 (TMA rows).
+ *   A      device, m x n row-major, leading dimension lda >= n, dtype a_dtype.
+ *          The tensor-core passes read A with TMA and need a 16-byte aligned base and
+ *          lda * sizeof(dtype) a multiple of 16; mma = AUTO falls back to the SIMT
+ *          passes when that does not hold, an explicit TF32 mode returns ERR_ALIGN.
  *   a_tile_scales  FP8 only: ceil(m/128) x ceil(n/128) float scales (row-major); else NULL.
  *   Phi    device, the Gaussian test matrix Psi (Sec. III): n x l (RIGHT) or m x l
  *          (LEFT) row-major, ldphi >= l, F64 for a_dtype F64 else F32.

@@ -338,7 +338,13 @@ def factor_distance(U1, T1, V1, U2, T2, V2) -> float:
     """rho = ||U1 T1 V1^T - U2 T2 V2^T||_F / ||U2 T2 V2^T||_F, computed in a
     joint orthonormal basis so that small differences do not cancel:
     with Qu = orth([U1 U2]), Qv = orth([V1 V2]) the difference is
-    Qu (Qu^T U1 T1 V1^T Qv - Qu^T U2 T2 V2^T Qv) Qv^T."""
+    Qu (Qu^T U1 T1 V1^T Qv - Qu^T U2 T2 V2^T Qv) Qv^T.
+    When 2l exceeds a dimension the products are formed explicitly."""
+    l1, l2 = U1.shape[1], U2.shape[1]
+    if U1.shape[0] < l1 + l2 or V1.shape[0] < l1 + l2:
+        X1 = gemm(gemm(U1, T1), V1.T)
+        X2 = gemm(gemm(U2, T2), V2.T)
+        return float(np.linalg.norm(X1 - X2) / np.linalg.norm(X2))
     Qu, _ = householder_qr(np.hstack([U1, U2]))
     Qv, _ = householder_qr(np.hstack([V1, V2]))
     X1 = gemm(gemm(gemm(Qu.T, U1), T1), gemm(V1.T, Qv))

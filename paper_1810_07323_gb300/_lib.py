@@ -22,7 +22,7 @@ ERR_CHOL_BREAKDOWN, ERR_BUSY, PENDING, ERR_UNSUPPORTED = 7, 8, 9, 10
 SIDE = {"right": 0, "left": 1}
 CORE = {"exact": 0, "sketch": 1}
 DTYPE = {"f64": 0, "f32": 1, "bf16": 2, "fp8": 3}
-MMA = {"auto": 0, "tf32": 1, "tf32x3": 2, "simt": 3}
+MMA = {"auto": 0, "tf32": 1, "tf32x3": 2, "simt": 3, "tf32t": 4}
 DIR = {"ax": 0, "aty": 1}
 
 

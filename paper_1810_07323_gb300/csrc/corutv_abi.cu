@@ -62,6 +62,7 @@ constexpr int64_t kAlign = 256;
 inline int64_t ld_for(int64_t len) { return round_up(len < 1 ? 1 : len, 64); }
 inline int elem_bytes(int dt) { return dt == CORUTV_F64 ? 8 : (dt == CORUTV_F32 ? 4 : (dt == CORUTV_BF16 ? 2 : 1)); }
 inline int tc_bytes(int dt) { return dt == CORUTV_F64 ? 8 : 4; }   // sketch / compute precision
+inline bool aligned16(const void* ptr) { return ((uintptr_t)ptr & 15u) == 0; }
 
 struct Carve {
   char* base;
@@ -78,14 +79,14 @@ struct Carve {
 // Workspace of one solve.
 struct Plan {
   int64_t len1, len2;       // lengths of the first (C1) and second (C2) sketch
-  int64_t ld1, ld2, ld3;
+  int64_t ld1, ld2, ld3, ldr;
   int LP;                   // rows of every ST buffer (>= l, 128 on the tensor-core path)
   size_t pass_partials;
   int gparts;
   int fparts;
   // carved pointers
   DevStatus* status;
-  void *P1, *P2, *P3;
+  void *P1, *P2, *P3, *Xr;
   void* partials;
   void* gram_parts;
   double *G, *D, *Qt, *fro_parts;
@@ -100,6 +101,7 @@ size_t plan_layout(Plan& pl, void* base) {
   pl.P1 = c.take((size_t)pl.LP * pl.ld1 * tb);
   pl.P2 = c.take((size_t)pl.LP * pl.ld2 * tb);
   pl.P3 = c.take((size_t)pl.LP * pl.ld3 * tb);
+  pl.Xr = c.take((size_t)pl.LP * pl.ldr * 4);
   pl.partials = c.take(pl.pass_partials);
   pl.gram_parts = c.take((size_t)pl.gparts * kMaxL * kMaxL * tb);
   pl.G = static_cast<double*>(c.take(sizeof(double) * kMaxL * kMaxL));
@@ -140,6 +142,7 @@ void make_plan(const corutv_params* p, int sms, Plan& pl) {
   pl.ld1 = ld_for(pl.len1);
   pl.ld2 = ld_for(pl.len2);
   pl.ld3 = std::max(pl.ld1, pl.ld2);
+  pl.ldr = pl.ld3;
   pl.LP = kMaxL;
   pl.pass_partials = pass_partial_bytes(p->m, p->n, p->l, p->a_dtype, sms);
   pl.gparts = std::max(gram_parts(pl.len1, sms), gram_parts(pl.len2, sms));
@@ -154,18 +157,17 @@ int check_params(const corutv_params* p) {
   if (p->side != CORUTV_SIDE_RIGHT && p->side != CORUTV_SIDE_LEFT) return CORUTV_ERR_INVALID_ARG;
   if (p->core != CORUTV_CORE_EXACT && p->core != CORUTV_CORE_SKETCH) return CORUTV_ERR_INVALID_ARG;
   if (p->orth != CORUTV_ORTH_STABILISED) return CORUTV_ERR_INVALID_ARG;
-  if (p->mma < CORUTV_MMA_AUTO || p->mma > CORUTV_MMA_SIMT) return CORUTV_ERR_INVALID_ARG;
+  if (p->mma < CORUTV_MMA_AUTO || p->mma > CORUTV_MMA_TF32_TRUNC) return CORUTV_ERR_INVALID_ARG;
+  if (p->mma == CORUTV_MMA_TF32X3) return CORUTV_ERR_UNSUPPORTED;
   if (p->m <= 0 || p->n <= 0) return CORUTV_ERR_SHAPE;
   if (p->k < 1 || p->k > p->l) return CORUTV_ERR_INVALID_ARG;      // 1 <= k <= l (Sec. III)
   if (p->q < 0) return CORUTV_ERR_INVALID_ARG;
   if (p->l >= std::min(p->m, p->n)) return CORUTV_ERR_SHAPE;      // l < min(m, n) (Sec. III)
   if (p->l > (p->a_dtype == CORUTV_F64 ? kMaxL64 : kMaxL)) return CORUTV_ERR_SHAPE;
-  if (p->a_dtype == CORUTV_F64 && (p->mma == CORUTV_MMA_TF32 || p->mma == CORUTV_MMA_TF32X3))
+  if (p->a_dtype != CORUTV_F32 && (p->mma == CORUTV_MMA_TF32 || p->mma == CORUTV_MMA_TF32_TRUNC))
     return CORUTV_ERR_UNSUPPORTED;
   return CORUTV_OK;
 }
-
-inline bool aligned16(const void* ptr) { return ((uintptr_t)ptr & 15u) == 0; }
 
 int ensure_workspace(corutv_handle* h, size_t need) {
   if (h->ws && h->ws_bytes >= need) return CORUTV_OK;
@@ -234,14 +236,20 @@ struct PhaseTimer {
   } while (0)
 
 // engine choice for a pass
-int pick_mma(int a_dtype, int mma) {
-  if (a_dtype == CORUTV_F64) return CORUTV_MMA_SIMT;
-  if (mma == CORUTV_MMA_AUTO) return CORUTV_MMA_TF32;
+// engine for a pass; AUTO picks the tensor cores for FP32 A whose rows TMA can address
+int pick_mma(int a_dtype, int mma, bool tma_ok = true) {
+  if (a_dtype != CORUTV_F32) return CORUTV_MMA_SIMT;
+  if (mma == CORUTV_MMA_AUTO) return tma_ok ? CORUTV_MMA_TF32 : CORUTV_MMA_SIMT;
   return mma;
 }
 
+inline bool tma_rows_ok(const void* A, int64_t lda, int a_dtype) {
+  return aligned16(A) && (lda * elem_bytes(a_dtype)) % 16 == 0;
+}
+
 int run_pass(corutv_handle* h, int dir, int a_dtype, int mma, const void* A, int64_t lda, int64_t m, int64_t n,
-             const float* scales, const void* Xt, int64_t ldx, int l, void* Ct, int64_t ldc, void* partials) {
+             const float* scales, const void* Xt, int64_t ldx, int l, void* Ct, int64_t ldc, void* partials,
+             float* Xr, int64_t ldr, double* fro_parts) {
   PassArgs a{};
   a.A = A;
   a.lda = lda;
@@ -257,14 +265,28 @@ int run_pass(corutv_handle* h, int dir, int a_dtype, int mma, const void* A, int
   a.partials = partials;
   a.len_out = dir == CORUTV_DIR_AX ? m : n;
   a.K = dir == CORUTV_DIR_AX ? n : m;
-  const int eng = pick_mma(a_dtype, mma);
+  const int eng = pick_mma(a_dtype, mma, tma_rows_ok(A, lda, a_dtype));
+  if (eng != CORUTV_MMA_SIMT && !tma_rows_ok(A, lda, a_dtype)) return CORUTV_ERR_ALIGN;
   const double bytes = (double)m * n * elem_bytes(a_dtype) + (double)l * (a.K + a.len_out) * tc_bytes(a_dtype);
   PhaseTimer tm(h, kPhPass, bytes);
   if (eng == CORUTV_MMA_SIMT) {
+    if (fro_parts) return CORUTV_ERR_UNSUPPORTED;
     CU(launch_pass_simt(a, dir, a_dtype, h->sms, h->stream));
   } else {
     if (!tc_pass_supported(dir, a_dtype, eng, l)) return CORUTV_ERR_UNSUPPORTED;
-    CU(launch_pass_tc(a, dir, a_dtype, eng, h->sms, h->status, h->stream));
+    if (eng == CORUTV_MMA_TF32) {
+      // the sketch operand rounded to TF32 (nearest) once per pass; A is rounded tile by tile in the kernel
+      CU(launch_round_tf32(static_cast<const float*>(Xt), ldx, Xr, ldr, l, a.K, h->stream));
+      a.Xt = Xr;
+      a.ldx = ldr;
+    }
+    CU(launch_pass_tc(a, dir, a_dtype, eng, h->sms, h->status, fro_parts, h->stream));
+    if (fro_parts) {
+      sum_parts_kernel<<<1, 32, 0, h->stream>>>(fro_parts, tc_pass_grid(a.len_out, a.K, h->sms), nullptr,
+                                                h->status);
+      CORUTV_COUNT_LAUNCH();
+      CU(cudaGetLastError());
+    }
   }
   return CORUTV_OK;
 }
@@ -307,10 +329,14 @@ int solve_impl(corutv_handle* h, const corutv_params* p, const Plan& pl, const v
     PhaseTimer tm(h, kPhAsm);
     CU(launch_stage_transpose<TC>(static_cast<const TC*>(Phi), ldphi, pl.len2, l, P2, pl.ld2, h->stream));
   }
+  // S9: ||A||_F^2 fused into the first pass where the tensor-core engine runs it
+  const bool fuse_fro2 = p->want_fro2 && pick_mma(p->a_dtype, p->mma, tma_rows_ok(A, lda, p->a_dtype)) !=
+                                              CORUTV_MMA_SIMT;
+  float* Xr = static_cast<float*>(pl.Xr);
   for (int it = 0; it <= p->q; ++it) {
     // S1: C1 = A X  (Alg. 3 step 3)
     int rc = run_pass(h, dir1, p->a_dtype, p->mma, A, lda, p->m, p->n, scales, P2, pl.ld2, l, P1, pl.ld1,
-                      pl.partials);
+                      pl.partials, Xr, pl.ldr, (it == 0 && fuse_fro2) ? pl.fro_parts : nullptr);
     if (rc) return rc;
     ++passes;
     // S2: orth(C1)
@@ -318,7 +344,7 @@ int solve_impl(corutv_handle* h, const corutv_params* p, const Plan& pl, const v
     if (rc) return rc;
     // S3: C2 = A^T Q1  (Alg. 3 step 4)
     rc = run_pass(h, dir2, p->a_dtype, p->mma, A, lda, p->m, p->n, scales, P1, pl.ld1, l, P2, pl.ld2,
-                  pl.partials);
+                  pl.partials, Xr, pl.ldr, nullptr);
     if (rc) return rc;
     ++passes;
     if (it == p->q && p->core == CORUTV_CORE_SKETCH)
@@ -331,7 +357,7 @@ int solve_impl(corutv_handle* h, const corutv_params* p, const Plan& pl, const v
   // S5: core D = Q1^T A Q2 (Alg. 2 step 5)
   if (p->core == CORUTV_CORE_EXACT) {
     int rc = run_pass(h, dir1, p->a_dtype, p->mma, A, lda, p->m, p->n, scales, P2, pl.ld2, l, P3, pl.ld3,
-                      pl.partials);   // E = A Q2 (ST, len1)
+                      pl.partials, Xr, pl.ldr, nullptr);   // E = A Q2 (ST, len1)
     if (rc) return rc;
     ++passes;
     PhaseTimer tm(h, kPhCore);
@@ -358,7 +384,7 @@ int solve_impl(corutv_handle* h, const corutv_params* p, const Plan& pl, const v
     CU(launch_gather_cols<TC>(P2, pl.ld2, pl.len2, l, perm, static_cast<TC*>(U), ldu, h->stream));
   }
   // S9: ||A||_F^2 on request
-  if (p->want_fro2) {
+  if (p->want_fro2 && !fuse_fro2) {
     PhaseTimer tm(h, kPhFro2, (double)p->m * p->n * elem_bytes(p->a_dtype));
     CU(launch_fro2(p->a_dtype, A, lda, p->m, p->n, scales, cdiv(p->n, 128), pl.fro_parts, pl.fparts,
                    &pl.status->fro2_A, h->stream));
@@ -461,7 +487,9 @@ int corutv_solve(corutv_handle* h, const corutv_params* p, const void* A, int64_
   if (p->a_dtype == CORUTV_FP8_E4M3 && !a_tile_scales) return CORUTV_ERR_INVALID_ARG;
   const int l = p->l;
   if (lda < p->n || ldphi < l || ldu < l || ldt < l || ldv < l) return CORUTV_ERR_SHAPE;
-  if (!aligned16(A) || (lda * elem_bytes(p->a_dtype)) % 16) return CORUTV_ERR_ALIGN;
+  if (pick_mma(p->a_dtype, p->mma, tma_rows_ok(A, lda, p->a_dtype)) != CORUTV_MMA_SIMT &&
+      !tma_rows_ok(A, lda, p->a_dtype))
+    return CORUTV_ERR_ALIGN;
   Plan pl{};
   make_plan(p, h->sms, pl);
   const size_t need = plan_layout(pl, nullptr);
@@ -543,6 +571,7 @@ static int block_ws(corutv_handle* h, int64_t m, int64_t n, int l, int a_dtype, 
   pl.len1 = std::max(m, n);
   pl.len2 = pl.len1;
   pl.ld1 = pl.ld2 = pl.ld3 = 64;   // sketch buffers unused by the building blocks
+  pl.ldr = ld_for(std::max(m, n));
   pl.gparts = gram_parts(std::max(m, n), h->sms);
   const size_t need = plan_layout(pl, nullptr);
   int rc = ensure_workspace(h, need);
@@ -556,14 +585,14 @@ int corutv_pass(corutv_handle* h, int dir, int a_dtype, int mma, const void* A, 
                 const float* a_tile_scales, const void* Xt, int64_t ldx, int32_t l, void* Ct, int64_t ldc) {
   if (!h || !A || !Xt || !Ct) return CORUTV_ERR_INVALID_ARG;
   if (dir != CORUTV_DIR_AX && dir != CORUTV_DIR_ATY) return CORUTV_ERR_INVALID_ARG;
-  if (a_dtype < CORUTV_F64 || a_dtype > CORUTV_FP8_E4M3 || mma < 0 || mma > CORUTV_MMA_SIMT)
+  if (a_dtype < CORUTV_F64 || a_dtype > CORUTV_FP8_E4M3 || mma < 0 || mma > CORUTV_MMA_TF32_TRUNC)
     return CORUTV_ERR_INVALID_ARG;
-  if (a_dtype == CORUTV_F64 && (mma == CORUTV_MMA_TF32 || mma == CORUTV_MMA_TF32X3)) return CORUTV_ERR_UNSUPPORTED;
+  if (mma == CORUTV_MMA_TF32X3) return CORUTV_ERR_UNSUPPORTED;
+  if (a_dtype != CORUTV_F32 && (mma == CORUTV_MMA_TF32 || mma == CORUTV_MMA_TF32_TRUNC)) return CORUTV_ERR_UNSUPPORTED;
   if (a_dtype == CORUTV_FP8_E4M3 && !a_tile_scales) return CORUTV_ERR_INVALID_ARG;
   if (m <= 0 || n <= 0 || l < 1 || l > kMaxL || lda < n) return CORUTV_ERR_SHAPE;
   const int64_t klen = dir == CORUTV_DIR_AX ? n : m, olen = dir == CORUTV_DIR_AX ? m : n;
   if (ldx < klen || ldc < olen) return CORUTV_ERR_SHAPE;
-  if (!aligned16(A) || (lda * elem_bytes(a_dtype)) % 16) return CORUTV_ERR_ALIGN;
   if (!aligned16(Xt) || (ldx * tc_bytes(a_dtype)) % 16) return CORUTV_ERR_ALIGN;
   if (!aligned16(Ct) || (ldc * tc_bytes(a_dtype)) % 16) return CORUTV_ERR_ALIGN;
   Plan pl{};
@@ -571,7 +600,8 @@ int corutv_pass(corutv_handle* h, int dir, int a_dtype, int mma, const void* A, 
   if (rc) return rc;
   CU(cudaMemsetAsync(pl.status, 0, sizeof(DevStatus), h->stream));
   const int64_t l0 = launch_counter();
-  rc = run_pass(h, dir, a_dtype, mma, A, lda, m, n, a_tile_scales, Xt, ldx, l, Ct, ldc, pl.partials);
+  rc = run_pass(h, dir, a_dtype, mma, A, lda, m, n, a_tile_scales, Xt, ldx, l, Ct, ldc, pl.partials,
+                static_cast<float*>(pl.Xr), pl.ldr, nullptr);
   h->launches += launch_counter() - l0;
   h->have_last = true;
   h->last = corutv_params{};

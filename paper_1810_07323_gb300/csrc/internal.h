@@ -39,9 +39,13 @@ cudaError_t launch_streamk_reduce_f32(float* Ct, int64_t ldc, const float* P, in
 
 // pass_tc.cu (tcgen05 + TMA, FP32/BF16/FP8 A)
 size_t tc_pass_partial_bytes(int64_t len, int64_t K, int sms);
+int tc_pass_grid(int64_t len, int64_t K, int sms);
 bool tc_pass_supported(int dir, int a_dtype, int mma, int l);
 cudaError_t launch_pass_tc(const PassArgs& a, int dir, int a_dtype, int mma, int sms, DevStatus* status,
-                           cudaStream_t st);
+                           double* fro_parts, cudaStream_t st);
+cudaError_t launch_round_tf32(const float* X, int64_t ldx, float* Xr, int64_t ldr, int l, int64_t len,
+                              cudaStream_t st);
+__global__ void sum_parts_kernel(const double* __restrict__ parts, int n, double* out, DevStatus* status);
 
 // small.cu
 template <typename TC>

@@ -2,13 +2,16 @@
 // Sec. III (C1 = A Psi, C2 = A^T C1) and Alg. 3 steps 3-4, as
 //     Ct (l x len) = Xt (l x K) * op(A)
 // with the l sketch columns as the MMA M dimension (M = 128) and A as the
-// N x K operand:
-//   dir AX : op(A) = A^T, B operand = A rows    (K-major, K = n)
-//   dir ATY: op(A) = A,   B operand = A columns (MN-major, K = m)
+// N x K operand, K-major in shared memory for both directions:
+//   dir AX : op(A) = A^T, B operand = A rows (TMA delivers them K-major, K = n)
+//   dir ATY: op(A) = A,   B operand = A columns (TMA delivers 32-row x 32-column
+//            boxes; the converter warps transpose each tile in shared memory, K = m)
 // A is streamed HBM -> shared memory by TMA (128-byte swizzle), consumed by
 // tcgen05.mma kind::tf32 issued from one thread, accumulated in TMEM (two
 // 128 x 256 FP32 accumulators, so the epilogue of one tile overlaps the
-// products of the next), and written out by four epilogue warps.
+// products of the next), and written out by four epilogue warps.  Converter
+// warps round A tiles to TF32 (nearest), transpose A^T tiles and accumulate
+// ||A||_F^2 where those are asked for.
 // The (tile, k-block) space is split Stream-K style over one CTA per SM;
 // tiles shared by several CTAs go through the ordered partial reduction.
 //
@@ -35,7 +38,8 @@ constexpr int kATileBytes = kTcBN * kTcBK * 4;   // 32 KB
 constexpr int kXTileBytes = kTcM * kTcBK * 4;    // 16 KB
 constexpr int kStageBytes = kATileBytes + kXTileBytes;
 constexpr int kThreads = 192;       // warp 0 TMA, warp 1 MMA, warps 2..5 epilogue
-constexpr int kSmemBytes = kStages * kStageBytes + 1024 /*align*/ + 256 /*barriers*/;
+constexpr int kThreadsMax = 320;    // + warps 6..9: TF32 rounding / ||A||^2 of each A tile
+constexpr int kSmemBytes = kStages * kStageBytes + 1024 /*align*/ + 512 /*barriers, reductions*/;
 
 // ------------------------------------------------------------------ PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -155,6 +159,21 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ float sel_comp(const float4& v, int j) {
+  float r = v.x;
+  r = (j == 1) ? v.y : r;
+  r = (j == 2) ? v.z : r;
+  r = (j == 3) ? v.w : r;
+  return r;
+}
+
+// FP32 -> TF32, round to nearest (ties away from zero); low 13 bits become zero.
+__device__ __forceinline__ float to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
 struct TcArgs {
   float* Ct;
   int64_t ldc;
@@ -162,22 +181,31 @@ struct TcArgs {
   int64_t len, K;
   int l;
   DevStatus* status;
+  double* fro_parts;   // per-CTA sum(a^2) when fused, else null
 };
 
 // ------------------------------------------------------------------ kernel
-template <int DIR>
-__global__ void __launch_bounds__(kThreads, 1)
+// CONV: warps 6..9 round every A tile in shared memory to TF32 (round to
+//       nearest, ties away) before the MMA reads it, so the tensor core's
+//       truncation of the low 13 bits is exact and the products carry no
+//       systematic shrink.
+// FRO:  the same warps accumulate sum(a^2) of the original tile values
+//       (FP32 per stage, folded into FP64), one partial per CTA.
+template <int DIR, bool CONV, bool FRO>
+__global__ void __launch_bounds__(kThreadsMax, 1)
     pass_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapX, TcArgs args) {
+  constexpr bool kConvWarps = CONV || FRO || DIR == 1;   // A^T tiles are always transposed in shared memory
   extern __shared__ uint8_t smem_dyn[];
   // 128-byte-swizzled tiles need 1024-byte aligned shared addresses
   uint8_t* smem = smem_dyn + ((1024u - (smem_u32(smem_dyn) & 1023u)) & 1023u);
   uint8_t* a_tiles = smem;                                   // kStages x 32 KB
   uint8_t* x_tiles = smem + kStages * kATileBytes;           // kStages x 16 KB
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
-  // bars: full[S], empty[S], tfull[2], tempty[2]; then the TMEM address
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 4);
-  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + kStages);
-  const uint32_t tfull0 = smem_u32(bars + 2 * kStages), tempty0 = smem_u32(bars + 2 * kStages + 2);
+  // bars: full[S], empty[S], conv[S], tfull[2], tempty[2]; then the TMEM address
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * kStages + 4);
+  double* fro_red = reinterpret_cast<double*>(bars + 3 * kStages + 6);   // 4 doubles + abort flag
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + kStages), conv0 = smem_u32(bars + 2 * kStages);
+  const uint32_t tfull0 = smem_u32(bars + 3 * kStages), tempty0 = smem_u32(bars + 3 * kStages + 2);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t KB = cdiv(args.K, kTcBK);
@@ -188,6 +216,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int i = 0; i < kStages; ++i) {
       mbar_init(full0 + 8 * i, 1);
       mbar_init(empty0 + 8 * i, 1);
+      mbar_init(conv0 + 8 * i, 4);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(tfull0 + 8 * b, 1);
@@ -246,7 +275,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == 1) {
     // ---------------------------------------------------------------- MMA issuer
     if (lane == 0) {
-      constexpr uint32_t idesc = idesc_tf32(kTcM, kTcBN, 0, DIR == 1 ? 1 : 0);
+      constexpr uint32_t idesc = idesc_tf32(kTcM, kTcBN, 0, 0);   // both operands K-major
+      const uint32_t ready0 = kConvWarps ? conv0 : full0;
       int64_t n = 0;     // fills consumed
       int seg = 0;       // tile segments started
       bool ok = true;
@@ -263,16 +293,14 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (; it < t * KB + kb1; ++it, ++n) {
           const int stage = (int)(n % kStages);
           const uint32_t ph = (uint32_t)((n / kStages) & 1);
-          if (!mbar_wait(full0 + 8 * stage, ph, args.status)) { ok = false; break; }
+          if (!mbar_wait(ready0 + 8 * stage, ph, args.status)) { ok = false; break; }
           tc_fence_after();
           const uint32_t abase = smem_u32(a_tiles + stage * kATileBytes);
           const uint32_t xbase = smem_u32(x_tiles + stage * kXTileBytes);
 #pragma unroll
           for (int kk = 0; kk < kTcBK / 8; ++kk) {
             const uint64_t adesc = smem_desc(xbase + kk * 32, 16, 1024);
-            uint64_t bdesc;
-            if (DIR == 0) bdesc = smem_desc(abase + kk * 32, 16, 1024);
-            else bdesc = smem_desc(abase + kk * 1024, kTcBK * 128, 1024);
+            const uint64_t bdesc = smem_desc(abase + kk * 32, 16, 1024);
             mma_tf32(tacc, adesc, bdesc, idesc, (first && kk == 0) ? 0u : 1u);
           }
           first = false;
@@ -283,7 +311,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         ++seg;
       }
     }
-  } else {
+  } else if (warp < 6) {
     // ---------------------------------------------------------------- epilogue (warps 2..5)
     const int g = warp & 3;                  // TMEM lane quarter this warp may access
     const int j = 32 * g + lane;             // output row (sketch column)
@@ -331,10 +359,88 @@ __global__ void __launch_bounds__(kThreads, 1)
       ++seg;
       it = t * KB + kb1;
     }
+  } else if (kConvWarps) {
+    // ---------------------------------------------------------------- converter (warps 6..9)
+    const int ct = threadIdx.x - 192;       // 0..127
+    volatile int* conv_abort = reinterpret_cast<volatile int*>(fro_red + 4);
+    if (ct == 0) *conv_abort = 0;
+    asm volatile("bar.sync 1, 128;" ::: "memory");
+    double fro = 0.0;
+    int64_t n = 0;
+    for (int64_t it = s; it < e; ++it, ++n) {
+      const int stage = (int)(n % kStages);
+      const uint32_t ph = (uint32_t)((n / kStages) & 1);
+      if (DIR == 0) {
+        if (!mbar_wait(full0 + 8 * stage, ph, args.status)) break;
+      } else {
+        // the transpose synchronises the four converter warps: they give up together
+        if (!mbar_wait(full0 + 8 * stage, ph, args.status)) *conv_abort = 1;
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+        if (*conv_abort) break;
+      }
+      uint8_t* tile = a_tiles + stage * kATileBytes;
+      float part = 0.f;
+      if (DIR == 0) {
+        // rows of A are already K-major: round in place
+        float4* a4 = reinterpret_cast<float4*>(tile);
+#pragma unroll 4
+        for (int q = ct; q < kATileBytes / 16; q += 128) {
+          float4 v = a4[q];
+          if (FRO) part = fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, fmaf(v.w, v.w, part))));
+          if (CONV) {
+            v.x = to_tf32(v.x); v.y = to_tf32(v.y); v.z = to_tf32(v.z); v.w = to_tf32(v.w);
+            a4[q] = v;
+          }
+        }
+      } else {
+        // A^T tile: loaded as 8 column chunks [c][k][32 n] (128-byte swizzle); rewrite it in
+        // place as the K-major tile [n][32 k] the MMA reads.  Thread block b covers
+        // k = 4 kb .. 4 kb + 3, n = 4 nb .. 4 nb + 3 (kb = q / 64, nb = q % 64).
+        float4 blk[4][4];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const int q = ct + 128 * b, kb = q >> 6, nb = q & 63;
+          const int c = nb >> 3, ch = nb & 7;
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int k = 4 * kb + i;
+            blk[b][i] = *reinterpret_cast<const float4*>(tile + c * 4096 + k * 128 + ((ch ^ (k & 7)) << 4));
+          }
+        }
+        // all four converter warps must finish reading before anyone overwrites the tile
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const int q = ct + 128 * b, kb = q >> 6, nb = q & 63;
+#pragma unroll
+          for (int jj = 0; jj < 4; ++jj) {
+            const int j = (jj + (nb >> 1)) & 3;        // rotate rows: conflict-free stores
+            float4 v;
+            v.x = sel_comp(blk[b][0], j); v.y = sel_comp(blk[b][1], j);
+            v.z = sel_comp(blk[b][2], j); v.w = sel_comp(blk[b][3], j);
+            if (FRO) part = fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, fmaf(v.w, v.w, part))));
+            if (CONV) { v.x = to_tf32(v.x); v.y = to_tf32(v.y); v.z = to_tf32(v.z); v.w = to_tf32(v.w); }
+            const int nrow = 4 * nb + j;
+            *reinterpret_cast<float4*>(tile + nrow * 128 + ((kb ^ (nrow & 7)) << 4)) = v;
+          }
+        }
+      }
+      fro += (double)part;
+      // generic-proxy writes must be visible to the tensor core (async proxy)
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(conv0 + 8 * stage);
+    }
+    if (FRO) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) fro += __shfl_xor_sync(0xffffffffu, fro, o);
+      if (lane == 0) fro_red[warp - 6] = fro;
+    }
   }
 
   tc_fence_before();
   __syncthreads();
+  if (FRO && threadIdx.x == 0) args.fro_parts[blockIdx.x] = (fro_red[0] + fro_red[1]) + (fro_red[2] + fro_red[3]);
   if (warp == 1) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem_base) : "memory");
@@ -379,12 +485,40 @@ size_t tc_pass_partial_bytes(int64_t len, int64_t K, int sms) {
   return (size_t)2 * sms * kTcM * kTcBN * sizeof(float);
 }
 
+int tc_pass_grid(int64_t len, int64_t K, int sms) {
+  const int64_t total = cdiv(len, kTcBN) * cdiv(K, kTcBK);
+  return (int)(sms < total ? sms : total);
+}
+
+// mma 1: TF32 with operands rounded to nearest (A in shared memory, X by the caller);
+// mma 4: TF32 as the tensor core truncates (no conversion).
 bool tc_pass_supported(int dir, int a_dtype, int mma, int l) {
-  return (dir == 0 || dir == 1) && a_dtype == 1 && mma == 1 && l >= 1 && l <= kTcM;
+  return (dir == 0 || dir == 1) && a_dtype == 1 && (mma == 1 || mma == 4) && l >= 1 && l <= kTcM;
+}
+
+template <int DIR, bool CONV, bool FRO>
+static cudaError_t launch_variant(const CUtensorMap& mapA, const CUtensorMap& mapX, const TcArgs& ta, int64_t G,
+                                  cudaStream_t st) {
+  auto kern = pass_tc_kernel<DIR, CONV, FRO>;
+  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+  if (err != cudaSuccess) return err;
+  const int threads = (CONV || FRO || DIR == 1) ? kThreadsMax : kThreads;
+  kern<<<(unsigned)G, threads, kSmemBytes, st>>>(mapA, mapX, ta);
+  CORUTV_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
+
+template <int DIR>
+static cudaError_t launch_dir_tc(const CUtensorMap& mapA, const CUtensorMap& mapX, const TcArgs& ta, bool conv,
+                                 bool fro, int64_t G, cudaStream_t st) {
+  if (conv && fro) return launch_variant<DIR, true, true>(mapA, mapX, ta, G, st);
+  if (conv) return launch_variant<DIR, true, false>(mapA, mapX, ta, G, st);
+  if (fro) return launch_variant<DIR, false, true>(mapA, mapX, ta, G, st);
+  return launch_variant<DIR, false, false>(mapA, mapX, ta, G, st);
 }
 
 cudaError_t launch_pass_tc(const PassArgs& a, int dir, int a_dtype, int mma, int sms, DevStatus* status,
-                           cudaStream_t st) {
+                           double* fro_parts, cudaStream_t st) {
   if (!tc_pass_supported(dir, a_dtype, mma, a.l)) return cudaErrorInvalidValue;
   CUtensorMap mapA, mapX;
   // A: m rows x n cols (row-major, lda)
@@ -395,25 +529,34 @@ cudaError_t launch_pass_tc(const PassArgs& a, int dir, int a_dtype, int mma, int
   }
   // Xt: l rows x K cols; the 128-row box reads zeros below row l
   if (!make_map(&mapX, a.Xt, a.l, a.K, a.ldx, kTcBK, kTcM)) return cudaErrorInvalidValue;
-  const int64_t total = cdiv(a.len_out, kTcBN) * cdiv(a.K, kTcBK);
-  int64_t G = sms < total ? sms : total;
+  const int64_t G = tc_pass_grid(a.len_out, a.K, sms);
   if (G <= 0) return cudaSuccess;
-  TcArgs ta{static_cast<float*>(a.Ct), a.ldc, static_cast<float*>(a.partials), a.len_out, a.K, a.l, status};
-  cudaError_t err;
-  if (dir == 0) {
-    err = cudaFuncSetAttribute(pass_tc_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
-    if (err != cudaSuccess) return err;
-    pass_tc_kernel<0><<<(unsigned)G, kThreads, kSmemBytes, st>>>(mapA, mapX, ta); CORUTV_COUNT_LAUNCH();
-  } else {
-    err = cudaFuncSetAttribute(pass_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
-    if (err != cudaSuccess) return err;
-    pass_tc_kernel<1><<<(unsigned)G, kThreads, kSmemBytes, st>>>(mapA, mapX, ta); CORUTV_COUNT_LAUNCH();
-  }
-  err = cudaGetLastError();
+  TcArgs ta{static_cast<float*>(a.Ct), a.ldc, static_cast<float*>(a.partials), a.len_out, a.K, a.l, status,
+            fro_parts};
+  const bool conv = (mma == 1), fro = fro_parts != nullptr;
+  cudaError_t err = dir == 0 ? launch_dir_tc<0>(mapA, mapX, ta, conv, fro, G, st)
+                             : launch_dir_tc<1>(mapA, mapX, ta, conv, fro, G, st);
   if (err != cudaSuccess) return err;
   // ordered reduction of split tiles
   return launch_streamk_reduce_f32(static_cast<float*>(a.Ct), a.ldc, static_cast<const float*>(a.partials), a.l,
                                    kTcM, kTcBN, a.len_out, cdiv(a.K, kTcBK), G, st);
+}
+
+// Xr = TF32(X) rounded to nearest, l rows of `len` (the sketch operand of a rounded pass).
+__global__ void round_tf32_kernel(const float* __restrict__ X, int64_t ldx, float* __restrict__ Xr, int64_t ldr,
+                                  int l, int64_t len) {
+  const int j = blockIdx.y;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x)
+    Xr[j * ldr + i] = to_tf32(X[j * ldx + i]);
+}
+
+cudaError_t launch_round_tf32(const float* X, int64_t ldx, float* Xr, int64_t ldr, int l, int64_t len,
+                              cudaStream_t st) {
+  dim3 grid((unsigned)(cdiv(len, 256) < 64 ? cdiv(len, 256) : 64), (unsigned)l);
+  if (grid.x == 0) return cudaSuccess;
+  round_tf32_kernel<<<grid, 256, 0, st>>>(X, ldx, Xr, ldr, l, len);
+  CORUTV_COUNT_LAUNCH();
+  return cudaGetLastError();
 }
 
 }  // namespace corutv

@@ -6,9 +6,10 @@ Primary parity measure (pivot- and sign-invariant, Sec. III: A ~ U T V^T):
 Tolerances, derived from the arithmetic of each engine:
   FP64 (SIMT, FP64 factorisations):     rho <= 1e-10
   FP32 SIMT products, FP32 factorisations: rho <= 1e-4
-  TF32 tensor-core products (operands keep 10 mantissa bits, products
-  truncated toward zero: up to ~2^-10 relative per product, a systematic
-  shrink of ~3.5e-4 on average): rho <= 5e-3
+  TF32 tensor-core products with operands rounded to nearest ("tf32": errors
+  up to 2^-10 relative per product, zero mean): rho <= 1e-3
+  TF32 products of raw FP32 operands ("tf32t": the tensor core truncates both
+  operands, a systematic shrink of ~7e-4 on average): rho <= 5e-3
 Structure is checked exactly where the method fixes it (T triangular,
 diag(T) >= 0 non-increasing, perm a permutation, V = Q2 P~ up to FP error).
 """
@@ -24,11 +25,14 @@ pytestmark = pytest.mark.gpu
 if torch.cuda.is_available():
     from paper_1810_07323_gb300 import corutv
 
-TOL = {"f64": 1e-10, "simt": 1e-4, "tf32": 5e-3}
+TOL = {"f64": 1e-10, "simt": 1e-4, "tf32": 1e-3, "tf32t": 5e-3}
 
 
 def _run(A, phi, k, l, q, dt, mma="auto", side="right", core="exact", want_fro2=False):
-    Ad = torch.tensor(A, dtype=torch.float64, device="cuda").to(dt)
+    m, n = A.shape
+    lda = -(-n // 8) * 8 + 8          # padded rows: a 16-byte pitch for TMA and lda > n
+    Ad = torch.zeros((m, lda), dtype=dt, device="cuda")[:, :n]
+    Ad.copy_(torch.tensor(A, dtype=torch.float64, device="cuda").to(dt))
     Pd = torch.tensor(phi, dtype=torch.float64, device="cuda").to(dt)
     r = corutv.solve(Ad, Pd, k, l, q, side=side, core=core, mma=mma, want_fro2=want_fro2)
     assert r.info.status == 0, corutv.status_string(r.info.status)
@@ -101,7 +105,7 @@ def slice2():
     return g.block(0, 4000, 0, 4000), W.phi(20000, 120)[:4000]
 
 
-@pytest.mark.parametrize("mma", ["tf32", "simt"])
+@pytest.mark.parametrize("mma", ["tf32", "tf32t", "simt"])
 @pytest.mark.parametrize("q", [0, 1, 2])
 def test_config2_slice_fp32_parity(slice2, mma, q):
     A, phi = slice2
@@ -115,7 +119,7 @@ def test_config2_slice_fp32_parity(slice2, mma, q):
     # rank-k error at most 1.05 x the oracle's (plus the engine's rounding floor)
     ek = O.fro_residual(A32, U, T, V, k=100)
     ek_ref = O.fro_residual(A32, ref["U"], ref["T"], ref["V"], k=100)
-    floor = (2.0 ** -10 if mma == "tf32" else 1e-6) * np.linalg.norm(A32)
+    floor = (2.0 ** -10 if mma.startswith("tf32") else 1e-6) * np.linalg.norm(A32)
     assert ek <= 1.05 * ek_ref + floor
 
 
@@ -176,7 +180,7 @@ def test_config2_full_size_properties():
     P64 = phi_d.double().cpu().numpy()
     ref = A_rows @ P64
     got = C1t[:, rows].double().cpu().numpy().T
-    assert np.all(np.abs(got - ref) <= 2.5 * 2.0 ** -10 * (np.abs(A_rows) @ np.abs(P64)))
+    assert np.all(np.abs(got - ref) <= 1.25 * 2.0 ** -10 * (np.abs(A_rows) @ np.abs(P64)))
     # the solve
     r = corutv.solve(A, phi_d, 100, 120, 1, want_fro2=True)
     assert r.info.status == 0
@@ -191,7 +195,11 @@ def test_config2_full_size_properties():
         blk = A[a:a + 2000].double() - (U[a:a + 2000].double() @ T) @ V.double().T
         res2 += float((blk * blk).sum())
     a2 = r.info.fro2_A
-    assert abs((a2 - r.info.fro2_T) - res2) < 2e-3 * a2
+    print(f"full size: ||A||^2 = {a2:.6e}, ||A||^2 - ||T||^2 = {a2 - r.info.fro2_T:.4e}, explicit {res2:.4e}")
+    assert abs(a2 - float((A.double() ** 2).sum())) < 1e-6 * a2
+    # Pythagorean readout: a2 - ||T||^2 = ||A - U T V^T||^2 - 2 <T, dT> - ||dT||^2 where dT is the
+    # core's TF32 error (|dT| <= 3e-4 |T| per the pass bound): |readout - explicit| <= 6e-4 ||A||^2
+    assert abs((a2 - r.info.fro2_T) - res2) < 6e-4 * a2
     # closed-form spectrum of the noise-free part: Eckart-Young floor and near-optimality
     R1 = O.householder_qr(g.g1(0, g.m))[1]
     R2 = O.householder_qr(g.g2(0, g.n))[1]
