@@ -233,6 +233,39 @@ int corutv_qrcp(corutv_handle* h, int dtype, const double* D, int64_t ldd, int32
 int corutv_fro2(corutv_handle* h, int a_dtype, const void* A, int64_t lda,
                 int64_t m, int64_t n, const float* a_tile_scales, double* out);
 
+/* ------------------------------------------------------------------------
+ * Allocation-free variant (no counterpart in the paper).
+ * ---------------------------------------------------------------------- */
+
+/* Size of the device array that corutv_gram_noalloc uses for its partial sums.
+ * Every GPU that loads the library holds it until the process exits. */
+#define CORUTV_NOALLOC_SCRATCH_BYTES (4u << 20)
+
+/*
+ * corutv_gram_noalloc -- the product G = X Y^T of corutv_gram (l x l, FP64,
+ * row-major, ld l, from skinny-transposed Xt, Yt of l rows and `len` columns,
+ * dtype F32 or F64) for callers that must not allocate device memory after
+ * start-up: a latency-bound loop in which cudaMalloc could synchronise the
+ * device, or a process whose device memory belongs to another allocator (a
+ * framework's caching pool) where an extra cudaMalloc may fail or fragment it.
+ *
+ *   - It takes a stream (cudaStream_t as void*) instead of a handle and calls
+ *     no cudaMalloc, cudaFree or allocating library routine.  Inputs and the
+ *     output G are the caller's device memory.
+ *   - Partial sums go to a fixed device array of CORUTV_NOALLOC_SCRATCH_BYTES
+ *     (32 partial blocks of up to 128 x 128 FP64): l > 128 is rejected with
+ *     CORUTV_ERR_SHAPE.  The array is fully rewritten by each call, so nothing
+ *     has to be cleared between calls.
+ *   - The first call on a device looks up the array's device address with that
+ *     device current (cudaGetSymbolAddress) and caches it; make that first call
+ *     before any stream capture.
+ *   - All calls on a device share the one array: calls whose work overlaps on
+ *     the GPU (different streams, or different host threads) race and give wrong
+ *     results.  Serialise them.
+ */
+int corutv_gram_noalloc(void* stream, int dtype, const void* Xt, int64_t ldx, const void* Yt, int64_t ldy,
+                        int64_t len, int32_t l, double* G);
+
 #ifdef __cplusplus
 }
 #endif

@@ -62,7 +62,7 @@ _lib = None
 EXPORTS = ("corutv_version", "corutv_status_string", "corutv_create", "corutv_destroy", "corutv_set_stream",
            "corutv_workspace_size", "corutv_set_workspace", "corutv_solve", "corutv_info_wait",
            "corutv_set_tracing", "corutv_trace_read", "corutv_pass", "corutv_orthonormalize", "corutv_gram",
-           "corutv_qrcp", "corutv_fro2")
+           "corutv_qrcp", "corutv_fro2", "corutv_gram_noalloc")
 
 
 def load() -> ctypes.CDLL:
@@ -90,6 +90,8 @@ def load() -> ctypes.CDLL:
     lib.corutv_gram.argtypes = [P, ctypes.c_int, P, I64, P, I64, I64, I32, P]
     lib.corutv_qrcp.argtypes = [P, ctypes.c_int, P, I64, I32, I32, P, P, P, P]
     lib.corutv_fro2.argtypes = [P, ctypes.c_int, P, I64, I64, I64, P, P]
+    lib.corutv_gram_noalloc.argtypes = [P, ctypes.c_int, P, I64, P, I64, I64, I32, P]
+    lib.corutv_gram_noalloc.restype = ctypes.c_int
     lib.corutv_set_tracing.argtypes = [P, ctypes.c_int]
     lib.corutv_trace_read.argtypes = [P, ctypes.POINTER(Trace)]
     for name in ("corutv_set_tracing", "corutv_trace_read", "corutv_create", "corutv_destroy", "corutv_set_stream", "corutv_workspace_size",
@@ -313,6 +315,22 @@ def gram(Xt, Yt, length: int, l: int, handle: Handle | None = None):
                             ctypes.c_void_p(G.data_ptr()))
     _check(rc, "corutv_gram")
     return G
+
+
+def gram_noalloc(Xt, Yt, length: int, l: int, out, stream=None):
+    """corutv_gram_noalloc: G = X Y^T into the caller's float64 (l x l) device
+    tensor `out`, without any device allocation by the library (its partial
+    sums use a fixed device array shared by all calls on the device)."""
+    import torch
+    _need_cuda(Xt, Yt, out)
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    rc = load().corutv_gram_noalloc(ctypes.c_void_p(stream.cuda_stream), _dt_code(Xt),
+                                    ctypes.c_void_p(Xt.data_ptr()), _rowmajor_ld(Xt),
+                                    ctypes.c_void_p(Yt.data_ptr()), _rowmajor_ld(Yt), int(length), int(l),
+                                    ctypes.c_void_p(out.data_ptr()))
+    _check(rc, "corutv_gram_noalloc")
+    return out
 
 
 def qrcp(D, k: int | None = None, dtype: str = "f64", handle: Handle | None = None):
