@@ -578,6 +578,10 @@ static int block_ws(corutv_handle* h, int64_t m, int64_t n, int l, int a_dtype, 
   if (rc) return rc;
   plan_layout(pl, h->ws);
   h->status = pl.status;
+  // the building blocks report through the same status block as a solve
+  h->have_last = true;
+  h->last = corutv_params{};
+  h->last_passes = 0;
   return CORUTV_OK;
 }
 

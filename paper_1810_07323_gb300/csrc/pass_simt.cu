@@ -111,19 +111,42 @@ __global__ void __launch_bounds__(256) pass_simt_kernel(PassArgs args) {
 
 // Ordered sum of Stream-K partial tiles: tile t (BN output positions, LP rows)
 // split across workers cf..cl is the sum of their slots in worker order.
+// Block (t, g) handles rows 16 g .. 16 g + 15 of tile t; the slot list is
+// resolved once per block.
 template <typename TC>
-__global__ void streamk_reduce_kernel(TC* __restrict__ Ct, int64_t ldc, const TC* __restrict__ P, int l, int LP,
-                                      int BN, int64_t len, int64_t KB, int64_t G) {
+__global__ void __launch_bounds__(256) streamk_reduce_kernel(TC* __restrict__ Ct, int64_t ldc,
+                                                             const TC* __restrict__ P, int l, int LP, int BN,
+                                                             int64_t len, int64_t KB, int64_t G) {
+  constexpr int kMaxSplit = 64;
+  __shared__ int64_t slot_off[kMaxSplit];
+  __shared__ int nsplit;
   StreamK sk((len + BN - 1) / BN, KB, G);
   const int64_t t = blockIdx.x;
-  const int64_t cf = sk.owner(t * KB), cl = sk.owner(t * KB + KB - 1);
-  if (cf == cl) return;  // written directly by its only worker
-  for (int x = threadIdx.x; x < l * BN; x += blockDim.x) {
-    const int j = x / BN, ii = x % BN;
-    const int64_t gi = t * BN + ii;
-    if (gi >= len) continue;
+  const int row0 = blockIdx.y * 16;
+  if (row0 >= l) return;
+  if (threadIdx.x == 0) {
+    const int64_t cf = sk.owner(t * KB), cl = sk.owner(t * KB + KB - 1);
+    int ns = (int)(cl - cf + 1);
+    if (cf == cl) ns = 0;                        // written directly by its only worker
+    if (ns > kMaxSplit) ns = -1;                 // never happens for the grids used here
+    nsplit = ns;
+    for (int i = 0; i < ns && i < kMaxSplit; ++i) slot_off[i] = (int64_t)sk.slot(cf + i, t) * LP * BN;
+  }
+  __syncthreads();
+  const int ns = nsplit;
+  if (ns == 0) return;
+  const int64_t p0 = t * BN;
+  for (int x = threadIdx.x; x < 16 * BN; x += blockDim.x) {
+    const int j = row0 + x / BN, ii = x % BN;
+    const int64_t gi = p0 + ii;
+    if (j >= l || gi >= len) continue;
     TC sum = TC(0);
-    for (int64_t c = cf; c <= cl; ++c) sum += P[((int64_t)sk.slot(c, t) * LP + j) * BN + ii];
+    if (ns > 0) {
+      for (int c = 0; c < ns; ++c) sum += P[slot_off[c] + (int64_t)j * BN + ii];
+    } else {
+      const int64_t cf = sk.owner(t * KB), cl = sk.owner(t * KB + KB - 1);
+      for (int64_t c = cf; c <= cl; ++c) sum += P[((int64_t)sk.slot(c, t) * LP + j) * BN + ii];
+    }
     Ct[j * ldc + gi] = sum;
   }
 }
@@ -136,7 +159,8 @@ template __global__ void streamk_reduce_kernel<double>(double*, int64_t, const d
 cudaError_t launch_streamk_reduce_f32(float* Ct, int64_t ldc, const float* P, int l, int LP, int BN, int64_t len,
                                       int64_t KB, int64_t G, cudaStream_t st) {
   const int64_t tiles = cdiv(len, BN);
-  if (tiles > 0) { streamk_reduce_kernel<float><<<(unsigned)tiles, 256, 0, st>>>(Ct, ldc, P, l, LP, BN, len, KB, G); CORUTV_COUNT_LAUNCH(); }
+  dim3 grid((unsigned)tiles, (unsigned)cdiv(l, 16));
+  if (tiles > 0) { streamk_reduce_kernel<float><<<grid, 256, 0, st>>>(Ct, ldc, P, l, LP, BN, len, KB, G); CORUTV_COUNT_LAUNCH(); }
   return cudaGetLastError();
 }
 
@@ -178,12 +202,13 @@ cudaError_t launch_pass_simt(const PassArgs& a, int dir, int a_dtype, int sms, c
   if (err != cudaSuccess) return err;
   const int LP = a.l <= 32 ? 32 : (a.l <= 64 ? 64 : 128);
   const int64_t tiles = cdiv(a.len_out, kBN), KB = cdiv(a.K, kBK);
+  const dim3 rgrid((unsigned)tiles, (unsigned)cdiv(a.l, 16));
   if (a_dtype == 0) {
-    streamk_reduce_kernel<double><<<(unsigned)tiles, 256, 0, st>>>(static_cast<double*>(a.Ct), a.ldc,
+    streamk_reduce_kernel<double><<<rgrid, 256, 0, st>>>(static_cast<double*>(a.Ct), a.ldc,
                                                                    static_cast<const double*>(a.partials), a.l, LP,
                                                                    kBN, a.len_out, KB, G);
   } else {
-    streamk_reduce_kernel<float><<<(unsigned)tiles, 256, 0, st>>>(static_cast<float*>(a.Ct), a.ldc,
+    streamk_reduce_kernel<float><<<rgrid, 256, 0, st>>>(static_cast<float*>(a.Ct), a.ldc,
                                                                   static_cast<const float*>(a.partials), a.l, LP,
                                                                   kBN, a.len_out, KB, G);
   }

@@ -15,66 +15,89 @@
 
 namespace corutv {
 
+constexpr int kCholTPR = 8;   // threads per row of the register Cholesky (1024 threads)
+constexpr int kQrcpTPC = 8;   // threads per column of the register QRCP (1024 threads)
+
 // =============================================================================== Gram
 // parts[c] = X[:, cols_c] Y[:, cols_c]^T over the c-th contiguous column range.
-template <typename TC, int JPT>
+// Outer-product tiling: thread (tx, ty) owns rows a = R ty + (0..R-1) and
+// columns b = R tx + (0..R-1) (R = LP / 16); the stage holds X and Y
+// transposed in shared memory (k-major rows padded by 4) so each k step is
+// two R-wide vector loads and R^2 FMAs.
+template <typename TC, int LP>
 __global__ void __launch_bounds__(256) gram_partial_kernel(const TC* __restrict__ Xt, int64_t ldx,
                                                            const TC* __restrict__ Yt, int64_t ldy, int64_t len,
                                                            int l, TC* __restrict__ parts) {
-  constexpr int LP = 16 * JPT;
+  constexpr int R = LP / 16;
   constexpr int BK = 32;
-  __shared__ TC Xs[LP][BK + 1];
-  __shared__ TC Ys[LP][BK + 1];
-  const int tid = threadIdx.x, ti = tid & 15, tj = tid >> 4;
+  constexpr int LPP = LP + 4;
+  __shared__ __align__(16) TC Xs[BK][LPP];
+  __shared__ __align__(16) TC Ys[BK][LPP];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int64_t chunk = cdiv(cdiv(len, BK), gridDim.x) * BK;
   const int64_t c0 = blockIdx.x * chunk;
   int64_t c1 = c0 + chunk;
   if (c1 > len) c1 = len;
-  TC acc[JPT][JPT];
+  TC acc[R][R];
 #pragma unroll
-  for (int v = 0; v < JPT; ++v)
+  for (int v = 0; v < R; ++v)
 #pragma unroll
-    for (int u = 0; u < JPT; ++u) acc[v][u] = TC(0);
+    for (int u = 0; u < R; ++u) acc[v][u] = TC(0);
   for (int64_t k0 = c0; k0 < c1; k0 += BK) {
     for (int x = tid; x < LP * BK; x += 256) {
       const int r = x / BK, kk = x % BK;
       const int64_t g = k0 + kk;
       const bool ok = r < l && g < c1;
-      Xs[r][kk] = ok ? Xt[r * ldx + g] : TC(0);
-      Ys[r][kk] = ok ? Yt[r * ldy + g] : TC(0);
+      Xs[kk][r] = ok ? Xt[r * ldx + g] : TC(0);
+      Ys[kk][r] = ok ? Yt[r * ldy + g] : TC(0);
     }
     __syncthreads();
-#pragma unroll 8
+#pragma unroll 4
     for (int kk = 0; kk < BK; ++kk) {
-      TC xa[JPT], yb[JPT];
+      TC xa[R], yb[R];
 #pragma unroll
-      for (int v = 0; v < JPT; ++v) xa[v] = Xs[tj + 16 * v][kk];
+      for (int v = 0; v < R; ++v) xa[v] = Xs[kk][R * ty + v];
 #pragma unroll
-      for (int u = 0; u < JPT; ++u) yb[u] = Ys[ti + 16 * u][kk];
+      for (int u = 0; u < R; ++u) yb[u] = Ys[kk][R * tx + u];
 #pragma unroll
-      for (int v = 0; v < JPT; ++v)
+      for (int v = 0; v < R; ++v)
 #pragma unroll
-        for (int u = 0; u < JPT; ++u) acc[v][u] = fma(xa[v], yb[u], acc[v][u]);
+        for (int u = 0; u < R; ++u) acc[v][u] = fma(xa[v], yb[u], acc[v][u]);
     }
     __syncthreads();
   }
   TC* out = parts + (int64_t)blockIdx.x * LP * LP;
 #pragma unroll
-  for (int v = 0; v < JPT; ++v)
+  for (int v = 0; v < R; ++v)
 #pragma unroll
-    for (int u = 0; u < JPT; ++u) out[(tj + 16 * v) * LP + ti + 16 * u] = acc[v][u];
+    for (int u = 0; u < R; ++u) out[(R * ty + v) * LP + R * tx + u] = acc[v][u];
 }
 
-// G[a][b] = sum over parts in order, in FP64.
+// G[a][b] = sum over parts in a fixed order, in FP64: four threads per element
+// each sum every fourth part, then (s0 + s1) + (s2 + s3).
 template <typename TC>
 __global__ void gram_reduce_kernel(const TC* __restrict__ parts, int nparts, int LP, int l, double* __restrict__ G,
                                    int64_t ldg) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= l * l) return;
-  const int a = e / l, b = e % l;
+  const int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 2;
+  const int q = threadIdx.x & 3;
+  const bool ok = e < l * l;
+  const int a = ok ? e / l : 0, b = ok ? e % l : 0;
   double s = 0.0;
-  for (int p = 0; p < nparts; ++p) s += (double)parts[((int64_t)p * LP + a) * LP + b];
-  G[a * ldg + b] = s;
+  if (ok) {
+    const TC* src = parts + (int64_t)a * LP + b;
+    const int64_t stride = (int64_t)LP * LP;
+    int p = q;
+    for (; p + 12 < nparts; p += 16) {
+      const double v0 = (double)src[p * stride], v1 = (double)src[(p + 4) * stride];
+      const double v2 = (double)src[(p + 8) * stride], v3 = (double)src[(p + 12) * stride];
+      s += v0; s += v1; s += v2; s += v3;
+    }
+    for (; p < nparts; p += 4) s += (double)src[p * stride];
+  }
+  const double s1 = __shfl_xor_sync(0xffffffffu, s, 1);
+  const double t = (q & 1) ? s1 + s : s + s1;                 // (s0 + s1), (s2 + s3)
+  const double t2 = __shfl_xor_sync(0xffffffffu, t, 2);
+  if (ok && q == 0) G[a * ldg + b] = t + t2;
 }
 
 int gram_parts(int64_t len, int sms) {
@@ -89,27 +112,29 @@ cudaError_t launch_gram(const TC* Xt, int64_t ldx, const TC* Yt, int64_t ldy, in
   int LP;
   if (l <= 32) {
     LP = 32;
-    gram_partial_kernel<TC, 2><<<gparts, 256, 0, st>>>(Xt, ldx, Yt, ldy, len, l, parts); CORUTV_COUNT_LAUNCH();
+    gram_partial_kernel<TC, 32><<<gparts, 256, 0, st>>>(Xt, ldx, Yt, ldy, len, l, parts); CORUTV_COUNT_LAUNCH();
   } else if (l <= 64) {
     LP = 64;
-    gram_partial_kernel<TC, 4><<<gparts, 256, 0, st>>>(Xt, ldx, Yt, ldy, len, l, parts); CORUTV_COUNT_LAUNCH();
+    gram_partial_kernel<TC, 64><<<gparts, 256, 0, st>>>(Xt, ldx, Yt, ldy, len, l, parts); CORUTV_COUNT_LAUNCH();
   } else {
     LP = 128;
-    gram_partial_kernel<TC, 8><<<gparts, 256, 0, st>>>(Xt, ldx, Yt, ldy, len, l, parts); CORUTV_COUNT_LAUNCH();
+    gram_partial_kernel<TC, 128><<<gparts, 256, 0, st>>>(Xt, ldx, Yt, ldy, len, l, parts); CORUTV_COUNT_LAUNCH();
   }
-  gram_reduce_kernel<TC><<<(unsigned)cdiv((int64_t)l * l, 256), 256, 0, st>>>(parts, gparts, LP, l, G, ldg); CORUTV_COUNT_LAUNCH();
+  gram_reduce_kernel<TC><<<(unsigned)cdiv((int64_t)l * l * 4, 256), 256, 0, st>>>(parts, gparts, LP, l, G, ldg); CORUTV_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 
 // =============================================================================== Cholesky
-// G + s I = R^T R (R upper, s = shift_rel * trace(G)), right-looking, with
-// R^-1 built column by column in the same sweep:
-//   Rinv[i][j] = (delta_ij - sum_{p=i}^{j-1} Rinv[i][p] R[p][j]) / R[j][j].
-// Storage: the active trailing matrix lives in the upper triangle of Gs, the
-// finished rows of R are stored transposed in its lower triangle
-// (R[p][b] at Gs[b][p]), so one barrier per column suffices.
-// A pivot d <= tol_rel * (G_jj + s) marks column j dependent: R[j][j] = 1,
-// R[j][>j] = 0, and defic[j] = 1 (the caller replaces that column of Q).
+// G + s I = R^T R (R upper, s = shift_rel * trace(G)) and R^-1, by symmetric
+// elimination of [G | I]: step j subtracts m_a = G[j][a] / G[j][j] times row j
+// from every row a > j (upper triangle of G only, by symmetry; the right block
+// receives the same row operations).  Afterwards G = L D L^T with the pivots
+// d_j = G[j][j] (as of step j), the upper triangle holding D L^T and the right
+// block holding L^-1, so R = D^(1/2) L^T and R^-1[p][j] = L^-1[j][p] / sqrt(d_j).
+// Every update of a step is independent: one block barrier per step, no long
+// dependent chains.  A pivot d <= tol_rel * (G_jj + s) marks column j
+// dependent: it eliminates nothing, R[j][j] = 1, R[j][>j] = 0, defic[j] = 1
+// (the caller replaces that column of Q).
 template <typename TC>
 __global__ void __launch_bounds__(512) cholinv_kernel(const double* __restrict__ G, int64_t ldg, int l,
                                                       double shift_rel, double tol_rel, TC* __restrict__ Rg,
@@ -117,10 +142,11 @@ __global__ void __launch_bounds__(512) cholinv_kernel(const double* __restrict__
                                                       DevStatus* status, double* __restrict__ Rout) {
   extern __shared__ unsigned char smem_raw[];
   const int LD = l + 1;
-  TC* Gs = reinterpret_cast<TC*>(smem_raw);     // l x LD
-  TC* Ri = Gs + l * LD;                          // l x LD, R^-1 (upper)
+  TC* Gs = reinterpret_cast<TC*>(smem_raw);     // l x LD, upper triangle used
+  TC* Li = Gs + l * LD;                          // l x LD, L^-1 (lower, unit diagonal)
   __shared__ double diag0[kMaxL];
-  __shared__ TC rdiag[kMaxL];
+  __shared__ TC piv[kMaxL];
+  __shared__ int dep_s[kMaxL];
   __shared__ double red[32];
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
 
@@ -129,7 +155,7 @@ __global__ void __launch_bounds__(512) cholinv_kernel(const double* __restrict__
     const int a = e / l, b = e % l;
     const double g = G[a * ldg + b];
     if (b >= a) Gs[a * LD + b] = (TC)g;
-    Ri[a * LD + b] = TC(0);
+    Li[a * LD + b] = (a == b) ? TC(1) : TC(0);
     if (a == b) tr += g;
   }
   for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
@@ -145,51 +171,343 @@ __global__ void __launch_bounds__(512) cholinv_kernel(const double* __restrict__
   }
   __syncthreads();
 
-  int nfall = 0;
   for (int j = 0; j < l; ++j) {
-    // every thread evaluates the pivot of column j (final since the last barrier)
     const TC d = Gs[j * LD + j];
     const bool dep = !((double)d > tol_rel * diag0[j]) || !(diag0[j] > 0.0);
-    const TC piv = dep ? TC(1) : (TC)sqrt(d);
-    const TC rs = dep ? TC(0) : TC(1) / piv;
+    const TC inv_d = dep ? TC(0) : TC(1) / d;
     if (tid == 0) {
-      defic[j] = dep ? 1 : 0;
-      rdiag[j] = piv;
-      nfall += dep ? 1 : 0;
+      piv[j] = dep ? TC(1) : d;
+      dep_s[j] = dep ? 1 : 0;
     }
-    // (a) column j of R^-1, rows i <= j (R[p][j] = Gs[j][p] for p < j)
-    for (int i = tid; i <= j; i += nt) {
-      TC s0 = (i == j) ? TC(1) : TC(0), s1 = TC(0);
-      int p = i;
-      for (; p + 1 < j; p += 2) {
-        s0 -= Ri[i * LD + p] * Gs[j * LD + p];
-        s1 -= Ri[i * LD + p + 1] * Gs[j * LD + p + 1];
-      }
-      if (p < j) s0 -= Ri[i * LD + p] * Gs[j * LD + p];
-      Ri[i * LD + j] = (s0 + s1) / piv;
-    }
-    // (b) trailing update, upper triangle: G[a][b] -= R[j][a] R[j][b], j < a <= b
+    // rows a > j, one warp per row: upper triangle b >= a of G, and L^-1 columns b <= j
     for (int a = j + 1 + warp; a < l; a += nw) {
-      const TC rja = Gs[j * LD + a] * rs;
-      for (int b = a + lane; b < l; b += 32) Gs[a * LD + b] -= rja * (Gs[j * LD + b] * rs);
+      const TC m = Gs[j * LD + a] * inv_d;
+      for (int b = a + lane; b < l; b += 32) Gs[a * LD + b] -= m * Gs[j * LD + b];
+      for (int b = lane; b <= j; b += 32) Li[a * LD + b] -= m * Li[j * LD + b];
     }
-    // (c) finished row j of R, stored transposed in the lower triangle
-    for (int b = j + 1 + tid; b < l; b += nt) Gs[b * LD + j] = Gs[j * LD + b] * rs;
     __syncthreads();
   }
+  int nfall = 0;
   for (int e = tid; e < l * l; e += nt) {
     const int a = e / l, b = e % l;
-    const TC r = (b > a) ? Gs[b * LD + a] : (b == a ? rdiag[a] : TC(0));
+    const TC ra = sqrt(piv[a]);
+    TC r = TC(0);
+    if (b == a) r = ra;
+    else if (b > a && !dep_s[a]) r = Gs[a * LD + b] / ra;
     Rg[a * kMaxL + b] = r;
-    Rinvg[a * kMaxL + b] = (b >= a) ? Ri[a * LD + b] : TC(0);
+    // R^-1[a][b] = L^-1[b][a] / sqrt(d_b)  (upper: a <= b)
+    Rinvg[a * kMaxL + b] = (b >= a) ? Li[b * LD + a] / sqrt(piv[b]) : TC(0);
     if (Rout) Rout[a * l + b] = (double)r;
   }
-  if (tid == 0 && nfall && status) atomicAdd(&status->chol_fallbacks, nfall);
+  for (int a = tid; a < l; a += nt) {
+    defic[a] = dep_s[a];
+    nfall += dep_s[a];
+  }
+  for (int o = 16; o > 0; o >>= 1) nfall += __shfl_xor_sync(0xffffffffu, nfall, o);
+  if (lane == 0 && nfall && status) atomicAdd(&status->chol_fallbacks, nfall);
+}
+
+// FP32 variant with rows in registers: thread (a, h) holds columns
+// b = 64 h .. 64 h + 63 of row a of both blocks.  Step j: the two threads of
+// row j publish it (double-buffered, one barrier per step) with the entries
+// that must not act zeroed -- G part only for b > j, L^-1 part only for b <= j
+// -- so every row a > j subtracts m_a = G[j][a] / d_j times it with
+// unpredicated vector loads.  Same algebra as cholinv_kernel.
+template <int TPR>
+__global__ void __launch_bounds__(kMaxL * TPR) cholinv_reg_kernel(const double* __restrict__ G, int64_t ldg, int l,
+                                                          double shift_rel, double tol_rel, float* __restrict__ Rg,
+                                                          float* __restrict__ Rinvg, int* __restrict__ defic,
+                                                          DevStatus* status, double* __restrict__ Rout) {
+  constexpr int CPT = kMaxL / TPR, NWARP = kMaxL * TPR / 32;
+  __shared__ __align__(16) float prow[2][kMaxL];
+  __shared__ __align__(16) float plrow[2][kMaxL];
+  __shared__ float pivm[2];             // [buf]: 1 / d_j (0 if dependent)
+  __shared__ double red[NWARP];
+  const int tid = threadIdx.x, a = tid / TPR, h = tid % TPR, lane = tid & 31, warp = tid >> 5;
+  const int b0 = h * CPT;
+  const unsigned grp = ((TPR == 32) ? 0xffffffffu : ((1u << TPR) - 1u)) << (lane & ~(TPR - 1));
+  float g[CPT], li[CPT];
+  double tr = 0.0;
+#pragma unroll
+  for (int s = 0; s < CPT; ++s) {
+    const int b = b0 + s;
+    const bool ok = a < l && b < l;
+    const double v = ok ? G[a * ldg + b] : 0.0;
+    g[s] = (float)v;
+    li[s] = (ok && a == b) ? 1.f : 0.f;
+    if (ok && a == b) tr += v;
+  }
+  for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
+  if (lane == 0) red[warp] = tr;
+  __syncthreads();
+  double trace = 0.0;
+  for (int w = 0; w < NWARP; ++w) trace += red[w];
+  const double shift = shift_rel * trace;
+  double diag0 = 0.0;
+#pragma unroll
+  for (int s = 0; s < CPT; ++s)
+    if (b0 + s == a && a < l) {
+      diag0 = (double)g[s] + shift;
+      g[s] = (float)diag0;
+    }
+#pragma unroll
+  for (int o = 1; o < TPR; o <<= 1) diag0 = fmax(diag0, __shfl_xor_sync(0xffffffffu, diag0, o));
+  float piv_mine = 1.f;
+  bool dep_mine = false;
+  for (int j = 0; j < l; ++j) {
+    const int buf = j & 1;
+    if (a == j) {
+      float dj = 0.f;
+#pragma unroll
+      for (int s = 0; s < CPT; ++s)
+        if (b0 + s == j) dj = g[s];
+#pragma unroll
+      for (int o = 1; o < TPR; o <<= 1) dj += __shfl_xor_sync(grp, dj, o);
+      const bool dep = !((double)dj > tol_rel * diag0) || !(diag0 > 0.0);
+      piv_mine = dep ? 1.f : dj;
+      dep_mine = dep;
+      float4* pr = reinterpret_cast<float4*>(&prow[buf][b0]);
+      float4* pl = reinterpret_cast<float4*>(&plrow[buf][b0]);
+#pragma unroll
+      for (int q = 0; q < CPT / 4; ++q) {
+        float4 vg, vl;
+        float* pg = &vg.x;
+        float* plv = &vl.x;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int s = 4 * q + e, b = b0 + s;
+          pg[e] = (b > j) ? g[s] : 0.f;
+          plv[e] = (b <= j) ? li[s] : 0.f;
+        }
+        pr[q] = vg;
+        pl[q] = vl;
+      }
+      if (h == 0) pivm[buf] = dep ? 0.f : 1.f / dj;
+    }
+    __syncthreads();
+    if (a > j && a < l) {
+      const float m = prow[buf][a] * pivm[buf];
+      const float4* pr = reinterpret_cast<const float4*>(&prow[buf][b0]);
+      const float4* pl = reinterpret_cast<const float4*>(&plrow[buf][b0]);
+#pragma unroll
+      for (int q = 0; q < CPT / 4; ++q) {
+        const float4 vg = pr[q], vl = pl[q];
+        g[4 * q + 0] -= m * vg.x; g[4 * q + 1] -= m * vg.y; g[4 * q + 2] -= m * vg.z; g[4 * q + 3] -= m * vg.w;
+        li[4 * q + 0] -= m * vl.x; li[4 * q + 1] -= m * vl.y; li[4 * q + 2] -= m * vl.z; li[4 * q + 3] -= m * vl.w;
+      }
+    }
+  }
+  __syncthreads();
+  if (a < l) {
+    const float ra = sqrtf(piv_mine);
+#pragma unroll
+    for (int s = 0; s < CPT; ++s) {
+      const int b = b0 + s;
+      if (b >= l) continue;
+      float r = 0.f;
+      if (b == a) r = ra;
+      else if (b > a && !dep_mine) r = g[s] / ra;
+      Rg[a * kMaxL + b] = r;
+      if (Rout) Rout[a * l + b] = (double)r;
+      // R^-1[b][a] = L^-1[a][b] / sqrt(d_a) for b <= a
+      Rinvg[b * kMaxL + a] = (b <= a) ? li[s] / ra : 0.f;
+    }
+  }
+  int nfall = (h == 0 && a < l && dep_mine) ? 1 : 0;
+  for (int o = 16; o > 0; o >>= 1) nfall += __shfl_xor_sync(0xffffffffu, nfall, o);
+  if (h == 0 && a < l) defic[a] = dep_mine ? 1 : 0;
+  if (lane == 0 && nfall && status) atomicAdd(&status->chol_fallbacks, nfall);
+}
+
+// FP32 blocked variant (l <= 128, padded with an identity block to 128 = 4
+// blocks of 32).  For each diagonal block o = 32 kb:
+//   1. one warp factors the 32 x 32 block by the same symmetric elimination
+//      (lane i holds column i of the block and of its L^-1 block; multipliers
+//      are broadcast with shuffles, no block barrier) and writes R11, R11^-1;
+//   2. panel: R12 = R11^-T A12 (rows of dependent columns zeroed);
+//   3. trailing update A22 -= R12^T R12.
+// Then R^-1 is completed block column by block column:
+//   X_kk = R_kk^-1,  X_ik = -(sum_{p=i}^{k-1} X_ip R_pk) X_kk.
+// About twenty block barriers in all; the same algebra and dependent-column
+// rule as cholinv_kernel.
+__global__ void __launch_bounds__(512) cholinv_blk_kernel(const double* __restrict__ G, int64_t ldg, int l,
+                                                          double shift_rel, double tol_rel, float* __restrict__ Rg,
+                                                          float* __restrict__ Rinvg, int* __restrict__ defic,
+                                                          DevStatus* status, double* __restrict__ Rout) {
+  constexpr int N = kMaxL, NB = 32, LD = N + 4;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* A = reinterpret_cast<float*>(smem_raw);      // N x LD: G, becomes R (upper)
+  float* X = A + N * LD;                             // N x LD: R^-1 (upper)
+  float* T = X + N * LD;                             // NB x LD scratch (panel / products)
+  __shared__ float diag0[N];
+  __shared__ int dep[N];
+  __shared__ double red[16];
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
+
+  double tr = 0.0;
+  for (int e = tid; e < N * N; e += nt) {
+    const int a = e / N, b = e % N;
+    float v;
+    if (a < l && b < l) {
+      const double g = G[a * ldg + b];
+      v = (float)g;
+      if (a == b) tr += g;
+    } else {
+      v = (a == b) ? 1.f : 0.f;
+    }
+    A[a * LD + b] = v;
+    X[a * LD + b] = 0.f;
+  }
+  for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
+  if (lane == 0) red[warp] = tr;
+  __syncthreads();
+  double trace = 0.0;
+  for (int w = 0; w < nt / 32; ++w) trace += red[w];
+  const float shift = (float)(shift_rel * trace);
+  for (int a = tid; a < N; a += nt) {
+    if (a < l) A[a * LD + a] += shift;
+    diag0[a] = A[a * LD + a];
+  }
+  __syncthreads();
+
+  for (int kb = 0; kb < N / NB; ++kb) {
+    const int o = NB * kb, rest = N - o - NB;
+    // ---- 1. diagonal block by one warp
+    if (warp == 0) {
+      float a[NB], w[NB];     // column `lane` of the block and of its L^-1
+#pragma unroll
+      for (int r = 0; r < NB; ++r) {
+        a[r] = A[(o + r) * LD + o + lane];
+        w[r] = (r == lane) ? 1.f : 0.f;
+      }
+      float dv = 1.f;          // pivot of row `lane`
+      bool dp = false;
+#pragma unroll
+      for (int j = 0; j < NB; ++j) {
+        const float d = __shfl_sync(0xffffffffu, a[j], j);
+        const bool depj = !(d > tol_rel * diag0[o + j]) || !(diag0[o + j] > 0.f);
+        const float inv_d = depj ? 0.f : 1.f / d;
+        if (lane == j) { dv = depj ? 1.f : d; dp = depj; }
+        const float rowj_a = a[j];            // A[j][lane] (row j of this column)
+        const float rowj_w = w[j];            // L^-1[j][lane]
+#pragma unroll
+        for (int k = j + 1; k < NB; ++k) {
+          const float m = __shfl_sync(0xffffffffu, a[j], k) * inv_d;   // A[j][k] / d
+          a[k] -= m * rowj_a;                 // row k of column lane (meaningful for lane >= k)
+          w[k] -= m * rowj_w;                 // row k of L^-1, column lane
+        }
+      }
+      // lane holds column `lane` of U = D L^T and of L^-1; its pivot is dv
+      const float sq = sqrtf(dv);
+      const float rsq = 1.f / sq;
+      dep[o + lane] = dp ? 1 : 0;
+      // R11[k][lane] = U[k][lane] / sqrt(d_k) for k <= lane (0 above for dependent rows)
+#pragma unroll
+      for (int k = 0; k < NB; ++k) {
+        const float rk = __shfl_sync(0xffffffffu, rsq, k);     // 1 / sqrt(d_k)
+        const int depk = __shfl_sync(0xffffffffu, dp ? 1 : 0, k);
+        float r = 0.f;
+        if (k == lane) r = sq;
+        else if (k < lane && !depk) r = a[k] * rk;
+        A[(o + k) * LD + o + lane] = r;
+        // R11^-1[lane][k] = L^-1[k][lane] / sqrt(d_k), k >= lane
+        X[(o + lane) * LD + o + k] = (k >= lane) ? w[k] * rk : 0.f;
+      }
+    }
+    __syncthreads();
+    if (rest > 0) {
+      // ---- 2. panel R12 = R11^-T A12 into T (NB x rest), then back into A
+      for (int e = tid; e < NB * rest; e += nt) {
+        const int k = e / rest, c = o + NB + e % rest;
+        float s0 = 0.f, s1 = 0.f;
+        int p = 0;
+        for (; p + 1 <= k; p += 2) {
+          s0 = fmaf(X[(o + p) * LD + o + k], A[(o + p) * LD + c], s0);
+          s1 = fmaf(X[(o + p + 1) * LD + o + k], A[(o + p + 1) * LD + c], s1);
+        }
+        if (p <= k) s0 = fmaf(X[(o + p) * LD + o + k], A[(o + p) * LD + c], s0);
+        T[k * LD + c] = dep[o + k] ? 0.f : s0 + s1;
+      }
+      __syncthreads();
+      for (int e = tid; e < NB * rest; e += nt) {
+        const int k = e / rest, c = o + NB + e % rest;
+        A[(o + k) * LD + c] = T[k * LD + c];
+      }
+      // ---- 3. trailing update, upper triangle: A22[a][b] -= sum_k R12[k][a] R12[k][b]
+      for (int e = tid; e < rest * rest; e += nt) {
+        const int a = o + NB + e / rest, b = o + NB + e % rest;
+        if (b < a) continue;
+        float s0 = 0.f, s1 = 0.f;
+#pragma unroll 8
+        for (int k = 0; k < NB; k += 2) {
+          s0 = fmaf(T[k * LD + a], T[k * LD + b], s0);
+          s1 = fmaf(T[(k + 1) * LD + a], T[(k + 1) * LD + b], s1);
+        }
+        A[a * LD + b] -= s0 + s1;
+      }
+      __syncthreads();
+    }
+  }
+  // ---- R^-1 off-diagonal blocks: X_ik = -(sum_{p=i}^{k-1} X_ip R_pk) X_kk.
+  // For block column k (columns ok .. ok+31) and every row r < ok:
+  //   S[r][c] = sum_{p=r}^{ok-1} X[r][p] R[p][c]   (kept in X's own (r, c) slots),
+  //   X[r][c] = -sum_{q=ok}^{c} S[r][q] X[q][c]    (staged in A's unused lower triangle).
+  for (int kb = 1; kb < N / NB; ++kb) {
+    const int ok = NB * kb;
+    for (int e = tid; e < ok * NB; e += nt) {
+      const int r = e / NB, c = ok + e % NB;
+      float s0 = 0.f, s1 = 0.f;
+      int p = r;
+      for (; p + 1 < ok; p += 2) {
+        s0 = fmaf(X[r * LD + p], A[p * LD + c], s0);
+        s1 = fmaf(X[r * LD + p + 1], A[(p + 1) * LD + c], s1);
+      }
+      if (p < ok) s0 = fmaf(X[r * LD + p], A[p * LD + c], s0);
+      X[r * LD + c] = s0 + s1;
+    }
+    __syncthreads();
+    for (int e = tid; e < ok * NB; e += nt) {
+      const int r = e / NB, c = ok + e % NB;
+      float s0 = 0.f;
+      for (int q = ok; q <= c; ++q) s0 = fmaf(X[r * LD + q], X[q * LD + c], s0);
+      A[c * LD + r] = -s0;
+    }
+    __syncthreads();
+    for (int e = tid; e < ok * NB; e += nt) {
+      const int r = e / NB, c = ok + e % NB;
+      X[r * LD + c] = A[c * LD + r];
+    }
+    __syncthreads();
+  }
+  // ---- outputs
+  int nfall = 0;
+  for (int e = tid; e < l * l; e += nt) {
+    const int a = e / l, b = e % l;
+    const float r = (b >= a) ? A[a * LD + b] : 0.f;
+    Rg[a * kMaxL + b] = r;
+    Rinvg[a * kMaxL + b] = (b >= a) ? X[a * LD + b] : 0.f;
+    if (Rout) Rout[a * l + b] = (double)r;
+  }
+  for (int a = tid; a < l; a += nt) {
+    defic[a] = dep[a];
+    nfall += dep[a];
+  }
+  for (int o2 = 16; o2 > 0; o2 >>= 1) nfall += __shfl_xor_sync(0xffffffffu, nfall, o2);
+  if (lane == 0 && nfall && status) atomicAdd(&status->chol_fallbacks, nfall);
 }
 
 template <typename TC>
 cudaError_t launch_cholinv(const double* G, int64_t ldg, int l, double shift_rel, double tol_rel, TC* R, TC* Rinv,
                            int* defic, DevStatus* status, double* Rout, cudaStream_t st) {
+  if constexpr (sizeof(TC) == 4) {
+    const size_t smem_blk = (size_t)(2 * kMaxL + 32) * (kMaxL + 4) * sizeof(float);
+    cudaError_t e0 = cudaFuncSetAttribute(cholinv_blk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem_blk);
+    if (e0 != cudaSuccess) return e0;
+    cholinv_blk_kernel<<<1, 512, smem_blk, st>>>(G, ldg, l, shift_rel, tol_rel, R, Rinv, defic, status, Rout);
+    CORUTV_COUNT_LAUNCH();
+    return cudaGetLastError();
+  }
   const size_t smem = (size_t)2 * l * (l + 1) * sizeof(TC);
   cudaError_t e = cudaFuncSetAttribute(cholinv_kernel<TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -199,63 +517,73 @@ cudaError_t launch_cholinv(const double* G, int64_t ldg, int l, double shift_rel
 
 // =============================================================================== lmul
 // Out[j][i] = sum_{p<l} S[p][j] In[p][i]   (Out = S^T In on ST blocks, i.e. C S in
-// the untransposed view).  out_rowmajor: write Out^T into a row-major len x l matrix.
-template <typename TC, typename TS, int JPT>
+// the untransposed view).  A CTA computes a BI-column tile; thread (tx, ty)
+// owns j = R ty + (0..R-1) and i = BI/16 tx + (0..BI/16-1).  upper: S is upper
+// triangular (S[p][j] = 0 for p > j), so the p loop stops at the thread's last j.
+// out_rowmajor: write Out^T into a row-major len x l matrix (staged through
+// shared memory so the row writes coalesce).
+template <typename TC, typename TS, int LP, int BI>
 __global__ void __launch_bounds__(256) lmul_kernel(const TC* __restrict__ In, int64_t ldi, int64_t len, int l,
                                                    const TS* __restrict__ S, int64_t lds, TC* __restrict__ Out,
-                                                   int64_t ldo, int out_rowmajor) {
-  constexpr int LP = 16 * JPT;
-  constexpr int BI = 64;
-  extern __shared__ unsigned char smem_raw[];
-  TC* Ss = reinterpret_cast<TC*>(smem_raw);      // LP x (LP+1)
-  TC* Is = Ss + LP * (LP + 1);                   // LP x (BI+1)
-  const int tid = threadIdx.x, ti = tid & 15, tj = tid >> 4;
+                                                   int64_t ldo, int out_rowmajor, int upper) {
+  constexpr int R = LP / 16, RI = BI / 16;
+  constexpr int SP = LP + 4, IP = BI + 4;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TC* Ss = reinterpret_cast<TC*>(smem_raw);      // LP x SP   (row p, column j)
+  TC* Is = Ss + LP * SP;                         // LP x IP   (row p, column i)
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int64_t i0 = (int64_t)blockIdx.x * BI;
   for (int e = tid; e < LP * LP; e += 256) {
     const int p = e / LP, j = e % LP;
-    Ss[p * (LP + 1) + j] = (p < l && j < l) ? (TC)S[p * lds + j] : TC(0);
+    Ss[p * SP + j] = (p < l && j < l) ? (TC)S[p * lds + j] : TC(0);
   }
   for (int e = tid; e < LP * BI; e += 256) {
     const int p = e / BI, ii = e % BI;
     const int64_t g = i0 + ii;
-    Is[p * (BI + 1) + ii] = (p < l && g < len) ? In[p * ldi + g] : TC(0);
+    Is[p * IP + ii] = (p < l && g < len) ? In[p * ldi + g] : TC(0);
   }
   __syncthreads();
-  TC acc[JPT][4];
+  TC acc[R][RI];
 #pragma unroll
-  for (int v = 0; v < JPT; ++v)
+  for (int v = 0; v < R; ++v)
 #pragma unroll
-    for (int u = 0; u < 4; ++u) acc[v][u] = TC(0);
-  for (int p = 0; p < l; ++p) {
-    TC sv[JPT], xv[4];
-#pragma unroll
-    for (int v = 0; v < JPT; ++v) sv[v] = Ss[p * (LP + 1) + tj + 16 * v];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) xv[u] = Is[p * (BI + 1) + ti + 16 * u];
-#pragma unroll
-    for (int v = 0; v < JPT; ++v)
-#pragma unroll
-      for (int u = 0; u < 4; ++u) acc[v][u] = fma(sv[v], xv[u], acc[v][u]);
+    for (int u = 0; u < RI; ++u) acc[v][u] = TC(0);
+  int pend = l;
+  if (upper) {
+    // the warp's rows: ty and ty ^ 1 (both halves of the warp); the larger bounds the loop
+    const int jmax = R * ((ty | 1) + 1);
+    pend = jmax < l ? jmax : l;
   }
-  __syncthreads();
+#pragma unroll 2
+  for (int p = 0; p < pend; ++p) {
+    TC sv[R], xv[RI];
+#pragma unroll
+    for (int v = 0; v < R; ++v) sv[v] = Ss[p * SP + R * ty + v];
+#pragma unroll
+    for (int u = 0; u < RI; ++u) xv[u] = Is[p * IP + RI * tx + u];
+#pragma unroll
+    for (int v = 0; v < R; ++v)
+#pragma unroll
+      for (int u = 0; u < RI; ++u) acc[v][u] = fma(sv[v], xv[u], acc[v][u]);
+  }
   if (!out_rowmajor) {
 #pragma unroll
-    for (int v = 0; v < JPT; ++v) {
-      const int j = tj + 16 * v;
+    for (int v = 0; v < R; ++v) {
+      const int j = R * ty + v;
       if (j >= l) continue;
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int64_t g = i0 + ti + 16 * u;
+      for (int u = 0; u < RI; ++u) {
+        const int64_t g = i0 + RI * tx + u;
         if (g < len) Out[j * ldo + g] = acc[v][u];
       }
     }
   } else {
-    // stage through shared memory (reuse Is as [BI][LP+1]) so row-major writes coalesce
-    TC* Os = Is;
+    __syncthreads();
+    TC* Os = Is;                                  // BI x (LP + 1)
 #pragma unroll
-    for (int v = 0; v < JPT; ++v)
+    for (int v = 0; v < R; ++v)
 #pragma unroll
-      for (int u = 0; u < 4; ++u) Os[(ti + 16 * u) * (LP + 1) + tj + 16 * v] = acc[v][u];
+      for (int u = 0; u < RI; ++u) Os[(RI * tx + u) * (LP + 1) + R * ty + v] = acc[v][u];
     __syncthreads();
     for (int e = tid; e < BI * l; e += 256) {
       const int ii = e / l, j = e % l;
@@ -265,41 +593,42 @@ __global__ void __launch_bounds__(256) lmul_kernel(const TC* __restrict__ In, in
   }
 }
 
+template <typename TC, typename TS, int LP, int BI>
+static cudaError_t lmul_variant(const TC* In, int64_t ldi, int64_t len, int l, const TS* S, int64_t lds, TC* Out,
+                                int64_t ldo, bool rowmajor, bool upper, cudaStream_t st) {
+  const unsigned grid = (unsigned)cdiv(len, BI);
+  if (grid == 0) return cudaSuccess;
+  const size_t a = (size_t)LP * (LP + 4) + (size_t)LP * (BI + 4);
+  const size_t b = (size_t)LP * (LP + 4) + (size_t)BI * (LP + 1);
+  const size_t sm = (a > b ? a : b) * sizeof(TC);
+  cudaError_t e = cudaFuncSetAttribute(lmul_kernel<TC, TS, LP, BI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sm);
+  if (e != cudaSuccess) return e;
+  lmul_kernel<TC, TS, LP, BI><<<grid, 256, sm, st>>>(In, ldi, len, l, S, lds, Out, ldo, rowmajor ? 1 : 0,
+                                                     upper ? 1 : 0);
+  CORUTV_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
+
 template <typename TC, typename TS>
 static cudaError_t lmul_dispatch(const TC* In, int64_t ldi, int64_t len, int l, const TS* S, int64_t lds, TC* Out,
-                                 int64_t ldo, bool rowmajor, cudaStream_t st) {
-  const unsigned grid = (unsigned)cdiv(len, 64);
-  if (grid == 0) return cudaSuccess;
-  int LP = l <= 32 ? 32 : (l <= 64 ? 64 : 128);
-  const size_t smem = (size_t)(LP * (LP + 1) + LP * 65) * sizeof(TC);
-  const size_t smem_out = (size_t)(LP * (LP + 1) + 64 * (LP + 1)) * sizeof(TC);
-  const size_t sm = smem > smem_out ? smem : smem_out;
-  cudaError_t e;
-  if (LP == 32) {
-    e = cudaFuncSetAttribute(lmul_kernel<TC, TS, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    lmul_kernel<TC, TS, 2><<<grid, 256, sm, st>>>(In, ldi, len, l, S, lds, Out, ldo, rowmajor); CORUTV_COUNT_LAUNCH();
-  } else if (LP == 64) {
-    e = cudaFuncSetAttribute(lmul_kernel<TC, TS, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    lmul_kernel<TC, TS, 4><<<grid, 256, sm, st>>>(In, ldi, len, l, S, lds, Out, ldo, rowmajor); CORUTV_COUNT_LAUNCH();
-  } else {
-    e = cudaFuncSetAttribute(lmul_kernel<TC, TS, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    lmul_kernel<TC, TS, 8><<<grid, 256, sm, st>>>(In, ldi, len, l, S, lds, Out, ldo, rowmajor); CORUTV_COUNT_LAUNCH();
-  }
-  return cudaGetLastError();
+                                 int64_t ldo, bool rowmajor, bool upper, cudaStream_t st) {
+  constexpr int BI = sizeof(TC) == 8 ? 64 : 128;
+  if (l <= 32) return lmul_variant<TC, TS, 32, BI>(In, ldi, len, l, S, lds, Out, ldo, rowmajor, upper, st);
+  if (l <= 64) return lmul_variant<TC, TS, 64, BI>(In, ldi, len, l, S, lds, Out, ldo, rowmajor, upper, st);
+  return lmul_variant<TC, TS, 128, BI>(In, ldi, len, l, S, lds, Out, ldo, rowmajor, upper, st);
 }
 
 template <typename TC>
 cudaError_t launch_lmul(const TC* In, int64_t ldi, int64_t len, int l, const TC* S, int64_t lds, TC* Out,
                         int64_t ldo, bool out_rowmajor, cudaStream_t st) {
-  return lmul_dispatch<TC, TC>(In, ldi, len, l, S, lds, Out, ldo, out_rowmajor, st);
+  // the CholeskyQR factor R^-1 is upper triangular
+  return lmul_dispatch<TC, TC>(In, ldi, len, l, S, lds, Out, ldo, out_rowmajor, true, st);
 }
 template <typename TC>
 cudaError_t launch_lmul_f64s(const TC* In, int64_t ldi, int64_t len, int l, const double* S, int64_t lds, TC* Out,
                              int64_t ldo, bool out_rowmajor, cudaStream_t st) {
-  return lmul_dispatch<TC, double>(In, ldi, len, l, S, lds, Out, ldo, out_rowmajor, st);
+  return lmul_dispatch<TC, double>(In, ldi, len, l, S, lds, Out, ldo, out_rowmajor, false, st);
 }
 
 // =============================================================================== deficient columns
@@ -390,14 +719,16 @@ cudaError_t launch_stage_transpose(const TC* Phi, int64_t ldphi, int64_t len, in
 }
 
 // =============================================================================== QRCP
-// One CTA, 16 warps.  Columns are never moved in shared memory: every warp
+// One CTA of 16 warps.  Warp w keeps columns c = w, w + 16, ... of D in
+// registers (lane holds rows lane + 32 r).  Columns never move: every warp
 // keeps the same position -> column map (4 entries per lane) and applies the
 // same swaps, so "first maximum by current position" matches the textbook
-// algorithm with physical column exchanges.  Warp w owns physical columns
-// c = w, w + 16, ...; each step it updates its trailing columns with the
-// reflector and recomputes their trailing norms exactly.  One block barrier
-// per step.  Q~ is then formed column by column (H_0 ... H_{l-1} e_c) without
-// barriers.
+// algorithm with physical column exchanges.  Step j: all warps pick the pivot
+// from the trailing norms (shared memory); its owner builds the Householder
+// vector and publishes it; every warp applies it to its trailing columns and
+// recomputes their trailing norms exactly.  Two block barriers per step; the
+// reductions of a warp's columns are interleaved.  Q~ = H_0 ... H_{l-1} is then
+// formed column by column in registers without barriers.
 template <typename TC>
 __device__ __forceinline__ TC warp_sum(TC v) {
 #pragma unroll
@@ -418,36 +749,50 @@ __global__ void __launch_bounds__(512) qrcp_kernel(const double* __restrict__ Dg
                                                    double* __restrict__ Qg, int64_t ldq, double* __restrict__ Rg,
                                                    int64_t ldr, int r_transposed, int32_t* __restrict__ perm,
                                                    double* __restrict__ fro2, DevStatus* status) {
+  constexpr int NW = 16, U = kMaxL / NW;    // 8 columns per warp
   extern __shared__ unsigned char smem_raw[];
-  const int LD = l + 1;
-  TC* Ds = reinterpret_cast<TC*>(smem_raw);   // column-major: Ds[c*LD + i] = D[i][c]
-  TC* Qs = Ds + l * LD;                        // column-major Q~
+  TC* Vs = reinterpret_cast<TC*>(smem_raw);  // Vs[j * kMaxL + i]: reflector j (rows i >= j)
   __shared__ TC norms[kMaxL];
-  __shared__ TC vdiag[kMaxL];
   __shared__ TC betas[kMaxL];
   __shared__ TC rdiag[kMaxL];
   __shared__ int pcol[kMaxL];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  __shared__ double red[NW][2];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
-  for (int e = tid; e < l * l; e += blockDim.x) {
-    const int i = e / l, c = e % l;
-    Ds[c * LD + i] = (TC)Dg[i * ldd + c];
+  TC d[U][4];
+  bool trailing[U];
+  int posof[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int c = warp + NW * u;
+    trailing[u] = c < l;
+    posof[u] = -1;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int i = lane + 32 * r;
+      d[u][r] = (c < l && i < l) ? (TC)Dg[i * ldd + c] : TC(0);
+    }
   }
-  __syncthreads();
-  for (int c = warp; c < l; c += nw) {
-    TC s = 0;
-    for (int i = lane; i < l; i += 32) s += Ds[c * LD + i] * Ds[c * LD + i];
-    s = warp_sum(s);
-    if (lane == 0) norms[c] = s;
+  {
+    TC nv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) nv[u] = d[u][0] * d[u][0] + d[u][1] * d[u][1] + d[u][2] * d[u][2] + d[u][3] * d[u][3];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int u = 0; u < U; ++u) nv[u] += __shfl_xor_sync(0xffffffffu, nv[u], o);
+    if (lane == 0)
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (warp + NW * u < l) norms[warp + NW * u] = nv[u];
   }
-  // position -> column map, lane holds positions lane + 32*r
   int map[4];
 #pragma unroll
   for (int r = 0; r < 4; ++r) map[r] = lane + 32 * r;
   __syncthreads();
 
   for (int j = 0; j < l; ++j) {
-    // argmax of trailing norms over positions j..l-1, first maximum wins
+    // pivot: first maximum of the trailing norms by current position
     TC best = TC(-1);
     int bpos = l;
 #pragma unroll
@@ -464,7 +809,6 @@ __global__ void __launch_bounds__(512) qrcp_kernel(const double* __restrict__ Dg
       const int op = __shfl_xor_sync(0xffffffffu, bpos, o);
       if (ob > best || (ob == best && op < bpos)) { best = ob; bpos = op; }
     }
-    // swap positions j and bpos in the map
     const int cj = __shfl_sync(0xffffffffu, sel4(map, j >> 5), j & 31);
     const int cp = __shfl_sync(0xffffffffu, sel4(map, (bpos >> 5) & 3), bpos & 31);
 #pragma unroll
@@ -473,106 +817,384 @@ __global__ void __launch_bounds__(512) qrcp_kernel(const double* __restrict__ Dg
       if (pos == j) map[r] = cp;
       else if (pos == bpos) map[r] = cj;
     }
-    const int c = cp;   // physical pivot column
-    // Householder vector of column c, rows j..l-1 (computed by every warp)
-    TC x0 = Ds[c * LD + j];
-    TC s = 0;
-    for (int i = j + lane; i < l; i += 32) s += Ds[c * LD + i] * Ds[c * LD + i];
-    s = warp_sum(s);
-    const TC nrm = sqrt(s);
-    TC alpha, v0, beta;
-    if (nrm == TC(0)) {
-      alpha = 0; v0 = 1; beta = 0;
-    } else {
-      alpha = (x0 >= TC(0)) ? -nrm : nrm;
-      v0 = x0 - alpha;
-      beta = TC(1) / (nrm * (nrm + fabs(x0)));
-    }
-    if (tid == 0) {
-      vdiag[j] = v0; betas[j] = beta; rdiag[j] = alpha; pcol[j] = c;
-    }
-    // update owned trailing columns (not yet pivoted: position > j)
-    for (int cc = warp; cc < l; cc += nw) {
-      // is column cc still trailing (at a position > j)?  every lane checks its 4 entries
-      bool mine = false;
+    // owner of the pivot column builds and publishes the reflector (rows j..l-1)
+    if (warp == cp % NW) {
+      const int up = cp / NW;
+      TC x[4];
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (u == up)
+#pragma unroll
+          for (int r = 0; r < 4; ++r) x[r] = d[u][r];
+      TC ss = 0;
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
-        const int pos = lane + 32 * r;
-        if (pos > j && pos < l && map[r] == cc) mine = true;
+        const int i = lane + 32 * r;
+        if (i >= j && i < l) ss += x[r] * x[r];
       }
-      if (!__any_sync(0xffffffffu, mine)) continue;
-      TC w = 0;
-      for (int i = j + lane; i < l; i += 32) {
-        const TC vi = (i == j) ? v0 : Ds[c * LD + i];
-        w += vi * Ds[cc * LD + i];
+      ss = warp_sum(ss);
+      const TC x0 = __shfl_sync(0xffffffffu, (j >> 5) == 0 ? x[0] : ((j >> 5) == 1 ? x[1] : ((j >> 5) == 2 ? x[2] : x[3])), j & 31);
+      const TC nrm = sqrt(ss);
+      TC alpha, v0, beta;
+      if (nrm == TC(0)) {
+        alpha = 0; v0 = 1; beta = 0;
+      } else {
+        alpha = (x0 >= TC(0)) ? -nrm : nrm;
+        v0 = x0 - alpha;
+        beta = TC(1) / (nrm * (nrm + fabs(x0)));
       }
-      w = warp_sum(w) * beta;
-      TC ns = 0;
-      for (int i = j + lane; i < l; i += 32) {
-        const TC vi = (i == j) ? v0 : Ds[c * LD + i];
-        const TC nv = Ds[cc * LD + i] - w * vi;
-        Ds[cc * LD + i] = nv;
-        if (i > j) ns += nv * nv;
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int i = lane + 32 * r;
+        if (i >= j && i < l) Vs[j * kMaxL + i] = (i == j) ? v0 : x[r];
       }
-      ns = warp_sum(ns);
-      if (lane == 0) norms[cc] = ns;
+      if (lane == 0) { betas[j] = beta; rdiag[j] = alpha; pcol[j] = cp; }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (u == up) { trailing[u] = false; posof[u] = j; }
     }
+    __syncthreads();
+    // apply the reflector to this warp's trailing columns and recompute their norms
+    const TC beta = betas[j];
+    TC v[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int i = lane + 32 * r;
+      v[r] = (i >= j && i < l) ? Vs[j * kMaxL + i] : TC(0);
+    }
+    TC w[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) w[u] = v[0] * d[u][0] + v[1] * d[u][1] + v[2] * d[u][2] + v[3] * d[u][3];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int u = 0; u < U; ++u) w[u] += __shfl_xor_sync(0xffffffffu, w[u], o);
+    TC nv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      nv[u] = 0;
+      if (trailing[u]) {
+        const TC f = beta * w[u];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          d[u][r] -= f * v[r];
+          const int i = lane + 32 * r;
+          if (i > j && i < l) nv[u] += d[u][r] * d[u][r];
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int u = 0; u < U; ++u) nv[u] += __shfl_xor_sync(0xffffffffu, nv[u], o);
+    if (lane == 0)
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (trailing[u]) norms[warp + NW * u] = nv[u];
     __syncthreads();
   }
 
-  // Q~ = H_0 H_1 ... H_{l-1}: column q of Q~ is H_0 ... H_q e_q
-  for (int q = warp; q < l; q += nw) {
-    for (int i = lane; i < l; i += 32) Qs[q * LD + i] = (i == q) ? TC(1) : TC(0);
-    __syncwarp();
-    for (int j = q; j >= 0; --j) {
-      const int c = pcol[j];
-      const TC beta = betas[j], v0 = vdiag[j];
-      TC w = 0;
-      for (int i = j + lane; i < l; i += 32) w += ((i == j) ? v0 : Ds[c * LD + i]) * Qs[q * LD + i];
-      w = warp_sum(w) * beta;
-      for (int i = j + lane; i < l; i += 32) Qs[q * LD + i] -= w * ((i == j) ? v0 : Ds[c * LD + i]);
-      __syncwarp();
+  // R (diag(R) >= 0 by flipping rows with a negative pivot) from each pivot column's owner
+  double fa = 0.0, fb = 0.0;
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int jp = posof[u];
+    if (jp < 0) continue;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int i = lane + 32 * r;
+      if (i >= l) continue;
+      TC val;
+      if (i < jp) val = (rdiag[i] < TC(0) ? TC(-1) : TC(1)) * d[u][r];
+      else if (i == jp) val = fabs(rdiag[i]);
+      else val = 0;
+      if (r_transposed) Rg[jp * ldr + i] = (double)val;
+      else Rg[i * ldr + jp] = (double)val;
+      fa += (double)val * (double)val;
+      if (i < k) fb += (double)val * (double)val;
     }
   }
-  __syncthreads();
-  // signs so that diag(R) >= 0; write R (or R^T), Q~, perm
-  for (int e = tid; e < l * l; e += blockDim.x) {
-    const int i = e / l, jj = e % l;   // R[i][jj]
-    const TC sg = rdiag[i] < TC(0) ? TC(-1) : TC(1);
-    TC r;
-    if (jj < i) r = 0;
-    else if (jj == i) r = fabs(rdiag[i]);
-    else r = sg * Ds[pcol[jj] * LD + i];
-    if (r_transposed) Rg[jj * ldr + i] = (double)r;
-    else Rg[i * ldr + jj] = (double)r;
-    const TC sq = rdiag[jj] < TC(0) ? TC(-1) : TC(1);
-    Qg[i * ldq + jj] = (double)(sq * Qs[jj * LD + i]);
+  fa = warp_sum(fa);
+  fb = warp_sum(fb);
+  if (lane == 0) { red[warp][0] = fa; red[warp][1] = fb; }
+  // Q~: column q = H_0 ... H_q e_q (registers reuse the warp's column slots)
+  TC qv[U][4];
+#pragma unroll
+  for (int u = 0; u < U; ++u)
+#pragma unroll
+    for (int r = 0; r < 4; ++r) qv[u][r] = (warp + NW * u == lane + 32 * r) ? TC(1) : TC(0);
+  for (int j = l - 1; j >= 0; --j) {
+    const TC beta = betas[j];
+    TC v[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int i = lane + 32 * r;
+      v[r] = (i >= j && i < l) ? Vs[j * kMaxL + i] : TC(0);
+    }
+    TC w[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) w[u] = v[0] * qv[u][0] + v[1] * qv[u][1] + v[2] * qv[u][2] + v[3] * qv[u][3];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int u = 0; u < U; ++u) w[u] += __shfl_xor_sync(0xffffffffu, w[u], o);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (warp + NW * u < j) continue;       // H_j leaves e_q untouched for q < j
+      const TC f = beta * w[u];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) qv[u][r] -= f * v[r];
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int q = warp + NW * u;
+    if (q >= l) continue;
+    const TC sg = rdiag[q] < TC(0) ? TC(-1) : TC(1);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int i = lane + 32 * r;
+      if (i < l) Qg[i * ldq + q] = (double)(sg * qv[u][r]);
+    }
   }
   for (int j = tid; j < l; j += blockDim.x) perm[j] = pcol[j];
-  // ||R||_F^2 and ||R(1:k,:)||_F^2 in FP64
   __syncthreads();
-  if (warp == 0) {
+  if (tid == 0) {
     double a = 0.0, b = 0.0;
-    for (int e = lane; e < l * l; e += 32) {
-      const int i = e / l, jj = e % l;
-      if (jj < i) continue;
-      const double r = (jj == i) ? (double)rdiag[i] : (double)Ds[pcol[jj] * LD + i];
-      a += r * r;
-      if (i < k) b += r * r;
+    for (int w2 = 0; w2 < NW; ++w2) { a += red[w2][0]; b += red[w2][1]; }
+    if (fro2) { fro2[0] = a; fro2[1] = b; }
+    if (status) { status->fro2_T = a; status->fro2_Tk = b; }
+  }
+}
+
+// FP32 variant with columns in registers: thread (c, h) holds rows
+// i = 64 h .. 64 h + 63 of column c, so every column reduction is a per-thread
+// sum (four independent partial sums) plus one shuffle.  The published
+// reflector is zero outside rows j..l-1, so it is applied with unpredicated
+// vector loads.  Step j: trailing norms are published by position; after a
+// barrier every warp evaluates the same argmax and applies the same swap to
+// its copy of the position map; the two threads of the pivot column publish
+// the reflector; after a second barrier every trailing column is updated and
+// its trailing norm recomputed exactly.  Same choices as the warp-per-column
+// kernel (first maximum by current position).
+template <int N>
+__device__ __forceinline__ float dotN(const float* __restrict__ v, const float (&x)[N]) {
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+  const float4* v4 = reinterpret_cast<const float4*>(v);
+#pragma unroll
+  for (int q = 0; q < N / 4; ++q) {
+    const float4 t = v4[q];
+    s0 = fmaf(t.x, x[4 * q + 0], s0);
+    s1 = fmaf(t.y, x[4 * q + 1], s1);
+    s2 = fmaf(t.z, x[4 * q + 2], s2);
+    s3 = fmaf(t.w, x[4 * q + 3], s3);
+  }
+  return (s0 + s1) + (s2 + s3);
+}
+
+template <int N>
+__device__ __forceinline__ void axpyN(const float* __restrict__ v, float f, float (&x)[N]) {
+  const float4* v4 = reinterpret_cast<const float4*>(v);
+#pragma unroll
+  for (int q = 0; q < N / 4; ++q) {
+    const float4 t = v4[q];
+    x[4 * q + 0] = fmaf(-f, t.x, x[4 * q + 0]);
+    x[4 * q + 1] = fmaf(-f, t.y, x[4 * q + 1]);
+    x[4 * q + 2] = fmaf(-f, t.z, x[4 * q + 2]);
+    x[4 * q + 3] = fmaf(-f, t.w, x[4 * q + 3]);
+  }
+}
+
+template <int TPC>
+__global__ void __launch_bounds__(kMaxL * TPC) qrcp_reg_kernel(const double* __restrict__ Dg, int64_t ldd, int l, int k,
+                                                       double* __restrict__ Qg, int64_t ldq, double* __restrict__ Rg,
+                                                       int64_t ldr, int r_transposed, int32_t* __restrict__ perm,
+                                                       double* __restrict__ fro2, DevStatus* status) {
+  constexpr int RPT = kMaxL / TPC, NWARP = kMaxL * TPC / 32;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* Vs = reinterpret_cast<float*>(smem_raw);   // Vs[j * kMaxL + i], zero outside rows j..l-1
+  __shared__ float npos[kMaxL];       // trailing norms by current position
+  __shared__ float betas[kMaxL];
+  __shared__ float rdiag[kMaxL];
+  __shared__ int pcol[kMaxL];
+  __shared__ double red[NWARP][2];
+  const int tid = threadIdx.x, c = tid / TPC, h = tid % TPC, lane = tid & 31, warp = tid >> 5;
+  const int i0 = RPT * h;
+  const unsigned pair = ((TPC == 32) ? 0xffffffffu : ((1u << TPC) - 1u)) << (lane & ~(TPC - 1));
+  float d[RPT];
+#pragma unroll
+  for (int r = 0; r < RPT; ++r) {
+    const int i = i0 + r;
+    d[r] = (c < l && i < l) ? (float)Dg[i * ldd + c] : 0.f;
+  }
+  int map[4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) map[r] = lane + 32 * r;
+  int mypos = c;
+  bool trailing = c < l;
+  int posof = -1;
+  {
+    float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+    for (int r = 0; r < RPT; r += 2) { s0 = fmaf(d[r], d[r], s0); s1 = fmaf(d[r + 1], d[r + 1], s1); }
+    float ss = s0 + s1;
+#pragma unroll
+    for (int o = 1; o < TPC; o <<= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    if (h == 0 && c < l) npos[c] = ss;
+  }
+  __syncthreads();
+  for (int j = 0; j < l; ++j) {
+    float best = -1.f;
+    int bpos = l;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int pos = lane + 32 * r;
+      if (pos >= j && pos < l) {
+        const float nv = npos[pos];
+        if (nv > best) { best = nv; bpos = pos; }
+      }
     }
-    a = warp_sum(a);
-    b = warp_sum(b);
-    if (lane == 0) {
-      if (fro2) { fro2[0] = a; fro2[1] = b; }
-      if (status) { status->fro2_T = a; status->fro2_Tk = b; }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int op = __shfl_xor_sync(0xffffffffu, bpos, o);
+      if (ob > best || (ob == best && op < bpos)) { best = ob; bpos = op; }
     }
+    const int cj = __shfl_sync(0xffffffffu, sel4(map, j >> 5), j & 31);
+    const int cp = __shfl_sync(0xffffffffu, sel4(map, (bpos >> 5) & 3), bpos & 31);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int pos = lane + 32 * r;
+      if (pos == j) map[r] = cp;
+      else if (pos == bpos) map[r] = cj;
+    }
+    if (c == cj) mypos = bpos;
+    if (c == cp) mypos = j;
+    float* vrow = Vs + j * kMaxL;
+    if (c == cp) {
+      // reflector of the pivot column, rows j..l-1 (zero elsewhere)
+      float s0 = 0.f, s1 = 0.f, x0 = 0.f;
+#pragma unroll
+      for (int r = 0; r < RPT; ++r) {
+        const int i = i0 + r;
+        const float x = (i >= j && i < l) ? d[r] : 0.f;
+        if (r & 1) s1 = fmaf(x, x, s1); else s0 = fmaf(x, x, s0);
+        if (i == j) x0 = d[r];
+      }
+      float ss = s0 + s1;
+#pragma unroll
+      for (int o = 1; o < TPC; o <<= 1) {
+        ss += __shfl_xor_sync(pair, ss, o);
+        x0 += __shfl_xor_sync(pair, x0, o);
+      }
+      const float nrm = sqrtf(ss);
+      float alpha, v0, beta;
+      if (nrm == 0.f) {
+        alpha = 0.f; v0 = 1.f; beta = 0.f;
+      } else {
+        alpha = (x0 >= 0.f) ? -nrm : nrm;
+        v0 = x0 - alpha;
+        beta = 1.f / (nrm * (nrm + fabsf(x0)));
+      }
+      float4* v4 = reinterpret_cast<float4*>(vrow + i0);
+#pragma unroll
+      for (int q = 0; q < RPT / 4; ++q) {
+        float4 t;
+        float* tp = &t.x;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int r = 4 * q + e, i = i0 + r;
+          tp[e] = (i == j) ? v0 : ((i > j && i < l) ? d[r] : 0.f);
+        }
+        v4[q] = t;
+      }
+      if (h == 0) { betas[j] = beta; rdiag[j] = alpha; pcol[j] = cp; }
+      trailing = false;
+      posof = j;
+    }
+    __syncthreads();
+    if (trailing) {
+      const float beta = betas[j];
+      float w = dotN<RPT>(vrow + i0, d);
+#pragma unroll
+      for (int o = 1; o < TPC; o <<= 1) w += __shfl_xor_sync(pair, w, o);
+      axpyN<RPT>(vrow + i0, beta * w, d);
+      float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+      for (int r = 0; r < RPT; ++r) {
+        const float x = (i0 + r > j) ? d[r] : 0.f;
+        if (r & 1) s1 = fmaf(x, x, s1); else s0 = fmaf(x, x, s0);
+      }
+      float ns = s0 + s1;
+#pragma unroll
+      for (int o = 1; o < TPC; o <<= 1) ns += __shfl_xor_sync(pair, ns, o);
+      if (h == 0) npos[mypos] = ns;
+    }
+    __syncthreads();
+  }
+  // R from each pivot column (rows above its position), diag(R) >= 0
+  double fa = 0.0, fb = 0.0;
+  if (posof >= 0) {
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      const int i = i0 + r;
+      if (i >= l) continue;
+      float val;
+      if (i < posof) val = (rdiag[i] < 0.f ? -1.f : 1.f) * d[r];
+      else if (i == posof) val = fabsf(rdiag[i]);
+      else val = 0.f;
+      if (r_transposed) Rg[posof * ldr + i] = (double)val;
+      else Rg[i * ldr + posof] = (double)val;
+      fa += (double)val * (double)val;
+      if (i < k) fb += (double)val * (double)val;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    fa += __shfl_xor_sync(0xffffffffu, fa, o);
+    fb += __shfl_xor_sync(0xffffffffu, fb, o);
+  }
+  if (lane == 0) { red[warp][0] = fa; red[warp][1] = fb; }
+  // Q~ column q = c: H_0 ... H_q e_q (reflectors are zero-padded)
+#pragma unroll
+  for (int r = 0; r < RPT; ++r) d[r] = (i0 + r == c) ? 1.f : 0.f;
+  for (int j = (c < l ? c : -1); j >= 0; --j) {
+    const float* vrow = Vs + j * kMaxL + i0;
+    float w = dotN<RPT>(vrow, d);
+#pragma unroll
+    for (int o = 1; o < TPC; o <<= 1) w += __shfl_xor_sync(pair, w, o);
+    axpyN<RPT>(vrow, betas[j] * w, d);
+  }
+  if (c < l) {
+    const float sg = rdiag[c] < 0.f ? -1.f : 1.f;
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      const int i = i0 + r;
+      if (i < l) Qg[i * ldq + c] = (double)(sg * d[r]);
+    }
+  }
+  for (int j = tid; j < l; j += blockDim.x) perm[j] = pcol[j];
+  __syncthreads();
+  if (tid == 0) {
+    double a2 = 0.0, b2 = 0.0;
+    for (int w2 = 0; w2 < NWARP; ++w2) { a2 += red[w2][0]; b2 += red[w2][1]; }
+    if (fro2) { fro2[0] = a2; fro2[1] = b2; }
+    if (status) { status->fro2_T = a2; status->fro2_Tk = b2; }
   }
 }
 
 template <typename TC>
 cudaError_t launch_qrcp(const double* D, int64_t ldd, int l, int k, double* Q, int64_t ldq, double* R, int64_t ldr,
                         bool r_transposed, int32_t* perm, double* fro2, DevStatus* status, cudaStream_t st) {
-  const size_t smem = (size_t)2 * l * (l + 1) * sizeof(TC);
+  const size_t smem = (size_t)l * kMaxL * sizeof(TC);
+  if constexpr (sizeof(TC) == 4) {
+    cudaError_t e = cudaFuncSetAttribute(qrcp_reg_kernel<kQrcpTPC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    qrcp_reg_kernel<kQrcpTPC><<<1, kMaxL * kQrcpTPC, smem, st>>>(D, ldd, l, k, Q, ldq, R, ldr, r_transposed ? 1 : 0,
+                                                                 perm, fro2, status);
+    CORUTV_COUNT_LAUNCH();
+    return cudaGetLastError();
+  }
   cudaError_t e = cudaFuncSetAttribute(qrcp_kernel<TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   qrcp_kernel<TC><<<1, 512, smem, st>>>(D, ldd, l, k, Q, ldq, R, ldr, r_transposed ? 1 : 0, perm, fro2, status); CORUTV_COUNT_LAUNCH();
