@@ -16,53 +16,68 @@
 namespace corutv {
 
 constexpr int kCholTPR = 8;   // threads per row of the register Cholesky (1024 threads)
-constexpr int kQrcpTPC = 8;   // threads per column of the register QRCP (1024 threads)
+constexpr int kQrcpTPC = 4;   // threads per column of the register QRCP (512 threads)
 
 // =============================================================================== Gram
 // parts[c] = X[:, cols_c] Y[:, cols_c]^T over the c-th contiguous column range.
-// Outer-product tiling: thread (tx, ty) owns rows a = R ty + (0..R-1) and
-// columns b = R tx + (0..R-1) (R = LP / 16); the stage holds X and Y
-// transposed in shared memory (k-major rows padded by 4) so each k step is
-// two R-wide vector loads and R^2 FMAs.
+// 512 threads, thread (tx, ty) (32 x 16) owns rows a = R ty + (0..R-1) and
+// columns b = C tx + (0..C-1) (R = LP/16, C = LP/32).  Stages of BK columns
+// are kept k-major in shared memory (rows padded by 4); the next stage's
+// global loads are issued into registers before the current stage is used.
 template <typename TC, int LP>
-__global__ void __launch_bounds__(256) gram_partial_kernel(const TC* __restrict__ Xt, int64_t ldx,
+__global__ void __launch_bounds__(512) gram_partial_kernel(const TC* __restrict__ Xt, int64_t ldx,
                                                            const TC* __restrict__ Yt, int64_t ldy, int64_t len,
                                                            int l, TC* __restrict__ parts) {
-  constexpr int R = LP / 16;
+  constexpr int R = LP / 16, CC = LP / 32;
   constexpr int BK = 32;
   constexpr int LPP = LP + 4;
+  constexpr int PER = LP * BK / 512;        // elements of X (and of Y) staged per thread
   __shared__ __align__(16) TC Xs[BK][LPP];
   __shared__ __align__(16) TC Ys[BK][LPP];
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
   const int64_t chunk = cdiv(cdiv(len, BK), gridDim.x) * BK;
   const int64_t c0 = blockIdx.x * chunk;
   int64_t c1 = c0 + chunk;
   if (c1 > len) c1 = len;
-  TC acc[R][R];
+  TC acc[R][CC];
 #pragma unroll
   for (int v = 0; v < R; ++v)
 #pragma unroll
-    for (int u = 0; u < R; ++u) acc[v][u] = TC(0);
-  for (int64_t k0 = c0; k0 < c1; k0 += BK) {
-    for (int x = tid; x < LP * BK; x += 256) {
+    for (int u = 0; u < CC; ++u) acc[v][u] = TC(0);
+  TC px[PER], py[PER];
+  auto fetch = [&](int64_t k0) {
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int x = tid + 512 * q;
       const int r = x / BK, kk = x % BK;
       const int64_t g = k0 + kk;
       const bool ok = r < l && g < c1;
-      Xs[kk][r] = ok ? Xt[r * ldx + g] : TC(0);
-      Ys[kk][r] = ok ? Yt[r * ldy + g] : TC(0);
+      px[q] = ok ? Xt[r * ldx + g] : TC(0);
+      py[q] = ok ? Yt[r * ldy + g] : TC(0);
+    }
+  };
+  if (c0 < c1) fetch(c0);
+  for (int64_t k0 = c0; k0 < c1; k0 += BK) {
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int x = tid + 512 * q;
+      const int r = x / BK, kk = x % BK;
+      Xs[kk][r] = px[q];
+      Ys[kk][r] = py[q];
     }
     __syncthreads();
+    if (k0 + BK < c1) fetch(k0 + BK);
 #pragma unroll 4
     for (int kk = 0; kk < BK; ++kk) {
-      TC xa[R], yb[R];
+      TC xa[R], yb[CC];
 #pragma unroll
       for (int v = 0; v < R; ++v) xa[v] = Xs[kk][R * ty + v];
 #pragma unroll
-      for (int u = 0; u < R; ++u) yb[u] = Ys[kk][R * tx + u];
+      for (int u = 0; u < CC; ++u) yb[u] = Ys[kk][CC * tx + u];
 #pragma unroll
       for (int v = 0; v < R; ++v)
 #pragma unroll
-        for (int u = 0; u < R; ++u) acc[v][u] = fma(xa[v], yb[u], acc[v][u]);
+        for (int u = 0; u < CC; ++u) acc[v][u] = fma(xa[v], yb[u], acc[v][u]);
     }
     __syncthreads();
   }
@@ -70,7 +85,7 @@ __global__ void __launch_bounds__(256) gram_partial_kernel(const TC* __restrict_
 #pragma unroll
   for (int v = 0; v < R; ++v)
 #pragma unroll
-    for (int u = 0; u < R; ++u) out[(R * ty + v) * LP + R * tx + u] = acc[v][u];
+    for (int u = 0; u < CC; ++u) out[(R * ty + v) * LP + CC * tx + u] = acc[v][u];
 }
 
 // G[a][b] = sum over parts in a fixed order, in FP64: four threads per element
@@ -112,13 +127,13 @@ cudaError_t launch_gram(const TC* Xt, int64_t ldx, const TC* Yt, int64_t ldy, in
   int LP;
   if (l <= 32) {
     LP = 32;
-    gram_partial_kernel<TC, 32><<<gparts, 256, 0, st>>>(Xt, ldx, Yt, ldy, len, l, parts); CORUTV_COUNT_LAUNCH();
+    gram_partial_kernel<TC, 32><<<gparts, 512, 0, st>>>(Xt, ldx, Yt, ldy, len, l, parts); CORUTV_COUNT_LAUNCH();
   } else if (l <= 64) {
     LP = 64;
-    gram_partial_kernel<TC, 64><<<gparts, 256, 0, st>>>(Xt, ldx, Yt, ldy, len, l, parts); CORUTV_COUNT_LAUNCH();
+    gram_partial_kernel<TC, 64><<<gparts, 512, 0, st>>>(Xt, ldx, Yt, ldy, len, l, parts); CORUTV_COUNT_LAUNCH();
   } else {
     LP = 128;
-    gram_partial_kernel<TC, 128><<<gparts, 256, 0, st>>>(Xt, ldx, Yt, ldy, len, l, parts); CORUTV_COUNT_LAUNCH();
+    gram_partial_kernel<TC, 128><<<gparts, 512, 0, st>>>(Xt, ldx, Yt, ldy, len, l, parts); CORUTV_COUNT_LAUNCH();
   }
   gram_reduce_kernel<TC><<<(unsigned)cdiv((int64_t)l * l * 4, 256), 256, 0, st>>>(parts, gparts, LP, l, G, ldg); CORUTV_COUNT_LAUNCH();
   return cudaGetLastError();
@@ -319,6 +334,59 @@ __global__ void __launch_bounds__(kMaxL * TPR) cholinv_reg_kernel(const double* 
   if (lane == 0 && nfall && status) atomicAdd(&status->chol_fallbacks, nfall);
 }
 
+// C (M x N) = op(A) B over K in shared memory, 4 x 4 register tiles spread
+// over the block's threads.  op(A)[r][k] = A[k][r] (TRANS_A) or A[r][k].
+// MODE 0: C = result, 1: C -= result, 2: C = -result.  upper_only skips
+// tiles strictly below the diagonal.  M, N multiples of 4; rows 16-byte aligned.
+template <bool TRANS_A, int MODE>
+__device__ __forceinline__ void smem_gemm44(const float* __restrict__ Ap, int lda, const float* __restrict__ Bp,
+                                            int ldb, float* __restrict__ Cp, int ldc, int M, int N, int K,
+                                            bool upper_only) {
+  const int tn = N >> 2, tiles = (M >> 2) * tn;
+  for (int t = threadIdx.x; t < tiles; t += blockDim.x) {
+    const int r0 = (t / tn) << 2, c0 = (t % tn) << 2;
+    if (upper_only && c0 + 3 < r0) continue;
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+#pragma unroll 4
+    for (int k = 0; k < K; ++k) {
+      float a[4];
+      if (TRANS_A) {
+        const float4 v = *reinterpret_cast<const float4*>(Ap + k * lda + r0);
+        a[0] = v.x; a[1] = v.y; a[2] = v.z; a[3] = v.w;
+      } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[i] = Ap[(r0 + i) * lda + k];
+      }
+      const float4 b = *reinterpret_cast<const float4*>(Bp + k * ldb + c0);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        acc[i][0] = fmaf(a[i], b.x, acc[i][0]);
+        acc[i][1] = fmaf(a[i], b.y, acc[i][1]);
+        acc[i][2] = fmaf(a[i], b.z, acc[i][2]);
+        acc[i][3] = fmaf(a[i], b.w, acc[i][3]);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      float4* c4 = reinterpret_cast<float4*>(Cp + (r0 + i) * ldc + c0);
+      float4 v;
+      if (MODE == 1) {
+        v = *c4;
+        v.x -= acc[i][0]; v.y -= acc[i][1]; v.z -= acc[i][2]; v.w -= acc[i][3];
+      } else if (MODE == 2) {
+        v = make_float4(-acc[i][0], -acc[i][1], -acc[i][2], -acc[i][3]);
+      } else {
+        v = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+      }
+      *c4 = v;
+    }
+  }
+}
+
 // FP32 blocked variant (l <= 128, padded with an identity block to 128 = 4
 // blocks of 32).  For each diagonal block o = 32 kb:
 //   1. one warp factors the 32 x 32 block by the same symmetric elimination
@@ -344,26 +412,30 @@ __global__ void __launch_bounds__(512) cholinv_blk_kernel(const double* __restri
   __shared__ double red[16];
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
 
-  double tr = 0.0;
-  for (int e = tid; e < N * N; e += nt) {
-    const int a = e / N, b = e % N;
-    float v;
-    if (a < l && b < l) {
-      const double g = G[a * ldg + b];
-      v = (float)g;
-      if (a == b) tr += g;
-    } else {
-      v = (a == b) ? 1.f : 0.f;
+  // 32 independent loads per thread, issued before any use (no accumulation in the loop)
+  {
+    float v[N * N / 512];
+#pragma unroll
+    for (int q = 0; q < N * N / 512; ++q) {
+      const int e = tid + 512 * q, a = e >> 7, b = e & (N - 1);
+      v[q] = (a < l && b < l) ? (float)G[a * ldg + b] : ((a == b) ? 1.f : 0.f);
     }
-    A[a * LD + b] = v;
-    X[a * LD + b] = 0.f;
+#pragma unroll
+    for (int q = 0; q < N * N / 512; ++q) {
+      const int e = tid + 512 * q, a = e >> 7, b = e & (N - 1);
+      A[a * LD + b] = v[q];
+      X[a * LD + b] = 0.f;
+    }
   }
+  __syncthreads();
+  double tr = (tid < l) ? (double)A[tid * LD + tid] : 0.0;
   for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
   if (lane == 0) red[warp] = tr;
   __syncthreads();
   double trace = 0.0;
   for (int w = 0; w < nt / 32; ++w) trace += red[w];
   const float shift = (float)(shift_rel * trace);
+  const float tolf = (float)tol_rel;
   for (int a = tid; a < N; a += nt) {
     if (a < l) A[a * LD + a] += shift;
     diag0[a] = A[a * LD + a];
@@ -380,22 +452,29 @@ __global__ void __launch_bounds__(512) cholinv_blk_kernel(const double* __restri
         a[r] = A[(o + r) * LD + o + lane];
         w[r] = (r == lane) ? 1.f : 0.f;
       }
+      const float dg0 = diag0[o + lane];
+      float* prow = T;        // staging of the multipliers of step j (T is free here)
       float dv = 1.f;          // pivot of row `lane`
       bool dp = false;
 #pragma unroll
       for (int j = 0; j < NB; ++j) {
+        // lane j owns the pivot: publish m_k = A[j][k] / d for every k (A[j][k] = lane k's a[j])
         const float d = __shfl_sync(0xffffffffu, a[j], j);
-        const bool depj = !(d > tol_rel * diag0[o + j]) || !(diag0[o + j] > 0.f);
-        const float inv_d = depj ? 0.f : 1.f / d;
+        const float d0 = __shfl_sync(0xffffffffu, dg0, j);
+        const bool depj = !(d > tolf * d0) || !(d0 > 0.f);
+        const float inv_d = depj ? 0.f : __frcp_rn(d);
         if (lane == j) { dv = depj ? 1.f : d; dp = depj; }
-        const float rowj_a = a[j];            // A[j][lane] (row j of this column)
+        prow[lane] = a[j] * inv_d;            // m_lane (used for k > j)
+        __syncwarp();
+        const float rowj_a = a[j];            // A[j][lane]
         const float rowj_w = w[j];            // L^-1[j][lane]
 #pragma unroll
         for (int k = j + 1; k < NB; ++k) {
-          const float m = __shfl_sync(0xffffffffu, a[j], k) * inv_d;   // A[j][k] / d
-          a[k] -= m * rowj_a;                 // row k of column lane (meaningful for lane >= k)
-          w[k] -= m * rowj_w;                 // row k of L^-1, column lane
+          const float m = prow[k];
+          a[k] = fmaf(-m, rowj_a, a[k]);
+          w[k] = fmaf(-m, rowj_w, w[k]);
         }
+        __syncwarp();
       }
       // lane holds column `lane` of U = D L^T and of L^-1; its pivot is dv
       const float sq = sqrtf(dv);
@@ -416,35 +495,21 @@ __global__ void __launch_bounds__(512) cholinv_blk_kernel(const double* __restri
     }
     __syncthreads();
     if (rest > 0) {
-      // ---- 2. panel R12 = R11^-T A12 into T (NB x rest), then back into A
-      for (int e = tid; e < NB * rest; e += nt) {
-        const int k = e / rest, c = o + NB + e % rest;
-        float s0 = 0.f, s1 = 0.f;
-        int p = 0;
-        for (; p + 1 <= k; p += 2) {
-          s0 = fmaf(X[(o + p) * LD + o + k], A[(o + p) * LD + c], s0);
-          s1 = fmaf(X[(o + p + 1) * LD + o + k], A[(o + p + 1) * LD + c], s1);
-        }
-        if (p <= k) s0 = fmaf(X[(o + p) * LD + o + k], A[(o + p) * LD + c], s0);
-        T[k * LD + c] = dep[o + k] ? 0.f : s0 + s1;
+      const int c0 = o + NB;
+      // ---- 2. panel R12 = R11^-T A12 (R11^-1 upper, zero below) into T, rows of dependent columns zeroed
+      smem_gemm44<true, 0>(X + o * LD + o, LD, A + o * LD + c0, LD, T + c0, LD, NB, rest, NB, false);
+      __syncthreads();
+      for (int e = threadIdx.x; e < NB * rest; e += blockDim.x) {
+        const int k = e / rest, c = c0 + e % rest;
+        if (dep[o + k]) T[k * LD + c] = 0.f;
       }
       __syncthreads();
-      for (int e = tid; e < NB * rest; e += nt) {
-        const int k = e / rest, c = o + NB + e % rest;
+      for (int e = threadIdx.x; e < NB * rest; e += blockDim.x) {
+        const int k = e / rest, c = c0 + e % rest;
         A[(o + k) * LD + c] = T[k * LD + c];
       }
-      // ---- 3. trailing update, upper triangle: A22[a][b] -= sum_k R12[k][a] R12[k][b]
-      for (int e = tid; e < rest * rest; e += nt) {
-        const int a = o + NB + e / rest, b = o + NB + e % rest;
-        if (b < a) continue;
-        float s0 = 0.f, s1 = 0.f;
-#pragma unroll 8
-        for (int k = 0; k < NB; k += 2) {
-          s0 = fmaf(T[k * LD + a], T[k * LD + b], s0);
-          s1 = fmaf(T[(k + 1) * LD + a], T[(k + 1) * LD + b], s1);
-        }
-        A[a * LD + b] -= s0 + s1;
-      }
+      // ---- 3. trailing update (upper tiles): A22 -= R12^T R12
+      smem_gemm44<true, 1>(T + c0, LD, T + c0, LD, A + c0 * LD + c0, LD, rest, rest, NB, true);
       __syncthreads();
     }
   }
@@ -454,28 +519,35 @@ __global__ void __launch_bounds__(512) cholinv_blk_kernel(const double* __restri
   //   X[r][c] = -sum_{q=ok}^{c} S[r][q] X[q][c]    (staged in A's unused lower triangle).
   for (int kb = 1; kb < N / NB; ++kb) {
     const int ok = NB * kb;
-    for (int e = tid; e < ok * NB; e += nt) {
-      const int r = e / NB, c = ok + e % NB;
-      float s0 = 0.f, s1 = 0.f;
-      int p = r;
-      for (; p + 1 < ok; p += 2) {
-        s0 = fmaf(X[r * LD + p], A[p * LD + c], s0);
-        s1 = fmaf(X[r * LD + p + 1], A[(p + 1) * LD + c], s1);
+    // S = X[0:ok, 0:ok] R[0:ok, ok:ok+NB] into T-sized staging (rows of X are zero left of the diagonal)
+    // staged in X's own (r, ok..ok+NB) slots, which are still zero and not read here
+    smem_gemm44<false, 0>(X, LD, A + ok, LD, X + ok, LD, ok, NB, ok, false);
+    __syncthreads();
+    // X[r, ok:ok+NB] = -S[r, :] X_kk, one row per thread (read the row, then overwrite it)
+    for (int r = tid; r < ok; r += nt) {
+      float sv[NB], out[NB];
+#pragma unroll
+      for (int q = 0; q < NB; q += 4) {
+        const float4 v = *reinterpret_cast<const float4*>(X + r * LD + ok + q);
+        sv[q] = v.x; sv[q + 1] = v.y; sv[q + 2] = v.z; sv[q + 3] = v.w;
       }
-      if (p < ok) s0 = fmaf(X[r * LD + p], A[p * LD + c], s0);
-      X[r * LD + c] = s0 + s1;
-    }
-    __syncthreads();
-    for (int e = tid; e < ok * NB; e += nt) {
-      const int r = e / NB, c = ok + e % NB;
-      float s0 = 0.f;
-      for (int q = ok; q <= c; ++q) s0 = fmaf(X[r * LD + q], X[q * LD + c], s0);
-      A[c * LD + r] = -s0;
-    }
-    __syncthreads();
-    for (int e = tid; e < ok * NB; e += nt) {
-      const int r = e / NB, c = ok + e % NB;
-      X[r * LD + c] = A[c * LD + r];
+#pragma unroll
+      for (int c = 0; c < NB; ++c) out[c] = 0.f;
+#pragma unroll
+      for (int q = 0; q < NB; ++q) {
+        const float* xk = X + (ok + q) * LD + ok;
+#pragma unroll
+        for (int c = 0; c < NB; c += 4) {
+          const float4 v = *reinterpret_cast<const float4*>(xk + c);
+          out[c] = fmaf(sv[q], v.x, out[c]);
+          out[c + 1] = fmaf(sv[q], v.y, out[c + 1]);
+          out[c + 2] = fmaf(sv[q], v.z, out[c + 2]);
+          out[c + 3] = fmaf(sv[q], v.w, out[c + 3]);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < NB; c += 4)
+        *reinterpret_cast<float4*>(X + r * LD + ok + c) = make_float4(-out[c], -out[c + 1], -out[c + 2], -out[c + 3]);
     }
     __syncthreads();
   }
@@ -537,6 +609,7 @@ __global__ void __launch_bounds__(256) lmul_kernel(const TC* __restrict__ In, in
     const int p = e / LP, j = e % LP;
     Ss[p * SP + j] = (p < l && j < l) ? (TC)S[p * lds + j] : TC(0);
   }
+  // (S rows p >= l and columns j >= l are zero: the p loop below can stop at l)
   for (int e = tid; e < LP * BI; e += 256) {
     const int p = e / BI, ii = e % BI;
     const int64_t g = i0 + ii;
@@ -613,7 +686,7 @@ static cudaError_t lmul_variant(const TC* In, int64_t ldi, int64_t len, int l, c
 template <typename TC, typename TS>
 static cudaError_t lmul_dispatch(const TC* In, int64_t ldi, int64_t len, int l, const TS* S, int64_t lds, TC* Out,
                                  int64_t ldo, bool rowmajor, bool upper, cudaStream_t st) {
-  constexpr int BI = sizeof(TC) == 8 ? 64 : 128;
+  constexpr int BI = 64;
   if (l <= 32) return lmul_variant<TC, TS, 32, BI>(In, ldi, len, l, S, lds, Out, ldo, rowmajor, upper, st);
   if (l <= 64) return lmul_variant<TC, TS, 64, BI>(In, ldi, len, l, S, lds, Out, ldo, rowmajor, upper, st);
   return lmul_variant<TC, TS, 128, BI>(In, ldi, len, l, S, lds, Out, ldo, rowmajor, upper, st);
@@ -1010,24 +1083,26 @@ __global__ void __launch_bounds__(kMaxL * TPC) qrcp_reg_kernel(const double* __r
                                                        double* __restrict__ Qg, int64_t ldq, double* __restrict__ Rg,
                                                        int64_t ldr, int r_transposed, int32_t* __restrict__ perm,
                                                        double* __restrict__ fro2, DevStatus* status) {
-  constexpr int RPT = kMaxL / TPC, NWARP = kMaxL * TPC / 32;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  float* Vs = reinterpret_cast<float*>(smem_raw);   // Vs[j * kMaxL + i], zero outside rows j..l-1
-  __shared__ float npos[kMaxL];       // trailing norms by current position
-  __shared__ float betas[kMaxL];
+  constexpr int RPT = kMaxL / TPC, NWARP = kMaxL * TPC / 32, CPW = 32 / TPC;   // columns per warp
+  __shared__ __align__(16) float vbuf[kMaxL];       // reflector of the current step (zero outside j..l-1)
+  __shared__ __align__(16) float pcolv[kMaxL];      // raw pivot column
+  __shared__ float npos[kMaxL];                      // trailing norms by current position
+  __shared__ float sc[2];                            // beta, alpha of the current step
+  __shared__ int piv[3];                             // pivot column, column previously at position j, its new position
   __shared__ float rdiag[kMaxL];
   __shared__ int pcol[kMaxL];
   __shared__ double red[NWARP][2];
   const int tid = threadIdx.x, c = tid / TPC, h = tid % TPC, lane = tid & 31, warp = tid >> 5;
   const int i0 = RPT * h;
-  const unsigned pair = ((TPC == 32) ? 0xffffffffu : ((1u << TPC) - 1u)) << (lane & ~(TPC - 1));
-  float d[RPT];
+  const unsigned grp = ((TPC == 32) ? 0xffffffffu : ((1u << TPC) - 1u)) << (lane & ~(TPC - 1));
+  float d[RPT], m[RPT];       // column c of D (rows i0..) and column c of M = H_j ... H_0 (rows i0..)
 #pragma unroll
   for (int r = 0; r < RPT; ++r) {
     const int i = i0 + r;
     d[r] = (c < l && i < l) ? (float)Dg[i * ldd + c] : 0.f;
+    m[r] = (i == c) ? 1.f : 0.f;
   }
-  int map[4];
+  int map[4];                 // position -> column (kept by warp 0)
 #pragma unroll
   for (int r = 0; r < 4; ++r) map[r] = lane + 32 * r;
   int mypos = c;
@@ -1044,49 +1119,59 @@ __global__ void __launch_bounds__(kMaxL * TPC) qrcp_reg_kernel(const double* __r
   }
   __syncthreads();
   for (int j = 0; j < l; ++j) {
-    float best = -1.f;
-    int bpos = l;
+    // ---- phase 1: warp 0 picks the pivot (first maximum by current position) and swaps the map
+    if (warp == 0) {
+      float best = -1.f;
+      int bpos = l;
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      const int pos = lane + 32 * r;
-      if (pos >= j && pos < l) {
-        const float nv = npos[pos];
-        if (nv > best) { best = nv; bpos = pos; }
+      for (int r = 0; r < 4; ++r) {
+        const int pos = lane + 32 * r;
+        if (pos >= j && pos < l) {
+          const float nv = npos[pos];
+          if (nv > best) { best = nv; bpos = pos; }
+        }
       }
-    }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-      const int op = __shfl_xor_sync(0xffffffffu, bpos, o);
-      if (ob > best || (ob == best && op < bpos)) { best = ob; bpos = op; }
-    }
-    const int cj = __shfl_sync(0xffffffffu, sel4(map, j >> 5), j & 31);
-    const int cp = __shfl_sync(0xffffffffu, sel4(map, (bpos >> 5) & 3), bpos & 31);
+      for (int o = 16; o > 0; o >>= 1) {
+        const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int op = __shfl_xor_sync(0xffffffffu, bpos, o);
+        if (ob > best || (ob == best && op < bpos)) { best = ob; bpos = op; }
+      }
+      const int cj = __shfl_sync(0xffffffffu, sel4(map, j >> 5), j & 31);
+      const int cp = __shfl_sync(0xffffffffu, sel4(map, (bpos >> 5) & 3), bpos & 31);
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      const int pos = lane + 32 * r;
-      if (pos == j) map[r] = cp;
-      else if (pos == bpos) map[r] = cj;
+      for (int r = 0; r < 4; ++r) {
+        const int pos = lane + 32 * r;
+        if (pos == j) map[r] = cp;
+        else if (pos == bpos) map[r] = cj;
+      }
+      if (lane == 0) { piv[0] = cp; piv[1] = cj; piv[2] = bpos; }
     }
-    if (c == cj) mypos = bpos;
+    __syncthreads();
+    const int cp = piv[0];
+    if (c == piv[1]) mypos = piv[2];
     if (c == cp) mypos = j;
-    float* vrow = Vs + j * kMaxL;
-    if (c == cp) {
-      // reflector of the pivot column, rows j..l-1 (zero elsewhere)
-      float s0 = 0.f, s1 = 0.f, x0 = 0.f;
+    // ---- phase 2: the pivot column's warp builds the reflector from a shared copy of the column
+    if (warp == cp / CPW) {
+      if (c == cp) {
+        float4* p4 = reinterpret_cast<float4*>(pcolv + i0);
 #pragma unroll
-      for (int r = 0; r < RPT; ++r) {
-        const int i = i0 + r;
-        const float x = (i >= j && i < l) ? d[r] : 0.f;
-        if (r & 1) s1 = fmaf(x, x, s1); else s0 = fmaf(x, x, s0);
-        if (i == j) x0 = d[r];
+        for (int q = 0; q < RPT / 4; ++q) p4[q] = make_float4(d[4 * q], d[4 * q + 1], d[4 * q + 2], d[4 * q + 3]);
+        trailing = false;
+        posof = j;
       }
-      float ss = s0 + s1;
+      __syncwarp();
+      const float4 x4 = reinterpret_cast<const float4*>(pcolv)[lane];   // rows 4 lane .. 4 lane + 3
+      float xv[4] = {x4.x, x4.y, x4.z, x4.w};
+      float ss = 0.f;
 #pragma unroll
-      for (int o = 1; o < TPC; o <<= 1) {
-        ss += __shfl_xor_sync(pair, ss, o);
-        x0 += __shfl_xor_sync(pair, x0, o);
+      for (int e = 0; e < 4; ++e) {
+        const int i = 4 * lane + e;
+        if (i >= j && i < l) ss = fmaf(xv[e], xv[e], ss);
       }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+      const float x0 = pcolv[j];
       const float nrm = sqrtf(ss);
       float alpha, v0, beta;
       if (nrm == 0.f) {
@@ -1096,39 +1181,56 @@ __global__ void __launch_bounds__(kMaxL * TPC) qrcp_reg_kernel(const double* __r
         v0 = x0 - alpha;
         beta = 1.f / (nrm * (nrm + fabsf(x0)));
       }
-      float4* v4 = reinterpret_cast<float4*>(vrow + i0);
+      float4 vo;
+      float* vp = &vo.x;
 #pragma unroll
-      for (int q = 0; q < RPT / 4; ++q) {
-        float4 t;
-        float* tp = &t.x;
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int r = 4 * q + e, i = i0 + r;
-          tp[e] = (i == j) ? v0 : ((i > j && i < l) ? d[r] : 0.f);
-        }
-        v4[q] = t;
+      for (int e = 0; e < 4; ++e) {
+        const int i = 4 * lane + e;
+        vp[e] = (i == j) ? v0 : ((i > j && i < l) ? xv[e] : 0.f);
       }
-      if (h == 0) { betas[j] = beta; rdiag[j] = alpha; pcol[j] = cp; }
-      trailing = false;
-      posof = j;
+      reinterpret_cast<float4*>(vbuf)[lane] = vo;
+      if (lane == 0) { sc[0] = beta; sc[1] = alpha; rdiag[j] = alpha; pcol[j] = cp; }
     }
     __syncthreads();
-    if (trailing) {
-      const float beta = betas[j];
-      float w = dotN<RPT>(vrow + i0, d);
+    // ---- phase 3: every column of M and every trailing column of D takes the reflector
+    {
+      float v[RPT];
+      const float4* v4 = reinterpret_cast<const float4*>(vbuf + i0);
 #pragma unroll
-      for (int o = 1; o < TPC; o <<= 1) w += __shfl_xor_sync(pair, w, o);
-      axpyN<RPT>(vrow + i0, beta * w, d);
+      for (int q = 0; q < RPT / 4; ++q) {
+        const float4 t = v4[q];
+        v[4 * q] = t.x; v[4 * q + 1] = t.y; v[4 * q + 2] = t.z; v[4 * q + 3] = t.w;
+      }
+      const float beta = sc[0];
+      float wm0 = 0.f, wm1 = 0.f, wd0 = 0.f, wd1 = 0.f;
+#pragma unroll
+      for (int r = 0; r < RPT; r += 2) {
+        wm0 = fmaf(v[r], m[r], wm0);
+        wm1 = fmaf(v[r + 1], m[r + 1], wm1);
+        wd0 = fmaf(v[r], d[r], wd0);
+        wd1 = fmaf(v[r + 1], d[r + 1], wd1);
+      }
+      float wm = wm0 + wm1, wd = trailing ? wd0 + wd1 : 0.f;
+#pragma unroll
+      for (int o = 1; o < TPC; o <<= 1) {
+        wm += __shfl_xor_sync(grp, wm, o);
+        wd += __shfl_xor_sync(grp, wd, o);
+      }
+      const float fm = beta * wm, fd = beta * wd;
       float s0 = 0.f, s1 = 0.f;
 #pragma unroll
       for (int r = 0; r < RPT; ++r) {
+        m[r] = fmaf(-fm, v[r], m[r]);
+        d[r] = fmaf(-fd, v[r], d[r]);          // fd = 0 for columns that are not trailing
         const float x = (i0 + r > j) ? d[r] : 0.f;
         if (r & 1) s1 = fmaf(x, x, s1); else s0 = fmaf(x, x, s0);
       }
-      float ns = s0 + s1;
+      if (trailing) {
+        float ns = s0 + s1;
 #pragma unroll
-      for (int o = 1; o < TPC; o <<= 1) ns += __shfl_xor_sync(pair, ns, o);
-      if (h == 0) npos[mypos] = ns;
+        for (int o = 1; o < TPC; o <<= 1) ns += __shfl_xor_sync(grp, ns, o);
+        if (h == 0) npos[mypos] = ns;
+      }
     }
     __syncthreads();
   }
@@ -1154,22 +1256,12 @@ __global__ void __launch_bounds__(kMaxL * TPC) qrcp_reg_kernel(const double* __r
     fb += __shfl_xor_sync(0xffffffffu, fb, o);
   }
   if (lane == 0) { red[warp][0] = fa; red[warp][1] = fb; }
-  // Q~ column q = c: H_0 ... H_q e_q (reflectors are zero-padded)
-#pragma unroll
-  for (int r = 0; r < RPT; ++r) d[r] = (i0 + r == c) ? 1.f : 0.f;
-  for (int j = (c < l ? c : -1); j >= 0; --j) {
-    const float* vrow = Vs + j * kMaxL + i0;
-    float w = dotN<RPT>(vrow, d);
-#pragma unroll
-    for (int o = 1; o < TPC; o <<= 1) w += __shfl_xor_sync(pair, w, o);
-    axpyN<RPT>(vrow, betas[j] * w, d);
-  }
+  // Q~ = H_0 ... H_{l-1} = M^T: Q~[c][q] = M[q][c] (thread holds M[i0.., c]), column sign from diag(R)
   if (c < l) {
-    const float sg = rdiag[c] < 0.f ? -1.f : 1.f;
 #pragma unroll
     for (int r = 0; r < RPT; ++r) {
-      const int i = i0 + r;
-      if (i < l) Qg[i * ldq + c] = (double)(sg * d[r]);
+      const int q = i0 + r;
+      if (q < l) Qg[c * ldq + q] = (double)((rdiag[q] < 0.f ? -1.f : 1.f) * m[r]);
     }
   }
   for (int j = tid; j < l; j += blockDim.x) perm[j] = pcol[j];
@@ -1187,10 +1279,7 @@ cudaError_t launch_qrcp(const double* D, int64_t ldd, int l, int k, double* Q, i
                         bool r_transposed, int32_t* perm, double* fro2, DevStatus* status, cudaStream_t st) {
   const size_t smem = (size_t)l * kMaxL * sizeof(TC);
   if constexpr (sizeof(TC) == 4) {
-    cudaError_t e = cudaFuncSetAttribute(qrcp_reg_kernel<kQrcpTPC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    qrcp_reg_kernel<kQrcpTPC><<<1, kMaxL * kQrcpTPC, smem, st>>>(D, ldd, l, k, Q, ldq, R, ldr, r_transposed ? 1 : 0,
+    qrcp_reg_kernel<kQrcpTPC><<<1, kMaxL * kQrcpTPC, 0, st>>>(D, ldd, l, k, Q, ldq, R, ldr, r_transposed ? 1 : 0,
                                                                  perm, fro2, status);
     CORUTV_COUNT_LAUNCH();
     return cudaGetLastError();
