@@ -60,13 +60,18 @@ typedef enum { CORUTV_CORE_EXACT = 0, CORUTV_CORE_SKETCH = 1 } corutv_core;
 typedef enum { CORUTV_ORTH_STABILISED = 0 } corutv_orth;
 typedef enum { CORUTV_F64 = 0, CORUTV_F32 = 1, CORUTV_BF16 = 2, CORUTV_FP8_E4M3 = 3 } corutv_dtype;
 typedef enum {
-  CORUTV_MMA_AUTO = 0,       /* F32 A: TF32 (rounded); other dtypes: SIMT */
+  CORUTV_MMA_AUTO = 0,       /* F32 A: TF32 (rounded); BF16 / FP8 A: BF16X2; F64 A: SIMT.  Falls back to
+                                SIMT where TMA cannot address the rows of A (see corutv_solve) */
   CORUTV_MMA_TF32 = 1,       /* tcgen05 kind::tf32 with both operands rounded to nearest TF32
                                 (A tile by tile in shared memory): unbiased products */
   CORUTV_MMA_TF32X3 = 2,     /* reserved (split-operand FP32-faithful products): returns UNSUPPORTED */
   CORUTV_MMA_SIMT = 3,       /* CUDA-core FMA in the storage precision (FP32 or FP64 products) */
-  CORUTV_MMA_TF32_TRUNC = 4  /* tcgen05 kind::tf32 reading raw FP32 (the tensor core drops the low
+  CORUTV_MMA_TF32_TRUNC = 4, /* tcgen05 kind::tf32 reading raw FP32 (the tensor core drops the low
                                 13 mantissa bits: products shrink by ~3.5e-4 on average) */
+  CORUTV_MMA_BF16X2 = 5      /* BF16 / FP8 A only: tcgen05 kind::f16 on BF16 A tiles (FP8 tiles are
+                                dequantised to BF16 in shared memory, e4m3 value x tile scale, exact
+                                when the scale is a power of two) against the sketch operand split
+                                into BF16 hi + lo parts (~16 bits kept); FP32 accumulation */
 } corutv_mma;
 
 typedef enum { CORUTV_DIR_AX = 0, CORUTV_DIR_ATY = 1 } corutv_dir;
@@ -139,7 +144,10 @@ int corutv_set_workspace(corutv_handle* h, void* dptr, size_t bytes);
  *          The tensor-core passes read A with TMA and need a 16-byte aligned base and
  *          lda * sizeof(dtype) a multiple of 16; mma = AUTO falls back to the SIMT
  *          passes when that does not hold, an explicit TF32 mode returns ERR_ALIGN.
- *   a_tile_scales  FP8 only: ceil(m/128) x ceil(n/128) float scales (row-major); else NULL.
+ *   a_tile_scales  FP8 only: ceil(m/128) x ceil(n/128) float scales (row-major); element
+ *          (i, j) of A is e4m3 code (i, j) times scale (i / 128, j / 128); else NULL.
+ *          corutv_quantize writes both.  The FP8 tensor-core pass needs lda a multiple
+ *          of 16, the BF16 one a multiple of 8 (16-byte row pitch).
  *   Phi    device, the Gaussian test matrix Psi (Sec. III): n x l (RIGHT) or m x l
  *          (LEFT) row-major, ldphi >= l, F64 for a_dtype F64 else F32.
  *   U      device out, m x l row-major (ldu >= l), same dtype as Phi.
@@ -160,6 +168,40 @@ int corutv_solve(corutv_handle* h, const corutv_params* p,
                  const void* Phi, int64_t ldphi,
                  void* U, int64_t ldu, double* T, int64_t ldt,
                  void* V, int64_t ldv, int32_t* perm);
+
+/*
+ * corutv_solve_corrected -- corutv_solve for A stored in BF16 or FP8 (a_dtype) plus
+ * the FP32 correction pass: the range finding (S1-S4 of the schedule, every pass
+ * over A) runs on the low-precision A, then the core D = Q1^T A_ref Q2 (Alg. 2
+ * step 5) is computed by one pass over the FP32 matrix A_ref (m x n row-major,
+ * lda_ref >= n, device) with the Q1, Q2 found.  Because D is the projection of
+ * A_ref onto the two bases, T then carries no storage error of A; only the
+ * subspaces do.  Requires p->core == EXACT; want_fro2 reports ||A_ref||_F^2.
+ * The pass over A_ref uses the TF32 tensor-core engine (SIMT when p->mma is SIMT
+ * or TMA cannot address A_ref's rows).  Other arguments as corutv_solve.
+ */
+int corutv_solve_corrected(corutv_handle* h, const corutv_params* p,
+                           const void* A, int64_t lda, const float* a_tile_scales,
+                           const float* A_ref, int64_t lda_ref,
+                           const void* Phi, int64_t ldphi,
+                           void* U, int64_t ldu, double* T, int64_t ldt,
+                           void* V, int64_t ldv, int32_t* perm);
+
+/*
+ * corutv_quantize -- storage conversion of an FP32 A (m x n row-major, lda) for the
+ * low-precision passes (no counterpart in the paper):
+ *   dtype BF16: out (m x n, ldo, __nv_bfloat16) = A rounded to nearest even;
+ *               tile_scales unused (may be NULL).
+ *   dtype FP8_E4M3: for every 128 x 128 tile (ragged at the edges) the scale
+ *               s = smallest power of two >= fl32(amax(|tile|) / 448) (s = 1 for an
+ *               all-zero tile) goes to tile_scales[(i/128) * ceil(n/128) + j/128] and
+ *               out (m x n, ldo bytes per row) holds e4m3(a / s), rounded to nearest
+ *               even with saturation at +-448.  a / s is exact, so each entry is
+ *               rounded once.
+ * A must be finite.  Device pointers; enqueued on the handle's stream.
+ */
+int corutv_quantize(corutv_handle* h, int dtype, const float* A, int64_t lda, int64_t m, int64_t n,
+                    void* out, int64_t ldo, float* tile_scales);
 
 /* Synchronise the handle's stream and return the outcome of the last solve. */
 int corutv_info_wait(corutv_handle* h, corutv_info* out);
@@ -196,7 +238,8 @@ int corutv_trace_read(corutv_handle* h, corutv_trace* out);
  * One streaming pass over A (Sec. III: C1 = A Psi, C2 = A^T C1; Alg. 3 steps 3-4).
  *   dir = AX : Ct (l x m, ST) = (A X)^T    with Xt (l x n, ST) = X^T
  *   dir = ATY: Ct (l x n, ST) = (A^T Y)^T  with Xt (l x m, ST) = Y^T
- * A: m x n row-major (lda), dtype a_dtype (F64 needs mma SIMT or AUTO).
+ * A: m x n row-major (lda), dtype a_dtype (F64 needs mma SIMT or AUTO; TF32 modes need F32,
+ * BF16X2 needs BF16 or FP8).
  * Rows l..(ST rows) of Xt are ignored.
  */
 int corutv_pass(corutv_handle* h, int dir, int a_dtype, int mma,

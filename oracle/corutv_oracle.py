@@ -225,7 +225,7 @@ def _check(m, n, k, l, q):
 
 
 def corutv(A: np.ndarray, Phi: np.ndarray, k: int, l: int, q: int = 0,
-           core: str = "exact", orth: str = "stabilised", side: str = "right") -> dict:
+           core: str = "exact", orth: str = "stabilised", side: str = "right", A_core=None) -> dict:
     """CoR-UTV (Alg. 2 for q = 0, Alg. 3 for q >= 0) in float64.
 
     side="right": the paper's order, Phi (= Psi) is n x l and C1 = A Psi first;
@@ -243,13 +243,23 @@ def corutv(A: np.ndarray, Phi: np.ndarray, k: int, l: int, q: int = 0,
     D_approx = Q1^T C1 (Q2^T C2_prev)^+ (Eq. (D_approx)), C2_prev being the
     non-updated sketch that produced the last C1.
 
+    A_core (optional, same shape as A, core="exact" only): the correction
+    pass of a low-precision A -- the range finding runs on A, the core is
+    the projection D = Q1^T A_core Q2 (Eq. (D)) of the full-precision matrix
+    onto the bases found.
+
     Returns U, T, V, perm (V[:, j] = Q2[:, perm[j]] for side="right"; for
     side="left" the permutation acts on U), plus the intermediates.
     """
     A = np.asarray(A, dtype=np.float64)
     Phi = np.asarray(Phi, dtype=np.float64)
+    if A_core is not None:
+        A_core = np.asarray(A_core, dtype=np.float64)
+        if A_core.shape != A.shape or core != "exact":
+            raise ValueError("A_core must match A and needs core='exact'")
     if side == "left":
-        r = corutv(A.T, Phi, k, l, q, core=core, orth=orth, side="right")
+        r = corutv(A.T, Phi, k, l, q, core=core, orth=orth, side="right",
+                   A_core=None if A_core is None else A_core.T)
         out = dict(r)
         out["U"], out["V"] = r["V"], r["U"]
         out["T"] = r["T"].T.copy()
@@ -280,7 +290,7 @@ def corutv(A: np.ndarray, Phi: np.ndarray, k: int, l: int, q: int = 0,
         raise ValueError("orth must be 'stabilised' or 'literal'")
 
     if core == "exact":
-        D = gemm(Q1.T, gemm(A, Q2))              # Alg. 2 step 5
+        D = gemm(Q1.T, gemm(A if A_core is None else A_core, Q2))   # Alg. 2 step 5
     elif core == "approx":
         D = gemm(gemm(Q1.T, C1), pinv(gemm(Q2.T, X_prev)))   # Eq. (D_approx)
     else:

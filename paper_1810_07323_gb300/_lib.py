@@ -22,7 +22,7 @@ ERR_CHOL_BREAKDOWN, ERR_BUSY, PENDING, ERR_UNSUPPORTED = 7, 8, 9, 10
 SIDE = {"right": 0, "left": 1}
 CORE = {"exact": 0, "sketch": 1}
 DTYPE = {"f64": 0, "f32": 1, "bf16": 2, "fp8": 3}
-MMA = {"auto": 0, "tf32": 1, "tf32x3": 2, "simt": 3, "tf32t": 4}
+MMA = {"auto": 0, "tf32": 1, "tf32x3": 2, "simt": 3, "tf32t": 4, "bf16x2": 5}
 DIR = {"ax": 0, "aty": 1}
 
 
@@ -62,7 +62,7 @@ _lib = None
 EXPORTS = ("corutv_version", "corutv_status_string", "corutv_create", "corutv_destroy", "corutv_set_stream",
            "corutv_workspace_size", "corutv_set_workspace", "corutv_solve", "corutv_info_wait",
            "corutv_set_tracing", "corutv_trace_read", "corutv_pass", "corutv_orthonormalize", "corutv_gram",
-           "corutv_qrcp", "corutv_fro2", "corutv_gram_noalloc")
+           "corutv_qrcp", "corutv_fro2", "corutv_gram_noalloc", "corutv_solve_corrected", "corutv_quantize")
 
 
 def load() -> ctypes.CDLL:
@@ -83,6 +83,9 @@ def load() -> ctypes.CDLL:
     lib.corutv_workspace_size.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_size_t)]
     lib.corutv_set_workspace.argtypes = [P, P, ctypes.c_size_t]
     lib.corutv_solve.argtypes = [P, ctypes.POINTER(Params), P, I64, P, P, I64, P, I64, P, I64, P, I64, P]
+    lib.corutv_solve_corrected.argtypes = [P, ctypes.POINTER(Params), P, I64, P, P, I64, P, I64, P, I64, P, I64,
+                                           P, I64, P]
+    lib.corutv_quantize.argtypes = [P, ctypes.c_int, P, I64, I64, I64, P, I64, P]
     lib.corutv_info_wait.argtypes = [P, ctypes.POINTER(Info)]
     lib.corutv_pass.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, I64, I64, I64, P, P, I64, I32, P,
                                 I64]
@@ -96,7 +99,8 @@ def load() -> ctypes.CDLL:
     lib.corutv_trace_read.argtypes = [P, ctypes.POINTER(Trace)]
     for name in ("corutv_set_tracing", "corutv_trace_read", "corutv_create", "corutv_destroy", "corutv_set_stream", "corutv_workspace_size",
                  "corutv_set_workspace", "corutv_solve", "corutv_info_wait", "corutv_pass",
-                 "corutv_orthonormalize", "corutv_gram", "corutv_qrcp", "corutv_fro2"):
+                 "corutv_orthonormalize", "corutv_gram", "corutv_qrcp", "corutv_fro2", "corutv_solve_corrected",
+                 "corutv_quantize"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -225,18 +229,21 @@ def _params(m, n, k, l, q, side, core, a_dtype_code, mma, want_fro2) -> Params:
 
 
 def solve(A, Phi, k: int, l: int, q: int = 0, side: str = "right", core: str = "exact", mma: str = "auto",
-          a_tile_scales=None, want_fro2: bool = False, out=None, wait: bool = True, handle: Handle | None = None):
+          a_tile_scales=None, want_fro2: bool = False, out=None, wait: bool = True, handle: Handle | None = None,
+          A_ref=None):
     """CoR-UTV of a device matrix A (Alg. 2 / Alg. 3): returns U, T, V, perm.
 
     A: (m, n) row-major float64 / float32 / bfloat16 / float8_e4m3fn (with
     a_tile_scales); Phi: (n, l) for side="right", (m, l) for side="left",
     float64 if A is float64 else float32.  T is float64.
+    A_ref: optional float32 (m, n) matrix for the correction pass of a
+    bfloat16 / float8 A (corutv_solve_corrected: the core D from A_ref).
     out: optional (U, T, V, perm) preallocated outputs.  wait=True
     synchronises and returns the device info; wait=False leaves the work
     enqueued on the current stream (info is None).
     """
     import torch
-    _need_cuda(A, Phi, a_tile_scales)
+    _need_cuda(A, Phi, a_tile_scales, A_ref)
     h = handle or handle_for()
     m, n = A.shape
     code = _dt_code(A)
@@ -253,14 +260,48 @@ def solve(A, Phi, k: int, l: int, q: int = 0, side: str = "right", core: str = "
     else:
         U, T, V, perm = out
     sc = a_tile_scales.data_ptr() if a_tile_scales is not None else 0
-    rc = load().corutv_solve(h.h, ctypes.byref(p), ctypes.c_void_p(A.data_ptr()), _rowmajor_ld(A),
-                             ctypes.c_void_p(sc), ctypes.c_void_p(Phi.data_ptr()), _rowmajor_ld(Phi),
-                             ctypes.c_void_p(U.data_ptr()), _rowmajor_ld(U), ctypes.c_void_p(T.data_ptr()),
-                             _rowmajor_ld(T), ctypes.c_void_p(V.data_ptr()), _rowmajor_ld(V),
-                             ctypes.c_void_p(perm.data_ptr()))
-    _check(rc, "corutv_solve")
+    tail = (ctypes.c_void_p(Phi.data_ptr()), _rowmajor_ld(Phi), ctypes.c_void_p(U.data_ptr()), _rowmajor_ld(U),
+            ctypes.c_void_p(T.data_ptr()), _rowmajor_ld(T), ctypes.c_void_p(V.data_ptr()), _rowmajor_ld(V),
+            ctypes.c_void_p(perm.data_ptr()))
+    if A_ref is None:
+        rc = load().corutv_solve(h.h, ctypes.byref(p), ctypes.c_void_p(A.data_ptr()), _rowmajor_ld(A),
+                                 ctypes.c_void_p(sc), *tail)
+        _check(rc, "corutv_solve")
+    else:
+        if A_ref.dtype != torch.float32 or tuple(A_ref.shape) != (m, n):
+            raise TypeError("A_ref must be a float32 (m, n) matrix")
+        rc = load().corutv_solve_corrected(h.h, ctypes.byref(p), ctypes.c_void_p(A.data_ptr()), _rowmajor_ld(A),
+                                           ctypes.c_void_p(sc), ctypes.c_void_p(A_ref.data_ptr()),
+                                           _rowmajor_ld(A_ref), *tail)
+        _check(rc, "corutv_solve_corrected")
     info = info_wait(h) if wait else None
     return SolveResult(U, T, V, perm, info)
+
+
+def quantize(A, dtype: str, out=None, tile_scales=None, handle: Handle | None = None):
+    """Storage conversion of a float32 device matrix (corutv_quantize):
+    dtype "bf16" -> bfloat16 A (scales None); "fp8" -> (float8_e4m3fn A, float32
+    tile scales of shape (ceil(m/128), ceil(n/128)), powers of two)."""
+    import torch
+    _need_cuda(A)
+    if A.dtype != torch.float32:
+        raise TypeError("quantize takes a float32 matrix")
+    h = handle or handle_for()
+    m, n = A.shape
+    code = DTYPE[dtype]
+    if code not in (2, 3):
+        raise ValueError("dtype must be 'bf16' or 'fp8'")
+    if out is None:
+        tdt = torch.bfloat16 if code == 2 else torch.float8_e4m3fn
+        ld = -(-n // 16) * 16          # 16-byte row pitch for the tensor-core passes
+        out = torch.empty((m, ld), dtype=tdt, device=A.device)[:, :n]
+    if code == 3 and tile_scales is None:
+        tile_scales = torch.empty((-(-m // 128), -(-n // 128)), dtype=torch.float32, device=A.device)
+    sc = tile_scales.data_ptr() if tile_scales is not None else 0
+    rc = load().corutv_quantize(h.h, code, ctypes.c_void_p(A.data_ptr()), _rowmajor_ld(A), m, n,
+                                ctypes.c_void_p(out.data_ptr()), _rowmajor_ld(out), ctypes.c_void_p(sc))
+    _check(rc, "corutv_quantize")
+    return (out, tile_scales) if code == 3 else (out, None)
 
 
 def info_wait(h: Handle | None = None) -> Info:

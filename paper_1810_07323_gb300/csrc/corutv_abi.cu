@@ -128,9 +128,16 @@ size_t pass_partial_bytes(int64_t m, int64_t n, int l, int a_dtype, int sms) {
   // both directions, both engines (the plan does not depend on the engine chosen later)
   b = std::max(b, simt_pass_partial_bytes(m, n, l, tc_bytes(a_dtype), sms));
   b = std::max(b, simt_pass_partial_bytes(n, m, l, tc_bytes(a_dtype), sms));
-  if (a_dtype != CORUTV_F64) {
+  if (a_dtype == CORUTV_F32) {
     b = std::max(b, tc_pass_partial_bytes(m, n, sms));
     b = std::max(b, tc_pass_partial_bytes(n, m, sms));
+  }
+  // the correction pass of a BF16 / FP8 solve runs on FP32 A
+  if (a_dtype == CORUTV_BF16 || a_dtype == CORUTV_FP8_E4M3) {
+    b = std::max(b, tc_lp_partial_bytes(sms));
+    b = std::max(b, tc_pass_partial_bytes(m, n, sms));
+    b = std::max(b, simt_pass_partial_bytes(m, n, l, 4, sms));
+    b = std::max(b, simt_pass_partial_bytes(n, m, l, 4, sms));
   }
   return b;
 }
@@ -149,6 +156,14 @@ void make_plan(const corutv_params* p, int sms, Plan& pl) {
   pl.fparts = fro2_parts(sms);
 }
 
+// engine allowed for a storage dtype
+bool mma_fits_dtype(int a_dtype, int mma) {
+  if (mma == CORUTV_MMA_AUTO || mma == CORUTV_MMA_SIMT) return true;
+  if (mma == CORUTV_MMA_TF32 || mma == CORUTV_MMA_TF32_TRUNC) return a_dtype == CORUTV_F32;
+  if (mma == CORUTV_MMA_BF16X2) return a_dtype == CORUTV_BF16 || a_dtype == CORUTV_FP8_E4M3;
+  return false;
+}
+
 int check_params(const corutv_params* p) {
   if (!p) return CORUTV_ERR_INVALID_ARG;
   for (int r : p->reserved)
@@ -157,15 +172,14 @@ int check_params(const corutv_params* p) {
   if (p->side != CORUTV_SIDE_RIGHT && p->side != CORUTV_SIDE_LEFT) return CORUTV_ERR_INVALID_ARG;
   if (p->core != CORUTV_CORE_EXACT && p->core != CORUTV_CORE_SKETCH) return CORUTV_ERR_INVALID_ARG;
   if (p->orth != CORUTV_ORTH_STABILISED) return CORUTV_ERR_INVALID_ARG;
-  if (p->mma < CORUTV_MMA_AUTO || p->mma > CORUTV_MMA_TF32_TRUNC) return CORUTV_ERR_INVALID_ARG;
+  if (p->mma < CORUTV_MMA_AUTO || p->mma > CORUTV_MMA_BF16X2) return CORUTV_ERR_INVALID_ARG;
   if (p->mma == CORUTV_MMA_TF32X3) return CORUTV_ERR_UNSUPPORTED;
   if (p->m <= 0 || p->n <= 0) return CORUTV_ERR_SHAPE;
   if (p->k < 1 || p->k > p->l) return CORUTV_ERR_INVALID_ARG;      // 1 <= k <= l (Sec. III)
   if (p->q < 0) return CORUTV_ERR_INVALID_ARG;
   if (p->l >= std::min(p->m, p->n)) return CORUTV_ERR_SHAPE;      // l < min(m, n) (Sec. III)
   if (p->l > (p->a_dtype == CORUTV_F64 ? kMaxL64 : kMaxL)) return CORUTV_ERR_SHAPE;
-  if (p->a_dtype != CORUTV_F32 && (p->mma == CORUTV_MMA_TF32 || p->mma == CORUTV_MMA_TF32_TRUNC))
-    return CORUTV_ERR_UNSUPPORTED;
+  if (!mma_fits_dtype(p->a_dtype, p->mma)) return CORUTV_ERR_UNSUPPORTED;
   return CORUTV_OK;
 }
 
@@ -235,13 +249,14 @@ struct PhaseTimer {
     }                                           \
   } while (0)
 
-// engine choice for a pass
-// engine for a pass; AUTO picks the tensor cores for FP32 A whose rows TMA can address
+// engine for a pass; AUTO picks the tensor cores for FP32, BF16 and FP8 A whose rows TMA can address
 int pick_mma(int a_dtype, int mma, bool tma_ok = true) {
-  if (a_dtype != CORUTV_F32) return CORUTV_MMA_SIMT;
-  if (mma == CORUTV_MMA_AUTO) return tma_ok ? CORUTV_MMA_TF32 : CORUTV_MMA_SIMT;
-  return mma;
+  if (a_dtype == CORUTV_F64) return CORUTV_MMA_SIMT;
+  if (mma != CORUTV_MMA_AUTO) return mma;
+  if (!tma_ok) return CORUTV_MMA_SIMT;
+  return a_dtype == CORUTV_F32 ? CORUTV_MMA_TF32 : CORUTV_MMA_BF16X2;
 }
+
 
 inline bool tma_rows_ok(const void* A, int64_t lda, int a_dtype) {
   return aligned16(A) && (lda * elem_bytes(a_dtype)) % 16 == 0;
@@ -272,6 +287,17 @@ int run_pass(corutv_handle* h, int dir, int a_dtype, int mma, const void* A, int
   if (eng == CORUTV_MMA_SIMT) {
     if (fro_parts) return CORUTV_ERR_UNSUPPORTED;
     CU(launch_pass_simt(a, dir, a_dtype, h->sms, h->stream));
+  } else if (eng == CORUTV_MMA_BF16X2) {
+    if (!tc_lp_supported(dir, a_dtype, l)) return CORUTV_ERR_UNSUPPORTED;
+    // the BF16 hi / lo parts of the sketch operand share the buffer of the rounded TF32 operand
+    void* Xh = Xr;
+    void* Xl = reinterpret_cast<char*>(Xr) + (size_t)kMaxL * ldr * 2;
+    CU(launch_pass_tc_lp(a, dir, a_dtype, h->sms, h->status, fro_parts, Xh, Xl, ldr, h->stream));
+    if (fro_parts) {
+      sum_parts_kernel<<<1, 32, 0, h->stream>>>(fro_parts, tc_lp_grid(a.len_out, a.K, h->sms), nullptr, h->status);
+      CORUTV_COUNT_LAUNCH();
+      CU(cudaGetLastError());
+    }
   } else {
     if (!tc_pass_supported(dir, a_dtype, eng, l)) return CORUTV_ERR_UNSUPPORTED;
     if (eng == CORUTV_MMA_TF32) {
@@ -309,10 +335,13 @@ int orth_st(corutv_handle* h, TC* Ct, int64_t ldc, int64_t len, int l, const Pla
   return CORUTV_OK;
 }
 
+// A_ref (FP32, lda_ref) non-null: correction pass -- the core D of S5 is computed from A_ref
+// with the Q1, Q2 found by the passes over A (stored in BF16 / FP8), and ||A_ref||_F^2 is the
+// readout.
 template <typename TC>
 int solve_impl(corutv_handle* h, const corutv_params* p, const Plan& pl, const void* A, int64_t lda,
-               const float* scales, const void* Phi, int64_t ldphi, void* U, int64_t ldu, double* T, int64_t ldt,
-               void* V, int64_t ldv, int32_t* perm) {
+               const float* scales, const float* A_ref, int64_t lda_ref, const void* Phi, int64_t ldphi, void* U,
+               int64_t ldu, double* T, int64_t ldt, void* V, int64_t ldv, int32_t* perm) {
   const bool right = p->side == CORUTV_SIDE_RIGHT;
   const int l = p->l;
   // RIGHT: first product A X (dir AX), second A^T Q1 (dir ATY); LEFT: swapped.
@@ -330,13 +359,15 @@ int solve_impl(corutv_handle* h, const corutv_params* p, const Plan& pl, const v
     CU(launch_stage_transpose<TC>(static_cast<const TC*>(Phi), ldphi, pl.len2, l, P2, pl.ld2, h->stream));
   }
   // S9: ||A||_F^2 fused into the first pass where the tensor-core engine runs it
-  const bool fuse_fro2 = p->want_fro2 && pick_mma(p->a_dtype, p->mma, tma_rows_ok(A, lda, p->a_dtype)) !=
-                                              CORUTV_MMA_SIMT;
+  const int ref_mma = p->mma == CORUTV_MMA_SIMT ? CORUTV_MMA_SIMT : CORUTV_MMA_AUTO;
+  const bool fuse_fro2 =
+      p->want_fro2 && (A_ref ? pick_mma(CORUTV_F32, ref_mma, tma_rows_ok(A_ref, lda_ref, CORUTV_F32))
+                             : pick_mma(p->a_dtype, p->mma, tma_rows_ok(A, lda, p->a_dtype))) != CORUTV_MMA_SIMT;
   float* Xr = static_cast<float*>(pl.Xr);
   for (int it = 0; it <= p->q; ++it) {
     // S1: C1 = A X  (Alg. 3 step 3)
     int rc = run_pass(h, dir1, p->a_dtype, p->mma, A, lda, p->m, p->n, scales, P2, pl.ld2, l, P1, pl.ld1,
-                      pl.partials, Xr, pl.ldr, (it == 0 && fuse_fro2) ? pl.fro_parts : nullptr);
+                      pl.partials, Xr, pl.ldr, (it == 0 && fuse_fro2 && !A_ref) ? pl.fro_parts : nullptr);
     if (rc) return rc;
     ++passes;
     // S2: orth(C1)
@@ -355,7 +386,16 @@ int solve_impl(corutv_handle* h, const corutv_params* p, const Plan& pl, const v
     if (rc) return rc;
   }
   // S5: core D = Q1^T A Q2 (Alg. 2 step 5)
-  if (p->core == CORUTV_CORE_EXACT) {
+  if (A_ref) {
+    // correction pass: E = A_ref Q2 over the FP32 matrix (||A_ref||^2 fused where the tensor cores run it)
+    int rc = run_pass(h, dir1, CORUTV_F32, ref_mma, A_ref, lda_ref, p->m, p->n, nullptr, P2, pl.ld2, l, P3,
+                      pl.ld3, pl.partials, Xr, pl.ldr, fuse_fro2 ? pl.fro_parts : nullptr);
+    if (rc) return rc;
+    ++passes;
+    PhaseTimer tm(h, kPhCore);
+    CU(launch_gram<TC>(P1, pl.ld1, P3, pl.ld3, pl.len1, l, static_cast<TC*>(pl.gram_parts),
+                       gram_parts(pl.len1, h->sms), pl.D, kMaxL, h->stream));   // D = Q1^T E
+  } else if (p->core == CORUTV_CORE_EXACT) {
     int rc = run_pass(h, dir1, p->a_dtype, p->mma, A, lda, p->m, p->n, scales, P2, pl.ld2, l, P3, pl.ld3,
                       pl.partials, Xr, pl.ldr, nullptr);   // E = A Q2 (ST, len1)
     if (rc) return rc;
@@ -385,9 +425,11 @@ int solve_impl(corutv_handle* h, const corutv_params* p, const Plan& pl, const v
   }
   // S9: ||A||_F^2 on request
   if (p->want_fro2 && !fuse_fro2) {
-    PhaseTimer tm(h, kPhFro2, (double)p->m * p->n * elem_bytes(p->a_dtype));
-    CU(launch_fro2(p->a_dtype, A, lda, p->m, p->n, scales, cdiv(p->n, 128), pl.fro_parts, pl.fparts,
-                   &pl.status->fro2_A, h->stream));
+    const int fdt = A_ref ? CORUTV_F32 : p->a_dtype;
+    PhaseTimer tm(h, kPhFro2, (double)p->m * p->n * elem_bytes(fdt));
+    CU(launch_fro2(fdt, A_ref ? static_cast<const void*>(A_ref) : A, A_ref ? lda_ref : lda, p->m, p->n,
+                   A_ref ? nullptr : scales, cdiv(p->n, 128), pl.fro_parts, pl.fparts, &pl.status->fro2_A,
+                   h->stream));
     ++passes;
   }
   h->last_passes = passes;
@@ -477,9 +519,10 @@ int corutv_set_workspace(corutv_handle* h, void* dptr, size_t bytes) {
   return CORUTV_OK;
 }
 
-int corutv_solve(corutv_handle* h, const corutv_params* p, const void* A, int64_t lda, const float* a_tile_scales,
-                 const void* Phi, int64_t ldphi, void* U, int64_t ldu, double* T, int64_t ldt, void* V, int64_t ldv,
-                 int32_t* perm) {
+static int solve_common(corutv_handle* h, const corutv_params* p, const void* A, int64_t lda,
+                        const float* a_tile_scales, const float* A_ref, int64_t lda_ref, const void* Phi,
+                        int64_t ldphi, void* U, int64_t ldu, double* T, int64_t ldt, void* V, int64_t ldv,
+                        int32_t* perm) {
   if (!h) return CORUTV_ERR_INVALID_ARG;
   int rc = check_params(p);
   if (rc) return rc;
@@ -490,6 +533,7 @@ int corutv_solve(corutv_handle* h, const corutv_params* p, const void* A, int64_
   if (pick_mma(p->a_dtype, p->mma, tma_rows_ok(A, lda, p->a_dtype)) != CORUTV_MMA_SIMT &&
       !tma_rows_ok(A, lda, p->a_dtype))
     return CORUTV_ERR_ALIGN;
+  if (A_ref && lda_ref < p->n) return CORUTV_ERR_SHAPE;
   Plan pl{};
   make_plan(p, h->sms, pl);
   const size_t need = plan_layout(pl, nullptr);
@@ -501,12 +545,40 @@ int corutv_solve(corutv_handle* h, const corutv_params* p, const void* A, int64_
   h->have_last = true;
   const int64_t l0 = launch_counter();
   if (p->a_dtype == CORUTV_F64)
-    rc = solve_impl<double>(h, p, pl, A, lda, a_tile_scales, Phi, ldphi, U, ldu, T, ldt, V, ldv, perm);
+    rc = solve_impl<double>(h, p, pl, A, lda, a_tile_scales, nullptr, 0, Phi, ldphi, U, ldu, T, ldt, V, ldv, perm);
   else
-    rc = solve_impl<float>(h, p, pl, A, lda, a_tile_scales, Phi, ldphi, U, ldu, T, ldt, V, ldv, perm);
+    rc = solve_impl<float>(h, p, pl, A, lda, a_tile_scales, A_ref, lda_ref, Phi, ldphi, U, ldu, T, ldt, V, ldv,
+                           perm);
   h->launches += launch_counter() - l0;
   if (h->tracing) h->acc.solves += 1;
   return rc;
+}
+
+int corutv_solve(corutv_handle* h, const corutv_params* p, const void* A, int64_t lda, const float* a_tile_scales,
+                 const void* Phi, int64_t ldphi, void* U, int64_t ldu, double* T, int64_t ldt, void* V, int64_t ldv,
+                 int32_t* perm) {
+  return solve_common(h, p, A, lda, a_tile_scales, nullptr, 0, Phi, ldphi, U, ldu, T, ldt, V, ldv, perm);
+}
+
+int corutv_solve_corrected(corutv_handle* h, const corutv_params* p, const void* A, int64_t lda,
+                           const float* a_tile_scales, const float* A_ref, int64_t lda_ref, const void* Phi,
+                           int64_t ldphi, void* U, int64_t ldu, double* T, int64_t ldt, void* V, int64_t ldv,
+                           int32_t* perm) {
+  if (!p || !A_ref) return CORUTV_ERR_INVALID_ARG;
+  if (p->a_dtype != CORUTV_BF16 && p->a_dtype != CORUTV_FP8_E4M3) return CORUTV_ERR_INVALID_ARG;
+  if (p->core != CORUTV_CORE_EXACT) return CORUTV_ERR_INVALID_ARG;
+  return solve_common(h, p, A, lda, a_tile_scales, A_ref, lda_ref, Phi, ldphi, U, ldu, T, ldt, V, ldv, perm);
+}
+
+int corutv_quantize(corutv_handle* h, int dtype, const float* A, int64_t lda, int64_t m, int64_t n, void* out,
+                    int64_t ldo, float* tile_scales) {
+  if (!h || !A || !out) return CORUTV_ERR_INVALID_ARG;
+  if (dtype != CORUTV_BF16 && dtype != CORUTV_FP8_E4M3) return CORUTV_ERR_INVALID_ARG;
+  if (dtype == CORUTV_FP8_E4M3 && !tile_scales) return CORUTV_ERR_INVALID_ARG;
+  if (m <= 0 || n <= 0 || lda < n || ldo < n) return CORUTV_ERR_SHAPE;
+  if (cdiv(m, 128) > 65535) return CORUTV_ERR_SHAPE;
+  CU(launch_quantize(dtype, A, lda, m, n, out, ldo, tile_scales, h->stream));
+  return CORUTV_OK;
 }
 
 int corutv_info_wait(corutv_handle* h, corutv_info* out) {
@@ -589,10 +661,9 @@ int corutv_pass(corutv_handle* h, int dir, int a_dtype, int mma, const void* A, 
                 const float* a_tile_scales, const void* Xt, int64_t ldx, int32_t l, void* Ct, int64_t ldc) {
   if (!h || !A || !Xt || !Ct) return CORUTV_ERR_INVALID_ARG;
   if (dir != CORUTV_DIR_AX && dir != CORUTV_DIR_ATY) return CORUTV_ERR_INVALID_ARG;
-  if (a_dtype < CORUTV_F64 || a_dtype > CORUTV_FP8_E4M3 || mma < 0 || mma > CORUTV_MMA_TF32_TRUNC)
+  if (a_dtype < CORUTV_F64 || a_dtype > CORUTV_FP8_E4M3 || mma < 0 || mma > CORUTV_MMA_BF16X2)
     return CORUTV_ERR_INVALID_ARG;
-  if (mma == CORUTV_MMA_TF32X3) return CORUTV_ERR_UNSUPPORTED;
-  if (a_dtype != CORUTV_F32 && (mma == CORUTV_MMA_TF32 || mma == CORUTV_MMA_TF32_TRUNC)) return CORUTV_ERR_UNSUPPORTED;
+  if (!mma_fits_dtype(a_dtype, mma)) return CORUTV_ERR_UNSUPPORTED;
   if (a_dtype == CORUTV_FP8_E4M3 && !a_tile_scales) return CORUTV_ERR_INVALID_ARG;
   if (m <= 0 || n <= 0 || l < 1 || l > kMaxL || lda < n) return CORUTV_ERR_SHAPE;
   const int64_t klen = dir == CORUTV_DIR_AX ? n : m, olen = dir == CORUTV_DIR_AX ? m : n;

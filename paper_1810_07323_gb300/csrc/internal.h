@@ -37,7 +37,7 @@ cudaError_t launch_pass_simt(const PassArgs& a, int dir, int a_dtype, int sms, c
 cudaError_t launch_streamk_reduce_f32(float* Ct, int64_t ldc, const float* P, int l, int LP, int BN, int64_t len,
                                       int64_t KB, int64_t G, cudaStream_t st);
 
-// pass_tc.cu (tcgen05 + TMA, FP32/BF16/FP8 A)
+// pass_tc.cu (tcgen05 kind::tf32 + TMA, FP32 A)
 size_t tc_pass_partial_bytes(int64_t len, int64_t K, int sms);
 int tc_pass_grid(int64_t len, int64_t K, int sms);
 bool tc_pass_supported(int dir, int a_dtype, int mma, int l);
@@ -45,6 +45,19 @@ cudaError_t launch_pass_tc(const PassArgs& a, int dir, int a_dtype, int mma, int
                            double* fro_parts, cudaStream_t st);
 cudaError_t launch_round_tf32(const float* X, int64_t ldx, float* Xr, int64_t ldr, int l, int64_t len,
                               cudaStream_t st);
+
+// pass_tc_lp.cu (tcgen05 kind::f16 + TMA, BF16 A or FP8 A with tile scales; the FP32
+// sketch operand is split into BF16 hi / lo parts Xh, Xl: l rows of K, leading dimension ldxs)
+size_t tc_lp_partial_bytes(int sms);
+int tc_lp_grid(int64_t len, int64_t K, int sms);
+bool tc_lp_supported(int dir, int a_dtype, int l);
+cudaError_t launch_pass_tc_lp(const PassArgs& a, int dir, int a_dtype, int sms, DevStatus* status,
+                              double* fro_parts, void* Xh, void* Xl, int64_t ldxs, cudaStream_t st);
+
+// quant.cu: FP32 A -> BF16, or FP8 e4m3 with one power-of-two scale per 128 x 128 tile
+cudaError_t launch_quantize(int dtype, const float* A, int64_t lda, int64_t m, int64_t n, void* out, int64_t ldo,
+                            float* scales, cudaStream_t st);
+
 __global__ void sum_parts_kernel(const double* __restrict__ parts, int n, double* out, DevStatus* status);
 
 // small.cu

@@ -210,3 +210,32 @@ def test_planted_wrong_sign_householder_is_caught(monkeypatch):
     C = np.random.default_rng(2).standard_normal((20, 5))
     Q, R = O.householder_qr(C)
     assert np.abs(Q @ R - C).max() > 1e-3
+
+
+def test_correction_core_is_projection_of_reference(cfg1):
+    """Correction pass (core from A_core): with A_core = A it is the plain exact core;
+    otherwise T is the compression U^T A_core V, the Pythagorean identity holds for
+    A_core, and for the fixed bases no other core (in particular the one from the
+    perturbed A) leaves a smaller residual of A_core (D = Q1^T A_core Q2 minimises
+    ||A_core - Q1 D Q2^T||_F)."""
+    from oracle import precision as P
+    A = cfg1.A
+    Phi = W.phi(1500, 30)
+    r0 = O.corutv(A, Phi, 20, 30, 1)
+    r1 = O.corutv(A, Phi, 20, 30, 1, A_core=A)
+    assert np.array_equal(r0["T"], r1["T"]) and np.array_equal(r0["U"], r1["U"])
+    vals, sc = P.quantize_fp8(A.astype(np.float32))
+    Aq = P.dequantize_fp8(vals, sc)
+    assert np.linalg.norm(Aq - A) > 1e-3 * np.linalg.norm(A)        # a real perturbation
+    rc = O.corutv(Aq, Phi, 20, 30, 1, A_core=A)
+    ru = O.corutv(Aq, Phi, 20, 30, 1)
+    assert np.abs(rc["U"].T @ A @ rc["V"] - rc["T"]).max() < 1e-13
+    a2 = np.linalg.norm(A) ** 2
+    e2 = O.fro_residual(A, rc["U"], rc["T"], rc["V"]) ** 2
+    assert abs(e2 - (a2 - np.linalg.norm(rc["T"]) ** 2)) < 1e-12 * a2
+    assert np.allclose(rc["Q1"], ru["Q1"]) and np.allclose(rc["Q2"], ru["Q2"])   # same range finding
+    e_u = np.linalg.norm(A - ru["Q1"] @ ru["D"] @ ru["Q2"].T)
+    e_c = np.linalg.norm(A - rc["Q1"] @ rc["D"] @ rc["Q2"].T)
+    assert e_c <= e_u
+    with pytest.raises(ValueError):
+        O.corutv(Aq, Phi, 20, 30, 1, core="approx", A_core=A)
