@@ -1,10 +1,18 @@
-"""Benchmark: CoR-UTV solves/s on the 20000 x 20000 FP32 workload (one GPU per
-process; N processes run N independent replicas -- the solve does not shard).
+"""Benchmark: CoR-UTV solves/s (one GPU per process; N processes run N
+independent replicas -- a solve does not shard).
 
-Step = one whole CoR-UTV solve (Alg. 3 with q power steps, exact core): Psi
-staging, 2q+3 streaming passes over A, shifted CholeskyQR3 of every sketch,
-the core reduction, QRCP of D, assembly of U and V, and the ||A||_F^2 readout.
-Inputs (A: 1.6 GB) are larger than L2, so no flush is needed between steps.
+Workloads (--workload):
+  fp32 (default)  20000 x 20000 FP32 A = G1 diag(i^-1.5) G2^T + 1e-8 noise,
+                  k=100, l=120, q=1, exact core, TF32 tensor-core passes.
+  bf16 / fp8      32768 x 16384 A with sigma_i = exp(-i/30), k=64, l=80, q=2:
+                  FP32 A quantised on the device (BF16, or FP8 e4m3 with
+                  128 x 128 tile scales), 2q+2 kind::f16 passes over the stored
+                  A, then the FP32 correction pass for the core.
+
+Step = one whole solve: (quantisation,) Psi staging, every streaming pass over
+A, shifted CholeskyQR3 of every sketch, the core reduction, QRCP of D,
+assembly of U and V, and the ||A||_F^2 readout.  Inputs (A >= 1.6 GB) are
+larger than L2, so no flush is needed between steps.
 
 Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on
 the host cores instead (the only other place this script runs oracle code).
@@ -22,24 +30,45 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-M = N = 20000
-K_RANK, L, CFG = 100, 120, 2
+WORKLOADS = {
+    # name: m, n, k, l, q, storage dtype, generator
+    "fp32": dict(m=20000, n=20000, k=100, l=120, q=1, dtype="f32", gen="config2"),
+    "bf16": dict(m=32768, n=16384, k=64, l=80, q=2, dtype="bf16", gen="config3"),
+    "fp8": dict(m=32768, n=16384, k=64, l=80, q=2, dtype="fp8", gen="config3"),
+}
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--q", type=int, default=1)
+    ap.add_argument("--workload", default="fp32", choices=sorted(WORKLOADS))
+    ap.add_argument("--q", type=int, default=None)
     ap.add_argument("--mma", default="auto")
     ap.add_argument("--core", default="exact")
-    ap.add_argument("--m", type=int, default=M)
-    ap.add_argument("--n", type=int, default=N)
+    ap.add_argument("--m", type=int, default=None)
+    ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    return ap.parse_args()
+    args = ap.parse_args()
+    w = dict(WORKLOADS[args.workload])
+    for key in ("m", "n", "q"):
+        if getattr(args, key) is not None:
+            w[key] = getattr(args, key)
+    args.w = w
+    return args
+
+
+def workload_label(w, core):
+    if w["gen"] == "config2":
+        a = f"{w['m']}x{w['n']} FP32 A = G1 diag(i^-1.5) G2^T + 1e-8 noise"
+    else:
+        store = "BF16" if w["dtype"] == "bf16" else "FP8 e4m3 (128x128 tile scales)"
+        a = (f"{w['m']}x{w['n']} A = G1 diag(exp(-i/30)) G2^T + 1e-8 noise stored {store}, "
+             f"quantised from FP32 each step, FP32 correction pass")
+    return f"{a}, k={w['k']}, l={w['l']}, q={w['q']}, {core} core, one solve per step"
 
 
 def dist_setup():
@@ -83,7 +112,7 @@ class Clocks:
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "50"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except OSError:
             self.p = None
@@ -123,24 +152,40 @@ def measured_peaks() -> dict:
         return {}
 
 
-def traffic_from_profiles(kernel: str):
-    """Per-launch DRAM bytes from the committed ncu summary of the pass kernel
-    (None if absent or recorded for another kernel version)."""
-    path = os.path.join(ROOT, "profiles", "pass_tc_traffic.json")
+def traffic_from_profiles(key: str):
+    """Per-launch DRAM bytes (read + write) of the timed pass kernel at the bench's
+    size, from a committed ncu summary under profiles/: a line
+    `traffic_bytes_per_launch <key> <bytes>`.  None if no summary records it."""
+    import re
+    d = os.path.join(ROOT, "profiles")
     try:
-        with open(path) as f:
-            d = json.load(f)
-        return d.get(kernel)
-    except (OSError, ValueError):
+        names = sorted(os.listdir(d))
+    except OSError:
         return None
+    for nm in names:
+        if not nm.endswith((".md", ".txt")):
+            continue
+        with open(os.path.join(d, nm)) as f:
+            for line in f:
+                mt = re.match(r"\s*traffic_bytes_per_launch\s+(\S+)\s+([0-9.eE+]+)", line)
+                if mt and mt.group(1) == key:
+                    return float(mt.group(2))
+    return None
 
 
-def make_inputs(m, n, device):
+def generator(w):
+    from synth import workloads as W
+    if w["gen"] == "config2":
+        return W.config2(m=w["m"], n=w["n"])
+    return W.config3(m=w["m"], n=w["n"])
+
+
+def make_inputs(w, device):
     import torch
     from synth import workloads as W
-    g = W.config2(m=m, n=n)
-    A = g.block_t(0, m, 0, n, device=device, dtype=torch.float32)
-    phi = W.phi_t(n, L, device=device).to(torch.float32)
+    g = generator(w)
+    A = g.block_t(0, w["m"], 0, w["n"], device=device, dtype=torch.float32)
+    phi = W.phi_t(w["n"], w["l"], device=device).to(torch.float32)
     return g, A, phi
 
 
@@ -151,12 +196,29 @@ def cpu_cores():
         return os.cpu_count()
 
 
-def oracle_solve_time(A64, phi64, q):
-    """One oracle solve (as it stands) on the host cores; returns seconds and the result."""
+def oracle_solve_time(A64, phi64, w):
+    """One oracle solve (as it stands) on the host cores; returns seconds and the result.
+    For the BF16 / FP8 workloads the oracle's storage conversion of the sample and
+    the correction-pass core are part of the timed solve."""
     from oracle import corutv_oracle as O
+    from oracle import precision as P
     t0 = time.perf_counter()
-    r = O.corutv(A64, phi64, K_RANK, L, q)
+    if w["dtype"] == "f32":
+        r = O.corutv(A64, phi64, w["k"], w["l"], w["q"])
+    else:
+        A32 = A64.astype("float32")
+        if w["dtype"] == "bf16":
+            Aq = P.bf16_round(A32).astype("float64")
+        else:
+            Aq = P.dequantize_fp8(*P.quantize_fp8(A32))
+        r = O.corutv(Aq, phi64, w["k"], w["l"], w["q"], A_core=A32.astype("float64"))
     return time.perf_counter() - t0, r
+
+
+def cpu_sample_shape(w):
+    """Bounded oracle sample: a leading block with the workload's aspect ratio."""
+    s = min(w["m"], 4000)
+    return s, max(min(w["n"], s * w["n"] // w["m"]), w["l"] + 1)
 
 
 def run_reference(args):
@@ -167,29 +229,29 @@ def run_reference(args):
     if rank != 0:
         return
     from synth import workloads as W
-    g = W.config2(m=args.m, n=args.n)
-    # bounded sample: a row/column block of the same workload, sized so that
+    w = args.w
+    g = generator(w)
+    # bounded sample: a leading block of the same workload, sized so that
     # warmup + steps finish within a few minutes
-    s = min(args.m, 4000)
-    A = g.block(0, s, 0, s)
-    phi = W.phi(args.n, L)[:s]
+    sm, sn = cpu_sample_shape(w)
+    A = g.block(0, sm, 0, sn)
+    phi = W.phi(w["n"], w["l"])[:sn]
     for _ in range(args.warmup):
-        oracle_solve_time(A, phi, args.q)
+        oracle_solve_time(A, phi, w)
     ts = []
     for _ in range(args.steps):
-        t, _ = oracle_solve_time(A, phi, args.q)
+        t, _ = oracle_solve_time(A, phi, w)
         ts.append(t)
     per = sum(ts) / len(ts)
-    scale = (args.m * args.n) / float(s * s)      # passes dominate: cost ~ m n
+    scale = (w["m"] * w["n"]) / float(sm * sn)      # passes dominate: cost ~ m n
     value = 1.0 / (per * scale)
-    sample = f"oracle solve of the {s}x{s} leading block (same generator, q={args.q}), scaled by m*n"
+    sample = f"oracle solve of the {sm}x{sn} leading block (same generator, q={w['q']}), scaled by m*n"
     out = {"impl": "reference", "metric": "CoR-UTV solves/s", "value": value, "unit": "solves/s",
            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic",
-           "config": {"workload": f"{args.m}x{args.n} FP32 low-rank+noise (sigma_i=i^-1.5), k={K_RANK}, l={L}, "
-                                  f"q={args.q}, exact core", "m": args.m, "n": args.n, "k": K_RANK, "l": L,
-                      "q": args.q},
+           "config": {"workload": workload_label(w, "exact"), "m": w["m"], "n": w["n"], "k": w["k"],
+                      "l": w["l"], "q": w["q"]},
            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
                             "sample": sample},
            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -201,24 +263,39 @@ def main():
     if args.impl == "reference":
         run_reference(args)
         return
-    import numpy as np
     import torch
     world, rank, local = dist_setup()
     from paper_1810_07323_gb300 import corutv
 
-    m, n, q = args.m, args.n, args.q
+    w = args.w
+    m, n, k, l, q = w["m"], w["n"], w["k"], w["l"], w["q"]
+    lowp = w["dtype"] != "f32"
     dev = torch.device("cuda", torch.cuda.current_device())
-    g, A, phi = make_inputs(m, n, dev)
-    U = torch.empty((m, L), device=dev)
-    T = torch.empty((L, L), dtype=torch.float64, device=dev)
-    V = torch.empty((n, L), device=dev)
-    perm = torch.empty((L,), dtype=torch.int32, device=dev)
+    g, A, phi = make_inputs(w, dev)
+    U = torch.empty((m, l), device=dev)
+    T = torch.empty((l, l), dtype=torch.float64, device=dev)
+    V = torch.empty((n, l), device=dev)
+    perm = torch.empty((l,), dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
     h = corutv.handle_for(stream)
+    if lowp:
+        # storage of the quantised A (16-byte row pitch) and its tile scales, reused every step
+        tdt = torch.bfloat16 if w["dtype"] == "bf16" else torch.float8_e4m3fn
+        A_lp = torch.empty((m, -(-n // 16) * 16), dtype=tdt, device=dev)[:, :n]
+        S = torch.empty((-(-m // 128), -(-n // 128)), dtype=torch.float32, device=dev) \
+            if w["dtype"] == "fp8" else None
+
+    def solve_on(A32, P32):
+        if lowp:
+            corutv.quantize(A32, w["dtype"], out=A_lp, tile_scales=S, handle=h)
+            corutv.solve(A_lp, P32, k, l, q, core=args.core, mma=args.mma, a_tile_scales=S, want_fro2=True,
+                         out=(U, T, V, perm), wait=False, handle=h, A_ref=A32)
+        else:
+            corutv.solve(A32, P32, k, l, q, core=args.core, mma=args.mma, want_fro2=True,
+                         out=(U, T, V, perm), wait=False, handle=h)
 
     def step():
-        corutv.solve(A, phi, K_RANK, L, q, core=args.core, mma=args.mma, want_fro2=True,
-                     out=(U, T, V, perm), wait=False, handle=h)
+        solve_on(A, phi)
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -255,15 +332,25 @@ def main():
     avg_pass_ms = tr.pass_ms / max(tr.pass_launches, 1)
     bytes_per_pass = tr.pass_bytes / max(tr.pass_launches, 1)
     achieved = bytes_per_pass / (avg_pass_ms / 1e3) / 1e9
+    if lowp:
+        kname = "pass_tc_lp_kernel (kind::f16, %s A, dir AX / ATY) incl. operand split and split-tile reduce" % (
+            "BF16" if w["dtype"] == "bf16" else "FP8")
+        tkey = f"pass_tc_lp_kernel/{w['dtype']}/{m}x{n}/l{l}"
+    else:
+        kname = "pass_tc_kernel (dir AX / ATY, TF32) incl. operand rounding and split-tile reduce"
+        tkey = f"pass_tc_kernel/f32/{m}x{n}/l{l}"
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "peak_source": peak_src, "kernel": "pass_tc_kernel (dir AX / ATY, TF32) incl. split-tile reduce",
-                "bytes_per_launch": bytes_per_pass, "ms_per_launch": avg_pass_ms,
-                "traffic": traffic_from_profiles("pass_tc_kernel")}
+                "peak_source": peak_src, "kernel": kname, "bytes_per_launch": bytes_per_pass,
+                "ms_per_launch": avg_pass_ms, "traffic": traffic_from_profiles(tkey)}
+    if lowp and tr.corr_launches:
+        corr_ms = tr.corr_ms / tr.corr_launches
+        roofline["correction_pass"] = {"ms_per_launch": corr_ms,
+                                       "achieved": tr.corr_bytes / tr.corr_launches / (corr_ms / 1e3) / 1e9}
 
     # ------------------------------------------------------------ error of the timed result
     res2 = 0.0
     with torch.no_grad():
-        Uk, Tk = U[:, :K_RANK].double(), T[:K_RANK].double()
+        Uk, Tk = U[:, :k].double(), T[:k].double()
         Vd = V.double()
         for a in range(0, m, 2048):
             blk = A[a:a + 2048].double() - (Uk[a:a + 2048] @ Tk) @ Vd.T
@@ -276,12 +363,12 @@ def main():
     if not args.no_e2e:
         A_h = torch.empty((m, n), dtype=torch.float32, pin_memory=True)
         A_h.copy_(A)
-        phi_h = torch.empty((n, L), dtype=torch.float32, pin_memory=True)
+        phi_h = torch.empty((n, l), dtype=torch.float32, pin_memory=True)
         phi_h.copy_(phi)
-        U_h = torch.empty((m, L), dtype=torch.float32, pin_memory=True)
-        V_h = torch.empty((n, L), dtype=torch.float32, pin_memory=True)
-        T_h = torch.empty((L, L), dtype=torch.float64, pin_memory=True)
-        p_h = torch.empty((L,), dtype=torch.int32, pin_memory=True)
+        U_h = torch.empty((m, l), dtype=torch.float32, pin_memory=True)
+        V_h = torch.empty((n, l), dtype=torch.float32, pin_memory=True)
+        T_h = torch.empty((l, l), dtype=torch.float64, pin_memory=True)
+        p_h = torch.empty((l,), dtype=torch.int32, pin_memory=True)
         A_d = torch.empty_like(A)
         phi_d = torch.empty_like(phi)
         e2e_steps = max(1, min(args.steps, 5))
@@ -289,8 +376,7 @@ def main():
         def e2e_step():
             A_d.copy_(A_h, non_blocking=True)
             phi_d.copy_(phi_h, non_blocking=True)
-            corutv.solve(A_d, phi_d, K_RANK, L, q, core=args.core, mma=args.mma, want_fro2=True,
-                         out=(U, T, V, perm), wait=False, handle=h)
+            solve_on(A_d, phi_d)
             U_h.copy_(U, non_blocking=True)
             V_h.copy_(V, non_blocking=True)
             T_h.copy_(T, non_blocking=True)
@@ -306,8 +392,8 @@ def main():
         f1.record(stream)
         torch.cuda.synchronize()
         ms_e2e = max_over_ranks(f0.elapsed_time(f1), world)
-        h2d = (m * n + n * L) * 4
-        d2h = (m + n) * L * 4 + L * L * 8 + L * 4
+        h2d = (m * n + n * l) * 4
+        d2h = (m + n) * l * 4 + l * l * 8 + l * 4
         e2e = {"value": world * e2e_steps / (ms_e2e / 1e3), "unit": "solves/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "steps": e2e_steps}
         del A_h
@@ -315,33 +401,36 @@ def main():
     # ------------------------------------------------------------ CPU baseline (oracle), rank 0, N=1
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        s = min(m, 4000)
-        A64 = A[:s, :s].double().cpu().numpy()
-        P64 = phi[:s].double().cpu().numpy()
-        t, _ = oracle_solve_time(A64, P64, q)
-        scale = (m * n) / float(s * s)
+        sm, sn = cpu_sample_shape(w)
+        A64 = A[:sm, :sn].double().cpu().numpy()
+        P64 = phi[:sn].double().cpu().numpy()
+        t, _ = oracle_solve_time(A64, P64, w)
+        scale = (m * n) / float(sm * sn)
         cpu = {"value": 1.0 / (t * scale), "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
-               "sample": f"one FP64 oracle solve of the {s}x{s} leading block of A (q={q}), {t:.2f} s, "
-                         f"scaled by m*n/({s}*{s})"}
+               "sample": f"one FP64 oracle solve of the {sm}x{sn} leading block of A (q={q}), {t:.2f} s, "
+                         f"scaled by m*n/({sm}*{sn})"}
 
     if rank == 0:
+        dtype = {"f32": "tf32", "bf16": "bf16", "fp8": "fp8-e4m3 (bf16 mma)"}[w["dtype"]]
         out = {"metric": "CoR-UTV solves/s", "value": value, "unit": "solves/s", "n_gpus": world,
                "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step,
-               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "tf32",
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
                "data": "synthetic",
-               "config": {"workload": f"{m}x{n} FP32 A = G1 diag(i^-1.5) G2^T + 1e-8 noise, k={K_RANK}, l={L}, "
-                                      f"q={q}, {args.core} core, one solve per step",
-                          "m": m, "n": n, "k": K_RANK, "l": L, "q": q, "core": args.core, "mma": args.mma,
-                          "passes_per_step": info.passes_over_A, "l2": "inputs larger than L2 (A is 1.6 GB)",
+               "config": {"workload": workload_label(w, args.core),
+                          "m": m, "n": n, "k": k, "l": l, "q": q, "core": args.core, "mma": args.mma,
+                          "passes_per_step": info.passes_over_A,
+                          "l2": "inputs larger than L2 (A is %.1f GB)" % (m * n * 4 / 1e9),
                           "parallelism": f"replicas x{world}"},
                "roofline": roofline,
                "cpu_baseline": cpu,
                "e2e": e2e,
                "gpu_launches": int(tr.launches),
                "clocks": clk,
-               "phases_ms_per_step": {"passes": tr.pass_ms / args.steps, "orth": tr.orth_ms / args.steps,
-                                      "core": tr.core_ms / args.steps, "qrcp": tr.qrcp_ms / args.steps,
-                                      "assembly": tr.assembly_ms / args.steps, "fro2": tr.fro2_ms / args.steps},
+               "phases_ms_per_step": {"quantise": tr.quant_ms / args.steps, "passes": tr.pass_ms / args.steps,
+                                      "correction": tr.corr_ms / args.steps,
+                                      "orth": tr.orth_ms / args.steps, "core": tr.core_ms / args.steps,
+                                      "qrcp": tr.qrcp_ms / args.steps, "assembly": tr.assembly_ms / args.steps,
+                                      "fro2": tr.fro2_ms / args.steps},
                "rel_err_rank_k": rel_err_k}
         print(json.dumps(out), flush=True)
     if world > 1:

@@ -39,7 +39,7 @@
 extern "C" {
 #endif
 
-#define CORUTV_ABI_VERSION 1
+#define CORUTV_ABI_VERSION 2
 
 typedef enum {
   CORUTV_OK = 0,
@@ -57,7 +57,12 @@ typedef enum {
 
 typedef enum { CORUTV_SIDE_RIGHT = 0, CORUTV_SIDE_LEFT = 1 } corutv_side;
 typedef enum { CORUTV_CORE_EXACT = 0, CORUTV_CORE_SKETCH = 1 } corutv_core;
-typedef enum { CORUTV_ORTH_STABILISED = 0 } corutv_orth;
+typedef enum {
+  CORUTV_ORTH_STABILISED = 0, /* the last power step's sketches (Q1, Q2) by shifted CholeskyQR3;
+                                 earlier sketches by one shifted CholeskyQR pass (a well-conditioned
+                                 basis of the same range: the same Q1, Q2 in exact arithmetic) */
+  CORUTV_ORTH_STRICT = 1      /* every sketch by shifted CholeskyQR3 */
+} corutv_orth;
 typedef enum { CORUTV_F64 = 0, CORUTV_F32 = 1, CORUTV_BF16 = 2, CORUTV_FP8_E4M3 = 3 } corutv_dtype;
 typedef enum {
   CORUTV_MMA_AUTO = 0,       /* F32 A: TF32 (rounded); BF16 / FP8 A: BF16X2; F64 A: SIMT.  Falls back to
@@ -87,7 +92,7 @@ typedef struct {
                             Psi m x l (sketch A^T Psi first), T lower (ULV form) */
   int32_t core;          /* corutv_core: EXACT = one more pass, D = Q1^T (A Q2) (Alg. 2 step 5);
                             SKETCH = D = (A^T Q1)^T Q2 from the last sketch, no extra pass */
-  int32_t orth;          /* corutv_orth: STABILISED (orthonormalise every sketch) */
+  int32_t orth;          /* corutv_orth (both orthonormalise every sketch before the next product) */
   int32_t a_dtype;       /* corutv_dtype of A (and of Psi, U, V: F64 for F64, F32 otherwise) */
   int32_t mma;           /* corutv_mma for the passes over A */
   int32_t want_fro2;     /* 1: also compute ||A||_F^2 into the info (fused into the first pass on the
@@ -157,10 +162,12 @@ int corutv_set_workspace(corutv_handle* h, void* dptr, size_t bytes);
  *   perm   device out, int32[l]: the QRCP pivots of the core (Sec. III, Eq. (D = Q~ R~ P~^T)).
  *          RIGHT: V[:, j] = Q2[:, perm[j]]; LEFT: U[:, j] is the permuted basis.
  *
- * Range finding is stabilised: every sketch is orthonormalised (Sec. III,
- * QR of C1 and C2) before the next product, which in exact arithmetic
- * yields the same Q1, Q2 as the literal loop of Alg. 3.  The orthonormalisation
- * is shifted CholeskyQR3 with an FP64 reduction of FP32 Gram partials.
+ * Range finding is stabilised: every sketch is normalised (Sec. III, QR of
+ * C1 and C2) before the next product, which in exact arithmetic yields the
+ * same Q1, Q2 as the literal loop of Alg. 3.  The final Q1, Q2 come from
+ * shifted CholeskyQR3 with an FP64 reduction of FP32 Gram partials (on the
+ * FP32 path the third pass is skipped when the second already gives
+ * max |Q^T Q - I| <= 2e-6); see corutv_orth for the intermediate sketches.
  * Returns a validation error synchronously; device conditions via corutv_info_wait.
  */
 int corutv_solve(corutv_handle* h, const corutv_params* p,
@@ -220,6 +227,11 @@ typedef struct {
   double qrcp_ms;          /* QRCP of D */
   double assembly_ms;      /* U = Q1 Q~, V = Q2 P~ and staging of Psi */
   double fro2_ms;          /* ||A||_F^2 */
+  int32_t corr_launches;   /* FP32 correction passes (corutv_solve_corrected), not counted above */
+  int32_t reserved1;
+  double corr_ms;          /* device time inside the correction passes */
+  double corr_bytes;       /* algorithmic bytes of those passes */
+  double quant_ms;         /* corutv_quantize calls on the handle */
 } corutv_trace;
 
 /* Enable (1) or disable (0) tracing on the handle. */
@@ -250,8 +262,10 @@ int corutv_pass(corutv_handle* h, int dir, int a_dtype, int mma,
  * Orthonormalise a tall-skinny block in place (Sec. III: C = Q R), ST layout:
  * Ct is l x len (ldc), F32 or F64 (dtype F32/F64).  Shifted CholeskyQR3:
  * R from the Cholesky factor of the FP64-reduced Gram matrix, Q = C R^-1,
- * three times, the first with a diagonal shift.  If R_out != NULL it
- * receives the l x l upper-triangular R (row-major FP64, ld l) with C = Q R.
+ * three times, the first with a diagonal shift (the FP32 third pass is skipped
+ * when the second already gives max |Q^T Q - I| <= 2e-6).  If R_out != NULL it
+ * receives the l x l upper-triangular R = R_3 R_2 R_1 (row-major FP64, ld l)
+ * with C = Q R.
  */
 int corutv_orthonormalize(corutv_handle* h, int dtype, void* Ct, int64_t ldc,
                           int64_t len, int32_t l, double* R_out);

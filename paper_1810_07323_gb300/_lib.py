@@ -22,6 +22,7 @@ ERR_CHOL_BREAKDOWN, ERR_BUSY, PENDING, ERR_UNSUPPORTED = 7, 8, 9, 10
 SIDE = {"right": 0, "left": 1}
 CORE = {"exact": 0, "sketch": 1}
 DTYPE = {"f64": 0, "f32": 1, "bf16": 2, "fp8": 3}
+ORTH = {"stabilised": 0, "strict": 1}
 MMA = {"auto": 0, "tf32": 1, "tf32x3": 2, "simt": 3, "tf32t": 4, "bf16x2": 5}
 DIR = {"ax": 0, "aty": 1}
 
@@ -50,7 +51,8 @@ class Trace(ctypes.Structure):
     _fields_ = [("solves", ctypes.c_int32), ("pass_launches", ctypes.c_int32), ("launches", ctypes.c_int64),
                 ("pass_ms", ctypes.c_double), ("pass_bytes", ctypes.c_double), ("orth_ms", ctypes.c_double),
                 ("core_ms", ctypes.c_double), ("qrcp_ms", ctypes.c_double), ("assembly_ms", ctypes.c_double),
-                ("fro2_ms", ctypes.c_double)]
+                ("fro2_ms", ctypes.c_double), ("corr_launches", ctypes.c_int32), ("reserved1", ctypes.c_int32),
+                ("corr_ms", ctypes.c_double), ("corr_bytes", ctypes.c_double), ("quant_ms", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -214,23 +216,23 @@ class SolveResult:
 
 
 def workspace_size(m, n, k, l, q=0, side="right", core="exact", a_dtype="f32", mma="auto") -> int:
-    p = _params(m, n, k, l, q, side, core, DTYPE[a_dtype], mma, False)
+    p = _params(m, n, k, l, q, side, core, DTYPE[a_dtype], mma, False, "stabilised")
     out = ctypes.c_size_t()
     _check(load().corutv_workspace_size(ctypes.byref(p), ctypes.byref(out)), "corutv_workspace_size")
     return out.value
 
 
-def _params(m, n, k, l, q, side, core, a_dtype_code, mma, want_fro2) -> Params:
+def _params(m, n, k, l, q, side, core, a_dtype_code, mma, want_fro2, orth) -> Params:
     p = Params()
     p.m, p.n, p.k, p.l, p.q = int(m), int(n), int(k), int(l), int(q)
-    p.side, p.core, p.orth = SIDE[side], CORE[core], 0
+    p.side, p.core, p.orth = SIDE[side], CORE[core], ORTH[orth]
     p.a_dtype, p.mma, p.want_fro2 = a_dtype_code, MMA[mma], 1 if want_fro2 else 0
     return p
 
 
 def solve(A, Phi, k: int, l: int, q: int = 0, side: str = "right", core: str = "exact", mma: str = "auto",
           a_tile_scales=None, want_fro2: bool = False, out=None, wait: bool = True, handle: Handle | None = None,
-          A_ref=None):
+          A_ref=None, orth: str = "stabilised"):
     """CoR-UTV of a device matrix A (Alg. 2 / Alg. 3): returns U, T, V, perm.
 
     A: (m, n) row-major float64 / float32 / bfloat16 / float8_e4m3fn (with
@@ -238,6 +240,8 @@ def solve(A, Phi, k: int, l: int, q: int = 0, side: str = "right", core: str = "
     float64 if A is float64 else float32.  T is float64.
     A_ref: optional float32 (m, n) matrix for the correction pass of a
     bfloat16 / float8 A (corutv_solve_corrected: the core D from A_ref).
+    orth: "stabilised" (one shifted CholeskyQR pass for the sketches of the
+    earlier power steps) or "strict" (shifted CholeskyQR3 for every sketch).
     out: optional (U, T, V, perm) preallocated outputs.  wait=True
     synchronises and returns the device info; wait=False leaves the work
     enqueued on the current stream (info is None).
@@ -250,7 +254,7 @@ def solve(A, Phi, k: int, l: int, q: int = 0, side: str = "right", core: str = "
     fdt = torch.float64 if code == 0 else torch.float32
     if Phi.dtype != fdt:
         raise TypeError(f"Phi must be {fdt}")
-    p = _params(m, n, k, l, q, side, core, code, mma, want_fro2)
+    p = _params(m, n, k, l, q, side, core, code, mma, want_fro2, orth)
     if out is None:
         dev = A.device
         U = torch.empty((m, l), dtype=fdt, device=dev)

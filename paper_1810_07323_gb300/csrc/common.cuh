@@ -16,7 +16,7 @@ struct DevStatus {
   int flags;            // kStat* bits
   int chol_fallbacks;   // dependent sketch columns replaced
   int timeouts;         // bounded waits that expired
-  int pad;
+  int orth_skip;        // 1: the last CholeskyQR pass found Q^T Q = I and was skipped
   double fro2_A;
   double fro2_T;
   double fro2_Tk;

@@ -23,7 +23,7 @@ int64_t& launch_counter() {
 }
 }  // namespace corutv
 
-enum Phase { kPhPass = 0, kPhOrth, kPhCore, kPhQrcp, kPhAsm, kPhFro2, kNumPh };
+enum Phase { kPhPass = 0, kPhOrth, kPhCore, kPhQrcp, kPhAsm, kPhFro2, kPhCorr, kPhQuant, kNumPh };
 
 struct TraceRec {
   int phase;
@@ -57,6 +57,9 @@ constexpr double kShiftRel32 = 1e-5;    // first CholeskyQR pass, FP32 arithmeti
 constexpr double kShiftRel64 = 1e-12;   // first CholeskyQR pass, FP64 arithmetic
 constexpr double kTolRel32 = 1e-7;      // dependent-column threshold, FP32
 constexpr double kTolRel64 = 1e-14;     // dependent-column threshold, FP64
+// Skip the third FP32 CholeskyQR pass when max |Q^T Q - I| after the second is at most
+// this: a further FP32 pass reaches ~c u32 l (1e-6 .. 1e-5 for l <= 128) and gains nothing
+constexpr float kSkipTol32 = 2e-6f;
 constexpr int64_t kAlign = 256;
 
 inline int64_t ld_for(int64_t len) { return round_up(len < 1 ? 1 : len, 64); }
@@ -171,7 +174,7 @@ int check_params(const corutv_params* p) {
   if (p->a_dtype < CORUTV_F64 || p->a_dtype > CORUTV_FP8_E4M3) return CORUTV_ERR_INVALID_ARG;
   if (p->side != CORUTV_SIDE_RIGHT && p->side != CORUTV_SIDE_LEFT) return CORUTV_ERR_INVALID_ARG;
   if (p->core != CORUTV_CORE_EXACT && p->core != CORUTV_CORE_SKETCH) return CORUTV_ERR_INVALID_ARG;
-  if (p->orth != CORUTV_ORTH_STABILISED) return CORUTV_ERR_INVALID_ARG;
+  if (p->orth != CORUTV_ORTH_STABILISED && p->orth != CORUTV_ORTH_STRICT) return CORUTV_ERR_INVALID_ARG;
   if (p->mma < CORUTV_MMA_AUTO || p->mma > CORUTV_MMA_BF16X2) return CORUTV_ERR_INVALID_ARG;
   if (p->mma == CORUTV_MMA_TF32X3) return CORUTV_ERR_UNSUPPORTED;
   if (p->m <= 0 || p->n <= 0) return CORUTV_ERR_SHAPE;
@@ -264,7 +267,7 @@ inline bool tma_rows_ok(const void* A, int64_t lda, int a_dtype) {
 
 int run_pass(corutv_handle* h, int dir, int a_dtype, int mma, const void* A, int64_t lda, int64_t m, int64_t n,
              const float* scales, const void* Xt, int64_t ldx, int l, void* Ct, int64_t ldc, void* partials,
-             float* Xr, int64_t ldr, double* fro_parts) {
+             float* Xr, int64_t ldr, double* fro_parts, int phase = kPhPass) {
   PassArgs a{};
   a.A = A;
   a.lda = lda;
@@ -283,7 +286,7 @@ int run_pass(corutv_handle* h, int dir, int a_dtype, int mma, const void* A, int
   const int eng = pick_mma(a_dtype, mma, tma_rows_ok(A, lda, a_dtype));
   if (eng != CORUTV_MMA_SIMT && !tma_rows_ok(A, lda, a_dtype)) return CORUTV_ERR_ALIGN;
   const double bytes = (double)m * n * elem_bytes(a_dtype) + (double)l * (a.K + a.len_out) * tc_bytes(a_dtype);
-  PhaseTimer tm(h, kPhPass, bytes);
+  PhaseTimer tm(h, phase, bytes);
   if (eng == CORUTV_MMA_SIMT) {
     if (fro_parts) return CORUTV_ERR_UNSUPPORTED;
     CU(launch_pass_simt(a, dir, a_dtype, h->sms, h->stream));
@@ -317,22 +320,43 @@ int run_pass(corutv_handle* h, int dir, int a_dtype, int mma, const void* A, int
   return CORUTV_OK;
 }
 
-// shifted CholeskyQR3 on an ST block (in place)
+// Shifted CholeskyQR on an ST block (in place).  passes = 3: shifted
+// CholeskyQR3, Q with orthonormal columns; on the FP32 path the third pass is
+// skipped when the Gram matrix of the second pass's Q is the identity within
+// kSkipTol32.  passes = 1: one shifted pass, Q spans range(C) and is well
+// conditioned (used for the sketches the power iteration only multiplies
+// again).  R_out (may be null): the product R = R_3 R_2 R_1 with C = Q R (FP64,
+// ld l); it uses the D and Qt scratch blocks, free outside a solve.
 template <typename TC>
-int orth_st(corutv_handle* h, TC* Ct, int64_t ldc, int64_t len, int l, const Plan& pl, double* Rout_last) {
+int orth_st(corutv_handle* h, TC* Ct, int64_t ldc, int64_t len, int l, const Plan& pl, int passes, double* Rout) {
   const bool f64 = sizeof(TC) == 8;
   PhaseTimer tm(h, kPhOrth);
-  for (int pass = 0; pass < 3; ++pass) {
+  for (int pass = 0; pass < passes; ++pass) {
     CU(launch_gram<TC>(Ct, ldc, Ct, ldc, len, l, static_cast<TC*>(pl.gram_parts), gram_parts(len, h->sms), pl.G,
                        kMaxL, h->stream));
     const double shift = pass == 0 ? (f64 ? kShiftRel64 : kShiftRel32) : 0.0;
     const double tol = f64 ? kTolRel64 : kTolRel32;
+    int* skip = (!f64 && passes == 3 && pass == 2) ? &pl.status->orth_skip : nullptr;
+    double* rpass = Rout ? (pass == 0 ? Rout : pl.D) : nullptr;
     CU(launch_cholinv<TC>(pl.G, kMaxL, l, shift, tol, static_cast<TC*>(pl.R), static_cast<TC*>(pl.Rinv), pl.defic,
-                          pl.status, pass == 2 ? Rout_last : nullptr, h->stream));
-    CU(launch_lmul<TC>(Ct, ldc, len, l, static_cast<const TC*>(pl.Rinv), kMaxL, Ct, ldc, false, h->stream));
-    CU(launch_fill_deficient<TC>(Ct, ldc, len, l, pl.defic, pass, h->stream));
+                          pl.status, rpass, skip, kSkipTol32, h->stream));
+    CU(launch_lmul<TC>(Ct, ldc, len, l, static_cast<const TC*>(pl.Rinv), kMaxL, Ct, ldc, false, pl.defic, pass,
+                       skip, h->stream));
+    if (Rout && pass > 0) {
+      // R <- R_pass R
+      CU(launch_upper_mul(pl.D, Rout, pl.Qt, l, h->stream));
+      CU(cudaMemcpyAsync(Rout, pl.Qt, sizeof(double) * l * l, cudaMemcpyDeviceToDevice, h->stream));
+    }
   }
   return CORUTV_OK;
+}
+
+// CholeskyQR passes for the sketches of power step `it`: the last step's sketches
+// become Q1 and Q2 and are orthonormalised in full; earlier ones only feed the next
+// product, which needs a well-conditioned basis of the same range (one shifted pass),
+// unless the caller asks for ORTH_STRICT.
+int orth_passes(const corutv_params* p, int it) {
+  return (it == p->q || p->orth == CORUTV_ORTH_STRICT) ? 3 : 1;
 }
 
 // A_ref (FP32, lda_ref) non-null: correction pass -- the core D of S5 is computed from A_ref
@@ -371,7 +395,7 @@ int solve_impl(corutv_handle* h, const corutv_params* p, const Plan& pl, const v
     if (rc) return rc;
     ++passes;
     // S2: orth(C1)
-    rc = orth_st<TC>(h, P1, pl.ld1, pl.len1, l, pl, nullptr);
+    rc = orth_st<TC>(h, P1, pl.ld1, pl.len1, l, pl, orth_passes(p, it), nullptr);
     if (rc) return rc;
     // S3: C2 = A^T Q1  (Alg. 3 step 4)
     rc = run_pass(h, dir2, p->a_dtype, p->mma, A, lda, p->m, p->n, scales, P1, pl.ld1, l, P2, pl.ld2,
@@ -382,14 +406,14 @@ int solve_impl(corutv_handle* h, const corutv_params* p, const Plan& pl, const v
       CU(cudaMemcpy2DAsync(P3, pl.ld3 * sizeof(TC), P2, pl.ld2 * sizeof(TC), pl.len2 * sizeof(TC), l,
                            cudaMemcpyDeviceToDevice, h->stream));
     // S4: orth(C2)
-    rc = orth_st<TC>(h, P2, pl.ld2, pl.len2, l, pl, nullptr);
+    rc = orth_st<TC>(h, P2, pl.ld2, pl.len2, l, pl, orth_passes(p, it), nullptr);
     if (rc) return rc;
   }
   // S5: core D = Q1^T A Q2 (Alg. 2 step 5)
   if (A_ref) {
     // correction pass: E = A_ref Q2 over the FP32 matrix (||A_ref||^2 fused where the tensor cores run it)
     int rc = run_pass(h, dir1, CORUTV_F32, ref_mma, A_ref, lda_ref, p->m, p->n, nullptr, P2, pl.ld2, l, P3,
-                      pl.ld3, pl.partials, Xr, pl.ldr, fuse_fro2 ? pl.fro_parts : nullptr);
+                      pl.ld3, pl.partials, Xr, pl.ldr, fuse_fro2 ? pl.fro_parts : nullptr, kPhCorr);
     if (rc) return rc;
     ++passes;
     PhaseTimer tm(h, kPhCore);
@@ -577,7 +601,12 @@ int corutv_quantize(corutv_handle* h, int dtype, const float* A, int64_t lda, in
   if (dtype == CORUTV_FP8_E4M3 && !tile_scales) return CORUTV_ERR_INVALID_ARG;
   if (m <= 0 || n <= 0 || lda < n || ldo < n) return CORUTV_ERR_SHAPE;
   if (cdiv(m, 128) > 65535) return CORUTV_ERR_SHAPE;
-  CU(launch_quantize(dtype, A, lda, m, n, out, ldo, tile_scales, h->stream));
+  const int64_t l0 = launch_counter();
+  {
+    PhaseTimer tm(h, kPhQuant);
+    CU(launch_quantize(dtype, A, lda, m, n, out, ldo, tile_scales, h->stream));
+  }
+  h->launches += launch_counter() - l0;
   return CORUTV_OK;
 }
 
@@ -618,6 +647,8 @@ int corutv_trace_read(corutv_handle* h, corutv_trace* out) {
       case kPhQrcp: t.qrcp_ms += ms; break;
       case kPhAsm: t.assembly_ms += ms; break;
       case kPhFro2: t.fro2_ms += ms; break;
+      case kPhCorr: t.corr_ms += ms; t.corr_bytes += r.bytes; t.corr_launches += 1; break;
+      case kPhQuant: t.quant_ms += ms; break;
       default: break;
     }
     h->ev_pool.push_back(r.a);
@@ -692,8 +723,8 @@ int corutv_orthonormalize(corutv_handle* h, int dtype, void* Ct, int64_t ldc, in
   int rc = block_ws(h, len, len, l, dtype, pl);
   if (rc) return rc;
   CU(cudaMemsetAsync(pl.status, 0, sizeof(DevStatus), h->stream));
-  if (dtype == CORUTV_F64) return orth_st<double>(h, static_cast<double*>(Ct), ldc, len, l, pl, R_out);
-  return orth_st<float>(h, static_cast<float*>(Ct), ldc, len, l, pl, R_out);
+  if (dtype == CORUTV_F64) return orth_st<double>(h, static_cast<double*>(Ct), ldc, len, l, pl, 3, R_out);
+  return orth_st<float>(h, static_cast<float*>(Ct), ldc, len, l, pl, 3, R_out);
 }
 
 int corutv_gram(corutv_handle* h, int dtype, const void* Xt, int64_t ldx, const void* Yt, int64_t ldy, int64_t len,

@@ -65,18 +65,23 @@ template <typename TC>
 cudaError_t launch_gram(const TC* Xt, int64_t ldx, const TC* Yt, int64_t ldy, int64_t len, int l, TC* parts,
                         int gparts, double* G, int64_t ldg, cudaStream_t st);
 int gram_parts(int64_t len, int sms);
+// skip_flag (FP32 only, may be null): skip the factorisation when max |G - I| <= skip_tol
+// (writes *skip_flag = 1 and R_out = I); launch_lmul with the same flag then does nothing
 template <typename TC>
 cudaError_t launch_cholinv(const double* G, int64_t ldg, int l, double shift_rel, double tol_rel, TC* R, TC* Rinv,
-                           int* defic, DevStatus* status, double* Rout, cudaStream_t st);
+                           int* defic, DevStatus* status, double* Rout, int* skip_flag, float skip_tol,
+                           cudaStream_t st);
+// Out = S^T In on ST blocks (S upper triangular); rows j with defic[j] set (defic may be
+// null) receive the deterministic replacement vector of `pass` instead
 template <typename TC>
 cudaError_t launch_lmul(const TC* In, int64_t ldi, int64_t len, int l, const TC* S, int64_t lds, TC* Out,
-                        int64_t ldo, bool out_rowmajor, cudaStream_t st);
+                        int64_t ldo, bool out_rowmajor, const int* defic, int pass, const int* skip_flag,
+                        cudaStream_t st);
 template <typename TC>
 cudaError_t launch_lmul_f64s(const TC* In, int64_t ldi, int64_t len, int l, const double* S, int64_t lds, TC* Out,
                              int64_t ldo, bool out_rowmajor, cudaStream_t st);
-template <typename TC>
-cudaError_t launch_fill_deficient(TC* Ct, int64_t ldc, int64_t len, int l, const int* defic, int pass,
-                                  cudaStream_t st);
+// C = A B for upper-triangular l x l FP64 matrices (row-major, ld l; C distinct from A, B)
+cudaError_t launch_upper_mul(const double* A, const double* B, double* C, int l, cudaStream_t st);
 template <typename TC>
 cudaError_t launch_gather_cols(const TC* St, int64_t lds, int64_t len, int l, const int32_t* perm, TC* Out,
                                int64_t ldo, cudaStream_t st);

@@ -15,7 +15,6 @@
 
 namespace corutv {
 
-constexpr int kCholTPR = 8;   // threads per row of the register Cholesky (1024 threads)
 constexpr int kQrcpTPC = 4;   // threads per column of the register QRCP (512 threads)
 
 // =============================================================================== Gram
@@ -222,361 +221,187 @@ __global__ void __launch_bounds__(512) cholinv_kernel(const double* __restrict__
   if (lane == 0 && nfall && status) atomicAdd(&status->chol_fallbacks, nfall);
 }
 
-// FP32 variant with rows in registers: thread (a, h) holds columns
-// b = 64 h .. 64 h + 63 of row a of both blocks.  Step j: the two threads of
-// row j publish it (double-buffered, one barrier per step) with the entries
-// that must not act zeroed -- G part only for b > j, L^-1 part only for b <= j
-// -- so every row a > j subtracts m_a = G[j][a] / d_j times it with
-// unpredicated vector loads.  Same algebra as cholinv_kernel.
-template <int TPR>
-__global__ void __launch_bounds__(kMaxL * TPR) cholinv_reg_kernel(const double* __restrict__ G, int64_t ldg, int l,
-                                                          double shift_rel, double tol_rel, float* __restrict__ Rg,
-                                                          float* __restrict__ Rinvg, int* __restrict__ defic,
-                                                          DevStatus* status, double* __restrict__ Rout) {
-  constexpr int CPT = kMaxL / TPR, NWARP = kMaxL * TPR / 32;
-  __shared__ __align__(16) float prow[2][kMaxL];
-  __shared__ __align__(16) float plrow[2][kMaxL];
-  __shared__ float pivm[2];             // [buf]: 1 / d_j (0 if dependent)
-  __shared__ double red[NWARP];
-  const int tid = threadIdx.x, a = tid / TPR, h = tid % TPR, lane = tid & 31, warp = tid >> 5;
-  const int b0 = h * CPT;
-  const unsigned grp = ((TPR == 32) ? 0xffffffffu : ((1u << TPR) - 1u)) << (lane & ~(TPR - 1));
-  float g[CPT], li[CPT];
-  double tr = 0.0;
-#pragma unroll
-  for (int s = 0; s < CPT; ++s) {
-    const int b = b0 + s;
-    const bool ok = a < l && b < l;
-    const double v = ok ? G[a * ldg + b] : 0.0;
-    g[s] = (float)v;
-    li[s] = (ok && a == b) ? 1.f : 0.f;
-    if (ok && a == b) tr += v;
-  }
-  for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
-  if (lane == 0) red[warp] = tr;
-  __syncthreads();
-  double trace = 0.0;
-  for (int w = 0; w < NWARP; ++w) trace += red[w];
-  const double shift = shift_rel * trace;
-  double diag0 = 0.0;
-#pragma unroll
-  for (int s = 0; s < CPT; ++s)
-    if (b0 + s == a && a < l) {
-      diag0 = (double)g[s] + shift;
-      g[s] = (float)diag0;
-    }
-#pragma unroll
-  for (int o = 1; o < TPR; o <<= 1) diag0 = fmax(diag0, __shfl_xor_sync(0xffffffffu, diag0, o));
-  float piv_mine = 1.f;
-  bool dep_mine = false;
-  for (int j = 0; j < l; ++j) {
-    const int buf = j & 1;
-    if (a == j) {
-      float dj = 0.f;
-#pragma unroll
-      for (int s = 0; s < CPT; ++s)
-        if (b0 + s == j) dj = g[s];
-#pragma unroll
-      for (int o = 1; o < TPR; o <<= 1) dj += __shfl_xor_sync(grp, dj, o);
-      const bool dep = !((double)dj > tol_rel * diag0) || !(diag0 > 0.0);
-      piv_mine = dep ? 1.f : dj;
-      dep_mine = dep;
-      float4* pr = reinterpret_cast<float4*>(&prow[buf][b0]);
-      float4* pl = reinterpret_cast<float4*>(&plrow[buf][b0]);
-#pragma unroll
-      for (int q = 0; q < CPT / 4; ++q) {
-        float4 vg, vl;
-        float* pg = &vg.x;
-        float* plv = &vl.x;
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int s = 4 * q + e, b = b0 + s;
-          pg[e] = (b > j) ? g[s] : 0.f;
-          plv[e] = (b <= j) ? li[s] : 0.f;
-        }
-        pr[q] = vg;
-        pl[q] = vl;
-      }
-      if (h == 0) pivm[buf] = dep ? 0.f : 1.f / dj;
-    }
-    __syncthreads();
-    if (a > j && a < l) {
-      const float m = prow[buf][a] * pivm[buf];
-      const float4* pr = reinterpret_cast<const float4*>(&prow[buf][b0]);
-      const float4* pl = reinterpret_cast<const float4*>(&plrow[buf][b0]);
-#pragma unroll
-      for (int q = 0; q < CPT / 4; ++q) {
-        const float4 vg = pr[q], vl = pl[q];
-        g[4 * q + 0] -= m * vg.x; g[4 * q + 1] -= m * vg.y; g[4 * q + 2] -= m * vg.z; g[4 * q + 3] -= m * vg.w;
-        li[4 * q + 0] -= m * vl.x; li[4 * q + 1] -= m * vl.y; li[4 * q + 2] -= m * vl.z; li[4 * q + 3] -= m * vl.w;
-      }
-    }
-  }
-  __syncthreads();
-  if (a < l) {
-    const float ra = sqrtf(piv_mine);
-#pragma unroll
-    for (int s = 0; s < CPT; ++s) {
-      const int b = b0 + s;
-      if (b >= l) continue;
-      float r = 0.f;
-      if (b == a) r = ra;
-      else if (b > a && !dep_mine) r = g[s] / ra;
-      Rg[a * kMaxL + b] = r;
-      if (Rout) Rout[a * l + b] = (double)r;
-      // R^-1[b][a] = L^-1[a][b] / sqrt(d_a) for b <= a
-      Rinvg[b * kMaxL + a] = (b <= a) ? li[s] / ra : 0.f;
-    }
-  }
-  int nfall = (h == 0 && a < l && dep_mine) ? 1 : 0;
-  for (int o = 16; o > 0; o >>= 1) nfall += __shfl_xor_sync(0xffffffffu, nfall, o);
-  if (h == 0 && a < l) defic[a] = dep_mine ? 1 : 0;
-  if (lane == 0 && nfall && status) atomicAdd(&status->chol_fallbacks, nfall);
+// FP32 variant with the matrices in registers: the same elimination of
+// [G + s I | I] as cholinv_kernel, with the upper triangle of G and the lower
+// triangle of L^-1 split into 4 x 4 blocks.  Thread t owns block (I, J), J >= I,
+// of G and block (J, I) of L^-1 (t enumerates the upper block triangle row by
+// row).  Step j reads row j of G and of L^-1 from a double-buffered shared row
+// (published at the end of step j - 1 by the owners of row j), applies its
+// multipliers m_a = G[j][a] / d_j to the rows a > j of both blocks, and the
+// owners of row j + 1 publish it: one block barrier per step.
+__device__ __forceinline__ float f4(const float4& v, int i) {
+  return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
 }
 
-// C (M x N) = op(A) B over K in shared memory, 4 x 4 register tiles spread
-// over the block's threads.  op(A)[r][k] = A[k][r] (TRANS_A) or A[r][k].
-// MODE 0: C = result, 1: C -= result, 2: C = -result.  upper_only skips
-// tiles strictly below the diagonal.  M, N multiples of 4; rows 16-byte aligned.
-template <bool TRANS_A, int MODE>
-__device__ __forceinline__ void smem_gemm44(const float* __restrict__ Ap, int lda, const float* __restrict__ Bp,
-                                            int ldb, float* __restrict__ Cp, int ldc, int M, int N, int K,
-                                            bool upper_only) {
-  const int tn = N >> 2, tiles = (M >> 2) * tn;
-  for (int t = threadIdx.x; t < tiles; t += blockDim.x) {
-    const int r0 = (t / tn) << 2, c0 = (t % tn) << 2;
-    if (upper_only && c0 + 3 < r0) continue;
-    float acc[4][4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-#pragma unroll 4
-    for (int k = 0; k < K; ++k) {
-      float a[4];
-      if (TRANS_A) {
-        const float4 v = *reinterpret_cast<const float4*>(Ap + k * lda + r0);
-        a[0] = v.x; a[1] = v.y; a[2] = v.z; a[3] = v.w;
-      } else {
-#pragma unroll
-        for (int i = 0; i < 4; ++i) a[i] = Ap[(r0 + i) * lda + k];
-      }
-      const float4 b = *reinterpret_cast<const float4*>(Bp + k * ldb + c0);
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        acc[i][0] = fmaf(a[i], b.x, acc[i][0]);
-        acc[i][1] = fmaf(a[i], b.y, acc[i][1]);
-        acc[i][2] = fmaf(a[i], b.z, acc[i][2]);
-        acc[i][3] = fmaf(a[i], b.w, acc[i][3]);
-      }
+constexpr int kPipeMaxThreads = (kMaxL / 4) * (kMaxL / 4 + 1) / 2 + 16;   // 528 blocks -> 544 threads
+
+// skip_flag (may be null): the kernel first measures max |G - I| over the l x l
+// block; at or below skip_tol it writes 1 to *skip_flag, R_out = I (if asked)
+// and returns (the caller's Q already has orthonormal columns to that level),
+// otherwise it writes 0 and factors as usual.
+__global__ void __launch_bounds__(kPipeMaxThreads, 1) cholinv_pipe_kernel(
+    const double* __restrict__ G, int64_t ldg, int l, double shift_rel, double tol_rel, float* __restrict__ Rg,
+    float* __restrict__ Rinvg, int* __restrict__ defic, DevStatus* status, double* __restrict__ Rout,
+    int* __restrict__ skip_flag, float skip_tol) {
+  __shared__ __align__(16) float rowbuf[2][kMaxL];
+  __shared__ __align__(16) float libuf[2][kMaxL];
+  __shared__ float diag0[kMaxL];
+  __shared__ float piv[kMaxL];
+  __shared__ int dep_s[kMaxL];
+  __shared__ double red[32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const int nb = (l + 3) >> 2;
+  const bool own = tid < nb * (nb + 1) / 2;
+  int I = 0, J = 0;
+  if (own) {
+    int t = tid, i = 0;
+    while (t >= nb - i) {
+      t -= nb - i;
+      ++i;
     }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      float4* c4 = reinterpret_cast<float4*>(Cp + (r0 + i) * ldc + c0);
-      float4 v;
-      if (MODE == 1) {
-        v = *c4;
-        v.x -= acc[i][0]; v.y -= acc[i][1]; v.z -= acc[i][2]; v.w -= acc[i][3];
-      } else if (MODE == 2) {
-        v = make_float4(-acc[i][0], -acc[i][1], -acc[i][2], -acc[i][3]);
-      } else {
-        v = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
-      }
-      *c4 = v;
-    }
+    I = i;
+    J = i + t;
   }
-}
-
-// FP32 blocked variant (l <= 128, padded with an identity block to 128 = 4
-// blocks of 32).  For each diagonal block o = 32 kb:
-//   1. one warp factors the 32 x 32 block by the same symmetric elimination
-//      (lane i holds column i of the block and of its L^-1 block; multipliers
-//      are broadcast with shuffles, no block barrier) and writes R11, R11^-1;
-//   2. panel: R12 = R11^-T A12 (rows of dependent columns zeroed);
-//   3. trailing update A22 -= R12^T R12.
-// Then R^-1 is completed block column by block column:
-//   X_kk = R_kk^-1,  X_ik = -(sum_{p=i}^{k-1} X_ip R_pk) X_kk.
-// About twenty block barriers in all; the same algebra and dependent-column
-// rule as cholinv_kernel.
-__global__ void __launch_bounds__(512) cholinv_blk_kernel(const double* __restrict__ G, int64_t ldg, int l,
-                                                          double shift_rel, double tol_rel, float* __restrict__ Rg,
-                                                          float* __restrict__ Rinvg, int* __restrict__ defic,
-                                                          DevStatus* status, double* __restrict__ Rout) {
-  constexpr int N = kMaxL, NB = 32, LD = N + 4;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  float* A = reinterpret_cast<float*>(smem_raw);      // N x LD: G, becomes R (upper)
-  float* X = A + N * LD;                             // N x LD: R^-1 (upper)
-  float* T = X + N * LD;                             // NB x LD scratch (panel / products)
-  __shared__ float diag0[N];
-  __shared__ int dep[N];
-  __shared__ double red[16];
-  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
-
-  // 32 independent loads per thread, issued before any use (no accumulation in the loop)
-  {
-    float v[N * N / 512];
+  __shared__ double redmax[32];
+  float g[4][4], li[4][4];
+  double tr = 0.0, dev = 0.0;
 #pragma unroll
-    for (int q = 0; q < N * N / 512; ++q) {
-      const int e = tid + 512 * q, a = e >> 7, b = e & (N - 1);
-      v[q] = (a < l && b < l) ? (float)G[a * ldg + b] : ((a == b) ? 1.f : 0.f);
-    }
+  for (int r = 0; r < 4; ++r)
 #pragma unroll
-    for (int q = 0; q < N * N / 512; ++q) {
-      const int e = tid + 512 * q, a = e >> 7, b = e & (N - 1);
-      A[a * LD + b] = v[q];
-      X[a * LD + b] = 0.f;
+    for (int c = 0; c < 4; ++c) {
+      const int a = 4 * I + r, b = 4 * J + c;
+      const double gv = (own && a < l && b < l) ? G[a * ldg + b] : 0.0;
+      if (own && a < l && b < l) dev = fmax(dev, fabs(gv - (a == b ? 1.0 : 0.0)));
+      g[r][c] = (float)gv;
+      li[r][c] = (4 * J + r == 4 * I + c) ? 1.f : 0.f;
     }
+  if (own && I == J) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+      if (4 * I + r < l) tr += (double)g[r][r];
+  }
+  for (int e = tid; e < 2 * kMaxL; e += blockDim.x) (&libuf[0][0])[e] = 0.f;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    tr += __shfl_xor_sync(0xffffffffu, tr, o);
+    dev = fmax(dev, __shfl_xor_sync(0xffffffffu, dev, o));
+  }
+  if (lane == 0) {
+    red[warp] = tr;
+    redmax[warp] = dev;
   }
   __syncthreads();
-  double tr = (tid < l) ? (double)A[tid * LD + tid] : 0.0;
-  for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
-  if (lane == 0) red[warp] = tr;
-  __syncthreads();
-  double trace = 0.0;
-  for (int w = 0; w < nt / 32; ++w) trace += red[w];
+  double trace = 0.0, devmax = 0.0;
+  for (int w = 0; w < nw; ++w) {
+    trace += red[w];
+    devmax = fmax(devmax, redmax[w]);
+  }
+  if (skip_flag) {
+    const bool skip = devmax <= (double)skip_tol;
+    if (tid == 0) *skip_flag = skip ? 1 : 0;
+    if (skip) {
+      if (Rout)
+        for (int e = tid; e < l * l; e += blockDim.x) Rout[e] = (e / l == e % l) ? 1.0 : 0.0;
+      return;
+    }
+  }
   const float shift = (float)(shift_rel * trace);
   const float tolf = (float)tol_rel;
-  for (int a = tid; a < N; a += nt) {
-    if (a < l) A[a * LD + a] += shift;
-    diag0[a] = A[a * LD + a];
+  if (own) {
+    if (I == J) {
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int a = 4 * I + r;
+        if (a < l) {
+          g[r][r] += shift;
+          diag0[a] = g[r][r];
+        }
+      }
+    }
+    // row 0 of G and of L^-1
+    if (I == 0) *reinterpret_cast<float4*>(&rowbuf[0][4 * J]) = make_float4(g[0][0], g[0][1], g[0][2], g[0][3]);
+    if (J == 0) *reinterpret_cast<float4*>(&libuf[0][4 * I]) = make_float4(li[0][0], li[0][1], li[0][2], li[0][3]);
   }
   __syncthreads();
 
-  for (int kb = 0; kb < N / NB; ++kb) {
-    const int o = NB * kb, rest = N - o - NB;
-    // ---- 1. diagonal block by one warp
-    if (warp == 0) {
-      float a[NB], w[NB];     // column `lane` of the block and of its L^-1
-#pragma unroll
-      for (int r = 0; r < NB; ++r) {
-        a[r] = A[(o + r) * LD + o + lane];
-        w[r] = (r == lane) ? 1.f : 0.f;
-      }
-      const float dg0 = diag0[o + lane];
-      float* prow = T;        // staging of the multipliers of step j (T is free here)
-      float dv = 1.f;          // pivot of row `lane`
-      bool dp = false;
-#pragma unroll
-      for (int j = 0; j < NB; ++j) {
-        // lane j owns the pivot: publish m_k = A[j][k] / d for every k (A[j][k] = lane k's a[j])
-        const float d = __shfl_sync(0xffffffffu, a[j], j);
-        const float d0 = __shfl_sync(0xffffffffu, dg0, j);
-        const bool depj = !(d > tolf * d0) || !(d0 > 0.f);
-        const float inv_d = depj ? 0.f : __frcp_rn(d);
-        if (lane == j) { dv = depj ? 1.f : d; dp = depj; }
-        prow[lane] = a[j] * inv_d;            // m_lane (used for k > j)
-        __syncwarp();
-        const float rowj_a = a[j];            // A[j][lane]
-        const float rowj_w = w[j];            // L^-1[j][lane]
-#pragma unroll
-        for (int k = j + 1; k < NB; ++k) {
-          const float m = prow[k];
-          a[k] = fmaf(-m, rowj_a, a[k]);
-          w[k] = fmaf(-m, rowj_w, w[k]);
-        }
-        __syncwarp();
-      }
-      // lane holds column `lane` of U = D L^T and of L^-1; its pivot is dv
-      const float sq = sqrtf(dv);
-      const float rsq = 1.f / sq;
-      dep[o + lane] = dp ? 1 : 0;
-      // R11[k][lane] = U[k][lane] / sqrt(d_k) for k <= lane (0 above for dependent rows)
-#pragma unroll
-      for (int k = 0; k < NB; ++k) {
-        const float rk = __shfl_sync(0xffffffffu, rsq, k);     // 1 / sqrt(d_k)
-        const int depk = __shfl_sync(0xffffffffu, dp ? 1 : 0, k);
-        float r = 0.f;
-        if (k == lane) r = sq;
-        else if (k < lane && !depk) r = a[k] * rk;
-        A[(o + k) * LD + o + lane] = r;
-        // R11^-1[lane][k] = L^-1[k][lane] / sqrt(d_k), k >= lane
-        X[(o + lane) * LD + o + k] = (k >= lane) ? w[k] * rk : 0.f;
-      }
+  for (int j = 0; j < l; ++j) {
+    const int buf = j & 1;
+    const float d = rowbuf[buf][j];
+    const float d0 = diag0[j];
+    const bool dep = !(d > tolf * d0) || !(d0 > 0.f);
+    const float inv_d = dep ? 0.f : 1.f / d;
+    if (tid == 0) {
+      piv[j] = dep ? 1.f : d;
+      dep_s[j] = dep ? 1 : 0;
     }
-    __syncthreads();
-    if (rest > 0) {
-      const int c0 = o + NB;
-      // ---- 2. panel R12 = R11^-T A12 (R11^-1 upper, zero below) into T, rows of dependent columns zeroed
-      smem_gemm44<true, 0>(X + o * LD + o, LD, A + o * LD + c0, LD, T + c0, LD, NB, rest, NB, false);
-      __syncthreads();
-      for (int e = threadIdx.x; e < NB * rest; e += blockDim.x) {
-        const int k = e / rest, c = c0 + e % rest;
-        if (dep[o + k]) T[k * LD + c] = 0.f;
-      }
-      __syncthreads();
-      for (int e = threadIdx.x; e < NB * rest; e += blockDim.x) {
-        const int k = e / rest, c = c0 + e % rest;
-        A[(o + k) * LD + c] = T[k * LD + c];
-      }
-      // ---- 3. trailing update (upper tiles): A22 -= R12^T R12
-      smem_gemm44<true, 1>(T + c0, LD, T + c0, LD, A + c0 * LD + c0, LD, rest, rest, NB, true);
-      __syncthreads();
-    }
-  }
-  // ---- R^-1 off-diagonal blocks: X_ik = -(sum_{p=i}^{k-1} X_ip R_pk) X_kk.
-  // For block column k (columns ok .. ok+31) and every row r < ok:
-  //   S[r][c] = sum_{p=r}^{ok-1} X[r][p] R[p][c]   (kept in X's own (r, c) slots),
-  //   X[r][c] = -sum_{q=ok}^{c} S[r][q] X[q][c]    (staged in A's unused lower triangle).
-  for (int kb = 1; kb < N / NB; ++kb) {
-    const int ok = NB * kb;
-    // S = X[0:ok, 0:ok] R[0:ok, ok:ok+NB] into T-sized staging (rows of X are zero left of the diagonal)
-    // staged in X's own (r, ok..ok+NB) slots, which are still zero and not read here
-    smem_gemm44<false, 0>(X, LD, A + ok, LD, X + ok, LD, ok, NB, ok, false);
-    __syncthreads();
-    // X[r, ok:ok+NB] = -S[r, :] X_kk, one row per thread (read the row, then overwrite it)
-    for (int r = tid; r < ok; r += nt) {
-      float sv[NB], out[NB];
+    if (own) {
+      const float4 rI = *reinterpret_cast<const float4*>(&rowbuf[buf][4 * I]);
+      const float4 rJ = *reinterpret_cast<const float4*>(&rowbuf[buf][4 * J]);
+      const float4 lI = *reinterpret_cast<const float4*>(&libuf[buf][4 * I]);
 #pragma unroll
-      for (int q = 0; q < NB; q += 4) {
-        const float4 v = *reinterpret_cast<const float4*>(X + r * LD + ok + q);
-        sv[q] = v.x; sv[q + 1] = v.y; sv[q + 2] = v.z; sv[q + 3] = v.w;
-      }
+      for (int r = 0; r < 4; ++r) {
+        const float mi = (4 * I + r > j) ? f4(rI, r) * inv_d : 0.f;   // rows of the G block
+        const float mj = (4 * J + r > j) ? f4(rJ, r) * inv_d : 0.f;   // rows of the L^-1 block
 #pragma unroll
-      for (int c = 0; c < NB; ++c) out[c] = 0.f;
-#pragma unroll
-      for (int q = 0; q < NB; ++q) {
-        const float* xk = X + (ok + q) * LD + ok;
-#pragma unroll
-        for (int c = 0; c < NB; c += 4) {
-          const float4 v = *reinterpret_cast<const float4*>(xk + c);
-          out[c] = fmaf(sv[q], v.x, out[c]);
-          out[c + 1] = fmaf(sv[q], v.y, out[c + 1]);
-          out[c + 2] = fmaf(sv[q], v.z, out[c + 2]);
-          out[c + 3] = fmaf(sv[q], v.w, out[c + 3]);
+        for (int c = 0; c < 4; ++c) {
+          g[r][c] = fmaf(-mi, f4(rJ, c), g[r][c]);
+          li[r][c] = fmaf(-mj, f4(lI, c), li[r][c]);
         }
       }
+      const int p = j + 1;
+      if (p < l) {
+        const int pb = p & 1, pr = p & 3;
 #pragma unroll
-      for (int c = 0; c < NB; c += 4)
-        *reinterpret_cast<float4*>(X + r * LD + ok + c) = make_float4(-out[c], -out[c + 1], -out[c + 2], -out[c + 3]);
+        for (int r = 0; r < 4; ++r) {
+          if (r == pr && I == (p >> 2))
+            *reinterpret_cast<float4*>(&rowbuf[pb][4 * J]) = make_float4(g[r][0], g[r][1], g[r][2], g[r][3]);
+          if (r == pr && J == (p >> 2))
+            *reinterpret_cast<float4*>(&libuf[pb][4 * I]) = make_float4(li[r][0], li[r][1], li[r][2], li[r][3]);
+        }
+      }
     }
     __syncthreads();
   }
-  // ---- outputs
+  // outputs: R = D^(1/2) L^T (upper; rows of dependent columns e_j^T), R^-1[a][b] = L^-1[b][a] / sqrt(d_b)
+  if (own) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int a = 4 * I + r, b = 4 * J + c;
+        if (a >= l || b >= l) continue;
+        float rv = 0.f, xv = 0.f;
+        if (b == a) rv = sqrtf(piv[a]);
+        else if (b > a && !dep_s[a]) rv = g[r][c] / sqrtf(piv[a]);
+        if (b >= a) xv = li[c][r] / sqrtf(piv[b]);
+        Rg[a * kMaxL + b] = rv;
+        Rinvg[a * kMaxL + b] = xv;
+        if (Rout) Rout[a * l + b] = (double)rv;
+        if (b > a) {            // the mirrored lower entries
+          Rg[b * kMaxL + a] = 0.f;
+          Rinvg[b * kMaxL + a] = 0.f;
+          if (Rout) Rout[b * l + a] = 0.0;
+        }
+      }
+  }
   int nfall = 0;
-  for (int e = tid; e < l * l; e += nt) {
-    const int a = e / l, b = e % l;
-    const float r = (b >= a) ? A[a * LD + b] : 0.f;
-    Rg[a * kMaxL + b] = r;
-    Rinvg[a * kMaxL + b] = (b >= a) ? X[a * LD + b] : 0.f;
-    if (Rout) Rout[a * l + b] = (double)r;
+  for (int a = tid; a < l; a += blockDim.x) {
+    defic[a] = dep_s[a];
+    nfall += dep_s[a];
   }
-  for (int a = tid; a < l; a += nt) {
-    defic[a] = dep[a];
-    nfall += dep[a];
-  }
-  for (int o2 = 16; o2 > 0; o2 >>= 1) nfall += __shfl_xor_sync(0xffffffffu, nfall, o2);
+  for (int o = 16; o > 0; o >>= 1) nfall += __shfl_xor_sync(0xffffffffu, nfall, o);
   if (lane == 0 && nfall && status) atomicAdd(&status->chol_fallbacks, nfall);
 }
 
 template <typename TC>
 cudaError_t launch_cholinv(const double* G, int64_t ldg, int l, double shift_rel, double tol_rel, TC* R, TC* Rinv,
-                           int* defic, DevStatus* status, double* Rout, cudaStream_t st) {
+                           int* defic, DevStatus* status, double* Rout, int* skip_flag, float skip_tol,
+                           cudaStream_t st) {
   if constexpr (sizeof(TC) == 4) {
-    const size_t smem_blk = (size_t)(2 * kMaxL + 32) * (kMaxL + 4) * sizeof(float);
-    cudaError_t e0 = cudaFuncSetAttribute(cholinv_blk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)smem_blk);
-    if (e0 != cudaSuccess) return e0;
-    cholinv_blk_kernel<<<1, 512, smem_blk, st>>>(G, ldg, l, shift_rel, tol_rel, R, Rinv, defic, status, Rout);
+    const int nb = (l + 3) / 4;
+    const int threads = (nb * (nb + 1) / 2 + 31) / 32 * 32;
+    cholinv_pipe_kernel<<<1, threads, 0, st>>>(G, ldg, l, shift_rel, tol_rel, R, Rinv, defic, status, Rout,
+                                               skip_flag, skip_tol);
     CORUTV_COUNT_LAUNCH();
     return cudaGetLastError();
   }
@@ -587,33 +412,114 @@ cudaError_t launch_cholinv(const double* G, int64_t ldg, int l, double shift_rel
   return cudaGetLastError();
 }
 
+// Dependent columns: row j of an ST block (column j of Q) flagged dependent is
+// replaced by a deterministic pseudo-random vector (SplitMix64 of (pass, j, i),
+// uniform in [-1, 1)); the next CholeskyQR pass orthonormalises it against the
+// others.
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ double replacement_value(int pass, int j, int64_t i) {
+  const uint64_t h =
+      mix64(0x5EEDull + ((uint64_t)pass << 48) + ((uint64_t)j << 32) + (uint64_t)i * 0x9E3779B97F4A7C15ull);
+  return 2.0 * ((double)(h >> 11) * (1.0 / 9007199254740992.0)) - 1.0;
+}
+
 // =============================================================================== lmul
 // Out[j][i] = sum_{p<l} S[p][j] In[p][i]   (Out = S^T In on ST blocks, i.e. C S in
 // the untransposed view).  A CTA computes a BI-column tile; thread (tx, ty)
 // owns j = R ty + (0..R-1) and i = BI/16 tx + (0..BI/16-1).  upper: S is upper
 // triangular (S[p][j] = 0 for p > j), so the p loop stops at the thread's last j.
+// S and the In tile are staged in shared memory with independent (vector, for
+// FP32) loads issued before any is used.  The tile is read completely before it
+// is written, so In == Out (in place) is allowed.
+// defic (may be null): rows j with defic[j] != 0 receive the replacement vector
+// of `pass` instead of the product.
 // out_rowmajor: write Out^T into a row-major len x l matrix (staged through
 // shared memory so the row writes coalesce).
 template <typename TC, typename TS, int LP, int BI>
-__global__ void __launch_bounds__(256) lmul_kernel(const TC* __restrict__ In, int64_t ldi, int64_t len, int l,
-                                                   const TS* __restrict__ S, int64_t lds, TC* __restrict__ Out,
-                                                   int64_t ldo, int out_rowmajor, int upper) {
+__global__ void __launch_bounds__(256, 1) lmul_kernel(const TC* __restrict__ In, int64_t ldi, int64_t len, int l,
+                                                      const TS* __restrict__ S, int64_t lds, TC* __restrict__ Out,
+                                                      int64_t ldo, int out_rowmajor, int upper,
+                                                      const int* __restrict__ defic, int pass,
+                                                      const int* __restrict__ skip_flag) {
+  if (skip_flag && *skip_flag) return;     // the factor was found to be the identity
   constexpr int R = LP / 16, RI = BI / 16;
   constexpr int SP = LP + 4, IP = BI + 4;
+  constexpr bool kVecIn = sizeof(TC) == 4;
+  constexpr bool kVecS = sizeof(TS) == 4;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TC* Ss = reinterpret_cast<TC*>(smem_raw);      // LP x SP   (row p, column j)
   TC* Is = Ss + LP * SP;                         // LP x IP   (row p, column i)
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int64_t i0 = (int64_t)blockIdx.x * BI;
-  for (int e = tid; e < LP * LP; e += 256) {
-    const int p = e / LP, j = e % LP;
-    Ss[p * SP + j] = (p < l && j < l) ? (TC)S[p * lds + j] : TC(0);
-  }
   // (S rows p >= l and columns j >= l are zero: the p loop below can stop at l)
-  for (int e = tid; e < LP * BI; e += 256) {
-    const int p = e / BI, ii = e % BI;
-    const int64_t g = i0 + ii;
-    Is[p * IP + ii] = (p < l && g < len) ? In[p * ldi + g] : TC(0);
+  if constexpr (kVecS) {
+    constexpr int N4 = LP * LP / 4 / 256;
+    float4 v[N4];
+#pragma unroll
+    for (int q = 0; q < N4; ++q) {
+      const int e = tid + 256 * q, p = e / (LP / 4), j = 4 * (e % (LP / 4));
+      float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (p < l) {
+        const TS* src = S + p * lds + j;
+        if (j + 3 < l && (lds & 3) == 0) {
+          t = *reinterpret_cast<const float4*>(src);
+        } else {
+          if (j < l) t.x = src[0];
+          if (j + 1 < l) t.y = src[1];
+          if (j + 2 < l) t.z = src[2];
+        }
+      }
+      v[q] = t;
+    }
+#pragma unroll
+    for (int q = 0; q < N4; ++q) {
+      const int e = tid + 256 * q, p = e / (LP / 4), j = 4 * (e % (LP / 4));
+      *reinterpret_cast<float4*>(reinterpret_cast<float*>(Ss) + p * SP + j) = v[q];
+    }
+  } else {
+    for (int e = tid; e < LP * LP; e += 256) {
+      const int p = e / LP, j = e % LP;
+      Ss[p * SP + j] = (p < l && j < l) ? (TC)S[p * lds + j] : TC(0);
+    }
+  }
+  if constexpr (kVecIn) {
+    constexpr int N4 = LP * BI / 4 / 256;
+    float4 v[N4];
+    const bool vec_ok = (ldi & 3) == 0 && ((uintptr_t)In & 15) == 0;
+#pragma unroll
+    for (int q = 0; q < N4; ++q) {
+      const int e = tid + 256 * q, p = e / (BI / 4), ii = 4 * (e % (BI / 4));
+      const int64_t g = i0 + ii;
+      float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (p < l) {
+        const TC* src = In + p * ldi + g;
+        if (vec_ok && g + 3 < len) {
+          t = *reinterpret_cast<const float4*>(src);
+        } else {
+          if (g < len) t.x = src[0];
+          if (g + 1 < len) t.y = src[1];
+          if (g + 2 < len) t.z = src[2];
+          if (g + 3 < len) t.w = src[3];
+        }
+      }
+      v[q] = t;
+    }
+#pragma unroll
+    for (int q = 0; q < N4; ++q) {
+      const int e = tid + 256 * q, p = e / (BI / 4), ii = 4 * (e % (BI / 4));
+      *reinterpret_cast<float4*>(reinterpret_cast<float*>(Is) + p * IP + ii) = v[q];
+    }
+  } else {
+    for (int e = tid; e < LP * BI; e += 256) {
+      const int p = e / BI, ii = e % BI;
+      const int64_t g = i0 + ii;
+      Is[p * IP + ii] = (p < l && g < len) ? In[p * ldi + g] : TC(0);
+    }
   }
   __syncthreads();
   TC acc[R][RI];
@@ -644,10 +550,11 @@ __global__ void __launch_bounds__(256) lmul_kernel(const TC* __restrict__ In, in
     for (int v = 0; v < R; ++v) {
       const int j = R * ty + v;
       if (j >= l) continue;
+      const bool repl = defic && defic[j];
 #pragma unroll
       for (int u = 0; u < RI; ++u) {
         const int64_t g = i0 + RI * tx + u;
-        if (g < len) Out[j * ldo + g] = acc[v][u];
+        if (g < len) Out[j * ldo + g] = repl ? (TC)replacement_value(pass, j, g) : acc[v][u];
       }
     }
   } else {
@@ -668,7 +575,8 @@ __global__ void __launch_bounds__(256) lmul_kernel(const TC* __restrict__ In, in
 
 template <typename TC, typename TS, int LP, int BI>
 static cudaError_t lmul_variant(const TC* In, int64_t ldi, int64_t len, int l, const TS* S, int64_t lds, TC* Out,
-                                int64_t ldo, bool rowmajor, bool upper, cudaStream_t st) {
+                                int64_t ldo, bool rowmajor, bool upper, const int* defic, int pass,
+                                const int* skip_flag, cudaStream_t st) {
   const unsigned grid = (unsigned)cdiv(len, BI);
   if (grid == 0) return cudaSuccess;
   const size_t a = (size_t)LP * (LP + 4) + (size_t)LP * (BI + 4);
@@ -678,59 +586,52 @@ static cudaError_t lmul_variant(const TC* In, int64_t ldi, int64_t len, int l, c
                                        (int)sm);
   if (e != cudaSuccess) return e;
   lmul_kernel<TC, TS, LP, BI><<<grid, 256, sm, st>>>(In, ldi, len, l, S, lds, Out, ldo, rowmajor ? 1 : 0,
-                                                     upper ? 1 : 0);
+                                                     upper ? 1 : 0, defic, pass, skip_flag);
   CORUTV_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 
 template <typename TC, typename TS>
 static cudaError_t lmul_dispatch(const TC* In, int64_t ldi, int64_t len, int l, const TS* S, int64_t lds, TC* Out,
-                                 int64_t ldo, bool rowmajor, bool upper, cudaStream_t st) {
-  constexpr int BI = 64;
-  if (l <= 32) return lmul_variant<TC, TS, 32, BI>(In, ldi, len, l, S, lds, Out, ldo, rowmajor, upper, st);
-  if (l <= 64) return lmul_variant<TC, TS, 64, BI>(In, ldi, len, l, S, lds, Out, ldo, rowmajor, upper, st);
-  return lmul_variant<TC, TS, 128, BI>(In, ldi, len, l, S, lds, Out, ldo, rowmajor, upper, st);
+                                 int64_t ldo, bool rowmajor, bool upper, const int* defic, int pass,
+                                 const int* skip_flag, cudaStream_t st) {
+  // FP32: 128-column tiles (S and the tile fill ~135 KB of shared memory); FP64: 64 columns
+  constexpr int BI = sizeof(TC) == 4 ? 128 : 64;
+  if (l <= 32)
+    return lmul_variant<TC, TS, 32, BI>(In, ldi, len, l, S, lds, Out, ldo, rowmajor, upper, defic, pass, skip_flag, st);
+  if (l <= 64)
+    return lmul_variant<TC, TS, 64, BI>(In, ldi, len, l, S, lds, Out, ldo, rowmajor, upper, defic, pass, skip_flag, st);
+  return lmul_variant<TC, TS, 128, BI>(In, ldi, len, l, S, lds, Out, ldo, rowmajor, upper, defic, pass, skip_flag, st);
 }
 
 template <typename TC>
 cudaError_t launch_lmul(const TC* In, int64_t ldi, int64_t len, int l, const TC* S, int64_t lds, TC* Out,
-                        int64_t ldo, bool out_rowmajor, cudaStream_t st) {
+                        int64_t ldo, bool out_rowmajor, const int* defic, int pass, const int* skip_flag,
+                        cudaStream_t st) {
   // the CholeskyQR factor R^-1 is upper triangular
-  return lmul_dispatch<TC, TC>(In, ldi, len, l, S, lds, Out, ldo, out_rowmajor, true, st);
+  return lmul_dispatch<TC, TC>(In, ldi, len, l, S, lds, Out, ldo, out_rowmajor, true, defic, pass, skip_flag, st);
 }
 template <typename TC>
 cudaError_t launch_lmul_f64s(const TC* In, int64_t ldi, int64_t len, int l, const double* S, int64_t lds, TC* Out,
                              int64_t ldo, bool out_rowmajor, cudaStream_t st) {
-  return lmul_dispatch<TC, double>(In, ldi, len, l, S, lds, Out, ldo, out_rowmajor, false, st);
+  return lmul_dispatch<TC, double>(In, ldi, len, l, S, lds, Out, ldo, out_rowmajor, false, nullptr, 0, nullptr, st);
 }
 
-// =============================================================================== deficient columns
-// Replace row j of an ST block (column j of Q) flagged dependent by a
-// deterministic pseudo-random vector (SplitMix64 of (pass, j, i), uniform in
-// [-1, 1)); the next CholeskyQR pass orthonormalises it against the others.
-__device__ __forceinline__ uint64_t mix64(uint64_t z) {
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  return z ^ (z >> 31);
-}
-
-template <typename TC>
-__global__ void fill_deficient_kernel(TC* __restrict__ Ct, int64_t ldc, int64_t len, int l,
-                                      const int* __restrict__ defic, int pass) {
-  const int j = blockIdx.y;
-  if (j >= l || !defic[j]) return;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x) {
-    const uint64_t h = mix64(0x5EEDull + ((uint64_t)pass << 48) + ((uint64_t)j << 32) + (uint64_t)i * 0x9E3779B97F4A7C15ull);
-    const double u = (double)(h >> 11) * (1.0 / 9007199254740992.0);
-    Ct[j * ldc + i] = (TC)(2.0 * u - 1.0);
+// =============================================================================== R composition
+// C = A B for upper-triangular A, B (l x l, FP64, ld l): C[i][j] = sum_{k=i..j} A[i][k] B[k][j].
+__global__ void upper_mul_kernel(const double* __restrict__ A, const double* __restrict__ B,
+                                 double* __restrict__ C, int l) {
+  const int i = blockIdx.x;
+  for (int j = threadIdx.x; j < l; j += blockDim.x) {
+    double s = 0.0;
+    for (int k = i; k <= j; ++k) s = fma(A[i * l + k], B[k * l + j], s);
+    C[i * l + j] = s;
   }
 }
 
-template <typename TC>
-cudaError_t launch_fill_deficient(TC* Ct, int64_t ldc, int64_t len, int l, const int* defic, int pass,
-                                  cudaStream_t st) {
-  dim3 grid(32, l);
-  fill_deficient_kernel<TC><<<grid, 256, 0, st>>>(Ct, ldc, len, l, defic, pass); CORUTV_COUNT_LAUNCH();
+cudaError_t launch_upper_mul(const double* A, const double* B, double* C, int l, cudaStream_t st) {
+  upper_mul_kernel<<<l, 128, 0, st>>>(A, B, C, l);
+  CORUTV_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 
@@ -1353,12 +1254,11 @@ cudaError_t launch_fro2(int a_dtype, const void* A, int64_t lda, int64_t m, int6
   template cudaError_t launch_gram<TC>(const TC*, int64_t, const TC*, int64_t, int64_t, int, TC*, int, double*,   \
                                        int64_t, cudaStream_t);                                                     \
   template cudaError_t launch_cholinv<TC>(const double*, int64_t, int, double, double, TC*, TC*, int*, DevStatus*, \
-                                          double*, cudaStream_t);                                                  \
+                                          double*, int*, float, cudaStream_t);                                     \
   template cudaError_t launch_lmul<TC>(const TC*, int64_t, int64_t, int, const TC*, int64_t, TC*, int64_t, bool,  \
-                                       cudaStream_t);                                                              \
+                                       const int*, int, const int*, cudaStream_t);                                 \
   template cudaError_t launch_lmul_f64s<TC>(const TC*, int64_t, int64_t, int, const double*, int64_t, TC*,        \
                                             int64_t, bool, cudaStream_t);                                          \
-  template cudaError_t launch_fill_deficient<TC>(TC*, int64_t, int64_t, int, const int*, int, cudaStream_t);      \
   template cudaError_t launch_gather_cols<TC>(const TC*, int64_t, int64_t, int, const int32_t*, TC*, int64_t,     \
                                               cudaStream_t);                                                       \
   template cudaError_t launch_stage_transpose<TC>(const TC*, int64_t, int64_t, int, TC*, int64_t, cudaStream_t);  \

@@ -28,7 +28,9 @@ def test_every_declared_symbol_is_exported():
 
 
 def test_version_and_status_strings():
-    assert corutv.version() == 1
+    src = open(os.path.join(ROOT, "include", "corutv.h")).read()
+    declared = int(re.search(r"#define CORUTV_ABI_VERSION (\d+)", src).group(1))
+    assert corutv.version() == declared
     assert corutv.status_string(0) == "ok"
     assert "timed out" in corutv.status_string(6)
     assert corutv.status_string(999) == "unknown status"
@@ -68,7 +70,7 @@ def test_null_pointers_rejected():
 
 
 def test_reserved_fields_must_be_zero():
-    p = corutv._params(100, 80, 5, 10, 0, "right", "exact", 1, "auto", False)
+    p = corutv._params(100, 80, 5, 10, 0, "right", "exact", 1, "auto", False, "stabilised")
     p.reserved[3] = 1
     out = ctypes.c_size_t()
     assert corutv.load().corutv_workspace_size(ctypes.byref(p), ctypes.byref(out)) == corutv.ERR_INVALID_ARG

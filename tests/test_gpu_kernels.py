@@ -179,6 +179,22 @@ def test_orthonormalize_ill_conditioned(dt, cond, orth_tol):
     assert np.linalg.norm(res) / np.linalg.norm(C0) < (2e-5 if dt == torch.float32 else 1e-13)
 
 
+@pytest.mark.parametrize("dt,cond", [(torch.float64, 1e8), (torch.float32, 1e3), (torch.float32, 1.0)])
+def test_orthonormalize_returns_R(dt, cond):
+    """R_out is the product of the three CholeskyQR factors: C = Q R, R upper
+    triangular with a positive diagonal (cond 1: the FP32 third pass is skipped)."""
+    length, l = 5000, 40
+    Ct = _ill_conditioned(length, l, cond, 21)
+    buf = _st(Ct, length, dt)
+    R = corutv.orthonormalize(buf, length, l, want_R=True).cpu().numpy()
+    Q = buf[:, :length].double().cpu().numpy().T
+    C0 = torch.tensor(Ct, dtype=dt).double().numpy().T
+    assert np.abs(np.tril(R, -1)).max() == 0.0 and np.all(np.diag(R) > 0)
+    tol = 1e-13 if dt == torch.float64 else 2e-5
+    assert np.linalg.norm(C0 - Q @ R) / np.linalg.norm(C0) < tol
+    assert O.orthonormality_error(Q) < (1e-13 if dt == torch.float64 else 5e-6)
+
+
 @pytest.mark.parametrize("dt", [torch.float64, torch.float32])
 def test_orthonormalize_rank_deficient(dt):
     """A numerically rank-deficient block (rank 20 of 30) still yields an

@@ -28,13 +28,13 @@ if torch.cuda.is_available():
 TOL = {"f64": 1e-10, "simt": 1e-4, "tf32": 1e-3, "tf32t": 5e-3}
 
 
-def _run(A, phi, k, l, q, dt, mma="auto", side="right", core="exact", want_fro2=False):
+def _run(A, phi, k, l, q, dt, mma="auto", side="right", core="exact", want_fro2=False, orth="stabilised"):
     m, n = A.shape
     lda = -(-n // 8) * 8 + 8          # padded rows: a 16-byte pitch for TMA and lda > n
     Ad = torch.zeros((m, lda), dtype=dt, device="cuda")[:, :n]
     Ad.copy_(torch.tensor(A, dtype=torch.float64, device="cuda").to(dt))
     Pd = torch.tensor(phi, dtype=torch.float64, device="cuda").to(dt)
-    r = corutv.solve(Ad, Pd, k, l, q, side=side, core=core, mma=mma, want_fro2=want_fro2)
+    r = corutv.solve(Ad, Pd, k, l, q, side=side, core=core, mma=mma, want_fro2=want_fro2, orth=orth)
     assert r.info.status == 0, corutv.status_string(r.info.status)
     A64 = Ad.double().cpu().numpy()
     P64 = Pd.double().cpu().numpy()
@@ -78,6 +78,21 @@ def test_config1_fp64_parity(cfg1, q, core):
     e2 = O.fro_residual(A, U, T, V) ** 2
     assert abs((r.info.fro2_A - r.info.fro2_T) - e2) < 1e-10 * a2
     assert r.info.passes_over_A == 2 * q + (3 if core == "exact" else 2) + 1
+
+
+@pytest.mark.parametrize("orth", ["stabilised", "strict"])
+def test_orth_modes_same_factorisation(cfg1, orth):
+    """Both normalisations of the intermediate sketches give the oracle's
+    factorisation (the same Q1, Q2 in exact arithmetic), FP64 and FP32."""
+    r, A, phi = _run(cfg1.A, W.phi(1500, 30), 20, 30, 2, torch.float64, orth=orth)
+    U, T, V, perm = _np(r)
+    ref = O.corutv(A, phi, 20, 30, 2)
+    assert O.factor_distance(U, T, V, ref["U"], ref["T"], ref["V"]) < TOL["f64"]
+    r, A, phi = _run(cfg1.A, W.phi(1500, 30), 20, 30, 2, torch.float32, mma="simt", orth=orth)
+    U, T, V, perm = _np(r)
+    ref = O.corutv(A, phi, 20, 30, 2)
+    assert O.factor_distance(U, T, V, ref["U"], ref["T"], ref["V"]) < TOL["simt"]
+    _structure(U, T, V, perm, 30, orth_tol=5e-5)
 
 
 def test_config1_exact_rank_recovery():
