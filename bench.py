@@ -173,6 +173,17 @@ def traffic_from_profiles(key: str):
     return None
 
 
+def kernel_source_tag(*names):
+    """Short hash of the kernel sources a traffic figure was measured with: a
+    figure recorded for other sources is not used (the kernel has changed)."""
+    import hashlib
+    h = hashlib.sha1()
+    for nm in names:
+        with open(os.path.join(ROOT, "paper_1810_07323_gb300", "csrc", nm), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:10]
+
+
 def generator(w):
     from synth import workloads as W
     if w["gen"] == "config2":
@@ -335,10 +346,11 @@ def main():
     if lowp:
         kname = "pass_tc_lp_kernel (kind::f16, %s A, dir AX / ATY) incl. operand split and split-tile reduce" % (
             "BF16" if w["dtype"] == "bf16" else "FP8")
-        tkey = f"pass_tc_lp_kernel/{w['dtype']}/{m}x{n}/l{l}"
+        tkey = f"pass_tc_lp_kernel/{w['dtype']}/{m}x{n}/l{l}/src-" + kernel_source_tag("pass_tc_lp.cu",
+                                                                                       "tc_common.cuh")
     else:
         kname = "pass_tc_kernel (dir AX / ATY, TF32) incl. operand rounding and split-tile reduce"
-        tkey = f"pass_tc_kernel/f32/{m}x{n}/l{l}"
+        tkey = f"pass_tc_kernel/f32/{m}x{n}/l{l}/src-" + kernel_source_tag("pass_tc.cu", "tc_common.cuh")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_source": peak_src, "kernel": kname, "bytes_per_launch": bytes_per_pass,
                 "ms_per_launch": avg_pass_ms, "traffic": traffic_from_profiles(tkey)}
