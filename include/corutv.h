@@ -210,6 +210,61 @@ int corutv_solve_corrected(corutv_handle* h, const corutv_params* p,
 int corutv_quantize(corutv_handle* h, int dtype, const float* A, int64_t lda, int64_t m, int64_t n,
                     void* out, int64_t ldo, float* tile_scales);
 
+/* ------------------------------------------------------------------------
+ * Batched solves: many independent problems of different shapes in one call.
+ * ---------------------------------------------------------------------- */
+
+/* One problem of a batched solve: the fields of corutv_params and the pointer
+ * arguments of corutv_solve (same meaning, layouts and ownership). */
+typedef struct {
+  int64_t m, n;
+  int32_t k, l, q, side, core, orth;
+  int32_t a_dtype;       /* F32, BF16 or FP8_E4M3 (Psi, U, V are FP32; T FP64) */
+  int32_t mma;           /* AUTO or SIMT: the batched passes run on the CUDA cores */
+  int32_t want_fro2;
+  int32_t reserved0;     /* must be zero */
+  const void* A;
+  int64_t lda;
+  const float* a_tile_scales;
+  const void* Phi;
+  int64_t ldphi;
+  void* U;
+  int64_t ldu;
+  double* T;
+  int64_t ldt;
+  void* V;
+  int64_t ldv;
+  int32_t* perm;
+  int64_t reserved[4];   /* must be zero */
+} corutv_problem;
+
+/* Device workspace a batch needs (sketches, Gram partials and l x l factors of
+ * every problem, plus the grouped-launch tables). */
+int corutv_batch_workspace_size(int count, const corutv_problem* probs, size_t* bytes);
+
+/*
+ * corutv_solve_batched -- `count` independent CoR-UTV solves (Alg. 2 / Alg. 3,
+ * each with its own m, n, k, l, q, side, core, dtype and pointers; probs is a
+ * host array).  Every step of the schedule runs as one grouped launch over all
+ * problems (problems beyond their last power step skip the loop's launches),
+ * so the launch count does not grow with `count`.  The passes run on the CUDA
+ * cores with FP32 accumulation, one CTA per 64 output positions over the whole
+ * reduction (no split), the orthonormalisation and QRCP as in corutv_solve.
+ * Limits: l <= 128; a_dtype F64 and the tensor-core mma modes return
+ * ERR_UNSUPPORTED.  The handle keeps a workspace and the tables of the last
+ * problem set; calling again with an identical problem array (same shapes,
+ * pointers and parameters) replays a CUDA graph of the whole batch (not on the
+ * legacy default stream).  Validation errors return synchronously and enqueue
+ * nothing.  infos: NULL (the call returns once the work is enqueued; read the
+ * outcome with corutv_batch_info_wait) or a host array of `count` entries (the
+ * call waits for the batch and fills it).
+ */
+int corutv_solve_batched(corutv_handle* h, int count, const corutv_problem* probs, corutv_info* infos);
+
+/* Synchronise the handle's stream and return the outcome of each problem of the
+ * last batch (count must equal that batch's count). */
+int corutv_batch_info_wait(corutv_handle* h, int count, corutv_info* infos);
+
 /* Synchronise the handle's stream and return the outcome of the last solve. */
 int corutv_info_wait(corutv_handle* h, corutv_info* out);
 

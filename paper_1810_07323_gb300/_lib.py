@@ -40,6 +40,18 @@ class Params(ctypes.Structure):
                 ("want_fro2", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
 
 
+class Problem(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("k", ctypes.c_int32), ("l", ctypes.c_int32),
+                ("q", ctypes.c_int32), ("side", ctypes.c_int32), ("core", ctypes.c_int32),
+                ("orth", ctypes.c_int32), ("a_dtype", ctypes.c_int32), ("mma", ctypes.c_int32),
+                ("want_fro2", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("A", ctypes.c_void_p), ("lda", ctypes.c_int64), ("a_tile_scales", ctypes.c_void_p),
+                ("Phi", ctypes.c_void_p), ("ldphi", ctypes.c_int64), ("U", ctypes.c_void_p),
+                ("ldu", ctypes.c_int64), ("T", ctypes.c_void_p), ("ldt", ctypes.c_int64),
+                ("V", ctypes.c_void_p), ("ldv", ctypes.c_int64), ("perm", ctypes.c_void_p),
+                ("reserved", ctypes.c_int64 * 4)]
+
+
 class Info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("passes_over_A", ctypes.c_int32),
                 ("chol_fallbacks", ctypes.c_int32), ("reserved0", ctypes.c_int32),
@@ -64,7 +76,8 @@ _lib = None
 EXPORTS = ("corutv_version", "corutv_status_string", "corutv_create", "corutv_destroy", "corutv_set_stream",
            "corutv_workspace_size", "corutv_set_workspace", "corutv_solve", "corutv_info_wait",
            "corutv_set_tracing", "corutv_trace_read", "corutv_pass", "corutv_orthonormalize", "corutv_gram",
-           "corutv_qrcp", "corutv_fro2", "corutv_gram_noalloc", "corutv_solve_corrected", "corutv_quantize")
+           "corutv_qrcp", "corutv_fro2", "corutv_gram_noalloc", "corutv_solve_corrected", "corutv_quantize",
+           "corutv_batch_workspace_size", "corutv_solve_batched", "corutv_batch_info_wait")
 
 
 def load() -> ctypes.CDLL:
@@ -88,6 +101,9 @@ def load() -> ctypes.CDLL:
     lib.corutv_solve_corrected.argtypes = [P, ctypes.POINTER(Params), P, I64, P, P, I64, P, I64, P, I64, P, I64,
                                            P, I64, P]
     lib.corutv_quantize.argtypes = [P, ctypes.c_int, P, I64, I64, I64, P, I64, P]
+    lib.corutv_batch_workspace_size.argtypes = [ctypes.c_int, ctypes.POINTER(Problem), ctypes.POINTER(ctypes.c_size_t)]
+    lib.corutv_solve_batched.argtypes = [P, ctypes.c_int, ctypes.POINTER(Problem), ctypes.POINTER(Info)]
+    lib.corutv_batch_info_wait.argtypes = [P, ctypes.c_int, ctypes.POINTER(Info)]
     lib.corutv_info_wait.argtypes = [P, ctypes.POINTER(Info)]
     lib.corutv_pass.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, I64, I64, I64, P, P, I64, I32, P,
                                 I64]
@@ -102,7 +118,8 @@ def load() -> ctypes.CDLL:
     for name in ("corutv_set_tracing", "corutv_trace_read", "corutv_create", "corutv_destroy", "corutv_set_stream", "corutv_workspace_size",
                  "corutv_set_workspace", "corutv_solve", "corutv_info_wait", "corutv_pass",
                  "corutv_orthonormalize", "corutv_gram", "corutv_qrcp", "corutv_fro2", "corutv_solve_corrected",
-                 "corutv_quantize"):
+                 "corutv_quantize", "corutv_batch_workspace_size", "corutv_solve_batched",
+                 "corutv_batch_info_wait"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -306,6 +323,73 @@ def quantize(A, dtype: str, out=None, tile_scales=None, handle: Handle | None = 
                                 ctypes.c_void_p(out.data_ptr()), _rowmajor_ld(out), ctypes.c_void_p(sc))
     _check(rc, "corutv_quantize")
     return (out, tile_scales) if code == 3 else (out, None)
+
+
+class Batch:
+    """A fixed set of problems for corutv_solve_batched.
+
+    items: list of dicts with keys A (device float32 / bfloat16 / float8_e4m3fn,
+    one dtype for the batch), Phi (float32, n x l for side "right", m x l for
+    "left"), k, l and optionally q, side, core, orth, want_fro2, a_tile_scales.
+    The outputs (U, T, V, perm per problem) are allocated once, so running the
+    same Batch again passes an identical problem array and the library replays
+    its CUDA graph of the batch."""
+
+    def __init__(self, items, handle: Handle | None = None):
+        import torch
+        self.handle = handle or handle_for()
+        self.items = list(items)
+        self.count = len(self.items)
+        self.arr = (Problem * self.count)()
+        self.results = []
+        for i, it in enumerate(self.items):
+            A, Phi = it["A"], it["Phi"]
+            _need_cuda(A, Phi, it.get("a_tile_scales"))
+            m, n = A.shape
+            l = int(it["l"])
+            if Phi.dtype != torch.float32:
+                raise TypeError("Phi must be float32")
+            U = torch.empty((m, l), dtype=torch.float32, device=A.device)
+            T = torch.empty((l, l), dtype=torch.float64, device=A.device)
+            V = torch.empty((n, l), dtype=torch.float32, device=A.device)
+            perm = torch.empty((l,), dtype=torch.int32, device=A.device)
+            p = self.arr[i]
+            p.m, p.n, p.k, p.l, p.q = m, n, int(it["k"]), l, int(it.get("q", 0))
+            p.side = SIDE[it.get("side", "right")]
+            p.core = CORE[it.get("core", "exact")]
+            p.orth = ORTH[it.get("orth", "stabilised")]
+            p.a_dtype = _dt_code(A)
+            p.mma = MMA[it.get("mma", "auto")]
+            p.want_fro2 = 1 if it.get("want_fro2", False) else 0
+            sc = it.get("a_tile_scales")
+            p.A, p.lda = A.data_ptr(), _rowmajor_ld(A)
+            p.a_tile_scales = sc.data_ptr() if sc is not None else None
+            p.Phi, p.ldphi = Phi.data_ptr(), _rowmajor_ld(Phi)
+            p.U, p.ldu = U.data_ptr(), _rowmajor_ld(U)
+            p.T, p.ldt = T.data_ptr(), _rowmajor_ld(T)
+            p.V, p.ldv = V.data_ptr(), _rowmajor_ld(V)
+            p.perm = perm.data_ptr()
+            self.results.append(SolveResult(U, T, V, perm, None))
+
+    def workspace_size(self) -> int:
+        out = ctypes.c_size_t()
+        _check(load().corutv_batch_workspace_size(self.count, self.arr, ctypes.byref(out)),
+               "corutv_batch_workspace_size")
+        return out.value
+
+    def run(self, wait: bool = True):
+        """Enqueue the batch; with wait=True synchronise and attach each problem's info."""
+        _check(load().corutv_solve_batched(self.handle.h, self.count, self.arr, None), "corutv_solve_batched")
+        if wait:
+            return self.wait()
+        return None
+
+    def wait(self):
+        infos = (Info * self.count)()
+        _check(load().corutv_batch_info_wait(self.handle.h, self.count, infos), "corutv_batch_info_wait")
+        for r, inf in zip(self.results, infos):
+            r.info = inf
+        return self.results
 
 
 def info_wait(h: Handle | None = None) -> Info:

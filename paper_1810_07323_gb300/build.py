@@ -20,7 +20,8 @@ LIB = os.path.join(PKG, "libcorutv.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I" + CSRC, "-I" + os.path.join(ROOT, "include")]
-UNITS = ["corutv_abi.cu", "pass_simt.cu", "pass_tc.cu", "pass_tc_lp.cu", "quant.cu", "small.cu", "noalloc.cu"]
+UNITS = ["corutv_abi.cu", "batched.cu", "pass_simt.cu", "pass_tc.cu", "pass_tc_lp.cu", "quant.cu", "small.cu",
+         "noalloc.cu"]
 
 
 def _nvcc() -> str:
@@ -63,7 +64,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
         list(ex.map(run, jobs))
     if jobs or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
         tmp = LIB + ".tmp"
-        run([nvcc, *ARCH, "-shared", "-o", tmp, *objs])
+        run([nvcc, *ARCH, "-shared", "-Xlinker", "--no-undefined", "-o", tmp, *objs])
         os.replace(tmp, LIB)
     return LIB
 

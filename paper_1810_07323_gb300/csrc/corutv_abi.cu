@@ -13,6 +13,7 @@
 #include "../../include/corutv.h"
 #include "common.cuh"
 #include "internal.h"
+#include "handle.h"
 
 using namespace corutv;
 
@@ -23,46 +24,11 @@ int64_t& launch_counter() {
 }
 }  // namespace corutv
 
-enum Phase { kPhPass = 0, kPhOrth, kPhCore, kPhQrcp, kPhAsm, kPhFro2, kPhCorr, kPhQuant, kNumPh };
-
-struct TraceRec {
-  int phase;
-  cudaEvent_t a, b;
-  double bytes;
-};
-
-struct corutv_handle {
-  cudaStream_t stream = nullptr;
-  bool tracing = false;
-  std::vector<cudaEvent_t> ev_pool;
-  std::vector<TraceRec> recs;
-  corutv_trace acc{};
-  int64_t launches = 0;
-  int device = 0;
-  int sms = 0;
-  void* ws = nullptr;          // workspace base (owned if own_ws)
-  size_t ws_bytes = 0;
-  bool own_ws = false;
-  DevStatus* status = nullptr; // inside the workspace
-  corutv_params last{};
-  int last_passes = 0;
-  double last_shift = 0.0;
-  bool have_last = false;
-};
-
 namespace {
 
 // ---------------------------------------------------------------- sizes
-constexpr double kShiftRel32 = 1e-5;    // first CholeskyQR pass, FP32 arithmetic
-constexpr double kShiftRel64 = 1e-12;   // first CholeskyQR pass, FP64 arithmetic
-constexpr double kTolRel32 = 1e-7;      // dependent-column threshold, FP32
-constexpr double kTolRel64 = 1e-14;     // dependent-column threshold, FP64
-// Skip the third FP32 CholeskyQR pass when max |Q^T Q - I| after the second is at most
-// this: a further FP32 pass reaches ~c u32 l (1e-6 .. 1e-5 for l <= 128) and gains nothing
-constexpr float kSkipTol32 = 2e-6f;
 constexpr int64_t kAlign = 256;
 
-inline int64_t ld_for(int64_t len) { return round_up(len < 1 ? 1 : len, 64); }
 inline int elem_bytes(int dt) { return dt == CORUTV_F64 ? 8 : (dt == CORUTV_F32 ? 4 : (dt == CORUTV_BF16 ? 2 : 1)); }
 inline int tc_bytes(int dt) { return dt == CORUTV_F64 ? 8 : 4; }   // sketch / compute precision
 inline bool aligned16(const void* ptr) { return ((uintptr_t)ptr & 15u) == 0; }
@@ -508,6 +474,7 @@ int corutv_destroy(corutv_handle* h) {
     cudaEventDestroy(r.b);
   }
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+  batch_state_free(h->batch);
   delete h;
   return CORUTV_OK;
 }

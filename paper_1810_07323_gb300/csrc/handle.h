@@ -1,0 +1,42 @@
+// The handle behind corutv_handle* (shared by the C-ABI translation units).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "../../include/corutv.h"
+#include "common.cuh"
+
+namespace corutv {
+struct BatchState;                  // batched-solve plan, workspace and graph cache (batched.cu)
+void batch_state_free(BatchState* b);
+}  // namespace corutv
+
+enum Phase { kPhPass = 0, kPhOrth, kPhCore, kPhQrcp, kPhAsm, kPhFro2, kPhCorr, kPhQuant, kNumPh };
+
+struct TraceRec {
+  int phase;
+  cudaEvent_t a, b;
+  double bytes;
+};
+
+struct corutv_handle {
+  cudaStream_t stream = nullptr;
+  bool tracing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<TraceRec> recs;
+  corutv_trace acc{};
+  int64_t launches = 0;
+  int device = 0;
+  int sms = 0;
+  void* ws = nullptr;          // workspace base (owned if own_ws)
+  size_t ws_bytes = 0;
+  bool own_ws = false;
+  corutv::DevStatus* status = nullptr; // inside the workspace
+  corutv_params last{};
+  int last_passes = 0;
+  double last_shift = 0.0;
+  bool have_last = false;
+  corutv::BatchState* batch = nullptr;
+};
+

@@ -8,6 +8,18 @@
 
 namespace corutv {
 
+// ---------------------------------------------------------------- CholeskyQR constants
+constexpr double kShiftRel32 = 1e-5;    // first CholeskyQR pass, FP32 arithmetic (relative to trace(G))
+constexpr double kShiftRel64 = 1e-12;   // first CholeskyQR pass, FP64 arithmetic
+constexpr double kTolRel32 = 1e-7;      // dependent-column threshold, FP32
+constexpr double kTolRel64 = 1e-14;     // dependent-column threshold, FP64
+// Skip the third FP32 CholeskyQR pass when max |Q^T Q - I| after the second is at most
+// this: a further FP32 pass reaches ~c u32 l (1e-6 .. 1e-5 for l <= 128) and gains nothing
+constexpr float kSkipTol32 = 2e-6f;
+
+// leading dimension of skinny-transposed workspace buffers of length len
+inline int64_t ld_for(int64_t len) { return round_up(len < 1 ? 1 : len, 64); }
+
 // Kernels launched by this host thread (read around a solve for its launch count).
 int64_t& launch_counter();
 #define CORUTV_COUNT_LAUNCH() (++::corutv::launch_counter())
@@ -94,5 +106,63 @@ cudaError_t launch_qrcp(const double* D, int64_t ldd, int l, int k, double* Q, i
 cudaError_t launch_fro2(int a_dtype, const void* A, int64_t lda, int64_t m, int64_t n, const float* scales,
                         int64_t sld, double* parts, int nparts, double* out, cudaStream_t st);
 int fro2_parts(int sms);
+
+// ------------------------------------------------------------------ batched solves
+// One problem of a batched solve as the grouped kernels see it (an array of these
+// lives in device memory).  RIGHT: C1 = A X (dir1 = AX, len1 = m), C2 = A^T Q1
+// (len2 = n); LEFT: the same on A^T.  l x l blocks are packed (ld l).
+struct BatchProb {
+  const void* A;
+  int64_t lda;
+  const float* scales;
+  int64_t sld;
+  const float* Phi;
+  int64_t ldphi;
+  float* U;
+  int64_t ldu;
+  double* T;
+  int64_t ldt;
+  float* V;
+  int64_t ldv;
+  int32_t* perm;
+  int64_t m, n, len1, len2;
+  int l, k, q, side, core, orth, want_fro2, dir1, dir2;
+  float *P1, *P2, *P3;
+  int64_t ld1, ld2, ld3;
+  float* gparts;        // Gram partial blocks (LP x LP each)
+  int gp1, gp2;         // partial blocks for sketches of length len1 / len2
+  double *G, *D, *Qt;
+  float *R, *Rinv;
+  int* defic;
+  double* fparts;       // ||A||^2 partials, one per tile of the first pass
+  int nfparts;
+  DevStatus* status;
+};
+
+// Block -> (problem, local block) maps drive every grouped launch.
+enum BatchSketch : int { kB_C1 = 0, kB_C2 = 1, kB_CORE = 2 };          // pass outputs
+enum BatchGram : int { kG_ORTH1 = 0, kG_ORTH2 = 1, kG_CORE_EXACT = 2, kG_CORE_SKETCH = 3 };
+
+// batched SIMT pass (pass_simt.cu): one CTA per 64 output positions, full K, no split
+constexpr int kBatchPassBN = 64;
+cudaError_t launch_pass_simt_grouped(const BatchProb* P, const int2* map, int nblocks, int lp, int a_dtype,
+                                     int which, int it, cudaStream_t st);
+// grouped small kernels (small.cu)
+constexpr int kBatchGramCols = 512;   // columns per Gram partial block
+constexpr int kBatchLmulBI = 128;     // columns per lmul tile
+constexpr int kBatchTile32 = 32;      // columns per stage / gather / copy tile
+cudaError_t launch_stage_grouped(const BatchProb* P, const int2* map32_2, int nblocks, cudaStream_t st);
+cudaError_t launch_gram_grouped(const BatchProb* P, const int2* map_parts, int nparts, const int2* map_red,
+                                int nred, int lp, int which, int it, int pass, cudaStream_t st);
+cudaError_t launch_cholinv_grouped(const BatchProb* P, int count, int lmax, int which, int it, int pass,
+                                   float skip_tol, double shift_rel, double tol_rel, cudaStream_t st);
+cudaError_t launch_lmul_orth_grouped(const BatchProb* P, const int2* map, int nblocks, int lp, int which, int it,
+                                     int pass, cudaStream_t st);
+cudaError_t launch_copy_sketch_grouped(const BatchProb* P, const int2* map32_2, int nblocks, int it,
+                                       cudaStream_t st);
+cudaError_t launch_qrcp_grouped(const BatchProb* P, int count, cudaStream_t st);
+cudaError_t launch_assemble_grouped(const BatchProb* P, const int2* map_lmul1, int n1, const int2* map32_2, int n2,
+                                    int lp, cudaStream_t st);
+cudaError_t launch_fro2_grouped(const BatchProb* P, int count, cudaStream_t st);
 
 }  // namespace corutv

@@ -107,7 +107,125 @@ __global__ void __launch_bounds__(256) pass_simt_kernel(PassArgs args) {
   }
 }
 
+// Batched pass: block b computes the kBN output positions map[b].y of problem
+// map[b].x over its whole K (no split, so no partials), direction and sizes
+// from the problem's descriptor.  `which` picks the product (C1 = op1(A) X from
+// P2 into P1, C2 = op2(A) Q1 from P1 into P2, or the core pass E from P2 into
+// P3); problems past their last power step (or without an exact core) exit.
+// The C1 pass of step 0 also folds sum(a^2) of the A slab it reads into
+// fparts (one FP64 partial per block, summed per problem in order later).
+template <typename TA, int JPT>
+__global__ void __launch_bounds__(256) pass_simt_grouped_kernel(const BatchProb* __restrict__ probs,
+                                                                const int2* __restrict__ map, int which, int it) {
+  using TC = typename Elem<TA>::acc;
+  constexpr int LP = 16 * JPT;
+  __shared__ TC As[kBN][kBK + 1];
+  __shared__ TC Xs[LP][kBK + 1];
+  __shared__ double fred[8];
+  const int2 pm = map[blockIdx.x];
+  const BatchProb& P = probs[pm.x];
+  if (which == kB_CORE ? P.core != 0 : it > P.q) return;
+  const int dir = which == kB_C2 ? P.dir2 : P.dir1;
+  const TC* Xt = which == kB_C2 ? P.P1 : P.P2;
+  const int64_t ldx = which == kB_C2 ? P.ld1 : P.ld2;
+  TC* Ct = which == kB_C1 ? P.P1 : (which == kB_C2 ? P.P2 : P.P3);
+  const int64_t ldc = which == kB_C1 ? P.ld1 : (which == kB_C2 ? P.ld2 : P.ld3);
+  const int64_t len = which == kB_C2 ? P.len2 : P.len1, K = which == kB_C2 ? P.len1 : P.len2;
+  const bool fro = which == kB_C1 && it == 0 && P.want_fro2;
+  const TA* A = static_cast<const TA*>(P.A);
+  const int l = P.l;
+  const int tid = threadIdx.x, ti = tid & 15, tj = tid >> 4;
+  const int64_t i0 = (int64_t)pm.y * kBN;
+  TC acc[JPT][4];
+#pragma unroll
+  for (int v = 0; v < JPT; ++v)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc[v][u] = TC(0);
+  float fsum = 0.f;
+  double fro_acc = 0.0;
+  for (int64_t k0 = 0; k0 < K; k0 += kBK) {
+    for (int x = tid; x < kBN * kBK; x += 256) {
+      int ii, kk;
+      if (dir == 0) { ii = x / kBK; kk = x % kBK; }   // coalesced along k (A rows)
+      else          { kk = x / kBN; ii = x % kBN; }   // coalesced along i (A columns)
+      const int64_t gi = i0 + ii, gk = k0 + kk;
+      TC val = TC(0);
+      if (gi < len && gk < K)
+        val = (dir == 0) ? Elem<TA>::load(A, gi, gk, P.lda, P.scales, P.sld)
+                         : Elem<TA>::load(A, gk, gi, P.lda, P.scales, P.sld);
+      As[ii][kk] = val;
+      if (fro) fsum = fmaf((float)val, (float)val, fsum);
+    }
+    for (int x = tid; x < LP * kBK; x += 256) {
+      const int jj = x / kBK, kk = x % kBK;
+      const int64_t gk = k0 + kk;
+      Xs[jj][kk] = (jj < l && gk < K) ? Xt[jj * ldx + gk] : TC(0);
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < kBK; ++kk) {
+      TC a[4], xv[JPT];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) a[u] = As[ti + 16 * u][kk];
+#pragma unroll
+      for (int v = 0; v < JPT; ++v) xv[v] = Xs[tj + 16 * v][kk];
+#pragma unroll
+      for (int v = 0; v < JPT; ++v)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[v][u] = fma(xv[v], a[u], acc[v][u]);
+    }
+    __syncthreads();
+    if (fro) {           // fold the FP32 squares of this stage into FP64
+      fro_acc += (double)fsum;
+      fsum = 0.f;
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < JPT; ++v) {
+    const int j = tj + 16 * v;
+    if (j >= l) continue;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t gi = i0 + ti + 16 * u;
+      if (gi < len) Ct[j * ldc + gi] = acc[v][u];
+    }
+  }
+  if (fro) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) fro_acc += __shfl_xor_sync(0xffffffffu, fro_acc, o);
+    if ((tid & 31) == 0) fred[tid >> 5] = fro_acc;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int w = 0; w < 8; ++w) t += fred[w];
+      P.fparts[pm.y] = t;
+    }
+  }
+}
+
+template <typename TA>
+cudaError_t launch_grouped_dt(const BatchProb* P, const int2* map, int nblocks, int lp, int which, int it,
+                              cudaStream_t st) {
+  if (lp <= 32) pass_simt_grouped_kernel<TA, 2><<<nblocks, 256, 0, st>>>(P, map, which, it);
+  else if (lp <= 64) pass_simt_grouped_kernel<TA, 4><<<nblocks, 256, 0, st>>>(P, map, which, it);
+  else pass_simt_grouped_kernel<TA, 8><<<nblocks, 256, 0, st>>>(P, map, which, it);
+  CORUTV_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t launch_pass_simt_grouped(const BatchProb* P, const int2* map, int nblocks, int lp, int a_dtype,
+                                     int which, int it, cudaStream_t st) {
+  static_assert(kBN == kBatchPassBN, "batched pass tile");
+  if (nblocks <= 0) return cudaSuccess;
+  switch (a_dtype) {
+    case 1: return launch_grouped_dt<float>(P, map, nblocks, lp, which, it, st);
+    case 2: return launch_grouped_dt<__nv_bfloat16>(P, map, nblocks, lp, which, it, st);
+    case 3: return launch_grouped_dt<__nv_fp8_e4m3>(P, map, nblocks, lp, which, it, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
 
 // Ordered sum of Stream-K partial tiles: tile t (BN output positions, LP rows)
 // split across workers cf..cl is the sum of their slots in worker order.

@@ -24,9 +24,9 @@ constexpr int kQrcpTPC = 4;   // threads per column of the register QRCP (512 th
 // are kept k-major in shared memory (rows padded by 4); the next stage's
 // global loads are issued into registers before the current stage is used.
 template <typename TC, int LP>
-__global__ void __launch_bounds__(512) gram_partial_kernel(const TC* __restrict__ Xt, int64_t ldx,
-                                                           const TC* __restrict__ Yt, int64_t ldy, int64_t len,
-                                                           int l, TC* __restrict__ parts) {
+__device__ __forceinline__ void gram_partial_body(const TC* __restrict__ Xt, int64_t ldx, const TC* __restrict__ Yt,
+                                                  int64_t ldy, int64_t len, int l, TC* __restrict__ parts, int cta,
+                                                  int ncta) {
   constexpr int R = LP / 16, CC = LP / 32;
   constexpr int BK = 32;
   constexpr int LPP = LP + 4;
@@ -34,8 +34,8 @@ __global__ void __launch_bounds__(512) gram_partial_kernel(const TC* __restrict_
   __shared__ __align__(16) TC Xs[BK][LPP];
   __shared__ __align__(16) TC Ys[BK][LPP];
   const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
-  const int64_t chunk = cdiv(cdiv(len, BK), gridDim.x) * BK;
-  const int64_t c0 = blockIdx.x * chunk;
+  const int64_t chunk = cdiv(cdiv(len, BK), ncta) * BK;
+  const int64_t c0 = cta * chunk;
   int64_t c1 = c0 + chunk;
   if (c1 > len) c1 = len;
   TC acc[R][CC];
@@ -80,19 +80,26 @@ __global__ void __launch_bounds__(512) gram_partial_kernel(const TC* __restrict_
     }
     __syncthreads();
   }
-  TC* out = parts + (int64_t)blockIdx.x * LP * LP;
+  TC* out = parts + (int64_t)cta * LP * LP;
 #pragma unroll
   for (int v = 0; v < R; ++v)
 #pragma unroll
     for (int u = 0; u < CC; ++u) out[(R * ty + v) * LP + CC * tx + u] = acc[v][u];
 }
 
+template <typename TC, int LP>
+__global__ void __launch_bounds__(512) gram_partial_kernel(const TC* __restrict__ Xt, int64_t ldx,
+                                                           const TC* __restrict__ Yt, int64_t ldy, int64_t len,
+                                                           int l, TC* __restrict__ parts) {
+  gram_partial_body<TC, LP>(Xt, ldx, Yt, ldy, len, l, parts, blockIdx.x, gridDim.x);
+}
+
 // G[a][b] = sum over parts in a fixed order, in FP64: four threads per element
 // each sum every fourth part, then (s0 + s1) + (s2 + s3).
 template <typename TC>
-__global__ void gram_reduce_kernel(const TC* __restrict__ parts, int nparts, int LP, int l, double* __restrict__ G,
-                                   int64_t ldg) {
-  const int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 2;
+__device__ __forceinline__ void gram_reduce_body(const TC* __restrict__ parts, int nparts, int LP, int l,
+                                                 double* __restrict__ G, int64_t ldg, int gtid) {
+  const int e = gtid >> 2;
   const int q = threadIdx.x & 3;
   const bool ok = e < l * l;
   const int a = ok ? e / l : 0, b = ok ? e % l : 0;
@@ -112,6 +119,12 @@ __global__ void gram_reduce_kernel(const TC* __restrict__ parts, int nparts, int
   const double t = (q & 1) ? s1 + s : s + s1;                 // (s0 + s1), (s2 + s3)
   const double t2 = __shfl_xor_sync(0xffffffffu, t, 2);
   if (ok && q == 0) G[a * ldg + b] = t + t2;
+}
+
+template <typename TC>
+__global__ void gram_reduce_kernel(const TC* __restrict__ parts, int nparts, int LP, int l, double* __restrict__ G,
+                                   int64_t ldg) {
+  gram_reduce_body<TC>(parts, nparts, LP, l, G, ldg, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 int gram_parts(int64_t len, int sms) {
@@ -239,10 +252,11 @@ constexpr int kPipeMaxThreads = (kMaxL / 4) * (kMaxL / 4 + 1) / 2 + 16;   // 528
 // block; at or below skip_tol it writes 1 to *skip_flag, R_out = I (if asked)
 // and returns (the caller's Q already has orthonormal columns to that level),
 // otherwise it writes 0 and factors as usual.
-__global__ void __launch_bounds__(kPipeMaxThreads, 1) cholinv_pipe_kernel(
-    const double* __restrict__ G, int64_t ldg, int l, double shift_rel, double tol_rel, float* __restrict__ Rg,
-    float* __restrict__ Rinvg, int* __restrict__ defic, DevStatus* status, double* __restrict__ Rout,
-    int* __restrict__ skip_flag, float skip_tol) {
+__device__ __forceinline__ void cholinv_pipe_body(const double* __restrict__ G, int64_t ldg, int l, double shift_rel,
+                                                  double tol_rel, float* __restrict__ Rg, float* __restrict__ Rinvg,
+                                                  int64_t ldr, int* __restrict__ defic, DevStatus* status,
+                                                  double* __restrict__ Rout, int* __restrict__ skip_flag,
+                                                  float skip_tol) {
   __shared__ __align__(16) float rowbuf[2][kMaxL];
   __shared__ __align__(16) float libuf[2][kMaxL];
   __shared__ float diag0[kMaxL];
@@ -374,12 +388,12 @@ __global__ void __launch_bounds__(kPipeMaxThreads, 1) cholinv_pipe_kernel(
         if (b == a) rv = sqrtf(piv[a]);
         else if (b > a && !dep_s[a]) rv = g[r][c] / sqrtf(piv[a]);
         if (b >= a) xv = li[c][r] / sqrtf(piv[b]);
-        Rg[a * kMaxL + b] = rv;
-        Rinvg[a * kMaxL + b] = xv;
+        Rg[a * ldr + b] = rv;
+        Rinvg[a * ldr + b] = xv;
         if (Rout) Rout[a * l + b] = (double)rv;
         if (b > a) {            // the mirrored lower entries
-          Rg[b * kMaxL + a] = 0.f;
-          Rinvg[b * kMaxL + a] = 0.f;
+          Rg[b * ldr + a] = 0.f;
+          Rinvg[b * ldr + a] = 0.f;
           if (Rout) Rout[b * l + a] = 0.0;
         }
       }
@@ -391,6 +405,13 @@ __global__ void __launch_bounds__(kPipeMaxThreads, 1) cholinv_pipe_kernel(
   }
   for (int o = 16; o > 0; o >>= 1) nfall += __shfl_xor_sync(0xffffffffu, nfall, o);
   if (lane == 0 && nfall && status) atomicAdd(&status->chol_fallbacks, nfall);
+}
+
+__global__ void __launch_bounds__(kPipeMaxThreads, 1) cholinv_pipe_kernel(
+    const double* __restrict__ G, int64_t ldg, int l, double shift_rel, double tol_rel, float* __restrict__ Rg,
+    float* __restrict__ Rinvg, int* __restrict__ defic, DevStatus* status, double* __restrict__ Rout,
+    int* __restrict__ skip_flag, float skip_tol) {
+  cholinv_pipe_body(G, ldg, l, shift_rel, tol_rel, Rg, Rinvg, kMaxL, defic, status, Rout, skip_flag, skip_tol);
 }
 
 template <typename TC>
@@ -441,12 +462,10 @@ __device__ __forceinline__ double replacement_value(int pass, int j, int64_t i) 
 // out_rowmajor: write Out^T into a row-major len x l matrix (staged through
 // shared memory so the row writes coalesce).
 template <typename TC, typename TS, int LP, int BI>
-__global__ void __launch_bounds__(256, 1) lmul_kernel(const TC* __restrict__ In, int64_t ldi, int64_t len, int l,
-                                                      const TS* __restrict__ S, int64_t lds, TC* __restrict__ Out,
-                                                      int64_t ldo, int out_rowmajor, int upper,
-                                                      const int* __restrict__ defic, int pass,
-                                                      const int* __restrict__ skip_flag) {
-  if (skip_flag && *skip_flag) return;     // the factor was found to be the identity
+__device__ __forceinline__ void lmul_body(const TC* __restrict__ In, int64_t ldi, int64_t len, int l,
+                                          const TS* __restrict__ S, int64_t lds, TC* __restrict__ Out, int64_t ldo,
+                                          int out_rowmajor, int upper, const int* __restrict__ defic, int pass,
+                                          int bx) {
   constexpr int R = LP / 16, RI = BI / 16;
   constexpr int SP = LP + 4, IP = BI + 4;
   constexpr bool kVecIn = sizeof(TC) == 4;
@@ -455,23 +474,25 @@ __global__ void __launch_bounds__(256, 1) lmul_kernel(const TC* __restrict__ In,
   TC* Ss = reinterpret_cast<TC*>(smem_raw);      // LP x SP   (row p, column j)
   TC* Is = Ss + LP * SP;                         // LP x IP   (row p, column i)
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  const int64_t i0 = (int64_t)blockIdx.x * BI;
+  const int64_t i0 = (int64_t)bx * BI;
   // (S rows p >= l and columns j >= l are zero: the p loop below can stop at l)
   if constexpr (kVecS) {
     constexpr int N4 = LP * LP / 4 / 256;
     float4 v[N4];
+    const bool s_vec = (lds & 3) == 0 && ((uintptr_t)S & 15) == 0;
 #pragma unroll
     for (int q = 0; q < N4; ++q) {
       const int e = tid + 256 * q, p = e / (LP / 4), j = 4 * (e % (LP / 4));
       float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
       if (p < l) {
         const TS* src = S + p * lds + j;
-        if (j + 3 < l && (lds & 3) == 0) {
+        if (j + 3 < l && s_vec) {
           t = *reinterpret_cast<const float4*>(src);
         } else {
           if (j < l) t.x = src[0];
           if (j + 1 < l) t.y = src[1];
           if (j + 2 < l) t.z = src[2];
+          if (j + 3 < l) t.w = src[3];
         }
       }
       v[q] = t;
@@ -574,6 +595,16 @@ __global__ void __launch_bounds__(256, 1) lmul_kernel(const TC* __restrict__ In,
 }
 
 template <typename TC, typename TS, int LP, int BI>
+__global__ void __launch_bounds__(256, 1) lmul_kernel(const TC* __restrict__ In, int64_t ldi, int64_t len, int l,
+                                                      const TS* __restrict__ S, int64_t lds, TC* __restrict__ Out,
+                                                      int64_t ldo, int out_rowmajor, int upper,
+                                                      const int* __restrict__ defic, int pass,
+                                                      const int* __restrict__ skip_flag) {
+  if (skip_flag && *skip_flag) return;     // the factor was found to be the identity
+  lmul_body<TC, TS, LP, BI>(In, ldi, len, l, S, lds, Out, ldo, out_rowmajor, upper, defic, pass, blockIdx.x);
+}
+
+template <typename TC, typename TS, int LP, int BI>
 static cudaError_t lmul_variant(const TC* In, int64_t ldi, int64_t len, int l, const TS* S, int64_t lds, TC* Out,
                                 int64_t ldo, bool rowmajor, bool upper, const int* defic, int pass,
                                 const int* skip_flag, cudaStream_t st) {
@@ -638,11 +669,12 @@ cudaError_t launch_upper_mul(const double* A, const double* B, double* C, int l,
 // =============================================================================== gather / stage
 // Out[i][j] = St[perm[j]][i]  (row-major len x l output from an ST block).
 template <typename TC>
-__global__ void gather_cols_kernel(const TC* __restrict__ St, int64_t lds, int64_t len, int l,
-                                   const int32_t* __restrict__ perm, TC* __restrict__ Out, int64_t ldo) {
+__device__ __forceinline__ void gather_cols_body(const TC* __restrict__ St, int64_t lds, int64_t len, int l,
+                                                 const int32_t* __restrict__ perm, TC* __restrict__ Out, int64_t ldo,
+                                                 int bx) {
   __shared__ TC tile[kMaxL][33];
   __shared__ int pm[kMaxL];
-  const int64_t i0 = (int64_t)blockIdx.x * 32;
+  const int64_t i0 = (int64_t)bx * 32;
   for (int j = threadIdx.x; j < l; j += blockDim.x) pm[j] = perm ? perm[j] : j;
   for (int e = threadIdx.x; e < l * 32; e += blockDim.x) {
     const int r = e / 32, ii = e % 32;
@@ -658,6 +690,12 @@ __global__ void gather_cols_kernel(const TC* __restrict__ St, int64_t lds, int64
 }
 
 template <typename TC>
+__global__ void gather_cols_kernel(const TC* __restrict__ St, int64_t lds, int64_t len, int l,
+                                   const int32_t* __restrict__ perm, TC* __restrict__ Out, int64_t ldo) {
+  gather_cols_body<TC>(St, lds, len, l, perm, Out, ldo, blockIdx.x);
+}
+
+template <typename TC>
 cudaError_t launch_gather_cols(const TC* St, int64_t lds, int64_t len, int l, const int32_t* perm, TC* Out,
                                int64_t ldo, cudaStream_t st) {
   const unsigned grid = (unsigned)cdiv(len, 32);
@@ -667,10 +705,10 @@ cudaError_t launch_gather_cols(const TC* St, int64_t lds, int64_t len, int l, co
 
 // Xt[j][i] = Phi[i][j] (ST staging of the caller's row-major Psi).
 template <typename TC>
-__global__ void stage_transpose_kernel(const TC* __restrict__ Phi, int64_t ldphi, int64_t len, int l,
-                                       TC* __restrict__ Xt, int64_t ldx) {
+__device__ __forceinline__ void stage_transpose_body(const TC* __restrict__ Phi, int64_t ldphi, int64_t len, int l,
+                                                     TC* __restrict__ Xt, int64_t ldx, int bx) {
   __shared__ TC tile[32][kMaxL + 1];
-  const int64_t i0 = (int64_t)blockIdx.x * 32;
+  const int64_t i0 = (int64_t)bx * 32;
   for (int e = threadIdx.x; e < 32 * l; e += blockDim.x) {
     const int ii = e / l, j = e % l;
     const int64_t g = i0 + ii;
@@ -682,6 +720,12 @@ __global__ void stage_transpose_kernel(const TC* __restrict__ Phi, int64_t ldphi
     const int64_t g = i0 + ii;
     if (g < len) Xt[j * ldx + g] = tile[ii][j];
   }
+}
+
+template <typename TC>
+__global__ void stage_transpose_kernel(const TC* __restrict__ Phi, int64_t ldphi, int64_t len, int l,
+                                       TC* __restrict__ Xt, int64_t ldx) {
+  stage_transpose_body<TC>(Phi, ldphi, len, l, Xt, ldx, blockIdx.x);
 }
 
 template <typename TC>
@@ -980,10 +1024,10 @@ __device__ __forceinline__ void axpyN(const float* __restrict__ v, float f, floa
 }
 
 template <int TPC>
-__global__ void __launch_bounds__(kMaxL * TPC) qrcp_reg_kernel(const double* __restrict__ Dg, int64_t ldd, int l, int k,
-                                                       double* __restrict__ Qg, int64_t ldq, double* __restrict__ Rg,
-                                                       int64_t ldr, int r_transposed, int32_t* __restrict__ perm,
-                                                       double* __restrict__ fro2, DevStatus* status) {
+__device__ __forceinline__ void qrcp_reg_body(const double* __restrict__ Dg, int64_t ldd, int l, int k,
+                                              double* __restrict__ Qg, int64_t ldq, double* __restrict__ Rg,
+                                              int64_t ldr, int r_transposed, int32_t* __restrict__ perm,
+                                              double* __restrict__ fro2, DevStatus* status) {
   constexpr int RPT = kMaxL / TPC, NWARP = kMaxL * TPC / 32, CPW = 32 / TPC;   // columns per warp
   __shared__ __align__(16) float vbuf[kMaxL];       // reflector of the current step (zero outside j..l-1)
   __shared__ __align__(16) float pcolv[kMaxL];      // raw pivot column
@@ -1175,6 +1219,14 @@ __global__ void __launch_bounds__(kMaxL * TPC) qrcp_reg_kernel(const double* __r
   }
 }
 
+template <int TPC>
+__global__ void __launch_bounds__(kMaxL * TPC) qrcp_reg_kernel(const double* __restrict__ Dg, int64_t ldd, int l, int k,
+                                                       double* __restrict__ Qg, int64_t ldq, double* __restrict__ Rg,
+                                                       int64_t ldr, int r_transposed, int32_t* __restrict__ perm,
+                                                       double* __restrict__ fro2, DevStatus* status) {
+  qrcp_reg_body<TPC>(Dg, ldd, l, k, Qg, ldq, Rg, ldr, r_transposed, perm, fro2, status);
+}
+
 template <typename TC>
 cudaError_t launch_qrcp(const double* D, int64_t ldd, int l, int k, double* Q, int64_t ldq, double* R, int64_t ldr,
                         bool r_transposed, int32_t* perm, double* fro2, DevStatus* status, cudaStream_t st) {
@@ -1246,6 +1298,281 @@ cudaError_t launch_fro2(int a_dtype, const void* A, int64_t lda, int64_t m, int6
     default: return cudaErrorInvalidValue;
   }
   sum_parts_kernel<<<1, 32, 0, st>>>(parts, nparts, out, nullptr); CORUTV_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
+
+// =============================================================================== batched (grouped) launches
+// Each grouped kernel runs the single-problem body for the problem a block map
+// assigns to its block (FP32 storage of the sketches).  A problem takes part in
+// an orthonormalisation pass while it is within its power steps and the pass
+// index is below its CholeskyQR pass count (3 for the last step or ORTH_STRICT,
+// else 1).
+__device__ __forceinline__ bool batch_orth_active(const BatchProb& P, int it, int pass) {
+  if (it > P.q) return false;
+  const int passes = (it == P.q || P.orth == 1) ? 3 : 1;
+  return pass < passes;
+}
+
+__global__ void __launch_bounds__(256) stage_grouped_kernel(const BatchProb* __restrict__ probs,
+                                                            const int2* __restrict__ map) {
+  const int2 pm = map[blockIdx.x];
+  const BatchProb& P = probs[pm.x];
+  stage_transpose_body<float>(P.Phi, P.ldphi, P.len2, P.l, P.P2, P.ld2, pm.y);
+}
+
+// which: kG_ORTH1 (P1 P1^T -> G), kG_ORTH2 (P2 P2^T -> G), kG_CORE_EXACT (P1 P3^T -> D),
+// kG_CORE_SKETCH (P3 P2^T -> D: the saved last C2 against Q2)
+__device__ __forceinline__ bool batch_gram_sel(const BatchProb& P, int which, int it, int pass, const float** X,
+                                               int64_t* ldx, const float** Y, int64_t* ldy, int64_t* len,
+                                               double** out) {
+  switch (which) {
+    case kG_ORTH1:
+      if (!batch_orth_active(P, it, pass)) return false;
+      *X = P.P1; *ldx = P.ld1; *Y = P.P1; *ldy = P.ld1; *len = P.len1; *out = P.G;
+      return true;
+    case kG_ORTH2:
+      if (!batch_orth_active(P, it, pass)) return false;
+      *X = P.P2; *ldx = P.ld2; *Y = P.P2; *ldy = P.ld2; *len = P.len2; *out = P.G;
+      return true;
+    case kG_CORE_EXACT:
+      if (P.core != 0) return false;
+      *X = P.P1; *ldx = P.ld1; *Y = P.P3; *ldy = P.ld3; *len = P.len1; *out = P.D;
+      return true;
+    default:
+      if (P.core == 0) return false;
+      *X = P.P3; *ldx = P.ld3; *Y = P.P2; *ldy = P.ld2; *len = P.len2; *out = P.D;
+      return true;
+  }
+}
+
+template <int LP>
+__global__ void __launch_bounds__(512) gram_partial_grouped_kernel(const BatchProb* __restrict__ probs,
+                                                                   const int2* __restrict__ map, int which, int it,
+                                                                   int pass) {
+  const int2 pm = map[blockIdx.x];
+  const BatchProb& P = probs[pm.x];
+  const float *X, *Y;
+  int64_t ldx, ldy, len;
+  double* out;
+  if (!batch_gram_sel(P, which, it, pass, &X, &ldx, &Y, &ldy, &len, &out)) return;
+  const int nparts = (which == kG_ORTH2 || which == kG_CORE_SKETCH) ? P.gp2 : P.gp1;
+  gram_partial_body<float, LP>(X, ldx, Y, ldy, len, P.l, P.gparts, pm.y, nparts);
+}
+
+template <int LP>
+__global__ void __launch_bounds__(256) gram_reduce_grouped_kernel(const BatchProb* __restrict__ probs,
+                                                                  const int2* __restrict__ map, int which, int it,
+                                                                  int pass) {
+  const int2 pm = map[blockIdx.x];
+  const BatchProb& P = probs[pm.x];
+  const float *X, *Y;
+  int64_t ldx, ldy, len;
+  double* out;
+  if (!batch_gram_sel(P, which, it, pass, &X, &ldx, &Y, &ldy, &len, &out)) return;
+  const int nparts = (which == kG_ORTH2 || which == kG_CORE_SKETCH) ? P.gp2 : P.gp1;
+  gram_reduce_body<float>(P.gparts, nparts, LP, P.l, out, P.l, pm.y * blockDim.x + threadIdx.x);
+}
+
+__global__ void __launch_bounds__(kPipeMaxThreads, 1) cholinv_grouped_kernel(const BatchProb* __restrict__ probs,
+                                                                            int it, int pass, float skip_tol,
+                                                                            double shift_rel, double tol_rel) {
+  const BatchProb& P = probs[blockIdx.x];
+  if (!batch_orth_active(P, it, pass)) return;     // uniform over the block
+  int* skip = (pass == 2) ? &P.status->orth_skip : nullptr;
+  cholinv_pipe_body(P.G, P.l, P.l, pass == 0 ? shift_rel : 0.0, tol_rel, P.R, P.Rinv, P.l, P.defic, P.status,
+                    nullptr, skip, skip_tol);
+}
+
+template <int LP>
+__global__ void __launch_bounds__(256, 1) lmul_orth_grouped_kernel(const BatchProb* __restrict__ probs,
+                                                                   const int2* __restrict__ map, int which, int it,
+                                                                   int pass) {
+  const int2 pm = map[blockIdx.x];
+  const BatchProb& P = probs[pm.x];
+  if (!batch_orth_active(P, it, pass)) return;
+  if (pass == 2 && P.status->orth_skip) return;
+  float* C = which == kG_ORTH1 ? P.P1 : P.P2;
+  const int64_t ldc = which == kG_ORTH1 ? P.ld1 : P.ld2;
+  const int64_t len = which == kG_ORTH1 ? P.len1 : P.len2;
+  lmul_body<float, float, LP, kBatchLmulBI>(C, ldc, len, P.l, P.Rinv, P.l, C, ldc, 0, 1, P.defic, pass, pm.y);
+}
+
+// the last C2 of a problem (power step it == q) is kept in P3 for the sketch core
+__global__ void __launch_bounds__(256) copy_sketch_grouped_kernel(const BatchProb* __restrict__ probs,
+                                                                  const int2* __restrict__ map, int it) {
+  const int2 pm = map[blockIdx.x];
+  const BatchProb& P = probs[pm.x];
+  if (P.core == 0 || it != P.q) return;
+  const int64_t i0 = (int64_t)pm.y * kBatchTile32;
+  for (int e = threadIdx.x; e < P.l * kBatchTile32; e += blockDim.x) {
+    const int j = e / kBatchTile32;
+    const int64_t g = i0 + e % kBatchTile32;
+    if (g < P.len2) P.P3[j * P.ld3 + g] = P.P2[j * P.ld2 + g];
+  }
+}
+
+__global__ void __launch_bounds__(kMaxL * kQrcpTPC) qrcp_grouped_kernel(const BatchProb* __restrict__ probs) {
+  const BatchProb& P = probs[blockIdx.x];
+  qrcp_reg_body<kQrcpTPC>(P.D, P.l, P.l, P.k, P.Qt, P.l, P.T, P.ldt, P.side == 1 ? 1 : 0, P.perm, nullptr,
+                          P.status);
+}
+
+// U = Q1 Q~ (RIGHT; V for LEFT), row-major out
+template <int LP>
+__global__ void __launch_bounds__(256, 1) assemble_lmul_grouped_kernel(const BatchProb* __restrict__ probs,
+                                                                       const int2* __restrict__ map) {
+  const int2 pm = map[blockIdx.x];
+  const BatchProb& P = probs[pm.x];
+  float* out = P.side == 1 ? P.V : P.U;
+  const int64_t ldo = P.side == 1 ? P.ldv : P.ldu;
+  lmul_body<float, double, LP, kBatchLmulBI>(P.P1, P.ld1, P.len1, P.l, P.Qt, P.l, out, ldo, 1, 0, nullptr, 0, pm.y);
+}
+
+// V = Q2 P~ (RIGHT; U for LEFT)
+__global__ void __launch_bounds__(256) assemble_gather_grouped_kernel(const BatchProb* __restrict__ probs,
+                                                                      const int2* __restrict__ map) {
+  const int2 pm = map[blockIdx.x];
+  const BatchProb& P = probs[pm.x];
+  float* out = P.side == 1 ? P.U : P.V;
+  const int64_t ldo = P.side == 1 ? P.ldu : P.ldv;
+  gather_cols_body<float>(P.P2, P.ld2, P.len2, P.l, P.perm, out, ldo, pm.y);
+}
+
+// ||A||_F^2 per problem: its first-pass partials summed in tile order
+__global__ void fro2_grouped_kernel(const BatchProb* __restrict__ probs) {
+  const BatchProb& P = probs[blockIdx.x];
+  if (threadIdx.x != 0) return;
+  double s = 0.0;
+  if (P.want_fro2)
+    for (int i = 0; i < P.nfparts; ++i) s += P.fparts[i];
+  P.status->fro2_A = P.want_fro2 ? s : 0.0;
+}
+
+cudaError_t launch_stage_grouped(const BatchProb* P, const int2* map32_2, int nblocks, cudaStream_t st) {
+  if (nblocks <= 0) return cudaSuccess;
+  stage_grouped_kernel<<<nblocks, 256, 0, st>>>(P, map32_2);
+  CORUTV_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gram_grouped(const BatchProb* P, const int2* map_parts, int nparts, const int2* map_red,
+                                int nred, int lp, int which, int it, int pass, cudaStream_t st) {
+  if (nparts <= 0 || nred <= 0) return cudaSuccess;
+  if (lp <= 32) {
+    gram_partial_grouped_kernel<32><<<nparts, 512, 0, st>>>(P, map_parts, which, it, pass);
+    CORUTV_COUNT_LAUNCH();
+    gram_reduce_grouped_kernel<32><<<nred, 256, 0, st>>>(P, map_red, which, it, pass);
+  } else if (lp <= 64) {
+    gram_partial_grouped_kernel<64><<<nparts, 512, 0, st>>>(P, map_parts, which, it, pass);
+    CORUTV_COUNT_LAUNCH();
+    gram_reduce_grouped_kernel<64><<<nred, 256, 0, st>>>(P, map_red, which, it, pass);
+  } else {
+    gram_partial_grouped_kernel<128><<<nparts, 512, 0, st>>>(P, map_parts, which, it, pass);
+    CORUTV_COUNT_LAUNCH();
+    gram_reduce_grouped_kernel<128><<<nred, 256, 0, st>>>(P, map_red, which, it, pass);
+  }
+  CORUTV_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cholinv_grouped(const BatchProb* P, int count, int lmax, int which, int it, int pass,
+                                   float skip_tol, double shift_rel, double tol_rel, cudaStream_t st) {
+  (void)which;
+  if (count <= 0) return cudaSuccess;
+  const int nb = (lmax + 3) / 4;
+  const int threads = (nb * (nb + 1) / 2 + 31) / 32 * 32;
+  cholinv_grouped_kernel<<<count, threads, 0, st>>>(P, it, pass, skip_tol, shift_rel, tol_rel);
+  CORUTV_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
+
+// Shared-memory limits are raised once per kernel and device (the first, uncaptured
+// run of a batch), so a later stream capture records launches only.
+constexpr int kAttrDevices = 64;
+static bool* attr_flag(bool (&flags)[kAttrDevices]) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kAttrDevices) return nullptr;
+  return &flags[dev];
+}
+
+template <int LP>
+static cudaError_t lmul_orth_grouped_lp(const BatchProb* P, const int2* map, int nblocks, int which, int it,
+                                        int pass, cudaStream_t st) {
+  const size_t sm = ((size_t)LP * (LP + 4) + (size_t)LP * (kBatchLmulBI + 4)) * sizeof(float);
+  static bool attr_set[kAttrDevices] = {};
+  bool* flag = attr_flag(attr_set);
+  if (!flag || !*flag) {
+    cudaError_t e = cudaFuncSetAttribute(lmul_orth_grouped_kernel<LP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sm);
+    if (e != cudaSuccess) return e;
+    if (flag) *flag = true;
+  }
+  lmul_orth_grouped_kernel<LP><<<nblocks, 256, sm, st>>>(P, map, which, it, pass);
+  CORUTV_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lmul_orth_grouped(const BatchProb* P, const int2* map, int nblocks, int lp, int which, int it,
+                                     int pass, cudaStream_t st) {
+  if (nblocks <= 0) return cudaSuccess;
+  if (lp <= 32) return lmul_orth_grouped_lp<32>(P, map, nblocks, which, it, pass, st);
+  if (lp <= 64) return lmul_orth_grouped_lp<64>(P, map, nblocks, which, it, pass, st);
+  return lmul_orth_grouped_lp<128>(P, map, nblocks, which, it, pass, st);
+}
+
+cudaError_t launch_copy_sketch_grouped(const BatchProb* P, const int2* map32_2, int nblocks, int it,
+                                       cudaStream_t st) {
+  if (nblocks <= 0) return cudaSuccess;
+  copy_sketch_grouped_kernel<<<nblocks, 256, 0, st>>>(P, map32_2, it);
+  CORUTV_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_qrcp_grouped(const BatchProb* P, int count, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  qrcp_grouped_kernel<<<count, kMaxL * kQrcpTPC, 0, st>>>(P);
+  CORUTV_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
+
+template <int LP>
+static cudaError_t assemble_lp(const BatchProb* P, const int2* map, int nblocks, cudaStream_t st) {
+  const size_t a = (size_t)LP * (LP + 4) + (size_t)LP * (kBatchLmulBI + 4);
+  const size_t b = (size_t)LP * (LP + 4) + (size_t)kBatchLmulBI * (LP + 1);
+  const size_t sm = (a > b ? a : b) * sizeof(float);
+  static bool attr_set[kAttrDevices] = {};
+  bool* flag = attr_flag(attr_set);
+  if (!flag || !*flag) {
+    cudaError_t e = cudaFuncSetAttribute(assemble_lmul_grouped_kernel<LP>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    if (flag) *flag = true;
+  }
+  assemble_lmul_grouped_kernel<LP><<<nblocks, 256, sm, st>>>(P, map);
+  CORUTV_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_assemble_grouped(const BatchProb* P, const int2* map_lmul1, int n1, const int2* map32_2, int n2,
+                                    int lp, cudaStream_t st) {
+  cudaError_t e = cudaSuccess;
+  if (n1 > 0) {
+    if (lp <= 32) e = assemble_lp<32>(P, map_lmul1, n1, st);
+    else if (lp <= 64) e = assemble_lp<64>(P, map_lmul1, n1, st);
+    else e = assemble_lp<128>(P, map_lmul1, n1, st);
+    if (e != cudaSuccess) return e;
+  }
+  if (n2 > 0) {
+    assemble_gather_grouped_kernel<<<n2, 256, 0, st>>>(P, map32_2);
+    CORUTV_COUNT_LAUNCH();
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fro2_grouped(const BatchProb* P, int count, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  fro2_grouped_kernel<<<count, 32, 0, st>>>(P);
+  CORUTV_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 

@@ -1,0 +1,191 @@
+"""GPU parity of corutv_solve_batched (grouped launches over many problems of
+different shapes) with the FP64 oracle run on each problem's stored values,
+replay determinism of the captured batch, and the 1024-problem workload
+(m ~ U{256..4096}, n ~ U{128..2048}, l = r + 8, q = 1) on sampled problems.
+
+The batched passes accumulate FP32 products of the stored A on the CUDA cores
+and the factorisations run in FP32 as in corutv_solve with mma = SIMT, so the
+bound is the FP32 one: rho <= 1e-4."""
+import numpy as np
+import pytest
+
+from oracle import corutv_oracle as O
+from oracle import precision as P
+from synth import counter as C
+from synth import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if torch.cuda.is_available():
+    from paper_1810_07323_gb300 import corutv
+
+TOL = 1e-4
+
+
+def _lowrank_sparse(seed, m, n, r):
+    return W.LowRankSparse(m, n, r, 0.05, 10.0, seed).dense()
+
+
+def _item(A32, phi, k, l, q=1, side="right", core="exact", orth="stabilised", want_fro2=True, kind="f32"):
+    m, n = A32.shape
+    if kind == "f32":
+        Ad = torch.tensor(A32, dtype=torch.float32, device="cuda")
+        S, Aq = None, A32.astype(np.float64)
+    elif kind == "bf16":
+        v = P.bf16_round(A32)
+        Ad = torch.tensor(v).to(torch.bfloat16).cuda()
+        S, Aq = None, v.astype(np.float64)
+    else:
+        vals, sc = P.quantize_fp8(A32)
+        Ad = torch.tensor(vals.astype(np.float32)).to(torch.float8_e4m3fn).cuda()
+        S, Aq = torch.tensor(sc, dtype=torch.float32, device="cuda"), P.dequantize_fp8(vals, sc)
+    it = dict(A=Ad, Phi=torch.tensor(phi, dtype=torch.float32, device="cuda"), k=k, l=l, q=q, side=side,
+              core=core, orth=orth, want_fro2=want_fro2)
+    if S is not None:
+        it["a_tile_scales"] = S
+    return it, Aq
+
+
+MIXED = [
+    # m, n, r, k, l, q, side, core, orth
+    (700, 300, 6, 6, 14, 1, "right", "exact", "stabilised"),
+    (256, 1100, 10, 10, 18, 1, "left", "exact", "stabilised"),
+    (1500, 900, 20, 20, 28, 2, "right", "sketch", "stabilised"),
+    (333, 129, 4, 4, 12, 0, "right", "exact", "stabilised"),
+    (2048, 2047, 32, 32, 40, 1, "right", "exact", "strict"),
+    (640, 1900, 12, 12, 20, 2, "left", "sketch", "stabilised"),
+    (4096, 128, 30, 30, 38, 1, "right", "exact", "stabilised"),
+    (1000, 1000, 60, 60, 100, 0, "right", "exact", "stabilised"),     # l = 100: the 128-row kernels
+]
+
+
+def _check(res, Aq, phi, k, l, q, side, core):
+    U = res.U.double().cpu().numpy()
+    T = res.T.cpu().numpy()
+    V = res.V.double().cpu().numpy()
+    perm = res.perm.cpu().numpy()
+    ref = O.corutv(Aq, phi.astype(np.float64), k, l, q, side=side)
+    rho = O.factor_distance(U, T, V, ref["U"], ref["T"], ref["V"])
+    tri = np.tril(T, -1) if side == "right" else np.triu(T, 1)
+    assert np.abs(tri).max() == 0.0
+    assert np.all(np.diag(T) >= 0) and sorted(perm) == list(range(l))
+    assert O.orthonormality_error(U) < 5e-5 and O.orthonormality_error(V) < 5e-5
+    return rho
+
+
+@pytest.mark.parametrize("kind", ["f32", "bf16", "fp8"])
+def test_batched_mixed_parity(kind):
+    items, refs = [], []
+    for i, (m, n, r, k, l, q, side, core, orth) in enumerate(MIXED):
+        A = _lowrank_sparse(C.stream_seed(77, i), m, n, r).astype(np.float32)
+        phi = C.normal_block_np(C.stream_seed(78, i), l, 0, m if side == "left" else n, 0, l)
+        it, Aq = _item(A, phi, k, l, q, side, core, orth, kind=kind)
+        items.append(it)
+        refs.append((Aq, phi, k, l, q, side, core))
+    b = corutv.Batch(items)
+    res = b.run()
+    for i, (r, (Aq, phi, k, l, q, side, core)) in enumerate(zip(res, refs)):
+        assert r.info.status == 0
+        rho = _check(r, Aq, phi, k, l, q, side, core)
+        print(f"{kind} problem {i} {MIXED[i][:2]}: rho={rho:.3e}")
+        assert rho < TOL, (i, rho)
+        a2 = float(np.sum(Aq ** 2))
+        assert abs(r.info.fro2_A - a2) < 1e-6 * a2
+        assert abs(r.info.fro2_T - float(np.sum(r.T.cpu().numpy() ** 2))) < 1e-9 * a2
+        assert r.info.passes_over_A == 2 * (q + 1) + (1 if core == "exact" else 0)
+
+
+def test_batched_replay_is_identical():
+    """First run (direct launches), second (captured into a CUDA graph) and third
+    (graph replay) give bit-identical factors."""
+    items = []
+    for i, (m, n, r, k, l, q, side, core, orth) in enumerate(MIXED[:6]):
+        A = _lowrank_sparse(C.stream_seed(90, i), m, n, r).astype(np.float32)
+        phi = C.normal_block_np(C.stream_seed(91, i), l, 0, m if side == "left" else n, 0, l)
+        items.append(_item(A, phi, k, l, q, side, core, orth)[0])
+    b = corutv.Batch(items)
+    outs = []
+    for _ in range(3):
+        res = b.run()
+        outs.append([(r.U.clone(), r.T.clone(), r.V.clone(), r.perm.clone()) for r in res])
+        assert all(r.info.status == 0 for r in res)
+    for run in outs[1:]:
+        for a, c in zip(outs[0], run):
+            assert all(torch.equal(x, y) for x, y in zip(a, c))
+
+
+def test_batched_single_problem_matches_solve():
+    """A batch of one agrees with corutv_solve (SIMT passes) to FP32 rounding."""
+    A = _lowrank_sparse(5, 1200, 700, 15).astype(np.float32)
+    phi = C.normal_block_np(6, 23, 0, 700, 0, 23)
+    it, _ = _item(A, phi, 15, 23, 1)
+    r = corutv.Batch([it]).run()[0]
+    s = corutv.solve(it["A"], it["Phi"], 15, 23, 1, mma="simt")
+    rho = O.factor_distance(r.U.double().cpu().numpy(), r.T.cpu().numpy(), r.V.double().cpu().numpy(),
+                            s.U.double().cpu().numpy(), s.T.cpu().numpy(), s.V.double().cpu().numpy())
+    assert rho < 1e-5, rho
+
+
+def test_batched_invalid_arguments():
+    A = torch.zeros((100, 80), device="cuda")
+    phi = torch.zeros((80, 10), device="cuda")
+    with pytest.raises(corutv.CorutvError) as e:
+        corutv.Batch([dict(A=A, Phi=phi, k=11, l=10)]).run()
+    assert e.value.status == corutv.ERR_INVALID_ARG
+    with pytest.raises(corutv.CorutvError) as e:
+        corutv.Batch([dict(A=A, Phi=torch.zeros((80, 80), device="cuda"), k=5, l=80)]).run()
+    assert e.value.status == corutv.ERR_SHAPE
+    A64 = torch.zeros((100, 80), dtype=torch.float64, device="cuda")
+    with pytest.raises(corutv.CorutvError) as e:
+        corutv.Batch([dict(A=A64, Phi=phi, k=5, l=10)]).run()
+    assert e.value.status == corutv.ERR_UNSUPPORTED
+    Ab = torch.zeros((100, 80), dtype=torch.bfloat16, device="cuda")
+    with pytest.raises(corutv.CorutvError) as e:           # one storage dtype per batch
+        corutv.Batch([dict(A=A, Phi=phi, k=5, l=10), dict(A=Ab, Phi=phi, k=5, l=10)]).run()
+    assert e.value.status == corutv.ERR_UNSUPPORTED
+
+
+def _config4_items(probs):
+    items = []
+    for p in probs:
+        side = "left" if p.m < p.n else "right"
+        A = p.content.dense_t(device="cuda", dtype=torch.float32)
+        phi = W.problem_phi_t(p, p.m if side == "left" else p.n, device="cuda").float()
+        items.append(dict(A=A, Phi=phi, k=p.k, l=p.l, q=p.q, side=side, want_fro2=True))
+    return items
+
+
+@pytest.mark.slow
+def test_config4_full_batch_sampled():
+    """The 1024-problem workload in one batched call: every problem's structure
+    and Pythagorean readout, 24 sampled problems against the oracle."""
+    probs = W.batch_config4()
+    items = _config4_items(probs)
+    b = corutv.Batch(items)
+    res = b.run()
+    rng = np.random.default_rng(0)
+    sample = set(rng.choice(len(probs), 24, replace=False).tolist())
+    for i, (p, it, r) in enumerate(zip(probs, items, res)):
+        assert r.info.status == 0
+        T = r.T
+        side = it["side"]
+        tri = torch.tril(T, -1) if side == "right" else torch.triu(T, 1)
+        assert float(tri.abs().max()) == 0.0
+        U, V = r.U.double(), r.V.double()
+        eye = torch.eye(p.l, dtype=torch.float64, device="cuda")
+        assert float((U.T @ U - eye).abs().max()) < 5e-5
+        assert float((V.T @ V - eye).abs().max()) < 5e-5
+        A = it["A"].double()
+        res2 = float(((A - (U @ T) @ V.T) ** 2).sum())
+        a2 = r.info.fro2_A
+        assert abs(a2 - float((A ** 2).sum())) < 1e-6 * a2
+        # exact core: ||A - U T V^T||^2 = ||A||^2 - ||T||^2 to FP32 rounding of the products
+        assert abs((a2 - r.info.fro2_T) - res2) < 1e-5 * a2
+        if i in sample:
+            Aq = it["A"].double().cpu().numpy()
+            phi = it["Phi"].double().cpu().numpy()
+            ref = O.corutv(Aq, phi, p.k, p.l, p.q, side=side)
+            rho = O.factor_distance(U.cpu().numpy(), T.cpu().numpy(), V.cpu().numpy(), ref["U"], ref["T"],
+                                    ref["V"])
+            assert rho < TOL, (i, rho)
