@@ -254,7 +254,8 @@ int corutv_batch_workspace_size(int count, const corutv_problem* probs, size_t* 
  * ERR_UNSUPPORTED.  The handle keeps a workspace and the tables of the last
  * problem set; calling again with an identical problem array (same shapes,
  * pointers and parameters) replays a CUDA graph of the whole batch (not on the
- * legacy default stream).  Validation errors return synchronously and enqueue
+ * legacy default stream, and not while tracing: traced runs launch directly so
+ * every phase gets its own event pair).  Validation errors return synchronously and enqueue
  * nothing.  infos: NULL (the call returns once the work is enqueued; read the
  * outcome with corutv_batch_info_wait) or a host array of `count` entries (the
  * call waits for the batch and fills it).

@@ -38,6 +38,7 @@ struct BatchState {
   int lp = 32, lmax = 1, maxq = 0, a_dtype = CORUTV_F32;
   bool any_exact = false, any_sketch = false, any_fro2 = false;
   std::vector<char> multi_pass;       // per power step: some problem runs more than one CholeskyQR pass
+  std::vector<double> pass_bytes;     // algorithmic bytes of each grouped pass: [3 * it + which]
   cudaGraphExec_t exec = nullptr;
   int64_t launches_per_run = 0;
 };
@@ -291,6 +292,19 @@ int build(corutv_handle* h, BatchState* B, int count, const corutv_problem* prob
     for (int it = 0; it <= p.q; ++it)
       if (it == p.q || p.orth == CORUTV_ORTH_STRICT) B->multi_pass[it] = 1;
   }
+  // algorithmic bytes of every grouped pass (A as stored + sketch operand + result of the
+  // problems taking part): index 3 * it + which, the core pass at 3 * (maxq + 1) + kB_CORE
+  B->pass_bytes.assign(3 * (maxq + 2), 0.0);
+  for (int i = 0; i < count; ++i) {
+    const corutv_problem& p = probs[i];
+    const int eb = p.a_dtype == CORUTV_F32 ? 4 : (p.a_dtype == CORUTV_BF16 ? 2 : 1);
+    const double a_bytes = (double)p.m * p.n * eb, sk = 4.0 * p.l * (double)(sz[i].len1 + sz[i].len2);
+    for (int it = 0; it <= p.q; ++it) {
+      B->pass_bytes[3 * it + kB_C1] += a_bytes + sk;
+      B->pass_bytes[3 * it + kB_C2] += a_bytes + sk;
+    }
+    if (p.core == CORUTV_CORE_EXACT) B->pass_bytes[3 * (maxq + 1) + kB_CORE] += a_bytes + sk;
+  }
   memcpy(hbase, T.probs.data(), sizeof(BatchProb) * count);
   CUB(cudaMemcpyAsync(B->ws, B->host, B->table_bytes, cudaMemcpyHostToDevice, h->stream));
   B->count = count;
@@ -307,6 +321,7 @@ int build(corutv_handle* h, BatchState* B, int count, const corutv_problem* prob
 }
 
 int orth_grouped(corutv_handle* h, const BatchState* B, int which, int it) {
+  PhaseTimer tm(h, kPhOrth);
   const bool second = which == kG_ORTH2;
   const int passes = B->multi_pass[it] ? 3 : 1;
   for (int pass = 0; pass < passes; ++pass) {
@@ -321,27 +336,49 @@ int orth_grouped(corutv_handle* h, const BatchState* B, int which, int it) {
 }
 
 // The whole batch, enqueued on the handle's stream.
+int pass_grouped(corutv_handle* h, const BatchState* B, int which, int it) {
+  const double bytes = B->pass_bytes[which == kB_CORE ? 3 * (B->maxq + 1) + kB_CORE : 3 * it + which];
+  PhaseTimer tm(h, kPhPass, bytes);
+  const bool first = which != kB_C2;
+  CUB(launch_pass_simt_grouped(B->dprobs, first ? B->t1 : B->t2, first ? B->nt1 : B->nt2, B->lp, B->a_dtype,
+                               which, it, h->stream));
+  return CORUTV_OK;
+}
+
 int enqueue(corutv_handle* h, const BatchState* B) {
   cudaStream_t st = h->stream;
   CUB(cudaMemsetAsync(B->dstatus, 0, sizeof(DevStatus) * B->count, st));
-  CUB(launch_stage_grouped(B->dprobs, B->s2, B->ns2, st));                             // S0
+  {
+    PhaseTimer tm(h, kPhAsm);
+    CUB(launch_stage_grouped(B->dprobs, B->s2, B->ns2, st));                           // S0
+  }
   for (int it = 0; it <= B->maxq; ++it) {
-    CUB(launch_pass_simt_grouped(B->dprobs, B->t1, B->nt1, B->lp, B->a_dtype, kB_C1, it, st));   // S1
-    int rc = orth_grouped(h, B, kG_ORTH1, it);                                           // S2
+    int rc = pass_grouped(h, B, kB_C1, it);                                              // S1
+    if (!rc) rc = orth_grouped(h, B, kG_ORTH1, it);                                      // S2
+    if (!rc) rc = pass_grouped(h, B, kB_C2, it);                                         // S3
     if (rc) return rc;
-    CUB(launch_pass_simt_grouped(B->dprobs, B->t2, B->nt2, B->lp, B->a_dtype, kB_C2, it, st));   // S3
     if (B->any_sketch) CUB(launch_copy_sketch_grouped(B->dprobs, B->s2, B->ns2, it, st));
     rc = orth_grouped(h, B, kG_ORTH2, it);                                               // S4
     if (rc) return rc;
   }
   if (B->any_exact) {                                                                    // S5
-    CUB(launch_pass_simt_grouped(B->dprobs, B->t1, B->nt1, B->lp, B->a_dtype, kB_CORE, 0, st));
+    const int rc = pass_grouped(h, B, kB_CORE, 0);
+    if (rc) return rc;
+    PhaseTimer tm(h, kPhCore);
     CUB(launch_gram_grouped(B->dprobs, B->g1, B->ng1, B->red, B->nred, B->lp, kG_CORE_EXACT, 0, 0, st));
   }
-  if (B->any_sketch)
+  if (B->any_sketch) {
+    PhaseTimer tm(h, kPhCore);
     CUB(launch_gram_grouped(B->dprobs, B->g2, B->ng2, B->red, B->nred, B->lp, kG_CORE_SKETCH, 0, 0, st));
-  CUB(launch_qrcp_grouped(B->dprobs, B->count, st));                                    // S6
-  CUB(launch_assemble_grouped(B->dprobs, B->lm1, B->nlm1, B->s2, B->ns2, B->lp, st));   // S7
+  }
+  {
+    PhaseTimer tm(h, kPhQrcp);
+    CUB(launch_qrcp_grouped(B->dprobs, B->count, st));                                  // S6
+  }
+  {
+    PhaseTimer tm(h, kPhAsm);
+    CUB(launch_assemble_grouped(B->dprobs, B->lm1, B->nlm1, B->s2, B->ns2, B->lp, st)); // S7
+  }
   if (B->any_fro2) CUB(launch_fro2_grouped(B->dprobs, B->count, st));                   // S9
   return CORUTV_OK;
 }
@@ -399,11 +436,12 @@ int corutv_solve_batched(corutv_handle* h, int count, const corutv_problem* prob
     rc = enqueue(h, B);                           // first run of a problem set: direct launches
     if (rc) return rc;
     B->launches_per_run = launch_counter() - l0;
-  } else if (B->exec) {
+  } else if (B->exec && !h->tracing) {
     CUB(cudaGraphLaunch(B->exec, h->stream));
     launch_counter() += B->launches_per_run;
-  } else if (h->stream == nullptr || h->stream == cudaStreamLegacy) {
-    int rc = enqueue(h, B);                       // the legacy stream cannot be captured
+  } else if (h->tracing || h->stream == nullptr || h->stream == cudaStreamLegacy) {
+    // traced runs record their own events; the legacy stream cannot be captured
+    int rc = enqueue(h, B);
     if (rc) return rc;
   } else {
     // second run of the same set: capture the sequence once, then replay it
@@ -429,6 +467,7 @@ int corutv_solve_batched(corutv_handle* h, int count, const corutv_problem* prob
     launch_counter() += B->launches_per_run;
   }
   h->launches += launch_counter() - l0;
+  if (h->tracing) h->acc.solves += count;
   if (infos) return corutv_batch_info_wait(h, count, infos);
   return CORUTV_OK;
 }

@@ -177,38 +177,6 @@ int ensure_workspace(corutv_handle* h, size_t need) {
   return CORUTV_OK;
 }
 
-cudaEvent_t ev_get(corutv_handle* h) {
-  if (!h->ev_pool.empty()) {
-    cudaEvent_t e = h->ev_pool.back();
-    h->ev_pool.pop_back();
-    return e;
-  }
-  cudaEvent_t e = nullptr;
-  cudaEventCreate(&e);
-  return e;
-}
-
-// RAII phase timer: records an event pair on the handle's stream when tracing.
-struct PhaseTimer {
-  corutv_handle* h;
-  int phase;
-  double bytes;
-  cudaEvent_t a = nullptr;
-  PhaseTimer(corutv_handle* h_, int ph, double by = 0.0) : h(h_), phase(ph), bytes(by) {
-    if (h->tracing) {
-      a = ev_get(h);
-      cudaEventRecord(a, h->stream);
-    }
-  }
-  ~PhaseTimer() {
-    if (h->tracing && a) {
-      cudaEvent_t b = ev_get(h);
-      cudaEventRecord(b, h->stream);
-      h->recs.push_back(TraceRec{phase, a, b, bytes});
-    }
-  }
-};
-
 #define CU(x)                                   \
   do {                                          \
     cudaError_t e_ = (x);                       \
