@@ -37,6 +37,8 @@ WORKLOADS = {
     "fp8": dict(m=32768, n=16384, k=64, l=80, q=2, dtype="fp8", gen="config3"),
     # 1024 problems m ~ U{256..4096}, n ~ U{128..2048}, rank r ~ U{4..32} + 5% sparse, l = r + 8, q = 1
     "batched": dict(count=1024, q=1, dtype="f32", gen="config4"),
+    # Poisson arrivals at 2000 req/s, sizes 70/25/5% of 1024x512, 8192x2048, 76800x200, BF16 A
+    "serving": dict(rate=2000.0, duration=10.0, dtype="bf16", gen="config5"),
 }
 
 
@@ -64,6 +66,10 @@ def parse():
 
 
 def workload_label(w, core):
+    if w["gen"] == "config5":
+        return (f"serving: Poisson arrivals at {w['rate']:.0f} req/s for {w['duration']:.0f} s, sizes 70/25/5% of "
+                f"1024x512, 8192x2048, 76800x200 (rank-5 + 5% sparse), k~U{{5,20,50}}, l=k+10, q~U{{0,1}}, "
+                f"BF16 A, one solve per request")
     if w["gen"] == "config4":
         return (f"{w['count']} uneven problems m~U{{256..4096}} x n~U{{128..2048}}, A = X Y^T (rank r~U{{4..32}}) "
                 f"+ 5% sparse U[-10,10], l = r+8, q = {w['q']}, FP32, exact core, side LEFT when m < n, "
@@ -458,10 +464,158 @@ def main_batched(args):
         dist.destroy_process_group()
 
 
+def serving_pools(dev, pool=4):
+    """Matrix contents per size class (the first `pool` requests' generators of that
+    class) and Psi per (class, k): requests cycle through them."""
+    import torch
+    from synth import counter as C
+    from synth import workloads as W
+    stream = W.serving_stream(2000.0, 5.0)
+    A = {}
+    for r in stream:
+        cls = W.SERVING_SIZES.index((r.m, r.n))
+        lst = A.setdefault(cls, [])
+        if len(lst) < pool:
+            lst.append(r.content.dense_t(device=dev, dtype=torch.float32).to(torch.bfloat16))
+    phi = {}
+    for cls, (m, n) in enumerate(W.SERVING_SIZES):
+        for k in (5, 20, 50):
+            phi[(cls, k)] = [C.normal_block_t(C.stream_seed(2005, 100 * cls + k + 7 * j), k + 10, 0, n, 0, k + 10,
+                                              device=dev).float() for j in range(pool)]
+    return A, phi
+
+
+def main_serving(args):
+    """Serving workload: requests submitted at their Poisson arrival times to a
+    corutv_server, latency = completion seen by the polling client - submission."""
+    import ctypes
+    import numpy as np
+    import torch
+    world, rank, local = dist_setup()
+    from paper_1810_07323_gb300 import corutv
+    from synth import workloads as W
+    w = args.w
+    dev = torch.device("cuda", torch.cuda.current_device())
+    pools, phis = serving_pools(dev)
+    reqs = W.serving_stream(w["rate"], w["duration"] + 1.0)
+    warm = [r for r in reqs if r.t_arrive < 1.0]
+    timed = [r for r in reqs if r.t_arrive >= 1.0]
+    lib = corutv.load()
+    # output rings per (class, k): a slot is reused only after its request finished
+    RING = 512
+    rings = {}
+    for cls, (m, n) in enumerate(W.SERVING_SIZES):
+        for k in (5, 20, 50):
+            l = k + 10
+            rings[(cls, k)] = [(torch.empty((m, l), device=dev), torch.empty((l, l), dtype=torch.float64, device=dev),
+                                torch.empty((n, l), device=dev), torch.empty((l,), dtype=torch.int32, device=dev))
+                               for _ in range(RING)]
+    srv = corutv.Server(hbm_budget=16 << 30, max_slots=64, queue_capacity=16384)
+    counters = {}
+    slot_busy = {}
+
+    def make_problem(i, r):
+        cls = W.SERVING_SIZES.index((r.m, r.n))
+        c = counters.get((cls, r.k), 0)
+        counters[(cls, r.k)] = c + 1
+        U, T, V, perm = rings[(cls, r.k)][c % RING]
+        key = (cls, r.k, c % RING)
+        A = pools[cls][i % len(pools[cls])]
+        phi = phis[(cls, r.k)][i % len(phis[(cls, r.k)])]
+        p = corutv.Problem()
+        p.m, p.n, p.k, p.l, p.q = r.m, r.n, r.k, r.l, r.q
+        p.side, p.core, p.orth, p.a_dtype, p.mma, p.want_fro2 = 0, 0, 0, 2, 0, 1
+        p.A, p.lda = A.data_ptr(), A.stride(0)
+        p.Phi, p.ldphi = phi.data_ptr(), phi.stride(0)
+        p.U, p.ldu, p.T, p.ldt = U.data_ptr(), U.stride(0), T.data_ptr(), T.stride(0)
+        p.V, p.ldv, p.perm = V.data_ptr(), V.stride(0), perm.data_ptr()
+        return p, key
+
+    def run(stream_reqs, base):
+        out = []
+        info = corutv.Info()
+        pending = {}
+        t0 = time.perf_counter()
+        i = 0
+        while i < len(stream_reqs) or pending:
+            now = time.perf_counter() - t0
+            while i < len(stream_reqs) and stream_reqs[i].t_arrive - base <= now:
+                p, key = make_problem(i, stream_reqs[i])
+                assert not slot_busy.get(key, False), "output ring too small"
+                t = ctypes.c_uint64()
+                ts = time.perf_counter()
+                rc = lib.corutv_server_submit(srv.s, ctypes.byref(p), ctypes.byref(t))
+                assert rc == 0, corutv.status_string(rc)
+                slot_busy[key] = True
+                pending[t.value] = (ts, key, stream_reqs[i])
+                i += 1
+                now = time.perf_counter() - t0
+            for tk in list(pending):
+                rc = lib.corutv_server_poll(srv.s, ctypes.c_uint64(tk), ctypes.byref(info))
+                if rc != corutv.PENDING:
+                    ts, key, r = pending.pop(tk)
+                    te = time.perf_counter()
+                    assert rc == 0 and info.status == 0, corutv.status_string(rc)
+                    slot_busy[key] = False
+                    out.append((te - ts, r))
+        return out, time.perf_counter() - t0
+
+    run(warm, 0.0)
+    st0 = srv.stats()
+    clocks = Clocks(torch.cuda.current_device()) if rank == 0 else None
+    res, wall = run(timed, 1.0)
+    clk = clocks.stop() if clocks else None
+    st1 = srv.stats()
+    srv.close()
+    lat = np.array([x[0] for x in res]) * 1e3
+    p50, p99 = float(np.percentile(lat, 50)), float(np.percentile(lat, 99))
+    by_cls = {}
+    for dt, r in res:
+        by_cls.setdefault(f"{r.m}x{r.n}", []).append(dt * 1e3)
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        from oracle import corutv_oracle as O
+        from oracle import precision as P
+        tsum, ns = 0.0, 0
+        for r in timed[:40]:
+            if r.m * r.n > 8192 * 2048:
+                continue
+            A = P.bf16_round(r.content.dense().astype(np.float32)).astype(np.float64)
+            phi = W.problem_phi(W.Problem(r.m, r.n, 5, r.l, r.q, r.k, r.content, r.phi_seed), r.n)
+            t1 = time.perf_counter()
+            O.corutv(A, phi, r.k, r.l, r.q)
+            tsum += time.perf_counter() - t1
+            ns += 1
+        cpu = {"value": ns / tsum, "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
+               "sample": f"FP64 oracle on {ns} of the first 40 timed requests (76800x200 ones skipped), sequential"}
+    if rank == 0:
+        out = {"metric": "CoR-UTV serving p99 latency", "value": p99, "unit": "ms", "n_gpus": world,
+               "steps": len(res), "warmup": len(warm), "ms_per_step": float(np.mean(lat)),
+               "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+               "data": "synthetic",
+               "config": {"workload": workload_label(w, "exact"), "requests": len(res),
+                          "content": "4 matrices per size class and 4 Psi per (class, k), cycled",
+                          "l2": "per-request A of 1-30 MB, many requests in flight",
+                          "parallelism": f"replicas x{world}"},
+               "p50_ms": p50, "p99_ms": p99, "solves_per_s": len(res) / wall,
+               "latency_ms_by_size": {k: {"p50": float(np.percentile(v, 50)), "p99": float(np.percentile(v, 99)),
+                                          "count": len(v)} for k, v in by_cls.items()},
+               "batches": st1["batches"] - st0["batches"],
+               "mean_batch": len(res) / max(1, st1["batches"] - st0["batches"]),
+               "roofline": None, "cpu_baseline": cpu,
+               "e2e": {"value": p99, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
+                       "note": "latency through the public server API with device-resident requests"},
+               "gpu_launches": None, "clocks": clk}
+        print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.w["gen"] == "config5":
+        main_serving(args)
         return
     if args.w["gen"] == "config4":
         main_batched(args)

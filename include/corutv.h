@@ -266,6 +266,47 @@ int corutv_solve_batched(corutv_handle* h, int count, const corutv_problem* prob
  * last batch (count must equal that batch's count). */
 int corutv_batch_info_wait(corutv_handle* h, int count, corutv_info* infos);
 
+/* ------------------------------------------------------------------------
+ * Serving: a request queue in front of corutv_solve_batched (no counterpart in
+ * the paper; each request is one solve of Alg. 2 / Alg. 3).
+ * ---------------------------------------------------------------------- */
+
+typedef struct corutv_server corutv_server;
+
+/*
+ * Start a server on `device`: a worker thread forms batches from pending
+ * requests -- one storage dtype per batch, at most max_slots requests, admitted
+ * while the sum of their HBM footprints (A as stored, m x lda elements, plus the
+ * batch workspace of the request) stays within hbm_budget bytes -- and runs them
+ * with corutv_solve_batched on two handles and streams in turn (the next batch
+ * is formed and enqueued while the previous one runs).  A request whose
+ * footprint alone exceeds the budget finishes with ERR_OOM.  queue_capacity
+ * bounds the requests waiting for admission.
+ */
+int corutv_server_create(corutv_server** out, int device, size_t hbm_budget, int max_slots, int queue_capacity);
+
+/*
+ * Queue one solve (device pointers as in corutv_solve_batched; the caller keeps
+ * A, Psi and the outputs valid and untouched until the request has finished).
+ * Never blocks: returns ERR_BUSY when the queue is full, a validation error for
+ * an invalid problem, else OK with *ticket set.
+ */
+int corutv_server_submit(corutv_server* s, const corutv_problem* p, uint64_t* ticket);
+
+/*
+ * CORUTV_PENDING while the request is queued or running; once it has finished,
+ * its final status (OK, ERR_OOM, ERR_TIMEOUT, ERR_CUDA ...) with *info filled
+ * (info may be NULL) -- the ticket is then released.  Unknown tickets:
+ * ERR_INVALID_ARG.
+ */
+int corutv_server_poll(corutv_server* s, uint64_t ticket, corutv_info* info);
+
+/* Counters: batches launched, requests finished, requests waiting (any may be NULL). */
+int corutv_server_stats(corutv_server* s, int64_t* batches, int64_t* solved, int64_t* pending);
+
+/* Stop accepting requests, finish the queued ones, stop the worker, free everything. */
+int corutv_server_destroy(corutv_server* s);
+
 /* Synchronise the handle's stream and return the outcome of the last solve. */
 int corutv_info_wait(corutv_handle* h, corutv_info* out);
 

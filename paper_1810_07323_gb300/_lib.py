@@ -77,7 +77,9 @@ EXPORTS = ("corutv_version", "corutv_status_string", "corutv_create", "corutv_de
            "corutv_workspace_size", "corutv_set_workspace", "corutv_solve", "corutv_info_wait",
            "corutv_set_tracing", "corutv_trace_read", "corutv_pass", "corutv_orthonormalize", "corutv_gram",
            "corutv_qrcp", "corutv_fro2", "corutv_gram_noalloc", "corutv_solve_corrected", "corutv_quantize",
-           "corutv_batch_workspace_size", "corutv_solve_batched", "corutv_batch_info_wait")
+           "corutv_batch_workspace_size", "corutv_solve_batched", "corutv_batch_info_wait",
+           "corutv_server_create", "corutv_server_submit", "corutv_server_poll", "corutv_server_stats",
+           "corutv_server_destroy")
 
 
 def load() -> ctypes.CDLL:
@@ -104,6 +106,11 @@ def load() -> ctypes.CDLL:
     lib.corutv_batch_workspace_size.argtypes = [ctypes.c_int, ctypes.POINTER(Problem), ctypes.POINTER(ctypes.c_size_t)]
     lib.corutv_solve_batched.argtypes = [P, ctypes.c_int, ctypes.POINTER(Problem), ctypes.POINTER(Info)]
     lib.corutv_batch_info_wait.argtypes = [P, ctypes.c_int, ctypes.POINTER(Info)]
+    lib.corutv_server_create.argtypes = [ctypes.POINTER(P), ctypes.c_int, ctypes.c_size_t, ctypes.c_int, ctypes.c_int]
+    lib.corutv_server_submit.argtypes = [P, ctypes.POINTER(Problem), ctypes.POINTER(ctypes.c_uint64)]
+    lib.corutv_server_poll.argtypes = [P, ctypes.c_uint64, ctypes.POINTER(Info)]
+    lib.corutv_server_stats.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I64)]
+    lib.corutv_server_destroy.argtypes = [P]
     lib.corutv_info_wait.argtypes = [P, ctypes.POINTER(Info)]
     lib.corutv_pass.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, I64, I64, I64, P, P, I64, I32, P,
                                 I64]
@@ -119,7 +126,8 @@ def load() -> ctypes.CDLL:
                  "corutv_set_workspace", "corutv_solve", "corutv_info_wait", "corutv_pass",
                  "corutv_orthonormalize", "corutv_gram", "corutv_qrcp", "corutv_fro2", "corutv_solve_corrected",
                  "corutv_quantize", "corutv_batch_workspace_size", "corutv_solve_batched",
-                 "corutv_batch_info_wait"):
+                 "corutv_batch_info_wait", "corutv_server_create", "corutv_server_submit", "corutv_server_poll",
+                 "corutv_server_stats", "corutv_server_destroy"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -325,6 +333,90 @@ def quantize(A, dtype: str, out=None, tile_scales=None, handle: Handle | None = 
     return (out, tile_scales) if code == 3 else (out, None)
 
 
+def _fill_problem(p, it):
+    """Fill a Problem struct from an item dict; returns the allocated SolveResult."""
+    import torch
+    A, Phi = it["A"], it["Phi"]
+    _need_cuda(A, Phi, it.get("a_tile_scales"))
+    m, n = A.shape
+    l = int(it["l"])
+    if Phi.dtype != torch.float32:
+        raise TypeError("Phi must be float32")
+    U = torch.empty((m, l), dtype=torch.float32, device=A.device)
+    T = torch.empty((l, l), dtype=torch.float64, device=A.device)
+    V = torch.empty((n, l), dtype=torch.float32, device=A.device)
+    perm = torch.empty((l,), dtype=torch.int32, device=A.device)
+    p.m, p.n, p.k, p.l, p.q = m, n, int(it["k"]), l, int(it.get("q", 0))
+    p.side = SIDE[it.get("side", "right")]
+    p.core = CORE[it.get("core", "exact")]
+    p.orth = ORTH[it.get("orth", "stabilised")]
+    p.a_dtype = _dt_code(A)
+    p.mma = MMA[it.get("mma", "auto")]
+    p.want_fro2 = 1 if it.get("want_fro2", False) else 0
+    sc = it.get("a_tile_scales")
+    p.A, p.lda = A.data_ptr(), _rowmajor_ld(A)
+    p.a_tile_scales = sc.data_ptr() if sc is not None else None
+    p.Phi, p.ldphi = Phi.data_ptr(), _rowmajor_ld(Phi)
+    p.U, p.ldu = U.data_ptr(), _rowmajor_ld(U)
+    p.T, p.ldt = T.data_ptr(), _rowmajor_ld(T)
+    p.V, p.ldv = V.data_ptr(), _rowmajor_ld(V)
+    p.perm = perm.data_ptr()
+    return SolveResult(U, T, V, perm, None)
+
+
+class Server:
+    """corutv_server: submit solves (item dicts as for Batch) and poll them.
+
+    The Server keeps each request's tensors alive until it has been polled as
+    finished."""
+
+    def __init__(self, hbm_budget: int, max_slots: int = 64, queue_capacity: int = 4096, device: int | None = None):
+        import torch
+        self.device = torch.cuda.current_device() if device is None else device
+        self.s = ctypes.c_void_p()
+        _check(load().corutv_server_create(ctypes.byref(self.s), self.device, int(hbm_budget), int(max_slots),
+                                           int(queue_capacity)), "corutv_server_create")
+        self.live = {}
+
+    def submit(self, item):
+        """Queue one solve; returns the ticket.  Raises CorutvError (ERR_BUSY when the queue is full)."""
+        p = Problem()
+        res = _fill_problem(p, item)
+        t = ctypes.c_uint64()
+        _check(load().corutv_server_submit(self.s, ctypes.byref(p), ctypes.byref(t)), "corutv_server_submit")
+        self.live[t.value] = (item, res)
+        return t.value
+
+    def poll(self, ticket: int):
+        """None while pending; else (status, SolveResult) and the ticket is released."""
+        info = Info()
+        rc = load().corutv_server_poll(self.s, ctypes.c_uint64(ticket), ctypes.byref(info))
+        if rc == PENDING:
+            return None
+        if rc == ERR_INVALID_ARG and ticket not in self.live:
+            raise CorutvError(rc, "corutv_server_poll")
+        item, res = self.live.pop(ticket)
+        res.info = info
+        return rc, res
+
+    def stats(self):
+        b, s, p = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(load().corutv_server_stats(self.s, ctypes.byref(b), ctypes.byref(s), ctypes.byref(p)),
+               "corutv_server_stats")
+        return dict(batches=b.value, solved=s.value, pending=p.value)
+
+    def close(self):
+        if self.s:
+            load().corutv_server_destroy(self.s)
+            self.s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Batch:
     """A fixed set of problems for corutv_solve_batched.
 
@@ -341,35 +433,7 @@ class Batch:
         self.items = list(items)
         self.count = len(self.items)
         self.arr = (Problem * self.count)()
-        self.results = []
-        for i, it in enumerate(self.items):
-            A, Phi = it["A"], it["Phi"]
-            _need_cuda(A, Phi, it.get("a_tile_scales"))
-            m, n = A.shape
-            l = int(it["l"])
-            if Phi.dtype != torch.float32:
-                raise TypeError("Phi must be float32")
-            U = torch.empty((m, l), dtype=torch.float32, device=A.device)
-            T = torch.empty((l, l), dtype=torch.float64, device=A.device)
-            V = torch.empty((n, l), dtype=torch.float32, device=A.device)
-            perm = torch.empty((l,), dtype=torch.int32, device=A.device)
-            p = self.arr[i]
-            p.m, p.n, p.k, p.l, p.q = m, n, int(it["k"]), l, int(it.get("q", 0))
-            p.side = SIDE[it.get("side", "right")]
-            p.core = CORE[it.get("core", "exact")]
-            p.orth = ORTH[it.get("orth", "stabilised")]
-            p.a_dtype = _dt_code(A)
-            p.mma = MMA[it.get("mma", "auto")]
-            p.want_fro2 = 1 if it.get("want_fro2", False) else 0
-            sc = it.get("a_tile_scales")
-            p.A, p.lda = A.data_ptr(), _rowmajor_ld(A)
-            p.a_tile_scales = sc.data_ptr() if sc is not None else None
-            p.Phi, p.ldphi = Phi.data_ptr(), _rowmajor_ld(Phi)
-            p.U, p.ldu = U.data_ptr(), _rowmajor_ld(U)
-            p.T, p.ldt = T.data_ptr(), _rowmajor_ld(T)
-            p.V, p.ldv = V.data_ptr(), _rowmajor_ld(V)
-            p.perm = perm.data_ptr()
-            self.results.append(SolveResult(U, T, V, perm, None))
+        self.results = [_fill_problem(self.arr[i], it) for i, it in enumerate(self.items)]
 
     def workspace_size(self) -> int:
         out = ctypes.c_size_t()
