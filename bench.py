@@ -331,7 +331,9 @@ def main_batched(args):
     items = []
     for p in probs:
         side = "left" if p.m < p.n else "right"
-        A = p.content.dense_t(device=dev, dtype=torch.float32)
+        # rows padded to a 16-byte pitch so the tensor-core passes can read them by TMA
+        A = torch.zeros((p.m, -(-p.n // 4) * 4), dtype=torch.float32, device=dev)[:, :p.n]
+        A.copy_(p.content.dense_t(device=dev, dtype=torch.float32))
         phi = W.problem_phi_t(p, p.m if side == "left" else p.n, device=dev).float()
         items.append(dict(A=A, Phi=phi, k=p.k, l=p.l, q=w["q"], side=side, want_fro2=True))
     stream = torch.cuda.current_stream()
@@ -376,10 +378,12 @@ def main_batched(args):
     avg_pass_ms = tr.pass_ms / max(tr.pass_launches, 1)
     bytes_per_pass = tr.pass_bytes / max(tr.pass_launches, 1)
     achieved = bytes_per_pass / (avg_pass_ms / 1e3) / 1e9
-    tkey = f"pass_simt_grouped_kernel/f32/config4x{count}/src-" + kernel_source_tag("pass_simt.cu", "elem.cuh")
+    tkey = f"pass_tc_grouped_kernel/f32/config4x{count}/src-" + kernel_source_tag("pass_tc_grouped.cu",
+                                                                                     "tc_common.cuh")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_source": peak_src,
-                "kernel": "pass_simt_grouped_kernel (all problems' A X or A^T Y in one launch, CUDA cores)",
+                "kernel": "pass_tc_grouped_kernel (all problems' A X or A^T Y in one TF32 launch) incl. operand "
+                          "rounding and split-tile reduce",
                 "bytes_per_launch": bytes_per_pass, "ms_per_launch": avg_pass_ms,
                 "traffic": traffic_from_profiles(tkey), "timing": "two traced, uncaptured runs of the batch"}
 

@@ -1,9 +1,13 @@
 // Batched CoR-UTV solves (corutv_solve_batched): the schedule of one solve
 // (Alg. 2 / Alg. 3, stabilised range finding) with every step a grouped launch
 // over all problems of the batch.  The host builds, once per problem set, a
-// device table of per-problem descriptors (BatchProb) and block -> (problem,
-// local block) maps for each kind of grouped launch; repeated calls with the
-// same problem set replay a CUDA graph of the whole sequence.
+// device table of per-problem descriptors (BatchProb), block -> (problem,
+// local block) maps for each kind of grouped launch and, for FP32 batches the
+// tensor cores can read, one table per grouped TF32 pass (GPassProb) with the
+// problems' tensor maps; repeated calls with the same problem set replay a
+// CUDA graph of the whole sequence.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
@@ -16,8 +20,22 @@
 #include "common.cuh"
 #include "handle.h"
 #include "internal.h"
+#include "tc_common.cuh"
 
 namespace corutv {
+
+// one grouped TF32 pass (its problem table lives in the device tables)
+struct PassTable {
+  int which = 0, it = 0;
+  size_t off_gp = 0, off_rmap = 0;
+  int np = 0, nround = 0;
+  int64_t iters = 0, tiles = 0;
+  int lmax = 1;
+  bool fro = false;
+  double bytes = 0.0;
+  GPassProb* d_gp = nullptr;
+  int2* d_rmap = nullptr;
+};
 
 struct BatchState {
   std::vector<unsigned char> key;     // bytes of the problem array the tables were built for
@@ -28,6 +46,8 @@ struct BatchState {
   size_t table_bytes = 0;
   BatchProb* dprobs = nullptr;
   DevStatus* dstatus = nullptr;
+  DevStatus* bstatus = nullptr;       // batch-wide (timeouts of the grouped tensor-core passes)
+  float* partials = nullptr;
   int count = 0;
   std::vector<int> passes;            // passes over A per problem
   std::vector<int> want_fro2;
@@ -37,8 +57,10 @@ struct BatchState {
   int nt1 = 0, nt2 = 0, ng1 = 0, ng2 = 0, nred = 0, nlm1 = 0, nlm2 = 0, ns2 = 0;
   int lp = 32, lmax = 1, maxq = 0, a_dtype = CORUTV_F32;
   bool any_exact = false, any_sketch = false, any_fro2 = false;
+  bool tc = false;                    // passes on the tensor cores
+  std::vector<PassTable> ptabs;       // index 2 * it + which (C1, C2), then the core pass
   std::vector<char> multi_pass;       // per power step: some problem runs more than one CholeskyQR pass
-  std::vector<double> pass_bytes;     // algorithmic bytes of each grouped pass: [3 * it + which]
+  std::vector<double> pass_bytes;     // SIMT passes: algorithmic bytes, [3 * it + which]
   cudaGraphExec_t exec = nullptr;
   int64_t launches_per_run = 0;
 };
@@ -60,6 +82,7 @@ namespace {
 constexpr size_t kBAlign = 256;
 
 size_t align_up(size_t x) { return (x + kBAlign - 1) / kBAlign * kBAlign; }
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
 int validate(const corutv_problem& p) {
   if (p.reserved0) return CORUTV_ERR_INVALID_ARG;
@@ -67,10 +90,9 @@ int validate(const corutv_problem& p) {
     if (r) return CORUTV_ERR_INVALID_ARG;
   if (p.a_dtype == CORUTV_F64) return CORUTV_ERR_UNSUPPORTED;
   if (p.a_dtype < CORUTV_F32 || p.a_dtype > CORUTV_FP8_E4M3) return CORUTV_ERR_INVALID_ARG;
-  if (p.mma != CORUTV_MMA_AUTO && p.mma != CORUTV_MMA_SIMT) {
-    if (p.mma < CORUTV_MMA_AUTO || p.mma > CORUTV_MMA_BF16X2) return CORUTV_ERR_INVALID_ARG;
+  if (p.mma < CORUTV_MMA_AUTO || p.mma > CORUTV_MMA_BF16X2) return CORUTV_ERR_INVALID_ARG;
+  if (p.mma != CORUTV_MMA_AUTO && p.mma != CORUTV_MMA_SIMT && !(p.mma == CORUTV_MMA_TF32 && p.a_dtype == CORUTV_F32))
     return CORUTV_ERR_UNSUPPORTED;
-  }
   if (p.side != CORUTV_SIDE_RIGHT && p.side != CORUTV_SIDE_LEFT) return CORUTV_ERR_INVALID_ARG;
   if (p.core != CORUTV_CORE_EXACT && p.core != CORUTV_CORE_SKETCH) return CORUTV_ERR_INVALID_ARG;
   if (p.orth != CORUTV_ORTH_STABILISED && p.orth != CORUTV_ORTH_STRICT) return CORUTV_ERR_INVALID_ARG;
@@ -81,17 +103,29 @@ int validate(const corutv_problem& p) {
   if (!p.A || !p.Phi || !p.U || !p.T || !p.V || !p.perm) return CORUTV_ERR_INVALID_ARG;
   if (p.a_dtype == CORUTV_FP8_E4M3 && !p.a_tile_scales) return CORUTV_ERR_INVALID_ARG;
   if (p.lda < p.n || p.ldphi < p.l || p.ldu < p.l || p.ldt < p.l || p.ldv < p.l) return CORUTV_ERR_SHAPE;
+  if (p.mma == CORUTV_MMA_TF32 && !(aligned16(p.A) && (p.lda * 4) % 16 == 0)) return CORUTV_ERR_ALIGN;
   return CORUTV_OK;
+}
+
+// TF32 tensor-core passes for the whole batch: FP32 A whose rows TMA can address,
+// no problem asking for SIMT.
+bool batch_uses_tc(int count, const corutv_problem* probs) {
+  for (int i = 0; i < count; ++i) {
+    const corutv_problem& p = probs[i];
+    if (p.a_dtype != CORUTV_F32 || p.mma == CORUTV_MMA_SIMT) return false;
+    if (!(aligned16(p.A) && (p.lda * 4) % 16 == 0)) return false;
+  }
+  return true;
 }
 
 // Sizes of one problem's buffers (FP32 sketches and factors, FP64 l x l blocks).
 struct ProbSizes {
   int64_t len1, len2, ld1, ld2, ld3;
   int gp1, gp2, nf;
-  size_t sk1, sk2, sk3, gparts, ll8, ll4, defic, fparts, status;
+  size_t sk1, sk2, sk3, xr, gparts, ll8, ll4, defic, fparts, status;
 };
 
-ProbSizes prob_sizes(const corutv_problem& p, int lp) {
+ProbSizes prob_sizes(const corutv_problem& p, int lp, bool tc) {
   ProbSizes z{};
   const bool right = p.side == CORUTV_SIDE_RIGHT;
   z.len1 = right ? p.m : p.n;
@@ -105,6 +139,7 @@ ProbSizes prob_sizes(const corutv_problem& p, int lp) {
   z.sk1 = sizeof(float) * p.l * z.ld1;
   z.sk2 = sizeof(float) * p.l * z.ld2;
   z.sk3 = sizeof(float) * p.l * z.ld3;
+  z.xr = tc ? z.sk3 : 0;
   z.gparts = sizeof(float) * (size_t)std::max(z.gp1, z.gp2) * lp * lp;
   z.ll8 = sizeof(double) * p.l * p.l;
   z.ll4 = sizeof(float) * p.l * p.l;
@@ -115,27 +150,14 @@ ProbSizes prob_sizes(const corutv_problem& p, int lp) {
 }
 
 size_t prob_bytes(const ProbSizes& z) {
-  return align_up(z.sk1) + align_up(z.sk2) + align_up(z.sk3) + align_up(z.gparts) + 3 * align_up(z.ll8) +
-         2 * align_up(z.ll4) + align_up(z.defic) + align_up(z.fparts) + align_up(z.status);
+  return align_up(z.sk1) + align_up(z.sk2) + align_up(z.sk3) + align_up(z.xr) + align_up(z.gparts) +
+         3 * align_up(z.ll8) + 2 * align_up(z.ll4) + align_up(z.defic) + align_up(z.fparts) + align_up(z.status);
 }
 
 int lp_for(int lmax) { return lmax <= 32 ? 32 : (lmax <= 64 ? 64 : 128); }
 
-// Host tables: the BatchProb array then the block maps, in one contiguous block.
-struct Tables {
-  std::vector<BatchProb> probs;
-  std::vector<int2> t1, t2, g1, g2, red, lm1, lm2, s2;
-};
-
 void add_blocks(std::vector<int2>& v, int p, int64_t n) {
   for (int64_t b = 0; b < n; ++b) v.push_back(make_int2(p, (int)b));
-}
-
-size_t tables_bytes(const Tables& t, int count) {
-  size_t b = align_up(sizeof(BatchProb) * count);
-  for (const std::vector<int2>* v : {&t.t1, &t.t2, &t.g1, &t.g2, &t.red, &t.lm1, &t.lm2, &t.s2})
-    b += align_up(sizeof(int2) * std::max<size_t>(1, v->size()));
-  return b;
 }
 
 #define CUB(x)                                                                         \
@@ -147,170 +169,304 @@ size_t tables_bytes(const Tables& t, int count) {
     }                                                                                  \
   } while (0)
 
+// Host-side plan: every table and its byte offset in the uploaded tables region.
+struct Plan {
+  int count = 0, lp = 32, lmax = 1, maxq = 0;
+  bool tc = false;
+  std::vector<ProbSizes> sz;
+  std::vector<int2> maps[8];          // t1, t2, g1, g2, red, lm1, lm2, s2
+  size_t off_maps[8] = {};
+  std::vector<PassTable> ptabs;
+  std::vector<std::vector<int>> pt_probs;     // problems of each pass table
+  std::vector<std::vector<int2>> pt_rmaps;
+  std::vector<std::vector<int64_t>> pt_fro;   // fro slots per problem of the table (0: none)
+  size_t off_tmaps = 0, off_fro = 0, table_bytes = 0, total_fro = 0;
+  size_t off_status = 0, off_bstatus = 0, off_partials = 0, off_probs = 0, need = 0;
+};
+
+void make_plan(Plan& L, int count, const corutv_problem* probs, int sms) {
+  L.count = count;
+  for (int i = 0; i < count; ++i) {
+    L.lmax = std::max(L.lmax, (int)probs[i].l);
+    L.maxq = std::max(L.maxq, (int)probs[i].q);
+  }
+  L.lp = lp_for(L.lmax);
+  L.tc = batch_uses_tc(count, probs);
+  L.sz.resize(count);
+  for (int i = 0; i < count; ++i) {
+    const corutv_problem& p = probs[i];
+    const ProbSizes& z = L.sz[i] = prob_sizes(p, L.lp, L.tc);
+    add_blocks(L.maps[0], i, cdiv(z.len1, kBatchPassBN));
+    add_blocks(L.maps[1], i, cdiv(z.len2, kBatchPassBN));
+    add_blocks(L.maps[2], i, z.gp1);
+    add_blocks(L.maps[3], i, z.gp2);
+    add_blocks(L.maps[4], i, cdiv((int64_t)4 * p.l * p.l, 256));
+    add_blocks(L.maps[5], i, cdiv(z.len1, kBatchLmulBI));
+    add_blocks(L.maps[6], i, cdiv(z.len2, kBatchLmulBI));
+    add_blocks(L.maps[7], i, cdiv(z.len2, kBatchTile32));
+  }
+  size_t off = align_up(sizeof(BatchProb) * count);
+  for (int k = 0; k < 8; ++k) {
+    L.off_maps[k] = off;
+    off += align_up(sizeof(int2) * std::max<size_t>(1, L.maps[k].size()));
+  }
+  if (L.tc) {
+    // pass tables: (C1, C2) of every power step, then the exact-core pass
+    for (int t = 0; t < 2 * (L.maxq + 1) + 1; ++t) {
+      PassTable T;
+      T.which = t < 2 * (L.maxq + 1) ? t % 2 : kB_CORE;
+      T.it = t < 2 * (L.maxq + 1) ? t / 2 : 0;
+      std::vector<int> members;
+      std::vector<int2> rmap;
+      for (int i = 0; i < count; ++i) {
+        const corutv_problem& p = probs[i];
+        const bool in = T.which == kB_CORE ? p.core == CORUTV_CORE_EXACT : T.it <= p.q;
+        if (!in) continue;
+        const ProbSizes& z = L.sz[i];
+        const int64_t len = T.which == kB_C2 ? z.len2 : z.len1, K = T.which == kB_C2 ? z.len1 : z.len2;
+        T.iters += tc_grouped_tiles(len) * tc_grouped_kblocks(K);
+        T.tiles += tc_grouped_tiles(len);
+        T.lmax = std::max(T.lmax, (int)p.l);
+        const int eb = 4;
+        T.bytes += (double)p.m * p.n * eb + 4.0 * p.l * (double)(len + K);
+        add_blocks(rmap, (int)members.size(), cdiv(K, 128));
+        members.push_back(i);
+      }
+      T.np = (int)members.size();
+      T.nround = (int)rmap.size();
+      std::vector<int64_t> fro(members.size(), 0);
+      if (T.which == kB_C1 && T.it == 0 && T.np > 0) {
+        const int64_t G = std::min<int64_t>(T.iters, sms);
+        int64_t base = 0;
+        for (size_t u = 0; u < members.size(); ++u) {
+          const int i = members[u];
+          const ProbSizes& z = L.sz[i];
+          const int64_t iters = tc_grouped_tiles(z.len1) * tc_grouped_kblocks(z.len2);
+          if (probs[i].want_fro2) {
+            fro[u] = 4 * (tc_grouped_owner(base + iters - 1, T.iters, G) - tc_grouped_owner(base, T.iters, G) + 1);
+            T.fro = true;
+            L.total_fro += (size_t)fro[u];
+          }
+          base += iters;
+        }
+      }
+      T.off_gp = off;
+      off += align_up(sizeof(GPassProb) * std::max(1, T.np));
+      T.off_rmap = off;
+      off += align_up(sizeof(int2) * std::max(1, T.nround));
+      L.ptabs.push_back(T);
+      L.pt_probs.push_back(members);
+      L.pt_rmaps.push_back(rmap);
+      L.pt_fro.push_back(fro);
+    }
+    L.off_tmaps = off;                              // 4 tensor maps per problem, 128 B each
+    off += align_up(sizeof(CUtensorMap) * 4 * (size_t)count);
+  }
+  L.table_bytes = off;                              // uploaded part
+  L.off_fro = off;
+  off += align_up(sizeof(double) * std::max<size_t>(1, L.total_fro));
+  L.off_status = off;
+  off += align_up(sizeof(DevStatus) * count);
+  L.off_bstatus = off;
+  off += align_up(sizeof(DevStatus));
+  L.off_partials = off;
+  if (L.tc) off += align_up(tc_grouped_partial_bytes(sms));
+  L.off_probs = off;
+  for (int i = 0; i < count; ++i) off += prob_bytes(L.sz[i]);
+  L.need = off;
+}
+
 // Build tables and buffers for a new problem set (the stream is idle).
 int build(corutv_handle* h, BatchState* B, int count, const corutv_problem* probs) {
-  int lmax = 1, maxq = 0;
-  for (int i = 0; i < count; ++i) {
-    lmax = std::max(lmax, (int)probs[i].l);
-    maxq = std::max(maxq, (int)probs[i].q);
-  }
-  const int lp = lp_for(lmax);
-  Tables T;
-  T.probs.resize(count);
-  std::vector<ProbSizes> sz(count);
-  size_t per = 0;
-  for (int i = 0; i < count; ++i) {
-    sz[i] = prob_sizes(probs[i], lp);
-    per += prob_bytes(sz[i]);
-    const corutv_problem& p = probs[i];
-    add_blocks(T.t1, i, cdiv(sz[i].len1, kBatchPassBN));
-    add_blocks(T.t2, i, cdiv(sz[i].len2, kBatchPassBN));
-    add_blocks(T.g1, i, sz[i].gp1);
-    add_blocks(T.g2, i, sz[i].gp2);
-    add_blocks(T.red, i, cdiv((int64_t)4 * p.l * p.l, 256));
-    add_blocks(T.lm1, i, cdiv(sz[i].len1, kBatchLmulBI));
-    add_blocks(T.lm2, i, cdiv(sz[i].len2, kBatchLmulBI));
-    add_blocks(T.s2, i, cdiv(sz[i].len2, kBatchTile32));
-  }
-  const size_t tb = tables_bytes(T, count);
-  const size_t need = tb + align_up(sizeof(DevStatus) * count) + per;
-  if (!B->ws || B->ws_bytes < need) {
+  Plan L;
+  make_plan(L, count, probs, h->sms);
+  if (!B->ws || B->ws_bytes < L.need) {
     if (B->ws) cudaFree(B->ws);
     B->ws = nullptr;
     B->ws_bytes = 0;
-    if (cudaMalloc(&B->ws, need) != cudaSuccess) {
+    if (cudaMalloc(&B->ws, L.need) != cudaSuccess) {
       cudaGetLastError();
       return CORUTV_ERR_OOM;
     }
-    B->ws_bytes = need;
+    B->ws_bytes = L.need;
   }
-  if (!B->host || B->host_bytes < tb) {
+  if (!B->host || B->host_bytes < L.table_bytes) {
     if (B->host) cudaFreeHost(B->host);
     B->host = nullptr;
     B->host_bytes = 0;
-    if (cudaMallocHost(&B->host, tb) != cudaSuccess) {
+    if (cudaMallocHost(&B->host, L.table_bytes) != cudaSuccess) {
       cudaGetLastError();
       return CORUTV_ERR_OOM;
     }
-    B->host_bytes = tb;
+    B->host_bytes = L.table_bytes;
   }
   char* d = static_cast<char*>(B->ws);
-  char* hbase = static_cast<char*>(B->host);
-  // the tables: same offsets on host and device
-  size_t off = 0;
-  B->dprobs = reinterpret_cast<BatchProb*>(d + off);
-  off += align_up(sizeof(BatchProb) * count);
-  auto place = [&](std::vector<int2>& v, int2** dptr, int* n) {
-    *dptr = reinterpret_cast<int2*>(d + off);
-    *n = (int)v.size();
-    if (!v.empty()) memcpy(hbase + off, v.data(), sizeof(int2) * v.size());
-    off += align_up(sizeof(int2) * std::max<size_t>(1, v.size()));
-  };
-  place(T.t1, &B->t1, &B->nt1);
-  place(T.t2, &B->t2, &B->nt2);
-  place(T.g1, &B->g1, &B->ng1);
-  place(T.g2, &B->g2, &B->ng2);
-  place(T.red, &B->red, &B->nred);
-  place(T.lm1, &B->lm1, &B->nlm1);
-  place(T.lm2, &B->lm2, &B->nlm2);
-  place(T.s2, &B->s2, &B->ns2);
-  B->table_bytes = off;
-  // statuses, then the per-problem buffers
-  B->dstatus = reinterpret_cast<DevStatus*>(d + off);
-  off += align_up(sizeof(DevStatus) * count);
+  char* hb = static_cast<char*>(B->host);
+  memset(hb, 0, L.table_bytes);
+  B->dprobs = reinterpret_cast<BatchProb*>(d);
+  int2** mp[8] = {&B->t1, &B->t2, &B->g1, &B->g2, &B->red, &B->lm1, &B->lm2, &B->s2};
+  int* mn[8] = {&B->nt1, &B->nt2, &B->ng1, &B->ng2, &B->nred, &B->nlm1, &B->nlm2, &B->ns2};
+  for (int k = 0; k < 8; ++k) {
+    *mp[k] = reinterpret_cast<int2*>(d + L.off_maps[k]);
+    *mn[k] = (int)L.maps[k].size();
+    if (!L.maps[k].empty()) memcpy(hb + L.off_maps[k], L.maps[k].data(), sizeof(int2) * L.maps[k].size());
+  }
+  B->dstatus = reinterpret_cast<DevStatus*>(d + L.off_status);
+  B->bstatus = reinterpret_cast<DevStatus*>(d + L.off_bstatus);
+  B->partials = L.tc ? reinterpret_cast<float*>(d + L.off_partials) : nullptr;
   B->passes.assign(count, 0);
   B->want_fro2.assign(count, 0);
-  B->multi_pass.assign(maxq + 1, 0);
+  B->multi_pass.assign(L.maxq + 1, 0);
   B->any_exact = B->any_sketch = B->any_fro2 = false;
+  std::vector<BatchProb> P(count);
+  size_t off = L.off_probs;
   for (int i = 0; i < count; ++i) {
     const corutv_problem& p = probs[i];
-    const ProbSizes& z = sz[i];
-    BatchProb& P = T.probs[i];
-    memset(&P, 0, sizeof(P));
-    P.A = p.A;
-    P.lda = p.lda;
-    P.scales = p.a_tile_scales;
-    P.sld = cdiv(p.n, 128);
-    P.Phi = static_cast<const float*>(p.Phi);
-    P.ldphi = p.ldphi;
-    P.U = static_cast<float*>(p.U);
-    P.ldu = p.ldu;
-    P.T = p.T;
-    P.ldt = p.ldt;
-    P.V = static_cast<float*>(p.V);
-    P.ldv = p.ldv;
-    P.perm = p.perm;
-    P.m = p.m;
-    P.n = p.n;
-    P.len1 = z.len1;
-    P.len2 = z.len2;
-    P.l = p.l;
-    P.k = p.k;
-    P.q = p.q;
-    P.side = p.side;
-    P.core = p.core;
-    P.orth = p.orth;
-    P.want_fro2 = p.want_fro2 ? 1 : 0;
+    const ProbSizes& z = L.sz[i];
+    BatchProb& Q = P[i];
+    memset(&Q, 0, sizeof(Q));
+    Q.A = p.A;
+    Q.lda = p.lda;
+    Q.scales = p.a_tile_scales;
+    Q.sld = cdiv(p.n, 128);
+    Q.Phi = static_cast<const float*>(p.Phi);
+    Q.ldphi = p.ldphi;
+    Q.U = static_cast<float*>(p.U);
+    Q.ldu = p.ldu;
+    Q.T = p.T;
+    Q.ldt = p.ldt;
+    Q.V = static_cast<float*>(p.V);
+    Q.ldv = p.ldv;
+    Q.perm = p.perm;
+    Q.m = p.m;
+    Q.n = p.n;
+    Q.len1 = z.len1;
+    Q.len2 = z.len2;
+    Q.l = p.l;
+    Q.k = p.k;
+    Q.q = p.q;
+    Q.side = p.side;
+    Q.core = p.core;
+    Q.orth = p.orth;
+    Q.want_fro2 = p.want_fro2 ? 1 : 0;
     const bool right = p.side == CORUTV_SIDE_RIGHT;
-    P.dir1 = right ? CORUTV_DIR_AX : CORUTV_DIR_ATY;
-    P.dir2 = right ? CORUTV_DIR_ATY : CORUTV_DIR_AX;
-    P.ld1 = z.ld1;
-    P.ld2 = z.ld2;
-    P.ld3 = z.ld3;
-    P.gp1 = z.gp1;
-    P.gp2 = z.gp2;
-    P.nfparts = z.nf;
-    P.status = B->dstatus + i;
-    P.P1 = reinterpret_cast<float*>(d + off);
-    off += align_up(z.sk1);
-    P.P2 = reinterpret_cast<float*>(d + off);
-    off += align_up(z.sk2);
-    P.P3 = reinterpret_cast<float*>(d + off);
-    off += align_up(z.sk3);
-    P.gparts = reinterpret_cast<float*>(d + off);
-    off += align_up(z.gparts);
-    P.G = reinterpret_cast<double*>(d + off);
-    off += align_up(z.ll8);
-    P.D = reinterpret_cast<double*>(d + off);
-    off += align_up(z.ll8);
-    P.Qt = reinterpret_cast<double*>(d + off);
-    off += align_up(z.ll8);
-    P.R = reinterpret_cast<float*>(d + off);
-    off += align_up(z.ll4);
-    P.Rinv = reinterpret_cast<float*>(d + off);
-    off += align_up(z.ll4);
-    P.defic = reinterpret_cast<int*>(d + off);
-    off += align_up(z.defic);
-    P.fparts = reinterpret_cast<double*>(d + off);
-    off += align_up(z.fparts);
-    off += align_up(z.status);
+    Q.dir1 = right ? CORUTV_DIR_AX : CORUTV_DIR_ATY;
+    Q.dir2 = right ? CORUTV_DIR_ATY : CORUTV_DIR_AX;
+    Q.ld1 = z.ld1;
+    Q.ld2 = z.ld2;
+    Q.ld3 = z.ld3;
+    Q.gp1 = z.gp1;
+    Q.gp2 = z.gp2;
+    Q.nfparts = z.nf;
+    Q.status = B->dstatus + i;
+    auto take = [&](size_t bytes) {
+      char* r = d + off;
+      off += align_up(bytes);
+      return r;
+    };
+    Q.P1 = reinterpret_cast<float*>(take(z.sk1));
+    Q.P2 = reinterpret_cast<float*>(take(z.sk2));
+    Q.P3 = reinterpret_cast<float*>(take(z.sk3));
+    float* Xr = reinterpret_cast<float*>(take(z.xr));
+    Q.gparts = reinterpret_cast<float*>(take(z.gparts));
+    Q.G = reinterpret_cast<double*>(take(z.ll8));
+    Q.D = reinterpret_cast<double*>(take(z.ll8));
+    Q.Qt = reinterpret_cast<double*>(take(z.ll8));
+    Q.R = reinterpret_cast<float*>(take(z.ll4));
+    Q.Rinv = reinterpret_cast<float*>(take(z.ll4));
+    Q.defic = reinterpret_cast<int*>(take(z.defic));
+    Q.fparts = reinterpret_cast<double*>(take(z.fparts));
+    take(z.status);
+    if (L.tc) {
+      // tensor maps: A rows (dir AX), A columns (dir ATY), Xr over len1 and over len2 columns
+      CUtensorMap* tm = reinterpret_cast<CUtensorMap*>(hb + L.off_tmaps) + 4 * i;
+      bool ok = make_map_2d(&tm[0], p.A, p.m, p.n, p.lda, 4, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 32, 256, true) &&
+                make_map_2d(&tm[1], p.A, p.m, p.n, p.lda, 4, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 32, 32, true) &&
+                make_map_2d(&tm[2], Xr, p.l, z.len1, z.ld3, 4, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 32, 128, true) &&
+                make_map_2d(&tm[3], Xr, p.l, z.len2, z.ld3, 4, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 32, 128, true);
+      if (!ok) return CORUTV_ERR_CUDA;
+    }
     B->passes[i] = 2 * (p.q + 1) + (p.core == CORUTV_CORE_EXACT ? 1 : 0);
-    B->want_fro2[i] = P.want_fro2;
+    B->want_fro2[i] = Q.want_fro2;
     B->any_exact |= p.core == CORUTV_CORE_EXACT;
     B->any_sketch |= p.core == CORUTV_CORE_SKETCH;
-    B->any_fro2 |= P.want_fro2 != 0;
+    B->any_fro2 |= Q.want_fro2 != 0;
     for (int it = 0; it <= p.q; ++it)
       if (it == p.q || p.orth == CORUTV_ORTH_STRICT) B->multi_pass[it] = 1;
+    (void)Xr;   // the pass tables find it right after P3 (carve order above)
   }
-  // algorithmic bytes of every grouped pass (A as stored + sketch operand + result of the
-  // problems taking part): index 3 * it + which, the core pass at 3 * (maxq + 1) + kB_CORE
-  B->pass_bytes.assign(3 * (maxq + 2), 0.0);
+  // pass tables (TF32 tensor cores)
+  B->tc = L.tc;
+  B->ptabs = L.ptabs;
+  if (L.tc) {
+    const CUtensorMap* dmaps = reinterpret_cast<const CUtensorMap*>(d + L.off_tmaps);
+    double* fro_base = reinterpret_cast<double*>(d + L.off_fro);
+    size_t fro_used = 0;
+    for (size_t t = 0; t < L.ptabs.size(); ++t) {
+      PassTable& T = B->ptabs[t];
+      T.d_gp = reinterpret_cast<GPassProb*>(d + T.off_gp);
+      T.d_rmap = reinterpret_cast<int2*>(d + T.off_rmap);
+      if (!L.pt_rmaps[t].empty())
+        memcpy(hb + T.off_rmap, L.pt_rmaps[t].data(), sizeof(int2) * L.pt_rmaps[t].size());
+      GPassProb* gpv = reinterpret_cast<GPassProb*>(hb + T.off_gp);
+      const int64_t G = std::min<int64_t>(T.iters, h->sms);
+      int64_t ibase = 0, tbase = 0;
+      for (int u = 0; u < T.np; ++u) {
+        const int i = L.pt_probs[t][u];
+        const BatchProb& Q = P[i];
+        const ProbSizes& z = L.sz[i];
+        GPassProb& g = gpv[u];
+        const bool second = T.which == kB_C2;
+        const int dir = second ? Q.dir2 : Q.dir1;
+        g.mapA = dmaps + 4 * i + (dir == CORUTV_DIR_AX ? 0 : 1);
+        g.mapX = dmaps + 4 * i + (second ? 2 : 3);
+        g.Ct = T.which == kB_C1 ? Q.P1 : (second ? Q.P2 : Q.P3);
+        g.ldc = T.which == kB_C1 ? Q.ld1 : (second ? Q.ld2 : Q.ld3);
+        g.X = second ? Q.P1 : Q.P2;
+        g.ldx = second ? Q.ld1 : Q.ld2;
+        // Xr sits right after P3 (see the carve order above)
+        g.Xr = reinterpret_cast<float*>(reinterpret_cast<char*>(Q.P3) + align_up(z.sk3));
+        g.ldr = z.ld3;
+        g.len = second ? z.len2 : z.len1;
+        g.K = second ? z.len1 : z.len2;
+        g.KB = tc_grouped_kblocks(g.K);
+        g.tiles = tc_grouped_tiles(g.len);
+        g.iter_base = ibase;
+        g.tile_base = tbase;
+        g.owner_first = tc_grouped_owner(ibase, T.iters, G);
+        g.l = Q.l;
+        g.dir = dir;
+        g.fro = nullptr;
+        if (L.pt_fro[t][u] > 0) {
+          g.fro = fro_base + fro_used;
+          P[i].fparts = g.fro;
+          P[i].nfparts = (int)L.pt_fro[t][u];
+          fro_used += (size_t)L.pt_fro[t][u];
+        }
+        ibase += g.tiles * g.KB;
+        tbase += g.tiles;
+      }
+    }
+  }
+  // SIMT passes: algorithmic bytes of every grouped pass, index 3 * it + which
+  B->pass_bytes.assign(3 * (L.maxq + 2), 0.0);
   for (int i = 0; i < count; ++i) {
     const corutv_problem& p = probs[i];
     const int eb = p.a_dtype == CORUTV_F32 ? 4 : (p.a_dtype == CORUTV_BF16 ? 2 : 1);
-    const double a_bytes = (double)p.m * p.n * eb, sk = 4.0 * p.l * (double)(sz[i].len1 + sz[i].len2);
+    const double a_bytes = (double)p.m * p.n * eb, sk = 4.0 * p.l * (double)(L.sz[i].len1 + L.sz[i].len2);
     for (int it = 0; it <= p.q; ++it) {
       B->pass_bytes[3 * it + kB_C1] += a_bytes + sk;
       B->pass_bytes[3 * it + kB_C2] += a_bytes + sk;
     }
-    if (p.core == CORUTV_CORE_EXACT) B->pass_bytes[3 * (maxq + 1) + kB_CORE] += a_bytes + sk;
+    if (p.core == CORUTV_CORE_EXACT) B->pass_bytes[3 * (L.maxq + 1) + kB_CORE] += a_bytes + sk;
   }
-  memcpy(hbase, T.probs.data(), sizeof(BatchProb) * count);
-  CUB(cudaMemcpyAsync(B->ws, B->host, B->table_bytes, cudaMemcpyHostToDevice, h->stream));
+  memcpy(hb, P.data(), sizeof(BatchProb) * count);
+  B->table_bytes = L.table_bytes;
+  CUB(cudaMemcpyAsync(B->ws, B->host, L.table_bytes, cudaMemcpyHostToDevice, h->stream));
   B->count = count;
-  B->lp = lp;
-  B->lmax = lmax;
-  B->maxq = maxq;
+  B->lp = L.lp;
+  B->lmax = L.lmax;
+  B->maxq = L.maxq;
   B->key.assign(reinterpret_cast<const unsigned char*>(probs),
                 reinterpret_cast<const unsigned char*>(probs) + sizeof(corutv_problem) * count);
   if (B->exec) {
@@ -335,8 +491,15 @@ int orth_grouped(corutv_handle* h, const BatchState* B, int which, int it) {
   return CORUTV_OK;
 }
 
-// The whole batch, enqueued on the handle's stream.
 int pass_grouped(corutv_handle* h, const BatchState* B, int which, int it) {
+  if (B->tc) {
+    const PassTable& T = B->ptabs[which == kB_CORE ? B->ptabs.size() - 1 : 2 * it + which];
+    if (T.np == 0) return CORUTV_OK;
+    PhaseTimer tm(h, kPhPass, T.bytes);
+    CUB(launch_pass_tc_grouped(T.d_gp, T.np, T.iters, T.tiles, T.lmax, T.d_rmap, T.nround, B->partials, T.fro,
+                               h->sms, B->bstatus, h->stream));
+    return CORUTV_OK;
+  }
   const double bytes = B->pass_bytes[which == kB_CORE ? 3 * (B->maxq + 1) + kB_CORE : 3 * it + which];
   PhaseTimer tm(h, kPhPass, bytes);
   const bool first = which != kB_C2;
@@ -345,9 +508,11 @@ int pass_grouped(corutv_handle* h, const BatchState* B, int which, int it) {
   return CORUTV_OK;
 }
 
+// The whole batch, enqueued on the handle's stream.
 int enqueue(corutv_handle* h, const BatchState* B) {
   cudaStream_t st = h->stream;
   CUB(cudaMemsetAsync(B->dstatus, 0, sizeof(DevStatus) * B->count, st));
+  CUB(cudaMemsetAsync(B->bstatus, 0, sizeof(DevStatus), st));
   {
     PhaseTimer tm(h, kPhAsm);
     CUB(launch_stage_grouped(B->dprobs, B->s2, B->ns2, st));                           // S0
@@ -394,24 +559,19 @@ extern "C" {
 
 int corutv_batch_workspace_size(int count, const corutv_problem* probs, size_t* bytes) {
   if (!bytes || !probs || count < 1) return CORUTV_ERR_INVALID_ARG;
-  int lmax = 1;
   for (int i = 0; i < count; ++i) {
     const int rc = validate(probs[i]);
     if (rc) return rc;
-    lmax = std::max(lmax, (int)probs[i].l);
   }
-  const int lp = lp_for(lmax);
-  Tables T;
-  size_t per = 0, blocks = 0;
-  for (int i = 0; i < count; ++i) {
-    const ProbSizes z = prob_sizes(probs[i], lp);
-    per += prob_bytes(z);
-    blocks += cdiv(z.len1, kBatchPassBN) + cdiv(z.len2, kBatchPassBN) + z.gp1 + z.gp2 +
-              cdiv((int64_t)4 * probs[i].l * probs[i].l, 256) + cdiv(z.len1, kBatchLmulBI) +
-              cdiv(z.len2, kBatchLmulBI) + cdiv(z.len2, kBatchTile32);
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                cudaSuccess) {
+    cudaGetLastError();
+    sms = 160;                                    // no device: an upper bound for the plan
   }
-  *bytes = align_up(sizeof(BatchProb) * count) + 8 * kBAlign + sizeof(int2) * blocks +
-           align_up(sizeof(DevStatus) * count) + per;
+  Plan L;
+  make_plan(L, count, probs, sms);
+  *bytes = L.need;
   return CORUTV_OK;
 }
 
@@ -478,12 +638,14 @@ int corutv_batch_info_wait(corutv_handle* h, int count, corutv_info* infos) {
   if (!B || B->count != count || B->key.empty()) return CORUTV_ERR_INVALID_ARG;
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return CORUTV_ERR_CUDA;
   std::vector<DevStatus> st(count);
-  if (cudaMemcpy(st.data(), B->dstatus, sizeof(DevStatus) * count, cudaMemcpyDeviceToHost) != cudaSuccess)
+  DevStatus bst{};
+  if (cudaMemcpy(st.data(), B->dstatus, sizeof(DevStatus) * count, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(&bst, B->bstatus, sizeof(DevStatus), cudaMemcpyDeviceToHost) != cudaSuccess)
     return CORUTV_ERR_CUDA;
   for (int i = 0; i < count; ++i) {
     corutv_info& o = infos[i];
     memset(&o, 0, sizeof(o));
-    o.status = (st[i].flags & kStatTimeout) ? CORUTV_ERR_TIMEOUT : CORUTV_OK;
+    o.status = ((st[i].flags | bst.flags) & kStatTimeout) ? CORUTV_ERR_TIMEOUT : CORUTV_OK;
     o.passes_over_A = B->passes[i];
     o.chol_fallbacks = st[i].chol_fallbacks;
     o.chol_shift_rel = kShiftRel32;

@@ -147,6 +147,29 @@ enum BatchGram : int { kG_ORTH1 = 0, kG_ORTH2 = 1, kG_CORE_EXACT = 2, kG_CORE_SK
 constexpr int kBatchPassBN = 64;
 cudaError_t launch_pass_simt_grouped(const BatchProb* P, const int2* map, int nblocks, int lp, int a_dtype,
                                      int which, int it, cudaStream_t st);
+// batched TF32 tensor-core pass (pass_tc_grouped.cu): one table entry per problem taking
+// part, problems in table order, iterations (tile, k-block) concatenated
+struct GPassProb {
+  const void* mapA;          // CUtensorMap of A (device memory) for this problem's direction
+  const void* mapX;          // CUtensorMap of Xr: l rows x K columns, box 32 x 128
+  float* Ct;
+  int64_t ldc;
+  const float* X;            // sketch operand (ST); rounded to TF32 into Xr before the pass
+  int64_t ldx;
+  float* Xr;
+  int64_t ldr;
+  int64_t len, K, KB, tiles, iter_base, tile_base, owner_first;
+  double* fro;               // 4 FP64 partials of sum(a^2) per CTA sharing the problem, or null
+  int l, dir;
+};
+size_t tc_grouped_partial_bytes(int sms);
+int64_t tc_grouped_tiles(int64_t len);
+int64_t tc_grouped_kblocks(int64_t K);
+int64_t tc_grouped_owner(int64_t x, int64_t total, int64_t G);
+cudaError_t launch_pass_tc_grouped(const GPassProb* gp, int np, int64_t total_iters, int64_t total_tiles, int lmax,
+                                   const int2* round_map, int nround, float* partials, bool fro, int sms,
+                                   DevStatus* status, cudaStream_t st);
+
 // grouped small kernels (small.cu)
 constexpr int kBatchGramCols = 512;   // columns per Gram partial block
 constexpr int kBatchLmulBI = 128;     // columns per lmul tile

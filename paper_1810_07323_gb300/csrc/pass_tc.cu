@@ -42,41 +42,6 @@ constexpr int kThreads = 192;       // warp 0 TMA, warp 1 MMA, warps 2..5 epilog
 constexpr int kThreadsMax = 320;    // + warps 6..9: TF32 rounding / ||A||^2 of each A tile
 constexpr int kSmemBytes = kStages * kStageBytes + 1024 /*align*/ + 512 /*barriers, reductions*/;
 
-// ------------------------------------------------------------------ PTX helpers
-// Instruction descriptor, kind::tf32: D fp32 (bit 4), A/B tf32 (2 at bits 7, 10),
-// A major (bit 15), B major (bit 16), N >> 3 (bits 17-22), M >> 4 (bits 24-28).
-__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N, int a_mn_major, int b_mn_major) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)a_mn_major << 15) | ((uint32_t)b_mn_major << 16) |
-         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                         uint32_t accumulate) {
-  asm volatile(
-      "{\n"
-      ".reg .pred p;\n"
-      "setp.ne.b32 p, %4, 0;\n"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n"
-      "}\n" ::"r"(tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-
-__device__ __forceinline__ float sel_comp(const float4& v, int j) {
-  float r = v.x;
-  r = (j == 1) ? v.y : r;
-  r = (j == 2) ? v.z : r;
-  r = (j == 3) ? v.w : r;
-  return r;
-}
-
-// FP32 -> TF32, round to nearest (ties away from zero); low 13 bits become zero.
-__device__ __forceinline__ float to_tf32(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
-}
-
 struct TcArgs {
   float* Ct;
   int64_t ldc;
@@ -238,52 +203,7 @@ __global__ void __launch_bounds__(kThreadsMax, 1)
         if (*conv_abort) break;
       }
       uint8_t* tile = a_tiles + stage * kATileBytes;
-      float part = 0.f;
-      if (DIR == 0) {
-        // rows of A are already K-major: round in place
-        float4* a4 = reinterpret_cast<float4*>(tile);
-#pragma unroll 4
-        for (int q = ct; q < kATileBytes / 16; q += 128) {
-          float4 v = a4[q];
-          if (FRO) part = fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, fmaf(v.w, v.w, part))));
-          if (CONV) {
-            v.x = to_tf32(v.x); v.y = to_tf32(v.y); v.z = to_tf32(v.z); v.w = to_tf32(v.w);
-            a4[q] = v;
-          }
-        }
-      } else {
-        // A^T tile: loaded as 8 column chunks [c][k][32 n] (128-byte swizzle); rewrite it in
-        // place as the K-major tile [n][32 k] the MMA reads.  Thread block b covers
-        // k = 4 kb .. 4 kb + 3, n = 4 nb .. 4 nb + 3 (kb = q / 64, nb = q % 64).
-        float4 blk[4][4];
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-          const int q = ct + 128 * b, kb = q >> 6, nb = q & 63;
-          const int c = nb >> 3, ch = nb & 7;
-#pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const int k = 4 * kb + i;
-            blk[b][i] = *reinterpret_cast<const float4*>(tile + c * 4096 + k * 128 + ((ch ^ (k & 7)) << 4));
-          }
-        }
-        // all four converter warps must finish reading before anyone overwrites the tile
-        asm volatile("bar.sync 1, 128;" ::: "memory");
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-          const int q = ct + 128 * b, kb = q >> 6, nb = q & 63;
-#pragma unroll
-          for (int jj = 0; jj < 4; ++jj) {
-            const int j = (jj + (nb >> 1)) & 3;        // rotate rows: conflict-free stores
-            float4 v;
-            v.x = sel_comp(blk[b][0], j); v.y = sel_comp(blk[b][1], j);
-            v.z = sel_comp(blk[b][2], j); v.w = sel_comp(blk[b][3], j);
-            if (FRO) part = fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, fmaf(v.w, v.w, part))));
-            if (CONV) { v.x = to_tf32(v.x); v.y = to_tf32(v.y); v.z = to_tf32(v.z); v.w = to_tf32(v.w); }
-            const int nrow = 4 * nb + j;
-            *reinterpret_cast<float4*>(tile + nrow * 128 + ((kb ^ (nrow & 7)) << 4)) = v;
-          }
-        }
-      }
+      const float part = DIR == 0 ? tc_conv_rows_tf32<CONV, FRO>(tile, ct) : tc_conv_transpose_tf32<CONV, FRO>(tile, ct);
       fro += (double)part;
       // generic-proxy writes must be visible to the tensor core (async proxy)
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");

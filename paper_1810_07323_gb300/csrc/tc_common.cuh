@@ -168,6 +168,103 @@ __device__ __forceinline__ void tc_epilogue(float* Ct, int64_t ldc, float* parti
   }
 }
 
+
+// ------------------------------------------------------------------ TF32 helpers
+// Instruction descriptor, kind::tf32: D fp32 (bit 4), A/B tf32 (2 at bits 7, 10),
+// A major (bit 15), B major (bit 16), N >> 3 (bits 17-22), M >> 4 (bits 24-28).
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N, int a_mn_major, int b_mn_major) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)a_mn_major << 15) | ((uint32_t)b_mn_major << 16) |
+         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n"
+      ".reg .pred p;\n"
+      "setp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n"
+      "}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ float sel_comp(const float4& v, int j) {
+  float r = v.x;
+  r = (j == 1) ? v.y : r;
+  r = (j == 2) ? v.z : r;
+  r = (j == 3) ? v.w : r;
+  return r;
+}
+
+// FP32 -> TF32, round to nearest (ties away from zero); low 13 bits become zero.
+__device__ __forceinline__ float to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// ------------------------------------------------------------------ converter warps (FP32 A tiles)
+// The four converter warps (ct = 0..127) prepare one 256-position x 32 FP32 A
+// tile (32 KB, 128-byte swizzle) for kind::tf32 and return their share of
+// sum(a^2) of the original values (FRO).  CONV rounds to TF32 (nearest).
+constexpr int kTf32TileBytes = 256 * 32 * 4;
+
+// rows of A (dir AX): already K-major, round in place
+template <bool CONV, bool FRO>
+__device__ __forceinline__ float tc_conv_rows_tf32(uint8_t* tile, int ct) {
+  float part = 0.f;
+  float4* a4 = reinterpret_cast<float4*>(tile);
+#pragma unroll 4
+  for (int q = ct; q < kTf32TileBytes / 16; q += 128) {
+    float4 v = a4[q];
+    if (FRO) part = fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, fmaf(v.w, v.w, part))));
+    if (CONV) {
+      v.x = to_tf32(v.x); v.y = to_tf32(v.y); v.z = to_tf32(v.z); v.w = to_tf32(v.w);
+      a4[q] = v;
+    }
+  }
+  return part;
+}
+
+// columns of A (dir ATY): the tile arrives as 8 column chunks [c][k][32 n]
+// (128-byte swizzle) and is rewritten in place as the K-major tile [n][32 k].
+// Thread block b covers k = 4 kb .. 4 kb + 3, n = 4 nb .. 4 nb + 3 (kb = q / 64,
+// nb = q % 64).  All four warps synchronise (named barrier 1) between reading
+// and writing.
+template <bool CONV, bool FRO>
+__device__ __forceinline__ float tc_conv_transpose_tf32(uint8_t* tile, int ct) {
+  float part = 0.f;
+  float4 blk[4][4];
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    const int q = ct + 128 * b, kb = q >> 6, nb = q & 63;
+    const int c = nb >> 3, ch = nb & 7;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int k = 4 * kb + i;
+      blk[b][i] = *reinterpret_cast<const float4*>(tile + c * 4096 + k * 128 + ((ch ^ (k & 7)) << 4));
+    }
+  }
+  asm volatile("bar.sync 1, 128;" ::: "memory");
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    const int q = ct + 128 * b, kb = q >> 6, nb = q & 63;
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) {
+      const int j = (jj + (nb >> 1)) & 3;        // rotate rows: conflict-free stores
+      float4 v;
+      v.x = sel_comp(blk[b][0], j); v.y = sel_comp(blk[b][1], j);
+      v.z = sel_comp(blk[b][2], j); v.w = sel_comp(blk[b][3], j);
+      if (FRO) part = fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, fmaf(v.w, v.w, part))));
+      if (CONV) { v.x = to_tf32(v.x); v.y = to_tf32(v.y); v.z = to_tf32(v.z); v.w = to_tf32(v.w); }
+      const int nrow = 4 * nb + j;
+      *reinterpret_cast<float4*>(tile + nrow * 128 + ((kb ^ (nrow & 7)) << 4)) = v;
+    }
+  }
+  return part;
+}
+
 // ------------------------------------------------------------------ host side
 inline PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;

@@ -3,9 +3,10 @@ different shapes) with the FP64 oracle run on each problem's stored values,
 replay determinism of the captured batch, and the 1024-problem workload
 (m ~ U{256..4096}, n ~ U{128..2048}, l = r + 8, q = 1) on sampled problems.
 
-The batched passes accumulate FP32 products of the stored A on the CUDA cores
-and the factorisations run in FP32 as in corutv_solve with mma = SIMT, so the
-bound is the FP32 one: rho <= 1e-4."""
+Batches of FP32 A whose rows TMA can address run the passes as grouped TF32
+tensor-core launches (bound rho <= 1e-3, as corutv_solve with mma = tf32);
+other batches accumulate FP32 products on the CUDA cores and the factorisations
+run in FP32 as in corutv_solve with mma = SIMT: rho <= 1e-4."""
 import numpy as np
 import pytest
 
@@ -120,11 +121,58 @@ def test_batched_single_problem_matches_solve():
     A = _lowrank_sparse(5, 1200, 700, 15).astype(np.float32)
     phi = C.normal_block_np(6, 23, 0, 700, 0, 23)
     it, _ = _item(A, phi, 15, 23, 1)
+    it["mma"] = "simt"
     r = corutv.Batch([it]).run()[0]
     s = corutv.solve(it["A"], it["Phi"], 15, 23, 1, mma="simt")
     rho = O.factor_distance(r.U.double().cpu().numpy(), r.T.cpu().numpy(), r.V.double().cpu().numpy(),
                             s.U.double().cpu().numpy(), s.T.cpu().numpy(), s.V.double().cpu().numpy())
     assert rho < 1e-5, rho
+
+
+def _padded(A32):
+    """Device FP32 copy with a 16-byte row pitch (the tensor-core passes read rows by TMA)."""
+    m, n = A32.shape
+    buf = torch.zeros((m, -(-n // 4) * 4 + 4), dtype=torch.float32, device="cuda")[:, :n]
+    buf.copy_(torch.tensor(A32, device="cuda"))
+    return buf
+
+
+@pytest.mark.parametrize("q_all", [None, 0])
+def test_batched_tensor_core_parity(q_all):
+    """FP32 batches whose rows TMA can address run every pass as one grouped
+    TF32 tensor-core launch (operands rounded to nearest): rho <= 1e-3 as for
+    corutv_solve with mma = tf32; ||A||^2 fused into the first pass."""
+    items, refs = [], []
+    for i, (m, n, r, k, l, q, side, core, orth) in enumerate(MIXED):
+        q = q if q_all is None else q_all
+        A = _lowrank_sparse(C.stream_seed(80, i), m, n, r).astype(np.float32)
+        phi = C.normal_block_np(C.stream_seed(81, i), l, 0, m if side == "left" else n, 0, l)
+        items.append(dict(A=_padded(A), Phi=torch.tensor(phi, dtype=torch.float32, device="cuda"), k=k, l=l, q=q,
+                          side=side, core=core, orth=orth, want_fro2=True, mma="tf32"))
+        refs.append((A.astype(np.float64), phi, k, l, q, side, core))
+    b = corutv.Batch(items)
+    res = b.run()
+    for i, (r, (Aq, phi, k, l, q, side, core)) in enumerate(zip(res, refs)):
+        assert r.info.status == 0
+        rho = _check(r, Aq, phi, k, l, q, side, core)
+        print(f"tc problem {i} {MIXED[i][:2]}: rho={rho:.3e}")
+        assert rho < 1e-3, (i, rho)
+        a2 = float(np.sum(Aq ** 2))
+        assert abs(r.info.fro2_A - a2) < 1e-6 * a2
+        assert r.info.passes_over_A == 2 * (q + 1) + (1 if core == "exact" else 0)
+    # deterministic: the same batch again (captured, then replayed) gives the same bits
+    U0 = [r.U.clone() for r in res]
+    for _ in range(2):
+        again = b.run()
+        assert all(torch.equal(a, r.U) for a, r in zip(U0, again))
+
+
+def test_batched_tf32_needs_aligned_rows():
+    A = torch.zeros((100, 81), device="cuda")                  # 324-byte rows
+    phi = torch.zeros((81, 10), device="cuda")
+    with pytest.raises(corutv.CorutvError) as e:
+        corutv.Batch([dict(A=A, Phi=phi, k=5, l=10, mma="tf32")]).run()
+    assert e.value.status == corutv.ERR_ALIGN
 
 
 def test_batched_invalid_arguments():
@@ -150,7 +198,9 @@ def _config4_items(probs):
     items = []
     for p in probs:
         side = "left" if p.m < p.n else "right"
-        A = p.content.dense_t(device="cuda", dtype=torch.float32)
+        dense = p.content.dense_t(device="cuda", dtype=torch.float32)
+        A = torch.zeros((p.m, -(-p.n // 4) * 4), dtype=torch.float32, device="cuda")[:, :p.n]
+        A.copy_(dense)
         phi = W.problem_phi_t(p, p.m if side == "left" else p.n, device="cuda").float()
         items.append(dict(A=A, Phi=phi, k=p.k, l=p.l, q=p.q, side=side, want_fro2=True))
     return items
@@ -180,12 +230,13 @@ def test_config4_full_batch_sampled():
         res2 = float(((A - (U @ T) @ V.T) ** 2).sum())
         a2 = r.info.fro2_A
         assert abs(a2 - float((A ** 2).sum())) < 1e-6 * a2
-        # exact core: ||A - U T V^T||^2 = ||A||^2 - ||T||^2 to FP32 rounding of the products
-        assert abs((a2 - r.info.fro2_T) - res2) < 1e-5 * a2
+        # exact core: ||A - U T V^T||^2 = ||A||^2 - ||T||^2, up to the TF32 error of the core
+        # (|dT| <= 2^-10 |T| per the pass bound, so within 2 * 2^-10 ||A||^2)
+        assert abs((a2 - r.info.fro2_T) - res2) < 2e-3 * a2
         if i in sample:
             Aq = it["A"].double().cpu().numpy()
             phi = it["Phi"].double().cpu().numpy()
             ref = O.corutv(Aq, phi, p.k, p.l, p.q, side=side)
             rho = O.factor_distance(U.cpu().numpy(), T.cpu().numpy(), V.cpu().numpy(), ref["U"], ref["T"],
                                     ref["V"])
-            assert rho < TOL, (i, rho)
+            assert rho < 1e-3, (i, rho)          # TF32 tensor-core passes

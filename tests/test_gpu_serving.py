@@ -1,6 +1,8 @@
-"""GPU tests of the serving queue (corutv_server_*): every request's result
-equals the same problem solved alone (bit for bit: the batched kernels compute
-each problem independently of the others in its batch), the queue reports
+"""GPU tests of the serving queue (corutv_server_*): every BF16 request's result
+equals the same problem solved alone (bit for bit: the CUDA-core batched
+kernels compute each problem independently of the others in its batch; FP32
+batches on the tensor cores split their passes by batch, so there results
+agree to rounding), the queue reports
 ERR_BUSY when full and never blocks, oversized requests fail with ERR_OOM,
 invalid ones are refused at submission, and results agree with the FP64
 oracle on sampled requests."""
@@ -80,7 +82,7 @@ def test_server_parity_with_oracle_sampled():
         ref = O.corutv(A, it["Phi"].double().cpu().numpy(), it["k"], it["l"], it["q"])
         rho = O.factor_distance(res.U.double().cpu().numpy(), res.T.cpu().numpy(), res.V.double().cpu().numpy(),
                                 ref["U"], ref["T"], ref["V"])
-        assert rho < 1e-4, rho
+        assert rho < 1e-3, rho       # FP32 rows TMA can read: grouped TF32 tensor-core passes
 
 
 def test_server_queue_full_is_busy_and_never_blocks():
