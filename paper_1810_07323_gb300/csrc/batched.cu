@@ -51,10 +51,12 @@ struct BatchState {
   int count = 0;
   std::vector<int> passes;            // passes over A per problem
   std::vector<int> want_fro2;
-  // grouped-launch maps (device) and their block counts
-  int2 *t1 = nullptr, *t2 = nullptr, *g1 = nullptr, *g2 = nullptr, *red = nullptr, *lm1 = nullptr,
-       *lm2 = nullptr, *s2 = nullptr;
-  int nt1 = 0, nt2 = 0, ng1 = 0, ng2 = 0, nred = 0, nlm1 = 0, nlm2 = 0, ns2 = 0;
+  // grouped-launch maps (device) and their block counts, per sketch-size class (problems
+  // with l <= 32, <= 64, <= 128 run the 32-, 64- and 128-row kernel variants); kinds:
+  // kMapT1/T2 SIMT pass tiles, kMapG1/G2 Gram partials, kMapRed Gram reduction, kMapLm1/Lm2
+  // lmul tiles, kMapS2 32-column tiles of the second sketch (class-independent: class 0)
+  int2* map[3][8] = {};
+  int nmap[3][8] = {};
   int lp = 32, lmax = 1, maxq = 0, a_dtype = CORUTV_F32;
   bool any_exact = false, any_sketch = false, any_fro2 = false;
   bool tc = false;                    // passes on the tensor cores
@@ -82,6 +84,10 @@ namespace {
 constexpr size_t kBAlign = 256;
 
 size_t align_up(size_t x) { return (x + kBAlign - 1) / kBAlign * kBAlign; }
+
+enum MapKind { kMapT1 = 0, kMapT2, kMapG1, kMapG2, kMapRed, kMapLm1, kMapLm2, kMapS2 };
+constexpr int kClassLP[3] = {32, 64, 128};
+int lclass(int l) { return l <= 32 ? 0 : (l <= 64 ? 1 : 2); }
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
 int validate(const corutv_problem& p) {
@@ -174,8 +180,8 @@ struct Plan {
   int count = 0, lp = 32, lmax = 1, maxq = 0;
   bool tc = false;
   std::vector<ProbSizes> sz;
-  std::vector<int2> maps[8];          // t1, t2, g1, g2, red, lm1, lm2, s2
-  size_t off_maps[8] = {};
+  std::vector<int2> maps[3][8];       // per class and MapKind
+  size_t off_maps[3][8] = {};
   std::vector<PassTable> ptabs;
   std::vector<std::vector<int>> pt_probs;     // problems of each pass table
   std::vector<std::vector<int2>> pt_rmaps;
@@ -195,21 +201,23 @@ void make_plan(Plan& L, int count, const corutv_problem* probs, int sms) {
   L.sz.resize(count);
   for (int i = 0; i < count; ++i) {
     const corutv_problem& p = probs[i];
-    const ProbSizes& z = L.sz[i] = prob_sizes(p, L.lp, L.tc);
-    add_blocks(L.maps[0], i, cdiv(z.len1, kBatchPassBN));
-    add_blocks(L.maps[1], i, cdiv(z.len2, kBatchPassBN));
-    add_blocks(L.maps[2], i, z.gp1);
-    add_blocks(L.maps[3], i, z.gp2);
-    add_blocks(L.maps[4], i, cdiv((int64_t)4 * p.l * p.l, 256));
-    add_blocks(L.maps[5], i, cdiv(z.len1, kBatchLmulBI));
-    add_blocks(L.maps[6], i, cdiv(z.len2, kBatchLmulBI));
-    add_blocks(L.maps[7], i, cdiv(z.len2, kBatchTile32));
+    const ProbSizes& z = L.sz[i] = prob_sizes(p, kClassLP[lclass(p.l)], L.tc);
+    std::vector<int2>* mc = L.maps[lclass(p.l)];
+    add_blocks(mc[kMapT1], i, cdiv(z.len1, kBatchPassBN));
+    add_blocks(mc[kMapT2], i, cdiv(z.len2, kBatchPassBN));
+    add_blocks(mc[kMapG1], i, z.gp1);
+    add_blocks(mc[kMapG2], i, z.gp2);
+    add_blocks(mc[kMapRed], i, cdiv((int64_t)4 * p.l * p.l, 256));
+    add_blocks(mc[kMapLm1], i, cdiv(z.len1, kBatchLmulBI));
+    add_blocks(mc[kMapLm2], i, cdiv(z.len2, kBatchLmulBI));
+    add_blocks(L.maps[0][kMapS2], i, cdiv(z.len2, kBatchTile32));
   }
   size_t off = align_up(sizeof(BatchProb) * count);
-  for (int k = 0; k < 8; ++k) {
-    L.off_maps[k] = off;
-    off += align_up(sizeof(int2) * std::max<size_t>(1, L.maps[k].size()));
-  }
+  for (int c = 0; c < 3; ++c)
+    for (int k = 0; k < 8; ++k) {
+      L.off_maps[c][k] = off;
+      off += align_up(sizeof(int2) * std::max<size_t>(1, L.maps[c][k].size()));
+    }
   if (L.tc) {
     // pass tables: (C1, C2) of every power step, then the exact-core pass
     for (int t = 0; t < 2 * (L.maxq + 1) + 1; ++t) {
@@ -304,13 +312,13 @@ int build(corutv_handle* h, BatchState* B, int count, const corutv_problem* prob
   char* hb = static_cast<char*>(B->host);
   memset(hb, 0, L.table_bytes);
   B->dprobs = reinterpret_cast<BatchProb*>(d);
-  int2** mp[8] = {&B->t1, &B->t2, &B->g1, &B->g2, &B->red, &B->lm1, &B->lm2, &B->s2};
-  int* mn[8] = {&B->nt1, &B->nt2, &B->ng1, &B->ng2, &B->nred, &B->nlm1, &B->nlm2, &B->ns2};
-  for (int k = 0; k < 8; ++k) {
-    *mp[k] = reinterpret_cast<int2*>(d + L.off_maps[k]);
-    *mn[k] = (int)L.maps[k].size();
-    if (!L.maps[k].empty()) memcpy(hb + L.off_maps[k], L.maps[k].data(), sizeof(int2) * L.maps[k].size());
-  }
+  for (int c = 0; c < 3; ++c)
+    for (int k = 0; k < 8; ++k) {
+      B->map[c][k] = reinterpret_cast<int2*>(d + L.off_maps[c][k]);
+      B->nmap[c][k] = (int)L.maps[c][k].size();
+      if (!L.maps[c][k].empty())
+        memcpy(hb + L.off_maps[c][k], L.maps[c][k].data(), sizeof(int2) * L.maps[c][k].size());
+    }
   B->dstatus = reinterpret_cast<DevStatus*>(d + L.off_status);
   B->bstatus = reinterpret_cast<DevStatus*>(d + L.off_bstatus);
   B->partials = L.tc ? reinterpret_cast<float*>(d + L.off_partials) : nullptr;
@@ -481,13 +489,23 @@ int orth_grouped(corutv_handle* h, const BatchState* B, int which, int it) {
   const bool second = which == kG_ORTH2;
   const int passes = B->multi_pass[it] ? 3 : 1;
   for (int pass = 0; pass < passes; ++pass) {
-    CUB(launch_gram_grouped(B->dprobs, second ? B->g2 : B->g1, second ? B->ng2 : B->ng1, B->red, B->nred, B->lp,
-                            which, it, pass, h->stream));
+    for (int c = 0; c < 3; ++c)
+      CUB(launch_gram_grouped(B->dprobs, B->map[c][second ? kMapG2 : kMapG1], B->nmap[c][second ? kMapG2 : kMapG1],
+                              B->map[c][kMapRed], B->nmap[c][kMapRed], kClassLP[c], which, it, pass, h->stream));
     CUB(launch_cholinv_grouped(B->dprobs, B->count, B->lmax, which, it, pass, kSkipTol32, kShiftRel32, kTolRel32,
                                h->stream));
-    CUB(launch_lmul_orth_grouped(B->dprobs, second ? B->lm2 : B->lm1, second ? B->nlm2 : B->nlm1, B->lp, which, it,
-                                 pass, h->stream));
+    for (int c = 0; c < 3; ++c)
+      CUB(launch_lmul_orth_grouped(B->dprobs, B->map[c][second ? kMapLm2 : kMapLm1],
+                                   B->nmap[c][second ? kMapLm2 : kMapLm1], kClassLP[c], which, it, pass, h->stream));
   }
+  return CORUTV_OK;
+}
+
+int gram_core_grouped(corutv_handle* h, const BatchState* B, int which) {
+  const int k = which == kG_CORE_EXACT ? kMapG1 : kMapG2;
+  for (int c = 0; c < 3; ++c)
+    CUB(launch_gram_grouped(B->dprobs, B->map[c][k], B->nmap[c][k], B->map[c][kMapRed], B->nmap[c][kMapRed],
+                            kClassLP[c], which, 0, 0, h->stream));
   return CORUTV_OK;
 }
 
@@ -502,9 +520,10 @@ int pass_grouped(corutv_handle* h, const BatchState* B, int which, int it) {
   }
   const double bytes = B->pass_bytes[which == kB_CORE ? 3 * (B->maxq + 1) + kB_CORE : 3 * it + which];
   PhaseTimer tm(h, kPhPass, bytes);
-  const bool first = which != kB_C2;
-  CUB(launch_pass_simt_grouped(B->dprobs, first ? B->t1 : B->t2, first ? B->nt1 : B->nt2, B->lp, B->a_dtype,
-                               which, it, h->stream));
+  const int k = which != kB_C2 ? kMapT1 : kMapT2;
+  for (int c = 0; c < 3; ++c)
+    CUB(launch_pass_simt_grouped(B->dprobs, B->map[c][k], B->nmap[c][k], kClassLP[c], B->a_dtype, which, it,
+                                 h->stream));
   return CORUTV_OK;
 }
 
@@ -515,14 +534,14 @@ int enqueue(corutv_handle* h, const BatchState* B) {
   CUB(cudaMemsetAsync(B->bstatus, 0, sizeof(DevStatus), st));
   {
     PhaseTimer tm(h, kPhAsm);
-    CUB(launch_stage_grouped(B->dprobs, B->s2, B->ns2, st));                           // S0
+    CUB(launch_stage_grouped(B->dprobs, B->map[0][kMapS2], B->nmap[0][kMapS2], st));    // S0
   }
   for (int it = 0; it <= B->maxq; ++it) {
     int rc = pass_grouped(h, B, kB_C1, it);                                              // S1
     if (!rc) rc = orth_grouped(h, B, kG_ORTH1, it);                                      // S2
     if (!rc) rc = pass_grouped(h, B, kB_C2, it);                                         // S3
     if (rc) return rc;
-    if (B->any_sketch) CUB(launch_copy_sketch_grouped(B->dprobs, B->s2, B->ns2, it, st));
+    if (B->any_sketch) CUB(launch_copy_sketch_grouped(B->dprobs, B->map[0][kMapS2], B->nmap[0][kMapS2], it, st));
     rc = orth_grouped(h, B, kG_ORTH2, it);                                               // S4
     if (rc) return rc;
   }
@@ -530,11 +549,13 @@ int enqueue(corutv_handle* h, const BatchState* B) {
     const int rc = pass_grouped(h, B, kB_CORE, 0);
     if (rc) return rc;
     PhaseTimer tm(h, kPhCore);
-    CUB(launch_gram_grouped(B->dprobs, B->g1, B->ng1, B->red, B->nred, B->lp, kG_CORE_EXACT, 0, 0, st));
+    const int rc2 = gram_core_grouped(h, B, kG_CORE_EXACT);
+    if (rc2) return rc2;
   }
   if (B->any_sketch) {
     PhaseTimer tm(h, kPhCore);
-    CUB(launch_gram_grouped(B->dprobs, B->g2, B->ng2, B->red, B->nred, B->lp, kG_CORE_SKETCH, 0, 0, st));
+    const int rc = gram_core_grouped(h, B, kG_CORE_SKETCH);
+    if (rc) return rc;
   }
   {
     PhaseTimer tm(h, kPhQrcp);
@@ -542,7 +563,9 @@ int enqueue(corutv_handle* h, const BatchState* B) {
   }
   {
     PhaseTimer tm(h, kPhAsm);
-    CUB(launch_assemble_grouped(B->dprobs, B->lm1, B->nlm1, B->s2, B->ns2, B->lp, st)); // S7
+    for (int c = 0; c < 3; ++c)                                                         // S7
+      CUB(launch_assemble_grouped(B->dprobs, B->map[c][kMapLm1], B->nmap[c][kMapLm1], B->map[0][kMapS2],
+                                  c == 0 ? B->nmap[0][kMapS2] : 0, kClassLP[c], st));
   }
   if (B->any_fro2) CUB(launch_fro2_grouped(B->dprobs, B->count, st));                   // S9
   return CORUTV_OK;

@@ -201,7 +201,7 @@ inline bool tma_rows_ok(const void* A, int64_t lda, int a_dtype) {
 
 int run_pass(corutv_handle* h, int dir, int a_dtype, int mma, const void* A, int64_t lda, int64_t m, int64_t n,
              const float* scales, const void* Xt, int64_t ldx, int l, void* Ct, int64_t ldc, void* partials,
-             float* Xr, int64_t ldr, double* fro_parts, int phase = kPhPass) {
+             float* Xr, int64_t ldr, double* fro_parts, int phase = kPhPass, bool x_rounded = false) {
   PassArgs a{};
   a.A = A;
   a.lda = lda;
@@ -238,8 +238,9 @@ int run_pass(corutv_handle* h, int dir, int a_dtype, int mma, const void* A, int
   } else {
     if (!tc_pass_supported(dir, a_dtype, eng, l)) return CORUTV_ERR_UNSUPPORTED;
     if (eng == CORUTV_MMA_TF32) {
-      // the sketch operand rounded to TF32 (nearest) once per pass; A is rounded tile by tile in the kernel
-      CU(launch_round_tf32(static_cast<const float*>(Xt), ldx, Xr, ldr, l, a.K, h->stream));
+      // the sketch operand rounded to TF32 (nearest) once per pass -- already done by its producer
+      // when x_rounded; A is rounded tile by tile in the kernel
+      if (!x_rounded) CU(launch_round_tf32(static_cast<const float*>(Xt), ldx, Xr, ldr, l, a.K, h->stream));
       a.Xt = Xr;
       a.ldx = ldr;
     }
@@ -261,8 +262,11 @@ int run_pass(corutv_handle* h, int dir, int a_dtype, int mma, const void* A, int
 // conditioned (used for the sketches the power iteration only multiplies
 // again).  R_out (may be null): the product R = R_3 R_2 R_1 with C = Q R (FP64,
 // ld l); it uses the D and Qt scratch blocks, free outside a solve.
+// round_out (FP32, may be null): the last pass also writes Q rounded to TF32 (ld ldr), the
+// operand of the next TF32 pass.
 template <typename TC>
-int orth_st(corutv_handle* h, TC* Ct, int64_t ldc, int64_t len, int l, const Plan& pl, int passes, double* Rout) {
+int orth_st(corutv_handle* h, TC* Ct, int64_t ldc, int64_t len, int l, const Plan& pl, int passes, double* Rout,
+            float* round_out = nullptr, int64_t ldr = 0) {
   const bool f64 = sizeof(TC) == 8;
   PhaseTimer tm(h, kPhOrth);
   for (int pass = 0; pass < passes; ++pass) {
@@ -275,7 +279,7 @@ int orth_st(corutv_handle* h, TC* Ct, int64_t ldc, int64_t len, int l, const Pla
     CU(launch_cholinv<TC>(pl.G, kMaxL, l, shift, tol, static_cast<TC*>(pl.R), static_cast<TC*>(pl.Rinv), pl.defic,
                           pl.status, rpass, skip, kSkipTol32, h->stream));
     CU(launch_lmul<TC>(Ct, ldc, len, l, static_cast<const TC*>(pl.Rinv), kMaxL, Ct, ldc, false, pl.defic, pass,
-                       skip, h->stream));
+                       skip, pass == passes - 1 ? round_out : nullptr, ldr, h->stream));
     if (Rout && pass > 0) {
       // R <- R_pass R
       CU(launch_upper_mul(pl.D, Rout, pl.Qt, l, h->stream));
@@ -311,36 +315,43 @@ int solve_impl(corutv_handle* h, const corutv_params* p, const Plan& pl, const v
   int passes = 0;
 
   CU(cudaMemsetAsync(pl.status, 0, sizeof(DevStatus), h->stream));
+  // TF32 passes over A: the producers of each sketch operand (the staging of Psi, the last
+  // CholeskyQR pass) also write its TF32-rounded copy into Xr for the next pass
+  const bool pre_round = sizeof(TC) == 4 &&
+                         pick_mma(p->a_dtype, p->mma, tma_rows_ok(A, lda, p->a_dtype)) == CORUTV_MMA_TF32;
+  float* Xr = static_cast<float*>(pl.Xr);
+  float* Xr_out = pre_round ? Xr : nullptr;
   {
     // S0: stage Psi^T into P2 (the "X" of the first product)
     PhaseTimer tm(h, kPhAsm);
-    CU(launch_stage_transpose<TC>(static_cast<const TC*>(Phi), ldphi, pl.len2, l, P2, pl.ld2, h->stream));
+    CU(launch_stage_transpose<TC>(static_cast<const TC*>(Phi), ldphi, pl.len2, l, P2, pl.ld2, Xr_out, pl.ldr,
+                                  h->stream));
   }
   // S9: ||A||_F^2 fused into the first pass where the tensor-core engine runs it
   const int ref_mma = p->mma == CORUTV_MMA_SIMT ? CORUTV_MMA_SIMT : CORUTV_MMA_AUTO;
   const bool fuse_fro2 =
       p->want_fro2 && (A_ref ? pick_mma(CORUTV_F32, ref_mma, tma_rows_ok(A_ref, lda_ref, CORUTV_F32))
                              : pick_mma(p->a_dtype, p->mma, tma_rows_ok(A, lda, p->a_dtype))) != CORUTV_MMA_SIMT;
-  float* Xr = static_cast<float*>(pl.Xr);
   for (int it = 0; it <= p->q; ++it) {
     // S1: C1 = A X  (Alg. 3 step 3)
     int rc = run_pass(h, dir1, p->a_dtype, p->mma, A, lda, p->m, p->n, scales, P2, pl.ld2, l, P1, pl.ld1,
-                      pl.partials, Xr, pl.ldr, (it == 0 && fuse_fro2 && !A_ref) ? pl.fro_parts : nullptr);
+                      pl.partials, Xr, pl.ldr, (it == 0 && fuse_fro2 && !A_ref) ? pl.fro_parts : nullptr, kPhPass,
+                      pre_round);
     if (rc) return rc;
     ++passes;
     // S2: orth(C1)
-    rc = orth_st<TC>(h, P1, pl.ld1, pl.len1, l, pl, orth_passes(p, it), nullptr);
+    rc = orth_st<TC>(h, P1, pl.ld1, pl.len1, l, pl, orth_passes(p, it), nullptr, Xr_out, pl.ldr);
     if (rc) return rc;
     // S3: C2 = A^T Q1  (Alg. 3 step 4)
     rc = run_pass(h, dir2, p->a_dtype, p->mma, A, lda, p->m, p->n, scales, P1, pl.ld1, l, P2, pl.ld2,
-                  pl.partials, Xr, pl.ldr, nullptr);
+                  pl.partials, Xr, pl.ldr, nullptr, kPhPass, pre_round);
     if (rc) return rc;
     ++passes;
     if (it == p->q && p->core == CORUTV_CORE_SKETCH)
       CU(cudaMemcpy2DAsync(P3, pl.ld3 * sizeof(TC), P2, pl.ld2 * sizeof(TC), pl.len2 * sizeof(TC), l,
                            cudaMemcpyDeviceToDevice, h->stream));
     // S4: orth(C2)
-    rc = orth_st<TC>(h, P2, pl.ld2, pl.len2, l, pl, orth_passes(p, it), nullptr);
+    rc = orth_st<TC>(h, P2, pl.ld2, pl.len2, l, pl, orth_passes(p, it), nullptr, Xr_out, pl.ldr);
     if (rc) return rc;
   }
   // S5: core D = Q1^T A Q2 (Alg. 2 step 5)
@@ -355,7 +366,7 @@ int solve_impl(corutv_handle* h, const corutv_params* p, const Plan& pl, const v
                        gram_parts(pl.len1, h->sms), pl.D, kMaxL, h->stream));   // D = Q1^T E
   } else if (p->core == CORUTV_CORE_EXACT) {
     int rc = run_pass(h, dir1, p->a_dtype, p->mma, A, lda, p->m, p->n, scales, P2, pl.ld2, l, P3, pl.ld3,
-                      pl.partials, Xr, pl.ldr, nullptr);   // E = A Q2 (ST, len1)
+                      pl.partials, Xr, pl.ldr, nullptr, kPhPass, pre_round);   // E = A Q2 (ST, len1)
     if (rc) return rc;
     ++passes;
     PhaseTimer tm(h, kPhCore);

@@ -84,11 +84,13 @@ cudaError_t launch_cholinv(const double* G, int64_t ldg, int l, double shift_rel
                            int* defic, DevStatus* status, double* Rout, int* skip_flag, float skip_tol,
                            cudaStream_t st);
 // Out = S^T In on ST blocks (S upper triangular); rows j with defic[j] set (defic may be
-// null) receive the deterministic replacement vector of `pass` instead
+// null) receive the deterministic replacement vector of `pass` instead.  round_out (FP32
+// only, may be null): also write the result rounded to TF32 (ld ldr), the operand of the
+// next TF32 pass.
 template <typename TC>
 cudaError_t launch_lmul(const TC* In, int64_t ldi, int64_t len, int l, const TC* S, int64_t lds, TC* Out,
                         int64_t ldo, bool out_rowmajor, const int* defic, int pass, const int* skip_flag,
-                        cudaStream_t st);
+                        float* round_out, int64_t ldr, cudaStream_t st);
 template <typename TC>
 cudaError_t launch_lmul_f64s(const TC* In, int64_t ldi, int64_t len, int l, const double* S, int64_t lds, TC* Out,
                              int64_t ldo, bool out_rowmajor, cudaStream_t st);
@@ -99,7 +101,7 @@ cudaError_t launch_gather_cols(const TC* St, int64_t lds, int64_t len, int l, co
                                int64_t ldo, cudaStream_t st);
 template <typename TC>
 cudaError_t launch_stage_transpose(const TC* Phi, int64_t ldphi, int64_t len, int l, TC* Xt, int64_t ldx,
-                                   cudaStream_t st);
+                                   float* round_out, int64_t ldr, cudaStream_t st);
 template <typename TC>
 cudaError_t launch_qrcp(const double* D, int64_t ldd, int l, int k, double* Q, int64_t ldq, double* R, int64_t ldr,
                         bool r_transposed, int32_t* perm, double* fro2, DevStatus* status, cudaStream_t st);

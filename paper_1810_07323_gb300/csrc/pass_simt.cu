@@ -274,11 +274,78 @@ template __global__ void streamk_reduce_kernel<float>(float*, int64_t, const flo
 template __global__ void streamk_reduce_kernel<double>(double*, int64_t, const double*, int, int, int, int64_t,
                                                        int64_t, int64_t);
 
+// FP32 version with 16-byte accesses: block (t, g) handles rows 8 g .. 8 g + 7 of tile t,
+// a thread 4 consecutive positions; all slot loads are issued before the ordered sum.
+__global__ void __launch_bounds__(256) streamk_reduce_f32v_kernel(float* __restrict__ Ct, int64_t ldc,
+                                                                  const float* __restrict__ P, int l, int LP, int BN,
+                                                                  int64_t len, int64_t KB, int64_t G) {
+  constexpr int kMaxSplit = 64, kUnroll = 4;
+  __shared__ int64_t slot_off[kMaxSplit];
+  __shared__ int nsplit;
+  StreamK sk((len + BN - 1) / BN, KB, G);
+  const int64_t t = blockIdx.x;
+  const int row0 = blockIdx.y * 8;
+  if (row0 >= l) return;
+  if (threadIdx.x == 0) {
+    const int64_t cf = sk.owner(t * KB), cl = sk.owner(t * KB + KB - 1);
+    int ns = (int)(cl - cf + 1);
+    if (cf == cl) ns = 0;                        // written directly by its only worker
+    if (ns > kMaxSplit) ns = kMaxSplit + 1;      // resolved per element below
+    nsplit = ns;
+    for (int i = 0; i < ns && i < kMaxSplit; ++i) slot_off[i] = (int64_t)sk.slot(cf + i, t) * LP * BN;
+  }
+  __syncthreads();
+  const int ns = nsplit;
+  if (ns == 0) return;
+  const int64_t p0 = t * BN;
+  const int q4 = BN / 4;
+  for (int x = threadIdx.x; x < 8 * q4; x += blockDim.x) {
+    const int j = row0 + x / q4, ii = 4 * (x % q4);
+    const int64_t gi = p0 + ii;
+    if (j >= l || gi >= len) continue;
+    float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (ns <= kMaxSplit) {
+      for (int c0 = 0; c0 < ns; c0 += kUnroll) {
+        float4 v[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u)
+          if (c0 + u < ns) v[u] = *reinterpret_cast<const float4*>(P + slot_off[c0 + u] + (int64_t)j * BN + ii);
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u)
+          if (c0 + u < ns) {
+            sum.x += v[u].x; sum.y += v[u].y; sum.z += v[u].z; sum.w += v[u].w;
+          }
+      }
+    } else {
+      const int64_t cf = sk.owner(t * KB), cl = sk.owner(t * KB + KB - 1);
+      for (int64_t c = cf; c <= cl; ++c) {
+        const float4 v = *reinterpret_cast<const float4*>(P + ((int64_t)sk.slot(c, t) * LP + j) * BN + ii);
+        sum.x += v.x; sum.y += v.y; sum.z += v.z; sum.w += v.w;
+      }
+    }
+    float* dst = Ct + j * ldc + gi;
+    if (gi + 3 < len && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0)) {
+      *reinterpret_cast<float4*>(dst) = sum;
+    } else {
+      const float sv[4] = {sum.x, sum.y, sum.z, sum.w};
+      for (int u = 0; u < 4; ++u)
+        if (gi + u < len) dst[u] = sv[u];
+    }
+  }
+}
+
 cudaError_t launch_streamk_reduce_f32(float* Ct, int64_t ldc, const float* P, int l, int LP, int BN, int64_t len,
                                       int64_t KB, int64_t G, cudaStream_t st) {
   const int64_t tiles = cdiv(len, BN);
-  dim3 grid((unsigned)tiles, (unsigned)cdiv(l, 16));
-  if (tiles > 0) { streamk_reduce_kernel<float><<<grid, 256, 0, st>>>(Ct, ldc, P, l, LP, BN, len, KB, G); CORUTV_COUNT_LAUNCH(); }
+  if (tiles <= 0) return cudaSuccess;
+  if (BN % 4 == 0) {
+    dim3 grid((unsigned)tiles, (unsigned)cdiv(l, 8));
+    streamk_reduce_f32v_kernel<<<grid, 256, 0, st>>>(Ct, ldc, P, l, LP, BN, len, KB, G);
+  } else {
+    dim3 grid((unsigned)tiles, (unsigned)cdiv(l, 16));
+    streamk_reduce_kernel<float><<<grid, 256, 0, st>>>(Ct, ldc, P, l, LP, BN, len, KB, G);
+  }
+  CORUTV_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 

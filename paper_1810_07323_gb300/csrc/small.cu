@@ -12,6 +12,7 @@
 #include "common.cuh"
 #include "elem.cuh"
 #include "internal.h"
+#include "tc_common.cuh"
 
 namespace corutv {
 
@@ -465,7 +466,7 @@ template <typename TC, typename TS, int LP, int BI>
 __device__ __forceinline__ void lmul_body(const TC* __restrict__ In, int64_t ldi, int64_t len, int l,
                                           const TS* __restrict__ S, int64_t lds, TC* __restrict__ Out, int64_t ldo,
                                           int out_rowmajor, int upper, const int* __restrict__ defic, int pass,
-                                          int bx) {
+                                          int bx, float* __restrict__ round_out = nullptr, int64_t ldr = 0) {
   constexpr int R = LP / 16, RI = BI / 16;
   constexpr int SP = LP + 4, IP = BI + 4;
   constexpr bool kVecIn = sizeof(TC) == 4;
@@ -575,7 +576,12 @@ __device__ __forceinline__ void lmul_body(const TC* __restrict__ In, int64_t ldi
 #pragma unroll
       for (int u = 0; u < RI; ++u) {
         const int64_t g = i0 + RI * tx + u;
-        if (g < len) Out[j * ldo + g] = repl ? (TC)replacement_value(pass, j, g) : acc[v][u];
+        if (g < len) {
+          const TC val = repl ? (TC)replacement_value(pass, j, g) : acc[v][u];
+          Out[j * ldo + g] = val;
+          if constexpr (sizeof(TC) == 4)
+            if (round_out) round_out[j * ldr + g] = to_tf32(val);   // the next pass's TF32 operand
+        }
       }
     }
   } else {
@@ -599,15 +605,29 @@ __global__ void __launch_bounds__(256, 1) lmul_kernel(const TC* __restrict__ In,
                                                       const TS* __restrict__ S, int64_t lds, TC* __restrict__ Out,
                                                       int64_t ldo, int out_rowmajor, int upper,
                                                       const int* __restrict__ defic, int pass,
-                                                      const int* __restrict__ skip_flag) {
-  if (skip_flag && *skip_flag) return;     // the factor was found to be the identity
-  lmul_body<TC, TS, LP, BI>(In, ldi, len, l, S, lds, Out, ldo, out_rowmajor, upper, defic, pass, blockIdx.x);
+                                                      const int* __restrict__ skip_flag, float* __restrict__ round_out,
+                                                      int64_t ldr) {
+  if (skip_flag && *skip_flag) {           // the factor was found to be the identity: Out = In
+    if constexpr (sizeof(TC) == 4) {
+      if (round_out) {
+        const int64_t i0 = (int64_t)blockIdx.x * BI;
+        for (int e = threadIdx.x; e < l * BI; e += blockDim.x) {
+          const int j = e / BI;
+          const int64_t g = i0 + e % BI;
+          if (g < len) round_out[j * ldr + g] = to_tf32(In[j * ldi + g]);
+        }
+      }
+    }
+    return;
+  }
+  lmul_body<TC, TS, LP, BI>(In, ldi, len, l, S, lds, Out, ldo, out_rowmajor, upper, defic, pass, blockIdx.x,
+                            round_out, ldr);
 }
 
 template <typename TC, typename TS, int LP, int BI>
 static cudaError_t lmul_variant(const TC* In, int64_t ldi, int64_t len, int l, const TS* S, int64_t lds, TC* Out,
                                 int64_t ldo, bool rowmajor, bool upper, const int* defic, int pass,
-                                const int* skip_flag, cudaStream_t st) {
+                                const int* skip_flag, float* round_out, int64_t ldr, cudaStream_t st) {
   const unsigned grid = (unsigned)cdiv(len, BI);
   if (grid == 0) return cudaSuccess;
   const size_t a = (size_t)LP * (LP + 4) + (size_t)LP * (BI + 4);
@@ -617,7 +637,7 @@ static cudaError_t lmul_variant(const TC* In, int64_t ldi, int64_t len, int l, c
                                        (int)sm);
   if (e != cudaSuccess) return e;
   lmul_kernel<TC, TS, LP, BI><<<grid, 256, sm, st>>>(In, ldi, len, l, S, lds, Out, ldo, rowmajor ? 1 : 0,
-                                                     upper ? 1 : 0, defic, pass, skip_flag);
+                                                     upper ? 1 : 0, defic, pass, skip_flag, round_out, ldr);
   CORUTV_COUNT_LAUNCH();
   return cudaGetLastError();
 }
@@ -625,27 +645,32 @@ static cudaError_t lmul_variant(const TC* In, int64_t ldi, int64_t len, int l, c
 template <typename TC, typename TS>
 static cudaError_t lmul_dispatch(const TC* In, int64_t ldi, int64_t len, int l, const TS* S, int64_t lds, TC* Out,
                                  int64_t ldo, bool rowmajor, bool upper, const int* defic, int pass,
-                                 const int* skip_flag, cudaStream_t st) {
+                                 const int* skip_flag, float* round_out, int64_t ldr, cudaStream_t st) {
   // FP32: 128-column tiles (S and the tile fill ~135 KB of shared memory); FP64: 64 columns
   constexpr int BI = sizeof(TC) == 4 ? 128 : 64;
   if (l <= 32)
-    return lmul_variant<TC, TS, 32, BI>(In, ldi, len, l, S, lds, Out, ldo, rowmajor, upper, defic, pass, skip_flag, st);
+    return lmul_variant<TC, TS, 32, BI>(In, ldi, len, l, S, lds, Out, ldo, rowmajor, upper, defic, pass, skip_flag,
+                                        round_out, ldr, st);
   if (l <= 64)
-    return lmul_variant<TC, TS, 64, BI>(In, ldi, len, l, S, lds, Out, ldo, rowmajor, upper, defic, pass, skip_flag, st);
-  return lmul_variant<TC, TS, 128, BI>(In, ldi, len, l, S, lds, Out, ldo, rowmajor, upper, defic, pass, skip_flag, st);
+    return lmul_variant<TC, TS, 64, BI>(In, ldi, len, l, S, lds, Out, ldo, rowmajor, upper, defic, pass, skip_flag,
+                                        round_out, ldr, st);
+  return lmul_variant<TC, TS, 128, BI>(In, ldi, len, l, S, lds, Out, ldo, rowmajor, upper, defic, pass, skip_flag,
+                                       round_out, ldr, st);
 }
 
 template <typename TC>
 cudaError_t launch_lmul(const TC* In, int64_t ldi, int64_t len, int l, const TC* S, int64_t lds, TC* Out,
                         int64_t ldo, bool out_rowmajor, const int* defic, int pass, const int* skip_flag,
-                        cudaStream_t st) {
+                        float* round_out, int64_t ldr, cudaStream_t st) {
   // the CholeskyQR factor R^-1 is upper triangular
-  return lmul_dispatch<TC, TC>(In, ldi, len, l, S, lds, Out, ldo, out_rowmajor, true, defic, pass, skip_flag, st);
+  return lmul_dispatch<TC, TC>(In, ldi, len, l, S, lds, Out, ldo, out_rowmajor, true, defic, pass, skip_flag,
+                               round_out, ldr, st);
 }
 template <typename TC>
 cudaError_t launch_lmul_f64s(const TC* In, int64_t ldi, int64_t len, int l, const double* S, int64_t lds, TC* Out,
                              int64_t ldo, bool out_rowmajor, cudaStream_t st) {
-  return lmul_dispatch<TC, double>(In, ldi, len, l, S, lds, Out, ldo, out_rowmajor, false, nullptr, 0, nullptr, st);
+  return lmul_dispatch<TC, double>(In, ldi, len, l, S, lds, Out, ldo, out_rowmajor, false, nullptr, 0, nullptr,
+                                   nullptr, 0, st);
 }
 
 // =============================================================================== R composition
@@ -706,7 +731,8 @@ cudaError_t launch_gather_cols(const TC* St, int64_t lds, int64_t len, int l, co
 // Xt[j][i] = Phi[i][j] (ST staging of the caller's row-major Psi).
 template <typename TC>
 __device__ __forceinline__ void stage_transpose_body(const TC* __restrict__ Phi, int64_t ldphi, int64_t len, int l,
-                                                     TC* __restrict__ Xt, int64_t ldx, int bx) {
+                                                     TC* __restrict__ Xt, int64_t ldx, int bx,
+                                                     float* __restrict__ round_out = nullptr, int64_t ldr = 0) {
   __shared__ TC tile[32][kMaxL + 1];
   const int64_t i0 = (int64_t)bx * 32;
   for (int e = threadIdx.x; e < 32 * l; e += blockDim.x) {
@@ -718,21 +744,28 @@ __device__ __forceinline__ void stage_transpose_body(const TC* __restrict__ Phi,
   for (int e = threadIdx.x; e < l * 32; e += blockDim.x) {
     const int j = e / 32, ii = e % 32;
     const int64_t g = i0 + ii;
-    if (g < len) Xt[j * ldx + g] = tile[ii][j];
+    if (g < len) {
+      Xt[j * ldx + g] = tile[ii][j];
+      if constexpr (sizeof(TC) == 4)
+        if (round_out) round_out[j * ldr + g] = to_tf32(tile[ii][j]);
+    }
   }
 }
 
 template <typename TC>
 __global__ void stage_transpose_kernel(const TC* __restrict__ Phi, int64_t ldphi, int64_t len, int l,
-                                       TC* __restrict__ Xt, int64_t ldx) {
-  stage_transpose_body<TC>(Phi, ldphi, len, l, Xt, ldx, blockIdx.x);
+                                       TC* __restrict__ Xt, int64_t ldx, float* __restrict__ round_out, int64_t ldr) {
+  stage_transpose_body<TC>(Phi, ldphi, len, l, Xt, ldx, blockIdx.x, round_out, ldr);
 }
 
 template <typename TC>
 cudaError_t launch_stage_transpose(const TC* Phi, int64_t ldphi, int64_t len, int l, TC* Xt, int64_t ldx,
-                                   cudaStream_t st) {
+                                   float* round_out, int64_t ldr, cudaStream_t st) {
   const unsigned grid = (unsigned)cdiv(len, 32);
-  if (grid) { stage_transpose_kernel<TC><<<grid, 256, 0, st>>>(Phi, ldphi, len, l, Xt, ldx); CORUTV_COUNT_LAUNCH(); }
+  if (grid) {
+    stage_transpose_kernel<TC><<<grid, 256, 0, st>>>(Phi, ldphi, len, l, Xt, ldx, round_out, ldr);
+    CORUTV_COUNT_LAUNCH();
+  }
   return cudaGetLastError();
 }
 
@@ -1583,12 +1616,13 @@ cudaError_t launch_fro2_grouped(const BatchProb* P, int count, cudaStream_t st) 
   template cudaError_t launch_cholinv<TC>(const double*, int64_t, int, double, double, TC*, TC*, int*, DevStatus*, \
                                           double*, int*, float, cudaStream_t);                                     \
   template cudaError_t launch_lmul<TC>(const TC*, int64_t, int64_t, int, const TC*, int64_t, TC*, int64_t, bool,  \
-                                       const int*, int, const int*, cudaStream_t);                                 \
+                                       const int*, int, const int*, float*, int64_t, cudaStream_t);                \
   template cudaError_t launch_lmul_f64s<TC>(const TC*, int64_t, int64_t, int, const double*, int64_t, TC*,        \
                                             int64_t, bool, cudaStream_t);                                          \
   template cudaError_t launch_gather_cols<TC>(const TC*, int64_t, int64_t, int, const int32_t*, TC*, int64_t,     \
                                               cudaStream_t);                                                       \
-  template cudaError_t launch_stage_transpose<TC>(const TC*, int64_t, int64_t, int, TC*, int64_t, cudaStream_t);  \
+  template cudaError_t launch_stage_transpose<TC>(const TC*, int64_t, int64_t, int, TC*, int64_t, float*, int64_t, \
+                                                  cudaStream_t);                                                  \
   template cudaError_t launch_qrcp<TC>(const double*, int64_t, int, int, double*, int64_t, double*, int64_t, bool, \
                                        int32_t*, double*, DevStatus*, cudaStream_t);
 INST(float)
