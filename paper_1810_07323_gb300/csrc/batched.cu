@@ -377,9 +377,9 @@ int build(corutv_handle* h, BatchState* B, int count, const corutv_problem* prob
     Q.P3 = reinterpret_cast<float*>(take(z.sk3));
     float* Xr = reinterpret_cast<float*>(take(z.xr));
     Q.gparts = reinterpret_cast<float*>(take(z.gparts));
-    Q.G = reinterpret_cast<double*>(take(z.ll8));
-    Q.D = reinterpret_cast<double*>(take(z.ll8));
-    Q.Qt = reinterpret_cast<double*>(take(z.ll8));
+    Q.G = reinterpret_cast<float*>(take(z.ll8));
+    Q.D = reinterpret_cast<float*>(take(z.ll8));
+    Q.Qt = reinterpret_cast<float*>(take(z.ll8));
     Q.R = reinterpret_cast<float*>(take(z.ll4));
     Q.Rinv = reinterpret_cast<float*>(take(z.ll4));
     Q.defic = reinterpret_cast<int*>(take(z.defic));

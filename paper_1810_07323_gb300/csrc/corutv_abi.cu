@@ -58,7 +58,8 @@ struct Plan {
   void *P1, *P2, *P3, *Xr;
   void* partials;
   void* gram_parts;
-  double *G, *D, *Qt, *fro_parts;
+  void *G, *D, *Qt;         // l x l Gram / core / Q~ in the compute type (FP64-sized)
+  double* fro_parts;
   void *R, *Rinv;
   int* defic;
 };
@@ -73,9 +74,9 @@ size_t plan_layout(Plan& pl, void* base) {
   pl.Xr = c.take((size_t)pl.LP * pl.ldr * 4);
   pl.partials = c.take(pl.pass_partials);
   pl.gram_parts = c.take((size_t)pl.gparts * kMaxL * kMaxL * tb);
-  pl.G = static_cast<double*>(c.take(sizeof(double) * kMaxL * kMaxL));
-  pl.D = static_cast<double*>(c.take(sizeof(double) * kMaxL * kMaxL));
-  pl.Qt = static_cast<double*>(c.take(sizeof(double) * kMaxL * kMaxL));
+  pl.G = c.take(sizeof(double) * kMaxL * kMaxL);
+  pl.D = c.take(sizeof(double) * kMaxL * kMaxL);
+  pl.Qt = c.take(sizeof(double) * kMaxL * kMaxL);
   pl.R = c.take((size_t)kMaxL * kMaxL * tb);
   pl.Rinv = c.take((size_t)kMaxL * kMaxL * tb);
   pl.defic = static_cast<int*>(c.take(sizeof(int) * kMaxL));
@@ -270,19 +271,20 @@ int orth_st(corutv_handle* h, TC* Ct, int64_t ldc, int64_t len, int l, const Pla
   const bool f64 = sizeof(TC) == 8;
   PhaseTimer tm(h, kPhOrth);
   for (int pass = 0; pass < passes; ++pass) {
-    CU(launch_gram<TC>(Ct, ldc, Ct, ldc, len, l, static_cast<TC*>(pl.gram_parts), gram_parts(len, h->sms), pl.G,
-                       kMaxL, h->stream));
+    CU((launch_gram<TC, TC>(Ct, ldc, Ct, ldc, len, l, static_cast<TC*>(pl.gram_parts), gram_parts(len, h->sms),
+                           static_cast<TC*>(pl.G),
+                       kMaxL, h->stream)));
     const double shift = pass == 0 ? (f64 ? kShiftRel64 : kShiftRel32) : 0.0;
     const double tol = f64 ? kTolRel64 : kTolRel32;
     int* skip = (!f64 && passes == 3 && pass == 2) ? &pl.status->orth_skip : nullptr;
-    double* rpass = Rout ? (pass == 0 ? Rout : pl.D) : nullptr;
-    CU(launch_cholinv<TC>(pl.G, kMaxL, l, shift, tol, static_cast<TC*>(pl.R), static_cast<TC*>(pl.Rinv), pl.defic,
+    double* rpass = Rout ? (pass == 0 ? Rout : static_cast<double*>(pl.D)) : nullptr;
+    CU(launch_cholinv<TC>(static_cast<const TC*>(pl.G), kMaxL, l, shift, tol, static_cast<TC*>(pl.R), static_cast<TC*>(pl.Rinv), pl.defic,
                           pl.status, rpass, skip, kSkipTol32, h->stream));
     CU(launch_lmul<TC>(Ct, ldc, len, l, static_cast<const TC*>(pl.Rinv), kMaxL, Ct, ldc, false, pl.defic, pass,
                        skip, pass == passes - 1 ? round_out : nullptr, ldr, h->stream));
     if (Rout && pass > 0) {
       // R <- R_pass R
-      CU(launch_upper_mul(pl.D, Rout, pl.Qt, l, h->stream));
+      CU(launch_upper_mul(static_cast<const double*>(pl.D), Rout, static_cast<double*>(pl.Qt), l, h->stream));
       CU(cudaMemcpyAsync(Rout, pl.Qt, sizeof(double) * l * l, cudaMemcpyDeviceToDevice, h->stream));
     }
   }
@@ -362,34 +364,37 @@ int solve_impl(corutv_handle* h, const corutv_params* p, const Plan& pl, const v
     if (rc) return rc;
     ++passes;
     PhaseTimer tm(h, kPhCore);
-    CU(launch_gram<TC>(P1, pl.ld1, P3, pl.ld3, pl.len1, l, static_cast<TC*>(pl.gram_parts),
-                       gram_parts(pl.len1, h->sms), pl.D, kMaxL, h->stream));   // D = Q1^T E
+    CU((launch_gram<TC, TC>(P1, pl.ld1, P3, pl.ld3, pl.len1, l, static_cast<TC*>(pl.gram_parts),
+                           gram_parts(pl.len1, h->sms), static_cast<TC*>(pl.D), kMaxL, h->stream)));   // D = Q1^T E
   } else if (p->core == CORUTV_CORE_EXACT) {
     int rc = run_pass(h, dir1, p->a_dtype, p->mma, A, lda, p->m, p->n, scales, P2, pl.ld2, l, P3, pl.ld3,
                       pl.partials, Xr, pl.ldr, nullptr, kPhPass, pre_round);   // E = A Q2 (ST, len1)
     if (rc) return rc;
     ++passes;
     PhaseTimer tm(h, kPhCore);
-    CU(launch_gram<TC>(P1, pl.ld1, P3, pl.ld3, pl.len1, l, static_cast<TC*>(pl.gram_parts),
-                       gram_parts(pl.len1, h->sms), pl.D, kMaxL, h->stream));   // D = Q1^T E
+    CU((launch_gram<TC, TC>(P1, pl.ld1, P3, pl.ld3, pl.len1, l, static_cast<TC*>(pl.gram_parts),
+                           gram_parts(pl.len1, h->sms), static_cast<TC*>(pl.D), kMaxL, h->stream)));   // D = Q1^T E
   } else {
     PhaseTimer tm(h, kPhCore);
     // D = Q1^T A Q2 = (A^T Q1)^T Q2 = C2^T Q2 with the saved C2 (ST, len2)
-    CU(launch_gram<TC>(P3, pl.ld3, P2, pl.ld2, pl.len2, l, static_cast<TC*>(pl.gram_parts),
-                       gram_parts(pl.len2, h->sms), pl.D, kMaxL, h->stream));
+    CU((launch_gram<TC, TC>(P3, pl.ld3, P2, pl.ld2, pl.len2, l, static_cast<TC*>(pl.gram_parts),
+                           gram_parts(pl.len2, h->sms), static_cast<TC*>(pl.D), kMaxL, h->stream)));
   }
   {
     // S6: QRCP of D (Alg. 2 step 6); T = R~ (RIGHT) or R~^T (LEFT)
     PhaseTimer tm(h, kPhQrcp);
-    CU(launch_qrcp<TC>(pl.D, kMaxL, l, p->k, pl.Qt, kMaxL, T, ldt, !right, perm, nullptr, pl.status, h->stream));
+    CU(launch_qrcp<TC>(static_cast<const TC*>(pl.D), kMaxL, l, p->k, static_cast<TC*>(pl.Qt), kMaxL, T, ldt, !right,
+                       perm, nullptr, pl.status, h->stream));
   }
   // S7: assembly (Alg. 2 step 7): Q1 Q~ and Q2 P~
   PhaseTimer tm_asm(h, kPhAsm);
   if (right) {
-    CU(launch_lmul_f64s<TC>(P1, pl.ld1, pl.len1, l, pl.Qt, kMaxL, static_cast<TC*>(U), ldu, true, h->stream));
+    CU(launch_lmul_full<TC>(P1, pl.ld1, pl.len1, l, static_cast<const TC*>(pl.Qt), kMaxL, static_cast<TC*>(U), ldu,
+                            true, h->stream));
     CU(launch_gather_cols<TC>(P2, pl.ld2, pl.len2, l, perm, static_cast<TC*>(V), ldv, h->stream));
   } else {
-    CU(launch_lmul_f64s<TC>(P1, pl.ld1, pl.len1, l, pl.Qt, kMaxL, static_cast<TC*>(V), ldv, true, h->stream));
+    CU(launch_lmul_full<TC>(P1, pl.ld1, pl.len1, l, static_cast<const TC*>(pl.Qt), kMaxL, static_cast<TC*>(V), ldv,
+                            true, h->stream));
     CU(launch_gather_cols<TC>(P2, pl.ld2, pl.len2, l, perm, static_cast<TC*>(U), ldu, h->stream));
   }
   // S9: ||A||_F^2 on request
@@ -682,11 +687,11 @@ int corutv_gram(corutv_handle* h, int dtype, const void* Xt, int64_t ldx, const 
   int rc = block_ws(h, len, len, l, dtype, pl);
   if (rc) return rc;
   if (dtype == CORUTV_F64)
-    CU(launch_gram<double>(static_cast<const double*>(Xt), ldx, static_cast<const double*>(Yt), ldy, len, l,
-                           static_cast<double*>(pl.gram_parts), gram_parts(len, h->sms), G, l, h->stream));
+    CU((launch_gram<double, double>(static_cast<const double*>(Xt), ldx, static_cast<const double*>(Yt), ldy, len, l,
+                                   static_cast<double*>(pl.gram_parts), gram_parts(len, h->sms), G, l, h->stream)));
   else
-    CU(launch_gram<float>(static_cast<const float*>(Xt), ldx, static_cast<const float*>(Yt), ldy, len, l,
-                          static_cast<float*>(pl.gram_parts), gram_parts(len, h->sms), G, l, h->stream));
+    CU((launch_gram<float, double>(static_cast<const float*>(Xt), ldx, static_cast<const float*>(Yt), ldy, len, l,
+                                  static_cast<float*>(pl.gram_parts), gram_parts(len, h->sms), G, l, h->stream)));
   return CORUTV_OK;
 }
 
@@ -696,9 +701,9 @@ int corutv_qrcp(corutv_handle* h, int dtype, const double* D, int64_t ldd, int32
   if (dtype != CORUTV_F32 && dtype != CORUTV_F64) return CORUTV_ERR_INVALID_ARG;
   if (l < 1 || l > (dtype == CORUTV_F64 ? kMaxL64 : kMaxL) || ldd < l || k < 0 || k > l) return CORUTV_ERR_SHAPE;
   if (dtype == CORUTV_F64)
-    CU(launch_qrcp<double>(D, ldd, l, k, Q, l, R, l, false, perm, fro2, nullptr, h->stream));
+    CU(launch_qrcp_f64io<double>(D, ldd, l, k, Q, l, R, l, perm, fro2, h->stream));
   else
-    CU(launch_qrcp<float>(D, ldd, l, k, Q, l, R, l, false, perm, fro2, nullptr, h->stream));
+    CU(launch_qrcp_f64io<float>(D, ldd, l, k, Q, l, R, l, perm, fro2, h->stream));
   return CORUTV_OK;
 }
 

@@ -73,14 +73,15 @@ cudaError_t launch_quantize(int dtype, const float* A, int64_t lda, int64_t m, i
 __global__ void sum_parts_kernel(const double* __restrict__ parts, int n, double* out, DevStatus* status);
 
 // small.cu
-template <typename TC>
+// G = X Y^T (l x l, type TG) of two ST blocks: per-CTA partials, then an ordered reduction
+template <typename TC, typename TG>
 cudaError_t launch_gram(const TC* Xt, int64_t ldx, const TC* Yt, int64_t ldy, int64_t len, int l, TC* parts,
-                        int gparts, double* G, int64_t ldg, cudaStream_t st);
+                        int gparts, TG* G, int64_t ldg, cudaStream_t st);
 int gram_parts(int64_t len, int sms);
 // skip_flag (FP32 only, may be null): skip the factorisation when max |G - I| <= skip_tol
 // (writes *skip_flag = 1 and R_out = I); launch_lmul with the same flag then does nothing
 template <typename TC>
-cudaError_t launch_cholinv(const double* G, int64_t ldg, int l, double shift_rel, double tol_rel, TC* R, TC* Rinv,
+cudaError_t launch_cholinv(const TC* G, int64_t ldg, int l, double shift_rel, double tol_rel, TC* R, TC* Rinv,
                            int* defic, DevStatus* status, double* Rout, int* skip_flag, float skip_tol,
                            cudaStream_t st);
 // Out = S^T In on ST blocks (S upper triangular); rows j with defic[j] set (defic may be
@@ -91,8 +92,9 @@ template <typename TC>
 cudaError_t launch_lmul(const TC* In, int64_t ldi, int64_t len, int l, const TC* S, int64_t lds, TC* Out,
                         int64_t ldo, bool out_rowmajor, const int* defic, int pass, const int* skip_flag,
                         float* round_out, int64_t ldr, cudaStream_t st);
+// Out = S^T In for a full l x l S
 template <typename TC>
-cudaError_t launch_lmul_f64s(const TC* In, int64_t ldi, int64_t len, int l, const double* S, int64_t lds, TC* Out,
+cudaError_t launch_lmul_full(const TC* In, int64_t ldi, int64_t len, int l, const TC* S, int64_t lds, TC* Out,
                              int64_t ldo, bool out_rowmajor, cudaStream_t st);
 // C = A B for upper-triangular l x l FP64 matrices (row-major, ld l; C distinct from A, B)
 cudaError_t launch_upper_mul(const double* A, const double* B, double* C, int l, cudaStream_t st);
@@ -102,9 +104,14 @@ cudaError_t launch_gather_cols(const TC* St, int64_t lds, int64_t len, int l, co
 template <typename TC>
 cudaError_t launch_stage_transpose(const TC* Phi, int64_t ldphi, int64_t len, int l, TC* Xt, int64_t ldx,
                                    float* round_out, int64_t ldr, cudaStream_t st);
+// QRCP of the l x l core (TC = FP32: D and Q~ in FP32; FP64: in FP64); R (= T) is FP64
 template <typename TC>
-cudaError_t launch_qrcp(const double* D, int64_t ldd, int l, int k, double* Q, int64_t ldq, double* R, int64_t ldr,
+cudaError_t launch_qrcp(const TC* D, int64_t ldd, int l, int k, TC* Q, int64_t ldq, double* R, int64_t ldr,
                         bool r_transposed, int32_t* perm, double* fro2, DevStatus* status, cudaStream_t st);
+// the same from an FP64 D to an FP64 Q~, with the arithmetic of TC (the building-block call)
+template <typename TC>
+cudaError_t launch_qrcp_f64io(const double* D, int64_t ldd, int l, int k, double* Q, int64_t ldq, double* R,
+                              int64_t ldr, int32_t* perm, double* fro2, cudaStream_t st);
 cudaError_t launch_fro2(int a_dtype, const void* A, int64_t lda, int64_t m, int64_t n, const float* scales,
                         int64_t sld, double* parts, int nparts, double* out, cudaStream_t st);
 int fro2_parts(int sms);
@@ -133,7 +140,7 @@ struct BatchProb {
   int64_t ld1, ld2, ld3;
   float* gparts;        // Gram partial blocks (LP x LP each)
   int gp1, gp2;         // partial blocks for sketches of length len1 / len2
-  double *G, *D, *Qt;
+  float *G, *D, *Qt;    // l x l Gram / core / Q~ (FP32)
   float *R, *Rinv;
   int* defic;
   double* fparts;       // ||A||^2 partials, one per tile of the first pass

@@ -77,10 +77,10 @@ extern "C" int corutv_gram_noalloc(void* stream, int dtype, const void* Xt, int6
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaError_t err;
   if (dtype == CORUTV_F64)
-    err = launch_gram<double>(static_cast<const double*>(Xt), ldx, static_cast<const double*>(Yt), ldy, len, l,
+    err = launch_gram<double, double>(static_cast<const double*>(Xt), ldx, static_cast<const double*>(Yt), ldy, len, l,
                               static_cast<double*>(scratch), parts, G, l, st);
   else
-    err = launch_gram<float>(static_cast<const float*>(Xt), ldx, static_cast<const float*>(Yt), ldy, len, l,
+    err = launch_gram<float, double>(static_cast<const float*>(Xt), ldx, static_cast<const float*>(Yt), ldy, len, l,
                              static_cast<float*>(scratch), parts, G, l, st);
   return err == cudaSuccess ? CORUTV_OK : CORUTV_ERR_CUDA;
 }

@@ -95,37 +95,79 @@ __global__ void __launch_bounds__(512) gram_partial_kernel(const TC* __restrict_
   gram_partial_body<TC, LP>(Xt, ldx, Yt, ldy, len, l, parts, blockIdx.x, gridDim.x);
 }
 
-// G[a][b] = sum over parts in a fixed order, in FP64: four threads per element
-// each sum every fourth part, then (s0 + s1) + (s2 + s3).
-template <typename TC>
+// Error-free sum of two FP32 numbers (Knuth's TwoSum): s = fl(a + b), a + b = s + e exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bp = s - a;
+  e = (a - (s - bp)) + (b - bp);
+}
+
+// G[a][b] = sum over parts in a fixed order: four threads per element each sum
+// every fourth part, then (s0 + s1) + (s2 + s3).  FP64 sketches: FP64 sums.  FP32
+// sketches: compensated FP32 sums (TwoSum, the rounding errors carried in a second
+// word), as accurate as an FP64 sum of these few hundred terms at the FP32 rate
+// (GB300's FP64 pipe is ~1/64 of it); the output is the rounded pair, in TG.
+template <typename TC, typename TG>
 __device__ __forceinline__ void gram_reduce_body(const TC* __restrict__ parts, int nparts, int LP, int l,
-                                                 double* __restrict__ G, int64_t ldg, int gtid) {
+                                                 TG* __restrict__ G, int64_t ldg, int gtid) {
   const int e = gtid >> 2;
   const int q = threadIdx.x & 3;
   const bool ok = e < l * l;
   const int a = ok ? e / l : 0, b = ok ? e % l : 0;
-  double s = 0.0;
-  if (ok) {
-    const TC* src = parts + (int64_t)a * LP + b;
-    const int64_t stride = (int64_t)LP * LP;
-    int p = q;
-    for (; p + 12 < nparts; p += 16) {
-      const double v0 = (double)src[p * stride], v1 = (double)src[(p + 4) * stride];
-      const double v2 = (double)src[(p + 8) * stride], v3 = (double)src[(p + 12) * stride];
-      s += v0; s += v1; s += v2; s += v3;
+  const TC* src = parts + (int64_t)a * LP + b;
+  const int64_t stride = (int64_t)LP * LP;
+  if constexpr (sizeof(TC) == 8) {
+    double s = 0.0;
+    if (ok) {
+      int p = q;
+      for (; p + 12 < nparts; p += 16) {
+        const double v0 = src[p * stride], v1 = src[(p + 4) * stride];
+        const double v2 = src[(p + 8) * stride], v3 = src[(p + 12) * stride];
+        s += v0; s += v1; s += v2; s += v3;
+      }
+      for (; p < nparts; p += 4) s += src[p * stride];
     }
-    for (; p < nparts; p += 4) s += (double)src[p * stride];
+    const double s1 = __shfl_xor_sync(0xffffffffu, s, 1);
+    const double t = (q & 1) ? s1 + s : s + s1;                 // (s0 + s1), (s2 + s3)
+    const double t2 = __shfl_xor_sync(0xffffffffu, t, 2);
+    if (ok && q == 0) G[a * ldg + b] = (TG)(t + t2);
+  } else {
+    float s = 0.f, c = 0.f, er;
+    if (ok) {
+      int p = q;
+      for (; p + 12 < nparts; p += 16) {
+        const float v0 = src[p * stride], v1 = src[(p + 4) * stride];
+        const float v2 = src[(p + 8) * stride], v3 = src[(p + 12) * stride];
+        two_sum(s, v0, s, er); c += er;
+        two_sum(s, v1, s, er); c += er;
+        two_sum(s, v2, s, er); c += er;
+        two_sum(s, v3, s, er); c += er;
+      }
+      for (; p < nparts; p += 4) {
+        two_sum(s, src[p * stride], s, er);
+        c += er;
+      }
+    }
+#pragma unroll
+    for (int o = 1; o <= 2; o <<= 1) {       // (s0 + s1), (s2 + s3), then their sum; lower index first
+      const float so = __shfl_xor_sync(0xffffffffu, s, o), co = __shfl_xor_sync(0xffffffffu, c, o);
+      const bool lo = (q & o) == 0;
+      float t;
+      two_sum(lo ? s : so, lo ? so : s, t, er);
+      c = (lo ? c + co : co + c) + er;
+      s = t;
+    }
+    if (ok && q == 0) {
+      if constexpr (sizeof(TG) == 8) G[a * ldg + b] = (double)s + (double)c;
+      else G[a * ldg + b] = s + c;
+    }
   }
-  const double s1 = __shfl_xor_sync(0xffffffffu, s, 1);
-  const double t = (q & 1) ? s1 + s : s + s1;                 // (s0 + s1), (s2 + s3)
-  const double t2 = __shfl_xor_sync(0xffffffffu, t, 2);
-  if (ok && q == 0) G[a * ldg + b] = t + t2;
 }
 
-template <typename TC>
-__global__ void gram_reduce_kernel(const TC* __restrict__ parts, int nparts, int LP, int l, double* __restrict__ G,
+template <typename TC, typename TG>
+__global__ void gram_reduce_kernel(const TC* __restrict__ parts, int nparts, int LP, int l, TG* __restrict__ G,
                                    int64_t ldg) {
-  gram_reduce_body<TC>(parts, nparts, LP, l, G, ldg, blockIdx.x * blockDim.x + threadIdx.x);
+  gram_reduce_body<TC, TG>(parts, nparts, LP, l, G, ldg, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 int gram_parts(int64_t len, int sms) {
@@ -134,9 +176,9 @@ int gram_parts(int64_t len, int sms) {
   return (int)(p < 1 ? 1 : p);
 }
 
-template <typename TC>
+template <typename TC, typename TG>
 cudaError_t launch_gram(const TC* Xt, int64_t ldx, const TC* Yt, int64_t ldy, int64_t len, int l, TC* parts,
-                        int gparts, double* G, int64_t ldg, cudaStream_t st) {
+                        int gparts, TG* G, int64_t ldg, cudaStream_t st) {
   int LP;
   if (l <= 32) {
     LP = 32;
@@ -148,7 +190,8 @@ cudaError_t launch_gram(const TC* Xt, int64_t ldx, const TC* Yt, int64_t ldy, in
     LP = 128;
     gram_partial_kernel<TC, 128><<<gparts, 512, 0, st>>>(Xt, ldx, Yt, ldy, len, l, parts); CORUTV_COUNT_LAUNCH();
   }
-  gram_reduce_kernel<TC><<<(unsigned)cdiv((int64_t)l * l * 4, 256), 256, 0, st>>>(parts, gparts, LP, l, G, ldg); CORUTV_COUNT_LAUNCH();
+  gram_reduce_kernel<TC, TG><<<(unsigned)cdiv((int64_t)l * l * 4, 256), 256, 0, st>>>(parts, gparts, LP, l, G, ldg);
+  CORUTV_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 
@@ -235,6 +278,36 @@ __global__ void __launch_bounds__(512) cholinv_kernel(const double* __restrict__
   if (lane == 0 && nfall && status) atomicAdd(&status->chol_fallbacks, nfall);
 }
 
+// FP32 variant, blocked: G + s I = L L^T by a right-looking Cholesky over
+// 32 x 32 diagonal blocks, then R = L^T and R^-1 = L^-T.  Per block column k:
+//   (a) one warp factors the diagonal block (lane i holds row i in registers,
+//       column j broadcast by shuffles) and forms its inverse X_kk = L_kk^-1;
+//   (b) the panel below it becomes L_ik = A_ik X_kk^T;
+//   (c) the trailing lower blocks take A_ij -= L_ik L_jk^T.
+// The off-diagonal blocks of L^-1 follow by block distance d = i - j:
+// X_ij = -X_ii (sum_{p=j}^{i-1} L_ip X_pj).  About 20 block barriers at l = 128
+// instead of one per column.  A pivot d <= tol_rel * (G_jj + s) marks column j
+// dependent: L[j][j] = 1 and the rest of column j is zero, so it eliminates
+// nothing, R[j][j] = 1, R[j][>j] = 0, defic[j] = 1 (the caller replaces that
+// column of Q).  The matrix is padded to 32 * ceil(l / 32) with the identity.
+// Reciprocal and reciprocal square root for the latency-bound one-CTA kernels:
+// the hardware approximation (MUFU) refined by one Newton-Raphson step,
+// y <- y (2 - x y) for 1 / x and r <- r (3 - x r^2) / 2 for 1 / sqrt(x), which
+// roughly doubles the correct bits (about 1 ulp after the step).  Inputs below
+// the smallest normal number take the IEEE path (the approximations flush
+// them).  The IEEE operators are not used on the common path: they branch to
+// a subroutine that costs hundreds of cycles per call in a large kernel.
+__device__ __forceinline__ float rcp_nr(float x) {
+  if (!(fabsf(x) >= 1.17549435e-38f)) return 1.f / x;
+  const float y = __fdividef(1.f, x);
+  return y * fmaf(-x, y, 2.f);
+}
+__device__ __forceinline__ float rsqrt_nr(float x) {
+  if (!(x >= 1.17549435e-38f)) return 1.f / sqrtf(x);
+  const float r = rsqrtf(x);
+  return r * fmaf(-0.5f * x * r, r, 1.5f);
+}
+
 // FP32 variant with the matrices in registers: the same elimination of
 // [G + s I | I] as cholinv_kernel, with the upper triangle of G and the lower
 // triangle of L^-1 split into 4 x 4 blocks.  Thread t owns block (I, J), J >= I,
@@ -253,7 +326,7 @@ constexpr int kPipeMaxThreads = (kMaxL / 4) * (kMaxL / 4 + 1) / 2 + 16;   // 528
 // block; at or below skip_tol it writes 1 to *skip_flag, R_out = I (if asked)
 // and returns (the caller's Q already has orthonormal columns to that level),
 // otherwise it writes 0 and factors as usual.
-__device__ __forceinline__ void cholinv_pipe_body(const double* __restrict__ G, int64_t ldg, int l, double shift_rel,
+__device__ __forceinline__ void cholinv_pipe_body(const float* __restrict__ G, int64_t ldg, int l, double shift_rel,
                                                   double tol_rel, float* __restrict__ Rg, float* __restrict__ Rinvg,
                                                   int64_t ldr, int* __restrict__ defic, DevStatus* status,
                                                   double* __restrict__ Rout, int* __restrict__ skip_flag,
@@ -262,8 +335,9 @@ __device__ __forceinline__ void cholinv_pipe_body(const double* __restrict__ G, 
   __shared__ __align__(16) float libuf[2][kMaxL];
   __shared__ float diag0[kMaxL];
   __shared__ float piv[kMaxL];
+  __shared__ float pivrs[kMaxL];     // 1 / sqrt(piv)
   __shared__ int dep_s[kMaxL];
-  __shared__ double red[32];
+  __shared__ float red[32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   const int nb = (l + 3) >> 2;
   const bool own = tid < nb * (nb + 1) / 2;
@@ -277,42 +351,42 @@ __device__ __forceinline__ void cholinv_pipe_body(const double* __restrict__ G, 
     I = i;
     J = i + t;
   }
-  __shared__ double redmax[32];
+  __shared__ float redmax[32];
   float g[4][4], li[4][4];
-  double tr = 0.0, dev = 0.0;
+  float tr = 0.f, dev = 0.f;
 #pragma unroll
   for (int r = 0; r < 4; ++r)
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       const int a = 4 * I + r, b = 4 * J + c;
-      const double gv = (own && a < l && b < l) ? G[a * ldg + b] : 0.0;
-      if (own && a < l && b < l) dev = fmax(dev, fabs(gv - (a == b ? 1.0 : 0.0)));
-      g[r][c] = (float)gv;
+      const bool in = own && a < l && b < l;
+      g[r][c] = in ? G[a * ldg + b] : 0.f;
+      if (in) dev = fmaxf(dev, fabsf(g[r][c] - (a == b ? 1.f : 0.f)));
       li[r][c] = (4 * J + r == 4 * I + c) ? 1.f : 0.f;
     }
   if (own && I == J) {
 #pragma unroll
     for (int r = 0; r < 4; ++r)
-      if (4 * I + r < l) tr += (double)g[r][r];
+      if (4 * I + r < l) tr += g[r][r];
   }
   for (int e = tid; e < 2 * kMaxL; e += blockDim.x) (&libuf[0][0])[e] = 0.f;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     tr += __shfl_xor_sync(0xffffffffu, tr, o);
-    dev = fmax(dev, __shfl_xor_sync(0xffffffffu, dev, o));
+    dev = fmaxf(dev, __shfl_xor_sync(0xffffffffu, dev, o));
   }
   if (lane == 0) {
     red[warp] = tr;
     redmax[warp] = dev;
   }
   __syncthreads();
-  double trace = 0.0, devmax = 0.0;
+  float trace = 0.f, devmax = 0.f;
   for (int w = 0; w < nw; ++w) {
     trace += red[w];
-    devmax = fmax(devmax, redmax[w]);
+    devmax = fmaxf(devmax, redmax[w]);
   }
   if (skip_flag) {
-    const bool skip = devmax <= (double)skip_tol;
+    const bool skip = devmax <= skip_tol;
     if (tid == 0) *skip_flag = skip ? 1 : 0;
     if (skip) {
       if (Rout)
@@ -320,7 +394,7 @@ __device__ __forceinline__ void cholinv_pipe_body(const double* __restrict__ G, 
       return;
     }
   }
-  const float shift = (float)(shift_rel * trace);
+  const float shift = (float)shift_rel * trace;
   const float tolf = (float)tol_rel;
   if (own) {
     if (I == J) {
@@ -344,9 +418,10 @@ __device__ __forceinline__ void cholinv_pipe_body(const double* __restrict__ G, 
     const float d = rowbuf[buf][j];
     const float d0 = diag0[j];
     const bool dep = !(d > tolf * d0) || !(d0 > 0.f);
-    const float inv_d = dep ? 0.f : 1.f / d;
+    const float inv_d = dep ? 0.f : rcp_nr(d);
     if (tid == 0) {
       piv[j] = dep ? 1.f : d;
+      pivrs[j] = dep ? 1.f : rsqrt_nr(d);
       dep_s[j] = dep ? 1 : 0;
     }
     if (own) {
@@ -386,9 +461,9 @@ __device__ __forceinline__ void cholinv_pipe_body(const double* __restrict__ G, 
         const int a = 4 * I + r, b = 4 * J + c;
         if (a >= l || b >= l) continue;
         float rv = 0.f, xv = 0.f;
-        if (b == a) rv = sqrtf(piv[a]);
-        else if (b > a && !dep_s[a]) rv = g[r][c] / sqrtf(piv[a]);
-        if (b >= a) xv = li[c][r] / sqrtf(piv[b]);
+        if (b == a) rv = piv[a] * pivrs[a];
+        else if (b > a && !dep_s[a]) rv = g[r][c] * pivrs[a];
+        if (b >= a) xv = li[c][r] * pivrs[b];
         Rg[a * ldr + b] = rv;
         Rinvg[a * ldr + b] = xv;
         if (Rout) Rout[a * l + b] = (double)rv;
@@ -409,14 +484,32 @@ __device__ __forceinline__ void cholinv_pipe_body(const double* __restrict__ G, 
 }
 
 __global__ void __launch_bounds__(kPipeMaxThreads, 1) cholinv_pipe_kernel(
-    const double* __restrict__ G, int64_t ldg, int l, double shift_rel, double tol_rel, float* __restrict__ Rg,
+    const float* __restrict__ G, int64_t ldg, int l, double shift_rel, double tol_rel, float* __restrict__ Rg,
     float* __restrict__ Rinvg, int* __restrict__ defic, DevStatus* status, double* __restrict__ Rout,
     int* __restrict__ skip_flag, float skip_tol) {
   cholinv_pipe_body(G, ldg, l, shift_rel, tol_rel, Rg, Rinvg, kMaxL, defic, status, Rout, skip_flag, skip_tol);
 }
 
+// Shared-memory limits are raised once per kernel and device (before any stream
+// capture records the launches).
+constexpr int kAttrDevices = 64;
+static bool* attr_flag(bool (&flags)[kAttrDevices]) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kAttrDevices) return nullptr;
+  return &flags[dev];
+}
+
+template <typename K>
+static cudaError_t raise_smem_once(K kernel, size_t bytes, bool (&flags)[kAttrDevices]) {
+  bool* flag = attr_flag(flags);
+  if (flag && *flag) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess && flag) *flag = true;
+  return e;
+}
+
 template <typename TC>
-cudaError_t launch_cholinv(const double* G, int64_t ldg, int l, double shift_rel, double tol_rel, TC* R, TC* Rinv,
+cudaError_t launch_cholinv(const TC* G, int64_t ldg, int l, double shift_rel, double tol_rel, TC* R, TC* Rinv,
                            int* defic, DevStatus* status, double* Rout, int* skip_flag, float skip_tol,
                            cudaStream_t st) {
   if constexpr (sizeof(TC) == 4) {
@@ -426,12 +519,14 @@ cudaError_t launch_cholinv(const double* G, int64_t ldg, int l, double shift_rel
                                                skip_flag, skip_tol);
     CORUTV_COUNT_LAUNCH();
     return cudaGetLastError();
+  } else {
+    const size_t smem = (size_t)2 * l * (l + 1) * sizeof(TC);
+    cudaError_t e = cudaFuncSetAttribute(cholinv_kernel<TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    cholinv_kernel<TC><<<1, 512, smem, st>>>(G, ldg, l, shift_rel, tol_rel, R, Rinv, defic, status, Rout);
+    CORUTV_COUNT_LAUNCH();
+    return cudaGetLastError();
   }
-  const size_t smem = (size_t)2 * l * (l + 1) * sizeof(TC);
-  cudaError_t e = cudaFuncSetAttribute(cholinv_kernel<TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  cholinv_kernel<TC><<<1, 512, smem, st>>>(G, ldg, l, shift_rel, tol_rel, R, Rinv, defic, status, Rout); CORUTV_COUNT_LAUNCH();
-  return cudaGetLastError();
 }
 
 // Dependent columns: row j of an ST block (column j of Q) flagged dependent is
@@ -667,10 +762,10 @@ cudaError_t launch_lmul(const TC* In, int64_t ldi, int64_t len, int l, const TC*
                                round_out, ldr, st);
 }
 template <typename TC>
-cudaError_t launch_lmul_f64s(const TC* In, int64_t ldi, int64_t len, int l, const double* S, int64_t lds, TC* Out,
+cudaError_t launch_lmul_full(const TC* In, int64_t ldi, int64_t len, int l, const TC* S, int64_t lds, TC* Out,
                              int64_t ldo, bool out_rowmajor, cudaStream_t st) {
-  return lmul_dispatch<TC, double>(In, ldi, len, l, S, lds, Out, ldo, out_rowmajor, false, nullptr, 0, nullptr,
-                                   nullptr, 0, st);
+  return lmul_dispatch<TC, TC>(In, ldi, len, l, S, lds, Out, ldo, out_rowmajor, false, nullptr, 0, nullptr, nullptr,
+                               0, st);
 }
 
 // =============================================================================== R composition
@@ -1019,46 +1114,18 @@ __global__ void __launch_bounds__(512) qrcp_kernel(const double* __restrict__ Dg
 }
 
 // FP32 variant with columns in registers: thread (c, h) holds rows
-// i = 64 h .. 64 h + 63 of column c, so every column reduction is a per-thread
-// sum (four independent partial sums) plus one shuffle.  The published
-// reflector is zero outside rows j..l-1, so it is applied with unpredicated
-// vector loads.  Step j: trailing norms are published by position; after a
-// barrier every warp evaluates the same argmax and applies the same swap to
-// its copy of the position map; the two threads of the pivot column publish
-// the reflector; after a second barrier every trailing column is updated and
-// its trailing norm recomputed exactly.  Same choices as the warp-per-column
-// kernel (first maximum by current position).
-template <int N>
-__device__ __forceinline__ float dotN(const float* __restrict__ v, const float (&x)[N]) {
-  float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-  const float4* v4 = reinterpret_cast<const float4*>(v);
-#pragma unroll
-  for (int q = 0; q < N / 4; ++q) {
-    const float4 t = v4[q];
-    s0 = fmaf(t.x, x[4 * q + 0], s0);
-    s1 = fmaf(t.y, x[4 * q + 1], s1);
-    s2 = fmaf(t.z, x[4 * q + 2], s2);
-    s3 = fmaf(t.w, x[4 * q + 3], s3);
-  }
-  return (s0 + s1) + (s2 + s3);
-}
-
-template <int N>
-__device__ __forceinline__ void axpyN(const float* __restrict__ v, float f, float (&x)[N]) {
-  const float4* v4 = reinterpret_cast<const float4*>(v);
-#pragma unroll
-  for (int q = 0; q < N / 4; ++q) {
-    const float4 t = v4[q];
-    x[4 * q + 0] = fmaf(-f, t.x, x[4 * q + 0]);
-    x[4 * q + 1] = fmaf(-f, t.y, x[4 * q + 1]);
-    x[4 * q + 2] = fmaf(-f, t.z, x[4 * q + 2]);
-    x[4 * q + 3] = fmaf(-f, t.w, x[4 * q + 3]);
-  }
-}
-
-template <int TPC>
-__device__ __forceinline__ void qrcp_reg_body(const double* __restrict__ Dg, int64_t ldd, int l, int k,
-                                              double* __restrict__ Qg, int64_t ldq, double* __restrict__ Rg,
+// i = RPT h .. RPT h + RPT - 1 of column c of D and of M = H_j ... H_0 (TPC
+// threads per column), so every column reduction is a per-thread sum plus
+// TPC - 1 shuffles.  Step j: warp 0 picks the pivot from the trailing norms
+// (first maximum by current position) and applies the swap to its position
+// map; the pivot column's warp builds the reflector and publishes it; every
+// trailing column (and every column of M) takes it and recomputes its trailing
+// norm exactly.  Three block barriers per step: the pivot choice and the
+// reflector are each formed once, which costs less than forming them in every
+// warp.  Same choices as the textbook algorithm with physical column exchanges.
+template <int TPC, typename TD, typename TQ>
+__device__ __forceinline__ void qrcp_reg_body(const TD* __restrict__ Dg, int64_t ldd, int l, int k,
+                                              TQ* __restrict__ Qg, int64_t ldq, double* __restrict__ Rg,
                                               int64_t ldr, int r_transposed, int32_t* __restrict__ perm,
                                               double* __restrict__ fro2, DevStatus* status) {
   constexpr int RPT = kMaxL / TPC, NWARP = kMaxL * TPC / 32, CPW = 32 / TPC;   // columns per warp
@@ -1150,14 +1217,14 @@ __device__ __forceinline__ void qrcp_reg_body(const double* __restrict__ Dg, int
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
       const float x0 = pcolv[j];
-      const float nrm = sqrtf(ss);
+      const float nrm = (ss > 0.f) ? ss * rsqrt_nr(ss) : 0.f;
       float alpha, v0, beta;
       if (nrm == 0.f) {
         alpha = 0.f; v0 = 1.f; beta = 0.f;
       } else {
         alpha = (x0 >= 0.f) ? -nrm : nrm;
         v0 = x0 - alpha;
-        beta = 1.f / (nrm * (nrm + fabsf(x0)));
+        beta = rcp_nr(nrm * (nrm + fabsf(x0)));
       }
       float4 vo;
       float* vp = &vo.x;
@@ -1212,8 +1279,16 @@ __device__ __forceinline__ void qrcp_reg_body(const double* __restrict__ Dg, int
     }
     __syncthreads();
   }
-  // R from each pivot column (rows above its position), diag(R) >= 0
-  double fa = 0.0, fb = 0.0;
+  // R from each pivot column (rows above its position), diag(R) >= 0; ||R||_F^2 and
+  // ||R(1:k, :)||_F^2 as compensated FP32 sums (exact squares, TwoSum), in FP64 across warps
+  float fa = 0.f, fae = 0.f, fb = 0.f, fbe = 0.f;
+  auto acc_sq = [](float v, float& sum, float& err) {
+    const float p = v * v;
+    float t, e;
+    two_sum(sum, p, t, e);
+    sum = t;
+    err += e + fmaf(v, v, -p);
+  };
   if (posof >= 0) {
 #pragma unroll
     for (int r = 0; r < RPT; ++r) {
@@ -1225,21 +1300,32 @@ __device__ __forceinline__ void qrcp_reg_body(const double* __restrict__ Dg, int
       else val = 0.f;
       if (r_transposed) Rg[posof * ldr + i] = (double)val;
       else Rg[i * ldr + posof] = (double)val;
-      fa += (double)val * (double)val;
-      if (i < k) fb += (double)val * (double)val;
+      acc_sq(val, fa, fae);
+      if (i < k) acc_sq(val, fb, fbe);
     }
   }
   for (int o = 16; o > 0; o >>= 1) {
-    fa += __shfl_xor_sync(0xffffffffu, fa, o);
-    fb += __shfl_xor_sync(0xffffffffu, fb, o);
+    const float oa = __shfl_xor_sync(0xffffffffu, fa, o), oae = __shfl_xor_sync(0xffffffffu, fae, o);
+    const float ob = __shfl_xor_sync(0xffffffffu, fb, o), obe = __shfl_xor_sync(0xffffffffu, fbe, o);
+    const bool lo = (lane & o) == 0;      // lower lane first: every lane forms the same sums
+    float t, e;
+    two_sum(lo ? fa : oa, lo ? oa : fa, t, e);
+    fa = t;
+    fae = (lo ? fae + oae : oae + fae) + e;
+    two_sum(lo ? fb : ob, lo ? ob : fb, t, e);
+    fb = t;
+    fbe = (lo ? fbe + obe : obe + fbe) + e;
   }
-  if (lane == 0) { red[warp][0] = fa; red[warp][1] = fb; }
+  if (lane == 0) {
+    red[warp][0] = (double)fa + (double)fae;
+    red[warp][1] = (double)fb + (double)fbe;
+  }
   // Q~ = H_0 ... H_{l-1} = M^T: Q~[c][q] = M[q][c] (thread holds M[i0.., c]), column sign from diag(R)
   if (c < l) {
 #pragma unroll
     for (int r = 0; r < RPT; ++r) {
       const int q = i0 + r;
-      if (q < l) Qg[c * ldq + q] = (double)((rdiag[q] < 0.f ? -1.f : 1.f) * m[r]);
+      if (q < l) Qg[c * ldq + q] = (TQ)((rdiag[q] < 0.f ? -1.f : 1.f) * m[r]);
     }
   }
   for (int j = tid; j < l; j += blockDim.x) perm[j] = pcol[j];
@@ -1252,28 +1338,43 @@ __device__ __forceinline__ void qrcp_reg_body(const double* __restrict__ Dg, int
   }
 }
 
-template <int TPC>
-__global__ void __launch_bounds__(kMaxL * TPC) qrcp_reg_kernel(const double* __restrict__ Dg, int64_t ldd, int l, int k,
-                                                       double* __restrict__ Qg, int64_t ldq, double* __restrict__ Rg,
+template <int TPC, typename TD, typename TQ>
+__global__ void __launch_bounds__(kMaxL * TPC) qrcp_reg_kernel(const TD* __restrict__ Dg, int64_t ldd, int l, int k,
+                                                       TQ* __restrict__ Qg, int64_t ldq, double* __restrict__ Rg,
                                                        int64_t ldr, int r_transposed, int32_t* __restrict__ perm,
                                                        double* __restrict__ fro2, DevStatus* status) {
-  qrcp_reg_body<TPC>(Dg, ldd, l, k, Qg, ldq, Rg, ldr, r_transposed, perm, fro2, status);
+  qrcp_reg_body<TPC, TD, TQ>(Dg, ldd, l, k, Qg, ldq, Rg, ldr, r_transposed, perm, fro2, status);
 }
 
 template <typename TC>
-cudaError_t launch_qrcp(const double* D, int64_t ldd, int l, int k, double* Q, int64_t ldq, double* R, int64_t ldr,
+cudaError_t launch_qrcp(const TC* D, int64_t ldd, int l, int k, TC* Q, int64_t ldq, double* R, int64_t ldr,
                         bool r_transposed, int32_t* perm, double* fro2, DevStatus* status, cudaStream_t st) {
-  const size_t smem = (size_t)l * kMaxL * sizeof(TC);
   if constexpr (sizeof(TC) == 4) {
-    qrcp_reg_kernel<kQrcpTPC><<<1, kMaxL * kQrcpTPC, 0, st>>>(D, ldd, l, k, Q, ldq, R, ldr, r_transposed ? 1 : 0,
-                                                                 perm, fro2, status);
+    qrcp_reg_kernel<kQrcpTPC, float, float><<<1, kMaxL * kQrcpTPC, 0, st>>>(D, ldd, l, k, Q, ldq, R, ldr,
+                                                                            r_transposed ? 1 : 0, perm, fro2, status);
+    CORUTV_COUNT_LAUNCH();
+    return cudaGetLastError();
+  } else {
+    const size_t smem = (size_t)l * kMaxL * sizeof(TC);
+    cudaError_t e = cudaFuncSetAttribute(qrcp_kernel<TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    qrcp_kernel<TC><<<1, 512, smem, st>>>(D, ldd, l, k, Q, ldq, R, ldr, r_transposed ? 1 : 0, perm, fro2, status);
     CORUTV_COUNT_LAUNCH();
     return cudaGetLastError();
   }
-  cudaError_t e = cudaFuncSetAttribute(qrcp_kernel<TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  qrcp_kernel<TC><<<1, 512, smem, st>>>(D, ldd, l, k, Q, ldq, R, ldr, r_transposed ? 1 : 0, perm, fro2, status); CORUTV_COUNT_LAUNCH();
-  return cudaGetLastError();
+}
+
+template <typename TC>
+cudaError_t launch_qrcp_f64io(const double* D, int64_t ldd, int l, int k, double* Q, int64_t ldq, double* R,
+                              int64_t ldr, int32_t* perm, double* fro2, cudaStream_t st) {
+  if constexpr (sizeof(TC) == 4) {
+    qrcp_reg_kernel<kQrcpTPC, double, double><<<1, kMaxL * kQrcpTPC, 0, st>>>(D, ldd, l, k, Q, ldq, R, ldr, 0, perm,
+                                                                              fro2, nullptr);
+    CORUTV_COUNT_LAUNCH();
+    return cudaGetLastError();
+  } else {
+    return launch_qrcp<double>(D, ldd, l, k, Q, ldq, R, ldr, false, perm, fro2, nullptr, st);
+  }
 }
 
 // =============================================================================== ||A||_F^2
@@ -1357,7 +1458,7 @@ __global__ void __launch_bounds__(256) stage_grouped_kernel(const BatchProb* __r
 // kG_CORE_SKETCH (P3 P2^T -> D: the saved last C2 against Q2)
 __device__ __forceinline__ bool batch_gram_sel(const BatchProb& P, int which, int it, int pass, const float** X,
                                                int64_t* ldx, const float** Y, int64_t* ldy, int64_t* len,
-                                               double** out) {
+                                               float** out) {
   switch (which) {
     case kG_ORTH1:
       if (!batch_orth_active(P, it, pass)) return false;
@@ -1386,7 +1487,7 @@ __global__ void __launch_bounds__(512) gram_partial_grouped_kernel(const BatchPr
   const BatchProb& P = probs[pm.x];
   const float *X, *Y;
   int64_t ldx, ldy, len;
-  double* out;
+  float* out;
   if (!batch_gram_sel(P, which, it, pass, &X, &ldx, &Y, &ldy, &len, &out)) return;
   const int nparts = (which == kG_ORTH2 || which == kG_CORE_SKETCH) ? P.gp2 : P.gp1;
   gram_partial_body<float, LP>(X, ldx, Y, ldy, len, P.l, P.gparts, pm.y, nparts);
@@ -1400,10 +1501,10 @@ __global__ void __launch_bounds__(256) gram_reduce_grouped_kernel(const BatchPro
   const BatchProb& P = probs[pm.x];
   const float *X, *Y;
   int64_t ldx, ldy, len;
-  double* out;
+  float* out;
   if (!batch_gram_sel(P, which, it, pass, &X, &ldx, &Y, &ldy, &len, &out)) return;
   const int nparts = (which == kG_ORTH2 || which == kG_CORE_SKETCH) ? P.gp2 : P.gp1;
-  gram_reduce_body<float>(P.gparts, nparts, LP, P.l, out, P.l, pm.y * blockDim.x + threadIdx.x);
+  gram_reduce_body<float, float>(P.gparts, nparts, LP, P.l, out, P.l, pm.y * blockDim.x + threadIdx.x);
 }
 
 __global__ void __launch_bounds__(kPipeMaxThreads, 1) cholinv_grouped_kernel(const BatchProb* __restrict__ probs,
@@ -1446,7 +1547,8 @@ __global__ void __launch_bounds__(256) copy_sketch_grouped_kernel(const BatchPro
 
 __global__ void __launch_bounds__(kMaxL * kQrcpTPC) qrcp_grouped_kernel(const BatchProb* __restrict__ probs) {
   const BatchProb& P = probs[blockIdx.x];
-  qrcp_reg_body<kQrcpTPC>(P.D, P.l, P.l, P.k, P.Qt, P.l, P.T, P.ldt, P.side == 1 ? 1 : 0, P.perm, nullptr,
+  qrcp_reg_body<kQrcpTPC, float, float>(P.D, P.l, P.l, P.k, P.Qt, P.l, P.T, P.ldt, P.side == 1 ? 1 : 0, P.perm,
+                                         nullptr,
                           P.status);
 }
 
@@ -1458,7 +1560,7 @@ __global__ void __launch_bounds__(256, 1) assemble_lmul_grouped_kernel(const Bat
   const BatchProb& P = probs[pm.x];
   float* out = P.side == 1 ? P.V : P.U;
   const int64_t ldo = P.side == 1 ? P.ldv : P.ldu;
-  lmul_body<float, double, LP, kBatchLmulBI>(P.P1, P.ld1, P.len1, P.l, P.Qt, P.l, out, ldo, 1, 0, nullptr, 0, pm.y);
+  lmul_body<float, float, LP, kBatchLmulBI>(P.P1, P.ld1, P.len1, P.l, P.Qt, P.l, out, ldo, 1, 0, nullptr, 0, pm.y);
 }
 
 // V = Q2 P~ (RIGHT; U for LEFT)
@@ -1517,15 +1619,6 @@ cudaError_t launch_cholinv_grouped(const BatchProb* P, int count, int lmax, int 
   cholinv_grouped_kernel<<<count, threads, 0, st>>>(P, it, pass, skip_tol, shift_rel, tol_rel);
   CORUTV_COUNT_LAUNCH();
   return cudaGetLastError();
-}
-
-// Shared-memory limits are raised once per kernel and device (the first, uncaptured
-// run of a batch), so a later stream capture records launches only.
-constexpr int kAttrDevices = 64;
-static bool* attr_flag(bool (&flags)[kAttrDevices]) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kAttrDevices) return nullptr;
-  return &flags[dev];
 }
 
 template <int LP>
@@ -1611,22 +1704,26 @@ cudaError_t launch_fro2_grouped(const BatchProb* P, int count, cudaStream_t st) 
 
 // ------------------------------------------------------------------ instantiations
 #define INST(TC)                                                                                                   \
-  template cudaError_t launch_gram<TC>(const TC*, int64_t, const TC*, int64_t, int64_t, int, TC*, int, double*,   \
-                                       int64_t, cudaStream_t);                                                     \
-  template cudaError_t launch_cholinv<TC>(const double*, int64_t, int, double, double, TC*, TC*, int*, DevStatus*, \
+  template cudaError_t launch_gram<TC, TC>(const TC*, int64_t, const TC*, int64_t, int64_t, int, TC*, int, TC*,     \
+                                           int64_t, cudaStream_t);                                                 \
+  template cudaError_t launch_cholinv<TC>(const TC*, int64_t, int, double, double, TC*, TC*, int*, DevStatus*,     \
                                           double*, int*, float, cudaStream_t);                                     \
   template cudaError_t launch_lmul<TC>(const TC*, int64_t, int64_t, int, const TC*, int64_t, TC*, int64_t, bool,  \
                                        const int*, int, const int*, float*, int64_t, cudaStream_t);                \
-  template cudaError_t launch_lmul_f64s<TC>(const TC*, int64_t, int64_t, int, const double*, int64_t, TC*,        \
-                                            int64_t, bool, cudaStream_t);                                          \
+  template cudaError_t launch_lmul_full<TC>(const TC*, int64_t, int64_t, int, const TC*, int64_t, TC*, int64_t,   \
+                                            bool, cudaStream_t);                                                   \
   template cudaError_t launch_gather_cols<TC>(const TC*, int64_t, int64_t, int, const int32_t*, TC*, int64_t,     \
                                               cudaStream_t);                                                       \
   template cudaError_t launch_stage_transpose<TC>(const TC*, int64_t, int64_t, int, TC*, int64_t, float*, int64_t, \
                                                   cudaStream_t);                                                  \
-  template cudaError_t launch_qrcp<TC>(const double*, int64_t, int, int, double*, int64_t, double*, int64_t, bool, \
-                                       int32_t*, double*, DevStatus*, cudaStream_t);
+  template cudaError_t launch_qrcp<TC>(const TC*, int64_t, int, int, TC*, int64_t, double*, int64_t, bool,         \
+                                       int32_t*, double*, DevStatus*, cudaStream_t);                               \
+  template cudaError_t launch_qrcp_f64io<TC>(const double*, int64_t, int, int, double*, int64_t, double*, int64_t, \
+                                             int32_t*, double*, cudaStream_t);
 INST(float)
 INST(double)
 #undef INST
+template cudaError_t launch_gram<float, double>(const float*, int64_t, const float*, int64_t, int64_t, int, float*,
+                                                 int, double*, int64_t, cudaStream_t);
 
 }  // namespace corutv
