@@ -207,7 +207,7 @@ void make_plan(Plan& L, int count, const corutv_problem* probs, int sms) {
     add_blocks(mc[kMapT2], i, cdiv(z.len2, kBatchPassBN));
     add_blocks(mc[kMapG1], i, z.gp1);
     add_blocks(mc[kMapG2], i, z.gp2);
-    add_blocks(mc[kMapRed], i, cdiv((int64_t)4 * p.l * p.l, 256));
+    add_blocks(mc[kMapRed], i, cdiv((int64_t)p.l * p.l, 32));
     add_blocks(mc[kMapLm1], i, cdiv(z.len1, kBatchLmulBI));
     add_blocks(mc[kMapLm2], i, cdiv(z.len2, kBatchLmulBI));
     add_blocks(L.maps[0][kMapS2], i, cdiv(z.len2, kBatchTile32));

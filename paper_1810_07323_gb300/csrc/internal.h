@@ -78,6 +78,7 @@ template <typename TC, typename TG>
 cudaError_t launch_gram(const TC* Xt, int64_t ldx, const TC* Yt, int64_t ldy, int64_t len, int l, TC* parts,
                         int gparts, TG* G, int64_t ldg, cudaStream_t st);
 int gram_parts(int64_t len, int sms);
+constexpr int kRedWarps = 8;   // Gram reduction: warps per CTA; a CTA reduces 32 consecutive elements
 // skip_flag (FP32 only, may be null): skip the factorisation when max |G - I| <= skip_tol
 // (writes *skip_flag = 1 and R_out = I); launch_lmul with the same flag then does nothing
 template <typename TC>

@@ -23,7 +23,8 @@ constexpr int kQrcpTPC = 4;   // threads per column of the register QRCP (512 th
 // 512 threads, thread (tx, ty) (32 x 16) owns rows a = R ty + (0..R-1) and
 // columns b = C tx + (0..C-1) (R = LP/16, C = LP/32).  Stages of BK columns
 // are kept k-major in shared memory (rows padded by 4); the next stage's
-// global loads are issued into registers before the current stage is used.
+// global loads (16-byte vectors where the rows allow) are issued into
+// registers before the current stage is used.
 template <typename TC, int LP>
 __device__ __forceinline__ void gram_partial_body(const TC* __restrict__ Xt, int64_t ldx, const TC* __restrict__ Yt,
                                                   int64_t ldy, int64_t len, int l, TC* __restrict__ parts, int cta,
@@ -31,7 +32,8 @@ __device__ __forceinline__ void gram_partial_body(const TC* __restrict__ Xt, int
   constexpr int R = LP / 16, CC = LP / 32;
   constexpr int BK = 32;
   constexpr int LPP = LP + 4;
-  constexpr int PER = LP * BK / 512;        // elements of X (and of Y) staged per thread
+  constexpr int VW = (sizeof(TC) == 4 && LP * BK / 4 >= 512) ? 4 : 1;   // elements per load
+  constexpr int PER = LP * BK / VW / 512;                              // loads of X (and of Y) per thread
   __shared__ __align__(16) TC Xs[BK][LPP];
   __shared__ __align__(16) TC Ys[BK][LPP];
   const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
@@ -39,21 +41,37 @@ __device__ __forceinline__ void gram_partial_body(const TC* __restrict__ Xt, int
   const int64_t c0 = cta * chunk;
   int64_t c1 = c0 + chunk;
   if (c1 > len) c1 = len;
+  const bool vec = VW == 4 && (ldx & 3) == 0 && (ldy & 3) == 0 && ((uintptr_t)Xt & 15) == 0 &&
+                   ((uintptr_t)Yt & 15) == 0;
   TC acc[R][CC];
 #pragma unroll
   for (int v = 0; v < R; ++v)
 #pragma unroll
     for (int u = 0; u < CC; ++u) acc[v][u] = TC(0);
-  TC px[PER], py[PER];
+  TC px[PER][VW], py[PER][VW];
   auto fetch = [&](int64_t k0) {
 #pragma unroll
     for (int q = 0; q < PER; ++q) {
       const int x = tid + 512 * q;
-      const int r = x / BK, kk = x % BK;
+      const int r = x / (BK / VW), kk = VW * (x % (BK / VW));
       const int64_t g = k0 + kk;
-      const bool ok = r < l && g < c1;
-      px[q] = ok ? Xt[r * ldx + g] : TC(0);
-      py[q] = ok ? Yt[r * ldy + g] : TC(0);
+      const TC* xs = Xt + r * ldx + g;
+      const TC* ys = Yt + r * ldy + g;
+      if constexpr (VW == 4) {
+        if (vec && r < l && g + 3 < c1) {
+          const float4 a4 = *reinterpret_cast<const float4*>(xs);
+          const float4 b4 = *reinterpret_cast<const float4*>(ys);
+          px[q][0] = a4.x; px[q][1] = a4.y; px[q][2] = a4.z; px[q][3] = a4.w;
+          py[q][0] = b4.x; py[q][1] = b4.y; py[q][2] = b4.z; py[q][3] = b4.w;
+          continue;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < VW; ++u) {
+        const bool ok = r < l && g + u < c1;
+        px[q][u] = ok ? xs[u] : TC(0);
+        py[q][u] = ok ? ys[u] : TC(0);
+      }
     }
   };
   if (c0 < c1) fetch(c0);
@@ -61,19 +79,35 @@ __device__ __forceinline__ void gram_partial_body(const TC* __restrict__ Xt, int
 #pragma unroll
     for (int q = 0; q < PER; ++q) {
       const int x = tid + 512 * q;
-      const int r = x / BK, kk = x % BK;
-      Xs[kk][r] = px[q];
-      Ys[kk][r] = py[q];
+      const int r = x / (BK / VW), kk = VW * (x % (BK / VW));
+#pragma unroll
+      for (int u = 0; u < VW; ++u) {
+        Xs[kk + u][r] = px[q][u];
+        Ys[kk + u][r] = py[q][u];
+      }
     }
     __syncthreads();
     if (k0 + BK < c1) fetch(k0 + BK);
 #pragma unroll 4
     for (int kk = 0; kk < BK; ++kk) {
       TC xa[R], yb[CC];
+      if constexpr (sizeof(TC) == 4 && R % 4 == 0 && CC % 4 == 0) {
 #pragma unroll
-      for (int v = 0; v < R; ++v) xa[v] = Xs[kk][R * ty + v];
+        for (int v = 0; v < R; v += 4) {
+          const float4 t = *reinterpret_cast<const float4*>(&Xs[kk][R * ty + v]);
+          xa[v] = t.x; xa[v + 1] = t.y; xa[v + 2] = t.z; xa[v + 3] = t.w;
+        }
 #pragma unroll
-      for (int u = 0; u < CC; ++u) yb[u] = Ys[kk][CC * tx + u];
+        for (int u = 0; u < CC; u += 4) {
+          const float4 t = *reinterpret_cast<const float4*>(&Ys[kk][CC * tx + u]);
+          yb[u] = t.x; yb[u + 1] = t.y; yb[u + 2] = t.z; yb[u + 3] = t.w;
+        }
+      } else {
+#pragma unroll
+        for (int v = 0; v < R; ++v) xa[v] = Xs[kk][R * ty + v];
+#pragma unroll
+        for (int u = 0; u < CC; ++u) yb[u] = Ys[kk][CC * tx + u];
+      }
 #pragma unroll
       for (int v = 0; v < R; ++v)
 #pragma unroll
@@ -102,72 +136,71 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = (a - (s - bp)) + (b - bp);
 }
 
-// G[a][b] = sum over parts in a fixed order: four threads per element each sum
-// every fourth part, then (s0 + s1) + (s2 + s3).  FP64 sketches: FP64 sums.  FP32
-// sketches: compensated FP32 sums (TwoSum, the rounding errors carried in a second
-// word), as accurate as an FP64 sum of these few hundred terms at the FP32 rate
+// G[a][b] = sum over parts in a fixed order.  A CTA of 256 threads takes 32
+// consecutive elements e = a l + b (one per lane, so every load of a warp is one
+// coalesced row segment); warp w sums parts w, w + 8, w + 16, ... with all its
+// loads issued before the first add, and lane 0..31 of warp 0 then adds the
+// eight warp sums in warp order.  FP64 sketches: FP64 sums.  FP32 sketches:
+// compensated FP32 sums (TwoSum, the rounding errors carried in a second word),
+// as accurate as an FP64 sum of these few hundred terms at the FP32 rate
 // (GB300's FP64 pipe is ~1/64 of it); the output is the rounded pair, in TG.
 template <typename TC, typename TG>
 __device__ __forceinline__ void gram_reduce_body(const TC* __restrict__ parts, int nparts, int LP, int l,
-                                                 TG* __restrict__ G, int64_t ldg, int gtid) {
-  const int e = gtid >> 2;
-  const int q = threadIdx.x & 3;
+                                                 TG* __restrict__ G, int64_t ldg, int blk) {
+  __shared__ TC red_s[kRedWarps][32], red_c[kRedWarps][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int e = blk * 32 + lane;
   const bool ok = e < l * l;
   const int a = ok ? e / l : 0, b = ok ? e % l : 0;
   const TC* src = parts + (int64_t)a * LP + b;
   const int64_t stride = (int64_t)LP * LP;
-  if constexpr (sizeof(TC) == 8) {
-    double s = 0.0;
-    if (ok) {
-      int p = q;
-      for (; p + 12 < nparts; p += 16) {
-        const double v0 = src[p * stride], v1 = src[(p + 4) * stride];
-        const double v2 = src[(p + 8) * stride], v3 = src[(p + 12) * stride];
-        s += v0; s += v1; s += v2; s += v3;
-      }
-      for (; p < nparts; p += 4) s += src[p * stride];
+  constexpr int U = 8;                       // loads in flight per thread
+  TC s = TC(0), c = TC(0);
+  for (int p0 = w; p0 < nparts; p0 += kRedWarps * U) {
+    TC v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int p = p0 + kRedWarps * u;
+      v[u] = (ok && p < nparts) ? src[p * stride] : TC(0);
     }
-    const double s1 = __shfl_xor_sync(0xffffffffu, s, 1);
-    const double t = (q & 1) ? s1 + s : s + s1;                 // (s0 + s1), (s2 + s3)
-    const double t2 = __shfl_xor_sync(0xffffffffu, t, 2);
-    if (ok && q == 0) G[a * ldg + b] = (TG)(t + t2);
-  } else {
-    float s = 0.f, c = 0.f, er;
-    if (ok) {
-      int p = q;
-      for (; p + 12 < nparts; p += 16) {
-        const float v0 = src[p * stride], v1 = src[(p + 4) * stride];
-        const float v2 = src[(p + 8) * stride], v3 = src[(p + 12) * stride];
-        two_sum(s, v0, s, er); c += er;
-        two_sum(s, v1, s, er); c += er;
-        two_sum(s, v2, s, er); c += er;
-        two_sum(s, v3, s, er); c += er;
-      }
-      for (; p < nparts; p += 4) {
-        two_sum(s, src[p * stride], s, er);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if constexpr (sizeof(TC) == 8) {
+        s += v[u];
+      } else {
+        float t, er;
+        two_sum(s, v[u], t, er);
+        s = t;
         c += er;
       }
     }
-#pragma unroll
-    for (int o = 1; o <= 2; o <<= 1) {       // (s0 + s1), (s2 + s3), then their sum; lower index first
-      const float so = __shfl_xor_sync(0xffffffffu, s, o), co = __shfl_xor_sync(0xffffffffu, c, o);
-      const bool lo = (q & o) == 0;
-      float t;
-      two_sum(lo ? s : so, lo ? so : s, t, er);
-      c = (lo ? c + co : co + c) + er;
-      s = t;
-    }
-    if (ok && q == 0) {
-      if constexpr (sizeof(TG) == 8) G[a * ldg + b] = (double)s + (double)c;
-      else G[a * ldg + b] = s + c;
+  }
+  red_s[w][lane] = s;
+  red_c[w][lane] = c;
+  __syncthreads();
+  if (w == 0 && ok) {
+    if constexpr (sizeof(TC) == 8) {
+      double t = red_s[0][lane];
+      for (int k = 1; k < kRedWarps; ++k) t += red_s[k][lane];
+      G[a * ldg + b] = (TG)t;
+    } else {
+      float t = red_s[0][lane], tc = red_c[0][lane];
+      for (int k = 1; k < kRedWarps; ++k) {
+        float u, er;
+        two_sum(t, red_s[k][lane], u, er);
+        t = u;
+        tc += red_c[k][lane] + er;
+      }
+      if constexpr (sizeof(TG) == 8) G[a * ldg + b] = (double)t + (double)tc;
+      else G[a * ldg + b] = t + tc;
     }
   }
 }
 
 template <typename TC, typename TG>
-__global__ void gram_reduce_kernel(const TC* __restrict__ parts, int nparts, int LP, int l, TG* __restrict__ G,
-                                   int64_t ldg) {
-  gram_reduce_body<TC, TG>(parts, nparts, LP, l, G, ldg, blockIdx.x * blockDim.x + threadIdx.x);
+__global__ void __launch_bounds__(kRedWarps * 32) gram_reduce_kernel(const TC* __restrict__ parts, int nparts, int LP,
+                                                                      int l, TG* __restrict__ G, int64_t ldg) {
+  gram_reduce_body<TC, TG>(parts, nparts, LP, l, G, ldg, blockIdx.x);
 }
 
 int gram_parts(int64_t len, int sms) {
@@ -190,7 +223,8 @@ cudaError_t launch_gram(const TC* Xt, int64_t ldx, const TC* Yt, int64_t ldy, in
     LP = 128;
     gram_partial_kernel<TC, 128><<<gparts, 512, 0, st>>>(Xt, ldx, Yt, ldy, len, l, parts); CORUTV_COUNT_LAUNCH();
   }
-  gram_reduce_kernel<TC, TG><<<(unsigned)cdiv((int64_t)l * l * 4, 256), 256, 0, st>>>(parts, gparts, LP, l, G, ldg);
+  gram_reduce_kernel<TC, TG><<<(unsigned)cdiv((int64_t)l * l, 32), kRedWarps * 32, 0, st>>>(parts, gparts, LP, l, G,
+                                                                                             ldg);
   CORUTV_COUNT_LAUNCH();
   return cudaGetLastError();
 }
@@ -311,11 +345,13 @@ __device__ __forceinline__ float rsqrt_nr(float x) {
 // FP32 variant with the matrices in registers: the same elimination of
 // [G + s I | I] as cholinv_kernel, with the upper triangle of G and the lower
 // triangle of L^-1 split into 4 x 4 blocks.  Thread t owns block (I, J), J >= I,
-// of G and block (J, I) of L^-1 (t enumerates the upper block triangle row by
-// row).  Step j reads row j of G and of L^-1 from a double-buffered shared row
-// (published at the end of step j - 1 by the owners of row j), applies its
+// of G and block (J, I) of L^-1 (t enumerates the upper block triangle column
+// by column).  Step j reads row j of G and of L^-1 from a double-buffered shared
+// row (published at the end of step j - 1 by the owners of row j), applies its
 // multipliers m_a = G[j][a] / d_j to the rows a > j of both blocks, and the
-// owners of row j + 1 publish it: one block barrier per step.
+// owners of row j + 1 publish it: one block barrier per step.  Reciprocals and
+// square roots come from rcp_nr / rsqrt_nr, and the input is the FP32 Gram
+// matrix (no FP64 arithmetic: GB300's FP64 pipe would dominate the step).
 __device__ __forceinline__ float f4(const float4& v, int i) {
   return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
 }
@@ -341,15 +377,14 @@ __device__ __forceinline__ void cholinv_pipe_body(const float* __restrict__ G, i
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   const int nb = (l + 3) >> 2;
   const bool own = tid < nb * (nb + 1) / 2;
+  // blocks enumerated column by column (t = J (J + 1) / 2 + I): a thread has nothing left
+  // to do once j >= 4 J + 3, and the threads of a warp reach that point together
   int I = 0, J = 0;
   if (own) {
-    int t = tid, i = 0;
-    while (t >= nb - i) {
-      t -= nb - i;
-      ++i;
-    }
-    I = i;
-    J = i + t;
+    int jj = 0;
+    while ((jj + 1) * (jj + 2) / 2 <= tid) ++jj;
+    J = jj;
+    I = tid - jj * (jj + 1) / 2;
   }
   __shared__ float redmax[32];
   float g[4][4], li[4][4];
@@ -424,7 +459,7 @@ __device__ __forceinline__ void cholinv_pipe_body(const float* __restrict__ G, i
       pivrs[j] = dep ? 1.f : rsqrt_nr(d);
       dep_s[j] = dep ? 1 : 0;
     }
-    if (own) {
+    if (own && 4 * J + 3 > j) {
       const float4 rI = *reinterpret_cast<const float4*>(&rowbuf[buf][4 * I]);
       const float4 rJ = *reinterpret_cast<const float4*>(&rowbuf[buf][4 * J]);
       const float4 lI = *reinterpret_cast<const float4*>(&libuf[buf][4 * I]);
@@ -547,32 +582,29 @@ __device__ __forceinline__ double replacement_value(int pass, int j, int64_t i) 
 
 // =============================================================================== lmul
 // Out[j][i] = sum_{p<l} S[p][j] In[p][i]   (Out = S^T In on ST blocks, i.e. C S in
-// the untransposed view).  A CTA computes a BI-column tile; thread (tx, ty)
-// owns j = R ty + (0..R-1) and i = BI/16 tx + (0..BI/16-1).  upper: S is upper
-// triangular (S[p][j] = 0 for p > j), so the p loop stops at the thread's last j.
-// S and the In tile are staged in shared memory with independent (vector, for
-// FP32) loads issued before any is used.  The tile is read completely before it
-// is written, so In == Out (in place) is allowed.
+// the untransposed view).  S (LP x LP) is staged in shared memory once per CTA;
+// the CTA then takes BI-column tiles of In in turn (a persistent loop over
+// tiles: the grid is sized to the resident CTAs, so no partial second wave).
+// Thread (tx, ty) owns rows j = R ty + (0..R-1) and columns i = BI/16 tx +
+// (0..BI/16-1) of the tile.  upper: S is upper triangular (S[p][j] = 0 for
+// p > j), so the p loop stops at the last row of the thread's warp.  The tile
+// is read completely before it is written, so In == Out (in place) is allowed.
 // defic (may be null): rows j with defic[j] != 0 receive the replacement vector
-// of `pass` instead of the product.
-// out_rowmajor: write Out^T into a row-major len x l matrix (staged through
-// shared memory so the row writes coalesce).
-template <typename TC, typename TS, int LP, int BI>
-__device__ __forceinline__ void lmul_body(const TC* __restrict__ In, int64_t ldi, int64_t len, int l,
-                                          const TS* __restrict__ S, int64_t lds, TC* __restrict__ Out, int64_t ldo,
-                                          int out_rowmajor, int upper, const int* __restrict__ defic, int pass,
-                                          int bx, float* __restrict__ round_out = nullptr, int64_t ldr = 0) {
-  constexpr int R = LP / 16, RI = BI / 16;
-  constexpr int SP = LP + 4, IP = BI + 4;
-  constexpr bool kVecIn = sizeof(TC) == 4;
-  constexpr bool kVecS = sizeof(TS) == 4;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  TC* Ss = reinterpret_cast<TC*>(smem_raw);      // LP x SP   (row p, column j)
-  TC* Is = Ss + LP * SP;                         // LP x IP   (row p, column i)
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  const int64_t i0 = (int64_t)bx * BI;
-  // (S rows p >= l and columns j >= l are zero: the p loop below can stop at l)
-  if constexpr (kVecS) {
+// of `pass` instead of the product.  out_rowmajor: write Out^T into a
+// row-major len x l matrix (staged through shared memory so the row writes
+// coalesce).  round_out (FP32, may be null): also write the rows rounded to TF32.
+template <typename TC, int LP, int BI>
+__host__ __device__ constexpr size_t lmul_smem_bytes() {
+  return ((size_t)LP * (LP + 4) + (size_t)(LP * (BI + 4) > BI * (LP + 1) ? LP * (BI + 4) : BI * (LP + 1))) *
+         sizeof(TC);
+}
+
+// S (l x l, ld lds, type TS) -> Ss (LP x (LP + 4), zero outside l x l)
+template <typename TC, typename TS, int LP>
+__device__ __forceinline__ void lmul_stage_S(const TS* __restrict__ S, int64_t lds, int l, TC* __restrict__ Ss) {
+  constexpr int SP = LP + 4;
+  const int tid = threadIdx.x;
+  if constexpr (sizeof(TS) == 4 && sizeof(TC) == 4) {
     constexpr int N4 = LP * LP / 4 / 256;
     float4 v[N4];
     const bool s_vec = (lds & 3) == 0 && ((uintptr_t)S & 15) == 0;
@@ -604,6 +636,19 @@ __device__ __forceinline__ void lmul_body(const TC* __restrict__ In, int64_t ldi
       Ss[p * SP + j] = (p < l && j < l) ? (TC)S[p * lds + j] : TC(0);
     }
   }
+}
+
+// one BI-column tile (index bx) with S already staged in Ss; Is: LP x (BI + 4)
+template <typename TC, int LP, int BI>
+__device__ __forceinline__ void lmul_tile(const TC* __restrict__ In, int64_t ldi, int64_t len, int l,
+                                          const TC* __restrict__ Ss, TC* __restrict__ Is, TC* __restrict__ Out,
+                                          int64_t ldo, int out_rowmajor, int upper, const int* __restrict__ defic,
+                                          int pass, int64_t bx, float* __restrict__ round_out, int64_t ldr) {
+  constexpr int R = LP / 16, RI = BI / 16;
+  constexpr int SP = LP + 4, IP = BI + 4;
+  constexpr bool kVecIn = sizeof(TC) == 4 && (LP * BI / 4) % 256 == 0;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int64_t i0 = bx * BI;
   if constexpr (kVecIn) {
     constexpr int N4 = LP * BI / 4 / 256;
     float4 v[N4];
@@ -679,6 +724,7 @@ __device__ __forceinline__ void lmul_body(const TC* __restrict__ In, int64_t ldi
         }
       }
     }
+    __syncthreads();                              // Is is refilled by the next tile
   } else {
     __syncthreads();
     TC* Os = Is;                                  // BI x (LP + 1)
@@ -692,45 +738,80 @@ __device__ __forceinline__ void lmul_body(const TC* __restrict__ In, int64_t ldi
       const int64_t g = i0 + ii;
       if (g < len) Out[g * ldo + j] = Os[ii * (LP + 1) + j];
     }
+    __syncthreads();
   }
 }
 
+// one CTA per block index bx (the grouped launches: one tile each)
 template <typename TC, typename TS, int LP, int BI>
-__global__ void __launch_bounds__(256, 1) lmul_kernel(const TC* __restrict__ In, int64_t ldi, int64_t len, int l,
+__device__ __forceinline__ void lmul_body(const TC* __restrict__ In, int64_t ldi, int64_t len, int l,
+                                          const TS* __restrict__ S, int64_t lds, TC* __restrict__ Out, int64_t ldo,
+                                          int out_rowmajor, int upper, const int* __restrict__ defic, int pass,
+                                          int bx, float* __restrict__ round_out = nullptr, int64_t ldr = 0) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TC* Ss = reinterpret_cast<TC*>(smem_raw);
+  TC* Is = Ss + LP * (LP + 4);
+  lmul_stage_S<TC, TS, LP>(S, lds, l, Ss);
+  lmul_tile<TC, LP, BI>(In, ldi, len, l, Ss, Is, Out, ldo, out_rowmajor, upper, defic, pass, bx, round_out, ldr);
+}
+
+template <typename TC, typename TS, int LP, int BI>
+__global__ void __launch_bounds__(256, 2) lmul_kernel(const TC* __restrict__ In, int64_t ldi, int64_t len, int l,
                                                       const TS* __restrict__ S, int64_t lds, TC* __restrict__ Out,
                                                       int64_t ldo, int out_rowmajor, int upper,
                                                       const int* __restrict__ defic, int pass,
                                                       const int* __restrict__ skip_flag, float* __restrict__ round_out,
                                                       int64_t ldr) {
+  const int64_t tiles = cdiv(len, BI);
   if (skip_flag && *skip_flag) {           // the factor was found to be the identity: Out = In
     if constexpr (sizeof(TC) == 4) {
       if (round_out) {
-        const int64_t i0 = (int64_t)blockIdx.x * BI;
-        for (int e = threadIdx.x; e < l * BI; e += blockDim.x) {
-          const int j = e / BI;
-          const int64_t g = i0 + e % BI;
-          if (g < len) round_out[j * ldr + g] = to_tf32(In[j * ldi + g]);
+        for (int64_t bx = blockIdx.x; bx < tiles; bx += gridDim.x) {
+          const int64_t i0 = bx * BI;
+          for (int e = threadIdx.x; e < l * BI; e += blockDim.x) {
+            const int j = e / BI;
+            const int64_t g = i0 + e % BI;
+            if (g < len) round_out[j * ldr + g] = to_tf32(In[j * ldi + g]);
+          }
         }
       }
     }
     return;
   }
-  lmul_body<TC, TS, LP, BI>(In, ldi, len, l, S, lds, Out, ldo, out_rowmajor, upper, defic, pass, blockIdx.x,
-                            round_out, ldr);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TC* Ss = reinterpret_cast<TC*>(smem_raw);
+  TC* Is = Ss + LP * (LP + 4);
+  lmul_stage_S<TC, TS, LP>(S, lds, l, Ss);
+  for (int64_t bx = blockIdx.x; bx < tiles; bx += gridDim.x)
+    lmul_tile<TC, LP, BI>(In, ldi, len, l, Ss, Is, Out, ldo, out_rowmajor, upper, defic, pass, bx, round_out, ldr);
 }
 
 template <typename TC, typename TS, int LP, int BI>
 static cudaError_t lmul_variant(const TC* In, int64_t ldi, int64_t len, int l, const TS* S, int64_t lds, TC* Out,
                                 int64_t ldo, bool rowmajor, bool upper, const int* defic, int pass,
                                 const int* skip_flag, float* round_out, int64_t ldr, cudaStream_t st) {
-  const unsigned grid = (unsigned)cdiv(len, BI);
-  if (grid == 0) return cudaSuccess;
-  const size_t a = (size_t)LP * (LP + 4) + (size_t)LP * (BI + 4);
-  const size_t b = (size_t)LP * (LP + 4) + (size_t)BI * (LP + 1);
-  const size_t sm = (a > b ? a : b) * sizeof(TC);
-  cudaError_t e = cudaFuncSetAttribute(lmul_kernel<TC, TS, LP, BI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)sm);
+  const int64_t tiles = cdiv(len, BI);
+  if (tiles == 0) return cudaSuccess;
+  constexpr size_t sm = lmul_smem_bytes<TC, LP, BI>();
+  static bool attr_set[kAttrDevices] = {};
+  static int resident[kAttrDevices] = {};
+  bool* flag = attr_flag(attr_set);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
+  if (!flag || !*flag) {
+    e = cudaFuncSetAttribute(lmul_kernel<TC, TS, LP, BI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0, sms = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lmul_kernel<TC, TS, LP, BI>, 256, sm);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    if (dev < kAttrDevices) resident[dev] = (per_sm < 1 ? 1 : per_sm) * sms;
+    if (flag) *flag = true;
+  }
+  const int cap = (dev < kAttrDevices && resident[dev] > 0) ? resident[dev] : 148;
+  const unsigned grid = (unsigned)(tiles < cap ? tiles : cap);
   lmul_kernel<TC, TS, LP, BI><<<grid, 256, sm, st>>>(In, ldi, len, l, S, lds, Out, ldo, rowmajor ? 1 : 0,
                                                      upper ? 1 : 0, defic, pass, skip_flag, round_out, ldr);
   CORUTV_COUNT_LAUNCH();
@@ -741,8 +822,9 @@ template <typename TC, typename TS>
 static cudaError_t lmul_dispatch(const TC* In, int64_t ldi, int64_t len, int l, const TS* S, int64_t lds, TC* Out,
                                  int64_t ldo, bool rowmajor, bool upper, const int* defic, int pass,
                                  const int* skip_flag, float* round_out, int64_t ldr, cudaStream_t st) {
-  // FP32: 128-column tiles (S and the tile fill ~135 KB of shared memory); FP64: 64 columns
-  constexpr int BI = sizeof(TC) == 4 ? 128 : 64;
+  // FP32: 32-column tiles (S and the tile in ~86 KB of shared memory: two CTAs per SM, and fine
+  // enough that the last round of tiles leaves few SMs idle); FP64: 32 columns
+  constexpr int BI = 32;
   if (l <= 32)
     return lmul_variant<TC, TS, 32, BI>(In, ldi, len, l, S, lds, Out, ldo, rowmajor, upper, defic, pass, skip_flag,
                                         round_out, ldr, st);
@@ -1504,7 +1586,7 @@ __global__ void __launch_bounds__(256) gram_reduce_grouped_kernel(const BatchPro
   float* out;
   if (!batch_gram_sel(P, which, it, pass, &X, &ldx, &Y, &ldy, &len, &out)) return;
   const int nparts = (which == kG_ORTH2 || which == kG_CORE_SKETCH) ? P.gp2 : P.gp1;
-  gram_reduce_body<float, float>(P.gparts, nparts, LP, P.l, out, P.l, pm.y * blockDim.x + threadIdx.x);
+  gram_reduce_body<float, float>(P.gparts, nparts, LP, P.l, out, P.l, pm.y);
 }
 
 __global__ void __launch_bounds__(kPipeMaxThreads, 1) cholinv_grouped_kernel(const BatchProb* __restrict__ probs,
@@ -1624,7 +1706,7 @@ cudaError_t launch_cholinv_grouped(const BatchProb* P, int count, int lmax, int 
 template <int LP>
 static cudaError_t lmul_orth_grouped_lp(const BatchProb* P, const int2* map, int nblocks, int which, int it,
                                         int pass, cudaStream_t st) {
-  const size_t sm = ((size_t)LP * (LP + 4) + (size_t)LP * (kBatchLmulBI + 4)) * sizeof(float);
+  constexpr size_t sm = lmul_smem_bytes<float, LP, kBatchLmulBI>();
   static bool attr_set[kAttrDevices] = {};
   bool* flag = attr_flag(attr_set);
   if (!flag || !*flag) {
@@ -1663,9 +1745,7 @@ cudaError_t launch_qrcp_grouped(const BatchProb* P, int count, cudaStream_t st) 
 
 template <int LP>
 static cudaError_t assemble_lp(const BatchProb* P, const int2* map, int nblocks, cudaStream_t st) {
-  const size_t a = (size_t)LP * (LP + 4) + (size_t)LP * (kBatchLmulBI + 4);
-  const size_t b = (size_t)LP * (LP + 4) + (size_t)kBatchLmulBI * (LP + 1);
-  const size_t sm = (a > b ? a : b) * sizeof(float);
+  constexpr size_t sm = lmul_smem_bytes<float, LP, kBatchLmulBI>();
   static bool attr_set[kAttrDevices] = {};
   bool* flag = attr_flag(attr_set);
   if (!flag || !*flag) {
