@@ -17,6 +17,9 @@
 namespace corutv {
 
 constexpr int kQrcpTPC = 4;   // threads per column of the register QRCP (512 threads)
+// its dynamic shared memory: the l reflectors (rows skewed by 4 per RPT-row piece), later
+// the l x (l + 1) staging tile of the outputs
+constexpr size_t kQrcpSmem = (size_t)kMaxL * (kMaxL + 4 * kQrcpTPC) * sizeof(float);
 
 // =============================================================================== Gram
 // parts[c] = X[:, cols_c] Y[:, cols_c]^T over the c-th contiguous column range.
@@ -1198,43 +1201,62 @@ __global__ void __launch_bounds__(512) qrcp_kernel(const double* __restrict__ Dg
 // FP32 variant with columns in registers: thread (c, h) holds rows
 // i = RPT h .. RPT h + RPT - 1 of column c of D and of M = H_j ... H_0 (TPC
 // threads per column), so every column reduction is a per-thread sum plus
-// TPC - 1 shuffles.  Step j: warp 0 picks the pivot from the trailing norms
-// (first maximum by current position) and applies the swap to its position
-// map; the pivot column's warp builds the reflector and publishes it; every
-// trailing column (and every column of M) takes it and recomputes its trailing
-// norm exactly.  Three block barriers per step: the pivot choice and the
-// reflector are each formed once, which costs less than forming them in every
-// warp.  Same choices as the textbook algorithm with physical column exchanges.
+// TPC - 1 shuffles.  Step j: warp 0 reduces the sixteen warp candidates (each
+// warp's trailing column of largest exact trailing norm, lowest current
+// position on ties) to the pivot; the pivot column's warp builds the reflector
+// and publishes it; every trailing column (and every column of M) takes it,
+// recomputes its trailing norm exactly and its warp forms the next candidate.
+// Three block barriers per step: the pivot choice and the reflector are each
+// formed once, which costs less than forming them in every warp.  Every column
+// tracks its own position (the pivot moves to j, the column at j to the
+// pivot's old place), so the choices are those of the textbook algorithm with
+// physical column exchanges.  The reflector and pivot column are stored with a
+// skew (row i at i + 4 (i / RPT)) so the TPC threads of a column read them
+// without shared-memory bank conflicts.
 template <int TPC, typename TD, typename TQ>
 __device__ __forceinline__ void qrcp_reg_body(const TD* __restrict__ Dg, int64_t ldd, int l, int k,
                                               TQ* __restrict__ Qg, int64_t ldq, double* __restrict__ Rg,
                                               int64_t ldr, int r_transposed, int32_t* __restrict__ perm,
                                               double* __restrict__ fro2, DevStatus* status) {
   constexpr int RPT = kMaxL / TPC, NWARP = kMaxL * TPC / 32, CPW = 32 / TPC;   // columns per warp
-  __shared__ __align__(16) float vbuf[kMaxL];       // reflector of the current step (zero outside j..l-1)
-  __shared__ __align__(16) float pcolv[kMaxL];      // raw pivot column
-  __shared__ float npos[kMaxL];                      // trailing norms by current position
-  __shared__ float sc[2];                            // beta, alpha of the current step
-  __shared__ int piv[3];                             // pivot column, column previously at position j, its new position
+  // row i of the reflector and of the pivot column lives at i + 4 (i / RPT): the RPT-row
+  // pieces that the TPC threads of a column read start in different banks
+  constexpr int SKW = kMaxL + 4 * TPC;
+  extern __shared__ __align__(16) unsigned char qrcp_smem[];
+  float* Vs = reinterpret_cast<float*>(qrcp_smem);   // reflector of step j in row j (zero outside j..l-1)
+  __shared__ __align__(16) float pcolv[SKW];         // raw pivot column
+  __shared__ float betas[kMaxL];
+  auto sk = [](int i) { return i + 4 * (i / RPT); };
+  __shared__ float cnrm[NWARP];                      // each warp's candidate: trailing norm^2 (-1: none),
+  __shared__ int cpos[NWARP], ccol[NWARP];           // its current position and its column
+  __shared__ int piv[3];                             // pivot column, -, its position before the swap
   __shared__ float rdiag[kMaxL];
   __shared__ int pcol[kMaxL];
   __shared__ double red[NWARP][2];
   const int tid = threadIdx.x, c = tid / TPC, h = tid % TPC, lane = tid & 31, warp = tid >> 5;
   const int i0 = RPT * h;
-  const unsigned grp = ((TPC == 32) ? 0xffffffffu : ((1u << TPC) - 1u)) << (lane & ~(TPC - 1));
-  float d[RPT], m[RPT];       // column c of D (rows i0..) and column c of M = H_j ... H_0 (rows i0..)
+  float d[RPT];               // column c of D (rows i0..)
 #pragma unroll
   for (int r = 0; r < RPT; ++r) {
     const int i = i0 + r;
     d[r] = (c < l && i < l) ? (float)Dg[i * ldd + c] : 0.f;
-    m[r] = (i == c) ? 1.f : 0.f;
   }
-  int map[4];                 // position -> column (kept by warp 0)
-#pragma unroll
-  for (int r = 0; r < 4; ++r) map[r] = lane + 32 * r;
   int mypos = c;
   bool trailing = c < l;
   int posof = -1;
+  // the warp's candidate for the next pivot: its trailing column of largest norm, lowest position on ties
+  auto publish = [&](float nrm2) {
+    float bn = trailing ? nrm2 : -1.f;
+    int bp = trailing ? mypos : 0x7fffffff, bc = c;
+#pragma unroll
+    for (int o = TPC; o < 32; o <<= 1) {
+      const float on = __shfl_xor_sync(0xffffffffu, bn, o);
+      const int op = __shfl_xor_sync(0xffffffffu, bp, o);
+      const int oc = __shfl_xor_sync(0xffffffffu, bc, o);
+      if (on > bn || (on == bn && op < bp)) { bn = on; bp = op; bc = oc; }
+    }
+    if (lane == 0) { cnrm[warp] = bn; cpos[warp] = bp; ccol[warp] = bc; }
+  };
   {
     float s0 = 0.f, s1 = 0.f;
 #pragma unroll
@@ -1242,53 +1264,40 @@ __device__ __forceinline__ void qrcp_reg_body(const TD* __restrict__ Dg, int64_t
     float ss = s0 + s1;
 #pragma unroll
     for (int o = 1; o < TPC; o <<= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-    if (h == 0 && c < l) npos[c] = ss;
+    publish(ss);
   }
   __syncthreads();
   for (int j = 0; j < l; ++j) {
-    // ---- phase 1: warp 0 picks the pivot (first maximum by current position) and swaps the map
+    // ---- phase 1: warp 0 reduces the warps' candidates to the pivot (first maximum by current
+    // position); the column at position j takes the pivot's old position
     if (warp == 0) {
-      float best = -1.f;
-      int bpos = l;
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        const int pos = lane + 32 * r;
-        if (pos >= j && pos < l) {
-          const float nv = npos[pos];
-          if (nv > best) { best = nv; bpos = pos; }
-        }
-      }
+      float bn = (lane < NWARP) ? cnrm[lane] : -1.f;
+      int bp = (lane < NWARP) ? cpos[lane] : 0x7fffffff;
+      int bc = (lane < NWARP) ? ccol[lane] : 0;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
-        const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-        const int op = __shfl_xor_sync(0xffffffffu, bpos, o);
-        if (ob > best || (ob == best && op < bpos)) { best = ob; bpos = op; }
+        const float on = __shfl_xor_sync(0xffffffffu, bn, o);
+        const int op = __shfl_xor_sync(0xffffffffu, bp, o);
+        const int oc = __shfl_xor_sync(0xffffffffu, bc, o);
+        if (on > bn || (on == bn && op < bp)) { bn = on; bp = op; bc = oc; }
       }
-      const int cj = __shfl_sync(0xffffffffu, sel4(map, j >> 5), j & 31);
-      const int cp = __shfl_sync(0xffffffffu, sel4(map, (bpos >> 5) & 3), bpos & 31);
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        const int pos = lane + 32 * r;
-        if (pos == j) map[r] = cp;
-        else if (pos == bpos) map[r] = cj;
-      }
-      if (lane == 0) { piv[0] = cp; piv[1] = cj; piv[2] = bpos; }
+      if (lane == 0) { piv[0] = bc; piv[2] = bp; }
     }
     __syncthreads();
     const int cp = piv[0];
-    if (c == piv[1]) mypos = piv[2];
     if (c == cp) mypos = j;
+    else if (mypos == j) mypos = piv[2];
     // ---- phase 2: the pivot column's warp builds the reflector from a shared copy of the column
     if (warp == cp / CPW) {
       if (c == cp) {
-        float4* p4 = reinterpret_cast<float4*>(pcolv + i0);
+        float4* p4 = reinterpret_cast<float4*>(pcolv + sk(i0));
 #pragma unroll
         for (int q = 0; q < RPT / 4; ++q) p4[q] = make_float4(d[4 * q], d[4 * q + 1], d[4 * q + 2], d[4 * q + 3]);
         trailing = false;
         posof = j;
       }
       __syncwarp();
-      const float4 x4 = reinterpret_cast<const float4*>(pcolv)[lane];   // rows 4 lane .. 4 lane + 3
+      const float4 x4 = *reinterpret_cast<const float4*>(pcolv + sk(4 * lane));   // rows 4 lane .. 4 lane + 3
       float xv[4] = {x4.x, x4.y, x4.z, x4.w};
       float ss = 0.f;
 #pragma unroll
@@ -1298,7 +1307,7 @@ __device__ __forceinline__ void qrcp_reg_body(const TD* __restrict__ Dg, int64_t
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-      const float x0 = pcolv[j];
+      const float x0 = pcolv[sk(j)];
       const float nrm = (ss > 0.f) ? ss * rsqrt_nr(ss) : 0.f;
       float alpha, v0, beta;
       if (nrm == 0.f) {
@@ -1315,54 +1324,81 @@ __device__ __forceinline__ void qrcp_reg_body(const TD* __restrict__ Dg, int64_t
         const int i = 4 * lane + e;
         vp[e] = (i == j) ? v0 : ((i > j && i < l) ? xv[e] : 0.f);
       }
-      reinterpret_cast<float4*>(vbuf)[lane] = vo;
-      if (lane == 0) { sc[0] = beta; sc[1] = alpha; rdiag[j] = alpha; pcol[j] = cp; }
+      *reinterpret_cast<float4*>(Vs + j * SKW + sk(4 * lane)) = vo;
+      if (lane == 0) { betas[j] = beta; rdiag[j] = alpha; pcol[j] = cp; }
     }
     __syncthreads();
-    // ---- phase 3: every column of M and every trailing column of D takes the reflector
+    // ---- phase 3: every trailing column of D takes the reflector
     {
       float v[RPT];
-      const float4* v4 = reinterpret_cast<const float4*>(vbuf + i0);
+      const float4* v4 = reinterpret_cast<const float4*>(Vs + j * SKW + sk(i0));
 #pragma unroll
       for (int q = 0; q < RPT / 4; ++q) {
         const float4 t = v4[q];
         v[4 * q] = t.x; v[4 * q + 1] = t.y; v[4 * q + 2] = t.z; v[4 * q + 3] = t.w;
       }
-      const float beta = sc[0];
-      float wm0 = 0.f, wm1 = 0.f, wd0 = 0.f, wd1 = 0.f;
+      const float beta = betas[j];
+      float wd0 = 0.f, wd1 = 0.f;
 #pragma unroll
       for (int r = 0; r < RPT; r += 2) {
-        wm0 = fmaf(v[r], m[r], wm0);
-        wm1 = fmaf(v[r + 1], m[r + 1], wm1);
         wd0 = fmaf(v[r], d[r], wd0);
         wd1 = fmaf(v[r + 1], d[r + 1], wd1);
       }
-      float wm = wm0 + wm1, wd = trailing ? wd0 + wd1 : 0.f;
+      float wd = trailing ? wd0 + wd1 : 0.f;
 #pragma unroll
-      for (int o = 1; o < TPC; o <<= 1) {
-        wm += __shfl_xor_sync(grp, wm, o);
-        wd += __shfl_xor_sync(grp, wd, o);
-      }
-      const float fm = beta * wm, fd = beta * wd;
+      for (int o = 1; o < TPC; o <<= 1) wd += __shfl_xor_sync(0xffffffffu, wd, o);   // within the column's group
+      const float fd = beta * wd;
       float s0 = 0.f, s1 = 0.f;
 #pragma unroll
       for (int r = 0; r < RPT; ++r) {
-        m[r] = fmaf(-fm, v[r], m[r]);
         d[r] = fmaf(-fd, v[r], d[r]);          // fd = 0 for columns that are not trailing
         const float x = (i0 + r > j) ? d[r] : 0.f;
         if (r & 1) s1 = fmaf(x, x, s1); else s0 = fmaf(x, x, s0);
       }
-      if (trailing) {
-        float ns = s0 + s1;
+      float ns = s0 + s1;
 #pragma unroll
-        for (int o = 1; o < TPC; o <<= 1) ns += __shfl_xor_sync(grp, ns, o);
-        if (h == 0) npos[mypos] = ns;
-      }
+      for (int o = 1; o < TPC; o <<= 1) ns += __shfl_xor_sync(0xffffffffu, ns, o);   // within the column's group
+      publish(ns);
     }
     __syncthreads();
   }
-  // R from each pivot column (rows above its position), diag(R) >= 0; ||R||_F^2 and
-  // ||R(1:k, :)||_F^2 as compensated FP32 sums (exact squares, TwoSum), in FP64 across warps
+  // Q~ = H_0 H_1 ... H_{l-1}, column by column: column c is H_0 (... (H_c e_c)) (the reflectors
+  // H_i with i > c leave e_c unchanged: v_i is zero above row i).  Every thread runs the same
+  // count (its warp's last column), so the shuffles stay warp-wide; for i > c the product
+  // v_i^T q is exactly zero.  No barriers: the reflectors are read-only now.
+  float q[RPT];
+#pragma unroll
+  for (int r = 0; r < RPT; ++r) q[r] = (i0 + r == c) ? 1.f : 0.f;
+  {
+    int imax = (warp + 1) * (32 / TPC) - 1;
+    if (imax > l - 1) imax = l - 1;
+    for (int i = imax; i >= 0; --i) {
+      float v[RPT];
+      const float4* v4 = reinterpret_cast<const float4*>(Vs + i * SKW + sk(i0));
+#pragma unroll
+      for (int qq = 0; qq < RPT / 4; ++qq) {
+        const float4 t = v4[qq];
+        v[4 * qq] = t.x; v[4 * qq + 1] = t.y; v[4 * qq + 2] = t.z; v[4 * qq + 3] = t.w;
+      }
+      float w0 = 0.f, w1 = 0.f;
+#pragma unroll
+      for (int r = 0; r < RPT; r += 2) {
+        w0 = fmaf(v[r], q[r], w0);
+        w1 = fmaf(v[r + 1], q[r + 1], w1);
+      }
+      float w = w0 + w1;
+#pragma unroll
+      for (int o = 1; o < TPC; o <<= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+      const float f = betas[i] * w;
+#pragma unroll
+      for (int r = 0; r < RPT; ++r) q[r] = fmaf(-f, v[r], q[r]);
+    }
+  }
+  __syncthreads();                             // the reflectors' memory becomes the staging tile
+  // ||R||_F^2 and ||R(1:k, :)||_F^2 as compensated FP32 sums (exact squares, TwoSum), in FP64
+  // across warps; R and Q~ go through a shared tile so that their rows are written whole
+  float* St = Vs;                              // l x (l + 1)
+  const int SL = l + 1;
   float fa = 0.f, fae = 0.f, fb = 0.f, fbe = 0.f;
   auto acc_sq = [](float v, float& sum, float& err) {
     const float p = v * v;
@@ -1371,6 +1407,22 @@ __device__ __forceinline__ void qrcp_reg_body(const TD* __restrict__ Dg, int64_t
     sum = t;
     err += e + fmaf(v, v, -p);
   };
+  // Q~[a][c] with the column sign of diag(R) (diag(R) >= 0)
+  if (c < l) {
+    const float sgn = rdiag[c] < 0.f ? -1.f : 1.f;
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      const int a = i0 + r;
+      if (a < l) St[a * SL + c] = sgn * q[r];
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < l * l; e += blockDim.x) {
+    const int a = e / l, b = e - a * l;
+    Qg[a * ldq + b] = (TQ)St[a * SL + b];
+  }
+  __syncthreads();
+  // R from each pivot column (rows above its position), diag(R) >= 0
   if (posof >= 0) {
 #pragma unroll
     for (int r = 0; r < RPT; ++r) {
@@ -1380,8 +1432,8 @@ __device__ __forceinline__ void qrcp_reg_body(const TD* __restrict__ Dg, int64_t
       if (i < posof) val = (rdiag[i] < 0.f ? -1.f : 1.f) * d[r];
       else if (i == posof) val = fabsf(rdiag[i]);
       else val = 0.f;
-      if (r_transposed) Rg[posof * ldr + i] = (double)val;
-      else Rg[i * ldr + posof] = (double)val;
+      if (r_transposed) St[posof * SL + i] = val;
+      else St[i * SL + posof] = val;
       acc_sq(val, fa, fae);
       if (i < k) acc_sq(val, fb, fbe);
     }
@@ -1402,16 +1454,12 @@ __device__ __forceinline__ void qrcp_reg_body(const TD* __restrict__ Dg, int64_t
     red[warp][0] = (double)fa + (double)fae;
     red[warp][1] = (double)fb + (double)fbe;
   }
-  // Q~ = H_0 ... H_{l-1} = M^T: Q~[c][q] = M[q][c] (thread holds M[i0.., c]), column sign from diag(R)
-  if (c < l) {
-#pragma unroll
-    for (int r = 0; r < RPT; ++r) {
-      const int q = i0 + r;
-      if (q < l) Qg[c * ldq + q] = (TQ)((rdiag[q] < 0.f ? -1.f : 1.f) * m[r]);
-    }
-  }
-  for (int j = tid; j < l; j += blockDim.x) perm[j] = pcol[j];
+  for (int jj = tid; jj < l; jj += blockDim.x) perm[jj] = pcol[jj];
   __syncthreads();
+  for (int e = tid; e < l * l; e += blockDim.x) {
+    const int a = e / l, b = e - a * l;
+    Rg[a * ldr + b] = (double)St[a * SL + b];
+  }
   if (tid == 0) {
     double a2 = 0.0, b2 = 0.0;
     for (int w2 = 0; w2 < NWARP; ++w2) { a2 += red[w2][0]; b2 += red[w2][1]; }
@@ -1432,8 +1480,12 @@ template <typename TC>
 cudaError_t launch_qrcp(const TC* D, int64_t ldd, int l, int k, TC* Q, int64_t ldq, double* R, int64_t ldr,
                         bool r_transposed, int32_t* perm, double* fro2, DevStatus* status, cudaStream_t st) {
   if constexpr (sizeof(TC) == 4) {
-    qrcp_reg_kernel<kQrcpTPC, float, float><<<1, kMaxL * kQrcpTPC, 0, st>>>(D, ldd, l, k, Q, ldq, R, ldr,
-                                                                            r_transposed ? 1 : 0, perm, fro2, status);
+    static bool attr_set[kAttrDevices] = {};
+    cudaError_t e = raise_smem_once(qrcp_reg_kernel<kQrcpTPC, float, float>, kQrcpSmem, attr_set);
+    if (e != cudaSuccess) return e;
+    qrcp_reg_kernel<kQrcpTPC, float, float><<<1, kMaxL * kQrcpTPC, kQrcpSmem, st>>>(D, ldd, l, k, Q, ldq, R, ldr,
+                                                                                    r_transposed ? 1 : 0, perm, fro2,
+                                                                                    status);
     CORUTV_COUNT_LAUNCH();
     return cudaGetLastError();
   } else {
@@ -1450,8 +1502,11 @@ template <typename TC>
 cudaError_t launch_qrcp_f64io(const double* D, int64_t ldd, int l, int k, double* Q, int64_t ldq, double* R,
                               int64_t ldr, int32_t* perm, double* fro2, cudaStream_t st) {
   if constexpr (sizeof(TC) == 4) {
-    qrcp_reg_kernel<kQrcpTPC, double, double><<<1, kMaxL * kQrcpTPC, 0, st>>>(D, ldd, l, k, Q, ldq, R, ldr, 0, perm,
-                                                                              fro2, nullptr);
+    static bool attr_set[kAttrDevices] = {};
+    cudaError_t e = raise_smem_once(qrcp_reg_kernel<kQrcpTPC, double, double>, kQrcpSmem, attr_set);
+    if (e != cudaSuccess) return e;
+    qrcp_reg_kernel<kQrcpTPC, double, double><<<1, kMaxL * kQrcpTPC, kQrcpSmem, st>>>(D, ldd, l, k, Q, ldq, R, ldr, 0,
+                                                                                      perm, fro2, nullptr);
     CORUTV_COUNT_LAUNCH();
     return cudaGetLastError();
   } else {
@@ -1738,7 +1793,10 @@ cudaError_t launch_copy_sketch_grouped(const BatchProb* P, const int2* map32_2, 
 
 cudaError_t launch_qrcp_grouped(const BatchProb* P, int count, cudaStream_t st) {
   if (count <= 0) return cudaSuccess;
-  qrcp_grouped_kernel<<<count, kMaxL * kQrcpTPC, 0, st>>>(P);
+  static bool attr_set[kAttrDevices] = {};
+  cudaError_t e = raise_smem_once(qrcp_grouped_kernel, kQrcpSmem, attr_set);
+  if (e != cudaSuccess) return e;
+  qrcp_grouped_kernel<<<count, kMaxL * kQrcpTPC, kQrcpSmem, st>>>(P);
   CORUTV_COUNT_LAUNCH();
   return cudaGetLastError();
 }
