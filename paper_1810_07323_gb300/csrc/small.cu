@@ -350,9 +350,9 @@ __device__ __forceinline__ float rsqrt_nr(float x) {
 // triangle of L^-1 split into 4 x 4 blocks.  Thread t owns block (I, J), J >= I,
 // of G and block (J, I) of L^-1 (t enumerates the upper block triangle column
 // by column).  Step j reads row j of G and of L^-1 from a double-buffered shared
-// row (published at the end of step j - 1 by the owners of row j), applies its
-// multipliers m_a = G[j][a] / d_j to the rows a > j of both blocks, and the
-// owners of row j + 1 publish it: one block barrier per step.  Reciprocals and
+// row (published by the owners of row j), applies its multipliers
+// m_a = G[j][a] / d_j to the rows a > j of both blocks; steps go in pairs with
+// one block barrier per pair (see the loop).  Reciprocals and
 // square roots come from rcp_nr / rsqrt_nr, and the input is the FP32 Gram
 // matrix (no FP64 arithmetic: GB300's FP64 pipe would dominate the step).
 __device__ __forceinline__ float f4(const float4& v, int i) {
@@ -370,8 +370,8 @@ __device__ __forceinline__ void cholinv_pipe_body(const float* __restrict__ G, i
                                                   int64_t ldr, int* __restrict__ defic, DevStatus* status,
                                                   double* __restrict__ Rout, int* __restrict__ skip_flag,
                                                   float skip_tol) {
-  __shared__ __align__(16) float rowbuf[2][kMaxL];
-  __shared__ __align__(16) float libuf[2][kMaxL];
+  __shared__ __align__(16) float rowbuf[2][2][kMaxL];   // [pair parity][row j / j + 1]
+  __shared__ __align__(16) float libuf[2][2][kMaxL];
   __shared__ float diag0[kMaxL];
   __shared__ float piv[kMaxL];
   __shared__ float pivrs[kMaxL];     // 1 / sqrt(piv)
@@ -407,7 +407,7 @@ __device__ __forceinline__ void cholinv_pipe_body(const float* __restrict__ G, i
     for (int r = 0; r < 4; ++r)
       if (4 * I + r < l) tr += g[r][r];
   }
-  for (int e = tid; e < 2 * kMaxL; e += blockDim.x) (&libuf[0][0])[e] = 0.f;
+  for (int e = tid; e < 4 * kMaxL; e += blockDim.x) (&libuf[0][0][0])[e] = 0.f;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     tr += __shfl_xor_sync(0xffffffffu, tr, o);
@@ -445,46 +445,99 @@ __device__ __forceinline__ void cholinv_pipe_body(const float* __restrict__ G, i
         }
       }
     }
-    // row 0 of G and of L^-1
-    if (I == 0) *reinterpret_cast<float4*>(&rowbuf[0][4 * J]) = make_float4(g[0][0], g[0][1], g[0][2], g[0][3]);
-    if (J == 0) *reinterpret_cast<float4*>(&libuf[0][4 * I]) = make_float4(li[0][0], li[0][1], li[0][2], li[0][3]);
+    // rows 0 and 1 of G and of L^-1
+    if (I == 0) {
+      *reinterpret_cast<float4*>(&rowbuf[0][0][4 * J]) = make_float4(g[0][0], g[0][1], g[0][2], g[0][3]);
+      *reinterpret_cast<float4*>(&rowbuf[0][1][4 * J]) = make_float4(g[1][0], g[1][1], g[1][2], g[1][3]);
+    }
+    if (J == 0) {
+      *reinterpret_cast<float4*>(&libuf[0][0][4 * I]) = make_float4(li[0][0], li[0][1], li[0][2], li[0][3]);
+      *reinterpret_cast<float4*>(&libuf[0][1][4 * I]) = make_float4(li[1][0], li[1][1], li[1][2], li[1][3]);
+    }
   }
   __syncthreads();
 
-  for (int j = 0; j < l; ++j) {
-    const int buf = j & 1;
-    const float d = rowbuf[buf][j];
-    const float d0 = diag0[j];
-    const bool dep = !(d > tolf * d0) || !(d0 > 0.f);
-    const float inv_d = dep ? 0.f : rcp_nr(d);
+  // Two elimination steps per barrier: step pair (j, j + 1) reads rows j and j + 1 as of
+  // step j - 1; every thread forms the part of row j + 1 after step j that it needs itself
+  // (row_{j+1} - m row_j, m = G[j][j+1] / d_j), so the owners publish rows j + 2 and j + 3
+  // once per pair.
+  for (int j = 0; j < l; j += 2) {
+    const int pb = (j >> 1) & 1;
+    const bool two = j + 1 < l;
+    const float dj = rowbuf[pb][0][j];
+    const float d0j = diag0[j];
+    const bool depj = !(dj > tolf * d0j) || !(d0j > 0.f);
+    const float invj = depj ? 0.f : rcp_nr(dj);
+    // row j + 1 after step j: its multiplier, pivot and dependence
+    const float m1 = two ? rowbuf[pb][0][j + 1] * invj : 0.f;
+    const float dk = two ? fmaf(-m1, rowbuf[pb][0][j + 1], rowbuf[pb][1][j + 1]) : 1.f;
+    const float d0k = two ? diag0[j + 1] : 1.f;
+    const bool depk = !(dk > tolf * d0k) || !(d0k > 0.f);
+    const float invk = (depk || !two) ? 0.f : rcp_nr(dk);
     if (tid == 0) {
-      piv[j] = dep ? 1.f : d;
-      pivrs[j] = dep ? 1.f : rsqrt_nr(d);
-      dep_s[j] = dep ? 1 : 0;
+      piv[j] = depj ? 1.f : dj;
+      pivrs[j] = depj ? 1.f : rsqrt_nr(dj);
+      dep_s[j] = depj ? 1 : 0;
+      if (two) {
+        piv[j + 1] = depk ? 1.f : dk;
+        pivrs[j + 1] = depk ? 1.f : rsqrt_nr(dk);
+        dep_s[j + 1] = depk ? 1 : 0;
+      }
     }
     if (own && 4 * J + 3 > j) {
-      const float4 rI = *reinterpret_cast<const float4*>(&rowbuf[buf][4 * I]);
-      const float4 rJ = *reinterpret_cast<const float4*>(&rowbuf[buf][4 * J]);
-      const float4 lI = *reinterpret_cast<const float4*>(&libuf[buf][4 * I]);
+      const float4 rI0 = *reinterpret_cast<const float4*>(&rowbuf[pb][0][4 * I]);
+      const float4 rJ0 = *reinterpret_cast<const float4*>(&rowbuf[pb][0][4 * J]);
+      const float4 lI0 = *reinterpret_cast<const float4*>(&libuf[pb][0][4 * I]);
+      float4 rI1 = *reinterpret_cast<const float4*>(&rowbuf[pb][1][4 * I]);
+      float4 rJ1 = *reinterpret_cast<const float4*>(&rowbuf[pb][1][4 * J]);
+      float4 lI1 = *reinterpret_cast<const float4*>(&libuf[pb][1][4 * I]);
+      // step j
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
-        const float mi = (4 * I + r > j) ? f4(rI, r) * inv_d : 0.f;   // rows of the G block
-        const float mj = (4 * J + r > j) ? f4(rJ, r) * inv_d : 0.f;   // rows of the L^-1 block
+        const float mi = (4 * I + r > j) ? f4(rI0, r) * invj : 0.f;   // rows of the G block
+        const float mj = (4 * J + r > j) ? f4(rJ0, r) * invj : 0.f;   // rows of the L^-1 block
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-          g[r][c] = fmaf(-mi, f4(rJ, c), g[r][c]);
-          li[r][c] = fmaf(-mj, f4(lI, c), li[r][c]);
+          g[r][c] = fmaf(-mi, f4(rJ0, c), g[r][c]);
+          li[r][c] = fmaf(-mj, f4(lI0, c), li[r][c]);
         }
       }
-      const int p = j + 1;
-      if (p < l) {
-        const int pb = p & 1, pr = p & 3;
+      // step j + 1 with row j + 1 as of step j (invk = 0 when there is no step j + 1)
+      rI1 = make_float4(fmaf(-m1, rI0.x, rI1.x), fmaf(-m1, rI0.y, rI1.y), fmaf(-m1, rI0.z, rI1.z),
+                        fmaf(-m1, rI0.w, rI1.w));
+      rJ1 = make_float4(fmaf(-m1, rJ0.x, rJ1.x), fmaf(-m1, rJ0.y, rJ1.y), fmaf(-m1, rJ0.z, rJ1.z),
+                        fmaf(-m1, rJ0.w, rJ1.w));
+      lI1 = make_float4(fmaf(-m1, lI0.x, lI1.x), fmaf(-m1, lI0.y, lI1.y), fmaf(-m1, lI0.z, lI1.z),
+                        fmaf(-m1, lI0.w, lI1.w));
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-          if (r == pr && I == (p >> 2))
-            *reinterpret_cast<float4*>(&rowbuf[pb][4 * J]) = make_float4(g[r][0], g[r][1], g[r][2], g[r][3]);
-          if (r == pr && J == (p >> 2))
-            *reinterpret_cast<float4*>(&libuf[pb][4 * I]) = make_float4(li[r][0], li[r][1], li[r][2], li[r][3]);
+      for (int r = 0; r < 4; ++r) {
+        const float mi = (4 * I + r > j + 1) ? f4(rI1, r) * invk : 0.f;
+        const float mj = (4 * J + r > j + 1) ? f4(rJ1, r) * invk : 0.f;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          g[r][c] = fmaf(-mi, f4(rJ1, c), g[r][c]);
+          li[r][c] = fmaf(-mj, f4(lI1, c), li[r][c]);
+        }
+      }
+      // publish rows j + 2 and j + 3 (the same block row; register rows 0, 1 or 2, 3)
+      const int p = j + 2;
+      if (p < l) {
+        const int qb = pb ^ 1, hi = (p & 3) >> 1;
+        if (I == (p >> 2)) {
+          const float4 a0 = hi ? make_float4(g[2][0], g[2][1], g[2][2], g[2][3])
+                               : make_float4(g[0][0], g[0][1], g[0][2], g[0][3]);
+          const float4 a1 = hi ? make_float4(g[3][0], g[3][1], g[3][2], g[3][3])
+                               : make_float4(g[1][0], g[1][1], g[1][2], g[1][3]);
+          *reinterpret_cast<float4*>(&rowbuf[qb][0][4 * J]) = a0;
+          *reinterpret_cast<float4*>(&rowbuf[qb][1][4 * J]) = a1;
+        }
+        if (J == (p >> 2)) {
+          const float4 b0 = hi ? make_float4(li[2][0], li[2][1], li[2][2], li[2][3])
+                               : make_float4(li[0][0], li[0][1], li[0][2], li[0][3]);
+          const float4 b1 = hi ? make_float4(li[3][0], li[3][1], li[3][2], li[3][3])
+                               : make_float4(li[1][0], li[1][1], li[1][2], li[1][3]);
+          *reinterpret_cast<float4*>(&libuf[qb][0][4 * I]) = b0;
+          *reinterpret_cast<float4*>(&libuf[qb][1][4 * I]) = b1;
         }
       }
     }
