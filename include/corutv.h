@@ -247,11 +247,15 @@ int corutv_batch_workspace_size(int count, const corutv_problem* probs, size_t* 
  * each with its own m, n, k, l, q, side, core, dtype and pointers; probs is a
  * host array).  Every step of the schedule runs as one grouped launch over all
  * problems (problems beyond their last power step skip the loop's launches),
- * so the launch count does not grow with `count`.  The passes run on the CUDA
- * cores with FP32 accumulation, one CTA per 64 output positions over the whole
- * reduction (no split), the orthonormalisation and QRCP as in corutv_solve.
- * Limits: l <= 128; a_dtype F64 and the tensor-core mma modes return
- * ERR_UNSUPPORTED.  The handle keeps a workspace and the tables of the last
+ * so the launch count does not grow with `count`.  FP32 batches whose rows TMA
+ * can address (16-byte aligned base and row pitch) run every pass as one
+ * grouped TF32 tensor-core launch (mma AUTO or TF32; rounded operands, FP32
+ * accumulation, problems' (tile, k-block) iterations concatenated and split
+ * evenly over the SMs); otherwise, and for mma SIMT or BF16 / FP8 storage, the
+ * passes run on the CUDA cores with FP32 accumulation, one CTA per 64 output
+ * positions over the whole reduction.  Orthonormalisation and QRCP as in
+ * corutv_solve.  Limits: l <= 128; a_dtype F64 and the BF16X2 / TF32_TRUNC
+ * modes return ERR_UNSUPPORTED (TF32 needs FP32 storage).  The handle keeps a workspace and the tables of the last
  * problem set; calling again with an identical problem array (same shapes,
  * pointers and parameters) replays a CUDA graph of the whole batch (not on the
  * legacy default stream, and not while tracing: traced runs launch directly so
