@@ -311,6 +311,53 @@ int corutv_server_stats(corutv_server* s, int64_t* batches, int64_t* solved, int
 /* Stop accepting requests, finish the queued ones, stop the worker, free everything. */
 int corutv_server_destroy(corutv_server* s);
 
+/* ------------------------------------------------------------------------
+ * Robust PCA by ALM-CoRUTV (Sec. V, Alg. 5): M = L + S with L low-rank and S
+ * sparse, one CoR-UTV solve per iteration.
+ * ---------------------------------------------------------------------- */
+
+typedef struct {
+  int64_t m, n;          /* shape of M */
+  int32_t k, l, q;       /* the CoR-UTV of every iteration (Alg. 2 / 3): k <= l < min(m, n), l <= 128 */
+  int32_t side;          /* corutv_side of that CoR-UTV (Phi n x l for RIGHT, m x l for LEFT) */
+  int32_t mma;           /* corutv_mma of its passes: AUTO or SIMT = FP32 products on the CUDA cores;
+                            TF32 = tensor cores (its ~2^-11 product errors can keep extra diagonals of T
+                            above the late, small thresholds 1 / mu) */
+  int32_t max_iter;      /* iteration limit (>= 1) */
+  double lambda;         /* weight of ||S||_1 (Sec. V); the customary choice is 1 / sqrt(max(m, n)) */
+  double mu0, rho, mu_bar;   /* penalty schedule: mu_{j+1} = min(rho mu_j, mu_bar), rho >= 1 */
+  double tol;            /* stop when ||M - L - S||_F / ||M||_F < tol (Sec. VI-C uses 1e-5) */
+  int32_t reserved[4];   /* must be zero */
+} corutv_rpca_params;
+
+typedef struct {
+  int32_t status;        /* corutv_status of the device work */
+  int32_t iters;         /* iterations run */
+  int32_t rank;          /* r of the last thresholding (diagonals of T above 1 / mu) */
+  int32_t converged;     /* 1 if the stopping rule was met */
+  double zeta;           /* ||M - L - S||_F / ||M||_F after the last iteration */
+  double mu;             /* penalty after the last update */
+} corutv_rpca_info;
+
+/*
+ * corutv_rpca -- Alg. 5 (ALM-CoRUTV) with Y_0 = S_0 = 0: per iteration
+ *   L = C_{1/mu}(M - S + Y / mu)     C_delta(B) = U(:,1:r) T(1:r,:) V^T, r = #{T_jj > delta},
+ *                                    U, T, V the CoR-UTV of B with the caller's Phi (Sec. V)
+ *   S = S_{lambda/mu}(M - L + Y / mu)  (shrinkage, sgn(x) max(|x| - delta, 0))
+ *   Y = Y + mu (M - L - S),  mu = min(rho mu, mu_bar)
+ * until ||M - L - S||_F / ||M||_F < tol or max_iter iterations.  All matrices
+ * are FP32, row-major, device, caller-owned: M (m x n, ldm) is read-only;
+ * L, S and Y (m x n, each ld >= n and a multiple of 4, 16-byte aligned, as the
+ * tensor-core passes read L's memory as the iteration's B) receive the
+ * results (Y the final multiplier); Phi as for corutv_solve, reused by every
+ * iteration.  The call returns when the iterations are done (it reads the
+ * residual back once per iteration); info (host) receives the outcome.  The
+ * handle keeps a lazily allocated buffer for the factors of the iterations.
+ */
+int corutv_rpca(corutv_handle* h, const corutv_rpca_params* p, const float* M, int64_t ldm, const float* Phi,
+                int64_t ldphi, float* L, int64_t ldl, float* S, int64_t lds, float* Y, int64_t ldy,
+                corutv_rpca_info* info);
+
 /* Synchronise the handle's stream and return the outcome of the last solve. */
 int corutv_info_wait(corutv_handle* h, corutv_info* out);
 

@@ -70,6 +70,19 @@ class Trace(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class RpcaParams(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("k", ctypes.c_int32), ("l", ctypes.c_int32),
+                ("q", ctypes.c_int32), ("side", ctypes.c_int32), ("mma", ctypes.c_int32),
+                ("max_iter", ctypes.c_int32), ("lam", ctypes.c_double), ("mu0", ctypes.c_double),
+                ("rho", ctypes.c_double), ("mu_bar", ctypes.c_double), ("tol", ctypes.c_double),
+                ("reserved", ctypes.c_int32 * 4)]
+
+
+class RpcaInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("iters", ctypes.c_int32), ("rank", ctypes.c_int32),
+                ("converged", ctypes.c_int32), ("zeta", ctypes.c_double), ("mu", ctypes.c_double)]
+
+
 _lib = None
 
 # every entry point declared in include/corutv.h
@@ -79,7 +92,7 @@ EXPORTS = ("corutv_version", "corutv_status_string", "corutv_create", "corutv_de
            "corutv_qrcp", "corutv_fro2", "corutv_gram_noalloc", "corutv_solve_corrected", "corutv_quantize",
            "corutv_batch_workspace_size", "corutv_solve_batched", "corutv_batch_info_wait",
            "corutv_server_create", "corutv_server_submit", "corutv_server_poll", "corutv_server_stats",
-           "corutv_server_destroy")
+           "corutv_server_destroy", "corutv_rpca")
 
 
 def load() -> ctypes.CDLL:
@@ -120,6 +133,8 @@ def load() -> ctypes.CDLL:
     lib.corutv_fro2.argtypes = [P, ctypes.c_int, P, I64, I64, I64, P, P]
     lib.corutv_gram_noalloc.argtypes = [P, ctypes.c_int, P, I64, P, I64, I64, I32, P]
     lib.corutv_gram_noalloc.restype = ctypes.c_int
+    lib.corutv_rpca.argtypes = [P, ctypes.POINTER(RpcaParams), P, I64, P, I64, P, I64, P, I64, P, I64,
+                                ctypes.POINTER(RpcaInfo)]
     lib.corutv_set_tracing.argtypes = [P, ctypes.c_int]
     lib.corutv_trace_read.argtypes = [P, ctypes.POINTER(Trace)]
     for name in ("corutv_set_tracing", "corutv_trace_read", "corutv_create", "corutv_destroy", "corutv_set_stream", "corutv_workspace_size",
@@ -127,7 +142,7 @@ def load() -> ctypes.CDLL:
                  "corutv_orthonormalize", "corutv_gram", "corutv_qrcp", "corutv_fro2", "corutv_solve_corrected",
                  "corutv_quantize", "corutv_batch_workspace_size", "corutv_solve_batched",
                  "corutv_batch_info_wait", "corutv_server_create", "corutv_server_submit", "corutv_server_poll",
-                 "corutv_server_stats", "corutv_server_destroy"):
+                 "corutv_server_stats", "corutv_server_destroy", "corutv_rpca"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -305,6 +320,47 @@ def solve(A, Phi, k: int, l: int, q: int = 0, side: str = "right", core: str = "
         _check(rc, "corutv_solve_corrected")
     info = info_wait(h) if wait else None
     return SolveResult(U, T, V, perm, info)
+
+
+class RpcaResult:
+    def __init__(self, L, S, Y, info):
+        self.L, self.S, self.Y, self.info = L, S, Y, info
+
+
+def rpca(M, Phi, k: int, l: int, q: int, lam: float, mu0: float, rho: float, mu_bar: float, tol: float = 1e-5,
+         max_iter: int = 100, side: str = "right", mma: str = "auto", out=None, handle: Handle | None = None):
+    """Robust PCA by ALM-CoRUTV (Alg. 5): M (m, n) float32 on the device ~ L + S.
+
+    Phi: (n, l) for side="right", (m, l) for side="left", float32.  out:
+    optional (L, S, Y) float32 (m, n) buffers with a row pitch of a multiple
+    of 4 elements.  Returns L, S, the final multiplier Y and the info
+    (iterations, rank, zeta, converged)."""
+    import torch
+    _need_cuda(M, Phi)
+    if M.dtype != torch.float32 or Phi.dtype != torch.float32:
+        raise TypeError("M and Phi must be float32")
+    h = handle or handle_for()
+    m, n = M.shape
+    if out is None:
+        pitch = -(-n // 4) * 4
+        L, S, Y = (torch.empty((m, pitch), dtype=torch.float32, device=M.device)[:, :n] for _ in range(3))
+    else:
+        L, S, Y = out
+    p = RpcaParams()
+    p.m, p.n, p.k, p.l, p.q = m, n, k, l, q
+    p.side = SIDE[side]
+    p.mma = MMA[mma]
+    p.max_iter = max_iter
+    p.lam, p.mu0, p.rho, p.mu_bar, p.tol = lam, mu0, rho, mu_bar, tol
+    info = RpcaInfo()
+    rc = load().corutv_rpca(h.h, ctypes.byref(p), ctypes.c_void_p(M.data_ptr()), _rowmajor_ld(M),
+                            ctypes.c_void_p(Phi.data_ptr()), _rowmajor_ld(Phi), ctypes.c_void_p(L.data_ptr()),
+                            _rowmajor_ld(L), ctypes.c_void_p(S.data_ptr()), _rowmajor_ld(S),
+                            ctypes.c_void_p(Y.data_ptr()), _rowmajor_ld(Y), ctypes.byref(info))
+    _check(rc, "corutv_rpca")
+    if info.status != 0:
+        raise CorutvError(info.status, "corutv_rpca (device)")
+    return RpcaResult(L, S, Y, info)
 
 
 def quantize(A, dtype: str, out=None, tile_scales=None, handle: Handle | None = None):

@@ -459,6 +459,7 @@ int corutv_destroy(corutv_handle* h) {
   }
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   batch_state_free(h->batch);
+  rpca_free(h);
   delete h;
   return CORUTV_OK;
 }

@@ -38,7 +38,11 @@ struct corutv_handle {
   double last_shift = 0.0;
   bool have_last = false;
   corutv::BatchState* batch = nullptr;
+  void* rpca_ws = nullptr;      // factors of the ALM-CoRUTV iterations (rpca.cu), lazily allocated
+  size_t rpca_ws_bytes = 0;
 };
+
+void rpca_free(corutv_handle* h);
 
 
 inline cudaEvent_t ev_get(corutv_handle* h) {
