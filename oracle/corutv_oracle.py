@@ -13,6 +13,7 @@ Decompositions for Low-Rank Approximations and Big Data Applications"
 Functions
   householder_qr   thin QR of a tall block, diag(R) >= 0       (Sec. III, QR of C1, C2)
   qrcp             Householder QR with column pivoting           (Sec. III, Eq. (D = Q~ R~ P~^T))
+  qlp              QRCP followed by an unpivoted QR of R^T (Stewart's QLP), the core variant
   jacobi_svd       one-sided cyclic Jacobi SVD (quality tool)    (Sec. II, Eq. (SVD))
   corutv           Alg. 2 / Alg. 3, stabilised or literal, exact or approximate core
   rank_k           Sec. VI-B2 rank-k view U(:,1:k) T(1:k,:) V^T
@@ -135,6 +136,21 @@ def qrcp(D: np.ndarray):
     return Q * d[None, :], R * d[:, None], perm
 
 
+def qlp(D: np.ndarray):
+    """Pivoted QLP of the core (Stewart's QLP approximation of the SVD, SIAM J. Sci.
+    Comput. 20 (1999): a QRCP followed by an unpivoted QR of R^T), the alternative
+    to Eq. (D = Q~ R~ P~^T) for the l x l core:
+        D P = Q R,  R^T = Qh Rh   =>   D = Q L W^T,  L = Rh^T lower triangular, W = P Qh.
+    Returns Q, L, W, perm (the QRCP's) and Qh; diag(L) >= 0.
+    """
+    Q, R, perm = qrcp(D)
+    Qh, Rh = householder_qr(R.T)
+    n = R.shape[0]
+    P = np.zeros((n, n))
+    P[perm, np.arange(n)] = 1.0                  # (D P)[:, j] = D[:, perm[j]]
+    return Q, Rh.T.copy(), gemm(P, Qh), perm, Qh
+
+
 # ============================================================================ Jacobi SVD
 def _round_robin(n: int):
     """Rounds of disjoint pairs covering every pair once (circle method), n even."""
@@ -225,7 +241,8 @@ def _check(m, n, k, l, q):
 
 
 def corutv(A: np.ndarray, Phi: np.ndarray, k: int, l: int, q: int = 0,
-           core: str = "exact", orth: str = "stabilised", side: str = "right", A_core=None) -> dict:
+           core: str = "exact", orth: str = "stabilised", side: str = "right", A_core=None,
+           factor: str = "qrcp") -> dict:
     """CoR-UTV (Alg. 2 for q = 0, Alg. 3 for q >= 0) in float64.
 
     side="right": the paper's order, Phi (= Psi) is n x l and C1 = A Psi first;
@@ -243,6 +260,11 @@ def corutv(A: np.ndarray, Phi: np.ndarray, k: int, l: int, q: int = 0,
     D_approx = Q1^T C1 (Q2^T C2_prev)^+ (Eq. (D_approx)), C2_prev being the
     non-updated sketch that produced the last C1.
 
+    factor="qrcp": the core's rank-revealing factorisation is the QRCP of
+    Eq. (D = Q~ R~ P~^T), T = R~ upper triangular; factor="qlp": its QLP
+    (see qlp), T = L lower triangular and V = Q2 P~ Qh (the URV becomes a ULV;
+    the diagonal of L tracks the singular values more closely).
+
     A_core (optional, same shape as A, core="exact" only): the correction
     pass of a low-precision A -- the range finding runs on A, the core is
     the projection D = Q1^T A_core Q2 (Eq. (D)) of the full-precision matrix
@@ -259,7 +281,7 @@ def corutv(A: np.ndarray, Phi: np.ndarray, k: int, l: int, q: int = 0,
             raise ValueError("A_core must match A and needs core='exact'")
     if side == "left":
         r = corutv(A.T, Phi, k, l, q, core=core, orth=orth, side="right",
-                   A_core=None if A_core is None else A_core.T)
+                   A_core=None if A_core is None else A_core.T, factor=factor)
         out = dict(r)
         out["U"], out["V"] = r["V"], r["U"]
         out["T"] = r["T"].T.copy()
@@ -296,10 +318,16 @@ def corutv(A: np.ndarray, Phi: np.ndarray, k: int, l: int, q: int = 0,
     else:
         raise ValueError("core must be 'exact' or 'approx'")
 
-    Qt, Rt, perm = qrcp(D)                       # Alg. 2 step 6
+    if factor == "qrcp":
+        Qt, Rt, perm = qrcp(D)                   # Alg. 2 step 6
+        T = Rt
+        V = Q2[:, perm]                          # V = Q2 P~ (columns of Q2 in pivot order)
+    elif factor == "qlp":
+        Qt, T, _, perm, Qh = qlp(D)
+        V = gemm(Q2[:, perm], Qh)                # V = Q2 P~ Qh
+    else:
+        raise ValueError("factor must be 'qrcp' or 'qlp'")
     U = gemm(Q1, Qt)                             # Alg. 2 step 7
-    T = Rt
-    V = Q2[:, perm]                              # V = Q2 P~ (columns of Q2 in pivot order)
     return dict(U=U, T=T, V=V, perm=perm, D=D, Q1=Q1, Q2=Q2, R1=R1, R2=R2,
                 C1=C1, Qt=Qt, side="right")
 

@@ -239,3 +239,22 @@ def test_correction_core_is_projection_of_reference(cfg1):
     assert e_c <= e_u
     with pytest.raises(ValueError):
         O.corutv(Aq, Phi, 20, 30, 1, core="approx", A_core=A)
+
+
+@pytest.mark.parametrize("q", [0, 1])
+def test_qlp_core_same_product(cfg1, q):
+    """factor="qlp" factors the same core: U T V^T is the QRCP form's product (to rounding),
+    T is lower triangular with a non-negative diagonal and U, V stay orthonormal."""
+    A = cfg1.A
+    phi = W.phi(A.shape[1], 30)
+    r1 = O.corutv(A, phi, 20, 30, q)
+    r2 = O.corutv(A, phi, 20, 30, q, factor="qlp")
+    assert O.factor_distance(r2["U"], r2["T"], r2["V"], r1["U"], r1["T"], r1["V"]) < 1e-13
+    assert np.all(np.triu(r2["T"], 1) == 0.0) and np.all(np.diag(r2["T"]) >= 0.0)
+    assert O.orthonormality_error(r2["U"]) < 1e-13 and O.orthonormality_error(r2["V"]) < 1e-13
+
+
+def test_qlp_exact_recovery(cfg1_exact):
+    A = cfg1_exact.A
+    r = O.corutv(A, W.phi(A.shape[1], 25), 20, 25, 0, factor="qlp")
+    assert O.fro_residual(A, r["U"], r["T"], r["V"]) / np.linalg.norm(A) < 1e-13

@@ -4,6 +4,7 @@ import numpy as np
 import pytest
 
 from oracle import corutv_oracle as O
+from synth import workloads as W
 
 
 def test_house_reflects_onto_e1():
@@ -120,3 +121,45 @@ def test_pinv_penrose_conditions():
     assert np.abs(P @ M @ P - P).max() < 1e-12
     assert np.abs((M @ P).T - M @ P).max() < 1e-12
     assert np.abs((P @ M).T - P @ M).max() < 1e-12
+
+
+# ---------------------------------------------------------------- QLP of the core
+def _gapped(c=0, n=60):
+    U = W.haar_orthonormal(300 + c, n, n)
+    V = W.haar_orthonormal(400 + c, n, n)
+    s = np.concatenate([np.linspace(1, 0.5, 20), 1e-3 * np.linspace(1, 0.5, n - 20)])
+    return (U * s) @ V.T, s
+
+
+def test_qlp_structure_and_reconstruction():
+    D, s = _gapped()
+    Q, L, Wm, perm, Qh = O.qlp(D)
+    assert np.linalg.norm(Q @ L @ Wm.T - D) < 1e-13 * np.linalg.norm(D)
+    assert np.all(np.triu(L, 1) == 0.0) and np.all(np.diag(L) >= 0.0)
+    for M in (Q, Wm, Qh):
+        assert np.abs(M.T @ M - np.eye(len(s))).max() < 1e-13
+    P = np.eye(len(s))[:, perm]
+    assert np.allclose(Wm, P @ Qh, atol=1e-15)
+
+
+@pytest.mark.parametrize("c", [0, 1, 2])
+def test_qlp_tracks_singular_values(c):
+    """Stewart's QLP property: the diagonal of L approximates the singular values far
+    better than the diagonal of the QRCP's R, and reveals the gap at least as sharply."""
+    D, s = _gapped(c)
+    _, R, _ = O.qrcp(D)
+    _, L, _, _, _ = O.qlp(D)
+    dr = np.abs(np.diag(R)) / s
+    dl = np.abs(np.diag(L)) / s
+    assert np.mean(np.abs(dl - 1)) < 0.5 * np.mean(np.abs(dr - 1))
+    assert 0.7 < dl.min() and dl.max() < 1.4
+    assert L[19, 19] / L[20, 20] > R[19, 19] / R[20, 20]
+
+
+def test_qlp_planted_mistake_qr_of_R():
+    """Planted mistake: the second QR taken of R instead of R^T does not reproduce D."""
+    D, s = _gapped()
+    Q, R, perm = O.qrcp(D)
+    Qh, Rh = O.householder_qr(R)                 # wrong: should be R^T
+    P = np.eye(len(s))[:, perm]
+    assert np.linalg.norm(Q @ Rh.T @ (P @ Qh).T - D) > 1e-3 * np.linalg.norm(D)
