@@ -39,7 +39,7 @@
 extern "C" {
 #endif
 
-#define CORUTV_ABI_VERSION 2
+#define CORUTV_ABI_VERSION 3
 
 typedef enum {
   CORUTV_OK = 0,
@@ -81,6 +81,16 @@ typedef enum {
 
 typedef enum { CORUTV_DIR_AX = 0, CORUTV_DIR_ATY = 1 } corutv_dir;
 
+/* Rank-revealing factorisation of the l x l core D (Alg. 2 step 6). */
+typedef enum {
+  CORUTV_FACTOR_QRCP = 0,    /* D = Q~ R~ P~^T (Eq. (D = Q~ R~ P~^T)): T = R~ (URV) */
+  CORUTV_FACTOR_QLP = 1      /* QLP (Stewart): the QRCP, then R~^T = Qh Rh, so D = Q~ L (P~ Qh)^T with
+                                L = Rh^T: T = L lower triangular and V = Q2 P~ Qh (RIGHT; LEFT gives the
+                                transposes); the diagonal of L tracks the singular values more closely.
+                                FP32-path solves only (F64 returns UNSUPPORTED); perm keeps the QRCP
+                                pivots */
+} corutv_factor;
+
 /* Parameters of one solve (Alg. 2 / Alg. 3). */
 typedef struct {
   int64_t m, n;          /* shape of A */
@@ -97,7 +107,8 @@ typedef struct {
   int32_t mma;           /* corutv_mma for the passes over A */
   int32_t want_fro2;     /* 1: also compute ||A||_F^2 into the info (fused into the first pass on the
                             tensor-core engine, one extra read of A otherwise) */
-  int32_t reserved[7];   /* must be zero */
+  int32_t factor;        /* corutv_factor of the core (QRCP by default) */
+  int32_t reserved[6];   /* must be zero */
 } corutv_params;
 
 /* Device-side outcome of the last solve on a handle. */

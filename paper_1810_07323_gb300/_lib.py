@@ -37,7 +37,7 @@ class Params(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("k", ctypes.c_int32), ("l", ctypes.c_int32),
                 ("q", ctypes.c_int32), ("side", ctypes.c_int32), ("core", ctypes.c_int32),
                 ("orth", ctypes.c_int32), ("a_dtype", ctypes.c_int32), ("mma", ctypes.c_int32),
-                ("want_fro2", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+                ("want_fro2", ctypes.c_int32), ("factor", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
 
 
 class Problem(ctypes.Structure):
@@ -262,17 +262,21 @@ def workspace_size(m, n, k, l, q=0, side="right", core="exact", a_dtype="f32", m
     return out.value
 
 
-def _params(m, n, k, l, q, side, core, a_dtype_code, mma, want_fro2, orth) -> Params:
+FACTOR = {"qrcp": 0, "qlp": 1}
+
+
+def _params(m, n, k, l, q, side, core, a_dtype_code, mma, want_fro2, orth, factor="qrcp") -> Params:
     p = Params()
     p.m, p.n, p.k, p.l, p.q = int(m), int(n), int(k), int(l), int(q)
     p.side, p.core, p.orth = SIDE[side], CORE[core], ORTH[orth]
     p.a_dtype, p.mma, p.want_fro2 = a_dtype_code, MMA[mma], 1 if want_fro2 else 0
+    p.factor = FACTOR[factor]
     return p
 
 
 def solve(A, Phi, k: int, l: int, q: int = 0, side: str = "right", core: str = "exact", mma: str = "auto",
           a_tile_scales=None, want_fro2: bool = False, out=None, wait: bool = True, handle: Handle | None = None,
-          A_ref=None, orth: str = "stabilised"):
+          A_ref=None, orth: str = "stabilised", factor: str = "qrcp"):
     """CoR-UTV of a device matrix A (Alg. 2 / Alg. 3): returns U, T, V, perm.
 
     A: (m, n) row-major float64 / float32 / bfloat16 / float8_e4m3fn (with
@@ -282,6 +286,8 @@ def solve(A, Phi, k: int, l: int, q: int = 0, side: str = "right", core: str = "
     bfloat16 / float8 A (corutv_solve_corrected: the core D from A_ref).
     orth: "stabilised" (one shifted CholeskyQR pass for the sketches of the
     earlier power steps) or "strict" (shifted CholeskyQR3 for every sketch).
+    factor: "qrcp" (T upper triangular) or "qlp" (T lower triangular, V
+    = Q2 P~ Qh; float32-path solves).
     out: optional (U, T, V, perm) preallocated outputs.  wait=True
     synchronises and returns the device info; wait=False leaves the work
     enqueued on the current stream (info is None).
@@ -294,7 +300,7 @@ def solve(A, Phi, k: int, l: int, q: int = 0, side: str = "right", core: str = "
     fdt = torch.float64 if code == 0 else torch.float32
     if Phi.dtype != fdt:
         raise TypeError(f"Phi must be {fdt}")
-    p = _params(m, n, k, l, q, side, core, code, mma, want_fro2, orth)
+    p = _params(m, n, k, l, q, side, core, code, mma, want_fro2, orth, factor)
     if out is None:
         dev = A.device
         U = torch.empty((m, l), dtype=fdt, device=dev)

@@ -150,6 +150,8 @@ int check_params(const corutv_params* p) {
   if (p->l >= std::min(p->m, p->n)) return CORUTV_ERR_SHAPE;      // l < min(m, n) (Sec. III)
   if (p->l > (p->a_dtype == CORUTV_F64 ? kMaxL64 : kMaxL)) return CORUTV_ERR_SHAPE;
   if (!mma_fits_dtype(p->a_dtype, p->mma)) return CORUTV_ERR_UNSUPPORTED;
+  if (p->factor != CORUTV_FACTOR_QRCP && p->factor != CORUTV_FACTOR_QLP) return CORUTV_ERR_INVALID_ARG;
+  if (p->factor == CORUTV_FACTOR_QLP && p->a_dtype == CORUTV_F64) return CORUTV_ERR_UNSUPPORTED;
   return CORUTV_OK;
 }
 
@@ -380,23 +382,33 @@ int solve_impl(corutv_handle* h, const corutv_params* p, const Plan& pl, const v
     CU((launch_gram<TC, TC>(P3, pl.ld3, P2, pl.ld2, pl.len2, l, static_cast<TC*>(pl.gram_parts),
                            gram_parts(pl.len2, h->sms), static_cast<TC*>(pl.D), kMaxL, h->stream)));
   }
+  const bool qlp = p->factor == CORUTV_FACTOR_QLP;
   {
     // S6: QRCP of D (Alg. 2 step 6); T = R~ (RIGHT) or R~^T (LEFT)
     PhaseTimer tm(h, kPhQrcp);
-    CU(launch_qrcp<TC>(static_cast<const TC*>(pl.D), kMaxL, l, p->k, static_cast<TC*>(pl.Qt), kMaxL, T, ldt, !right,
-                       perm, nullptr, pl.status, h->stream));
+    CU(launch_qrcp<TC>(static_cast<const TC*>(pl.D), kMaxL, l, p->k, static_cast<TC*>(pl.Qt), kMaxL, T, ldt,
+                       !right && !qlp, perm, nullptr, pl.status, h->stream));
+    if constexpr (sizeof(TC) == 4) {
+      if (qlp) {
+        // QLP: R~^T = Qh Rh; T = L = Rh^T (RIGHT) or Rh (LEFT); the Q2 side becomes Q2 P~ Qh
+        CU(launch_qlp_second(T, ldt, l, p->k, static_cast<float*>(pl.G), right,
+                             reinterpret_cast<int32_t*>(static_cast<float*>(pl.R)), pl.status, h->stream));
+        CU(launch_perm_rows(static_cast<const float*>(pl.G), perm, l, static_cast<float*>(pl.Rinv), h->stream));
+      }
+    }
   }
-  // S7: assembly (Alg. 2 step 7): Q1 Q~ and Q2 P~
+  // S7: assembly (Alg. 2 step 7): Q1 Q~ and Q2 P~ (Q2 P~ Qh for the QLP)
   PhaseTimer tm_asm(h, kPhAsm);
-  if (right) {
-    CU(launch_lmul_full<TC>(P1, pl.ld1, pl.len1, l, static_cast<const TC*>(pl.Qt), kMaxL, static_cast<TC*>(U), ldu,
-                            true, h->stream));
-    CU(launch_gather_cols<TC>(P2, pl.ld2, pl.len2, l, perm, static_cast<TC*>(V), ldv, h->stream));
-  } else {
-    CU(launch_lmul_full<TC>(P1, pl.ld1, pl.len1, l, static_cast<const TC*>(pl.Qt), kMaxL, static_cast<TC*>(V), ldv,
-                            true, h->stream));
-    CU(launch_gather_cols<TC>(P2, pl.ld2, pl.len2, l, perm, static_cast<TC*>(U), ldu, h->stream));
-  }
+  TC* out1 = static_cast<TC*>(right ? U : V);
+  TC* out2 = static_cast<TC*>(right ? V : U);
+  const int64_t ld1o = right ? ldu : ldv, ld2o = right ? ldv : ldu;
+  CU(launch_lmul_full<TC>(P1, pl.ld1, pl.len1, l, static_cast<const TC*>(pl.Qt), kMaxL, out1, ld1o, true,
+                          h->stream));
+  if (qlp)
+    CU(launch_lmul_full<TC>(P2, pl.ld2, pl.len2, l, static_cast<const TC*>(pl.Rinv), l, out2, ld2o, true,
+                            h->stream));
+  else
+    CU(launch_gather_cols<TC>(P2, pl.ld2, pl.len2, l, perm, out2, ld2o, h->stream));
   // S9: ||A||_F^2 on request
   if (p->want_fro2 && !fuse_fro2) {
     const int fdt = A_ref ? CORUTV_F32 : p->a_dtype;

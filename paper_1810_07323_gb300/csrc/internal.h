@@ -113,6 +113,11 @@ cudaError_t launch_qrcp(const TC* D, int64_t ldd, int l, int k, TC* Q, int64_t l
 template <typename TC>
 cudaError_t launch_qrcp_f64io(const double* D, int64_t ldd, int l, int k, double* Q, int64_t ldq, double* R,
                               int64_t ldr, int32_t* perm, double* fro2, cudaStream_t st);
+// QLP (second half): unpivoted QR of R~^T held in R; R receives L = Rh^T (to_lower) or Rh; Qh FP32
+cudaError_t launch_qlp_second(double* R, int64_t ldr, int l, int k, float* Qh, bool to_lower, int32_t* perm_scratch,
+                              DevStatus* status, cudaStream_t st);
+// S[perm[j]][c] = Qh[j][c] (l x l)
+cudaError_t launch_perm_rows(const float* Qh, const int32_t* perm, int l, float* S, cudaStream_t st);
 cudaError_t launch_fro2(int a_dtype, const void* A, int64_t lda, int64_t m, int64_t n, const float* scales,
                         int64_t sld, double* parts, int nparts, double* out, cudaStream_t st);
 int fro2_parts(int sms);

@@ -1266,11 +1266,16 @@ __global__ void __launch_bounds__(512) qrcp_kernel(const double* __restrict__ Dg
 // physical column exchanges.  The reflector and pivot column are stored with a
 // skew (row i at i + 4 (i / RPT)) so the TPC threads of a column read them
 // without shared-memory bank conflicts.
-template <int TPC, typename TD, typename TQ>
+// PIVOT = false: the unpivoted Householder QR (step j takes the column at position j), the
+// second factorisation of the QLP.  d_transposed: the input is D^T (Dg read column-wise).
+// tk_by_col: the rank-k readout sums the squares of the first k columns of R (the first k
+// rows of the output R^T) instead of its first k rows.
+template <int TPC, typename TD, typename TQ, bool PIVOT = true>
 __device__ __forceinline__ void qrcp_reg_body(const TD* __restrict__ Dg, int64_t ldd, int l, int k,
                                               TQ* __restrict__ Qg, int64_t ldq, double* __restrict__ Rg,
                                               int64_t ldr, int r_transposed, int32_t* __restrict__ perm,
-                                              double* __restrict__ fro2, DevStatus* status) {
+                                              double* __restrict__ fro2, DevStatus* status, int d_transposed = 0,
+                                              int tk_by_col = 0) {
   constexpr int RPT = kMaxL / TPC, NWARP = kMaxL * TPC / 32, CPW = 32 / TPC;   // columns per warp
   // row i of the reflector and of the pivot column lives at i + 4 (i / RPT): the RPT-row
   // pieces that the TPC threads of a column read start in different banks
@@ -1292,7 +1297,7 @@ __device__ __forceinline__ void qrcp_reg_body(const TD* __restrict__ Dg, int64_t
 #pragma unroll
   for (int r = 0; r < RPT; ++r) {
     const int i = i0 + r;
-    d[r] = (c < l && i < l) ? (float)Dg[i * ldd + c] : 0.f;
+    d[r] = (c < l && i < l) ? (float)Dg[d_transposed ? c * ldd + i : i * ldd + c] : 0.f;
   }
   int mypos = c;
   bool trailing = c < l;
@@ -1317,13 +1322,13 @@ __device__ __forceinline__ void qrcp_reg_body(const TD* __restrict__ Dg, int64_t
     float ss = s0 + s1;
 #pragma unroll
     for (int o = 1; o < TPC; o <<= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-    publish(ss);
+    if constexpr (PIVOT) publish(ss);
   }
   __syncthreads();
   for (int j = 0; j < l; ++j) {
     // ---- phase 1: warp 0 reduces the warps' candidates to the pivot (first maximum by current
     // position); the column at position j takes the pivot's old position
-    if (warp == 0) {
+    if (PIVOT && warp == 0) {
       float bn = (lane < NWARP) ? cnrm[lane] : -1.f;
       int bp = (lane < NWARP) ? cpos[lane] : 0x7fffffff;
       int bc = (lane < NWARP) ? ccol[lane] : 0;
@@ -1336,8 +1341,8 @@ __device__ __forceinline__ void qrcp_reg_body(const TD* __restrict__ Dg, int64_t
       }
       if (lane == 0) { piv[0] = bc; piv[2] = bp; }
     }
-    __syncthreads();
-    const int cp = piv[0];
+    if constexpr (PIVOT) __syncthreads();
+    const int cp = PIVOT ? piv[0] : j;
     if (c == cp) mypos = j;
     else if (mypos == j) mypos = piv[2];
     // ---- phase 2: the pivot column's warp builds the reflector from a shared copy of the column
@@ -1488,7 +1493,7 @@ __device__ __forceinline__ void qrcp_reg_body(const TD* __restrict__ Dg, int64_t
       if (r_transposed) St[posof * SL + i] = val;
       else St[i * SL + posof] = val;
       acc_sq(val, fa, fae);
-      if (i < k) acc_sq(val, fb, fbe);
+      if ((tk_by_col ? posof : i) < k) acc_sq(val, fb, fbe);
     }
   }
   for (int o = 16; o > 0; o >>= 1) {
@@ -1521,12 +1526,14 @@ __device__ __forceinline__ void qrcp_reg_body(const TD* __restrict__ Dg, int64_t
   }
 }
 
-template <int TPC, typename TD, typename TQ>
+template <int TPC, typename TD, typename TQ, bool PIVOT = true>
 __global__ void __launch_bounds__(kMaxL * TPC) qrcp_reg_kernel(const TD* __restrict__ Dg, int64_t ldd, int l, int k,
                                                        TQ* __restrict__ Qg, int64_t ldq, double* __restrict__ Rg,
                                                        int64_t ldr, int r_transposed, int32_t* __restrict__ perm,
-                                                       double* __restrict__ fro2, DevStatus* status) {
-  qrcp_reg_body<TPC, TD, TQ>(Dg, ldd, l, k, Qg, ldq, Rg, ldr, r_transposed, perm, fro2, status);
+                                                       double* __restrict__ fro2, DevStatus* status,
+                                                       int d_transposed, int tk_by_col) {
+  qrcp_reg_body<TPC, TD, TQ, PIVOT>(Dg, ldd, l, k, Qg, ldq, Rg, ldr, r_transposed, perm, fro2, status, d_transposed,
+                                    tk_by_col);
 }
 
 template <typename TC>
@@ -1538,7 +1545,7 @@ cudaError_t launch_qrcp(const TC* D, int64_t ldd, int l, int k, TC* Q, int64_t l
     if (e != cudaSuccess) return e;
     qrcp_reg_kernel<kQrcpTPC, float, float><<<1, kMaxL * kQrcpTPC, kQrcpSmem, st>>>(D, ldd, l, k, Q, ldq, R, ldr,
                                                                                     r_transposed ? 1 : 0, perm, fro2,
-                                                                                    status);
+                                                                                    status, 0, 0);
     CORUTV_COUNT_LAUNCH();
     return cudaGetLastError();
   } else {
@@ -1551,6 +1558,36 @@ cudaError_t launch_qrcp(const TC* D, int64_t ldd, int l, int k, TC* Q, int64_t l
   }
 }
 
+// Second half of the QLP of the core: an unpivoted QR of R~^T, R~^T = Qh Rh.  R (FP64,
+// l x l, ld ldr) holds R~ on entry and receives L = Rh^T (to_lower, the URV side) or Rh
+// (the ULV side); Qh (FP32, l x l, ld l).  status->fro2_T / fro2_Tk are refreshed
+// (||L||_F^2 = ||R~||_F^2; the rank-k part is L(1:k, 1:k)).
+cudaError_t launch_qlp_second(double* R, int64_t ldr, int l, int k, float* Qh, bool to_lower, int32_t* perm_scratch,
+                              DevStatus* status, cudaStream_t st) {
+  static bool attr_set[kAttrDevices] = {};
+  cudaError_t e = raise_smem_once(qrcp_reg_kernel<kQrcpTPC, double, float, false>, kQrcpSmem, attr_set);
+  if (e != cudaSuccess) return e;
+  qrcp_reg_kernel<kQrcpTPC, double, float, false><<<1, kMaxL * kQrcpTPC, kQrcpSmem, st>>>(
+      R, ldr, l, k, Qh, l, R, ldr, to_lower ? 1 : 0, perm_scratch, nullptr, status, 1, to_lower ? 1 : 0);
+  CORUTV_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
+
+// S = P~ Qh: S[perm[j]][c] = Qh[j][c] (l x l, ld l)
+__global__ void perm_rows_kernel(const float* __restrict__ Qh, const int32_t* __restrict__ perm, int l,
+                                 float* __restrict__ S) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < l * l; e += gridDim.x * blockDim.x) {
+    const int j = e / l, c = e % l;
+    S[perm[j] * l + c] = Qh[j * l + c];
+  }
+}
+
+cudaError_t launch_perm_rows(const float* Qh, const int32_t* perm, int l, float* S, cudaStream_t st) {
+  perm_rows_kernel<<<(l * l + 255) / 256, 256, 0, st>>>(Qh, perm, l, S);
+  CORUTV_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
+
 template <typename TC>
 cudaError_t launch_qrcp_f64io(const double* D, int64_t ldd, int l, int k, double* Q, int64_t ldq, double* R,
                               int64_t ldr, int32_t* perm, double* fro2, cudaStream_t st) {
@@ -1559,7 +1596,7 @@ cudaError_t launch_qrcp_f64io(const double* D, int64_t ldd, int l, int k, double
     cudaError_t e = raise_smem_once(qrcp_reg_kernel<kQrcpTPC, double, double>, kQrcpSmem, attr_set);
     if (e != cudaSuccess) return e;
     qrcp_reg_kernel<kQrcpTPC, double, double><<<1, kMaxL * kQrcpTPC, kQrcpSmem, st>>>(D, ldd, l, k, Q, ldq, R, ldr, 0,
-                                                                                      perm, fro2, nullptr);
+                                                                                      perm, fro2, nullptr, 0, 0);
     CORUTV_COUNT_LAUNCH();
     return cudaGetLastError();
   } else {
