@@ -266,16 +266,22 @@ int run_pass(corutv_handle* h, int dir, int a_dtype, int mma, const void* A, int
 // again).  R_out (may be null): the product R = R_3 R_2 R_1 with C = Q R (FP64,
 // ld l); it uses the D and Qt scratch blocks, free outside a solve.
 // round_out (FP32, may be null): the last pass also writes Q rounded to TF32 (ld ldr), the
-// operand of the next TF32 pass.
+// operand of the next TF32 pass.  tc_gram: the sketches come from tensor-core passes (TF32 or
+// BF16 products, relative errors >= 2^-17), so the shifted first pass may form its Gram from the
+// 3xTF32 tensor-core partials (~1e-6); every other Gram uses FP32 products.
 template <typename TC>
 int orth_st(corutv_handle* h, TC* Ct, int64_t ldc, int64_t len, int l, const Plan& pl, int passes, double* Rout,
-            float* round_out = nullptr, int64_t ldr = 0) {
+            float* round_out = nullptr, int64_t ldr = 0, bool tc_gram = false) {
   const bool f64 = sizeof(TC) == 8;
   PhaseTimer tm(h, kPhOrth);
   for (int pass = 0; pass < passes; ++pass) {
-    CU((launch_gram<TC, TC>(Ct, ldc, Ct, ldc, len, l, static_cast<TC*>(pl.gram_parts), gram_parts(len, h->sms),
-                           static_cast<TC*>(pl.G),
-                       kMaxL, h->stream)));
+    // Only the shifted first pass may take the tensor-core Gram: its shift (kShiftRel32 trace(G))
+    // dominates the 3xTF32 error, so R stays well defined.  The unshifted passes factor the Gram
+    // of an already-processed basis whose smallest eigenvalues reach ~1e-7 of the largest once the
+    // power steps have sharpened the spectrum; there the tensor core's accumulation error is of the
+    // same size and would spoil R (and with it the range), so those Grams use FP32 products.
+    CU((launch_gram_auto<TC, TC>(Ct, ldc, Ct, ldc, len, l, static_cast<TC*>(pl.gram_parts), h->sms, pl.status,
+                                 static_cast<TC*>(pl.G), kMaxL, h->stream, tc_gram && pass == 0)));
     const double shift = pass == 0 ? (f64 ? kShiftRel64 : kShiftRel32) : 0.0;
     const double tol = f64 ? kTolRel64 : kTolRel32;
     int* skip = (!f64 && passes == 3 && pass == 2) ? &pl.status->orth_skip : nullptr;
@@ -321,10 +327,13 @@ int solve_impl(corutv_handle* h, const corutv_params* p, const Plan& pl, const v
   CU(cudaMemsetAsync(pl.status, 0, sizeof(DevStatus), h->stream));
   // TF32 passes over A: the producers of each sketch operand (the staging of Psi, the last
   // CholeskyQR pass) also write its TF32-rounded copy into Xr for the next pass
-  const bool pre_round = sizeof(TC) == 4 &&
-                         pick_mma(p->a_dtype, p->mma, tma_rows_ok(A, lda, p->a_dtype)) == CORUTV_MMA_TF32;
+  const int eng = pick_mma(p->a_dtype, p->mma, tma_rows_ok(A, lda, p->a_dtype));
+  const bool pre_round = sizeof(TC) == 4 && eng == CORUTV_MMA_TF32;
   float* Xr = static_cast<float*>(pl.Xr);
   float* Xr_out = pre_round ? Xr : nullptr;
+  // Gram engine: the 3xTF32 tensor-core partials where the passes themselves run on the tensor cores
+  const bool tc_gram = sizeof(TC) == 4 && (eng == CORUTV_MMA_TF32 || eng == CORUTV_MMA_TF32_TRUNC ||
+                                           eng == CORUTV_MMA_BF16X2);
   {
     // S0: stage Psi^T into P2 (the "X" of the first product)
     PhaseTimer tm(h, kPhAsm);
@@ -344,7 +353,7 @@ int solve_impl(corutv_handle* h, const corutv_params* p, const Plan& pl, const v
     if (rc) return rc;
     ++passes;
     // S2: orth(C1)
-    rc = orth_st<TC>(h, P1, pl.ld1, pl.len1, l, pl, orth_passes(p, it), nullptr, Xr_out, pl.ldr);
+    rc = orth_st<TC>(h, P1, pl.ld1, pl.len1, l, pl, orth_passes(p, it), nullptr, Xr_out, pl.ldr, tc_gram);
     if (rc) return rc;
     // S3: C2 = A^T Q1  (Alg. 3 step 4)
     rc = run_pass(h, dir2, p->a_dtype, p->mma, A, lda, p->m, p->n, scales, P1, pl.ld1, l, P2, pl.ld2,
@@ -355,7 +364,7 @@ int solve_impl(corutv_handle* h, const corutv_params* p, const Plan& pl, const v
       CU(cudaMemcpy2DAsync(P3, pl.ld3 * sizeof(TC), P2, pl.ld2 * sizeof(TC), pl.len2 * sizeof(TC), l,
                            cudaMemcpyDeviceToDevice, h->stream));
     // S4: orth(C2)
-    rc = orth_st<TC>(h, P2, pl.ld2, pl.len2, l, pl, orth_passes(p, it), nullptr, Xr_out, pl.ldr);
+    rc = orth_st<TC>(h, P2, pl.ld2, pl.len2, l, pl, orth_passes(p, it), nullptr, Xr_out, pl.ldr, tc_gram);
     if (rc) return rc;
   }
   // S5: core D = Q1^T A Q2 (Alg. 2 step 5)
@@ -366,21 +375,21 @@ int solve_impl(corutv_handle* h, const corutv_params* p, const Plan& pl, const v
     if (rc) return rc;
     ++passes;
     PhaseTimer tm(h, kPhCore);
-    CU((launch_gram<TC, TC>(P1, pl.ld1, P3, pl.ld3, pl.len1, l, static_cast<TC*>(pl.gram_parts),
-                           gram_parts(pl.len1, h->sms), static_cast<TC*>(pl.D), kMaxL, h->stream)));   // D = Q1^T E
+    CU((launch_gram_auto<TC, TC>(P1, pl.ld1, P3, pl.ld3, pl.len1, l, static_cast<TC*>(pl.gram_parts),
+                           h->sms, pl.status, static_cast<TC*>(pl.D), kMaxL, h->stream, tc_gram)));   // D = Q1^T E
   } else if (p->core == CORUTV_CORE_EXACT) {
     int rc = run_pass(h, dir1, p->a_dtype, p->mma, A, lda, p->m, p->n, scales, P2, pl.ld2, l, P3, pl.ld3,
                       pl.partials, Xr, pl.ldr, nullptr, kPhPass, pre_round);   // E = A Q2 (ST, len1)
     if (rc) return rc;
     ++passes;
     PhaseTimer tm(h, kPhCore);
-    CU((launch_gram<TC, TC>(P1, pl.ld1, P3, pl.ld3, pl.len1, l, static_cast<TC*>(pl.gram_parts),
-                           gram_parts(pl.len1, h->sms), static_cast<TC*>(pl.D), kMaxL, h->stream)));   // D = Q1^T E
+    CU((launch_gram_auto<TC, TC>(P1, pl.ld1, P3, pl.ld3, pl.len1, l, static_cast<TC*>(pl.gram_parts),
+                           h->sms, pl.status, static_cast<TC*>(pl.D), kMaxL, h->stream, tc_gram)));   // D = Q1^T E
   } else {
     PhaseTimer tm(h, kPhCore);
     // D = Q1^T A Q2 = (A^T Q1)^T Q2 = C2^T Q2 with the saved C2 (ST, len2)
-    CU((launch_gram<TC, TC>(P3, pl.ld3, P2, pl.ld2, pl.len2, l, static_cast<TC*>(pl.gram_parts),
-                           gram_parts(pl.len2, h->sms), static_cast<TC*>(pl.D), kMaxL, h->stream)));
+    CU((launch_gram_auto<TC, TC>(P3, pl.ld3, P2, pl.ld2, pl.len2, l, static_cast<TC*>(pl.gram_parts),
+                           h->sms, pl.status, static_cast<TC*>(pl.D), kMaxL, h->stream, tc_gram)));
   }
   const bool qlp = p->factor == CORUTV_FACTOR_QLP;
   {
@@ -703,8 +712,8 @@ int corutv_gram(corutv_handle* h, int dtype, const void* Xt, int64_t ldx, const 
     CU((launch_gram<double, double>(static_cast<const double*>(Xt), ldx, static_cast<const double*>(Yt), ldy, len, l,
                                    static_cast<double*>(pl.gram_parts), gram_parts(len, h->sms), G, l, h->stream)));
   else
-    CU((launch_gram<float, double>(static_cast<const float*>(Xt), ldx, static_cast<const float*>(Yt), ldy, len, l,
-                                  static_cast<float*>(pl.gram_parts), gram_parts(len, h->sms), G, l, h->stream)));
+    CU((launch_gram_auto<float, double>(static_cast<const float*>(Xt), ldx, static_cast<const float*>(Yt), ldy, len, l,
+                                  static_cast<float*>(pl.gram_parts), h->sms, pl.status, G, l, h->stream, false)));
   return CORUTV_OK;
 }
 

@@ -78,6 +78,17 @@ template <typename TC, typename TG>
 cudaError_t launch_gram(const TC* Xt, int64_t ldx, const TC* Yt, int64_t ldy, int64_t len, int l, TC* parts,
                         int gparts, TG* G, int64_t ldg, cudaStream_t st);
 int gram_parts(int64_t len, int sms);
+// gram_tc.cu: 3xTF32 tensor-core Gram partials (FP32 ST blocks whose rows TMA can address)
+int gram_tc_parts(int64_t len, int sms);
+bool gram_tc_ok(const float* X, int64_t ldx, const float* Y, int64_t ldy, int l);
+cudaError_t launch_gram_tc_partials(const float* X, int64_t ldx, const float* Y, int64_t ldy, int64_t len, int l,
+                                    float* parts, int sms, DevStatus* status, cudaStream_t st);
+// G = X Y^T choosing the engine: FP32 blocks on the tensor cores (3xTF32 partials, ~1e-6 relative)
+// where TMA can read them and allow_tc, else the CUDA-core FP32 partials (~u32); then the ordered
+// reduction.  parts holds at least gram_parts(len, sms) blocks of 128 x 128 TC.
+template <typename TC, typename TG>
+cudaError_t launch_gram_auto(const TC* Xt, int64_t ldx, const TC* Yt, int64_t ldy, int64_t len, int l, TC* parts,
+                             int sms, DevStatus* status, TG* G, int64_t ldg, cudaStream_t st, bool allow_tc);
 constexpr int kRedWarps = 8;   // Gram reduction: warps per CTA; a CTA reduces 32 consecutive elements
 // skip_flag (FP32 only, may be null): skip the factorisation when max |G - I| <= skip_tol
 // (writes *skip_flag = 1 and R_out = I); launch_lmul with the same flag then does nothing

@@ -232,6 +232,22 @@ cudaError_t launch_gram(const TC* Xt, int64_t ldx, const TC* Yt, int64_t ldy, in
   return cudaGetLastError();
 }
 
+template <typename TC, typename TG>
+cudaError_t launch_gram_auto(const TC* Xt, int64_t ldx, const TC* Yt, int64_t ldy, int64_t len, int l, TC* parts,
+                             int sms, DevStatus* status, TG* G, int64_t ldg, cudaStream_t st, bool allow_tc) {
+  if constexpr (sizeof(TC) == 4) {
+    if (allow_tc && gram_tc_ok(Xt, ldx, Yt, ldy, l)) {
+      cudaError_t e = launch_gram_tc_partials(Xt, ldx, Yt, ldy, len, l, parts, sms, status, st);
+      if (e != cudaSuccess) return e;
+      gram_reduce_kernel<TC, TG><<<(unsigned)cdiv((int64_t)l * l, 32), kRedWarps * 32, 0, st>>>(
+          parts, gram_tc_parts(len, sms), 128, l, G, ldg);
+      CORUTV_COUNT_LAUNCH();
+      return cudaGetLastError();
+    }
+  }
+  return launch_gram<TC, TG>(Xt, ldx, Yt, ldy, len, l, parts, gram_parts(len, sms), G, ldg, st);
+}
+
 // =============================================================================== Cholesky
 // G + s I = R^T R (R upper, s = shift_rel * trace(G)) and R^-1, by symmetric
 // elimination of [G | I]: step j subtracts m_a = G[j][a] / G[j][j] times row j
@@ -1951,6 +1967,13 @@ cudaError_t launch_fro2_grouped(const BatchProb* P, int count, cudaStream_t st) 
 INST(float)
 INST(double)
 #undef INST
+template cudaError_t launch_gram_auto<float, float>(const float*, int64_t, const float*, int64_t, int64_t, int, float*,
+                                                   int, DevStatus*, float*, int64_t, cudaStream_t, bool);
+template cudaError_t launch_gram_auto<float, double>(const float*, int64_t, const float*, int64_t, int64_t, int,
+                                                    float*, int, DevStatus*, double*, int64_t, cudaStream_t, bool);
+template cudaError_t launch_gram_auto<double, double>(const double*, int64_t, const double*, int64_t, int64_t, int,
+                                                     double*, int, DevStatus*, double*, int64_t, cudaStream_t,
+                                                     bool);
 template cudaError_t launch_gram<float, double>(const float*, int64_t, const float*, int64_t, int64_t, int, float*,
                                                  int, double*, int64_t, cudaStream_t);
 
