@@ -13,6 +13,9 @@ Workloads (--workload):
   rpca            ALM-CoRUTV robust PCA (Alg. 5) of the Sec. VI-C synthetic
                   2000 x 2000 matrix (--n 1000 for the other Table I size):
                   time of one whole run to the stopping rule.
+  host            the fp32 solve with A in page-locked host memory
+                  (corutv_solve_host): every one of the 2q+3 passes streams A
+                  to the GPU in row chunks (--chunk rows, 0 = ~256 MiB).
 
 Step = one whole solve: (quantisation,) Psi staging, every streaming pass over
 A, shifted CholeskyQR3 of every sketch, the core reduction, QRCP of D,
@@ -47,6 +50,8 @@ WORKLOADS = {
     # ALM-CoRUTV robust PCA (Alg. 5) on the Sec. VI-C synthetic data: n x n, rank 0.05 n, 5% +-80 spikes,
     # l = rank + 2, q = 1 (Table I row n = 2000)
     "rpca": dict(n=2000, sparse=0.05, q=1, dtype="f32", gen="rpca"),
+    # the fp32 solve with A left in page-locked HOST memory: every pass streams it over C2C
+    "host": dict(m=20000, n=20000, k=100, l=120, q=1, dtype="f32", gen="config2", host=True),
 }
 # the paper's ALM-CoRUTV times (Table I, seconds, MATLAB on a 4-core i5-4430): context, not a target
 PAPER_RPCA_S = {(1000, 0.05): 0.6, (2000, 0.05): 3.7, (1000, 0.10): 0.7, (2000, 0.10): 4.1}
@@ -67,6 +72,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--sparse", type=float, default=None)
+    ap.add_argument("--chunk", type=int, default=0)
     args = ap.parse_args()
     w = dict(WORKLOADS[args.workload])
     for key in ("m", "n", "q"):
@@ -89,6 +95,8 @@ def workload_label(w, core):
                 f"one batched call per step")
     if w["gen"] == "config2":
         a = f"{w['m']}x{w['n']} FP32 A = G1 diag(i^-1.5) G2^T + 1e-8 noise"
+        if w.get("host"):
+            a += " in page-locked host memory, streamed to the GPU in row chunks every pass"
     else:
         store = "BF16" if w["dtype"] == "bf16" else "FP8 e4m3 (128x128 tile scales)"
         a = (f"{w['m']}x{w['n']} A = G1 diag(exp(-i/30)) G2^T + 1e-8 noise stored {store}, "
@@ -175,6 +183,29 @@ def measured_peaks() -> dict:
             return json.load(f)
     except OSError:
         return {}
+
+
+def h2d_copy_gbs(nbytes: int = 1 << 30) -> float:
+    """Bandwidth of one plain page-locked host -> device cudaMemcpyAsync of nbytes,
+    timed with CUDA events (best of 5 after 2 warm-ups): the ceiling of a pass over a
+    host-resident A."""
+    import torch
+    src = torch.empty(nbytes // 4, dtype=torch.float32, pin_memory=True)
+    src.fill_(1.0)
+    dst = torch.empty(nbytes // 4, dtype=torch.float32, device="cuda")
+    for _ in range(2):
+        dst.copy_(src, non_blocking=True)
+    torch.cuda.synchronize()
+    best = 0.0
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        dst.copy_(src, non_blocking=True)
+        e1.record()
+        torch.cuda.synchronize()
+        best = max(best, nbytes / (e0.elapsed_time(e1) / 1e3) / 1e9)
+    del src, dst
+    return best
 
 
 def traffic_from_profiles(key: str):
@@ -799,8 +830,16 @@ def main():
         S = torch.empty((-(-m // 128), -(-n // 128)), dtype=torch.float32, device=dev) \
             if w["dtype"] == "fp8" else None
 
+    hosted = bool(w.get("host"))
+    if hosted:
+        A_host = torch.empty((m, n), dtype=torch.float32, pin_memory=True)
+        A_host.copy_(A)
+
     def solve_on(A32, P32):
-        if lowp:
+        if hosted:
+            corutv.solve_host(A_host, P32, k, l, q, core=args.core, mma=args.mma, want_fro2=True,
+                              chunk_rows=args.chunk, out=(U, T, V, perm), wait=False, handle=h)
+        elif lowp:
             corutv.quantize(A32, w["dtype"], out=A_lp, tile_scales=S, handle=h)
             corutv.solve(A_lp, P32, k, l, q, core=args.core, mma=args.mma, a_tile_scales=S, want_fro2=True,
                          out=(U, T, V, perm), wait=False, handle=h, A_ref=A32)
@@ -857,6 +896,18 @@ def main():
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_source": peak_src, "kernel": kname, "bytes_per_launch": bytes_per_pass,
                 "ms_per_launch": avg_pass_ms, "traffic": traffic_from_profiles(tkey)}
+    if hosted:
+        # the bound is the host -> device link: A crosses it once per pass
+        c2c = h2d_copy_gbs()
+        a_bytes = info.passes_over_A * m * n * 4
+        ach = a_bytes / (ms_per_step / 1e3) / 1e9
+        roofline = {"bound": "c2c", "achieved": ach, "peak": c2c, "unit": "GB/s", "frac": ach / c2c,
+                    "peak_source": "measured in this run: one 1 GiB page-locked host-to-device cudaMemcpyAsync",
+                    "kernel": "whole step: %d streamed passes of A (%d x %d FP32) per solve" % (
+                        info.passes_over_A, m, n),
+                    "bytes_per_launch": a_bytes, "ms_per_launch": ms_per_step, "traffic": None,
+                    "pass_kernels": {"ms_per_step": tr.pass_ms / args.steps,
+                                     "hbm_gbs_while_running": achieved}}
     if lowp and tr.corr_launches:
         corr_ms = tr.corr_ms / tr.corr_launches
         roofline["correction_pass"] = {"ms_per_launch": corr_ms,
@@ -876,8 +927,9 @@ def main():
     # ------------------------------------------------------------ e2e through the public API
     e2e = None
     if not args.no_e2e:
-        A_h = torch.empty((m, n), dtype=torch.float32, pin_memory=True)
-        A_h.copy_(A)
+        A_h = A_host if hosted else torch.empty((m, n), dtype=torch.float32, pin_memory=True)
+        if not hosted:
+            A_h.copy_(A)
         phi_h = torch.empty((n, l), dtype=torch.float32, pin_memory=True)
         phi_h.copy_(phi)
         U_h = torch.empty((m, l), dtype=torch.float32, pin_memory=True)
@@ -889,7 +941,8 @@ def main():
         e2e_steps = max(1, min(args.steps, 5))
 
         def e2e_step():
-            A_d.copy_(A_h, non_blocking=True)
+            if not hosted:
+                A_d.copy_(A_h, non_blocking=True)
             phi_d.copy_(phi_h, non_blocking=True)
             solve_on(A_d, phi_d)
             U_h.copy_(U, non_blocking=True)
@@ -907,7 +960,7 @@ def main():
         f1.record(stream)
         torch.cuda.synchronize()
         ms_e2e = max_over_ranks(f0.elapsed_time(f1), world)
-        h2d = (m * n + n * l) * 4
+        h2d = (m * n * (info.passes_over_A if hosted else 1) + n * l) * 4
         d2h = (m + n) * l * 4 + l * l * 8 + l * 4
         e2e = {"value": world * e2e_steps / (ms_e2e / 1e3), "unit": "solves/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "steps": e2e_steps}
@@ -935,6 +988,7 @@ def main():
                           "m": m, "n": n, "k": k, "l": l, "q": q, "core": args.core, "mma": args.mma,
                           "passes_per_step": info.passes_over_A,
                           "l2": "inputs larger than L2 (A is %.1f GB)" % (m * n * 4 / 1e9),
+                          "a_resident": "host (page-locked), streamed every pass" if hosted else "HBM",
                           "parallelism": f"replicas x{world}"},
                "roofline": roofline,
                "cpu_baseline": cpu,

@@ -39,7 +39,7 @@
 extern "C" {
 #endif
 
-#define CORUTV_ABI_VERSION 3
+#define CORUTV_ABI_VERSION 4
 
 typedef enum {
   CORUTV_OK = 0,
@@ -186,6 +186,30 @@ int corutv_solve(corutv_handle* h, const corutv_params* p,
                  const void* Phi, int64_t ldphi,
                  void* U, int64_t ldu, double* T, int64_t ldt,
                  void* V, int64_t ldv, int32_t* perm);
+
+/*
+ * corutv_solve_host -- corutv_solve for an A that stays in HOST memory (Grace LPDDR,
+ * read over NVLink-C2C): the matrix "stored externally" of Sec. I, which the
+ * method reads only 2q + 3 times (Sec. IV-C; 2q + 2 with core = SKETCH).  Every
+ * pass streams A through a ring of three device buffers, chunk_rows rows at a
+ * time: the copy of the next chunks runs on the handle's copy stream while the
+ * pass kernels read the current one, so device memory holds three chunks, the
+ * sketches and the outputs, whatever m.  A X writes each chunk's rows of the
+ * sketch directly; A^T Y sums the chunks' products (one extra l x n add per chunk).
+ *   A        HOST, m x n row-major, lda >= n elements, F32 or F64 (a_dtype; BF16 /
+ *            FP8 return ERR_UNSUPPORTED).  Page-locked memory (cudaHostAlloc /
+ *            cudaHostRegister) gives full C2C bandwidth; pageable memory works but
+ *            each copy is staged by the driver.  The caller keeps A unchanged and
+ *            alive until the solve is complete (corutv_info_wait or a stream sync).
+ *   chunk_rows  rows per chunk, a multiple of 128 (ERR_SHAPE otherwise); 0 picks
+ *            about 256 MiB per chunk.  Clamped to m rounded up to 128.
+ * Phi, U, T, V, perm and the engines as corutv_solve (device); want_fro2 sums
+ * ||A_c||_F^2 over the chunks of the first pass.  The device allocations (ring
+ * and workspace) are made on first use and kept by the handle.
+ */
+int corutv_solve_host(corutv_handle* h, const corutv_params* p, const void* A, int64_t lda, int64_t chunk_rows,
+                      const void* Phi, int64_t ldphi, void* U, int64_t ldu, double* T, int64_t ldt,
+                      void* V, int64_t ldv, int32_t* perm);
 
 /*
  * corutv_solve_corrected -- corutv_solve for A stored in BF16 or FP8 (a_dtype) plus

@@ -92,7 +92,7 @@ EXPORTS = ("corutv_version", "corutv_status_string", "corutv_create", "corutv_de
            "corutv_qrcp", "corutv_fro2", "corutv_gram_noalloc", "corutv_solve_corrected", "corutv_quantize",
            "corutv_batch_workspace_size", "corutv_solve_batched", "corutv_batch_info_wait",
            "corutv_server_create", "corutv_server_submit", "corutv_server_poll", "corutv_server_stats",
-           "corutv_server_destroy", "corutv_rpca")
+           "corutv_server_destroy", "corutv_rpca", "corutv_solve_host")
 
 
 def load() -> ctypes.CDLL:
@@ -115,6 +115,7 @@ def load() -> ctypes.CDLL:
     lib.corutv_solve.argtypes = [P, ctypes.POINTER(Params), P, I64, P, P, I64, P, I64, P, I64, P, I64, P]
     lib.corutv_solve_corrected.argtypes = [P, ctypes.POINTER(Params), P, I64, P, P, I64, P, I64, P, I64, P, I64,
                                            P, I64, P]
+    lib.corutv_solve_host.argtypes = [P, ctypes.POINTER(Params), P, I64, I64, P, I64, P, I64, P, I64, P, I64, P]
     lib.corutv_quantize.argtypes = [P, ctypes.c_int, P, I64, I64, I64, P, I64, P]
     lib.corutv_batch_workspace_size.argtypes = [ctypes.c_int, ctypes.POINTER(Problem), ctypes.POINTER(ctypes.c_size_t)]
     lib.corutv_solve_batched.argtypes = [P, ctypes.c_int, ctypes.POINTER(Problem), ctypes.POINTER(Info)]
@@ -142,7 +143,7 @@ def load() -> ctypes.CDLL:
                  "corutv_orthonormalize", "corutv_gram", "corutv_qrcp", "corutv_fro2", "corutv_solve_corrected",
                  "corutv_quantize", "corutv_batch_workspace_size", "corutv_solve_batched",
                  "corutv_batch_info_wait", "corutv_server_create", "corutv_server_submit", "corutv_server_poll",
-                 "corutv_server_stats", "corutv_server_destroy", "corutv_rpca"):
+                 "corutv_server_stats", "corutv_server_destroy", "corutv_rpca", "corutv_solve_host"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -324,6 +325,47 @@ def solve(A, Phi, k: int, l: int, q: int = 0, side: str = "right", core: str = "
                                            ctypes.c_void_p(sc), ctypes.c_void_p(A_ref.data_ptr()),
                                            _rowmajor_ld(A_ref), *tail)
         _check(rc, "corutv_solve_corrected")
+    info = info_wait(h) if wait else None
+    return SolveResult(U, T, V, perm, info)
+
+
+def solve_host(A, Phi, k: int, l: int, q: int = 0, side: str = "right", core: str = "exact", mma: str = "auto",
+               want_fro2: bool = False, chunk_rows: int = 0, out=None, wait: bool = True,
+               handle: Handle | None = None, orth: str = "stabilised", factor: str = "qrcp"):
+    """CoR-UTV of a HOST matrix A streamed to the GPU pass by pass (corutv_solve_host).
+
+    A: (m, n) row-major float32 / float64 CPU tensor (page-locked, e.g.
+    torch.empty(..., pin_memory=True), for full host-to-device bandwidth); it
+    must stay unchanged until the solve is complete.  Phi and the outputs are
+    device tensors as for solve().  chunk_rows: rows per streamed chunk (a
+    multiple of 128; 0 = about 256 MiB).
+    """
+    import torch
+    if A.is_cuda:
+        raise TypeError("solve_host takes a host (CPU) A; use solve() for a device A")
+    if A.dim() != 2 or A.stride(1) != 1:
+        raise TypeError("A must be a row-major 2-D tensor")
+    _need_cuda(Phi)
+    h = handle or handle_for()
+    m, n = A.shape
+    code = _dt_code(A)
+    fdt = torch.float64 if code == 0 else torch.float32
+    if Phi.dtype != fdt:
+        raise TypeError(f"Phi must be {fdt}")
+    p = _params(m, n, k, l, q, side, core, code, mma, want_fro2, orth, factor)
+    if out is None:
+        dev = Phi.device
+        U = torch.empty((m, l), dtype=fdt, device=dev)
+        T = torch.empty((l, l), dtype=torch.float64, device=dev)
+        V = torch.empty((n, l), dtype=fdt, device=dev)
+        perm = torch.empty((l,), dtype=torch.int32, device=dev)
+    else:
+        U, T, V, perm = out
+    rc = load().corutv_solve_host(h.h, ctypes.byref(p), ctypes.c_void_p(A.data_ptr()), A.stride(0), int(chunk_rows),
+                                  ctypes.c_void_p(Phi.data_ptr()), _rowmajor_ld(Phi), ctypes.c_void_p(U.data_ptr()),
+                                  _rowmajor_ld(U), ctypes.c_void_p(T.data_ptr()), _rowmajor_ld(T),
+                                  ctypes.c_void_p(V.data_ptr()), _rowmajor_ld(V), ctypes.c_void_p(perm.data_ptr()))
+    _check(rc, "corutv_solve_host")
     info = info_wait(h) if wait else None
     return SolveResult(U, T, V, perm, info)
 

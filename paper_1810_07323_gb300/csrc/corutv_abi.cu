@@ -258,6 +258,69 @@ int run_pass(corutv_handle* h, int dir, int a_dtype, int mma, const void* A, int
   return CORUTV_OK;
 }
 
+// A held in host memory (Grace LPDDR, read over NVLink-C2C) instead of HBM: every pass
+// streams it through the handle's ring, one row chunk at a time -- the externally stored
+// matrix of Sec. I that the method reads only 2q + 3 times (Sec. IV-C).
+struct HostSrc {
+  const char* A;            // host, row-major, pitch lda elements
+  int64_t lda;
+  int es;                   // bytes per element
+  int64_t chunk;            // rows per chunk (a multiple of 128)
+  int64_t ldd;              // pitch of a ring buffer (elements; 16-byte rows for TMA)
+  char* buf[HostRing::kBufs];
+  void* acc;                // ATY: the product of one chunk, added into the output
+  double* fro_chunk;        // ||A_c||_F^2 of every chunk (first pass, on request)
+  int64_t seq = 0;          // chunks issued so far: the ring position
+  double h2d_bytes = 0.0;
+};
+
+// One pass over A: resident (run_pass) or streamed chunk by chunk.  For a chunk of rows
+// [r0, r0 + rows): A X gives columns r0.. of the ST output directly; A^T Y takes columns
+// r0.. of the ST operand Y and its product is summed over the chunks.  The copy of chunk
+// c + 1 (and c + 2) runs on the copy stream while the pass reads chunk c.
+template <typename TC>
+int do_pass(corutv_handle* h, HostSrc* hs, const Plan& pl, int dir, int a_dtype, int mma, const void* A, int64_t lda,
+            int64_t m, int64_t n, const float* scales, TC* Xt, int64_t ldx, int l, TC* Ct, int64_t ldc, float* Xr,
+            int64_t ldr, double* fro_parts, int phase, bool x_rounded, bool chunk_fro2 = false) {
+  if (!hs)
+    return run_pass(h, dir, a_dtype, mma, A, lda, m, n, scales, Xt, ldx, l, Ct, ldc, pl.partials, Xr, ldr, fro_parts,
+                    phase, x_rounded);
+  HostRing& R = h->ring;
+  int64_t c = 0;
+  for (int64_t r0 = 0; r0 < m; r0 += hs->chunk, ++c) {
+    const int64_t rows = std::min(hs->chunk, m - r0);
+    const int b = (int)(hs->seq % HostRing::kBufs);
+    if (hs->seq >= HostRing::kBufs) CU(cudaStreamWaitEvent(R.copy, R.freed[b], 0));
+    CU(cudaMemcpy2DAsync(hs->buf[b], (size_t)hs->ldd * hs->es, hs->A + (size_t)r0 * hs->lda * hs->es,
+                         (size_t)hs->lda * hs->es, (size_t)n * hs->es, (size_t)rows, cudaMemcpyHostToDevice, R.copy));
+    CU(cudaEventRecord(R.filled[b], R.copy));
+    CU(cudaStreamWaitEvent(h->stream, R.filled[b], 0));
+    int rc;
+    if (dir == CORUTV_DIR_AX) {
+      rc = run_pass(h, dir, a_dtype, mma, hs->buf[b], hs->ldd, rows, n, nullptr, Xt, ldx, l, Ct + r0, ldc,
+                    pl.partials, Xr, ldr, nullptr, phase, x_rounded);
+    } else {
+      TC* out = r0 == 0 ? Ct : static_cast<TC*>(hs->acc);
+      rc = run_pass(h, dir, a_dtype, mma, hs->buf[b], hs->ldd, rows, n, nullptr, Xt + r0, ldx, l, out, ldc,
+                    pl.partials, Xr ? Xr + r0 : nullptr, ldr, nullptr, phase, x_rounded);
+      if (!rc && r0 > 0) CU(launch_add_st<TC>(static_cast<const TC*>(hs->acc), ldc, l, n, Ct, ldc, h->stream));
+    }
+    if (rc) return rc;
+    if (chunk_fro2)
+      CU(launch_fro2(a_dtype, hs->buf[b], hs->ldd, rows, n, nullptr, 0, pl.fro_parts, pl.fparts, hs->fro_chunk + c,
+                     h->stream));
+    CU(cudaEventRecord(R.freed[b], h->stream));
+    ++hs->seq;
+    hs->h2d_bytes += (double)rows * n * hs->es;
+  }
+  if (chunk_fro2) {
+    sum_parts_kernel<<<1, 32, 0, h->stream>>>(hs->fro_chunk, (int)c, nullptr, pl.status);
+    CORUTV_COUNT_LAUNCH();
+    CU(cudaGetLastError());
+  }
+  return CORUTV_OK;
+}
+
 // Shifted CholeskyQR on an ST block (in place).  passes = 3: shifted
 // CholeskyQR3, Q with orthonormal columns; on the FP32 path the third pass is
 // skipped when the Gram matrix of the second pass's Q is the identity within
@@ -313,7 +376,7 @@ int orth_passes(const corutv_params* p, int it) {
 template <typename TC>
 int solve_impl(corutv_handle* h, const corutv_params* p, const Plan& pl, const void* A, int64_t lda,
                const float* scales, const float* A_ref, int64_t lda_ref, const void* Phi, int64_t ldphi, void* U,
-               int64_t ldu, double* T, int64_t ldt, void* V, int64_t ldv, int32_t* perm) {
+               int64_t ldu, double* T, int64_t ldt, void* V, int64_t ldv, int32_t* perm, HostSrc* hs = nullptr) {
   const bool right = p->side == CORUTV_SIDE_RIGHT;
   const int l = p->l;
   // RIGHT: first product A X (dir AX), second A^T Q1 (dir ATY); LEFT: swapped.
@@ -343,21 +406,21 @@ int solve_impl(corutv_handle* h, const corutv_params* p, const Plan& pl, const v
   // S9: ||A||_F^2 fused into the first pass where the tensor-core engine runs it
   const int ref_mma = p->mma == CORUTV_MMA_SIMT ? CORUTV_MMA_SIMT : CORUTV_MMA_AUTO;
   const bool fuse_fro2 =
-      p->want_fro2 && (A_ref ? pick_mma(CORUTV_F32, ref_mma, tma_rows_ok(A_ref, lda_ref, CORUTV_F32))
+      !hs && p->want_fro2 && (A_ref ? pick_mma(CORUTV_F32, ref_mma, tma_rows_ok(A_ref, lda_ref, CORUTV_F32))
                              : pick_mma(p->a_dtype, p->mma, tma_rows_ok(A, lda, p->a_dtype))) != CORUTV_MMA_SIMT;
   for (int it = 0; it <= p->q; ++it) {
     // S1: C1 = A X  (Alg. 3 step 3)
-    int rc = run_pass(h, dir1, p->a_dtype, p->mma, A, lda, p->m, p->n, scales, P2, pl.ld2, l, P1, pl.ld1,
-                      pl.partials, Xr, pl.ldr, (it == 0 && fuse_fro2 && !A_ref) ? pl.fro_parts : nullptr, kPhPass,
-                      pre_round);
+    int rc = do_pass<TC>(h, hs, pl, dir1, p->a_dtype, p->mma, A, lda, p->m, p->n, scales, P2, pl.ld2, l, P1,
+                         pl.ld1, Xr, pl.ldr, (it == 0 && fuse_fro2 && !A_ref) ? pl.fro_parts : nullptr, kPhPass,
+                         pre_round, hs && it == 0 && p->want_fro2);
     if (rc) return rc;
     ++passes;
     // S2: orth(C1)
     rc = orth_st<TC>(h, P1, pl.ld1, pl.len1, l, pl, orth_passes(p, it), nullptr, Xr_out, pl.ldr, tc_gram);
     if (rc) return rc;
     // S3: C2 = A^T Q1  (Alg. 3 step 4)
-    rc = run_pass(h, dir2, p->a_dtype, p->mma, A, lda, p->m, p->n, scales, P1, pl.ld1, l, P2, pl.ld2,
-                  pl.partials, Xr, pl.ldr, nullptr, kPhPass, pre_round);
+    rc = do_pass<TC>(h, hs, pl, dir2, p->a_dtype, p->mma, A, lda, p->m, p->n, scales, P1, pl.ld1, l, P2, pl.ld2,
+                     Xr, pl.ldr, nullptr, kPhPass, pre_round);
     if (rc) return rc;
     ++passes;
     if (it == p->q && p->core == CORUTV_CORE_SKETCH)
@@ -378,8 +441,8 @@ int solve_impl(corutv_handle* h, const corutv_params* p, const Plan& pl, const v
     CU((launch_gram_auto<TC, TC>(P1, pl.ld1, P3, pl.ld3, pl.len1, l, static_cast<TC*>(pl.gram_parts),
                            h->sms, pl.status, static_cast<TC*>(pl.D), kMaxL, h->stream, tc_gram)));   // D = Q1^T E
   } else if (p->core == CORUTV_CORE_EXACT) {
-    int rc = run_pass(h, dir1, p->a_dtype, p->mma, A, lda, p->m, p->n, scales, P2, pl.ld2, l, P3, pl.ld3,
-                      pl.partials, Xr, pl.ldr, nullptr, kPhPass, pre_round);   // E = A Q2 (ST, len1)
+    int rc = do_pass<TC>(h, hs, pl, dir1, p->a_dtype, p->mma, A, lda, p->m, p->n, scales, P2, pl.ld2, l, P3,
+                         pl.ld3, Xr, pl.ldr, nullptr, kPhPass, pre_round);   // E = A Q2 (ST, len1)
     if (rc) return rc;
     ++passes;
     PhaseTimer tm(h, kPhCore);
@@ -419,7 +482,7 @@ int solve_impl(corutv_handle* h, const corutv_params* p, const Plan& pl, const v
   else
     CU(launch_gather_cols<TC>(P2, pl.ld2, pl.len2, l, perm, out2, ld2o, h->stream));
   // S9: ||A||_F^2 on request
-  if (p->want_fro2 && !fuse_fro2) {
+  if (p->want_fro2 && !fuse_fro2 && !hs) {
     const int fdt = A_ref ? CORUTV_F32 : p->a_dtype;
     PhaseTimer tm(h, kPhFro2, (double)p->m * p->n * elem_bytes(fdt));
     CU(launch_fro2(fdt, A_ref ? static_cast<const void*>(A_ref) : A, A_ref ? lda_ref : lda, p->m, p->n,
@@ -432,7 +495,49 @@ int solve_impl(corutv_handle* h, const corutv_params* p, const Plan& pl, const v
   return CORUTV_OK;
 }
 
+constexpr int64_t kRingChunkBytes = 256ll << 20;   // default chunk of a host-streamed A
+
+int ensure_ring(corutv_handle* h, size_t need) {
+  HostRing& R = h->ring;
+  if (!R.copy) {
+    if (cudaStreamCreateWithFlags(&R.copy, cudaStreamNonBlocking) != cudaSuccess) return CORUTV_ERR_CUDA;
+    for (int b = 0; b < HostRing::kBufs; ++b)
+      if (cudaEventCreateWithFlags(&R.filled[b], cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&R.freed[b], cudaEventDisableTiming) != cudaSuccess)
+        return CORUTV_ERR_CUDA;
+    if (cudaEventCreateWithFlags(&R.start, cudaEventDisableTiming) != cudaSuccess) return CORUTV_ERR_CUDA;
+  }
+  if (R.mem && R.bytes >= need) return CORUTV_OK;
+  if (R.mem) {
+    cudaStreamSynchronize(h->stream);
+    cudaStreamSynchronize(R.copy);
+    cudaFree(R.mem);
+    R.mem = nullptr;
+    R.bytes = 0;
+  }
+  if (cudaMalloc(&R.mem, need) != cudaSuccess) {
+    cudaGetLastError();
+    R.mem = nullptr;
+    return CORUTV_ERR_OOM;
+  }
+  R.bytes = need;
+  return CORUTV_OK;
+}
+
 }  // namespace
+
+void ring_free(corutv_handle* h) {
+  HostRing& R = h->ring;
+  if (R.copy) cudaStreamSynchronize(R.copy);
+  if (R.mem) cudaFree(R.mem);
+  for (int b = 0; b < HostRing::kBufs; ++b) {
+    if (R.filled[b]) cudaEventDestroy(R.filled[b]);
+    if (R.freed[b]) cudaEventDestroy(R.freed[b]);
+  }
+  if (R.start) cudaEventDestroy(R.start);
+  if (R.copy) cudaStreamDestroy(R.copy);
+  R = HostRing{};
+}
 
 // =============================================================================== exported
 extern "C" {
@@ -481,6 +586,7 @@ int corutv_destroy(corutv_handle* h) {
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   batch_state_free(h->batch);
   rpca_free(h);
+  ring_free(h);
   delete h;
   return CORUTV_OK;
 }
@@ -565,6 +671,63 @@ int corutv_solve_corrected(corutv_handle* h, const corutv_params* p, const void*
   if (p->a_dtype != CORUTV_BF16 && p->a_dtype != CORUTV_FP8_E4M3) return CORUTV_ERR_INVALID_ARG;
   if (p->core != CORUTV_CORE_EXACT) return CORUTV_ERR_INVALID_ARG;
   return solve_common(h, p, A, lda, a_tile_scales, A_ref, lda_ref, Phi, ldphi, U, ldu, T, ldt, V, ldv, perm);
+}
+
+int corutv_solve_host(corutv_handle* h, const corutv_params* p, const void* A, int64_t lda, int64_t chunk_rows,
+                      const void* Phi, int64_t ldphi, void* U, int64_t ldu, double* T, int64_t ldt, void* V,
+                      int64_t ldv, int32_t* perm) {
+  if (!h) return CORUTV_ERR_INVALID_ARG;
+  int rc = check_params(p);
+  if (rc) return rc;
+  if (p->a_dtype != CORUTV_F32 && p->a_dtype != CORUTV_F64) return CORUTV_ERR_UNSUPPORTED;
+  if (!A || !Phi || !U || !T || !V || !perm) return CORUTV_ERR_INVALID_ARG;
+  const int l = p->l;
+  if (lda < p->n || ldphi < l || ldu < l || ldt < l || ldv < l) return CORUTV_ERR_SHAPE;
+  if (chunk_rows < 0 || chunk_rows % 128) return CORUTV_ERR_SHAPE;
+  const int es = elem_bytes(p->a_dtype);
+  const int64_t ldd = round_up(p->n, 16 / es);   // 16-byte rows: TMA reads the ring buffers
+  int64_t chunk = chunk_rows;
+  if (chunk == 0) chunk = std::max<int64_t>(128, kRingChunkBytes / (ldd * es) / 128 * 128);
+  chunk = std::min(chunk, round_up(p->m, 128));
+  const int64_t nchunks = cdiv(p->m, chunk);
+  Plan pl{};
+  make_plan(p, h->sms, pl);
+  pl.pass_partials = std::max(pl.pass_partials, pass_partial_bytes(chunk, p->n, l, p->a_dtype, h->sms));
+  rc = ensure_workspace(h, plan_layout(pl, nullptr));
+  if (rc) return rc;
+  plan_layout(pl, h->ws);
+  // the ring: kBufs chunk buffers, the accumulator of the A^T Y products, one double per chunk
+  const size_t buf_bytes = (size_t)round_up(chunk * ldd * es, kAlign);
+  const size_t acc_bytes = (size_t)round_up((int64_t)kMaxL * pl.ld3 * tc_bytes(p->a_dtype), kAlign);
+  rc = ensure_ring(h, HostRing::kBufs * buf_bytes + acc_bytes + sizeof(double) * nchunks);
+  if (rc) return rc;
+  HostRing& R = h->ring;
+  HostSrc hs{};
+  hs.A = static_cast<const char*>(A);
+  hs.lda = lda;
+  hs.es = es;
+  hs.chunk = chunk;
+  hs.ldd = ldd;
+  for (int b = 0; b < HostRing::kBufs; ++b) hs.buf[b] = static_cast<char*>(R.mem) + b * buf_bytes;
+  hs.acc = static_cast<char*>(R.mem) + HostRing::kBufs * buf_bytes;
+  hs.fro_chunk = reinterpret_cast<double*>(static_cast<char*>(hs.acc) + acc_bytes);
+  h->status = pl.status;
+  h->last = *p;
+  h->have_last = true;
+  // the copies of this solve wait for the work already on the solve's stream: an earlier
+  // solve may still be reading the ring
+  CU(cudaEventRecord(R.start, h->stream));
+  CU(cudaStreamWaitEvent(R.copy, R.start, 0));
+  const int64_t l0 = launch_counter();
+  if (p->a_dtype == CORUTV_F64)
+    rc = solve_impl<double>(h, p, pl, hs.buf[0], ldd, nullptr, nullptr, 0, Phi, ldphi, U, ldu, T, ldt, V, ldv, perm,
+                            &hs);
+  else
+    rc = solve_impl<float>(h, p, pl, hs.buf[0], ldd, nullptr, nullptr, 0, Phi, ldphi, U, ldu, T, ldt, V, ldv, perm,
+                           &hs);
+  h->launches += launch_counter() - l0;
+  if (h->tracing) h->acc.solves += 1;
+  return rc;
 }
 
 int corutv_quantize(corutv_handle* h, int dtype, const float* A, int64_t lda, int64_t m, int64_t n, void* out,

@@ -20,6 +20,17 @@ struct TraceRec {
   double bytes;
 };
 
+// Ring of device buffers through which corutv_solve_host streams a host-resident A, one
+// row chunk at a time, on a copy stream that runs ahead of the passes.
+struct HostRing {
+  static constexpr int kBufs = 3;
+  cudaStream_t copy = nullptr;                     // host -> device copies
+  cudaEvent_t filled[kBufs] = {}, freed[kBufs] = {};
+  cudaEvent_t start = nullptr;                     // the solve's work may begin (ring free)
+  void* mem = nullptr;                             // ring buffers, ATY accumulator, per-chunk ||A||^2
+  size_t bytes = 0;
+};
+
 struct corutv_handle {
   cudaStream_t stream = nullptr;
   bool tracing = false;
@@ -40,9 +51,11 @@ struct corutv_handle {
   corutv::BatchState* batch = nullptr;
   void* rpca_ws = nullptr;      // factors of the ALM-CoRUTV iterations (rpca.cu), lazily allocated
   size_t rpca_ws_bytes = 0;
+  HostRing ring;
 };
 
 void rpca_free(corutv_handle* h);
+void ring_free(corutv_handle* h);
 
 
 inline cudaEvent_t ev_get(corutv_handle* h) {

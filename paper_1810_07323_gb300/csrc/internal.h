@@ -71,6 +71,10 @@ cudaError_t launch_quantize(int dtype, const float* A, int64_t lda, int64_t m, i
                             float* scales, cudaStream_t st);
 
 __global__ void sum_parts_kernel(const double* __restrict__ parts, int n, double* out, DevStatus* status);
+// dst[a][t] += src[a][t], a < l, t < len (ST blocks)
+template <typename TC>
+cudaError_t launch_add_st(const TC* src, int64_t lds, int l, int64_t len, TC* dst, int64_t ldd, cudaStream_t st);
+
 
 // small.cu
 // G = X Y^T (l x l, type TG) of two ST blocks: per-CTA partials, then an ordered reduction

@@ -1650,6 +1650,28 @@ __global__ void __launch_bounds__(256) fro2_kernel(const TA* __restrict__ A, int
   }
 }
 
+// dst[a][t] += src[a][t] for a < l, t < len: sums the row-chunk products A_c^T Y_c of a pass
+// over a host-streamed A (ST blocks, one CTA row per sketch column)
+template <typename TC>
+__global__ void add_st_kernel(const TC* __restrict__ src, int64_t lds, int64_t len, TC* __restrict__ dst,
+                              int64_t ldd) {
+  const int64_t a = blockIdx.y;
+  const TC* s = src + a * lds;
+  TC* d = dst + a * ldd;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < len; t += (int64_t)gridDim.x * blockDim.x)
+    d[t] += s[t];
+}
+
+template <typename TC>
+cudaError_t launch_add_st(const TC* src, int64_t lds, int l, int64_t len, TC* dst, int64_t ldd, cudaStream_t st) {
+  const int64_t bx = cdiv(len, 256) < 32 ? cdiv(len, 256) : 32;
+  add_st_kernel<TC><<<dim3((unsigned)bx, (unsigned)l), 256, 0, st>>>(src, lds, len, dst, ldd);
+  CORUTV_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
+template cudaError_t launch_add_st<float>(const float*, int64_t, int, int64_t, float*, int64_t, cudaStream_t);
+template cudaError_t launch_add_st<double>(const double*, int64_t, int, int64_t, double*, int64_t, cudaStream_t);
+
 __global__ void sum_parts_kernel(const double* __restrict__ parts, int n, double* out, DevStatus* status) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     double s = 0.0;
