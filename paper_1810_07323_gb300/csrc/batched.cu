@@ -48,6 +48,8 @@ struct BatchState {
   DevStatus* dstatus = nullptr;
   DevStatus* bstatus = nullptr;       // batch-wide (timeouts of the grouped tensor-core passes)
   float* partials = nullptr;
+  int* kcount = nullptr;              // split counters of the SIMT passes (all problems)
+  size_t kcount_bytes = 0;
   int count = 0;
   std::vector<int> passes;            // passes over A per problem
   std::vector<int> want_fro2;
@@ -126,9 +128,9 @@ bool batch_uses_tc(int count, const corutv_problem* probs) {
 
 // Sizes of one problem's buffers (FP32 sketches and factors, FP64 l x l blocks).
 struct ProbSizes {
-  int64_t len1, len2, ld1, ld2, ld3;
-  int gp1, gp2, nf;
-  size_t sk1, sk2, sk3, xr, gparts, ll8, ll4, defic, fparts, status;
+  int64_t len1, len2, ld1, ld2, ld3, tiles1, tiles2;
+  int gp1, gp2, nf, ks1, ks2, ntiles;
+  size_t sk1, sk2, sk3, xr, gparts, ll8, ll4, defic, fparts, status, kparts;
 };
 
 ProbSizes prob_sizes(const corutv_problem& p, int lp, bool tc) {
@@ -141,7 +143,13 @@ ProbSizes prob_sizes(const corutv_problem& p, int lp, bool tc) {
   z.ld3 = std::max(z.ld1, z.ld2);
   z.gp1 = (int)std::max<int64_t>(1, cdiv(z.len1, kBatchGramCols));
   z.gp2 = (int)std::max<int64_t>(1, cdiv(z.len2, kBatchGramCols));
-  z.nf = (int)cdiv(z.len1, kBatchPassBN);
+  z.tiles1 = cdiv(z.len1, kBatchPassBN);
+  z.tiles2 = cdiv(z.len2, kBatchPassBN);
+  // SIMT passes: C1 and the core reduce over len2, C2 over len1
+  z.ks1 = batch_ksplit(z.len2);
+  z.ks2 = batch_ksplit(z.len1);
+  z.ntiles = (int)std::max(z.tiles1, z.tiles2);
+  z.nf = (int)(z.tiles1 * z.ks1);
   z.sk1 = sizeof(float) * p.l * z.ld1;
   z.sk2 = sizeof(float) * p.l * z.ld2;
   z.sk3 = sizeof(float) * p.l * z.ld3;
@@ -152,12 +160,15 @@ ProbSizes prob_sizes(const corutv_problem& p, int lp, bool tc) {
   z.defic = sizeof(int) * p.l;
   z.fparts = sizeof(double) * z.nf;
   z.status = sizeof(DevStatus);
+  z.kparts = sizeof(float) * (size_t)p.l *
+             std::max<int64_t>(z.ks1 > 1 ? z.ks1 * z.len1 : 0, z.ks2 > 1 ? z.ks2 * z.len2 : 0);
   return z;
 }
 
 size_t prob_bytes(const ProbSizes& z) {
   return align_up(z.sk1) + align_up(z.sk2) + align_up(z.sk3) + align_up(z.xr) + align_up(z.gparts) +
-         3 * align_up(z.ll8) + 2 * align_up(z.ll4) + align_up(z.defic) + align_up(z.fparts) + align_up(z.status);
+         3 * align_up(z.ll8) + 2 * align_up(z.ll4) + align_up(z.defic) + align_up(z.fparts) + align_up(z.status) +
+         align_up(z.kparts);
 }
 
 int lp_for(int lmax) { return lmax <= 32 ? 32 : (lmax <= 64 ? 64 : 128); }
@@ -188,6 +199,7 @@ struct Plan {
   std::vector<std::vector<int64_t>> pt_fro;   // fro slots per problem of the table (0: none)
   size_t off_tmaps = 0, off_fro = 0, table_bytes = 0, total_fro = 0;
   size_t off_status = 0, off_bstatus = 0, off_partials = 0, off_probs = 0, need = 0;
+  size_t off_kcount = 0, kcount_bytes = 0;    // split counters of the SIMT passes, all problems
 };
 
 void make_plan(Plan& L, int count, const corutv_problem* probs, int sms) {
@@ -203,8 +215,9 @@ void make_plan(Plan& L, int count, const corutv_problem* probs, int sms) {
     const corutv_problem& p = probs[i];
     const ProbSizes& z = L.sz[i] = prob_sizes(p, kClassLP[lclass(p.l)], L.tc);
     std::vector<int2>* mc = L.maps[lclass(p.l)];
-    add_blocks(mc[kMapT1], i, cdiv(z.len1, kBatchPassBN));
-    add_blocks(mc[kMapT2], i, cdiv(z.len2, kBatchPassBN));
+    add_blocks(mc[kMapT1], i, z.tiles1 * z.ks1);
+    add_blocks(mc[kMapT2], i, z.tiles2 * z.ks2);
+    L.kcount_bytes += sizeof(int) * z.ntiles;
     add_blocks(mc[kMapG1], i, z.gp1);
     add_blocks(mc[kMapG2], i, z.gp2);
     add_blocks(mc[kMapRed], i, cdiv((int64_t)p.l * p.l, 32));
@@ -279,6 +292,8 @@ void make_plan(Plan& L, int count, const corutv_problem* probs, int sms) {
   off += align_up(sizeof(DevStatus));
   L.off_partials = off;
   if (L.tc) off += align_up(tc_grouped_partial_bytes(sms));
+  L.off_kcount = off;
+  off += align_up(std::max<size_t>(sizeof(int), L.kcount_bytes));
   L.off_probs = off;
   for (int i = 0; i < count; ++i) off += prob_bytes(L.sz[i]);
   L.need = off;
@@ -322,6 +337,9 @@ int build(corutv_handle* h, BatchState* B, int count, const corutv_problem* prob
   B->dstatus = reinterpret_cast<DevStatus*>(d + L.off_status);
   B->bstatus = reinterpret_cast<DevStatus*>(d + L.off_bstatus);
   B->partials = L.tc ? reinterpret_cast<float*>(d + L.off_partials) : nullptr;
+  B->kcount = reinterpret_cast<int*>(d + L.off_kcount);
+  B->kcount_bytes = std::max<size_t>(sizeof(int), L.kcount_bytes);
+  size_t kc_off = 0;
   B->passes.assign(count, 0);
   B->want_fro2.assign(count, 0);
   B->multi_pass.assign(L.maxq + 1, 0);
@@ -367,6 +385,10 @@ int build(corutv_handle* h, BatchState* B, int count, const corutv_problem* prob
     Q.gp2 = z.gp2;
     Q.nfparts = z.nf;
     Q.status = B->dstatus + i;
+    Q.ks1 = z.ks1;
+    Q.ks2 = z.ks2;
+    Q.kcount = B->kcount + kc_off;
+    kc_off += z.ntiles;
     auto take = [&](size_t bytes) {
       char* r = d + off;
       off += align_up(bytes);
@@ -385,6 +407,7 @@ int build(corutv_handle* h, BatchState* B, int count, const corutv_problem* prob
     Q.defic = reinterpret_cast<int*>(take(z.defic));
     Q.fparts = reinterpret_cast<double*>(take(z.fparts));
     take(z.status);
+    Q.kparts = z.kparts ? reinterpret_cast<float*>(take(z.kparts)) : nullptr;
     if (L.tc) {
       // tensor maps: A rows (dir AX), A columns (dir ATY), Xr over len1 and over len2 columns
       CUtensorMap* tm = reinterpret_cast<CUtensorMap*>(hb + L.off_tmaps) + 4 * i;
@@ -531,6 +554,7 @@ int pass_grouped(corutv_handle* h, const BatchState* B, int which, int it) {
 int enqueue(corutv_handle* h, const BatchState* B) {
   cudaStream_t st = h->stream;
   CUB(cudaMemsetAsync(B->dstatus, 0, sizeof(DevStatus) * B->count, st));
+  CUB(cudaMemsetAsync(B->kcount, 0, B->kcount_bytes, st));
   CUB(cudaMemsetAsync(B->bstatus, 0, sizeof(DevStatus), st));
   {
     PhaseTimer tm(h, kPhAsm);

@@ -164,17 +164,29 @@ struct BatchProb {
   float *G, *D, *Qt;    // l x l Gram / core / Q~ (FP32)
   float *R, *Rinv;
   int* defic;
-  double* fparts;       // ||A||^2 partials, one per tile of the first pass
+  double* fparts;       // ||A||^2 partials, one per block of the first pass
   int nfparts;
   DevStatus* status;
+  int ks1, ks2;         // SIMT passes: K splits of the len1-output (C1, core) and len2-output (C2) passes
+  float* kparts;        // their partial products, [split][l][len] (null when neither pass splits)
+  int* kcount;          // per output tile: splits finished so far (zero between passes)
 };
 
 // Block -> (problem, local block) maps drive every grouped launch.
 enum BatchSketch : int { kB_C1 = 0, kB_C2 = 1, kB_CORE = 2 };          // pass outputs
 enum BatchGram : int { kG_ORTH1 = 0, kG_ORTH2 = 1, kG_CORE_EXACT = 2, kG_CORE_SKETCH = 3 };
 
-// batched SIMT pass (pass_simt.cu): one CTA per 64 output positions, full K, no split
+// batched SIMT pass (pass_simt.cu): one CTA per 64 output positions and K range; a problem
+// whose K exceeds 2 kBatchSplitK is split into ceil(K / kBatchSplitK) ranges (at most
+// kBatchMaxSplit), summed in range order by the last CTA of each tile
 constexpr int kBatchPassBN = 64;
+constexpr int64_t kBatchSplitK = 2048;
+constexpr int kBatchMaxSplit = 64;
+inline int batch_ksplit(int64_t K) {
+  if (K <= 2 * kBatchSplitK) return 1;
+  const int64_t s = (K + kBatchSplitK - 1) / kBatchSplitK;
+  return (int)(s < kBatchMaxSplit ? s : kBatchMaxSplit);
+}
 cudaError_t launch_pass_simt_grouped(const BatchProb* P, const int2* map, int nblocks, int lp, int a_dtype,
                                      int which, int it, cudaStream_t st);
 // batched TF32 tensor-core pass (pass_tc_grouped.cu): one table entry per problem taking

@@ -107,13 +107,16 @@ __global__ void __launch_bounds__(256) pass_simt_kernel(PassArgs args) {
   }
 }
 
-// Batched pass: block b computes the kBN output positions map[b].y of problem
-// map[b].x over its whole K (no split, so no partials), direction and sizes
-// from the problem's descriptor.  `which` picks the product (C1 = op1(A) X from
-// P2 into P1, C2 = op2(A) Q1 from P1 into P2, or the core pass E from P2 into
-// P3); problems past their last power step (or without an exact core) exit.
-// The C1 pass of step 0 also folds sum(a^2) of the A slab it reads into
-// fparts (one FP64 partial per block, summed per problem in order later).
+// Batched pass: block b computes, for problem map[b].x, the kBN output positions
+// of tile t over K range s (map[b].y = s * tiles + t), direction and sizes from the
+// problem's descriptor.  `which` picks the product (C1 = op1(A) X from P2 into P1,
+// C2 = op2(A) Q1 from P1 into P2, or the core pass E from P2 into P3); problems
+// past their last power step (or without an exact core) exit.  With one range the
+// block writes its tile; with S ranges it writes a partial, and the last of the
+// tile's S blocks to finish (a counter per tile, no waiting) adds the S partials in
+// range order, so the sum does not depend on the schedule.  The C1 pass of step 0
+// also folds sum(a^2) of the A slab it reads into fparts (one FP64 partial per
+// block, summed per problem in order later).
 template <typename TA, int JPT>
 __global__ void __launch_bounds__(256) pass_simt_grouped_kernel(const BatchProb* __restrict__ probs,
                                                                 const int2* __restrict__ map, int which, int it) {
@@ -135,7 +138,13 @@ __global__ void __launch_bounds__(256) pass_simt_grouped_kernel(const BatchProb*
   const TA* A = static_cast<const TA*>(P.A);
   const int l = P.l;
   const int tid = threadIdx.x, ti = tid & 15, tj = tid >> 4;
-  const int64_t i0 = (int64_t)pm.y * kBN;
+  const int S = which == kB_C2 ? P.ks2 : P.ks1;
+  const int64_t tiles = cdiv_d(len, kBN);
+  const int64_t tile = pm.y % tiles;
+  const int rs = (int)(pm.y / tiles);
+  const int64_t KC = cdiv_d(cdiv_d(K, S), kBK) * kBK;      // K range of one split, whole stages
+  const int64_t kbeg = rs * KC, kend = kbeg + KC < K ? kbeg + KC : K;
+  const int64_t i0 = tile * kBN;
   TC acc[JPT][4];
 #pragma unroll
   for (int v = 0; v < JPT; ++v)
@@ -143,14 +152,14 @@ __global__ void __launch_bounds__(256) pass_simt_grouped_kernel(const BatchProb*
     for (int u = 0; u < 4; ++u) acc[v][u] = TC(0);
   float fsum = 0.f;
   double fro_acc = 0.0;
-  for (int64_t k0 = 0; k0 < K; k0 += kBK) {
+  for (int64_t k0 = kbeg; k0 < kend; k0 += kBK) {
     for (int x = tid; x < kBN * kBK; x += 256) {
       int ii, kk;
       if (dir == 0) { ii = x / kBK; kk = x % kBK; }   // coalesced along k (A rows)
       else          { kk = x / kBN; ii = x % kBN; }   // coalesced along i (A columns)
       const int64_t gi = i0 + ii, gk = k0 + kk;
       TC val = TC(0);
-      if (gi < len && gk < K)
+      if (gi < len && gk < kend)
         val = (dir == 0) ? Elem<TA>::load(A, gi, gk, P.lda, P.scales, P.sld)
                          : Elem<TA>::load(A, gk, gi, P.lda, P.scales, P.sld);
       As[ii][kk] = val;
@@ -159,7 +168,7 @@ __global__ void __launch_bounds__(256) pass_simt_grouped_kernel(const BatchProb*
     for (int x = tid; x < LP * kBK; x += 256) {
       const int jj = x / kBK, kk = x % kBK;
       const int64_t gk = k0 + kk;
-      Xs[jj][kk] = (jj < l && gk < K) ? Xt[jj * ldx + gk] : TC(0);
+      Xs[jj][kk] = (jj < l && gk < kend) ? Xt[jj * ldx + gk] : TC(0);
     }
     __syncthreads();
 #pragma unroll 8
@@ -180,6 +189,9 @@ __global__ void __launch_bounds__(256) pass_simt_grouped_kernel(const BatchProb*
       fsum = 0.f;
     }
   }
+  // one K range: the tile itself; several: this range's partial, [range][j][i] with pitch len
+  TC* dst = S == 1 ? Ct : P.kparts + (int64_t)rs * l * len;
+  const int64_t ldd = S == 1 ? ldc : len;
 #pragma unroll
   for (int v = 0; v < JPT; ++v) {
     const int j = tj + 16 * v;
@@ -187,7 +199,26 @@ __global__ void __launch_bounds__(256) pass_simt_grouped_kernel(const BatchProb*
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int64_t gi = i0 + ti + 16 * u;
-      if (gi < len) Ct[j * ldc + gi] = acc[v][u];
+      if (gi < len) dst[j * ldd + gi] = acc[v][u];
+    }
+  }
+  if (S > 1) {
+    __shared__ int last;
+    __threadfence();                     // this block's partial is visible before it is counted
+    __syncthreads();
+    if (tid == 0) last = atomicAdd(&P.kcount[tile], 1) == S - 1;
+    __syncthreads();
+    if (last) {
+      __threadfence();
+      for (int x = tid; x < l * kBN; x += 256) {
+        const int j = x / kBN;
+        const int64_t gi = i0 + x % kBN;
+        if (gi >= len) continue;
+        TC sum = TC(0);
+        for (int r = 0; r < S; ++r) sum += __ldcg(P.kparts + ((int64_t)r * l + j) * len + gi);
+        Ct[j * ldc + gi] = sum;
+      }
+      if (tid == 0) P.kcount[tile] = 0;   // ready for the next pass
     }
   }
   if (fro) {

@@ -97,6 +97,46 @@ def test_batched_mixed_parity(kind):
         assert r.info.passes_over_A == 2 * (q + 1) + (1 if core == "exact" else 0)
 
 
+SPLIT = [
+    # SIMT passes whose reduction length K exceeds 2 x 2048 run as K ranges summed by the last CTA of
+    # each tile: C2 = A^T Q1 over 9000 rows, C2 = A Q1 over 8500 columns (LEFT), C1 and the core
+    # over 9000 columns (with ||A||^2 folded over the split blocks), 20 ranges over 40000 rows
+    (9000, 150, 8, 8, 16, 1, "right", "exact", "stabilised"),
+    (200, 8500, 6, 6, 14, 1, "left", "exact", "stabilised"),
+    (300, 9000, 10, 10, 18, 0, "right", "exact", "stabilised"),
+    (40000, 130, 5, 5, 12, 1, "right", "sketch", "stabilised"),
+    (700, 300, 6, 6, 14, 1, "right", "exact", "stabilised"),
+]
+
+
+@pytest.mark.parametrize("kind", ["f32simt", "bf16", "fp8"])
+def test_batched_split_k_parity(kind):
+    items, refs = [], []
+    for i, (m, n, r, k, l, q, side, core, orth) in enumerate(SPLIT):
+        A = _lowrank_sparse(C.stream_seed(81, i), m, n, r).astype(np.float32)
+        phi = C.normal_block_np(C.stream_seed(82, i), l, 0, m if side == "left" else n, 0, l)
+        it, Aq = _item(A, phi, k, l, q, side, core, orth, kind="f32" if kind == "f32simt" else kind)
+        if kind == "f32simt":
+            it["mma"] = "simt"
+        items.append(it)
+        refs.append((Aq, phi, k, l, q, side, core))
+    b = corutv.Batch(items)
+    outs = []
+    for run in range(3):          # direct launches, capture, replay: identical (the range sums are ordered)
+        res = b.run()
+        outs.append([(x.U.clone(), x.T.clone(), x.V.clone()) for x in res])
+    for o in outs[1:]:
+        for a, c in zip(outs[0], o):
+            assert all(torch.equal(x, y) for x, y in zip(a, c))
+    for i, (r, (Aq, phi, k, l, q, side, core)) in enumerate(zip(res, refs)):
+        assert r.info.status == 0
+        rho = _check(r, Aq, phi, k, l, q, side, core)
+        print(f"{kind} split problem {i} {SPLIT[i][:2]}: rho={rho:.3e}")
+        assert rho < TOL, (i, rho)
+        a2 = float(np.sum(Aq ** 2))
+        assert abs(r.info.fro2_A - a2) < 1e-6 * a2
+
+
 def test_batched_replay_is_identical():
     """First run (direct launches), second (captured into a CUDA graph) and third
     (graph replay) give bit-identical factors."""

@@ -143,3 +143,26 @@ def test_streamed_bad_args(slice2):
         corutv.solve_host(Ah.to(torch.bfloat16), P, 10, 40, 0)      # host streaming: F32 / F64 only
     with pytest.raises(TypeError):
         corutv.solve_host(Ah.cuda(), P, 10, 40, 0)                  # A must be on the host
+
+
+@pytest.mark.parametrize("shape,chunk,side", [((200, 150), 128, "right"), ((129, 300), 128, "left"),
+                                               ((700, 90), 256, "right")])
+def test_streamed_small_shapes(shape, chunk, side):
+    """Edge cases: fewer rows than one chunk plus one row, a chunk of 128 rows with a one-row
+    tail, m much larger than n; F64 so the comparison is exact to rounding."""
+    m, n = shape
+    rng = np.random.default_rng(m * 7 + n)
+    A = rng.standard_normal((m, n)) @ np.diag(0.7 ** np.arange(n)) if m >= n else \
+        np.diag(0.7 ** np.arange(m)) @ rng.standard_normal((m, n))
+    l = 30
+    phi = rng.standard_normal((n if side == "right" else m, l))
+    Ah = _host(A, torch.float64, pinned=(m % 2 == 0))
+    P = torch.tensor(phi, dtype=torch.float64, device="cuda")
+    r = corutv.solve_host(Ah, P, 10, l, 1, side=side, want_fro2=True, chunk_rows=chunk)
+    U, T, V, perm = _np(r)
+    ref = O.corutv(A, phi, 10, l, 1, side=side)
+    assert O.factor_distance(U, T, V, ref["U"], ref["T"], ref["V"]) < TOL["f64"]
+    assert np.array_equal(perm, ref["perm"])
+    _structure(U, T, V, perm, l, side=side)
+    a2 = np.sum(A ** 2)
+    assert abs(r.info.fro2_A - a2) < 1e-12 * a2
