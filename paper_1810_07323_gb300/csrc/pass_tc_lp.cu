@@ -5,10 +5,11 @@
 // A in BF16 is exact; the FP32 sketch operand is split X = X_hi + X_lo into two
 // BF16 parts (both products accumulate in the same TMEM tile), so each product
 // keeps ~16 bits of X.  FP8 tiles are dequantised with their tile scale into
-// BF16 in shared memory by converter warps; tiles of the A^T direction are
-// transposed there too (8 x 8 blocks of 16-bit elements), so both MMA
-// operands are K-major.  Stream-K split, bounded waits and the epilogue are
-// those of pass_tc.cu.
+// BF16 in shared memory by converter warps.  A X reads A tiles K-major (rows of
+// A); A^T Y reads them MN-major (the tile as TMA lands it: rows of A are the K
+// direction, 64 positions per 128-byte swizzled row, four such 8 KB blocks side
+// by side), so no tile is transposed.  Stream-K split, bounded waits and the
+// epilogue are those of pass_tc.cu.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -39,9 +40,10 @@ struct LpCfg {
   static constexpr int kSmem = kStages * kStage + 1024 + 512;
 };
 
-// kind::f16 instruction descriptor: D fp32, A/B BF16 (1), both K-major.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+// kind::f16 instruction descriptor: D fp32, A/B BF16 (1), A K-major, B K-major or (b_mn) MN-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, bool b_mn = false) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((b_mn ? 1u : 0u) << 16) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
 }
 
 __device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
@@ -54,15 +56,6 @@ __device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t adesc, uint64_
       "}\n" ::"r"(tmem_d),
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
-}
-
-// two 16-bit elements: low halves (sel 0x5410) or high halves (0x7632) of a and b
-__device__ __forceinline__ uint32_t pick16(uint32_t a, uint32_t b, bool hi) {
-  return __byte_perm(a, b, hi ? 0x7632 : 0x5410);
-}
-
-__device__ __forceinline__ uint32_t word4(const uint4& v, int w) {
-  return w == 0 ? v.x : (w == 1 ? v.y : (w == 2 ? v.z : v.w));
 }
 
 __device__ __forceinline__ float bf16lo(uint32_t w) { return __uint_as_float(w << 16); }
@@ -110,7 +103,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                       const __grid_constant__ CUtensorMap mapXl, LpArgs args) {
   using Cfg = LpCfg<FP8>;
   constexpr int S = Cfg::kStages;
-  constexpr bool kConv = FP8 || FRO || DIR == 1;
+  constexpr bool kConv = FP8 || FRO;
   extern __shared__ uint8_t smem_dyn[];
   uint8_t* smem = smem_dyn + ((1024u - (smem_u32(smem_dyn) & 1023u)) & 1023u);
   // stage s: [A bf16 | X_hi | X_lo | (FP8 staging)]
@@ -196,7 +189,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == 1) {
     // ---------------------------------------------------------------- MMA issuer
     if (lane == 0) {
-      constexpr uint32_t idesc = idesc_bf16(kM, kBN);
+      constexpr uint32_t idesc = idesc_bf16(kM, kBN, DIR == 1);
       const uint32_t ready0 = kConv ? conv0 : full0;
       int64_t n = 0;
       int seg = 0;
@@ -220,7 +213,10 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t hbase = smem_u32(xh_tile(stage)), lbase = smem_u32(xl_tile(stage));
 #pragma unroll
           for (int kk = 0; kk < kBK / 16; ++kk) {
-            const uint64_t bdesc = smem_desc(abase + kk * 32, 16, 1024);
+            // K-major: the k-step is 32 bytes inside the swizzled rows; MN-major: 16 rows (2 KB), the
+            // next 8-row group 1 KB on (SBO) and the next 64 positions 8 KB on (LBO)
+            const uint64_t bdesc =
+                DIR == 0 ? smem_desc(abase + kk * 32, 16, 1024) : smem_desc(abase + kk * 2048, kBK * 128, 1024);
             mma_f16(tacc, smem_desc(hbase + kk * 32, 16, 1024), bdesc, idesc, (first && kk == 0) ? 0u : 1u);
             mma_f16(tacc, smem_desc(lbase + kk * 32, 16, 1024), bdesc, idesc, 1u);
           }
@@ -246,7 +242,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int64_t it = s; it < e; ++it, ++n) {
       const int stage = (int)(n % S);
       const uint32_t ph = (uint32_t)((n / S) & 1);
-      // the converter warps synchronise among themselves (transposes): they give up together
+      // the converter warps give up together (one abort flag per stage)
       if (!mbar_wait(full0 + 8 * stage, ph, args.status)) *conv_abort = 1;
       asm volatile("bar.sync 1, 128;" ::: "memory");
       if (*conv_abort) break;
@@ -255,8 +251,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int p0 = (int)(t * kBN);
       uint8_t* at = a_tile(stage);
       float part = 0.f;
-      if (DIR == 0 && !FP8) {
-        // BF16 rows are already K-major: only ||A||^2
+      if (!FP8) {
+        // BF16 tiles are read as TMA lands them: only ||A||^2
         const uint4* a4 = reinterpret_cast<const uint4*>(at);
 #pragma unroll 4
         for (int q = ct; q < kATile / 16; q += 128) {
@@ -268,7 +264,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             part = fmaf(lo, lo, fmaf(hi, hi, part));
           }
         }
-      } else if (DIR == 0 && FP8) {
+      } else if (DIR == 0) {
         // staging [256 rows][64 B] -> BF16 [256 rows][64] (128-byte swizzle), times the tile scale
         // the 256 rows span two 128-row tile rows; the 64 columns lie in one tile column
         const uint8_t* f8 = f8_tile(stage);
@@ -291,62 +287,26 @@ __global__ void __launch_bounds__(kThreads, 1)
           *reinterpret_cast<uint4*>(at + r * 128 + ((c8 ^ (r & 7)) << 4)) = o;
         }
       } else {
-        // A^T tile -> K-major [256 n][64 k].  8 x 8 blocks: kb8 = q / 32 (k), nb8 = q % 32 (n).
-        uint4 blk[2][8];
+        // staging [64 k][256 B] -> BF16 MN-major: row k of the 64-position block c at c * 8 KB + 128 k
+        // (128-byte swizzle), times the tile scale; the 64 k rows lie in one 128-row tile row and 8
+        // consecutive positions in one tile column
+        const uint8_t* f8 = f8_tile(stage);
+        const int64_t tr = (int64_t)k0 >> 7;
+#pragma unroll 4
+        for (int u = ct; u < kBK * (kBN / 8); u += 128) {
+          const int k = u >> 5, c8 = u & 31;
+          int64_t tc = (int64_t)(p0 + 8 * c8) >> 7;
+          if (tc >= args.scols) tc = args.scols - 1;
+          float f[8];
+          fp8x8_to_float(*reinterpret_cast<const uint2*>(f8 + k * kBN + 8 * c8), args.scales[tr * args.sld + tc], f);
+          if (FRO)
 #pragma unroll
-        for (int b = 0; b < 2; ++b) {
-          const int q = ct + 128 * b, kb8 = q >> 5, nb8 = q & 31;
-          float sc = 1.f;
-          if (FP8) {
-            // 8 rows of one 64-row k-block and 8 columns never straddle a 128 x 128 tile
-            const int64_t tr = (int64_t)k0 >> 7;
-            int64_t tc = (int64_t)(p0 + 8 * nb8) >> 7;
-            if (tc >= args.scols) tc = args.scols - 1;
-            sc = args.scales[tr * args.sld + tc];
-          }
-#pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const int k = 8 * kb8 + i;
-            if (FP8) {
-              float f[8];
-              fp8x8_to_float(*reinterpret_cast<const uint2*>(f8_tile(stage) + k * 256 + 8 * nb8), sc, f);
-              if (FRO)
-#pragma unroll
-                for (int x = 0; x < 8; ++x) part = fmaf(f[x], f[x], part);
-              blk[b][i].x = pack_bf16(f[0], f[1]); blk[b][i].y = pack_bf16(f[2], f[3]);
-              blk[b][i].z = pack_bf16(f[4], f[5]); blk[b][i].w = pack_bf16(f[6], f[7]);
-            } else {
-              const int c = nb8 >> 3, ch = nb8 & 7;     // 64-column chunk, 16-byte slot in the row
-              blk[b][i] = *reinterpret_cast<const uint4*>(at + c * (kBK * 128) + k * 128 + ((ch ^ (k & 7)) << 4));
-              if (FRO) {
-                const uint32_t w[4] = {blk[b][i].x, blk[b][i].y, blk[b][i].z, blk[b][i].w};
-#pragma unroll
-                for (int x = 0; x < 4; ++x) {
-                  const float lo = bf16lo(w[x]), hi = bf16hi(w[x]);
-                  part = fmaf(lo, lo, fmaf(hi, hi, part));
-                }
-              }
-            }
-          }
-        }
-        // every converter warp must finish reading before the tile is overwritten (BF16 transposes in place)
-        if (!FP8) asm volatile("bar.sync 1, 128;" ::: "memory");
-#pragma unroll
-        for (int b = 0; b < 2; ++b) {
-          const int q = ct + 128 * b, kb8 = q >> 5, nb8 = q & 31;
-#pragma unroll
-          for (int jj = 0; jj < 8; ++jj) {
-            const int j = (jj + nb8) & 7;           // rotate rows: conflict-free stores
-            const int w = j >> 1;
-            const bool hi = (j & 1) != 0;
-            uint4 o;
-            o.x = pick16(word4(blk[b][0], w), word4(blk[b][1], w), hi);
-            o.y = pick16(word4(blk[b][2], w), word4(blk[b][3], w), hi);
-            o.z = pick16(word4(blk[b][4], w), word4(blk[b][5], w), hi);
-            o.w = pick16(word4(blk[b][6], w), word4(blk[b][7], w), hi);
-            const int nrow = 8 * nb8 + j;
-            *reinterpret_cast<uint4*>(at + nrow * 128 + ((kb8 ^ (nrow & 7)) << 4)) = o;
-          }
+            for (int i = 0; i < 8; ++i) part = fmaf(f[i], f[i], part);
+          uint4 o;
+          o.x = pack_bf16(f[0], f[1]); o.y = pack_bf16(f[2], f[3]);
+          o.z = pack_bf16(f[4], f[5]); o.w = pack_bf16(f[6], f[7]);
+          const int c = c8 >> 3, ch = c8 & 7;
+          *reinterpret_cast<uint4*>(at + c * (kBK * 128) + k * 128 + ((ch ^ (k & 7)) << 4)) = o;
         }
       }
       fro += (double)part;
@@ -388,7 +348,7 @@ cudaError_t launch_lp_variant(const CUtensorMap& mA, const CUtensorMap& mH, cons
   auto kern = pass_tc_lp_kernel<DIR, FP8, FRO>;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, LpCfg<FP8>::kSmem);
   if (err != cudaSuccess) return err;
-  constexpr bool conv = FP8 || FRO || DIR == 1;
+  constexpr bool conv = FP8 || FRO;
   kern<<<(unsigned)G, conv ? kThreads : 192, LpCfg<FP8>::kSmem, st>>>(mA, mH, mL, la);
   CORUTV_COUNT_LAUNCH();
   return cudaGetLastError();
