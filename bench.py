@@ -923,6 +923,10 @@ def main():
             res2 += float((blk * blk).sum())
     a2 = info.fro2_A
     rel_err_k = (res2 / a2) ** 0.5
+    # spectral error of the rank-k view (library readout, 30 power steps from a seeded start vector)
+    from synth import counter as SC
+    x0 = SC.normal_block_t(SC.stream_seed(5000, 0), n, 0, 1, 0, n, device=dev).reshape(n).float()
+    e2_k = corutv.residual_norm2(A, U, T, V, x0, k=k, iters=30, handle=h)
 
     # ------------------------------------------------------------ e2e through the public API
     e2e = None
@@ -1000,7 +1004,8 @@ def main():
                                       "orth": tr.orth_ms / args.steps, "core": tr.core_ms / args.steps,
                                       "qrcp": tr.qrcp_ms / args.steps, "assembly": tr.assembly_ms / args.steps,
                                       "fro2": tr.fro2_ms / args.steps},
-               "rel_err_rank_k": rel_err_k}
+               "rel_err_rank_k": rel_err_k,
+               "spectral_err_rank_k": {"e_k2": e2_k, "over_T11": e2_k / float(T[0, 0])}}
         print(json.dumps(out), flush=True)
     if world > 1:
         import torch.distributed as dist

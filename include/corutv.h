@@ -39,7 +39,7 @@
 extern "C" {
 #endif
 
-#define CORUTV_ABI_VERSION 4
+#define CORUTV_ABI_VERSION 5
 
 typedef enum {
   CORUTV_OK = 0,
@@ -392,6 +392,28 @@ typedef struct {
 int corutv_rpca(corutv_handle* h, const corutv_rpca_params* p, const float* M, int64_t ldm, const float* Phi,
                 int64_t ldphi, float* L, int64_t ldl, float* S, int64_t lds, float* Y, int64_t ldy,
                 corutv_rpca_info* info);
+
+/*
+ * corutv_residual_norm2 -- the spectral readout of S9 / Sec. VI-B (e_k,2): an
+ * estimate of ||A - U(:,1:k) T(1:k,:) V^T||_2 by `iters` power iterations on
+ * R^T R from the caller's start vector, R applied as an operator (each
+ * iteration reads A twice: y = R x, x = R^T y / ||R^T y||); *out = ||R x|| for
+ * the final x (0 if an iterate vanishes).  The estimate is a lower bound that
+ * converges to ||R||_2 at the rate (sigma_2(R) / sigma_1(R))^(2 iters).
+ *   a_dtype  F32 or F64 (others: ERR_UNSUPPORTED); A, U, V and x0 in that type.
+ *   A        device, m x n row-major, lda >= n.
+ *   U, V     device, m x l and n x l row-major (ldu, ldv >= l): a solve's outputs.
+ *   T        device, l x l row-major FP64 (ldt >= l).  1 <= k <= l <= 128.
+ *   x0       device, n elements: the start vector (normalised here; any
+ *            non-zero vector, e.g. Gaussian, drawn by the caller).
+ * FP32 A: the length-n and length-m dot products use compensated (Dot2)
+ * arithmetic and the low-rank part is formed in FP64 before the subtraction;
+ * norms in FP64.  Synchronous on the handle's stream (the result is a host
+ * double); the handle keeps a lazily allocated buffer of the vectors.
+ */
+int corutv_residual_norm2(corutv_handle* h, int a_dtype, const void* A, int64_t lda, int64_t m, int64_t n,
+                          const void* U, int64_t ldu, const double* T, int64_t ldt, const void* V, int64_t ldv,
+                          int l, int k, const void* x0, int iters, double* out);
 
 /* Synchronise the handle's stream and return the outcome of the last solve. */
 int corutv_info_wait(corutv_handle* h, corutv_info* out);

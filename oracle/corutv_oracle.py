@@ -344,9 +344,11 @@ def fro_residual(A, U, T, V, k: int | None = None) -> float:
     return float(np.linalg.norm(np.asarray(A, dtype=np.float64) - B))
 
 
-def spectral_residual(A, U, T, V, k: int | None = None, iters: int = 50, seed: int = 7) -> float:
-    """||A - U T V^T||_2 estimated by power iteration on R^T R (R applied as an
-    operator, never formed)."""
+def spectral_residual(A, U, T, V, k: int | None = None, iters: int = 50, seed: int = 7, x0=None) -> float:
+    """||A - U T V^T||_2 (or of the rank-k view) estimated by power iteration on
+    R^T R (R applied as an operator, never formed): per step y = R x,
+    x = R^T y / ||R^T y||; the estimate is ||R x|| for the final x.  The start
+    vector is x0 if given, else a seeded Gaussian draw; either is normalised."""
     A = np.asarray(A, dtype=np.float64)
     kk = T.shape[0] if k is None else k
     Uk, Tk = U[:, :kk], T[:kk, :]
@@ -357,8 +359,10 @@ def spectral_residual(A, U, T, V, k: int | None = None, iters: int = 50, seed: i
     def rtv(y):
         return A.T @ y - V @ (Tk.T @ (Uk.T @ y))
 
-    rng = np.random.default_rng(seed)
-    x = rng.standard_normal(A.shape[1])
+    if x0 is None:
+        x = np.random.default_rng(seed).standard_normal(A.shape[1])
+    else:
+        x = np.array(x0, dtype=np.float64)
     x /= np.linalg.norm(x)
     s = 0.0
     for _ in range(iters):

@@ -92,7 +92,8 @@ EXPORTS = ("corutv_version", "corutv_status_string", "corutv_create", "corutv_de
            "corutv_qrcp", "corutv_fro2", "corutv_gram_noalloc", "corutv_solve_corrected", "corutv_quantize",
            "corutv_batch_workspace_size", "corutv_solve_batched", "corutv_batch_info_wait",
            "corutv_server_create", "corutv_server_submit", "corutv_server_poll", "corutv_server_stats",
-           "corutv_server_destroy", "corutv_rpca", "corutv_solve_host")
+           "corutv_server_destroy", "corutv_rpca", "corutv_solve_host",
+           "corutv_residual_norm2")
 
 
 def load() -> ctypes.CDLL:
@@ -116,6 +117,8 @@ def load() -> ctypes.CDLL:
     lib.corutv_solve_corrected.argtypes = [P, ctypes.POINTER(Params), P, I64, P, P, I64, P, I64, P, I64, P, I64,
                                            P, I64, P]
     lib.corutv_solve_host.argtypes = [P, ctypes.POINTER(Params), P, I64, I64, P, I64, P, I64, P, I64, P, I64, P]
+    lib.corutv_residual_norm2.argtypes = [P, ctypes.c_int, P, I64, I64, I64, P, I64, P, I64, P, I64, ctypes.c_int,
+                                          ctypes.c_int, P, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
     lib.corutv_quantize.argtypes = [P, ctypes.c_int, P, I64, I64, I64, P, I64, P]
     lib.corutv_batch_workspace_size.argtypes = [ctypes.c_int, ctypes.POINTER(Problem), ctypes.POINTER(ctypes.c_size_t)]
     lib.corutv_solve_batched.argtypes = [P, ctypes.c_int, ctypes.POINTER(Problem), ctypes.POINTER(Info)]
@@ -143,7 +146,8 @@ def load() -> ctypes.CDLL:
                  "corutv_orthonormalize", "corutv_gram", "corutv_qrcp", "corutv_fro2", "corutv_solve_corrected",
                  "corutv_quantize", "corutv_batch_workspace_size", "corutv_solve_batched",
                  "corutv_batch_info_wait", "corutv_server_create", "corutv_server_submit", "corutv_server_poll",
-                 "corutv_server_stats", "corutv_server_destroy", "corutv_rpca", "corutv_solve_host"):
+                 "corutv_server_stats", "corutv_server_destroy", "corutv_rpca", "corutv_solve_host",
+                 "corutv_residual_norm2"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -368,6 +372,31 @@ def solve_host(A, Phi, k: int, l: int, q: int = 0, side: str = "right", core: st
     _check(rc, "corutv_solve_host")
     info = info_wait(h) if wait else None
     return SolveResult(U, T, V, perm, info)
+
+
+def residual_norm2(A, U, T, V, x0, k: int | None = None, iters: int = 30, handle: Handle | None = None) -> float:
+    """||A - U(:,1:k) T(1:k,:) V^T||_2 by power iteration from x0 (corutv_residual_norm2).
+
+    A (m, n), U (m, l), V (n, l), x0 (n,): device float32 / float64 of one dtype;
+    T (l, l) device float64.  k defaults to l."""
+    _need_cuda(A, U, T, V, x0)
+    h = handle or handle_for()
+    m, n = A.shape
+    l = U.shape[1]
+    code = _dt_code(A)
+    for t in (U, V, x0):
+        if t.dtype != A.dtype:
+            raise TypeError("U, V and x0 must have A's dtype")
+    if x0.dim() != 1 or x0.shape[0] != n or x0.stride(0) != 1:
+        raise TypeError("x0 must be a contiguous vector of length n")
+    out = ctypes.c_double()
+    rc = load().corutv_residual_norm2(h.h, code, ctypes.c_void_p(A.data_ptr()), _rowmajor_ld(A), m, n,
+                                      ctypes.c_void_p(U.data_ptr()), _rowmajor_ld(U), ctypes.c_void_p(T.data_ptr()),
+                                      _rowmajor_ld(T), ctypes.c_void_p(V.data_ptr()), _rowmajor_ld(V), int(l),
+                                      int(l if k is None else k), ctypes.c_void_p(x0.data_ptr()), int(iters),
+                                      ctypes.byref(out))
+    _check(rc, "corutv_residual_norm2")
+    return out.value
 
 
 class RpcaResult:

@@ -587,6 +587,7 @@ int corutv_destroy(corutv_handle* h) {
   batch_state_free(h->batch);
   rpca_free(h);
   ring_free(h);
+  resid_free(h);
   delete h;
   return CORUTV_OK;
 }

@@ -52,9 +52,14 @@ struct corutv_handle {
   void* rpca_ws = nullptr;      // factors of the ALM-CoRUTV iterations (rpca.cu), lazily allocated
   size_t rpca_ws_bytes = 0;
   HostRing ring;
+  void* resid_ws = nullptr;     // vectors of the spectral readout (resid.cu), lazily allocated
+  size_t resid_ws_bytes = 0;
 };
 
 void rpca_free(corutv_handle* h);
+namespace corutv {
+void resid_free(corutv_handle* h);
+}
 void ring_free(corutv_handle* h);
 
 

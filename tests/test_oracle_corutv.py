@@ -258,3 +258,41 @@ def test_qlp_exact_recovery(cfg1_exact):
     A = cfg1_exact.A
     r = O.corutv(A, W.phi(A.shape[1], 25), 20, 25, 0, factor="qlp")
     assert O.fro_residual(A, r["U"], r["T"], r["V"]) / np.linalg.norm(A) < 1e-13
+
+
+def _gapped(m=90, n=60, c=11):
+    """A with sigma = 10, 9, ..., 6 (five), then 1, 0.5, 0.25, ...: a rank-5 view leaves
+    a residual whose top two singular values are about 1 and 0.5 (power iteration converges
+    like 0.25^iters)."""
+    U = W.haar_orthonormal(301 + c, m, n)
+    V = W.haar_orthonormal(302 + c, n, n)
+    s = np.concatenate([np.arange(10.0, 5.0, -1.0), 0.5 ** np.arange(n - 5)])
+    return (U * s) @ V.T
+
+
+@pytest.mark.parametrize("k", [5, 8])
+def test_spectral_residual_power_iteration(k):
+    """The spectral readout against the largest singular value of the explicitly formed
+    residual R = A - U(:,1:k) T(1:k,:) V^T (Jacobi SVD and LAPACK): converged after enough
+    steps, a lower bound after any number of steps, and the start vector only sets the
+    path.  A residual formed with all l rows of T (a dropped truncation) gives another value."""
+    A = _gapped()
+    l = 8
+    r = O.corutv(A, W.phi(60, l, c=5), 5, l, 1)
+    R = A - O.rank_k(r["U"], r["T"], r["V"], k)
+    s_exact = O.jacobi_svd(R)[0]
+    assert abs(s_exact - np.linalg.svd(R, compute_uv=False)[0]) < 1e-12 * s_exact
+    x0 = np.random.default_rng(3).standard_normal(60)
+    est = O.spectral_residual(A, r["U"], r["T"], r["V"], k=k, iters=200, x0=x0)
+    assert abs(est - s_exact) < 1e-10 * s_exact
+    for it in (0, 1, 3):
+        e = O.spectral_residual(A, r["U"], r["T"], r["V"], k=k, iters=it, x0=x0)
+        assert e <= s_exact * (1 + 1e-12)
+    # y = R x0 / ||x0|| after zero steps
+    assert abs(O.spectral_residual(A, r["U"], r["T"], r["V"], k=k, iters=0, x0=x0)
+               - np.linalg.norm(R @ x0) / np.linalg.norm(x0)) < 1e-12 * s_exact
+    est_seed = O.spectral_residual(A, r["U"], r["T"], r["V"], k=k, iters=200, seed=9)
+    assert abs(est_seed - s_exact) < 1e-10 * s_exact
+    if k < l:
+        full = O.spectral_residual(A, r["U"], r["T"], r["V"], k=None, iters=200, x0=x0)
+        assert abs(full - s_exact) > 1e-3 * s_exact
