@@ -30,7 +30,7 @@ constexpr int kBK = 64;              // elements of K per stage (one 128-byte ro
 constexpr int kATile = kBN * kBK * 2;        // 32 KB BF16 A tile (K-major, 128-byte swizzle)
 constexpr int kXTile = kM * kBK * 2;         // 16 KB per BF16 X part
 constexpr int kF8Tile = kBN * kBK;           // 16 KB FP8 staging tile
-constexpr int kThreads = 320;        // 0 TMA, 1 MMA, 2..5 epilogue, 6..9 converter
+constexpr int kMaxThreads = 448;     // 0 TMA, 1 MMA, 2..5 epilogue, 6.. converter (4 BF16, 8 FP8 warps)
 
 template <bool FP8>
 struct LpCfg {
@@ -38,6 +38,10 @@ struct LpCfg {
   static constexpr int kStages = FP8 ? 2 : 3;
   static constexpr int kTx = (FP8 ? kF8Tile : kATile) + 2 * kXTile;
   static constexpr int kSmem = kStages * kStage + 1024 + 512;
+  // FP8 tiles are dequantised element by element: twice the converter warps keep two per SM
+  // sub-partition issuing; BF16 converters only sum squares
+  static constexpr int kConvWarps = FP8 ? 8 : 4;
+  static constexpr int kThreads = 192 + 32 * kConvWarps;
 };
 
 // kind::f16 instruction descriptor: D fp32, A/B BF16 (1), A K-major, B K-major or (b_mn) MN-major.
@@ -98,7 +102,7 @@ struct LpArgs {
 };
 
 template <int DIR, bool FP8, bool FRO>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kMaxThreads, 1)
     pass_tc_lp_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapXh,
                       const __grid_constant__ CUtensorMap mapXl, LpArgs args) {
   using Cfg = LpCfg<FP8>;
@@ -114,7 +118,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S * Cfg::kStage);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * S + 4);
   double* fro_red = reinterpret_cast<double*>(bars + 3 * S + 6);
-  volatile int* conv_abort = reinterpret_cast<volatile int*>(fro_red + 4);
+  volatile int* conv_abort = reinterpret_cast<volatile int*>(fro_red + 8);
   const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + S), conv0 = smem_u32(bars + 2 * S);
   const uint32_t tfull0 = smem_u32(bars + 3 * S), tempty0 = smem_u32(bars + 3 * S + 2);
 
@@ -127,7 +131,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int i = 0; i < S; ++i) {
       mbar_init(full0 + 8 * i, 1);
       mbar_init(empty0 + 8 * i, 1);
-      mbar_init(conv0 + 8 * i, 4);
+      mbar_init(conv0 + 8 * i, Cfg::kConvWarps);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(tfull0 + 8 * b, 1);
@@ -234,9 +238,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                          tempty0, args.status);
   } else if (kConv) {
     // ---------------------------------------------------------------- converter (warps 6..9)
+    constexpr int CT = 32 * Cfg::kConvWarps;   // converter threads
     const int ct = threadIdx.x - 192;
     if (ct == 0) *conv_abort = 0;
-    asm volatile("bar.sync 1, 128;" ::: "memory");
+    asm volatile("bar.sync 1, %0;" ::"n"(CT) : "memory");
     double fro = 0.0;
     int64_t n = 0;
     for (int64_t it = s; it < e; ++it, ++n) {
@@ -244,7 +249,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t ph = (uint32_t)((n / S) & 1);
       // the converter warps give up together (one abort flag per stage)
       if (!mbar_wait(full0 + 8 * stage, ph, args.status)) *conv_abort = 1;
-      asm volatile("bar.sync 1, 128;" ::: "memory");
+      asm volatile("bar.sync 1, %0;" ::"n"(CT) : "memory");
       if (*conv_abort) break;
       const int64_t t = it / KB, kb = it - t * KB;
       const int k0 = (int)(kb * kBK);
@@ -255,7 +260,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         // BF16 tiles are read as TMA lands them: only ||A||^2
         const uint4* a4 = reinterpret_cast<const uint4*>(at);
 #pragma unroll 4
-        for (int q = ct; q < kATile / 16; q += 128) {
+        for (int q = ct; q < kATile / 16; q += CT) {
           const uint4 v = a4[q];
           const uint32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
@@ -273,7 +278,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const float sc0 = args.scales[tr0 * args.sld + (k0 >> 7)];
         const float sc1 = args.scales[tr1 * args.sld + (k0 >> 7)];
 #pragma unroll 4
-        for (int u = ct; u < kBN * 8; u += 128) {
+        for (int u = ct; u < kBN * 8; u += CT) {
           const int r = u >> 3, c8 = u & 7;
           const float sc = r < 128 ? sc0 : sc1;
           float f[8];
@@ -293,7 +298,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint8_t* f8 = f8_tile(stage);
         const int64_t tr = (int64_t)k0 >> 7;
 #pragma unroll 4
-        for (int u = ct; u < kBK * (kBN / 8); u += 128) {
+        for (int u = ct; u < kBK * (kBN / 8); u += CT) {
           const int k = u >> 5, c8 = u & 31;
           int64_t tc = (int64_t)(p0 + 8 * c8) >> 7;
           if (tc >= args.scols) tc = args.scols - 1;
@@ -323,7 +328,11 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   tc_fence_before();
   __syncthreads();
-  if (FRO && threadIdx.x == 0) args.fro_parts[blockIdx.x] = (fro_red[0] + fro_red[1]) + (fro_red[2] + fro_red[3]);
+  if (FRO && threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < Cfg::kConvWarps; ++w) t += fro_red[w];
+    args.fro_parts[blockIdx.x] = t;
+  }
   if (warp == 1) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem_base) : "memory");
@@ -349,7 +358,7 @@ cudaError_t launch_lp_variant(const CUtensorMap& mA, const CUtensorMap& mH, cons
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, LpCfg<FP8>::kSmem);
   if (err != cudaSuccess) return err;
   constexpr bool conv = FP8 || FRO;
-  kern<<<(unsigned)G, conv ? kThreads : 192, LpCfg<FP8>::kSmem, st>>>(mA, mH, mL, la);
+  kern<<<(unsigned)G, conv ? LpCfg<FP8>::kThreads : 192, LpCfg<FP8>::kSmem, st>>>(mA, mH, mL, la);
   CORUTV_COUNT_LAUNCH();
   return cudaGetLastError();
 }
