@@ -243,17 +243,34 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     if (ct == 0) *conv_abort = 0;
     asm volatile("bar.sync 1, %0;" ::"n"(CT) : "memory");
     double fro = 0.0;
+    // FP8 tile scales of iteration i2 for this thread -- A X: the two 128-row tile rows of the 256
+    // positions; A^T Y: the tile column of the thread's eight positions (c8 = ct mod 32 in every
+    // stage) -- loaded one iteration ahead, so their latency hides behind a stage's conversion
+    auto scales_of = [&](int64_t i2, float& a, float& b) {
+      const int64_t t2 = i2 / KB, kb2 = i2 - t2 * KB;
+      const int64_t kcol = (kb2 * kBK) >> 7, p02 = t2 * kBN;
+      if (DIR == 0) {
+        const int64_t tr0 = p02 >> 7, tr1 = tr0 + 1 < args.srows ? tr0 + 1 : tr0;
+        a = args.scales[tr0 * args.sld + kcol];
+        b = args.scales[tr1 * args.sld + kcol];
+      } else {
+        int64_t tc = (p02 + 8 * (ct & 31)) >> 7;
+        if (tc >= args.scols) tc = args.scols - 1;
+        a = b = args.scales[kcol * args.sld + tc];
+      }
+    };
+    float sca = 1.f, scb = 1.f;
+    if (FP8 && s < e) scales_of(s, sca, scb);
     int64_t n = 0;
     for (int64_t it = s; it < e; ++it, ++n) {
       const int stage = (int)(n % S);
       const uint32_t ph = (uint32_t)((n / S) & 1);
+      float nsa = 1.f, nsb = 1.f;
+      if (FP8 && it + 1 < e) scales_of(it + 1, nsa, nsb);
       // the converter warps give up together (one abort flag per stage)
       if (!mbar_wait(full0 + 8 * stage, ph, args.status)) *conv_abort = 1;
       asm volatile("bar.sync 1, %0;" ::"n"(CT) : "memory");
       if (*conv_abort) break;
-      const int64_t t = it / KB, kb = it - t * KB;
-      const int k0 = (int)(kb * kBK);
-      const int p0 = (int)(t * kBN);
       uint8_t* at = a_tile(stage);
       float part = 0.f;
       if (!FP8) {
@@ -273,14 +290,10 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
         // staging [256 rows][64 B] -> BF16 [256 rows][64] (128-byte swizzle), times the tile scale
         // the 256 rows span two 128-row tile rows; the 64 columns lie in one tile column
         const uint8_t* f8 = f8_tile(stage);
-        const int64_t tr0 = (int64_t)p0 >> 7;
-        const int64_t tr1 = tr0 + 1 < args.srows ? tr0 + 1 : tr0;
-        const float sc0 = args.scales[tr0 * args.sld + (k0 >> 7)];
-        const float sc1 = args.scales[tr1 * args.sld + (k0 >> 7)];
 #pragma unroll 4
         for (int u = ct; u < kBN * 8; u += CT) {
           const int r = u >> 3, c8 = u & 7;
-          const float sc = r < 128 ? sc0 : sc1;
+          const float sc = r < 128 ? sca : scb;
           float f[8];
           fp8x8_to_float(*reinterpret_cast<const uint2*>(f8 + r * 64 + 8 * c8), sc, f);
           if (FRO)
@@ -296,14 +309,11 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
         // (128-byte swizzle), times the tile scale; the 64 k rows lie in one 128-row tile row and 8
         // consecutive positions in one tile column
         const uint8_t* f8 = f8_tile(stage);
-        const int64_t tr = (int64_t)k0 >> 7;
 #pragma unroll 4
         for (int u = ct; u < kBK * (kBN / 8); u += CT) {
           const int k = u >> 5, c8 = u & 31;
-          int64_t tc = (int64_t)(p0 + 8 * c8) >> 7;
-          if (tc >= args.scols) tc = args.scols - 1;
           float f[8];
-          fp8x8_to_float(*reinterpret_cast<const uint2*>(f8 + k * kBN + 8 * c8), args.scales[tr * args.sld + tc], f);
+          fp8x8_to_float(*reinterpret_cast<const uint2*>(f8 + k * kBN + 8 * c8), sca, f);
           if (FRO)
 #pragma unroll
             for (int i = 0; i < 8; ++i) part = fmaf(f[i], f[i], part);
@@ -315,6 +325,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
         }
       }
       fro += (double)part;
+      sca = nsa;
+      scb = nsb;
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
       if (lane == 0) mbar_arrive(conv0 + 8 * stage);
