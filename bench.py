@@ -105,14 +105,20 @@ def workload_label(w, core):
 
 
 def dist_setup():
+    """One process per GPU (torchrun's RANK / LOCAL_RANK / WORLD_SIZE): NCCL between GPUs, gloo
+    where there is no GPU (the host-side replica logic).  The ranks run independent replicas; the
+    process group only carries the barriers and the max-over-ranks time."""
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        else:
+            dist.init_process_group("gloo")
     else:
         if torch.cuda.is_available():
             torch.cuda.set_device(0)
@@ -130,9 +136,17 @@ def max_over_ranks(x: float, world: int) -> float:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_rate(units_per_rank: float, ms_local: float, world: int):
+    """Whole-job rate of N independent replicas: the units of all ranks over the slowest
+    rank's time.  Returns (units per second, that time in ms)."""
+    ms = max_over_ranks(ms_local, world)
+    return world * units_per_rank / (ms / 1e3), ms
 
 
 class Clocks:
@@ -868,14 +882,12 @@ def main():
     torch.cuda.synchronize()
     barrier(world)
     clk = clocks.stop() if clocks else None
-    ms_total = e0.elapsed_time(e1)
-    ms_total = max_over_ranks(ms_total, world)
+    value, ms_total = replica_rate(args.steps, e0.elapsed_time(e1), world)
     tr = h.trace_read()
     h.set_tracing(False)
     info = corutv.info_wait(h)
     assert info.status == 0, corutv.status_string(info.status)
     ms_per_step = ms_total / args.steps
-    value = world * args.steps / (ms_total / 1e3)
 
     # ------------------------------------------------------------ roofline of the pass kernel
     peaks = measured_peaks()
