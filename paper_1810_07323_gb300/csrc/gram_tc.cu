@@ -53,6 +53,7 @@ template <bool SAME>
 __global__ void __launch_bounds__(kGThreads, 1)
     gram_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapY, int64_t KB,
                    int64_t chunk, float* __restrict__ parts, DevStatus* status) {
+  pdl_enter();
   extern __shared__ uint8_t smem_dyn[];
   uint8_t* smem = smem_dyn + ((1024u - (smem_u32(smem_dyn) & 1023u)) & 1023u);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kGStages * kGStageBytes);
@@ -228,11 +229,12 @@ cudaError_t launch_gram_tc_partials(const float* X, int64_t ldx, const float* Y,
     if (flag) *flag = true;
   }
   if (same)
-    gram_tc_kernel<true><<<G, kGThreads, kGSmem, st>>>(mapX, mapY, KB, chunk, parts, status);
+    e = launch_pdl(gram_tc_kernel<true>, G, kGThreads, kGSmem, st, mapX, mapY, KB, chunk, parts, status);
   else
-    gram_tc_kernel<false><<<G, kGThreads, kGSmem, st>>>(mapX, mapY, KB, chunk, parts, status);
+    e = launch_pdl(gram_tc_kernel<false>, G, kGThreads, kGSmem, st, mapX, mapY, KB, chunk, parts, status);
+  if (e != cudaSuccess) return e;
   CORUTV_COUNT_LAUNCH();
-  return cudaGetLastError();
+  return cudaSuccess;
 }
 
 }  // namespace corutv

@@ -129,6 +129,7 @@ template <typename TC, int LP>
 __global__ void __launch_bounds__(512) gram_partial_kernel(const TC* __restrict__ Xt, int64_t ldx,
                                                            const TC* __restrict__ Yt, int64_t ldy, int64_t len,
                                                            int l, TC* __restrict__ parts) {
+  pdl_enter();
   gram_partial_body<TC, LP>(Xt, ldx, Yt, ldy, len, l, parts, blockIdx.x, gridDim.x);
 }
 
@@ -203,6 +204,7 @@ __device__ __forceinline__ void gram_reduce_body(const TC* __restrict__ parts, i
 template <typename TC, typename TG>
 __global__ void __launch_bounds__(kRedWarps * 32) gram_reduce_kernel(const TC* __restrict__ parts, int nparts, int LP,
                                                                       int l, TG* __restrict__ G, int64_t ldg) {
+  pdl_enter();
   gram_reduce_body<TC, TG>(parts, nparts, LP, l, G, ldg, blockIdx.x);
 }
 
@@ -218,18 +220,21 @@ cudaError_t launch_gram(const TC* Xt, int64_t ldx, const TC* Yt, int64_t ldy, in
   int LP;
   if (l <= 32) {
     LP = 32;
-    gram_partial_kernel<TC, 32><<<gparts, 512, 0, st>>>(Xt, ldx, Yt, ldy, len, l, parts); CORUTV_COUNT_LAUNCH();
+    CU_RET(launch_pdl(gram_partial_kernel<TC, 32>, gparts, 512, 0, st, Xt, ldx, Yt, ldy, len, l, parts));
+    CORUTV_COUNT_LAUNCH();
   } else if (l <= 64) {
     LP = 64;
-    gram_partial_kernel<TC, 64><<<gparts, 512, 0, st>>>(Xt, ldx, Yt, ldy, len, l, parts); CORUTV_COUNT_LAUNCH();
+    CU_RET(launch_pdl(gram_partial_kernel<TC, 64>, gparts, 512, 0, st, Xt, ldx, Yt, ldy, len, l, parts));
+    CORUTV_COUNT_LAUNCH();
   } else {
     LP = 128;
-    gram_partial_kernel<TC, 128><<<gparts, 512, 0, st>>>(Xt, ldx, Yt, ldy, len, l, parts); CORUTV_COUNT_LAUNCH();
+    CU_RET(launch_pdl(gram_partial_kernel<TC, 128>, gparts, 512, 0, st, Xt, ldx, Yt, ldy, len, l, parts));
+    CORUTV_COUNT_LAUNCH();
   }
-  gram_reduce_kernel<TC, TG><<<(unsigned)cdiv((int64_t)l * l, 32), kRedWarps * 32, 0, st>>>(parts, gparts, LP, l, G,
-                                                                                             ldg);
+  CU_RET(launch_pdl(gram_reduce_kernel<TC, TG>, (unsigned)cdiv((int64_t)l * l, 32), kRedWarps * 32, 0, st, parts,
+                    gparts, LP, l, G, ldg));
   CORUTV_COUNT_LAUNCH();
-  return cudaGetLastError();
+  return cudaSuccess;
 }
 
 template <typename TC, typename TG>
@@ -239,10 +244,10 @@ cudaError_t launch_gram_auto(const TC* Xt, int64_t ldx, const TC* Yt, int64_t ld
     if (allow_tc && gram_tc_ok(Xt, ldx, Yt, ldy, l)) {
       cudaError_t e = launch_gram_tc_partials(Xt, ldx, Yt, ldy, len, l, parts, sms, status, st);
       if (e != cudaSuccess) return e;
-      gram_reduce_kernel<TC, TG><<<(unsigned)cdiv((int64_t)l * l, 32), kRedWarps * 32, 0, st>>>(
-          parts, gram_tc_parts(len, sms), 128, l, G, ldg);
+      CU_RET(launch_pdl(gram_reduce_kernel<TC, TG>, (unsigned)cdiv((int64_t)l * l, 32), kRedWarps * 32, 0, st,
+                        parts, gram_tc_parts(len, sms), 128, l, G, ldg));
       CORUTV_COUNT_LAUNCH();
-      return cudaGetLastError();
+      return cudaSuccess;
     }
   }
   return launch_gram<TC, TG>(Xt, ldx, Yt, ldy, len, l, parts, gram_parts(len, sms), G, ldg, st);
@@ -594,6 +599,7 @@ __global__ void __launch_bounds__(kPipeMaxThreads, 1) cholinv_pipe_kernel(
     const float* __restrict__ G, int64_t ldg, int l, double shift_rel, double tol_rel, float* __restrict__ Rg,
     float* __restrict__ Rinvg, int* __restrict__ defic, DevStatus* status, double* __restrict__ Rout,
     int* __restrict__ skip_flag, float skip_tol) {
+  pdl_enter();
   cholinv_pipe_body(G, ldg, l, shift_rel, tol_rel, Rg, Rinvg, kMaxL, defic, status, Rout, skip_flag, skip_tol);
 }
 
@@ -622,10 +628,10 @@ cudaError_t launch_cholinv(const TC* G, int64_t ldg, int l, double shift_rel, do
   if constexpr (sizeof(TC) == 4) {
     const int nb = (l + 3) / 4;
     const int threads = (nb * (nb + 1) / 2 + 31) / 32 * 32;
-    cholinv_pipe_kernel<<<1, threads, 0, st>>>(G, ldg, l, shift_rel, tol_rel, R, Rinv, defic, status, Rout,
-                                               skip_flag, skip_tol);
+    CU_RET(launch_pdl(cholinv_pipe_kernel, 1, threads, 0, st, G, ldg, l, shift_rel, tol_rel, R, Rinv, defic, status,
+                      Rout, skip_flag, skip_tol));
     CORUTV_COUNT_LAUNCH();
-    return cudaGetLastError();
+    return cudaSuccess;
   } else {
     const size_t smem = (size_t)2 * l * (l + 1) * sizeof(TC);
     cudaError_t e = cudaFuncSetAttribute(cholinv_kernel<TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -834,6 +840,7 @@ __global__ void __launch_bounds__(256, 2) lmul_kernel(const TC* __restrict__ In,
                                                       const int* __restrict__ defic, int pass,
                                                       const int* __restrict__ skip_flag, float* __restrict__ round_out,
                                                       int64_t ldr) {
+  pdl_enter();
   const int64_t tiles = cdiv(len, BI);
   if (skip_flag && *skip_flag) {           // the factor was found to be the identity: Out = In
     if constexpr (sizeof(TC) == 4) {
@@ -884,10 +891,10 @@ static cudaError_t lmul_variant(const TC* In, int64_t ldi, int64_t len, int l, c
   }
   const int cap = (dev < kAttrDevices && resident[dev] > 0) ? resident[dev] : 148;
   const unsigned grid = (unsigned)(tiles < cap ? tiles : cap);
-  lmul_kernel<TC, TS, LP, BI><<<grid, 256, sm, st>>>(In, ldi, len, l, S, lds, Out, ldo, rowmajor ? 1 : 0,
-                                                     upper ? 1 : 0, defic, pass, skip_flag, round_out, ldr);
+  CU_RET(launch_pdl(lmul_kernel<TC, TS, LP, BI>, grid, 256, sm, st, In, ldi, len, l, S, lds, Out, ldo,
+                    rowmajor ? 1 : 0, upper ? 1 : 0, defic, pass, skip_flag, round_out, ldr));
   CORUTV_COUNT_LAUNCH();
-  return cudaGetLastError();
+  return cudaSuccess;
 }
 
 template <typename TC, typename TS>
