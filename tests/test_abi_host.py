@@ -80,3 +80,25 @@ def test_device_tensors_required():
     import torch
     with pytest.raises(ValueError):
         corutv.solve(torch.zeros(10, 8), torch.zeros(8, 2), 1, 2)
+
+
+def test_null_handles_rejected_by_the_newer_entry_points():
+    lib = corutv.load()
+    p = corutv.Params()
+    out = ctypes.c_double()
+    assert lib.corutv_solve_host(None, ctypes.byref(p), None, 0, 0, None, 0, None, 0, None, 0, None, 0,
+                                 None) == corutv.ERR_INVALID_ARG
+    assert lib.corutv_residual_norm2(None, 1, None, 0, 0, 0, None, 0, None, 0, None, 0, 1, 1, None, 1,
+                                     ctypes.byref(out)) == corutv.ERR_INVALID_ARG
+    assert lib.corutv_rpca(None, None, None, 0, None, 0, None, 0, None, 0, None, 0, None) == corutv.ERR_INVALID_ARG
+
+
+def test_host_entry_points_check_their_tensors():
+    import torch
+    with pytest.raises(TypeError):
+        corutv.solve_host(torch.zeros(10), torch.zeros(8, 2), 1, 2)          # A must be 2-D row-major
+    with pytest.raises(TypeError):
+        corutv.solve_host(torch.zeros(10, 8).t(), torch.zeros(8, 2), 1, 2)  # not row-major
+    with pytest.raises(ValueError):
+        corutv.residual_norm2(torch.zeros(10, 8), torch.zeros(10, 2), torch.zeros(2, 2, dtype=torch.float64),
+                              torch.zeros(8, 2), torch.zeros(8))             # device tensors required
