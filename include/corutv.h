@@ -213,8 +213,9 @@ int corutv_solve_host(corutv_handle* h, const corutv_params* p, const void* A, i
 
 /*
  * corutv_solve_corrected -- corutv_solve for A stored in BF16 or FP8 (a_dtype) plus
- * the FP32 correction pass: the range finding (S1-S4 of the schedule, every pass
- * over A) runs on the low-precision A, then the core D = Q1^T A_ref Q2 (Alg. 2
+ * the FP32 correction pass: the range finding (the products of Alg. 3 steps 3-4
+ * and their orthonormalisations: every pass over A but the core's) runs on the
+ * low-precision A, then the core D = Q1^T A_ref Q2 (Alg. 2
  * step 5) is computed by one pass over the FP32 matrix A_ref (m x n row-major,
  * lda_ref >= n, device) with the Q1, Q2 found.  Because D is the projection of
  * A_ref onto the two bases, T then carries no storage error of A; only the
@@ -394,7 +395,7 @@ int corutv_rpca(corutv_handle* h, const corutv_rpca_params* p, const float* M, i
                 corutv_rpca_info* info);
 
 /*
- * corutv_residual_norm2 -- the spectral readout of S9 / Sec. VI-B (e_k,2): an
+ * corutv_residual_norm2 -- the spectral quality readout (e_k,2 of Sec. VI-B): an
  * estimate of ||A - U(:,1:k) T(1:k,:) V^T||_2 by `iters` power iterations on
  * R^T R from the caller's start vector, R applied as an operator (each
  * iteration reads A twice: y = R x, x = R^T y / ||R^T y||); *out = ||R x|| for

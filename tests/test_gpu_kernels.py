@@ -214,7 +214,8 @@ def test_orthonormalize_rank_deficient(dt):
 
 def test_orthonormalize_replaces_zero_columns():
     """Exactly dependent (zero) columns break the unshifted Cholesky: they are
-    detected, replaced by pseudo-random columns and orthonormalised (R7)."""
+    detected, replaced by pseudo-random columns and orthonormalised (any orthonormal
+    completion of the range is correct: U T V^T does not change)."""
     length, l = 2000, 24
     B = _gauss(14, length, l)
     B[:, [3, 11, 20]] = 0.0

@@ -1,4 +1,4 @@
-"""GPU parity of the spectral readout corutv_residual_norm2 (S9, e_k,2 of
+"""GPU parity of the spectral readout corutv_residual_norm2 (e_k,2 of
 Sec. VI-B) with the oracle's power iteration on the same operator: the same
 A, U, T, V (the GPU solve's factors, promoted to FP64) and the same start
 vector.  FP64: the two iterations differ only in the order of FP64 sums

@@ -71,7 +71,7 @@ def test_config1_fp64_parity(cfg1, q, core):
     _structure(U, T, V, perm, 30)
     assert np.array_equal(perm, ref["perm"])
     assert np.abs(T - ref["T"]).max() < 1e-10
-    # S9: ||A - U T V^T||_F^2 = ||A||_F^2 - ||T||_F^2 from the device readouts
+    # quality readout: ||A - U T V^T||_F^2 = ||A||_F^2 - ||T||_F^2 from the device readouts
     a2 = np.sum(A ** 2)
     assert abs(r.info.fro2_A - a2) < 1e-12 * a2
     assert abs(r.info.fro2_T - np.sum(T ** 2)) < 1e-12 * a2
