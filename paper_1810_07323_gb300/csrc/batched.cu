@@ -550,7 +550,7 @@ int pass_grouped(corutv_handle* h, const BatchState* B, int which, int it) {
   return CORUTV_OK;
 }
 
-// The whole batch, enqueued on the handle's stream.
+// The whole batch, enqueued on the handle's stream; steps S0 .. S9 as in a single solve (corutv_abi.cu).
 int enqueue(corutv_handle* h, const BatchState* B) {
   cudaStream_t st = h->stream;
   CUB(cudaMemsetAsync(B->dstatus, 0, sizeof(DevStatus) * B->count, st));

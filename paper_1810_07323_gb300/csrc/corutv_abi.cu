@@ -370,6 +370,10 @@ int orth_passes(const corutv_params* p, int it) {
   return (it == p->q || p->orth == CORUTV_ORTH_STRICT) ? 3 : 1;
 }
 
+// The steps of one solve, as labelled below: S0 stage Psi; S1 C1 = op1(A) X (Alg. 3 step 3); S2 orthonormalise
+// C1; S3 C2 = op2(A) Q1, the other direction (Alg. 3 step 4); S4 orthonormalise C2; S5 the core D = Q1^T A Q2
+// (Alg. 2 step 5); S6 QRCP (or QLP) of D (Alg. 2 step 6); S7 U, V and T (Alg. 2 step 7); S9 the readout
+// ||A||_F^2 (with ||T||_F^2 it gives ||A - U T V^T||_F^2 for the exact core).
 // A_ref (FP32, lda_ref) non-null: correction pass -- the core D of S5 is computed from A_ref
 // with the Q1, Q2 found by the passes over A (stored in BF16 / FP8), and ||A_ref||_F^2 is the
 // readout.
