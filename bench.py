@@ -13,6 +13,8 @@ Workloads (--workload):
   rpca            ALM-CoRUTV robust PCA (Alg. 5) of the Sec. VI-C synthetic
                   2000 x 2000 matrix (--n 1000 for the other Table I size):
                   time of one whole run to the stopping rule.
+  fp32c3          the FP32 (TF32-pass) solve of the bf16 / fp8 workload's matrix:
+                  the three precisions on one A at the same k, l, q.
   host            the fp32 solve with A in page-locked host memory
                   (corutv_solve_host): every one of the 2q+3 passes streams A
                   to the GPU in row chunks (--chunk rows, 0 = ~256 MiB).
@@ -52,6 +54,8 @@ WORKLOADS = {
     "rpca": dict(n=2000, sparse=0.05, q=1, dtype="f32", gen="rpca"),
     # the fp32 solve with A left in page-locked HOST memory: every pass streams it over C2C
     "host": dict(m=20000, n=20000, k=100, l=120, q=1, dtype="f32", gen="config2", host=True),
+    # the FP32 form of the bf16 / fp8 workload (same matrix, k, l, q): the precisions side by side
+    "fp32c3": dict(m=32768, n=16384, k=64, l=80, q=2, dtype="f32", gen="config3"),
 }
 # the paper's ALM-CoRUTV times (Table I, seconds, MATLAB on a 4-core i5-4430): context, not a target
 PAPER_RPCA_S = {(1000, 0.05): 0.6, (2000, 0.05): 3.7, (1000, 0.10): 0.7, (2000, 0.10): 4.1}
@@ -97,6 +101,8 @@ def workload_label(w, core):
         a = f"{w['m']}x{w['n']} FP32 A = G1 diag(i^-1.5) G2^T + 1e-8 noise"
         if w.get("host"):
             a += " in page-locked host memory, streamed to the GPU in row chunks every pass"
+    elif w["dtype"] == "f32":
+        a = f"{w['m']}x{w['n']} FP32 A = G1 diag(exp(-i/30)) G2^T + 1e-8 noise"
     else:
         store = "BF16" if w["dtype"] == "bf16" else "FP8 e4m3 (128x128 tile scales)"
         a = (f"{w['m']}x{w['n']} A = G1 diag(exp(-i/30)) G2^T + 1e-8 noise stored {store}, "
