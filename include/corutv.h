@@ -501,7 +501,10 @@ int corutv_fro2(corutv_handle* h, int a_dtype, const void* A, int64_t lda,
  * ---------------------------------------------------------------------- */
 
 /* Size of the device array that corutv_gram_noalloc uses for its partial sums.
- * Every GPU that loads the library holds it until the process exits. */
+ * A GPU holds it once the library's device code is loaded there (under lazy
+ * module loading, the CUDA default, at the library's first kernel launch or
+ * symbol lookup on that device) until its context is destroyed or the process
+ * exits. */
 #define CORUTV_NOALLOC_SCRATCH_BYTES (4u << 20)
 
 /*
@@ -520,8 +523,12 @@ int corutv_fro2(corutv_handle* h, int a_dtype, const void* A, int64_t lda,
  *     CORUTV_ERR_SHAPE.  The array is fully rewritten by each call, so nothing
  *     has to be cleared between calls.
  *   - The first call on a device looks up the array's device address with that
- *     device current (cudaGetSymbolAddress) and caches it; make that first call
- *     before any stream capture.
+ *     device current (cudaGetSymbolAddress) and caches it with the device's
+ *     current context (a new context, e.g. after cudaDeviceReset, is looked up
+ *     again).  Under lazy module loading that first call may itself load the
+ *     library's device code on the device, the 4 MiB array included, which
+ *     allocates and synchronises: make it once at start-up, before any stream
+ *     capture, so that later calls allocate nothing.
  *   - All calls on a device share the one array: calls whose work overlaps on
  *     the GPU (different streams, or different host threads) race and give wrong
  *     results.  Serialise them.

@@ -5,8 +5,13 @@
 // caching pool), where an extra cudaMalloc may fail or fragment that pool.
 //
 // The per-CTA partial products live in a fixed, file-scope device array
-// instead of a handle workspace.  Every GPU that loads this library holds the
-// array (kNoAllocScratchBytes) until the process exits.
+// instead of a handle workspace.  The array (kNoAllocScratchBytes) exists on a
+// GPU once the library's device code is loaded there -- under lazy module
+// loading (the default since CUDA 12.2) that happens at the first kernel launch
+// or symbol lookup of this library on that device -- and stays until the
+// context is destroyed or the process exits.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -30,22 +35,47 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_scratch_ptr[kMaxDevices] = {};
+CUcontext g_scratch_ctx[kMaxDevices] = {};
+
+// The driver's current context (null if it cannot be queried).
+CUcontext current_context() {
+  static PFN_cuCtxGetCurrent_v4000 fn = nullptr;
+  static bool looked = false;
+  if (!looked) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(p);
+    looked = true;
+  }
+  CUcontext c = nullptr;
+  if (fn && fn(&c) != CUDA_SUCCESS) c = nullptr;
+  return c;
+}
 
 // Device address of the scratch array on the current device.  In host code
-// the symbol is only a host-side stand-in, so the address is looked up once
-// per device (with that device current) and cached.
+// the symbol is only a host-side stand-in, so the address is looked up with
+// the device current and cached per device together with the context it
+// belongs to; a new context on that device (after cudaDeviceReset, say) gets a
+// fresh lookup, so a stale address is never handed to a kernel.
 int scratch_for_current_device(void** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return CORUTV_ERR_CUDA;
   if (dev < 0 || dev >= kMaxDevices) return CORUTV_ERR_UNSUPPORTED;
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_ptr[dev]) {
+  // the runtime makes the device's primary context current on its first call
+  // above; query the context after that
+  const CUcontext ctx = current_context();
+  if (!g_scratch_ptr[dev] || !ctx || ctx != g_scratch_ctx[dev]) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
       cudaGetLastError();
+      g_scratch_ptr[dev] = nullptr;
       return CORUTV_ERR_CUDA;
     }
     g_scratch_ptr[dev] = p;
+    g_scratch_ctx[dev] = ctx;
   }
   *out = g_scratch_ptr[dev];
   return CORUTV_OK;
