@@ -61,6 +61,15 @@ WORKLOADS = {
 PAPER_RPCA_S = {(1000, 0.05): 0.6, (2000, 0.05): 3.7, (1000, 0.10): 0.7, (2000, 0.10): 4.1}
 
 
+# the arithmetic of the passes over an FP32 A for each --mma value (AUTO picks TF32X3 on the tensor cores)
+F32_DTYPE = {"tf32x3": "fp32 (3xtf32 split operands)", "tf32": "tf32", "tf32t": "tf32 (truncated operands)",
+             "simt": "fp32"}
+
+
+def f32_engine(mma: str) -> str:
+    return "tf32x3" if mma == "auto" else mma
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -908,6 +917,10 @@ def main():
             "BF16" if w["dtype"] == "bf16" else "FP8")
         tkey = f"pass_tc_lp_kernel/{w['dtype']}/{m}x{n}/l{l}/src-" + kernel_source_tag("pass_tc_lp.cu",
                                                                                        "tc_common.cuh")
+    elif f32_engine(args.mma) == "tf32x3":
+        kname = "pass_tc3_kernel (dir AX / ATY, split-operand TF32, A in TMEM) incl. operand split and " \
+                "split-tile reduce"
+        tkey = f"pass_tc3_kernel/f32/{m}x{n}/l{l}/src-" + kernel_source_tag("pass_tc3.cu", "tc_common.cuh")
     else:
         kname = "pass_tc_kernel (dir AX / ATY, TF32) incl. operand rounding and split-tile reduce"
         tkey = f"pass_tc_kernel/f32/{m}x{n}/l{l}/src-" + kernel_source_tag("pass_tc.cu", "tc_common.cuh")
@@ -1017,7 +1030,8 @@ def main():
                          f"scaled by m*n/({sm}*{sn})"}
 
     if rank == 0:
-        dtype = {"f32": "tf32", "bf16": "bf16", "fp8": "fp8-e4m3 (bf16 mma)"}[w["dtype"]]
+        dtype = {"f32": F32_DTYPE[f32_engine(args.mma)], "bf16": "bf16",
+                 "fp8": "fp8-e4m3 (bf16 mma)"}[w["dtype"]]
         out = {"metric": "CoR-UTV solves/s", "value": value, "unit": "solves/s", "n_gpus": world,
                "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step,
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,

@@ -65,11 +65,17 @@ typedef enum {
 } corutv_orth;
 typedef enum { CORUTV_F64 = 0, CORUTV_F32 = 1, CORUTV_BF16 = 2, CORUTV_FP8_E4M3 = 3 } corutv_dtype;
 typedef enum {
-  CORUTV_MMA_AUTO = 0,       /* F32 A: TF32 (rounded); BF16 / FP8 A: BF16X2; F64 A: SIMT.  Falls back to
-                                SIMT where TMA cannot address the rows of A (see corutv_solve) */
+  CORUTV_MMA_AUTO = 0,       /* F32 A: TF32X3 (split operands, FP32-class); BF16 / FP8 A: BF16X2; F64 A:
+                                SIMT.  Falls back to SIMT where TMA cannot address the rows of A (see
+                                corutv_solve) */
   CORUTV_MMA_TF32 = 1,       /* tcgen05 kind::tf32 with both operands rounded to nearest TF32
-                                (A tile by tile in shared memory): unbiased products */
-  CORUTV_MMA_TF32X3 = 2,     /* reserved (split-operand FP32-faithful products): returns UNSUPPORTED */
+                                (A tile by tile in shared memory): unbiased products, ~2^-11 relative */
+  CORUTV_MMA_TF32X3 = 2,     /* split-operand FP32-class products on the tensor cores: every FP32 value
+                                v = h + c with h = TF32(v), c = BF16(v - h) (|v - h - c| <= 2^-19 |v|);
+                                a x ~ h_a h_x (kind::tf32, exact products) + [c_a, bf16(h_a)] . [bf16(h_x),
+                                c_x] (one kind::f16 MMA for both cross terms): <= 2^-16.9 relative per
+                                product, then the tensor core's FP32 accumulation (measured ~1e-6 relative
+                                at K = 4096, growing with K; FP32 CUDA-core products: ~2e-7) */
   CORUTV_MMA_SIMT = 3,       /* CUDA-core FMA in the storage precision (FP32 or FP64 products) */
   CORUTV_MMA_TF32_TRUNC = 4, /* tcgen05 kind::tf32 reading raw FP32 (the tensor core drops the low
                                 13 mantissa bits: products shrink by ~3.5e-4 on average) */
@@ -176,9 +182,13 @@ int corutv_set_workspace(corutv_handle* h, void* dptr, size_t bytes);
  * Range finding is stabilised: every sketch is normalised (Sec. III, QR of
  * C1 and C2) before the next product, which in exact arithmetic yields the
  * same Q1, Q2 as the literal loop of Alg. 3.  The final Q1, Q2 come from
- * shifted CholeskyQR3 with an FP64 reduction of FP32 Gram partials (on the
- * FP32 path the third pass is skipped when the second already gives
- * max |Q^T Q - I| <= 2e-6); see corutv_orth for the intermediate sketches.
+ * shifted CholeskyQR3 (see corutv_orth for the intermediate sketches).  The
+ * small factorisations run in the precision of the sketches: FP64 A gets FP64
+ * Gram matrices, Cholesky and QRCP; every other dtype gets FP32 ones -- Gram
+ * partials from FP32 products (3xTF32 tensor-core products for the shifted
+ * first pass and the core when the passes run on the tensor cores), reduced
+ * with compensated FP32 sums.  On the FP32 path the third CholeskyQR pass is
+ * skipped when the second already gives max |Q^T Q - I| <= 2e-6.
  * Returns a validation error synchronously; device conditions via corutv_info_wait.
  */
 int corutv_solve(corutv_handle* h, const corutv_params* p,
@@ -220,8 +230,9 @@ int corutv_solve_host(corutv_handle* h, const corutv_params* p, const void* A, i
  * lda_ref >= n, device) with the Q1, Q2 found.  Because D is the projection of
  * A_ref onto the two bases, T then carries no storage error of A; only the
  * subspaces do.  Requires p->core == EXACT; want_fro2 reports ||A_ref||_F^2.
- * The pass over A_ref uses the TF32 tensor-core engine (SIMT when p->mma is SIMT
- * or TMA cannot address A_ref's rows).  Other arguments as corutv_solve.
+ * The pass over A_ref uses the FP32-class split-operand engine TF32X3 (SIMT when
+ * p->mma is SIMT or TMA cannot address A_ref's rows).  Other arguments as
+ * corutv_solve.
  */
 int corutv_solve_corrected(corutv_handle* h, const corutv_params* p,
                            const void* A, int64_t lda, const float* a_tile_scales,
@@ -467,9 +478,11 @@ int corutv_pass(corutv_handle* h, int dir, int a_dtype, int mma,
 /*
  * Orthonormalise a tall-skinny block in place (Sec. III: C = Q R), ST layout:
  * Ct is l x len (ldc), F32 or F64 (dtype F32/F64).  Shifted CholeskyQR3:
- * R from the Cholesky factor of the FP64-reduced Gram matrix, Q = C R^-1,
- * three times, the first with a diagonal shift (the FP32 third pass is skipped
- * when the second already gives max |Q^T Q - I| <= 2e-6).  If R_out != NULL it
+ * R from the Cholesky factor of the Gram matrix (FP64 Gram and Cholesky for
+ * F64 blocks; FP32-product partials, a compensated FP32 reduction and an FP32
+ * Cholesky for F32 blocks), Q = C R^-1, three times, the first with a diagonal
+ * shift (the FP32 third pass is skipped when the second already gives
+ * max |Q^T Q - I| <= 2e-6).  If R_out != NULL it
  * receives the l x l upper-triangular R = R_3 R_2 R_1 (row-major FP64, ld l)
  * with C = Q R.
  */

@@ -71,7 +71,9 @@ size_t plan_layout(Plan& pl, void* base) {
   pl.P1 = c.take((size_t)pl.LP * pl.ld1 * tb);
   pl.P2 = c.take((size_t)pl.LP * pl.ld2 * tb);
   pl.P3 = c.take((size_t)pl.LP * pl.ld3 * tb);
-  pl.Xr = c.take((size_t)pl.LP * pl.ldr * 4);
+  // the sketch operand of a tensor-core pass: TF32-rounded (first half), TF32 hi / lo split
+  // (both halves), or BF16 hi / lo (first half)
+  pl.Xr = c.take((size_t)2 * pl.LP * pl.ldr * 4);
   pl.partials = c.take(pl.pass_partials);
   pl.gram_parts = c.take((size_t)pl.gparts * kMaxL * kMaxL * tb);
   pl.G = c.take(sizeof(double) * kMaxL * kMaxL);
@@ -101,11 +103,13 @@ size_t pass_partial_bytes(int64_t m, int64_t n, int l, int a_dtype, int sms) {
   if (a_dtype == CORUTV_F32) {
     b = std::max(b, tc_pass_partial_bytes(m, n, sms));
     b = std::max(b, tc_pass_partial_bytes(n, m, sms));
+    b = std::max(b, tc3_pass_partial_bytes(sms));
   }
   // the correction pass of a BF16 / FP8 solve runs on FP32 A
   if (a_dtype == CORUTV_BF16 || a_dtype == CORUTV_FP8_E4M3) {
     b = std::max(b, tc_lp_partial_bytes(sms));
     b = std::max(b, tc_pass_partial_bytes(m, n, sms));
+    b = std::max(b, tc3_pass_partial_bytes(sms));
     b = std::max(b, simt_pass_partial_bytes(m, n, l, 4, sms));
     b = std::max(b, simt_pass_partial_bytes(n, m, l, 4, sms));
   }
@@ -129,7 +133,7 @@ void make_plan(const corutv_params* p, int sms, Plan& pl) {
 // engine allowed for a storage dtype
 bool mma_fits_dtype(int a_dtype, int mma) {
   if (mma == CORUTV_MMA_AUTO || mma == CORUTV_MMA_SIMT) return true;
-  if (mma == CORUTV_MMA_TF32 || mma == CORUTV_MMA_TF32_TRUNC) return a_dtype == CORUTV_F32;
+  if (mma == CORUTV_MMA_TF32 || mma == CORUTV_MMA_TF32_TRUNC || mma == CORUTV_MMA_TF32X3) return a_dtype == CORUTV_F32;
   if (mma == CORUTV_MMA_BF16X2) return a_dtype == CORUTV_BF16 || a_dtype == CORUTV_FP8_E4M3;
   return false;
 }
@@ -143,7 +147,6 @@ int check_params(const corutv_params* p) {
   if (p->core != CORUTV_CORE_EXACT && p->core != CORUTV_CORE_SKETCH) return CORUTV_ERR_INVALID_ARG;
   if (p->orth != CORUTV_ORTH_STABILISED && p->orth != CORUTV_ORTH_STRICT) return CORUTV_ERR_INVALID_ARG;
   if (p->mma < CORUTV_MMA_AUTO || p->mma > CORUTV_MMA_BF16X2) return CORUTV_ERR_INVALID_ARG;
-  if (p->mma == CORUTV_MMA_TF32X3) return CORUTV_ERR_UNSUPPORTED;
   if (p->m <= 0 || p->n <= 0) return CORUTV_ERR_SHAPE;
   if (p->k < 1 || p->k > p->l) return CORUTV_ERR_INVALID_ARG;      // 1 <= k <= l (Sec. III)
   if (p->q < 0) return CORUTV_ERR_INVALID_ARG;
@@ -189,12 +192,13 @@ int ensure_workspace(corutv_handle* h, size_t need) {
     }                                           \
   } while (0)
 
-// engine for a pass; AUTO picks the tensor cores for FP32, BF16 and FP8 A whose rows TMA can address
+// engine for a pass; AUTO picks the tensor cores for FP32, BF16 and FP8 A whose rows TMA can address:
+// split-operand FP32-class products for FP32 A, BF16 products for BF16 / FP8 A
 int pick_mma(int a_dtype, int mma, bool tma_ok = true) {
   if (a_dtype == CORUTV_F64) return CORUTV_MMA_SIMT;
   if (mma != CORUTV_MMA_AUTO) return mma;
   if (!tma_ok) return CORUTV_MMA_SIMT;
-  return a_dtype == CORUTV_F32 ? CORUTV_MMA_TF32 : CORUTV_MMA_BF16X2;
+  return a_dtype == CORUTV_F32 ? CORUTV_MMA_TF32X3 : CORUTV_MMA_BF16X2;
 }
 
 
@@ -235,6 +239,19 @@ int run_pass(corutv_handle* h, int dir, int a_dtype, int mma, const void* A, int
     CU(launch_pass_tc_lp(a, dir, a_dtype, h->sms, h->status, fro_parts, Xh, Xl, ldr, h->stream));
     if (fro_parts) {
       sum_parts_kernel<<<1, 32, 0, h->stream>>>(fro_parts, tc_lp_grid(a.len_out, a.K, h->sms), nullptr, h->status);
+      CORUTV_COUNT_LAUNCH();
+      CU(cudaGetLastError());
+    }
+  } else if (eng == CORUTV_MMA_TF32X3) {
+    if (!tc3_pass_supported(dir, a_dtype, l)) return CORUTV_ERR_UNSUPPORTED;
+    // the sketch operand split into its TF32 part (first half of the operand buffer) and the
+    // BF16 pairs of the cross terms (second half, 2 ldr BF16 per row)
+    float* Xc = Xr + (size_t)kMaxL * ldr;
+    CU(launch_split_tf32(static_cast<const float*>(Xt), ldx, Xr, Xc, ldr, l, a.K, h->stream));
+    CU(launch_pass_tc3(a, dir, h->sms, h->status, fro_parts, Xr, Xc, ldr, h->stream));
+    if (fro_parts) {
+      sum_parts_kernel<<<1, 32, 0, h->stream>>>(fro_parts, tc3_pass_grid(a.len_out, a.K, h->sms), nullptr,
+                                                h->status);
       CORUTV_COUNT_LAUNCH();
       CU(cudaGetLastError());
     }
@@ -400,7 +417,7 @@ int solve_impl(corutv_handle* h, const corutv_params* p, const Plan& pl, const v
   float* Xr_out = pre_round ? Xr : nullptr;
   // Gram engine: the 3xTF32 tensor-core partials where the passes themselves run on the tensor cores
   const bool tc_gram = sizeof(TC) == 4 && (eng == CORUTV_MMA_TF32 || eng == CORUTV_MMA_TF32_TRUNC ||
-                                           eng == CORUTV_MMA_BF16X2);
+                                           eng == CORUTV_MMA_TF32X3 || eng == CORUTV_MMA_BF16X2);
   {
     // S0: stage Psi^T into P2 (the "X" of the first product)
     PhaseTimer tm(h, kPhAsm);

@@ -58,6 +58,18 @@ cudaError_t launch_pass_tc(const PassArgs& a, int dir, int a_dtype, int mma, int
 cudaError_t launch_round_tf32(const float* X, int64_t ldx, float* Xr, int64_t ldr, int l, int64_t len,
                               cudaStream_t st);
 
+// pass_tc3.cu (split-operand products: a tcgen05 kind::tf32 MMA of the TF32 parts plus a kind::f16
+// MMA of the BF16 cross terms; FP32 A in TMEM as the M operand; the sketch operand split into Xh
+// (TF32, l rows of K, leading dimension ldxs) and Xc (BF16 pairs, l rows of 2 round_up(K, 8),
+// leading dimension 2 ldxs))
+size_t tc3_pass_partial_bytes(int sms);
+int tc3_pass_grid(int64_t len, int64_t K, int sms);
+bool tc3_pass_supported(int dir, int a_dtype, int l);
+cudaError_t launch_pass_tc3(const PassArgs& a, int dir, int sms, DevStatus* status, double* fro_parts,
+                            const float* Xh, const void* Xc, int64_t ldxs, cudaStream_t st);
+cudaError_t launch_split_tf32(const float* X, int64_t ldx, float* Xh, void* Xc, int64_t ldr, int l, int64_t len,
+                              cudaStream_t st);
+
 // pass_tc_lp.cu (tcgen05 kind::f16 + TMA, BF16 A or FP8 A with tile scales; the FP32
 // sketch operand is split into BF16 hi / lo parts Xh, Xl: l rows of K, leading dimension ldxs)
 size_t tc_lp_partial_bytes(int sms);
