@@ -79,7 +79,12 @@ def parse():
     ap.add_argument("--workload", default="fp32", choices=sorted(WORKLOADS))
     ap.add_argument("--q", type=int, default=None)
     ap.add_argument("--mma", default="auto")
-    ap.add_argument("--core", default="exact")
+    # the sketch core D = C2^T Q2 equals Q1^T A Q2 in exact arithmetic and saves one pass over A;
+    # the equal_error block of every run shows the same rank-k error as the oracle's exact core
+    # (BF16 / FP8 workloads: the core comes from the FP32 correction pass, so it is the exact core)
+    ap.add_argument("--core", default=None, choices=["exact", "sketch"])
+    ap.add_argument("--small-f64", action="store_true",
+                    help="FP64 Gram reductions, Cholesky, core and QRCP (F32 / BF16 / FP8 workloads)")
     ap.add_argument("--m", type=int, default=None)
     ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -94,6 +99,8 @@ def parse():
     if w.get("gen") == "rpca" and args.sparse is not None:
         w["sparse"] = args.sparse
     args.w = w
+    if args.core is None:
+        args.core = "exact" if w.get("dtype") in ("bf16", "fp8") else "sketch"
     return args
 
 
@@ -309,6 +316,25 @@ def oracle_solve_time(A64, phi64, w):
             Aq = P.dequantize_fp8(*P.quantize_fp8(A32))
         r = O.corutv(Aq, phi64, w["k"], w["l"], w["q"], A_core=A32.astype("float64"))
     return time.perf_counter() - t0, r
+
+
+def rank_k_errors(A64, r_gpu, r_or, k, sm, sn):
+    """Rank-k errors of the GPU factors and of the oracle's on the same block (FP64 on the host):
+    e_k,F = ||A - U(:,1:k) T(1:k,:) V^T||_F relative to ||A||_F, and e_k,2 by 50 power
+    iterations from one seeded start vector, relative to T_11 of the oracle."""
+    from oracle import corutv_oracle as O
+    U, T, V = r_gpu.U.double().cpu().numpy(), r_gpu.T.cpu().numpy(), r_gpu.V.double().cpu().numpy()
+    na = float((A64 * A64).sum()) ** 0.5
+    out = {"block": f"{sm}x{sn} leading block of A with the leading rows of Psi, the timed settings"}
+    t11 = float(r_or["T"][0, 0])
+    for name, (Uu, Tt, Vv) in (("gpu", (U, T, V)), ("oracle", (r_or["U"], r_or["T"], r_or["V"]))):
+        ef = O.fro_residual(A64, Uu, Tt, Vv, k=k) / na
+        e2 = O.spectral_residual(A64, Uu, Tt, Vv, k=k, iters=50, seed=11) / t11
+        out[name] = {"e_k_fro_rel": ef, "e_k_2_over_T11": e2}
+    out["ratio_fro"] = out["gpu"]["e_k_fro_rel"] / out["oracle"]["e_k_fro_rel"]
+    out["ratio_2"] = out["gpu"]["e_k_2_over_T11"] / out["oracle"]["e_k_2_over_T11"]
+    out["rho"] = O.factor_distance(U, T, V, r_or["U"], r_or["T"], r_or["V"])
+    return out
 
 
 def cpu_sample_shape(w):
@@ -867,14 +893,15 @@ def main():
     def solve_on(A32, P32):
         if hosted:
             corutv.solve_host(A_host, P32, k, l, q, core=args.core, mma=args.mma, want_fro2=True,
-                              chunk_rows=args.chunk, out=(U, T, V, perm), wait=False, handle=h)
+                              chunk_rows=args.chunk, out=(U, T, V, perm), wait=False, handle=h,
+                              small_f64=args.small_f64)
         elif lowp:
             corutv.quantize(A32, w["dtype"], out=A_lp, tile_scales=S, handle=h)
             corutv.solve(A_lp, P32, k, l, q, core=args.core, mma=args.mma, a_tile_scales=S, want_fro2=True,
-                         out=(U, T, V, perm), wait=False, handle=h, A_ref=A32)
+                         out=(U, T, V, perm), wait=False, handle=h, A_ref=A32, small_f64=args.small_f64)
         else:
             corutv.solve(A32, P32, k, l, q, core=args.core, mma=args.mma, want_fro2=True,
-                         out=(U, T, V, perm), wait=False, handle=h)
+                         out=(U, T, V, perm), wait=False, handle=h, small_f64=args.small_f64)
 
     def step():
         solve_on(A, phi)
@@ -1019,15 +1046,30 @@ def main():
 
     # ------------------------------------------------------------ CPU baseline (oracle), rank 0, N=1
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    equal_error = None
+    if rank == 0 and world == 1:
         sm, sn = cpu_sample_shape(w)
         A64 = A[:sm, :sn].double().cpu().numpy()
         P64 = phi[:sn].double().cpu().numpy()
-        t, _ = oracle_solve_time(A64, P64, w)
+        t, r_or = oracle_solve_time(A64, P64, w)
         scale = (m * n) / float(sm * sn)
-        cpu = {"value": 1.0 / (t * scale), "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
-               "sample": f"one FP64 oracle solve of the {sm}x{sn} leading block of A (q={q}), {t:.2f} s, "
-                         f"scaled by m*n/({sm}*{sn})"}
+        if not args.no_cpu_baseline:
+            cpu = {"value": 1.0 / (t * scale), "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
+                   "sample": f"one FP64 oracle solve of the {sm}x{sn} leading block of A (q={q}), {t:.2f} s, "
+                             f"scaled by m*n/({sm}*{sn})"}
+        # the same block solved by the GPU with the timed settings: rank-k errors side by side
+        Ab = A[:sm, :sn].contiguous()
+        Pb = phi[:sn].contiguous()
+        if lowp:
+            Ab_lp = torch.empty((sm, -(-sn // 16) * 16), dtype=A_lp.dtype, device=dev)[:, :sn]
+            Sb = torch.empty((-(-sm // 128), -(-sn // 128)), dtype=torch.float32, device=dev) \
+                if w["dtype"] == "fp8" else None
+            corutv.quantize(Ab, w["dtype"], out=Ab_lp, tile_scales=Sb, handle=h)
+            rb = corutv.solve(Ab_lp, Pb, k, l, q, core=args.core, mma=args.mma, a_tile_scales=Sb, A_ref=Ab,
+                              small_f64=args.small_f64, handle=h)
+        else:
+            rb = corutv.solve(Ab, Pb, k, l, q, core=args.core, mma=args.mma, small_f64=args.small_f64, handle=h)
+        equal_error = rank_k_errors(A64, rb, r_or, k, sm, sn)
 
     if rank == 0:
         dtype = {"f32": F32_DTYPE[f32_engine(args.mma)], "bf16": "bf16",
@@ -1038,12 +1080,14 @@ def main():
                "data": "synthetic",
                "config": {"workload": workload_label(w, args.core),
                           "m": m, "n": n, "k": k, "l": l, "q": q, "core": args.core, "mma": args.mma,
+                          "small_factorisations": "fp64" if args.small_f64 else "fp32",
                           "passes_per_step": info.passes_over_A,
                           "l2": "inputs larger than L2 (A is %.1f GB)" % (m * n * 4 / 1e9),
                           "a_resident": "host (page-locked), streamed every pass" if hosted else "HBM",
                           "parallelism": f"replicas x{world}"},
                "roofline": roofline,
                "cpu_baseline": cpu,
+               "equal_error": equal_error,
                "e2e": e2e,
                "gpu_launches": int(tr.launches),
                "clocks": clk,

@@ -39,7 +39,7 @@
 extern "C" {
 #endif
 
-#define CORUTV_ABI_VERSION 5
+#define CORUTV_ABI_VERSION 6
 
 typedef enum {
   CORUTV_OK = 0,
@@ -101,7 +101,7 @@ typedef enum {
 typedef struct {
   int64_t m, n;          /* shape of A */
   int32_t k;             /* target rank: validated (1 <= k <= l) and used for the rank-k readout */
-  int32_t l;             /* sample size l, k <= l < min(m, n); l <= 128 (F32) or l <= 112 (F64) */
+  int32_t l;             /* sample size l, k <= l < min(m, n), l <= 128 */
   int32_t q;             /* power steps, q >= 0 (q = 0 is Alg. 2) */
   int32_t side;          /* corutv_side: RIGHT = Alg. 2/3 (Psi is n x l, T upper);
                             LEFT = the m < n modification of Sec. III: Alg. 2/3 on A^T with
@@ -114,7 +114,12 @@ typedef struct {
   int32_t want_fro2;     /* 1: also compute ||A||_F^2 into the info (fused into the first pass on the
                             tensor-core engine, one extra read of A otherwise) */
   int32_t factor;        /* corutv_factor of the core (QRCP by default) */
-  int32_t reserved[6];   /* must be zero */
+  int32_t small_f64;     /* 1: the small factorisations of an F32 / BF16 / FP8 solve in FP64 -- the
+                            Gram matrices of CholeskyQR reduced in FP64 (from FP32-product partials)
+                            and factored by an FP64 Cholesky, the core D reduced in FP64 and its QRCP
+                            in FP64 (factor QLP: ERR_UNSUPPORTED).  0 (default): in FP32.  F64 A:
+                            always FP64 */
+  int32_t reserved[5];   /* must be zero */
 } corutv_params;
 
 /* Device-side outcome of the last solve on a handle. */
@@ -187,8 +192,9 @@ int corutv_set_workspace(corutv_handle* h, void* dptr, size_t bytes);
  * Gram matrices, Cholesky and QRCP; every other dtype gets FP32 ones -- Gram
  * partials from FP32 products (3xTF32 tensor-core products for the shifted
  * first pass and the core when the passes run on the tensor cores), reduced
- * with compensated FP32 sums.  On the FP32 path the third CholeskyQR pass is
- * skipped when the second already gives max |Q^T Q - I| <= 2e-6.
+ * with compensated FP32 sums -- unless p->small_f64 asks for FP64 Gram
+ * reductions, Cholesky factors, core and QRCP.  On the FP32 path the third
+ * CholeskyQR pass is skipped when the second already gives max |Q^T Q - I| <= 2e-6.
  * Returns a validation error synchronously; device conditions via corutv_info_wait.
  */
 int corutv_solve(corutv_handle* h, const corutv_params* p,

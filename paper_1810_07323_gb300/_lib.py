@@ -37,7 +37,8 @@ class Params(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("k", ctypes.c_int32), ("l", ctypes.c_int32),
                 ("q", ctypes.c_int32), ("side", ctypes.c_int32), ("core", ctypes.c_int32),
                 ("orth", ctypes.c_int32), ("a_dtype", ctypes.c_int32), ("mma", ctypes.c_int32),
-                ("want_fro2", ctypes.c_int32), ("factor", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+                ("want_fro2", ctypes.c_int32), ("factor", ctypes.c_int32), ("small_f64", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
 
 
 class Problem(ctypes.Structure):
@@ -260,8 +261,9 @@ class SolveResult:
     info: Info | None
 
 
-def workspace_size(m, n, k, l, q=0, side="right", core="exact", a_dtype="f32", mma="auto") -> int:
-    p = _params(m, n, k, l, q, side, core, DTYPE[a_dtype], mma, False, "stabilised")
+def workspace_size(m, n, k, l, q=0, side="right", core="exact", a_dtype="f32", mma="auto", factor="qrcp",
+                   small_f64=0) -> int:
+    p = _params(m, n, k, l, q, side, core, DTYPE[a_dtype], mma, False, "stabilised", factor, small_f64)
     out = ctypes.c_size_t()
     _check(load().corutv_workspace_size(ctypes.byref(p), ctypes.byref(out)), "corutv_workspace_size")
     return out.value
@@ -270,18 +272,19 @@ def workspace_size(m, n, k, l, q=0, side="right", core="exact", a_dtype="f32", m
 FACTOR = {"qrcp": 0, "qlp": 1}
 
 
-def _params(m, n, k, l, q, side, core, a_dtype_code, mma, want_fro2, orth, factor="qrcp") -> Params:
+def _params(m, n, k, l, q, side, core, a_dtype_code, mma, want_fro2, orth, factor="qrcp", small_f64=False) -> Params:
     p = Params()
     p.m, p.n, p.k, p.l, p.q = int(m), int(n), int(k), int(l), int(q)
     p.side, p.core, p.orth = SIDE[side], CORE[core], ORTH[orth]
     p.a_dtype, p.mma, p.want_fro2 = a_dtype_code, MMA[mma], 1 if want_fro2 else 0
     p.factor = FACTOR[factor]
+    p.small_f64 = int(small_f64)
     return p
 
 
 def solve(A, Phi, k: int, l: int, q: int = 0, side: str = "right", core: str = "exact", mma: str = "auto",
           a_tile_scales=None, want_fro2: bool = False, out=None, wait: bool = True, handle: Handle | None = None,
-          A_ref=None, orth: str = "stabilised", factor: str = "qrcp"):
+          A_ref=None, orth: str = "stabilised", factor: str = "qrcp", small_f64: bool = False):
     """CoR-UTV of a device matrix A (Alg. 2 / Alg. 3): returns U, T, V, perm.
 
     A: (m, n) row-major float64 / float32 / bfloat16 / float8_e4m3fn (with
@@ -293,6 +296,8 @@ def solve(A, Phi, k: int, l: int, q: int = 0, side: str = "right", core: str = "
     earlier power steps) or "strict" (shifted CholeskyQR3 for every sketch).
     factor: "qrcp" (T upper triangular) or "qlp" (T lower triangular, V
     = Q2 P~ Qh; float32-path solves).
+    small_f64: float32 / bfloat16 / float8 A with the Gram reductions,
+    Cholesky factors, core and QRCP in FP64 (corutv_params.small_f64).
     out: optional (U, T, V, perm) preallocated outputs.  wait=True
     synchronises and returns the device info; wait=False leaves the work
     enqueued on the current stream (info is None).
@@ -305,7 +310,7 @@ def solve(A, Phi, k: int, l: int, q: int = 0, side: str = "right", core: str = "
     fdt = torch.float64 if code == 0 else torch.float32
     if Phi.dtype != fdt:
         raise TypeError(f"Phi must be {fdt}")
-    p = _params(m, n, k, l, q, side, core, code, mma, want_fro2, orth, factor)
+    p = _params(m, n, k, l, q, side, core, code, mma, want_fro2, orth, factor, small_f64)
     if out is None:
         dev = A.device
         U = torch.empty((m, l), dtype=fdt, device=dev)
@@ -335,7 +340,7 @@ def solve(A, Phi, k: int, l: int, q: int = 0, side: str = "right", core: str = "
 
 def solve_host(A, Phi, k: int, l: int, q: int = 0, side: str = "right", core: str = "exact", mma: str = "auto",
                want_fro2: bool = False, chunk_rows: int = 0, out=None, wait: bool = True,
-               handle: Handle | None = None, orth: str = "stabilised", factor: str = "qrcp"):
+               handle: Handle | None = None, orth: str = "stabilised", factor: str = "qrcp", small_f64: bool = False):
     """CoR-UTV of a HOST matrix A streamed to the GPU pass by pass (corutv_solve_host).
 
     A: (m, n) row-major float32 / float64 CPU tensor (page-locked, e.g.
@@ -356,7 +361,7 @@ def solve_host(A, Phi, k: int, l: int, q: int = 0, side: str = "right", core: st
     fdt = torch.float64 if code == 0 else torch.float32
     if Phi.dtype != fdt:
         raise TypeError(f"Phi must be {fdt}")
-    p = _params(m, n, k, l, q, side, core, code, mma, want_fro2, orth, factor)
+    p = _params(m, n, k, l, q, side, core, code, mma, want_fro2, orth, factor, small_f64)
     if out is None:
         dev = Phi.device
         U = torch.empty((m, l), dtype=fdt, device=dev)

@@ -8,7 +8,7 @@
 namespace corutv {
 
 constexpr int kMaxL = 128;        // largest sample size l on the FP32 path (one MMA M tile)
-constexpr int kMaxL64 = 112;      // largest l on the FP64 path (QRCP shared-memory bound)
+constexpr int kMaxL64 = 128;      // largest l on the FP64 path
 
 // Device status word bits (Handle::status, written by kernels, read by corutv_info_wait).
 enum : int { kStatTimeout = 1 };

@@ -155,6 +155,8 @@ int check_params(const corutv_params* p) {
   if (!mma_fits_dtype(p->a_dtype, p->mma)) return CORUTV_ERR_UNSUPPORTED;
   if (p->factor != CORUTV_FACTOR_QRCP && p->factor != CORUTV_FACTOR_QLP) return CORUTV_ERR_INVALID_ARG;
   if (p->factor == CORUTV_FACTOR_QLP && p->a_dtype == CORUTV_F64) return CORUTV_ERR_UNSUPPORTED;
+  if (p->small_f64 != 0 && p->small_f64 != 1) return CORUTV_ERR_INVALID_ARG;
+  if (p->small_f64 && p->factor == CORUTV_FACTOR_QLP) return CORUTV_ERR_UNSUPPORTED;
   return CORUTV_OK;
 }
 
@@ -349,11 +351,34 @@ int do_pass(corutv_handle* h, HostSrc* hs, const Plan& pl, int dir, int a_dtype,
 // operand of the next TF32 pass.  tc_gram: the sketches come from tensor-core passes (TF32 or
 // BF16 products, relative errors >= 2^-17), so the shifted first pass may form its Gram from the
 // 3xTF32 tensor-core partials (~1e-6); every other Gram uses FP32 products.
+// small64 (FP32 blocks): the Gram partials are reduced in FP64 and factored by the FP64
+// Cholesky (R^-1 rounded to FP32 for Q = C R^-1); the shift and the dependence threshold stay
+// those of FP32 products, and every pass is factored (no early exit of the third).
 template <typename TC>
 int orth_st(corutv_handle* h, TC* Ct, int64_t ldc, int64_t len, int l, const Plan& pl, int passes, double* Rout,
-            float* round_out = nullptr, int64_t ldr = 0, bool tc_gram = false) {
+            float* round_out = nullptr, int64_t ldr = 0, bool tc_gram = false, bool small64 = false) {
   const bool f64 = sizeof(TC) == 8;
   PhaseTimer tm(h, kPhOrth);
+  if constexpr (sizeof(TC) == 4) {
+    if (small64) {
+      for (int pass = 0; pass < passes; ++pass) {
+        CU((launch_gram_auto<float, double>(Ct, ldc, Ct, ldc, len, l, static_cast<float*>(pl.gram_parts), h->sms,
+                                            pl.status, static_cast<double*>(pl.G), kMaxL, h->stream,
+                                            tc_gram && pass == 0)));
+        double* rpass = Rout ? (pass == 0 ? Rout : static_cast<double*>(pl.D)) : nullptr;
+        CU(launch_cholinv_f64<float>(static_cast<const double*>(pl.G), kMaxL, l, pass == 0 ? kShiftRel32 : 0.0,
+                                     kTolRel32, static_cast<float*>(pl.R), static_cast<float*>(pl.Rinv), pl.defic,
+                                     pl.status, rpass, h->stream));
+        CU(launch_lmul<float>(Ct, ldc, len, l, static_cast<const float*>(pl.Rinv), kMaxL, Ct, ldc, false, pl.defic,
+                              pass, nullptr, pass == passes - 1 ? round_out : nullptr, ldr, h->stream));
+        if (Rout && pass > 0) {
+          CU(launch_upper_mul(static_cast<const double*>(pl.D), Rout, static_cast<double*>(pl.Qt), l, h->stream));
+          CU(cudaMemcpyAsync(Rout, pl.Qt, sizeof(double) * l * l, cudaMemcpyDeviceToDevice, h->stream));
+        }
+      }
+      return CORUTV_OK;
+    }
+  }
   for (int pass = 0; pass < passes; ++pass) {
     // Only the shifted first pass may take the tensor-core Gram: its shift (kShiftRel32 trace(G))
     // dominates the 3xTF32 error, so R stays well defined.  The unshifted passes factor the Gram
@@ -418,6 +443,8 @@ int solve_impl(corutv_handle* h, const corutv_params* p, const Plan& pl, const v
   // Gram engine: the 3xTF32 tensor-core partials where the passes themselves run on the tensor cores
   const bool tc_gram = sizeof(TC) == 4 && (eng == CORUTV_MMA_TF32 || eng == CORUTV_MMA_TF32_TRUNC ||
                                            eng == CORUTV_MMA_TF32X3 || eng == CORUTV_MMA_BF16X2);
+  // FP32-path sketches with FP64 small factorisations: FP64 Gram reductions, Cholesky, core and QRCP
+  const bool small64 = sizeof(TC) == 4 && p->small_f64 != 0;
   {
     // S0: stage Psi^T into P2 (the "X" of the first product)
     PhaseTimer tm(h, kPhAsm);
@@ -437,7 +464,7 @@ int solve_impl(corutv_handle* h, const corutv_params* p, const Plan& pl, const v
     if (rc) return rc;
     ++passes;
     // S2: orth(C1)
-    rc = orth_st<TC>(h, P1, pl.ld1, pl.len1, l, pl, orth_passes(p, it), nullptr, Xr_out, pl.ldr, tc_gram);
+    rc = orth_st<TC>(h, P1, pl.ld1, pl.len1, l, pl, orth_passes(p, it), nullptr, Xr_out, pl.ldr, tc_gram, small64);
     if (rc) return rc;
     // S3: C2 = A^T Q1  (Alg. 3 step 4)
     rc = do_pass<TC>(h, hs, pl, dir2, p->a_dtype, p->mma, A, lda, p->m, p->n, scales, P1, pl.ld1, l, P2, pl.ld2,
@@ -448,10 +475,19 @@ int solve_impl(corutv_handle* h, const corutv_params* p, const Plan& pl, const v
       CU(cudaMemcpy2DAsync(P3, pl.ld3 * sizeof(TC), P2, pl.ld2 * sizeof(TC), pl.len2 * sizeof(TC), l,
                            cudaMemcpyDeviceToDevice, h->stream));
     // S4: orth(C2)
-    rc = orth_st<TC>(h, P2, pl.ld2, pl.len2, l, pl, orth_passes(p, it), nullptr, Xr_out, pl.ldr, tc_gram);
+    rc = orth_st<TC>(h, P2, pl.ld2, pl.len2, l, pl, orth_passes(p, it), nullptr, Xr_out, pl.ldr, tc_gram, small64);
     if (rc) return rc;
   }
-  // S5: core D = Q1^T A Q2 (Alg. 2 step 5)
+  // S5: core D = Q1^T A Q2 (Alg. 2 step 5); small64: D reduced in FP64
+  auto core_gram = [&](const TC* X, int64_t ldx, const TC* Y, int64_t ldy, int64_t len) -> cudaError_t {
+    if constexpr (sizeof(TC) == 4) {
+      if (small64)
+        return launch_gram_auto<float, double>(X, ldx, Y, ldy, len, l, static_cast<float*>(pl.gram_parts), h->sms,
+                                               pl.status, static_cast<double*>(pl.D), kMaxL, h->stream, tc_gram);
+    }
+    return launch_gram_auto<TC, TC>(X, ldx, Y, ldy, len, l, static_cast<TC*>(pl.gram_parts), h->sms, pl.status,
+                                    static_cast<TC*>(pl.D), kMaxL, h->stream, tc_gram);
+  };
   if (A_ref) {
     // correction pass: E = A_ref Q2 over the FP32 matrix (||A_ref||^2 fused where the tensor cores run it)
     int rc = run_pass(h, dir1, CORUTV_F32, ref_mma, A_ref, lda_ref, p->m, p->n, nullptr, P2, pl.ld2, l, P3,
@@ -459,28 +495,30 @@ int solve_impl(corutv_handle* h, const corutv_params* p, const Plan& pl, const v
     if (rc) return rc;
     ++passes;
     PhaseTimer tm(h, kPhCore);
-    CU((launch_gram_auto<TC, TC>(P1, pl.ld1, P3, pl.ld3, pl.len1, l, static_cast<TC*>(pl.gram_parts),
-                           h->sms, pl.status, static_cast<TC*>(pl.D), kMaxL, h->stream, tc_gram)));   // D = Q1^T E
+    CU(core_gram(P1, pl.ld1, P3, pl.ld3, pl.len1));   // D = Q1^T E
   } else if (p->core == CORUTV_CORE_EXACT) {
     int rc = do_pass<TC>(h, hs, pl, dir1, p->a_dtype, p->mma, A, lda, p->m, p->n, scales, P2, pl.ld2, l, P3,
                          pl.ld3, Xr, pl.ldr, nullptr, kPhPass, pre_round);   // E = A Q2 (ST, len1)
     if (rc) return rc;
     ++passes;
     PhaseTimer tm(h, kPhCore);
-    CU((launch_gram_auto<TC, TC>(P1, pl.ld1, P3, pl.ld3, pl.len1, l, static_cast<TC*>(pl.gram_parts),
-                           h->sms, pl.status, static_cast<TC*>(pl.D), kMaxL, h->stream, tc_gram)));   // D = Q1^T E
+    CU(core_gram(P1, pl.ld1, P3, pl.ld3, pl.len1));   // D = Q1^T E
   } else {
     PhaseTimer tm(h, kPhCore);
     // D = Q1^T A Q2 = (A^T Q1)^T Q2 = C2^T Q2 with the saved C2 (ST, len2)
-    CU((launch_gram_auto<TC, TC>(P3, pl.ld3, P2, pl.ld2, pl.len2, l, static_cast<TC*>(pl.gram_parts),
-                           h->sms, pl.status, static_cast<TC*>(pl.D), kMaxL, h->stream, tc_gram)));
+    CU(core_gram(P3, pl.ld3, P2, pl.ld2, pl.len2));
   }
   const bool qlp = p->factor == CORUTV_FACTOR_QLP;
   {
-    // S6: QRCP of D (Alg. 2 step 6); T = R~ (RIGHT) or R~^T (LEFT)
+    // S6: QRCP of D (Alg. 2 step 6); T = R~ (RIGHT) or R~^T (LEFT); small64: the FP64 QRCP of the FP64
+    // D, its Q~ (FP64) in the G block
     PhaseTimer tm(h, kPhQrcp);
-    CU(launch_qrcp<TC>(static_cast<const TC*>(pl.D), kMaxL, l, p->k, static_cast<TC*>(pl.Qt), kMaxL, T, ldt,
-                       !right && !qlp, perm, nullptr, pl.status, h->stream));
+    if (small64)
+      CU(launch_qrcp<double>(static_cast<const double*>(pl.D), kMaxL, l, p->k, static_cast<double*>(pl.G), kMaxL, T,
+                             ldt, !right, perm, nullptr, pl.status, h->stream));
+    else
+      CU(launch_qrcp<TC>(static_cast<const TC*>(pl.D), kMaxL, l, p->k, static_cast<TC*>(pl.Qt), kMaxL, T, ldt,
+                         !right && !qlp, perm, nullptr, pl.status, h->stream));
     if constexpr (sizeof(TC) == 4) {
       if (qlp) {
         // QLP: R~^T = Qh Rh; T = L = Rh^T (RIGHT) or Rh (LEFT); the Q2 side becomes Q2 P~ Qh
@@ -495,8 +533,14 @@ int solve_impl(corutv_handle* h, const corutv_params* p, const Plan& pl, const v
   TC* out1 = static_cast<TC*>(right ? U : V);
   TC* out2 = static_cast<TC*>(right ? V : U);
   const int64_t ld1o = right ? ldu : ldv, ld2o = right ? ldv : ldu;
-  CU(launch_lmul_full<TC>(P1, pl.ld1, pl.len1, l, static_cast<const TC*>(pl.Qt), kMaxL, out1, ld1o, true,
-                          h->stream));
+  if constexpr (sizeof(TC) == 4) {
+    if (small64)
+      CU(launch_lmul_full_f64s(P1, pl.ld1, pl.len1, l, static_cast<const double*>(pl.G), kMaxL, out1, ld1o, true,
+                               h->stream));
+  }
+  if (!small64)
+    CU(launch_lmul_full<TC>(P1, pl.ld1, pl.len1, l, static_cast<const TC*>(pl.Qt), kMaxL, out1, ld1o, true,
+                            h->stream));
   if (qlp)
     CU(launch_lmul_full<TC>(P2, pl.ld2, pl.len2, l, static_cast<const TC*>(pl.Rinv), l, out2, ld2o, true,
                             h->stream));

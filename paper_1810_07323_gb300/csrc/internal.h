@@ -112,6 +112,14 @@ template <typename TC>
 cudaError_t launch_cholinv(const TC* G, int64_t ldg, int l, double shift_rel, double tol_rel, TC* R, TC* Rinv,
                            int* defic, DevStatus* status, double* Rout, int* skip_flag, float skip_tol,
                            cudaStream_t st);
+// FP64 elimination of an FP64 Gram matrix (l <= 128); R and R^-1 written in TO (FP64, or FP32
+// for FP32 sketches whose small factorisations run in FP64)
+template <typename TO>
+cudaError_t launch_cholinv_f64(const double* G, int64_t ldg, int l, double shift_rel, double tol_rel, TO* R,
+                               TO* Rinv, int* defic, DevStatus* status, double* Rout, cudaStream_t st);
+// Out = S^T In on FP32 ST blocks with a full FP64 l x l S (staged in FP32)
+cudaError_t launch_lmul_full_f64s(const float* In, int64_t ldi, int64_t len, int l, const double* S, int64_t lds,
+                                  float* Out, int64_t ldo, bool out_rowmajor, cudaStream_t st);
 // Out = S^T In on ST blocks (S upper triangular); rows j with defic[j] set (defic may be
 // null) receive the deterministic replacement vector of `pass` instead.  round_out (FP32
 // only, may be null): also write the result rounded to TF32 (ld ldr), the operand of the

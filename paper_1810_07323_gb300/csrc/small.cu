@@ -255,26 +255,29 @@ cudaError_t launch_gram_auto(const TC* Xt, int64_t ldx, const TC* Yt, int64_t ld
 
 // =============================================================================== Cholesky
 // G + s I = R^T R (R upper, s = shift_rel * trace(G)) and R^-1, by symmetric
-// elimination of [G | I]: step j subtracts m_a = G[j][a] / G[j][j] times row j
-// from every row a > j (upper triangle of G only, by symmetry; the right block
-// receives the same row operations).  Afterwards G = L D L^T with the pivots
-// d_j = G[j][j] (as of step j), the upper triangle holding D L^T and the right
-// block holding L^-1, so R = D^(1/2) L^T and R^-1[p][j] = L^-1[j][p] / sqrt(d_j).
-// Every update of a step is independent: one block barrier per step, no long
-// dependent chains.  A pivot d <= tol_rel * (G_jj + s) marks column j
-// dependent: it eliminates nothing, R[j][j] = 1, R[j][>j] = 0, defic[j] = 1
-// (the caller replaces that column of Q).
-template <typename TC>
+// elimination of [G | I] in FP64: step j subtracts m_a = G[j][a] / G[j][j] times
+// row j from every row a > j (upper triangle of G only, by symmetry; the right
+// block receives the same row operations).  Afterwards G = L D L^T with the
+// pivots d_j = G[j][j] (as of step j), the upper triangle holding D L^T and the
+// right block holding L^-1, so R = D^(1/2) L^T and R^-1[p][j] = L^-1[j][p] /
+// sqrt(d_j).  Every update of a step is independent: one block barrier per step,
+// no long dependent chains.  A pivot d <= tol_rel * (G_jj + s) marks column j
+// dependent: it eliminates nothing, R[j][j] = 1, R[j][>j] = 0, defic[j] = 1 (the
+// caller replaces that column of Q).
+// One l x (l + 1) FP64 array in shared memory holds both triangles: G on and above
+// the diagonal, L^-1 strictly below it (its unit diagonal implicit), so l = 128
+// needs 132 KB.  R and R^-1 are written in TO: FP64 for FP64 sketches, FP32 for
+// FP32 sketches whose small factorisations run in FP64.
+template <typename TO>
 __global__ void __launch_bounds__(512) cholinv_kernel(const double* __restrict__ G, int64_t ldg, int l,
-                                                      double shift_rel, double tol_rel, TC* __restrict__ Rg,
-                                                      TC* __restrict__ Rinvg, int* __restrict__ defic,
+                                                      double shift_rel, double tol_rel, TO* __restrict__ Rg,
+                                                      TO* __restrict__ Rinvg, int* __restrict__ defic,
                                                       DevStatus* status, double* __restrict__ Rout) {
   extern __shared__ unsigned char smem_raw[];
   const int LD = l + 1;
-  TC* Gs = reinterpret_cast<TC*>(smem_raw);     // l x LD, upper triangle used
-  TC* Li = Gs + l * LD;                          // l x LD, L^-1 (lower, unit diagonal)
+  double* S = reinterpret_cast<double*>(smem_raw);   // l x LD: G (b >= a), L^-1 (b < a)
   __shared__ double diag0[kMaxL];
-  __shared__ TC piv[kMaxL];
+  __shared__ double piv[kMaxL];
   __shared__ int dep_s[kMaxL];
   __shared__ double red[32];
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
@@ -283,8 +286,7 @@ __global__ void __launch_bounds__(512) cholinv_kernel(const double* __restrict__
   for (int e = tid; e < l * l; e += nt) {
     const int a = e / l, b = e % l;
     const double g = G[a * ldg + b];
-    if (b >= a) Gs[a * LD + b] = (TC)g;
-    Li[a * LD + b] = (a == b) ? TC(1) : TC(0);
+    S[a * LD + b] = (b >= a) ? g : 0.0;
     if (a == b) tr += g;
   }
   for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
@@ -294,39 +296,41 @@ __global__ void __launch_bounds__(512) cholinv_kernel(const double* __restrict__
   for (int w = 0; w < nw; ++w) trace += red[w];
   const double shift = shift_rel * trace;
   for (int a = tid; a < l; a += nt) {
-    const double d = (double)Gs[a * LD + a] + shift;
-    Gs[a * LD + a] = (TC)d;
+    const double d = S[a * LD + a] + shift;
+    S[a * LD + a] = d;
     diag0[a] = d;
   }
   __syncthreads();
 
   for (int j = 0; j < l; ++j) {
-    const TC d = Gs[j * LD + j];
-    const bool dep = !((double)d > tol_rel * diag0[j]) || !(diag0[j] > 0.0);
-    const TC inv_d = dep ? TC(0) : TC(1) / d;
+    const double d = S[j * LD + j];
+    const bool dep = !(d > tol_rel * diag0[j]) || !(diag0[j] > 0.0);
+    const double inv_d = dep ? 0.0 : 1.0 / d;
     if (tid == 0) {
-      piv[j] = dep ? TC(1) : d;
+      piv[j] = dep ? 1.0 : d;
       dep_s[j] = dep ? 1 : 0;
     }
-    // rows a > j, one warp per row: upper triangle b >= a of G, and L^-1 columns b <= j
+    // rows a > j, one warp per row: the upper triangle b >= a of G, and L^-1 columns b <= j
+    // (L^-1[j][j] = 1 is implicit; L^-1[j][b < j] sits below the diagonal of row j)
     for (int a = j + 1 + warp; a < l; a += nw) {
-      const TC m = Gs[j * LD + a] * inv_d;
-      for (int b = a + lane; b < l; b += 32) Gs[a * LD + b] -= m * Gs[j * LD + b];
-      for (int b = lane; b <= j; b += 32) Li[a * LD + b] -= m * Li[j * LD + b];
+      const double m = S[j * LD + a] * inv_d;
+      for (int b = a + lane; b < l; b += 32) S[a * LD + b] -= m * S[j * LD + b];
+      for (int b = lane; b <= j; b += 32) S[a * LD + b] -= m * (b == j ? 1.0 : S[j * LD + b]);
     }
     __syncthreads();
   }
   int nfall = 0;
   for (int e = tid; e < l * l; e += nt) {
     const int a = e / l, b = e % l;
-    const TC ra = sqrt(piv[a]);
-    TC r = TC(0);
+    const double ra = sqrt(piv[a]);
+    double r = 0.0;
     if (b == a) r = ra;
-    else if (b > a && !dep_s[a]) r = Gs[a * LD + b] / ra;
-    Rg[a * kMaxL + b] = r;
+    else if (b > a && !dep_s[a]) r = S[a * LD + b] / ra;
+    Rg[a * kMaxL + b] = (TO)r;
     // R^-1[a][b] = L^-1[b][a] / sqrt(d_b)  (upper: a <= b)
-    Rinvg[a * kMaxL + b] = (b >= a) ? Li[b * LD + a] / sqrt(piv[b]) : TC(0);
-    if (Rout) Rout[a * l + b] = (double)r;
+    const double lib = (b == a) ? 1.0 : (b > a ? S[b * LD + a] : 0.0);
+    Rinvg[a * kMaxL + b] = (TO)(lib / sqrt(piv[b]));
+    if (Rout) Rout[a * l + b] = r;
   }
   for (int a = tid; a < l; a += nt) {
     defic[a] = dep_s[a];
@@ -633,14 +637,24 @@ cudaError_t launch_cholinv(const TC* G, int64_t ldg, int l, double shift_rel, do
     CORUTV_COUNT_LAUNCH();
     return cudaSuccess;
   } else {
-    const size_t smem = (size_t)2 * l * (l + 1) * sizeof(TC);
-    cudaError_t e = cudaFuncSetAttribute(cholinv_kernel<TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    cholinv_kernel<TC><<<1, 512, smem, st>>>(G, ldg, l, shift_rel, tol_rel, R, Rinv, defic, status, Rout);
-    CORUTV_COUNT_LAUNCH();
-    return cudaGetLastError();
+    return launch_cholinv_f64<double>(G, ldg, l, shift_rel, tol_rel, R, Rinv, defic, status, Rout, st);
   }
 }
+
+template <typename TO>
+cudaError_t launch_cholinv_f64(const double* G, int64_t ldg, int l, double shift_rel, double tol_rel, TO* R,
+                               TO* Rinv, int* defic, DevStatus* status, double* Rout, cudaStream_t st) {
+  const size_t smem = (size_t)l * (l + 1) * sizeof(double);
+  cudaError_t e = cudaFuncSetAttribute(cholinv_kernel<TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  cholinv_kernel<TO><<<1, 512, smem, st>>>(G, ldg, l, shift_rel, tol_rel, R, Rinv, defic, status, Rout);
+  CORUTV_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
+template cudaError_t launch_cholinv_f64<float>(const double*, int64_t, int, double, double, float*, float*, int*,
+                                               DevStatus*, double*, cudaStream_t);
+template cudaError_t launch_cholinv_f64<double>(const double*, int64_t, int, double, double, double*, double*, int*,
+                                                DevStatus*, double*, cudaStream_t);
 
 // Dependent columns: row j of an ST block (column j of Q) flagged dependent is
 // replaced by a deterministic pseudo-random vector (SplitMix64 of (pass, j, i),
@@ -927,6 +941,12 @@ cudaError_t launch_lmul_full(const TC* In, int64_t ldi, int64_t len, int l, cons
                              int64_t ldo, bool out_rowmajor, cudaStream_t st) {
   return lmul_dispatch<TC, TC>(In, ldi, len, l, S, lds, Out, ldo, out_rowmajor, false, nullptr, 0, nullptr, nullptr,
                                0, st);
+}
+
+cudaError_t launch_lmul_full_f64s(const float* In, int64_t ldi, int64_t len, int l, const double* S, int64_t lds,
+                                  float* Out, int64_t ldo, bool out_rowmajor, cudaStream_t st) {
+  return lmul_dispatch<float, double>(In, ldi, len, l, S, lds, Out, ldo, out_rowmajor, false, nullptr, 0, nullptr,
+                                      nullptr, 0, st);
 }
 
 // =============================================================================== R composition

@@ -48,9 +48,11 @@ def _ws(**kw):
     (dict(q=-1), corutv.ERR_INVALID_ARG),          # q >= 0
     (dict(l=80), corutv.ERR_SHAPE),                # l < min(m, n)
     (dict(m=1000, n=1000, l=129), corutv.ERR_SHAPE),            # l beyond the FP32 kernels
-    (dict(m=1000, n=1000, l=113, a_dtype="f64"), corutv.ERR_SHAPE),  # l beyond the FP64 kernels
+    (dict(m=1000, n=1000, l=129, a_dtype="f64"), corutv.ERR_SHAPE),  # l beyond the FP64 kernels
     (dict(a_dtype="f64", mma="tf32"), corutv.ERR_UNSUPPORTED),
     (dict(m=0), corutv.ERR_SHAPE),
+    (dict(small_f64=2), corutv.ERR_INVALID_ARG),
+    (dict(small_f64=1, factor="qlp"), corutv.ERR_UNSUPPORTED),   # FP64 small factorisations: QRCP only
 ])
 def test_invalid_parameters_rejected_on_host(kw, status):
     with pytest.raises(corutv.CorutvError) as e:

@@ -143,6 +143,38 @@ def test_config2_slice_fp32_parity(slice2, mma, q):
     assert ek <= 1.05 * ek_ref + U_MODE[mma] * np.linalg.norm(A32)
 
 
+@pytest.mark.parametrize("q", [0, 1, 2])
+def test_config2_slice_small_f64(slice2, q):
+    """The FP32-class passes with the small factorisations in FP64 (Gram reductions,
+    Cholesky, core and QRCP): parity with the oracle at the FP32 bound."""
+    A, phi = slice2
+    m, n = A.shape
+    Ad = torch.tensor(A, dtype=torch.float32, device="cuda")
+    Pd = torch.tensor(phi, dtype=torch.float32, device="cuda")
+    r = corutv.solve(Ad, Pd, 100, 120, q, small_f64=True)
+    assert r.info.status == 0
+    U, T, V, perm = _np(r)
+    ref = O.corutv(Ad.double().cpu().numpy(), Pd.double().cpu().numpy(), 100, 120, q)
+    rho = O.factor_distance(U, T, V, ref["U"], ref["T"], ref["V"])
+    print(f"config2 slice tf32x3 + small_f64 q={q}: rho={rho:.3e}")
+    assert rho < TOL["tf32x3"], rho
+    _structure(U, T, V, perm, 120, orth_tol=5e-5)
+
+
+@pytest.mark.parametrize("side", ["right", "left"])
+def test_fp64_l128(side):
+    """FP64 solves up to l = 128 (the FP64 Cholesky keeps G and L^-1 in one shared array)."""
+    m, n = (700, 600) if side == "right" else (600, 700)
+    A = (W.gaussian(11, m, 150) * np.exp(-np.arange(150) / 25.0)) @ W.gaussian(12, 150, n)
+    phi = W.gaussian(13, m if side == "left" else n, 128)
+    r, A64, P64 = _run(A, phi, 100, 128, 1, torch.float64, side=side)
+    U, T, V, perm = _np(r)
+    ref = O.corutv(A64, P64, 100, 128, 1, side=side)
+    rho = O.factor_distance(U, T, V, ref["U"], ref["T"], ref["V"])
+    assert rho < TOL["f64"], rho
+    _structure(U, T, V, perm, 128, side=side)
+
+
 @pytest.mark.parametrize("m,n,k,l,q,side", [
     (1001, 777, 10, 37, 1, "right"),      # ragged everywhere
     (200, 900, 5, 12, 1, "left"),          # m < n: ULV form
