@@ -228,6 +228,17 @@ int corutv_solve_host(corutv_handle* h, const corutv_params* p, const void* A, i
                       void* V, int64_t ldv, int32_t* perm);
 
 /*
+ * corutv_host_read_time -- the host link as a kernel sees it, for the host-streamed solve
+ * (no counterpart in the paper): a kernel on the handle's stream reads `bytes` of
+ * page-locked HOST memory directly through its address (16-byte loads over all SMs) and
+ * *ms receives the kernel's duration (CUDA events; the call synchronises).  host must be
+ * 16-byte aligned and bytes a non-zero multiple of 16 (ERR_ALIGN); memory that CUDA does
+ * not know as page-locked host memory gives ERR_INVALID_ARG.  bytes / ms compares with
+ * the copy engine's rate (cudaMemcpyAsync), which corutv_solve_host uses.
+ */
+int corutv_host_read_time(corutv_handle* h, const void* host, size_t bytes, float* ms);
+
+/*
  * corutv_solve_corrected -- corutv_solve for A stored in BF16 or FP8 (a_dtype) plus
  * the FP32 correction pass: the range finding (the products of Alg. 3 steps 3-4
  * and their orthonormalisations: every pass over A but the core's) runs on the

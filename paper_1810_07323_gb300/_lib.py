@@ -94,7 +94,7 @@ EXPORTS = ("corutv_version", "corutv_status_string", "corutv_create", "corutv_de
            "corutv_batch_workspace_size", "corutv_solve_batched", "corutv_batch_info_wait",
            "corutv_server_create", "corutv_server_submit", "corutv_server_poll", "corutv_server_stats",
            "corutv_server_destroy", "corutv_rpca", "corutv_solve_host",
-           "corutv_residual_norm2")
+           "corutv_residual_norm2", "corutv_host_read_time")
 
 
 def load() -> ctypes.CDLL:
@@ -140,6 +140,7 @@ def load() -> ctypes.CDLL:
     lib.corutv_gram_noalloc.restype = ctypes.c_int
     lib.corutv_rpca.argtypes = [P, ctypes.POINTER(RpcaParams), P, I64, P, I64, P, I64, P, I64, P, I64,
                                 ctypes.POINTER(RpcaInfo)]
+    lib.corutv_host_read_time.argtypes = [P, P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_float)]
     lib.corutv_set_tracing.argtypes = [P, ctypes.c_int]
     lib.corutv_trace_read.argtypes = [P, ctypes.POINTER(Trace)]
     for name in ("corutv_set_tracing", "corutv_trace_read", "corutv_create", "corutv_destroy", "corutv_set_stream", "corutv_workspace_size",
@@ -148,7 +149,7 @@ def load() -> ctypes.CDLL:
                  "corutv_quantize", "corutv_batch_workspace_size", "corutv_solve_batched",
                  "corutv_batch_info_wait", "corutv_server_create", "corutv_server_submit", "corutv_server_poll",
                  "corutv_server_stats", "corutv_server_destroy", "corutv_rpca", "corutv_solve_host",
-                 "corutv_residual_norm2"):
+                 "corutv_residual_norm2", "corutv_host_read_time"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -646,6 +647,18 @@ def gram(Xt, Yt, length: int, l: int, handle: Handle | None = None):
                             ctypes.c_void_p(G.data_ptr()))
     _check(rc, "corutv_gram")
     return G
+
+
+def host_read_time(host_tensor, handle: Handle | None = None) -> float:
+    """corutv_host_read_time: milliseconds for a kernel to read the page-locked host
+    tensor directly (the host link as a kernel sees it)."""
+    h = handle or handle_for()
+    ms = ctypes.c_float()
+    nbytes = host_tensor.numel() * host_tensor.element_size()
+    rc = load().corutv_host_read_time(h.h, ctypes.c_void_p(host_tensor.data_ptr()), ctypes.c_size_t(nbytes),
+                                      ctypes.byref(ms))
+    _check(rc, "corutv_host_read_time")
+    return float(ms.value)
 
 
 def gram_noalloc(Xt, Yt, length: int, l: int, out, stream=None):

@@ -562,6 +562,22 @@ int solve_impl(corutv_handle* h, const corutv_params* p, const Plan& pl, const v
 
 constexpr int64_t kRingChunkBytes = 256ll << 20;   // default chunk of a host-streamed A
 
+// Direct device reads of page-locked host memory (through its host address, which the
+// device can dereference): 16-byte loads in a grid-stride loop, folded into one word per
+// block so the loads are not removed.  The rate of the host link seen by a kernel, beside
+// the copy engine's (cudaMemcpyAsync) used by the host-streamed passes.
+__device__ unsigned long long g_host_read_sink;
+__global__ void __launch_bounds__(512) host_read_kernel(const uint4* __restrict__ src, int64_t n16) {
+  uint32_t acc = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n16; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint4 v = src[i];
+    acc ^= v.x ^ v.y ^ v.z ^ v.w;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc ^= __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0 && acc == 0x9E3779B9u) atomicAdd(&g_host_read_sink, 1ull);
+}
+
 int ensure_ring(corutv_handle* h, size_t need) {
   HostRing& R = h->ring;
   if (!R.copy) {
@@ -794,6 +810,30 @@ int corutv_solve_host(corutv_handle* h, const corutv_params* p, const void* A, i
   h->launches += launch_counter() - l0;
   if (h->tracing) h->acc.solves += 1;
   return rc;
+}
+
+int corutv_host_read_time(corutv_handle* h, const void* host, size_t bytes, float* ms) {
+  if (!h || !host || !ms) return CORUTV_ERR_INVALID_ARG;
+  if (!aligned16(host) || bytes % 16 || bytes == 0) return CORUTV_ERR_ALIGN;
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, host) != cudaSuccess || at.type != cudaMemoryTypeHost) {
+    cudaGetLastError();
+    return CORUTV_ERR_INVALID_ARG;   // not page-locked host memory known to CUDA
+  }
+  const void* dev = at.devicePointer ? at.devicePointer : host;
+  cudaEvent_t e0, e1;
+  CU(cudaEventCreate(&e0));
+  CU(cudaEventCreate(&e1));
+  CU(cudaEventRecord(e0, h->stream));
+  host_read_kernel<<<4 * h->sms, 512, 0, h->stream>>>(static_cast<const uint4*>(dev), (int64_t)(bytes / 16));
+  CORUTV_COUNT_LAUNCH();
+  CU(cudaGetLastError());
+  CU(cudaEventRecord(e1, h->stream));
+  CU(cudaEventSynchronize(e1));
+  CU(cudaEventElapsedTime(ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return CORUTV_OK;
 }
 
 int corutv_quantize(corutv_handle* h, int dtype, const float* A, int64_t lda, int64_t m, int64_t n, void* out,

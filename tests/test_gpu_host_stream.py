@@ -166,3 +166,18 @@ def test_streamed_small_shapes(shape, chunk, side):
     _structure(U, T, V, perm, l, side=side)
     a2 = np.sum(A ** 2)
     assert abs(r.info.fro2_A - a2) < 1e-12 * a2
+
+
+def test_host_read_time():
+    """corutv_host_read_time: a kernel reads page-locked host memory directly; the rate is
+    positive and finite; unaligned sizes and memory CUDA does not know as page-locked are
+    refused before anything is launched."""
+    src = torch.ones(1 << 22, dtype=torch.float32, pin_memory=True)     # 16 MiB
+    ms = corutv.host_read_time(src)
+    assert 0.0 < ms < 1e4
+    with pytest.raises(corutv.CorutvError) as e:
+        corutv.host_read_time(src[:3])                                   # 12 bytes: not a multiple of 16
+    assert e.value.status == corutv.ERR_ALIGN
+    with pytest.raises(corutv.CorutvError) as e:
+        corutv.host_read_time(torch.ones(1 << 10, dtype=torch.float32))  # pageable
+    assert e.value.status == corutv.ERR_INVALID_ARG
