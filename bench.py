@@ -91,6 +91,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--sparse", type=float, default=None)
     ap.add_argument("--chunk", type=int, default=0)
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="batched / serving workloads: the fixed plan shapes instead of the autotuned ones")
+    ap.add_argument("--autotune-cache", default=None,
+                    help="JSON cache of tuned batch shapes (default: $CORUTV_AUTOTUNE_CACHE, else none)")
     args = ap.parse_args()
     w = dict(WORKLOADS[args.workload])
     for key in ("m", "n", "q"):
@@ -507,11 +511,16 @@ def main_batched(args):
         items.append(dict(A=A, Phi=phi, k=p.k, l=p.l, q=w["q"], side=side, want_fro2=True))
     stream = torch.cuda.current_stream()
     h = corutv.handle_for(stream)
+    tuning = None
+    if not args.no_autotune:
+        # the plan's shapes picked by measurement on the first call (cached per problem-set key)
+        corutv.set_autotune(1, args.autotune_cache or os.environ.get("CORUTV_AUTOTUNE_CACHE"), handle=h)
     b = corutv.Batch(items, handle=h)
-    for _ in range(max(args.warmup, 3)):        # build, capture, replay
+    for _ in range(max(args.warmup, 3)):        # build (and tune), capture, replay
         b.run(wait=False)
     res = b.wait()
     assert all(r.info.status == 0 for r in res)
+    tuning = corutv.batch_tuning(h)
     # per-phase device times from two traced (uncaptured) runs of the same batch
     h.trace_read()
     h.set_tracing(True)
@@ -627,6 +636,9 @@ def main_batched(args):
                           "l2": "inputs larger than L2 (9.7 GB of A per step)",
                           "parallelism": f"replicas x{world}"},
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+               "autotune": (dict(tuning, speedup_in_search=(tuning["default_ms"] / tuning["tuned_ms"]
+                                                             if tuning["tuned_ms"] > 0 else None))
+                            if tuning and tuning["tuned"] else {"tuned": False}),
                "gpu_launches": int(launches), "clocks": clk,
                "phases_ms_per_step": {"passes": tr.pass_ms / 2, "orth": tr.orth_ms / 2, "core": tr.core_ms / 2,
                                       "qrcp": tr.qrcp_ms / 2, "assembly": tr.assembly_ms / 2},

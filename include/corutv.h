@@ -334,6 +334,39 @@ int corutv_solve_batched(corutv_handle* h, int count, const corutv_problem* prob
  * last batch (count must equal that batch's count). */
 int corutv_batch_info_wait(corutv_handle* h, int count, corutv_info* infos);
 
+/*
+ * corutv_set_autotune -- shapes of the batched plan picked by measurement (no
+ * counterpart in the paper).  mode 1: the first corutv_solve_batched call with a new
+ * problem set (never a graph replay) runs a coordinate search -- the order of the
+ * problems in the tensor-core pass tables (as given / largest reduction first), the
+ * columns per Gram partial block (256, 512, 1024, 2048) and, for CUDA-core passes, the
+ * K range of one split (1024, 2048, 4096) -- timing whole batches (one warm run, the
+ * faster of two timed runs per candidate) and builds the plan with the fastest shapes;
+ * the search's runs write the problems' outputs, which the final run then overwrites.
+ * The choice is cached per key (storage dtype, pass engine, l class of the largest l,
+ * power-of-two buckets of the mean m, mean n and count, largest q) in the JSON file
+ * cache_path (NULL: the file named by the environment variable CORUTV_AUTOTUNE_CACHE, or
+ * no file) and on the handle; a key found in either is used without a search (the handle's
+ * own earlier searches come first).  mode 0 (the default): the
+ * fixed shapes.  The next batched call on the handle builds a new plan.  Different
+ * shapes change the order of floating-point sums, not the arithmetic.
+ */
+int corutv_set_autotune(corutv_handle* h, int mode, const char* cache_path);
+
+typedef struct {
+  int32_t tuned;        /* 1: the current plan's shapes come from the autotuner */
+  int32_t from_cache;   /* 1: read from the cache file (no search ran) */
+  int32_t gram_cols;    /* columns per Gram partial block */
+  int32_t split_k;      /* K range of one split of the CUDA-core passes */
+  int32_t tc_order;     /* tensor-core pass tables: 0 problems as given, 1 largest reduction first */
+  int32_t reserved0;
+  double tuned_ms;      /* whole-batch time of the chosen shapes in the search (0 if from the cache) */
+  double default_ms;    /* whole-batch time of the fixed shapes in the search (0 if from the cache) */
+} corutv_batch_tuning;
+
+/* The shapes of the handle's current batched plan (ERR_INVALID_ARG before any batch). */
+int corutv_batch_tuning_read(corutv_handle* h, corutv_batch_tuning* out);
+
 /* ------------------------------------------------------------------------
  * Serving: a request queue in front of corutv_solve_batched (no counterpart in
  * the paper; each request is one solve of Alg. 2 / Alg. 3).

@@ -41,6 +41,12 @@ class Params(ctypes.Structure):
                 ("reserved", ctypes.c_int32 * 5)]
 
 
+class BatchTuning(ctypes.Structure):
+    _fields_ = [("tuned", ctypes.c_int32), ("from_cache", ctypes.c_int32), ("gram_cols", ctypes.c_int32),
+                ("split_k", ctypes.c_int32), ("tc_order", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("tuned_ms", ctypes.c_double), ("default_ms", ctypes.c_double)]
+
+
 class Problem(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("k", ctypes.c_int32), ("l", ctypes.c_int32),
                 ("q", ctypes.c_int32), ("side", ctypes.c_int32), ("core", ctypes.c_int32),
@@ -94,7 +100,7 @@ EXPORTS = ("corutv_version", "corutv_status_string", "corutv_create", "corutv_de
            "corutv_batch_workspace_size", "corutv_solve_batched", "corutv_batch_info_wait",
            "corutv_server_create", "corutv_server_submit", "corutv_server_poll", "corutv_server_stats",
            "corutv_server_destroy", "corutv_rpca", "corutv_solve_host",
-           "corutv_residual_norm2", "corutv_host_read_time")
+           "corutv_residual_norm2", "corutv_host_read_time", "corutv_set_autotune", "corutv_batch_tuning_read")
 
 
 def load() -> ctypes.CDLL:
@@ -141,6 +147,8 @@ def load() -> ctypes.CDLL:
     lib.corutv_rpca.argtypes = [P, ctypes.POINTER(RpcaParams), P, I64, P, I64, P, I64, P, I64, P, I64,
                                 ctypes.POINTER(RpcaInfo)]
     lib.corutv_host_read_time.argtypes = [P, P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_float)]
+    lib.corutv_set_autotune.argtypes = [P, ctypes.c_int, ctypes.c_char_p]
+    lib.corutv_batch_tuning_read.argtypes = [P, ctypes.POINTER(BatchTuning)]
     lib.corutv_set_tracing.argtypes = [P, ctypes.c_int]
     lib.corutv_trace_read.argtypes = [P, ctypes.POINTER(Trace)]
     for name in ("corutv_set_tracing", "corutv_trace_read", "corutv_create", "corutv_destroy", "corutv_set_stream", "corutv_workspace_size",
@@ -149,7 +157,8 @@ def load() -> ctypes.CDLL:
                  "corutv_quantize", "corutv_batch_workspace_size", "corutv_solve_batched",
                  "corutv_batch_info_wait", "corutv_server_create", "corutv_server_submit", "corutv_server_poll",
                  "corutv_server_stats", "corutv_server_destroy", "corutv_rpca", "corutv_solve_host",
-                 "corutv_residual_norm2", "corutv_host_read_time"):
+                 "corutv_residual_norm2", "corutv_host_read_time", "corutv_set_autotune",
+                 "corutv_batch_tuning_read"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -647,6 +656,23 @@ def gram(Xt, Yt, length: int, l: int, handle: Handle | None = None):
                             ctypes.c_void_p(G.data_ptr()))
     _check(rc, "corutv_gram")
     return G
+
+
+def set_autotune(mode: int, cache_path: str | None = None, handle: Handle | None = None):
+    """corutv_set_autotune: 1 = pick the batched plan's shapes by measurement (cached in
+    cache_path, or in $CORUTV_AUTOTUNE_CACHE when cache_path is None), 0 = fixed shapes."""
+    h = handle or handle_for()
+    rc = load().corutv_set_autotune(h.h, int(mode), cache_path.encode() if cache_path is not None else None)
+    _check(rc, "corutv_set_autotune")
+
+
+def batch_tuning(handle: Handle | None = None) -> dict:
+    """corutv_batch_tuning_read: the shapes of the handle's current batched plan."""
+    h = handle or handle_for()
+    t = BatchTuning()
+    _check(load().corutv_batch_tuning_read(h.h, ctypes.byref(t)), "corutv_batch_tuning_read")
+    return {"tuned": bool(t.tuned), "from_cache": bool(t.from_cache), "gram_cols": t.gram_cols,
+            "split_k": t.split_k, "tc_order": t.tc_order, "tuned_ms": t.tuned_ms, "default_ms": t.default_ms}
 
 
 def host_read_time(host_tensor, handle: Handle | None = None) -> float:

@@ -13,7 +13,10 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <stdlib.h>
+
 #include <algorithm>
+#include <string>
 #include <vector>
 
 #include "../../include/corutv.h"
@@ -37,8 +40,19 @@ struct PassTable {
   int2* d_rmap = nullptr;
 };
 
+// Shapes of a batched plan that the autotuner may change (defaults: the fixed plan).
+struct BatchTune {
+  int gram_cols = kBatchGramCols;     // columns per Gram partial block
+  int64_t split_k = kBatchSplitK;     // K range of one split of the CUDA-core passes
+  int tc_order = 0;                   // tensor-core pass tables: 0 problems as given, 1 largest K first
+};
+
 struct BatchState {
   std::vector<unsigned char> key;     // bytes of the problem array the tables were built for
+  BatchTune tune;                     // shapes the tables were built with
+  bool tuned = false, tune_from_cache = false;
+  double tuned_ms = 0.0, default_ms = 0.0;
+  std::vector<std::pair<std::string, BatchTune>> tuned_keys;   // this handle's searches, by key
   void* ws = nullptr;                 // device: tables + per-problem buffers (owned)
   size_t ws_bytes = 0;
   void* host = nullptr;               // pinned staging of the tables
@@ -89,6 +103,9 @@ size_t align_up(size_t x) { return (x + kBAlign - 1) / kBAlign * kBAlign; }
 
 enum MapKind { kMapT1 = 0, kMapT2, kMapG1, kMapG2, kMapRed, kMapLm1, kMapLm2, kMapS2 };
 constexpr int kClassLP[3] = {32, 64, 128};
+// autotuner candidates (the first of each list is the largest plan: the workspace query sizes for it)
+constexpr int kTuneGramCols[4] = {256, 512, 1024, 2048};
+constexpr int64_t kTuneSplitK[3] = {1024, 2048, 4096};
 int lclass(int l) { return l <= 32 ? 0 : (l <= 64 ? 1 : 2); }
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
@@ -133,7 +150,7 @@ struct ProbSizes {
   size_t sk1, sk2, sk3, xr, gparts, ll8, ll4, defic, fparts, status, kparts;
 };
 
-ProbSizes prob_sizes(const corutv_problem& p, int lp, bool tc) {
+ProbSizes prob_sizes(const corutv_problem& p, int lp, bool tc, const BatchTune& tune) {
   ProbSizes z{};
   const bool right = p.side == CORUTV_SIDE_RIGHT;
   z.len1 = right ? p.m : p.n;
@@ -141,13 +158,13 @@ ProbSizes prob_sizes(const corutv_problem& p, int lp, bool tc) {
   z.ld1 = ld_for(z.len1);
   z.ld2 = ld_for(z.len2);
   z.ld3 = std::max(z.ld1, z.ld2);
-  z.gp1 = (int)std::max<int64_t>(1, cdiv(z.len1, kBatchGramCols));
-  z.gp2 = (int)std::max<int64_t>(1, cdiv(z.len2, kBatchGramCols));
+  z.gp1 = (int)std::max<int64_t>(1, cdiv(z.len1, tune.gram_cols));
+  z.gp2 = (int)std::max<int64_t>(1, cdiv(z.len2, tune.gram_cols));
   z.tiles1 = cdiv(z.len1, kBatchPassBN);
   z.tiles2 = cdiv(z.len2, kBatchPassBN);
   // SIMT passes: C1 and the core reduce over len2, C2 over len1
-  z.ks1 = batch_ksplit(z.len2);
-  z.ks2 = batch_ksplit(z.len1);
+  z.ks1 = batch_ksplit(z.len2, tune.split_k);
+  z.ks2 = batch_ksplit(z.len1, tune.split_k);
   z.ntiles = (int)std::max(z.tiles1, z.tiles2);
   z.nf = (int)(z.tiles1 * z.ks1);
   z.sk1 = sizeof(float) * p.l * z.ld1;
@@ -202,7 +219,7 @@ struct Plan {
   size_t off_kcount = 0, kcount_bytes = 0;    // split counters of the SIMT passes, all problems
 };
 
-void make_plan(Plan& L, int count, const corutv_problem* probs, int sms) {
+void make_plan(Plan& L, int count, const corutv_problem* probs, int sms, const BatchTune& tune) {
   L.count = count;
   for (int i = 0; i < count; ++i) {
     L.lmax = std::max(L.lmax, (int)probs[i].l);
@@ -213,7 +230,7 @@ void make_plan(Plan& L, int count, const corutv_problem* probs, int sms) {
   L.sz.resize(count);
   for (int i = 0; i < count; ++i) {
     const corutv_problem& p = probs[i];
-    const ProbSizes& z = L.sz[i] = prob_sizes(p, kClassLP[lclass(p.l)], L.tc);
+    const ProbSizes& z = L.sz[i] = prob_sizes(p, kClassLP[lclass(p.l)], L.tc, tune);
     std::vector<int2>* mc = L.maps[lclass(p.l)];
     add_blocks(mc[kMapT1], i, z.tiles1 * z.ks1);
     add_blocks(mc[kMapT2], i, z.tiles2 * z.ks2);
@@ -241,8 +258,19 @@ void make_plan(Plan& L, int count, const corutv_problem* probs, int sms) {
       std::vector<int2> rmap;
       for (int i = 0; i < count; ++i) {
         const corutv_problem& p = probs[i];
-        const bool in = T.which == kB_CORE ? p.core == CORUTV_CORE_EXACT : T.it <= p.q;
-        if (!in) continue;
+        if (T.which == kB_CORE ? p.core == CORUTV_CORE_EXACT : T.it <= p.q) members.push_back(i);
+      }
+      if (tune.tc_order == 1) {
+        // largest reduction first (ties: larger output, then the given order)
+        auto kk = [&](int i) { return T.which == kB_C2 ? L.sz[i].len1 : L.sz[i].len2; };
+        auto ll = [&](int i) { return T.which == kB_C2 ? L.sz[i].len2 : L.sz[i].len1; };
+        std::stable_sort(members.begin(), members.end(), [&](int a, int b) {
+          return kk(a) != kk(b) ? kk(a) > kk(b) : ll(a) > ll(b);
+        });
+      }
+      for (size_t u = 0; u < members.size(); ++u) {
+        const int i = members[u];
+        const corutv_problem& p = probs[i];
         const ProbSizes& z = L.sz[i];
         const int64_t len = T.which == kB_C2 ? z.len2 : z.len1, K = T.which == kB_C2 ? z.len1 : z.len2;
         T.iters += tc_grouped_tiles(len) * tc_grouped_kblocks(K);
@@ -250,8 +278,7 @@ void make_plan(Plan& L, int count, const corutv_problem* probs, int sms) {
         T.lmax = std::max(T.lmax, (int)p.l);
         const int eb = 4;
         T.bytes += (double)p.m * p.n * eb + 4.0 * p.l * (double)(len + K);
-        add_blocks(rmap, (int)members.size(), cdiv(K, 128));
-        members.push_back(i);
+        add_blocks(rmap, (int)u, cdiv(K, 128));
       }
       T.np = (int)members.size();
       T.nround = (int)rmap.size();
@@ -300,9 +327,9 @@ void make_plan(Plan& L, int count, const corutv_problem* probs, int sms) {
 }
 
 // Build tables and buffers for a new problem set (the stream is idle).
-int build(corutv_handle* h, BatchState* B, int count, const corutv_problem* probs) {
+int build(corutv_handle* h, BatchState* B, int count, const corutv_problem* probs, const BatchTune& tune) {
   Plan L;
-  make_plan(L, count, probs, h->sms);
+  make_plan(L, count, probs, h->sms, tune);
   if (!B->ws || B->ws_bytes < L.need) {
     if (B->ws) cudaFree(B->ws);
     B->ws = nullptr;
@@ -500,6 +527,7 @@ int build(corutv_handle* h, BatchState* B, int count, const corutv_problem* prob
   B->maxq = L.maxq;
   B->key.assign(reinterpret_cast<const unsigned char*>(probs),
                 reinterpret_cast<const unsigned char*>(probs) + sizeof(corutv_problem) * count);
+  B->tune = tune;
   if (B->exec) {
     cudaGraphExecDestroy(B->exec);
     B->exec = nullptr;
@@ -595,6 +623,193 @@ int enqueue(corutv_handle* h, const BatchState* B) {
   return CORUTV_OK;
 }
 
+// ------------------------------------------------------------------ autotuner
+// Cache key: storage dtype, pass engine, sketch-size class of the largest l, and power-of-two
+// buckets of the mean m, the mean n and the count, plus the largest q.
+int bucket_log2(double x) { return x <= 1.0 ? 0 : (int)floor(log2(x) + 0.5); }
+
+std::string tune_key(int count, const corutv_problem* probs, bool tc) {
+  double sm = 0.0, sn = 0.0;
+  int lmax = 1, qmax = 0;
+  for (int i = 0; i < count; ++i) {
+    sm += (double)probs[i].m;
+    sn += (double)probs[i].n;
+    lmax = std::max(lmax, (int)probs[i].l);
+    qmax = std::max(qmax, (int)probs[i].q);
+  }
+  char buf[160];
+  snprintf(buf, sizeof(buf), "dtype%d/%s/lclass%d/m%d/n%d/count%d/q%d", (int)probs[0].a_dtype, tc ? "tc" : "simt",
+           lclass(lmax), bucket_log2(sm / count), bucket_log2(sn / count), bucket_log2((double)count), qmax);
+  return std::string(buf);
+}
+
+// The cache is a JSON object with one entry object per line:
+//   {"corutv_autotune": 1, "entries": [
+//   {"key": "...", "gram_cols": 512, "split_k": 2048, "tc_order": 0, "tuned_ms": 17.2, "default_ms": 17.6},
+//   ...
+//   ]}
+bool json_int(const std::string& line, const char* name, int64_t* out) {
+  const std::string pat = std::string("\"") + name + "\":";
+  const size_t at = line.find(pat);
+  if (at == std::string::npos) return false;
+  *out = strtoll(line.c_str() + at + pat.size(), nullptr, 10);
+  return true;
+}
+
+std::string line_key(const std::string& line) {
+  const std::string pat = "\"key\": \"";
+  const size_t at = line.find(pat);
+  if (at == std::string::npos) return std::string();
+  const size_t end = line.find('"', at + pat.size());
+  return end == std::string::npos ? std::string() : line.substr(at + pat.size(), end - at - pat.size());
+}
+
+std::vector<std::string> cache_entries(const std::string& path) {
+  std::vector<std::string> v;
+  FILE* f = fopen(path.c_str(), "r");
+  if (!f) return v;
+  char buf[1024];
+  while (fgets(buf, sizeof(buf), f)) {
+    std::string line(buf);
+    if (!line_key(line).empty()) {
+      while (!line.empty() && (line.back() == '\n' || line.back() == ',' || line.back() == '\r')) line.pop_back();
+      v.push_back(line);
+    }
+  }
+  fclose(f);
+  return v;
+}
+
+bool cache_lookup(const std::string& path, const std::string& key, BatchTune* t) {
+  for (const std::string& line : cache_entries(path)) {
+    if (line_key(line) != key) continue;
+    int64_t gc = 0, sk = 0, order = 0;
+    if (!json_int(line, "gram_cols", &gc) || !json_int(line, "split_k", &sk) || !json_int(line, "tc_order", &order))
+      return false;
+    bool ok_gc = false, ok_sk = false;
+    for (int c : kTuneGramCols) ok_gc |= c == gc;
+    for (int64_t c : kTuneSplitK) ok_sk |= c == sk;
+    if (!ok_gc || !ok_sk || (order != 0 && order != 1)) return false;   // not a shape this build offers
+    t->gram_cols = (int)gc;
+    t->split_k = sk;
+    t->tc_order = (int)order;
+    return true;
+  }
+  return false;
+}
+
+void cache_store(const std::string& path, const std::string& key, const BatchTune& t, double tuned_ms,
+                 double default_ms) {
+  std::vector<std::string> v = cache_entries(path);
+  v.erase(std::remove_if(v.begin(), v.end(), [&](const std::string& x) { return line_key(x) == key; }), v.end());
+  char buf[512];
+  snprintf(buf, sizeof(buf),
+           "{\"key\": \"%s\", \"gram_cols\": %d, \"split_k\": %lld, \"tc_order\": %d, \"tuned_ms\": %.4f, "
+           "\"default_ms\": %.4f}",
+           key.c_str(), t.gram_cols, (long long)t.split_k, t.tc_order, tuned_ms, default_ms);
+  v.push_back(buf);
+  const std::string tmp = path + ".tmp";
+  FILE* f = fopen(tmp.c_str(), "w");
+  if (!f) return;                                  // an unwritable cache only costs a later search
+  fprintf(f, "{\"corutv_autotune\": 1, \"entries\": [\n");
+  for (size_t i = 0; i < v.size(); ++i) fprintf(f, "%s%s\n", v[i].c_str(), i + 1 < v.size() ? "," : "");
+  fprintf(f, "]}\n");
+  fclose(f);
+  rename(tmp.c_str(), path.c_str());
+}
+
+// Whole-batch time of the plan built with shapes t: one warm run, then the faster of two timed runs.
+int time_plan(corutv_handle* h, BatchState* B, int count, const corutv_problem* probs, const BatchTune& t,
+              double* ms) {
+  int rc = build(h, B, count, probs, t);
+  if (rc) return rc;
+  rc = enqueue(h, B);
+  if (rc) return rc;
+  cudaEvent_t e0, e1;
+  CUB(cudaEventCreate(&e0));
+  CUB(cudaEventCreate(&e1));
+  double best = 1e30;
+  for (int r = 0; r < 2 && !rc; ++r) {
+    CUB(cudaEventRecord(e0, h->stream));
+    rc = enqueue(h, B);
+    CUB(cudaEventRecord(e1, h->stream));
+    CUB(cudaEventSynchronize(e1));
+    float f = 0.f;
+    CUB(cudaEventElapsedTime(&f, e0, e1));
+    best = std::min(best, (double)f);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *ms = best;
+  return rc;
+}
+
+// Coordinate search over the plan's shapes, timing whole batches (outside any capture: the
+// first call of a problem set).  The cache answers first when it holds the key.
+int autotune(corutv_handle* h, BatchState* B, int count, const corutv_problem* probs, BatchTune* out) {
+  const bool tc = batch_uses_tc(count, probs);
+  const std::string key = tune_key(count, probs, tc);
+  BatchTune best;
+  for (const auto& kv : B->tuned_keys) {
+    if (kv.first != key) continue;
+    *out = kv.second;                             // searched before on this handle
+    B->tuned = true;
+    B->tune_from_cache = true;
+    B->tuned_ms = B->default_ms = 0.0;
+    return CORUTV_OK;
+  }
+  if (!h->tune_cache.empty() && cache_lookup(h->tune_cache, key, &best)) {
+    *out = best;
+    B->tuned = true;
+    B->tune_from_cache = true;
+    B->tuned_ms = B->default_ms = 0.0;
+    return CORUTV_OK;
+  }
+  const bool was_tracing = h->tracing;
+  h->tracing = false;
+  double best_ms = 0.0;
+  int rc = time_plan(h, B, count, probs, best, &best_ms);
+  const double default_ms = best_ms;
+  auto try_shape = [&](const BatchTune& cand) {
+    if (rc) return;
+    double ms = 0.0;
+    rc = time_plan(h, B, count, probs, cand, &ms);
+    if (!rc && ms < best_ms) {
+      best_ms = ms;
+      best = cand;
+    }
+  };
+  if (tc) {
+    BatchTune c = best;
+    c.tc_order = 1;
+    try_shape(c);
+  }
+  for (int gc : kTuneGramCols) {
+    if (gc == best.gram_cols) continue;
+    BatchTune c = best;
+    c.gram_cols = gc;
+    try_shape(c);
+  }
+  if (!tc) {
+    for (int64_t sk : kTuneSplitK) {
+      if (sk == best.split_k) continue;
+      BatchTune c = best;
+      c.split_k = sk;
+      try_shape(c);
+    }
+  }
+  h->tracing = was_tracing;
+  if (rc) return rc;
+  *out = best;
+  B->tuned = true;
+  B->tune_from_cache = false;
+  B->tuned_ms = best_ms;
+  B->default_ms = default_ms;
+  B->tuned_keys.emplace_back(key, best);
+  if (!h->tune_cache.empty()) cache_store(h->tune_cache, key, best, best_ms, default_ms);
+  return CORUTV_OK;
+}
+
 bool same_key(const BatchState* B, int count, const corutv_problem* probs) {
   return B->count == count && B->key.size() == sizeof(corutv_problem) * (size_t)count &&
          memcmp(B->key.data(), probs, B->key.size()) == 0;
@@ -616,9 +831,14 @@ int corutv_batch_workspace_size(int count, const corutv_problem* probs, size_t* 
     cudaGetLastError();
     sms = 160;                                    // no device: an upper bound for the plan
   }
-  Plan L;
-  make_plan(L, count, probs, sms);
-  *bytes = L.need;
+  // the largest plan the autotuner can choose (more Gram partials and K splits than the defaults)
+  BatchTune big;
+  big.gram_cols = kTuneGramCols[0];
+  big.split_k = kTuneSplitK[0];
+  Plan L, L2;
+  make_plan(L, count, probs, sms, BatchTune{});
+  make_plan(L2, count, probs, sms, big);
+  *bytes = std::max(L.need, L2.need);
   return CORUTV_OK;
 }
 
@@ -633,11 +853,21 @@ int corutv_solve_batched(corutv_handle* h, int count, const corutv_problem* prob
   if (!h->batch) h->batch = new (std::nothrow) BatchState();
   if (!h->batch) return CORUTV_ERR_OOM;
   BatchState* B = h->batch;
-  const int64_t l0 = launch_counter();
+  int64_t l0 = launch_counter();
   if (!same_key(B, count, probs)) {
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return CORUTV_ERR_CUDA;
     B->key.clear();
-    int rc = build(h, B, count, probs);
+    BatchTune tune;
+    B->tuned = B->tune_from_cache = false;
+    B->tuned_ms = B->default_ms = 0.0;
+    if (h->autotune) {
+      B->a_dtype = a_dtype;
+      int rc = autotune(h, B, count, probs, &tune);
+      if (rc) return rc;
+      B->key.clear();
+      l0 = launch_counter();                      // the search's runs are not this call's launches
+    }
+    int rc = build(h, B, count, probs, tune);
     if (rc) return rc;
     B->a_dtype = a_dtype;
     rc = enqueue(h, B);                           // first run of a problem set: direct launches
@@ -676,6 +906,38 @@ int corutv_solve_batched(corutv_handle* h, int count, const corutv_problem* prob
   h->launches += launch_counter() - l0;
   if (h->tracing) h->acc.solves += count;
   if (infos) return corutv_batch_info_wait(h, count, infos);
+  return CORUTV_OK;
+}
+
+int corutv_set_autotune(corutv_handle* h, int mode, const char* cache_path) {
+  if (!h || (mode != 0 && mode != 1)) return CORUTV_ERR_INVALID_ARG;
+  h->autotune = mode;
+  if (cache_path) {
+    h->tune_cache = cache_path;
+  } else {
+    const char* env = getenv("CORUTV_AUTOTUNE_CACHE");
+    h->tune_cache = env ? env : "";
+  }
+  if (h->batch) {
+    // the next batched call builds a new plan with (or without) tuned shapes
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return CORUTV_ERR_CUDA;
+    h->batch->key.clear();
+  }
+  return CORUTV_OK;
+}
+
+int corutv_batch_tuning_read(corutv_handle* h, corutv_batch_tuning* out) {
+  if (!h || !out) return CORUTV_ERR_INVALID_ARG;
+  memset(out, 0, sizeof(*out));
+  const BatchState* B = h->batch;
+  if (!B || B->key.empty()) return CORUTV_ERR_INVALID_ARG;
+  out->tuned = B->tuned ? 1 : 0;
+  out->from_cache = B->tune_from_cache ? 1 : 0;
+  out->gram_cols = B->tune.gram_cols;
+  out->split_k = (int32_t)B->tune.split_k;
+  out->tc_order = B->tune.tc_order;
+  out->tuned_ms = B->tuned_ms;
+  out->default_ms = B->default_ms;
   return CORUTV_OK;
 }
 

@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <string>
 #include <vector>
 
 #include "../../include/corutv.h"
@@ -54,6 +55,8 @@ struct corutv_handle {
   HostRing ring;
   void* resid_ws = nullptr;     // vectors of the spectral readout (resid.cu), lazily allocated
   size_t resid_ws_bytes = 0;
+  int autotune = 0;             // batched solves: 1 = search (or read from the cache) the plan's shapes
+  std::string tune_cache;       // JSON cache of tuned shapes ("" = none)
 };
 
 void rpca_free(corutv_handle* h);

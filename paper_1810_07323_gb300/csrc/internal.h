@@ -202,9 +202,9 @@ enum BatchGram : int { kG_ORTH1 = 0, kG_ORTH2 = 1, kG_CORE_EXACT = 2, kG_CORE_SK
 constexpr int kBatchPassBN = 64;
 constexpr int64_t kBatchSplitK = 2048;
 constexpr int kBatchMaxSplit = 64;
-inline int batch_ksplit(int64_t K) {
-  if (K <= 2 * kBatchSplitK) return 1;
-  const int64_t s = (K + kBatchSplitK - 1) / kBatchSplitK;
+inline int batch_ksplit(int64_t K, int64_t splitk = kBatchSplitK) {
+  if (K <= 2 * splitk) return 1;
+  const int64_t s = (K + splitk - 1) / splitk;
   return (int)(s < kBatchMaxSplit ? s : kBatchMaxSplit);
 }
 cudaError_t launch_pass_simt_grouped(const BatchProb* P, const int2* map, int nblocks, int lp, int a_dtype,

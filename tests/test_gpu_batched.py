@@ -280,3 +280,54 @@ def test_config4_full_batch_sampled():
             rho = O.factor_distance(U.cpu().numpy(), T.cpu().numpy(), V.cpu().numpy(), ref["U"], ref["T"],
                                     ref["V"])
             assert rho < 1e-3, (i, rho)          # TF32 tensor-core passes
+
+
+@pytest.mark.parametrize("kind", ["f32", "bf16"])
+def test_autotune_plans_agree_and_cache_round_trip(kind, tmp_path):
+    """The autotuner searches the plan's shapes on the first call, writes its choice to the
+    JSON cache, and a second handle reads it back without searching.  Tuned and fixed plans
+    give the same factorisations up to the order of FP32 sums (rho <= 1e-5 between them, and
+    each within the oracle bound); the same plan replayed is bit-identical."""
+    import json
+    items, refs = [], []
+    for i, (m, n, r, k, l, q, side, core, orth) in enumerate(MIXED + SPLIT):
+        A = _lowrank_sparse(C.stream_seed(91, i), m, n, r).astype(np.float32)
+        phi = C.normal_block_np(C.stream_seed(92, i), l, 0, m if side == "left" else n, 0, l)
+        it, Aq = _item(A, phi, k, l, q, side, core, orth, kind=kind)
+        items.append(it)
+        refs.append((Aq, phi, k, l, q, side, core))
+    cache = str(tmp_path / "tune.json")
+
+    def factors(res):
+        return [(x.U.double().cpu().numpy(), x.T.cpu().numpy(), x.V.double().cpu().numpy()) for x in res]
+
+    h0 = corutv.Handle()
+    fixed = factors(corutv.Batch(items, handle=h0).run())
+    assert not corutv.batch_tuning(h0)["tuned"]
+
+    h1 = corutv.Handle()
+    corutv.set_autotune(1, cache, handle=h1)
+    b1 = corutv.Batch(items, handle=h1)
+    tuned = factors(b1.run())
+    t1 = corutv.batch_tuning(h1)
+    print(kind, t1)
+    assert t1["tuned"] and not t1["from_cache"] and 0 < t1["tuned_ms"] <= t1["default_ms"]
+    entries = json.load(open(cache))["entries"]
+    assert len(entries) == 1 and entries[0]["gram_cols"] == t1["gram_cols"]
+    again = factors(b1.run())                          # graph replay of the tuned plan
+    for a, b in zip(tuned, again):
+        assert all(np.array_equal(x, y) for x, y in zip(a, b))
+
+    h2 = corutv.Handle()
+    corutv.set_autotune(1, cache, handle=h2)
+    cached = factors(corutv.Batch(items, handle=h2).run())
+    t2 = corutv.batch_tuning(h2)
+    assert t2["tuned"] and t2["from_cache"]
+    assert (t2["gram_cols"], t2["split_k"], t2["tc_order"]) == (t1["gram_cols"], t1["split_k"], t1["tc_order"])
+    for a, b in zip(tuned, cached):                    # same shapes: the same arithmetic
+        assert all(np.array_equal(x, y) for x, y in zip(a, b))
+
+    for i, ((U0, T0, V0), (U1, T1, V1), (Aq, phi, k, l, q, side, core)) in enumerate(zip(fixed, tuned, refs)):
+        assert O.factor_distance(U1, T1, V1, U0, T0, V0) < 1e-5, i
+        ref = O.corutv(Aq, phi.astype(np.float64), k, l, q, side=side)
+        assert O.factor_distance(U1, T1, V1, ref["U"], ref["T"], ref["V"]) < TOL, i
