@@ -698,13 +698,26 @@ def main_serving(args):
     srv = corutv.Server(hbm_budget=16 << 30, max_slots=64, queue_capacity=16384)
     counters = {}
     slot_busy = {}
+    # sampled timed requests (the first of each size class, then every 50th) keep their own
+    # output buffers, compared with the oracle after the timed window
+    N_SAMPLE = 24
+    sampled, seen_cls = [], set()
+    for j, r in enumerate(timed):
+        cls = W.SERVING_SIZES.index((r.m, r.n))
+        if (cls not in seen_cls or j % 50 == 0) and len(sampled) < N_SAMPLE:
+            seen_cls.add(cls)
+            sampled.append(j)
+    sample_out = {j: (torch.empty((timed[j].m, timed[j].l), device=dev),
+                      torch.empty((timed[j].l, timed[j].l), dtype=torch.float64, device=dev),
+                      torch.empty((timed[j].n, timed[j].l), device=dev),
+                      torch.empty((timed[j].l,), dtype=torch.int32, device=dev)) for j in sampled}
 
-    def make_problem(i, r):
+    def make_problem(i, r, own=None):
         cls = W.SERVING_SIZES.index((r.m, r.n))
         c = counters.get((cls, r.k), 0)
         counters[(cls, r.k)] = c + 1
-        U, T, V, perm = rings[(cls, r.k)][c % RING]
-        key = (cls, r.k, c % RING)
+        U, T, V, perm = own if own is not None else rings[(cls, r.k)][c % RING]
+        key = (cls, r.k, c % RING) if own is None else ("sample", i)
         A = pools[cls][i % len(pools[cls])]
         phi = phis[(cls, r.k)][i % len(phis[(cls, r.k)])]
         p = corutv.Problem()
@@ -716,7 +729,8 @@ def main_serving(args):
         p.V, p.ldv, p.perm = V.data_ptr(), V.stride(0), perm.data_ptr()
         return p, key
 
-    def run(stream_reqs, base):
+    def run(stream_reqs, base, own=None):
+        own = own or {}
         out = []
         info = corutv.Info()
         pending = {}
@@ -725,7 +739,7 @@ def main_serving(args):
         while i < len(stream_reqs) or pending:
             now = time.perf_counter() - t0
             while i < len(stream_reqs) and stream_reqs[i].t_arrive - base <= now:
-                p, key = make_problem(i, stream_reqs[i])
+                p, key = make_problem(i, stream_reqs[i], own.get(i))
                 assert not slot_busy.get(key, False), "output ring too small"
                 t = ctypes.c_uint64()
                 ts = time.perf_counter()
@@ -748,7 +762,7 @@ def main_serving(args):
     run(warm, 0.0)
     st0 = srv.stats()
     clocks = Clocks(torch.cuda.current_device()) if rank == 0 else None
-    res, wall = run(timed, 1.0)
+    res, wall = run(timed, 1.0, sample_out)
     clk = clocks.stop() if clocks else None
     st1 = srv.stats()
     srv.close()
@@ -757,22 +771,37 @@ def main_serving(args):
     by_cls = {}
     for dt, r in res:
         by_cls.setdefault(f"{r.m}x{r.n}", []).append(dt * 1e3)
-    cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
+    # the sampled requests against the FP64 oracle on the same stored (BF16) values and Psi: factor
+    # distance and rank-k errors; the oracle's solve times are the CPU baseline
+    cpu, err = None, None
+    if rank == 0:
+        from types import SimpleNamespace
         from oracle import corutv_oracle as O
-        from oracle import precision as P
-        tsum, ns = 0.0, 0
-        for r in timed[:40]:
-            if r.m * r.n > 8192 * 2048:
-                continue
-            A = P.bf16_round(r.content.dense().astype(np.float32)).astype(np.float64)
-            phi = W.problem_phi(W.Problem(r.m, r.n, 5, r.l, r.q, r.k, r.content, r.phi_seed), r.n)
+        tsum, rows = 0.0, []
+        for j in sampled:
+            r = timed[j]
+            cls = W.SERVING_SIZES.index((r.m, r.n))
+            A64 = pools[cls][j % len(pools[cls])].double().cpu().numpy()
+            phi = phis[(cls, r.k)][j % len(phis[(cls, r.k)])].double().cpu().numpy()
             t1 = time.perf_counter()
-            O.corutv(A, phi, r.k, r.l, r.q)
+            ref = O.corutv(A64, phi, r.k, r.l, r.q)
             tsum += time.perf_counter() - t1
-            ns += 1
-        cpu = {"value": ns / tsum, "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
-               "sample": f"FP64 oracle on {ns} of the first 40 timed requests (76800x200 ones skipped), sequential"}
+            U, T, V, _ = sample_out[j]
+            e = rank_k_errors(A64, SimpleNamespace(U=U, T=T, V=V), ref, r.k, r.m, r.n)
+            rows.append((f"{r.m}x{r.n}", r.k, r.q, e))
+        rhos = np.array([x[3]["rho"] for x in rows])
+        rf = np.array([x[3]["ratio_fro"] for x in rows])
+        r2 = np.array([x[3]["ratio_2"] for x in rows])
+        err = {"requests": len(rows), "sizes": sorted({x[0] for x in rows}),
+               "rho_max": float(rhos.max()), "rho_median": float(np.median(rhos)),
+               "ratio_fro_max": float(rf.max()), "ratio_fro_median": float(np.median(rf)),
+               "ratio_2_max": float(r2.max()), "ratio_2_median": float(np.median(r2)),
+               "note": "GPU factors of sampled timed requests (own output buffers) vs the FP64 oracle on the "
+                       "same BF16 values and Psi; ratio = GPU rank-k error / oracle's"}
+        if not args.no_cpu_baseline:
+            cpu = {"value": len(rows) / tsum, "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
+                   "sample": f"FP64 oracle on the {len(rows)} sampled timed requests (all size classes), "
+                             "sequential"}
     if rank == 0:
         out = {"metric": "CoR-UTV serving p99 latency", "value": p99, "unit": "ms", "n_gpus": world,
                "steps": len(res), "warmup": len(warm), "ms_per_step": float(np.mean(lat)),
@@ -787,10 +816,10 @@ def main_serving(args):
                                           "count": len(v)} for k, v in by_cls.items()},
                "batches": st1["batches"] - st0["batches"],
                "mean_batch": len(res) / max(1, st1["batches"] - st0["batches"]),
-               "roofline": None, "cpu_baseline": cpu,
+               "roofline": None, "cpu_baseline": cpu, "error_vs_oracle": err,
                "e2e": {"value": p99, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
                        "note": "latency through the public server API with device-resident requests"},
-               "gpu_launches": None, "clocks": clk}
+               "gpu_launches": int(st1["launches"] - st0["launches"]), "clocks": clk}
         print(json.dumps(out), flush=True)
 
 

@@ -405,6 +405,10 @@ int corutv_server_poll(corutv_server* s, uint64_t ticket, corutv_info* info);
 /* Counters: batches launched, requests finished, requests waiting (any may be NULL). */
 int corutv_server_stats(corutv_server* s, int64_t* batches, int64_t* solved, int64_t* pending);
 
+/* Library kernels launched by the server's batches so far (direct launches and the kernels of
+ * replayed CUDA graphs), counted on the host as they are enqueued. */
+int corutv_server_launches(corutv_server* s, int64_t* launches);
+
 /* Stop accepting requests, finish the queued ones, stop the worker, free everything. */
 int corutv_server_destroy(corutv_server* s);
 

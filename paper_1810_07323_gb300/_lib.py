@@ -99,7 +99,7 @@ EXPORTS = ("corutv_version", "corutv_status_string", "corutv_create", "corutv_de
            "corutv_qrcp", "corutv_fro2", "corutv_gram_noalloc", "corutv_solve_corrected", "corutv_quantize",
            "corutv_batch_workspace_size", "corutv_solve_batched", "corutv_batch_info_wait",
            "corutv_server_create", "corutv_server_submit", "corutv_server_poll", "corutv_server_stats",
-           "corutv_server_destroy", "corutv_rpca", "corutv_solve_host",
+           "corutv_server_launches", "corutv_server_destroy", "corutv_rpca", "corutv_solve_host",
            "corutv_residual_norm2", "corutv_host_read_time", "corutv_set_autotune", "corutv_batch_tuning_read")
 
 
@@ -134,6 +134,7 @@ def load() -> ctypes.CDLL:
     lib.corutv_server_submit.argtypes = [P, ctypes.POINTER(Problem), ctypes.POINTER(ctypes.c_uint64)]
     lib.corutv_server_poll.argtypes = [P, ctypes.c_uint64, ctypes.POINTER(Info)]
     lib.corutv_server_stats.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I64)]
+    lib.corutv_server_launches.argtypes = [P, ctypes.POINTER(I64)]
     lib.corutv_server_destroy.argtypes = [P]
     lib.corutv_info_wait.argtypes = [P, ctypes.POINTER(Info)]
     lib.corutv_pass.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, I64, I64, I64, P, P, I64, I32, P,
@@ -156,7 +157,8 @@ def load() -> ctypes.CDLL:
                  "corutv_orthonormalize", "corutv_gram", "corutv_qrcp", "corutv_fro2", "corutv_solve_corrected",
                  "corutv_quantize", "corutv_batch_workspace_size", "corutv_solve_batched",
                  "corutv_batch_info_wait", "corutv_server_create", "corutv_server_submit", "corutv_server_poll",
-                 "corutv_server_stats", "corutv_server_destroy", "corutv_rpca", "corutv_solve_host",
+                 "corutv_server_stats", "corutv_server_launches", "corutv_server_destroy", "corutv_rpca",
+                 "corutv_solve_host",
                  "corutv_residual_norm2", "corutv_host_read_time", "corutv_set_autotune",
                  "corutv_batch_tuning_read"):
         getattr(lib, name).restype = ctypes.c_int
@@ -551,7 +553,9 @@ class Server:
         b, s, p = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
         _check(load().corutv_server_stats(self.s, ctypes.byref(b), ctypes.byref(s), ctypes.byref(p)),
                "corutv_server_stats")
-        return dict(batches=b.value, solved=s.value, pending=p.value)
+        n = ctypes.c_int64()
+        _check(load().corutv_server_launches(self.s, ctypes.byref(n)), "corutv_server_launches")
+        return dict(batches=b.value, solved=s.value, pending=p.value, launches=n.value)
 
     def close(self):
         if self.s:

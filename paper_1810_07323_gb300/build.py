@@ -21,7 +21,8 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I" + CSRC, "-I" + os.path.join(ROOT, "include")]
 UNITS = ["corutv_abi.cu", "batched.cu", "server.cu", "pass_simt.cu", "pass_tc.cu", "pass_tc_grouped.cu",
-         "pass_tc_lp.cu", "pass_tc3.cu", "quant.cu", "small.cu", "noalloc.cu", "rpca.cu", "gram_tc.cu", "resid.cu"]
+         "pass_tc_lp.cu", "pass_tc_lp_grouped.cu", "pass_tc3.cu", "quant.cu", "small.cu", "noalloc.cu", "rpca.cu",
+         "gram_tc.cu", "resid.cu"]
 
 
 def _nvcc() -> str:

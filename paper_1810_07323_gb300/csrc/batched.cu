@@ -40,6 +40,19 @@ struct PassTable {
   int2* d_rmap = nullptr;
 };
 
+// one grouped kind::f16 pass (BF16 / FP8 problems): its problem table, the CTAs' runs of work
+// units, and the block maps of the sketch operand's split and of the ordered split-K reduction
+struct LpTable {
+  int which = 0, it = 0;
+  size_t off_gp = 0, off_cta = 0, off_smap = 0, off_rmap = 0;
+  int np = 0, G = 0, nsplit = 0, nred = 0, lmax = 1;
+  bool fro = false;
+  GLpProb* d_gp = nullptr;
+  int* d_cta = nullptr;
+  int2* d_smap = nullptr;
+  int2* d_rmap = nullptr;
+};
+
 // Shapes of a batched plan that the autotuner may change (defaults: the fixed plan).
 struct BatchTune {
   int gram_cols = kBatchGramCols;     // columns per Gram partial block
@@ -75,8 +88,10 @@ struct BatchState {
   int nmap[3][8] = {};
   int lp = 32, lmax = 1, maxq = 0, a_dtype = CORUTV_F32;
   bool any_exact = false, any_sketch = false, any_fro2 = false;
-  bool tc = false;                    // passes on the tensor cores
+  bool tc = false;                    // FP32 batch: passes on the tensor cores (grouped TF32)
   std::vector<PassTable> ptabs;       // index 2 * it + which (C1, C2), then the core pass
+  bool lpt = false;                   // BF16 / FP8 batch: some problems' passes on the grouped kind::f16 kernel
+  std::vector<LpTable> ltabs;         // index as ptabs
   std::vector<char> multi_pass;       // per power step: some problem runs more than one CholeskyQR pass
   std::vector<double> pass_bytes;     // SIMT passes: algorithmic bytes, [3 * it + which]
   cudaGraphExec_t exec = nullptr;
@@ -143,6 +158,24 @@ bool batch_uses_tc(int count, const corutv_problem* probs) {
   return true;
 }
 
+// Grouped kind::f16 passes for one BF16 / FP8 problem: rows TMA can address, no SIMT request.
+// Decided per problem, so a problem's pass engine (and its result) does not depend on its batch.
+bool f16_ok(const corutv_problem& p) {
+  if (p.a_dtype != CORUTV_BF16 && p.a_dtype != CORUTV_FP8_E4M3) return false;
+  if (p.mma != CORUTV_MMA_AUTO) return false;
+  const int eb = p.a_dtype == CORUTV_BF16 ? 2 : 1;
+  return aligned16(p.A) && (p.lda * eb) % 16 == 0;
+}
+
+enum PassEngine : char { kEngSimt = 0, kEngTf32 = 1, kEngF16 = 2 };
+
+void engines(int count, const corutv_problem* probs, std::vector<char>& eng) {
+  const bool tf32 = batch_uses_tc(count, probs);
+  eng.assign(count, kEngSimt);
+  for (int i = 0; i < count; ++i)
+    eng[i] = tf32 ? kEngTf32 : (f16_ok(probs[i]) ? kEngF16 : kEngSimt);
+}
+
 // Sizes of one problem's buffers (FP32 sketches and factors, FP64 l x l blocks).
 struct ProbSizes {
   int64_t len1, len2, ld1, ld2, ld3, tiles1, tiles2;
@@ -150,7 +183,7 @@ struct ProbSizes {
   size_t sk1, sk2, sk3, xr, gparts, ll8, ll4, defic, fparts, status, kparts;
 };
 
-ProbSizes prob_sizes(const corutv_problem& p, int lp, bool tc, const BatchTune& tune) {
+ProbSizes prob_sizes(const corutv_problem& p, int lp, char eng, const BatchTune& tune) {
   ProbSizes z{};
   const bool right = p.side == CORUTV_SIDE_RIGHT;
   z.len1 = right ? p.m : p.n;
@@ -170,7 +203,7 @@ ProbSizes prob_sizes(const corutv_problem& p, int lp, bool tc, const BatchTune& 
   z.sk1 = sizeof(float) * p.l * z.ld1;
   z.sk2 = sizeof(float) * p.l * z.ld2;
   z.sk3 = sizeof(float) * p.l * z.ld3;
-  z.xr = tc ? z.sk3 : 0;
+  z.xr = eng != kEngSimt ? z.sk3 : 0;       // TF32 operand, or its two BF16 parts
   z.gparts = sizeof(float) * (size_t)std::max(z.gp1, z.gp2) * lp * lp;
   z.ll8 = sizeof(double) * p.l * p.l;
   z.ll4 = sizeof(float) * p.l * p.l;
@@ -179,6 +212,16 @@ ProbSizes prob_sizes(const corutv_problem& p, int lp, bool tc, const BatchTune& 
   z.status = sizeof(DevStatus);
   z.kparts = sizeof(float) * (size_t)p.l *
              std::max<int64_t>(z.ks1 > 1 ? z.ks1 * z.len1 : 0, z.ks2 > 1 ? z.ks2 * z.len2 : 0);
+  if (eng == kEngF16) {
+    // grouped kind::f16 units: C1 / core reduce over len2 into len1 positions, C2 the other way;
+    // partials [split][l][ld], one sum(a^2) per unit of the first pass
+    const int s1 = lp_unit_nsplit(z.len2), s2 = lp_unit_nsplit(z.len1);
+    const size_t kp = sizeof(float) * (size_t)p.l *
+                      std::max<int64_t>(s1 > 1 ? s1 * z.ld1 : 0, s2 > 1 ? s2 * z.ld2 : 0);
+    z.kparts = std::max(z.kparts, kp);
+    z.nf = (int)std::max<int64_t>(z.nf, cdiv(z.len1, kLpUnitBN) * s1);
+    z.fparts = sizeof(double) * z.nf;
+  }
   return z;
 }
 
@@ -206,7 +249,8 @@ void add_blocks(std::vector<int2>& v, int p, int64_t n) {
 // Host-side plan: every table and its byte offset in the uploaded tables region.
 struct Plan {
   int count = 0, lp = 32, lmax = 1, maxq = 0;
-  bool tc = false;
+  bool tc = false, lpt = false;
+  std::vector<char> eng;              // pass engine per problem
   std::vector<ProbSizes> sz;
   std::vector<int2> maps[3][8];       // per class and MapKind
   size_t off_maps[3][8] = {};
@@ -214,6 +258,10 @@ struct Plan {
   std::vector<std::vector<int>> pt_probs;     // problems of each pass table
   std::vector<std::vector<int2>> pt_rmaps;
   std::vector<std::vector<int64_t>> pt_fro;   // fro slots per problem of the table (0: none)
+  std::vector<LpTable> ltabs;                 // grouped kind::f16 tables, index as ptabs
+  std::vector<std::vector<int>> lt_probs;     // problems of each table
+  std::vector<std::vector<int>> lt_cta;       // first unit of each CTA (G + 1 entries)
+  std::vector<std::vector<int2>> lt_smap, lt_rmap;
   size_t off_tmaps = 0, off_fro = 0, table_bytes = 0, total_fro = 0;
   size_t off_status = 0, off_bstatus = 0, off_partials = 0, off_probs = 0, need = 0;
   size_t off_kcount = 0, kcount_bytes = 0;    // split counters of the SIMT passes, all problems
@@ -227,13 +275,17 @@ void make_plan(Plan& L, int count, const corutv_problem* probs, int sms, const B
   }
   L.lp = lp_for(L.lmax);
   L.tc = batch_uses_tc(count, probs);
+  engines(count, probs, L.eng);
   L.sz.resize(count);
   for (int i = 0; i < count; ++i) {
     const corutv_problem& p = probs[i];
-    const ProbSizes& z = L.sz[i] = prob_sizes(p, kClassLP[lclass(p.l)], L.tc, tune);
+    const ProbSizes& z = L.sz[i] = prob_sizes(p, kClassLP[lclass(p.l)], L.eng[i], tune);
     std::vector<int2>* mc = L.maps[lclass(p.l)];
-    add_blocks(mc[kMapT1], i, z.tiles1 * z.ks1);
-    add_blocks(mc[kMapT2], i, z.tiles2 * z.ks2);
+    L.lpt |= L.eng[i] == kEngF16;
+    if (L.eng[i] == kEngSimt) {                 // CUDA-core pass blocks
+      add_blocks(mc[kMapT1], i, z.tiles1 * z.ks1);
+      add_blocks(mc[kMapT2], i, z.tiles2 * z.ks2);
+    }
     L.kcount_bytes += sizeof(int) * z.ntiles;
     add_blocks(mc[kMapG1], i, z.gp1);
     add_blocks(mc[kMapG2], i, z.gp2);
@@ -309,6 +361,74 @@ void make_plan(Plan& L, int count, const corutv_problem* probs, int sms, const B
     }
     L.off_tmaps = off;                              // 4 tensor maps per problem, 128 B each
     off += align_up(sizeof(CUtensorMap) * 4 * (size_t)count);
+  }
+  if (L.lpt) {
+    // grouped kind::f16 tables: (C1, C2) of every power step, then the exact-core pass
+    for (int t = 0; t < 2 * (L.maxq + 1) + 1; ++t) {
+      LpTable T;
+      T.which = t < 2 * (L.maxq + 1) ? t % 2 : kB_CORE;
+      T.it = t < 2 * (L.maxq + 1) ? t / 2 : 0;
+      std::vector<int> members;
+      for (int i = 0; i < count; ++i) {
+        const corutv_problem& p = probs[i];
+        if (L.eng[i] != kEngF16) continue;
+        if (T.which == kB_CORE ? p.core == CORUTV_CORE_EXACT : T.it <= p.q) members.push_back(i);
+      }
+      auto kk = [&](int i) { return T.which == kB_C2 ? L.sz[i].len1 : L.sz[i].len2; };
+      auto ll = [&](int i) { return T.which == kB_C2 ? L.sz[i].len2 : L.sz[i].len1; };
+      if (tune.tc_order == 1)
+        std::stable_sort(members.begin(), members.end(), [&](int a, int b) {
+          return kk(a) != kk(b) ? kk(a) > kk(b) : ll(a) > ll(b);
+        });
+      // units in table order, weighted by k-blocks (+1 for the epilogue's tile write)
+      std::vector<int> w;
+      std::vector<int2> smap, rmap;
+      for (size_t u = 0; u < members.size(); ++u) {
+        const int i = members[u];
+        const int64_t len = ll(i), K = kk(i);
+        const int64_t tiles = cdiv(len, kLpUnitBN), KB = lp_unit_kblocks(K), kbc = lp_unit_kbc(K);
+        const int S = lp_unit_nsplit(K);
+        for (int s2 = 0; s2 < S; ++s2)
+          for (int64_t t2 = 0; t2 < tiles; ++t2) w.push_back((int)(std::min(KB, (s2 + 1) * kbc) - s2 * kbc) + 1);
+        add_blocks(smap, (int)u, cdiv(K, 256));
+        if (S > 1) add_blocks(rmap, (int)u, tiles);
+        T.lmax = std::max(T.lmax, (int)probs[i].l);
+        T.fro |= T.which == kB_C1 && T.it == 0 && probs[i].want_fro2;
+      }
+      const int64_t U = (int64_t)w.size();
+      T.np = (int)members.size();
+      T.G = (int)std::min<int64_t>(U, sms);
+      std::vector<int> first(T.G + 1, (int)U);
+      if (T.G > 0) {
+        // CTA c runs units [first[c], first[c + 1]): first[c] = first unit whose prefix weight
+        // reaches c / G of the total
+        double total = 0.0, acc = 0.0;
+        for (int x : w) total += x;
+        int c = 1;
+        first[0] = 0;
+        for (int64_t u = 0; u < U; ++u) {
+          while (c < T.G && acc >= total * c / T.G) first[c++] = (int)u;
+          acc += w[u];
+        }
+      }
+      T.nsplit = (int)smap.size();
+      T.nred = (int)rmap.size();
+      T.off_gp = off;
+      off += align_up(sizeof(GLpProb) * std::max(1, T.np));
+      T.off_cta = off;
+      off += align_up(sizeof(int) * first.size());
+      T.off_smap = off;
+      off += align_up(sizeof(int2) * std::max<size_t>(1, smap.size()));
+      T.off_rmap = off;
+      off += align_up(sizeof(int2) * std::max<size_t>(1, rmap.size()));
+      L.ltabs.push_back(T);
+      L.lt_probs.push_back(members);
+      L.lt_cta.push_back(first);
+      L.lt_smap.push_back(smap);
+      L.lt_rmap.push_back(rmap);
+    }
+    L.off_tmaps = off;                              // 6 tensor maps per problem, 128 B each
+    off += align_up(sizeof(CUtensorMap) * 6 * (size_t)count);
   }
   L.table_bytes = off;                              // uploaded part
   L.off_fro = off;
@@ -444,6 +564,26 @@ int build(corutv_handle* h, BatchState* B, int count, const corutv_problem* prob
                 make_map_2d(&tm[3], Xr, p.l, z.len2, z.ld3, 4, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 32, 128, true);
       if (!ok) return CORUTV_ERR_CUDA;
     }
+    if (L.eng[i] == kEngF16) {
+      // tensor maps: A tiles for A X and for A^T Y, the BF16 parts (Xh, Xl) of the sketch operand
+      // over len1 and over len2 columns; Xh and Xl share the Xr buffer (l rows of ld3 each)
+      CUtensorMap* tm = reinterpret_cast<CUtensorMap*>(hb + L.off_tmaps) + 6 * i;
+      char* Xh = reinterpret_cast<char*>(Xr);
+      char* Xl = Xh + 2 * (size_t)p.l * z.ld3;
+      const auto bf = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+      bool ok;
+      if (p.a_dtype == CORUTV_FP8_E4M3)       // raw bytes, no swizzle: 64 x 256 and 256 x 64 boxes
+        ok = make_map_2d(&tm[0], p.A, p.m, p.n, p.lda, 1, CU_TENSOR_MAP_DATA_TYPE_UINT8, 64, 256, false) &&
+             make_map_2d(&tm[1], p.A, p.m, p.n, p.lda, 1, CU_TENSOR_MAP_DATA_TYPE_UINT8, 256, 64, false);
+      else
+        ok = make_map_2d(&tm[0], p.A, p.m, p.n, p.lda, 2, bf, 64, 256, true) &&
+             make_map_2d(&tm[1], p.A, p.m, p.n, p.lda, 2, bf, 64, 64, true);
+      ok = ok && make_map_2d(&tm[2], Xh, p.l, z.len1, z.ld3, 2, bf, 64, 128, true) &&
+           make_map_2d(&tm[3], Xl, p.l, z.len1, z.ld3, 2, bf, 64, 128, true) &&
+           make_map_2d(&tm[4], Xh, p.l, z.len2, z.ld3, 2, bf, 64, 128, true) &&
+           make_map_2d(&tm[5], Xl, p.l, z.len2, z.ld3, 2, bf, 64, 128, true);
+      if (!ok) return CORUTV_ERR_CUDA;
+    }
     B->passes[i] = 2 * (p.q + 1) + (p.core == CORUTV_CORE_EXACT ? 1 : 0);
     B->want_fro2[i] = Q.want_fro2;
     B->any_exact |= p.core == CORUTV_CORE_EXACT;
@@ -503,6 +643,66 @@ int build(corutv_handle* h, BatchState* B, int count, const corutv_problem* prob
         }
         ibase += g.tiles * g.KB;
         tbase += g.tiles;
+      }
+    }
+  }
+  // grouped kind::f16 tables
+  B->lpt = L.lpt;
+  B->ltabs = L.ltabs;
+  if (L.lpt) {
+    const CUtensorMap* dmaps = reinterpret_cast<const CUtensorMap*>(d + L.off_tmaps);
+    for (size_t t = 0; t < L.ltabs.size(); ++t) {
+      LpTable& T = B->ltabs[t];
+      T.d_gp = reinterpret_cast<GLpProb*>(d + T.off_gp);
+      T.d_cta = reinterpret_cast<int*>(d + T.off_cta);
+      T.d_smap = reinterpret_cast<int2*>(d + T.off_smap);
+      T.d_rmap = reinterpret_cast<int2*>(d + T.off_rmap);
+      memcpy(hb + T.off_cta, L.lt_cta[t].data(), sizeof(int) * L.lt_cta[t].size());
+      if (!L.lt_smap[t].empty()) memcpy(hb + T.off_smap, L.lt_smap[t].data(), sizeof(int2) * L.lt_smap[t].size());
+      if (!L.lt_rmap[t].empty()) memcpy(hb + T.off_rmap, L.lt_rmap[t].data(), sizeof(int2) * L.lt_rmap[t].size());
+      GLpProb* gpv = reinterpret_cast<GLpProb*>(hb + T.off_gp);
+      int64_t ubase = 0;
+      for (int u = 0; u < T.np; ++u) {
+        const int i = L.lt_probs[t][u];
+        const corutv_problem& p = probs[i];
+        const BatchProb& Q = P[i];
+        const ProbSizes& z = L.sz[i];
+        GLpProb& g = gpv[u];
+        const bool second = T.which == kB_C2;
+        const int dir = second ? Q.dir2 : Q.dir1;
+        g.mapA = dmaps + 6 * i + (dir == CORUTV_DIR_AX ? 0 : 1);
+        g.mapXh = dmaps + 6 * i + (second ? 2 : 4);
+        g.mapXl = dmaps + 6 * i + (second ? 3 : 5);
+        g.Ct = T.which == kB_C1 ? Q.P1 : (second ? Q.P2 : Q.P3);
+        g.ldc = T.which == kB_C1 ? Q.ld1 : (second ? Q.ld2 : Q.ld3);
+        g.kparts = Q.kparts;
+        g.ldk = second ? z.ld2 : z.ld1;
+        g.X = second ? Q.P1 : Q.P2;
+        g.ldx = second ? Q.ld1 : Q.ld2;
+        // Xh / Xl sit right after P3 (see the carve order above)
+        g.Xh = reinterpret_cast<char*>(Q.P3) + align_up(z.sk3);
+        g.Xl = static_cast<char*>(g.Xh) + 2 * (size_t)p.l * z.ld3;
+        g.ldxs = z.ld3;
+        g.scales = p.a_tile_scales;
+        g.sld = cdiv(p.n, 128);
+        g.srows = cdiv(p.m, 128);
+        g.scols = cdiv(p.n, 128);
+        g.len = second ? z.len2 : z.len1;
+        g.K = second ? z.len1 : z.len2;
+        g.KB = lp_unit_kblocks(g.K);
+        g.kbc = lp_unit_kbc(g.K);
+        g.S = lp_unit_nsplit(g.K);
+        g.tiles = cdiv(g.len, kLpUnitBN);
+        g.units = g.tiles * g.S;
+        g.unit_base = ubase;
+        g.l = p.l;
+        g.dir = dir;
+        g.fro = nullptr;
+        if (T.which == kB_C1 && T.it == 0 && p.want_fro2) {
+          g.fro = Q.fparts;
+          P[i].nfparts = (int)g.units;
+        }
+        ubase += g.units;
       }
     }
   }
@@ -571,6 +771,11 @@ int pass_grouped(corutv_handle* h, const BatchState* B, int which, int it) {
   }
   const double bytes = B->pass_bytes[which == kB_CORE ? 3 * (B->maxq + 1) + kB_CORE : 3 * it + which];
   PhaseTimer tm(h, kPhPass, bytes);
+  if (B->lpt) {
+    const LpTable& T = B->ltabs[which == kB_CORE ? B->ltabs.size() - 1 : 2 * it + which];
+    CUB(launch_pass_lp_grouped(T.d_gp, T.np, B->a_dtype == CORUTV_FP8_E4M3, T.fro, T.d_cta, T.G, T.d_smap,
+                               T.nsplit, T.d_rmap, T.nred, T.lmax, B->bstatus, h->stream));
+  }
   const int k = which != kB_C2 ? kMapT1 : kMapT2;
   for (int c = 0; c < 3; ++c)
     CUB(launch_pass_simt_grouped(B->dprobs, B->map[c][k], B->nmap[c][k], kClassLP[c], B->a_dtype, which, it,
@@ -747,7 +952,13 @@ int time_plan(corutv_handle* h, BatchState* B, int count, const corutv_problem* 
 // Coordinate search over the plan's shapes, timing whole batches (outside any capture: the
 // first call of a problem set).  The cache answers first when it holds the key.
 int autotune(corutv_handle* h, BatchState* B, int count, const corutv_problem* probs, BatchTune* out) {
-  const bool tc = batch_uses_tc(count, probs);
+  std::vector<char> eng;
+  engines(count, probs, eng);
+  bool tc = false, simt = false;               // some problems on tensor-core tables / on CUDA cores
+  for (char e : eng) {
+    tc |= e != kEngSimt;
+    simt |= e == kEngSimt;
+  }
   const std::string key = tune_key(count, probs, tc);
   BatchTune best;
   for (const auto& kv : B->tuned_keys) {
@@ -790,7 +1001,7 @@ int autotune(corutv_handle* h, BatchState* B, int count, const corutv_problem* p
     c.gram_cols = gc;
     try_shape(c);
   }
-  if (!tc) {
+  if (simt) {
     for (int64_t sk : kTuneSplitK) {
       if (sk == best.split_k) continue;
       BatchTune c = best;

@@ -232,6 +232,55 @@ cudaError_t launch_pass_tc_grouped(const GPassProb* gp, int np, int64_t total_it
                                    const int2* round_map, int nround, float* partials, bool fro, int sms,
                                    DevStatus* status, cudaStream_t st);
 
+// Grouped kind::f16 passes (pass_tc_lp_grouped.cu) for batched BF16 / FP8 problems.  Work is
+// cut into units that depend on the problem alone -- one 256-position output tile and one K range
+// of kLpUnitK (whole 64-element k-blocks) -- so a problem's result does not depend on the other
+// problems of its batch: every unit starts its TMEM accumulator from zero, and a tile cut into S
+// K ranges is summed in range order by a separate reduction.  A CTA runs a contiguous run of
+// units (table cta_first, balanced by k-blocks on the host).
+constexpr int kLpUnitBN = 256;
+constexpr int kLpUnitBK = 64;
+constexpr int64_t kLpUnitK = 2048;
+constexpr int kLpMaxSplit = 64;
+inline int lp_unit_split(int64_t K) {
+  if (K <= 2 * kLpUnitK) return 1;
+  const int64_t s = (K + kLpUnitK - 1) / kLpUnitK;
+  return (int)(s < kLpMaxSplit ? s : kLpMaxSplit);
+}
+struct GLpProb {
+  const void* mapA;          // CUtensorMap of A (device memory) in this problem's direction
+  const void* mapXh;         // CUtensorMaps of the BF16 parts of the sketch operand: l rows x K,
+  const void* mapXl;         //   box 64 x 128, 128-byte swizzle
+  float* Ct;
+  int64_t ldc;
+  float* kparts;             // [split][l][ldk] partial products when S > 1
+  int64_t ldk;
+  const float* X;            // FP32 sketch operand (ST), split into Xh / Xl before the pass
+  int64_t ldx;
+  void* Xh;                  // BF16, l rows, leading dimension ldxs
+  void* Xl;
+  int64_t ldxs;
+  const float* scales;       // FP8: tile scales (srows x scols, leading dimension sld)
+  int64_t sld, srows, scols;
+  double* fro;               // one FP64 sum(a^2) per unit, or null
+  int64_t len, K, KB, kbc;   // kbc: k-blocks per unit (the last unit of a tile may hold fewer)
+  int64_t tiles, units, unit_base;
+  int S, l, dir;
+};
+// units of one problem's pass and their k-blocks
+inline int64_t lp_unit_kblocks(int64_t K) { return (K + kLpUnitBK - 1) / kLpUnitBK; }
+inline int64_t lp_unit_kbc(int64_t K) {
+  const int64_t KB = lp_unit_kblocks(K), S = lp_unit_split(K);
+  return (KB + S - 1) / S;
+}
+inline int lp_unit_nsplit(int64_t K) {
+  const int64_t KB = lp_unit_kblocks(K), c = lp_unit_kbc(K);
+  return (int)((KB + c - 1) / c);
+}
+cudaError_t launch_pass_lp_grouped(const GLpProb* gp, int np, bool fp8, bool fro, const int* cta_first, int G,
+                                   const int2* split_map, int nsplit, const int2* red_map, int nred, int lmax,
+                                   DevStatus* status, cudaStream_t st);
+
 // grouped small kernels (small.cu)
 constexpr int kBatchGramCols = 512;   // columns per Gram partial block
 constexpr int kBatchLmulBI = 128;     // columns per lmul tile

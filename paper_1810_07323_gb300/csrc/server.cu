@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "../../include/corutv.h"
+#include "handle.h"
 
 namespace {
 
@@ -64,6 +65,7 @@ struct corutv_server {
   cudaStream_t st[2] = {nullptr, nullptr};
   Inflight fl[2];
   int64_t batches = 0, solved = 0;
+  int64_t launches = 0;     // library kernels the batches launched (direct or in replayed graphs)
 };
 
 namespace {
@@ -134,13 +136,16 @@ void worker_main(corutv_server* s) {
     if (!f.busy) {
       form_batch(s, f);
       if (!f.tickets.empty()) {
+        const int64_t l0 = s->h[turn]->launches;
         const int rc = corutv_solve_batched(s->h[turn], (int)f.probs.size(), f.probs.data(), nullptr);
         if (rc != CORUTV_OK) {
           finish(s, f, rc);
         } else {
           cudaEventRecord(f.done, s->st[turn]);
           f.busy = true;
+          std::lock_guard<std::mutex> lk(s->mu);
           s->batches += 1;
+          s->launches += s->h[turn]->launches - l0;
         }
         turn ^= 1;
         progressed = true;
@@ -243,6 +248,13 @@ int corutv_server_stats(corutv_server* s, int64_t* batches, int64_t* solved, int
   if (batches) *batches = s->batches;
   if (solved) *solved = s->solved;
   if (pending) *pending = (int64_t)s->pending.size();
+  return CORUTV_OK;
+}
+
+int corutv_server_launches(corutv_server* s, int64_t* launches) {
+  if (!s || !launches) return CORUTV_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
+  *launches = s->launches;
   return CORUTV_OK;
 }
 

@@ -4,9 +4,13 @@ replay determinism of the captured batch, and the 1024-problem workload
 (m ~ U{256..4096}, n ~ U{128..2048}, l = r + 8, q = 1) on sampled problems.
 
 Batches of FP32 A whose rows TMA can address run the passes as grouped TF32
-tensor-core launches (bound rho <= 1e-3, as corutv_solve with mma = tf32);
-other batches accumulate FP32 products on the CUDA cores and the factorisations
-run in FP32 as in corutv_solve with mma = SIMT: rho <= 1e-4."""
+tensor-core launches (bound rho <= 1e-3, as corutv_solve with mma = tf32).
+BF16 / FP8 problems whose rows TMA can address run theirs as grouped kind::f16
+launches (BF16 A exact, the sketch split into two BF16 parts, FP32
+accumulation) whose work units depend on the problem alone, so each result is
+the same bits alone and in any batch; the rest accumulate FP32 products on the
+CUDA cores.  Both forms hold rho <= 1e-4, the factorisations running in FP32
+as in corutv_solve with mma = SIMT."""
 import numpy as np
 import pytest
 
@@ -135,6 +139,56 @@ def test_batched_split_k_parity(kind):
         assert rho < TOL, (i, rho)
         a2 = float(np.sum(Aq ** 2))
         assert abs(r.info.fro2_A - a2) < 1e-6 * a2
+
+
+F16 = [
+    # BF16 / FP8 rows TMA can address (n a multiple of 16): grouped kind::f16 passes.  K cut into
+    # ranges of 2048 k (C2 over 9216 and 40000 rows, the LEFT problem's C2 over 8704 columns, C1
+    # and the core over 9216 columns with ||A||^2 folded per unit), ragged tiles, l = 128, both
+    # sides and cores; the last problem's rows (129 elements) take the CUDA-core pass in the same batch
+    (9216, 160, 8, 8, 16, 1, "right", "exact", "stabilised"),
+    (208, 8704, 6, 6, 14, 1, "left", "exact", "stabilised"),
+    (304, 9216, 10, 10, 18, 0, "right", "exact", "stabilised"),
+    (40000, 144, 5, 5, 12, 1, "right", "sketch", "stabilised"),
+    (1000, 1008, 60, 60, 128, 2, "right", "exact", "strict"),
+    (700, 304, 6, 6, 14, 1, "right", "exact", "stabilised"),
+    (333, 129, 4, 4, 12, 0, "right", "exact", "stabilised"),
+]
+
+
+@pytest.mark.parametrize("kind", ["bf16", "fp8"])
+def test_batched_f16_grouped_parity_and_alone(kind):
+    """Grouped kind::f16 passes: parity with the oracle on the stored values, ||A||^2 from
+    the first pass's units, replays bit-identical, and every problem's factors the same bits
+    when solved alone as in the batch."""
+    items, refs = [], []
+    for i, (m, n, r, k, l, q, side, core, orth) in enumerate(F16):
+        A = _lowrank_sparse(C.stream_seed(83, i), m, n, r).astype(np.float32)
+        phi = C.normal_block_np(C.stream_seed(84, i), l, 0, m if side == "left" else n, 0, l)
+        it, Aq = _item(A, phi, k, l, q, side, core, orth, kind=kind)
+        items.append(it)
+        refs.append((Aq, phi, k, l, q, side, core))
+    b = corutv.Batch(items)
+    outs = []
+    for _ in range(3):            # direct launches, capture, replay
+        res = b.run()
+        outs.append([(x.U.clone(), x.T.clone(), x.V.clone(), x.perm.clone()) for x in res])
+    for o in outs[1:]:
+        for a, c in zip(outs[0], o):
+            assert all(torch.equal(x, y) for x, y in zip(a, c))
+    for i, (r, (Aq, phi, k, l, q, side, core)) in enumerate(zip(res, refs)):
+        assert r.info.status == 0
+        rho = _check(r, Aq, phi, k, l, q, side, core)
+        print(f"{kind} f16 problem {i} {F16[i][:2]}: rho={rho:.3e}")
+        assert rho < TOL, (i, rho)
+        a2 = float(np.sum(Aq ** 2))
+        assert abs(r.info.fro2_A - a2) < 1e-6 * a2
+        assert r.info.passes_over_A == 2 * (q + 1) + (1 if core == "exact" else 0)
+    for i, (it, r) in enumerate(zip(items, res)):
+        alone = corutv.Batch([it]).run()[0]
+        assert torch.equal(alone.U, r.U) and torch.equal(alone.T, r.T), i
+        assert torch.equal(alone.V, r.V) and torch.equal(alone.perm, r.perm), i
+        assert alone.info.fro2_A == r.info.fro2_A and alone.info.fro2_T == r.info.fro2_T, i
 
 
 def test_batched_replay_is_identical():

@@ -1,8 +1,10 @@
 """GPU tests of the serving queue (corutv_server_*): every BF16 request's result
-equals the same problem solved alone (bit for bit: the CUDA-core batched
-kernels compute each problem independently of the others in its batch; FP32
-batches on the tensor cores split their passes by batch, so there results
-agree to rounding), the queue reports
+equals the same problem solved alone (bit for bit: the grouped kind::f16
+passes cut each problem into work units of its own -- output tile and K range
+-- and add split tiles in range order, and the other batched kernels compute
+each problem independently of the others in its batch; FP32 batches on the
+TF32 tensor-core pass split their passes by batch, so there results agree to
+rounding), the queue reports
 ERR_BUSY when full and never blocks, oversized requests fail with ERR_OOM,
 invalid ones are refused at submission, and results agree with the FP64
 oracle on sampled requests."""
@@ -60,6 +62,7 @@ def test_server_results_equal_solved_alone():
     st = srv.stats()
     srv.close()
     assert st["solved"] == len(items) and st["batches"] >= 3     # several batches, up to 8 requests each
+    assert st["launches"] >= 10 * st["batches"]                  # library kernels ran for every batch
     for t, it in zip(tickets, items):
         rc, res = done[t]
         assert rc == corutv.OK and res.info.status == 0
