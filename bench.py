@@ -47,6 +47,8 @@ WORKLOADS = {
     "fp8": dict(m=32768, n=16384, k=64, l=80, q=2, dtype="fp8", gen="config3"),
     # 1024 problems m ~ U{256..4096}, n ~ U{128..2048}, rank r ~ U{4..32} + 5% sparse, l = r + 8, q = 1
     "batched": dict(count=1024, q=1, dtype="f32", gen="config4"),
+    # the same 1024 problems with A stored in BF16 (grouped kind::f16 passes)
+    "batched_bf16": dict(count=1024, q=1, dtype="bf16", gen="config4"),
     # Poisson arrivals at 2000 req/s, sizes 70/25/5% of 1024x512, 8192x2048, 76800x200, BF16 A
     "serving": dict(rate=2000.0, duration=60.0, dtype="bf16", gen="config5"),
     # ALM-CoRUTV robust PCA (Alg. 5) on the Sec. VI-C synthetic data: n x n, rank 0.05 n, 5% +-80 spikes,
@@ -95,9 +97,11 @@ def parse():
                     help="batched / serving workloads: the fixed plan shapes instead of the autotuned ones")
     ap.add_argument("--autotune-cache", default=None,
                     help="JSON cache of tuned batch shapes (default: $CORUTV_AUTOTUNE_CACHE, else none)")
+    ap.add_argument("--count", type=int, default=None,
+                    help="batched workloads: the first COUNT problems of the 1024 (a smaller case for profiling)")
     args = ap.parse_args()
     w = dict(WORKLOADS[args.workload])
-    for key in ("m", "n", "q"):
+    for key in ("m", "n", "q", "count"):
         if getattr(args, key) is not None and key in w:
             w[key] = getattr(args, key)
     if w.get("gen") == "rpca" and args.sparse is not None:
@@ -115,7 +119,8 @@ def workload_label(w, core):
                 f"BF16 A, one solve per request")
     if w["gen"] == "config4":
         return (f"{w['count']} uneven problems m~U{{256..4096}} x n~U{{128..2048}}, A = X Y^T (rank r~U{{4..32}}) "
-                f"+ 5% sparse U[-10,10], l = r+8, q = {w['q']}, FP32, exact core, side LEFT when m < n, "
+                f"+ 5% sparse U[-10,10], l = r+8, q = {w['q']}, {'BF16' if w['dtype'] == 'bf16' else 'FP32'} A, "
+                f"exact core, side LEFT when m < n, "
                 f"one batched call per step")
     if w["gen"] == "config2":
         a = f"{w['m']}x{w['n']} FP32 A = G1 diag(i^-1.5) G2^T + 1e-8 noise"
@@ -501,11 +506,13 @@ def main_batched(args):
     w = args.w
     dev = torch.device("cuda", torch.cuda.current_device())
     probs = W.batch_config4(w["count"])
+    bf16 = w["dtype"] == "bf16"
+    adt, eb = (torch.bfloat16, 2) if bf16 else (torch.float32, 4)
     items = []
     for p in probs:
         side = "left" if p.m < p.n else "right"
         # rows padded to a 16-byte pitch so the tensor-core passes can read them by TMA
-        A = torch.zeros((p.m, -(-p.n // 4) * 4), dtype=torch.float32, device=dev)[:, :p.n]
+        A = torch.zeros((p.m, -(-p.n * eb // 16) * 16 // eb), dtype=adt, device=dev)[:, :p.n]
         A.copy_(p.content.dense_t(device=dev, dtype=torch.float32))
         phi = W.problem_phi_t(p, p.m if side == "left" else p.n, device=dev).float()
         items.append(dict(A=A, Phi=phi, k=p.k, l=p.l, q=w["q"], side=side, want_fro2=True))
@@ -556,12 +563,19 @@ def main_batched(args):
     avg_pass_ms = tr.pass_ms / max(tr.pass_launches, 1)
     bytes_per_pass = tr.pass_bytes / max(tr.pass_launches, 1)
     achieved = bytes_per_pass / (avg_pass_ms / 1e3) / 1e9
-    tkey = f"pass_tc_grouped_kernel/f32/config4x{count}/src-" + kernel_source_tag("pass_tc_grouped.cu",
-                                                                                     "tc_common.cuh")
+    if bf16:
+        tkey = f"pass_lp_grouped_kernel/bf16/config4x{count}/src-" + kernel_source_tag(
+            "pass_tc_lp_grouped.cu", "tc_lp_common.cuh", "tc_common.cuh")
+        kdesc = ("pass_lp_grouped_kernel (all problems' A X or A^T Y in one kind::f16 launch of per-problem "
+                 "units) incl. the sketch operand's BF16 split and the ordered split-K reduction")
+    else:
+        tkey = f"pass_tc_grouped_kernel/f32/config4x{count}/src-" + kernel_source_tag("pass_tc_grouped.cu",
+                                                                                         "tc_common.cuh")
+        kdesc = ("pass_tc_grouped_kernel (all problems' A X or A^T Y in one TF32 launch) incl. operand "
+                 "rounding and split-tile reduce")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_source": peak_src,
-                "kernel": "pass_tc_grouped_kernel (all problems' A X or A^T Y in one TF32 launch) incl. operand "
-                          "rounding and split-tile reduce",
+                "kernel": kdesc,
                 "bytes_per_launch": bytes_per_pass, "ms_per_launch": avg_pass_ms,
                 "traffic": traffic_from_profiles(tkey), "timing": "two traced, uncaptured runs of the batch"}
 
@@ -578,7 +592,7 @@ def main_batched(args):
     e2e = None
     if not args.no_e2e:
         total = sum(it["A"].numel() for it in items)
-        host = torch.empty(total, dtype=torch.float32, pin_memory=True)
+        host = torch.empty(total, dtype=adt, pin_memory=True)
         views, off = [], 0
         for it in items:
             nel = it["A"].numel()
@@ -610,7 +624,7 @@ def main_batched(args):
         f1.record(stream)
         torch.cuda.synchronize()
         ms_e2e = max_over_ranks(f0.elapsed_time(f1), world)
-        h2d = total * 4
+        h2d = total * eb
         d2h = sum(r.U.numel() * 4 + r.V.numel() * 4 + r.T.numel() * 8 + r.perm.numel() * 4 for r in res)
         e2e = {"value": world * count * e2e_steps / (ms_e2e / 1e3), "unit": "solves/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": e2e_steps}
@@ -628,12 +642,14 @@ def main_batched(args):
     if rank == 0:
         out = {"metric": "CoR-UTV solves/s", "value": value, "unit": "solves/s", "n_gpus": world,
                "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_total / args.steps,
-               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+               "dtype": "bf16 A, fp32 products (split sketch operand)" if bf16 else "f32",
                "data": "synthetic",
                "config": {"workload": workload_label(w, "exact"), "count": count,
-                          "A_GB": sum(it["A"].numel() for it in items) * 4 / 1e9,
+                          "A_GB": sum(it["A"].numel() for it in items) * eb / 1e9,
                           "passes_per_step": 2 * (w["q"] + 1) + 1,
-                          "l2": "inputs larger than L2 (9.7 GB of A per step)",
+                          "l2": f"inputs larger than L2 ({sum(it['A'].numel() for it in items) * eb / 1e9:.1f} GB "
+                                f"of A per step)",
                           "parallelism": f"replicas x{world}"},
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                "autotune": (dict(tuning, speedup_in_search=(tuning["default_ms"] / tuning["tuned_ms"]
