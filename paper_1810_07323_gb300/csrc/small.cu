@@ -776,22 +776,30 @@ __device__ __forceinline__ void lmul_tile(const TC* __restrict__ In, int64_t ldi
     }
   }
   __syncthreads();
+  // A thread's R rows: H = R / 2 rows from the top half, [H ty, H ty + H), and H from the bottom
+  // half in reverse order, [LP - H (ty + 1), LP - H ty).  With an upper-triangular S (row j needs
+  // p <= j) every thread then does the same work: H (ty + 1) + (LP - H ty) steps over its halves.
+  constexpr int H = R / 2;
+  static_assert(H >= 1 && 2 * H == R, "lmul rows per thread");
+  auto row_of = [&](int v) { return v < H ? H * ty + v : LP - H * (ty + 1) + (v - H); };
   TC acc[R][RI];
 #pragma unroll
   for (int v = 0; v < R; ++v)
 #pragma unroll
     for (int u = 0; u < RI; ++u) acc[v][u] = TC(0);
-  int pend = l;
+  // steps for both halves, then the bottom half alone (bounds taken over the warp's two ty)
+  int pA = l, pB = l;
   if (upper) {
-    // the warp's rows: ty and ty ^ 1 (both halves of the warp); the larger bounds the loop
-    const int jmax = R * ((ty | 1) + 1);
-    pend = jmax < l ? jmax : l;
+    pA = H * ((ty | 1) + 1);
+    pB = LP - H * (ty & ~1);
+    pA = pA < l ? pA : l;
+    pB = pB < l ? pB : l;
   }
 #pragma unroll 2
-  for (int p = 0; p < pend; ++p) {
+  for (int p = 0; p < pA; ++p) {
     TC sv[R], xv[RI];
 #pragma unroll
-    for (int v = 0; v < R; ++v) sv[v] = Ss[p * SP + R * ty + v];
+    for (int v = 0; v < R; ++v) sv[v] = Ss[p * SP + row_of(v)];
 #pragma unroll
     for (int u = 0; u < RI; ++u) xv[u] = Is[p * IP + RI * tx + u];
 #pragma unroll
@@ -799,10 +807,22 @@ __device__ __forceinline__ void lmul_tile(const TC* __restrict__ In, int64_t ldi
 #pragma unroll
       for (int u = 0; u < RI; ++u) acc[v][u] = fma(sv[v], xv[u], acc[v][u]);
   }
+#pragma unroll 2
+  for (int p = pA; p < pB; ++p) {
+    TC sv[H], xv[RI];
+#pragma unroll
+    for (int v = 0; v < H; ++v) sv[v] = Ss[p * SP + row_of(H + v)];
+#pragma unroll
+    for (int u = 0; u < RI; ++u) xv[u] = Is[p * IP + RI * tx + u];
+#pragma unroll
+    for (int v = 0; v < H; ++v)
+#pragma unroll
+      for (int u = 0; u < RI; ++u) acc[H + v][u] = fma(sv[v], xv[u], acc[H + v][u]);
+  }
   if (!out_rowmajor) {
 #pragma unroll
     for (int v = 0; v < R; ++v) {
-      const int j = R * ty + v;
+      const int j = row_of(v);
       if (j >= l) continue;
       const bool repl = defic && defic[j];
 #pragma unroll
@@ -823,7 +843,7 @@ __device__ __forceinline__ void lmul_tile(const TC* __restrict__ In, int64_t ldi
 #pragma unroll
     for (int v = 0; v < R; ++v)
 #pragma unroll
-      for (int u = 0; u < RI; ++u) Os[(RI * tx + u) * (LP + 1) + R * ty + v] = acc[v][u];
+      for (int u = 0; u < RI; ++u) Os[(RI * tx + u) * (LP + 1) + row_of(v)] = acc[v][u];
     __syncthreads();
     for (int e = tid; e < BI * l; e += 256) {
       const int ii = e / l, j = e % l;
@@ -1771,8 +1791,118 @@ __device__ __forceinline__ bool batch_gram_sel(const BatchProb& P, int which, in
   }
 }
 
+// FP32 Gram partial of one column range for the grouped launches, with register tiles: a
+// thread owns a TM x TM tile of the LP x LP partial (TM = 4 for LP <= 64, 8 for LP = 128), so
+// each k costs two or four 16-byte shared loads per 16 or 64 FMAs.  For LP = 32 the 64 tiles are
+// computed by four groups of 64 threads, group g taking the columns k = g mod 4 of every staged
+// block; the group sums are added in group order at the end.  The sums are over this problem's
+// own column range only, so the result does not depend on the other problems of the batch.
 template <int LP>
-__global__ void __launch_bounds__(512) gram_partial_grouped_kernel(const BatchProb* __restrict__ probs,
+__device__ __forceinline__ void gram_tiles_body(const float* __restrict__ Xt, int64_t ldx,
+                                                const float* __restrict__ Yt, int64_t ldy, int64_t len, int l,
+                                                float* __restrict__ parts, int cta, int ncta) {
+  constexpr int TM = LP == 128 ? 8 : 4;
+  constexpr int TS = LP / TM, NT = TS * TS, G = 256 / NT;
+  static_assert(G >= 1 && NT * G == 256, "gram tiles");
+  constexpr int BK = 32, LPP = LP + 4;
+  constexpr int PER = LP * BK / 4 / 256;        // 16-byte loads of X (and of Y) per thread per stage
+  __shared__ __align__(16) float Xs[BK][LPP];
+  __shared__ __align__(16) float Ys[BK][LPP];
+  __shared__ __align__(16) float red[G > 1 ? NT * TM * TM : 1];
+  const int tid = threadIdx.x;
+  const int g = tid / NT, t = tid - g * NT, ti = t / TS, tj = t - ti * TS;
+  const int64_t chunk = cdiv(cdiv(len, BK), ncta) * BK;
+  const int64_t c0 = cta * chunk;
+  int64_t c1 = c0 + chunk;
+  if (c1 > len) c1 = len;
+  const bool same = Xt == Yt && ldx == ldy;     // X X^T: Y is not staged separately
+  const bool vec = (ldx & 3) == 0 && (ldy & 3) == 0 && ((uintptr_t)Xt & 15) == 0 && ((uintptr_t)Yt & 15) == 0;
+  float acc[TM][TM];
+#pragma unroll
+  for (int v = 0; v < TM; ++v)
+#pragma unroll
+    for (int u = 0; u < TM; ++u) acc[v][u] = 0.f;
+  float4 px[PER], py[PER];
+  auto load4 = [&](const float* base, int64_t ld, int r, int64_t g0) {
+    float4 v4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (r >= l) return v4;
+    const float* src = base + r * ld + g0;
+    if (vec && g0 + 3 < c1) return *reinterpret_cast<const float4*>(src);
+    if (g0 < c1) v4.x = src[0];
+    if (g0 + 1 < c1) v4.y = src[1];
+    if (g0 + 2 < c1) v4.z = src[2];
+    if (g0 + 3 < c1) v4.w = src[3];
+    return v4;
+  };
+  auto fetch = [&](int64_t k0) {
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int x = tid + 256 * q, r = x / (BK / 4), kk = 4 * (x % (BK / 4));
+      px[q] = load4(Xt, ldx, r, k0 + kk);
+      if (!same) py[q] = load4(Yt, ldy, r, k0 + kk);
+    }
+  };
+  if (c0 < c1) fetch(c0);
+  for (int64_t k0 = c0; k0 < c1; k0 += BK) {
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int x = tid + 256 * q, r = x / (BK / 4), kk = 4 * (x % (BK / 4));
+      Xs[kk][r] = px[q].x; Xs[kk + 1][r] = px[q].y; Xs[kk + 2][r] = px[q].z; Xs[kk + 3][r] = px[q].w;
+      if (!same) {
+        Ys[kk][r] = py[q].x; Ys[kk + 1][r] = py[q].y; Ys[kk + 2][r] = py[q].z; Ys[kk + 3][r] = py[q].w;
+      }
+    }
+    __syncthreads();
+    if (k0 + BK < c1) fetch(k0 + BK);
+    const float (*Yv)[LPP] = same ? Xs : Ys;
+#pragma unroll 4
+    for (int kk = g; kk < BK; kk += G) {
+      float xa[TM], yb[TM];
+#pragma unroll
+      for (int v = 0; v < TM; v += 4) {
+        const float4 a4 = *reinterpret_cast<const float4*>(&Xs[kk][TM * ti + v]);
+        const float4 b4 = *reinterpret_cast<const float4*>(&Yv[kk][TM * tj + v]);
+        xa[v] = a4.x; xa[v + 1] = a4.y; xa[v + 2] = a4.z; xa[v + 3] = a4.w;
+        yb[v] = b4.x; yb[v + 1] = b4.y; yb[v + 2] = b4.z; yb[v + 3] = b4.w;
+      }
+#pragma unroll
+      for (int v = 0; v < TM; ++v)
+#pragma unroll
+        for (int u = 0; u < TM; ++u) acc[v][u] = fmaf(xa[v], yb[u], acc[v][u]);
+    }
+    __syncthreads();
+  }
+  if constexpr (G > 1) {
+    // group sums in group order
+#pragma unroll 1
+    for (int gg = 1; gg < G; ++gg) {
+      if (g == gg)
+#pragma unroll
+        for (int v = 0; v < TM; ++v)
+#pragma unroll
+          for (int u = 0; u < TM; ++u) red[(t * TM + v) * TM + u] = acc[v][u];
+      __syncthreads();
+      if (g == 0)
+#pragma unroll
+        for (int v = 0; v < TM; ++v)
+#pragma unroll
+          for (int u = 0; u < TM; ++u) acc[v][u] += red[(t * TM + v) * TM + u];
+      __syncthreads();
+    }
+  }
+  if (g == 0) {
+    float* out = parts + (int64_t)cta * LP * LP;
+#pragma unroll
+    for (int v = 0; v < TM; ++v)
+#pragma unroll
+      for (int u = 0; u < TM; u += 4)
+        *reinterpret_cast<float4*>(&out[(TM * ti + v) * LP + TM * tj + u]) =
+            make_float4(acc[v][u], acc[v][u + 1], acc[v][u + 2], acc[v][u + 3]);
+  }
+}
+
+template <int LP>
+__global__ void __launch_bounds__(256) gram_partial_grouped_kernel(const BatchProb* __restrict__ probs,
                                                                    const int2* __restrict__ map, int which, int it,
                                                                    int pass) {
   const int2 pm = map[blockIdx.x];
@@ -1782,7 +1912,7 @@ __global__ void __launch_bounds__(512) gram_partial_grouped_kernel(const BatchPr
   float* out;
   if (!batch_gram_sel(P, which, it, pass, &X, &ldx, &Y, &ldy, &len, &out)) return;
   const int nparts = (which == kG_ORTH2 || which == kG_CORE_SKETCH) ? P.gp2 : P.gp1;
-  gram_partial_body<float, LP>(X, ldx, Y, ldy, len, P.l, P.gparts, pm.y, nparts);
+  gram_tiles_body<LP>(X, ldx, Y, ldy, len, P.l, P.gparts, pm.y, nparts);
 }
 
 template <int LP>
@@ -1886,15 +2016,15 @@ cudaError_t launch_gram_grouped(const BatchProb* P, const int2* map_parts, int n
                                 int nred, int lp, int which, int it, int pass, cudaStream_t st) {
   if (nparts <= 0 || nred <= 0) return cudaSuccess;
   if (lp <= 32) {
-    gram_partial_grouped_kernel<32><<<nparts, 512, 0, st>>>(P, map_parts, which, it, pass);
+    gram_partial_grouped_kernel<32><<<nparts, 256, 0, st>>>(P, map_parts, which, it, pass);
     CORUTV_COUNT_LAUNCH();
     gram_reduce_grouped_kernel<32><<<nred, 256, 0, st>>>(P, map_red, which, it, pass);
   } else if (lp <= 64) {
-    gram_partial_grouped_kernel<64><<<nparts, 512, 0, st>>>(P, map_parts, which, it, pass);
+    gram_partial_grouped_kernel<64><<<nparts, 256, 0, st>>>(P, map_parts, which, it, pass);
     CORUTV_COUNT_LAUNCH();
     gram_reduce_grouped_kernel<64><<<nred, 256, 0, st>>>(P, map_red, which, it, pass);
   } else {
-    gram_partial_grouped_kernel<128><<<nparts, 512, 0, st>>>(P, map_parts, which, it, pass);
+    gram_partial_grouped_kernel<128><<<nparts, 256, 0, st>>>(P, map_parts, which, it, pass);
     CORUTV_COUNT_LAUNCH();
     gram_reduce_grouped_kernel<128><<<nred, 256, 0, st>>>(P, map_red, which, it, pass);
   }
