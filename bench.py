@@ -1046,10 +1046,15 @@ def main():
     bytes_per_pass = tr.pass_bytes / max(tr.pass_launches, 1)
     achieved = bytes_per_pass / (avg_pass_ms / 1e3) / 1e9
     if lowp:
-        kname = "pass_tc_lp_kernel (kind::f16, %s A, dir AX / ATY) incl. operand split and split-tile reduce" % (
-            "BF16" if w["dtype"] == "bf16" else "FP8")
-        tkey = f"pass_tc_lp_kernel/{w['dtype']}/{m}x{n}/l{l}/src-" + kernel_source_tag("pass_tc_lp.cu",
-                                                                                       "tc_common.cuh")
+        if w["dtype"] == "bf16":
+            kname = "pass_tc_lp_kernel (kind::f16, BF16 A, dir AX / ATY) incl. operand split and split-tile reduce"
+            kfn = "pass_tc_lp_kernel"
+        else:
+            kname = ("pass_tc_lp8_kernel (kind::f16, FP8 A dequantised to BF16 by converter warps through "
+                     "decoupled rings, dir AX / ATY) incl. operand split and split-tile reduce")
+            kfn = "pass_tc_lp8_kernel"
+        tkey = f"{kfn}/{w['dtype']}/{m}x{n}/l{l}/src-" + kernel_source_tag("pass_tc_lp.cu", "tc_lp_common.cuh",
+                                                                           "tc_common.cuh")
     elif f32_engine(args.mma) == "tf32x3":
         kname = "pass_tc3_kernel (dir AX / ATY, split-operand TF32, A in TMEM) incl. operand split and " \
                 "split-tile reduce"

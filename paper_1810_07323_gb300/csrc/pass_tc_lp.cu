@@ -228,6 +228,234 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
   }
 }
 
+// FP8 A with decoupled rings.  The FP8 tiles, the dequantised BF16 tiles and the sketch tiles
+// each get their own ring, so a stage no longer holds its shared memory from the TMA copy
+// through the conversion to the MMA: FP8 copies (16 KB) run four ahead of the converter warps,
+// the converters fill two BF16 slots ahead of the MMA, and a second producer warp keeps three
+// sketch stages ahead of the MMA.  (One 80 KB stage per iteration allows only two in flight,
+// and the DRAM latency then bounds the pass.)  Warps: 0 FP8 TMA, 1 MMA, 2..5 epilogue, 6..13
+// converters, 14 sketch TMA.
+constexpr int k8S = 4;                     // FP8 staging slots
+constexpr int k8A = 2;                     // BF16 A slots
+constexpr int k8X = 3;                     // sketch (X_hi + X_lo) slots
+constexpr int k8ConvWarps = 8;
+constexpr int k8XWarp = 6 + k8ConvWarps;
+constexpr int k8Threads = 32 * (k8XWarp + 1);
+constexpr int k8Smem = k8S * kF8Tile + k8A * kATile + k8X * 2 * kXTile + 1024 + 512;
+static_assert(k8Smem <= 232448, "shared memory");
+
+template <int DIR, bool FRO>
+__global__ void __launch_bounds__(k8Threads, 1)
+    pass_tc_lp8_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapXh,
+                       const __grid_constant__ CUtensorMap mapXl, LpArgs args) {
+  extern __shared__ uint8_t smem_dyn[];
+  uint8_t* smem = smem_dyn + ((1024u - (smem_u32(smem_dyn) & 1023u)) & 1023u);
+  uint8_t* a_slots = smem;                                   // k8A x 32 KB (1024-aligned)
+  uint8_t* x_slots = a_slots + k8A * kATile;                 // k8X x (X_hi 16 KB | X_lo 16 KB)
+  uint8_t* f_slots = x_slots + k8X * 2 * kXTile;             // k8S x 16 KB
+  auto a_tile = [&](int q) { return a_slots + q * kATile; };
+  auto xh_tile = [&](int q) { return x_slots + q * 2 * kXTile; };
+  auto xl_tile = [&](int q) { return x_slots + q * 2 * kXTile + kXTile; };
+  auto f8_tile = [&](int q) { return f_slots + q * kF8Tile; };
+  uint64_t* bars = reinterpret_cast<uint64_t*>(f_slots + k8S * kF8Tile);
+  // ffull/fempty[k8S], afull/aempty[k8A], xfull/xempty[k8X], tfull/tempty[2]
+  constexpr int kBars = 2 * k8S + 2 * k8A + 2 * k8X + 4;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + kBars);
+  double* fro_red = reinterpret_cast<double*>(bars + kBars + 2);
+  volatile int* conv_abort = reinterpret_cast<volatile int*>(fro_red + k8ConvWarps);
+  const uint32_t ffull0 = smem_u32(bars), fempty0 = ffull0 + 8 * k8S;
+  const uint32_t afull0 = fempty0 + 8 * k8S, aempty0 = afull0 + 8 * k8A;
+  const uint32_t xfull0 = aempty0 + 8 * k8A, xempty0 = xfull0 + 8 * k8X;
+  const uint32_t tfull0 = xempty0 + 8 * k8X, tempty0 = tfull0 + 16;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t KB = cdiv(args.K, kBK);
+  StreamK sk(cdiv(args.len, kBN), KB, gridDim.x);
+  const int64_t s = sk.start(blockIdx.x), e = sk.start(blockIdx.x + 1);
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < k8S; ++i) {
+      mbar_init(ffull0 + 8 * i, 1);
+      mbar_init(fempty0 + 8 * i, k8ConvWarps);
+    }
+    for (int i = 0; i < k8A; ++i) {
+      mbar_init(afull0 + 8 * i, k8ConvWarps);
+      mbar_init(aempty0 + 8 * i, 1);
+    }
+    for (int i = 0; i < k8X; ++i) {
+      mbar_init(xfull0 + 8 * i, 1);
+      mbar_init(xempty0 + 8 * i, 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(tfull0 + 8 * b, 1);
+      mbar_init(tempty0 + 8 * b, 4);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tmem_slot))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0 || warp == k8XWarp) {
+    // ---------------------------------------------------------------- TMA producers
+    // warp 0: FP8 tiles of A, paced by the converters; the last warp: the sketch tiles, paced by the MMA
+    if (lane == 0) {
+      const bool isA = warp == 0;
+      const int S = isA ? k8S : k8X;
+      const uint32_t full0 = isA ? ffull0 : xfull0, empty0 = isA ? fempty0 : xempty0;
+      const uint64_t pol = isA ? policy_evict_first() : policy_evict_last();
+      int64_t n = 0;
+      bool ok = true;
+      for (int64_t it = s; it < e; ++it, ++n) {
+        const int q = (int)(n % S);
+        const uint32_t ph = (uint32_t)((n / S) & 1);
+        if (!mbar_wait(empty0 + 8 * q, ph ^ 1, args.status)) { ok = false; break; }
+        const int64_t t = it / KB, kb = it - t * KB;
+        const int k0 = (int)(kb * kBK), p0 = (int)(t * kBN);
+        const uint32_t fb = full0 + 8 * q;
+        if (isA) {
+          mbar_arrive_expect_tx(fb, kF8Tile);
+          if (DIR == 0) tma_load_2d(smem_u32(f8_tile(q)), &mapA, fb, k0, p0, pol);   // 256 rows x 64 B
+          else tma_load_2d(smem_u32(f8_tile(q)), &mapA, fb, p0, k0, pol);            // 64 rows x 256 B
+        } else {
+          mbar_arrive_expect_tx(fb, 2 * kXTile);
+          tma_load_2d(smem_u32(xh_tile(q)), &mapXh, fb, k0, 0, pol);
+          tma_load_2d(smem_u32(xl_tile(q)), &mapXl, fb, k0, 0, pol);
+        }
+      }
+      // drain: every issued copy is consumed (or, after a timeout, has landed) before the exit
+      const int64_t first = n > S ? n - S : 0;
+      for (int64_t f = first; f < n; ++f) {
+        const int q = (int)(f % S);
+        const uint32_t ph = (uint32_t)((f / S) & 1);
+        if (ok) {
+          if (!mbar_wait(empty0 + 8 * q, ph, args.status)) ok = false;
+        }
+        if (!ok) mbar_wait(full0 + 8 * q, ph, args.status);
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_bf16(kM, kBN, DIR == 1);
+      int64_t n = 0;
+      int seg = 0;
+      bool ok = true;
+      int64_t it = s;
+      while (it < e && ok) {
+        const int64_t t = it / KB;
+        const int64_t kb1 = (e - t * KB < KB) ? (e - t * KB) : KB;
+        const int b = seg & 1;
+        const uint32_t tph = (uint32_t)((seg >> 1) & 1);
+        if (!mbar_wait(tempty0 + 8 * b, tph ^ 1, args.status)) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t tacc = tmem_base + (uint32_t)(b * kBN);
+        bool first = true;
+        for (; it < t * KB + kb1; ++it, ++n) {
+          const int qa = (int)(n % k8A), qx = (int)(n % k8X);
+          if (!mbar_wait(afull0 + 8 * qa, (uint32_t)((n / k8A) & 1), args.status) ||
+              !mbar_wait(xfull0 + 8 * qx, (uint32_t)((n / k8X) & 1), args.status)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t abase = smem_u32(a_tile(qa));
+          const uint32_t hbase = smem_u32(xh_tile(qx)), lbase = smem_u32(xl_tile(qx));
+#pragma unroll
+          for (int kk = 0; kk < kBK / 16; ++kk) {
+            const uint64_t bdesc =
+                DIR == 0 ? smem_desc(abase + kk * 32, 16, 1024) : smem_desc(abase + kk * 2048, kBK * 128, 1024);
+            mma_f16(tacc, smem_desc(hbase + kk * 32, 16, 1024), bdesc, idesc, (first && kk == 0) ? 0u : 1u);
+            mma_f16(tacc, smem_desc(lbase + kk * 32, 16, 1024), bdesc, idesc, 1u);
+          }
+          first = false;
+          mma_commit(aempty0 + 8 * qa);
+          mma_commit(xempty0 + 8 * qx);
+        }
+        if (!ok) break;
+        mma_commit(tfull0 + 8 * b);
+        ++seg;
+      }
+    }
+  } else if (warp < 6) {
+    // ---------------------------------------------------------------- epilogue (warps 2..5)
+    tc_epilogue<kBN, kM>(args.Ct, args.ldc, args.partials, args.len, args.l, KB, sk, s, e, tmem_base, tfull0,
+                         tempty0, args.status);
+  } else {
+    // ---------------------------------------------------------------- converters (warps 6..13)
+    constexpr int CT = 32 * k8ConvWarps;
+    const int ct = threadIdx.x - 192;
+    if (ct == 0) *conv_abort = 0;
+    asm volatile("bar.sync 1, %0;" ::"n"(CT) : "memory");
+    double fro = 0.0;
+    // FP8 tile scales of iteration i2, loaded one iteration ahead
+    auto scales_of = [&](int64_t i2, float& a, float& b) {
+      const int64_t t2 = i2 / KB, kb2 = i2 - t2 * KB;
+      lp_stage_scales(args.scales, args.sld, args.srows, args.scols, DIR, kb2, t2 * kBN, ct, a, b);
+    };
+    float sca = 1.f, scb = 1.f;
+    if (s < e) scales_of(s, sca, scb);
+    int64_t n = 0;
+    for (int64_t it = s; it < e; ++it, ++n) {
+      const int qf = (int)(n % k8S), qa = (int)(n % k8A);
+      float nsa = 1.f, nsb = 1.f;
+      if (it + 1 < e) scales_of(it + 1, nsa, nsb);
+      // the FP8 tile has landed and the MMA has released the BF16 slot; the converter warps give
+      // up together (one abort flag per stage)
+      if (!mbar_wait(ffull0 + 8 * qf, (uint32_t)((n / k8S) & 1), args.status) ||
+          !mbar_wait(aempty0 + 8 * qa, (uint32_t)(((n / k8A) & 1) ^ 1), args.status))
+        *conv_abort = 1;
+      asm volatile("bar.sync 1, %0;" ::"n"(CT) : "memory");
+      if (*conv_abort) break;
+      tc_fence_after();
+      fro += (double)lp_convert_stage<true, FRO, CT>(a_tile(qa), f8_tile(qf), DIR, sca, scb, ct);
+      sca = nsa;
+      scb = nsb;
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(afull0 + 8 * qa);
+        mbar_arrive(fempty0 + 8 * qf);
+      }
+    }
+    if (FRO) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) fro += __shfl_xor_sync(0xffffffffu, fro, o);
+      if (lane == 0) fro_red[warp - 6] = fro;
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (FRO && threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < k8ConvWarps; ++w) t += fro_red[w];
+    args.fro_parts[blockIdx.x] = t;
+  }
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem_base) : "memory");
+  }
+}
+
+template <int DIR, bool FRO>
+cudaError_t launch_lp8_variant(const CUtensorMap& mA, const CUtensorMap& mH, const CUtensorMap& mL,
+                               const LpArgs& la, int64_t G, cudaStream_t st) {
+  auto kern = pass_tc_lp8_kernel<DIR, FRO>;
+  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, k8Smem);
+  if (err != cudaSuccess) return err;
+  kern<<<(unsigned)G, k8Threads, k8Smem, st>>>(mA, mH, mL, la);
+  CORUTV_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
+
 // X (FP32 ST) -> X_hi = bf16(X), X_lo = bf16(X - X_hi)
 __global__ void split_bf16_kernel(const float* __restrict__ X, int64_t ldx, __nv_bfloat16* __restrict__ Xh,
                                   __nv_bfloat16* __restrict__ Xl, int64_t ldo, int l, int64_t len) {
@@ -305,8 +533,13 @@ cudaError_t launch_pass_tc_lp(const PassArgs& a, int dir, int a_dtype, int sms, 
             fro_parts, a.scales, a.scale_ld, cdiv(a.m, 128), cdiv(a.n, 128)};
   const bool fro = fro_parts != nullptr;
   cudaError_t err;
-  if (fp8) err = dir == 0 ? launch_lp_dir<0, true>(mA, mH, mL, la, fro, G, st) : launch_lp_dir<1, true>(mA, mH, mL, la, fro, G, st);
-  else err = dir == 0 ? launch_lp_dir<0, false>(mA, mH, mL, la, fro, G, st) : launch_lp_dir<1, false>(mA, mH, mL, la, fro, G, st);
+  if (fp8) {
+    if (dir == 0) err = fro ? launch_lp8_variant<0, true>(mA, mH, mL, la, G, st) : launch_lp8_variant<0, false>(mA, mH, mL, la, G, st);
+    else err = fro ? launch_lp8_variant<1, true>(mA, mH, mL, la, G, st) : launch_lp8_variant<1, false>(mA, mH, mL, la, G, st);
+  }
+  else {
+    err = dir == 0 ? launch_lp_dir<0, false>(mA, mH, mL, la, fro, G, st) : launch_lp_dir<1, false>(mA, mH, mL, la, fro, G, st);
+  }
   if (err != cudaSuccess) return err;
   return launch_streamk_reduce_f32(static_cast<float*>(a.Ct), a.ldc, static_cast<const float*>(a.partials), a.l,
                                    kM, kBN, a.len_out, cdiv(a.K, kBK), G, st);

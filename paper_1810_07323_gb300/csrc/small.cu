@@ -776,30 +776,22 @@ __device__ __forceinline__ void lmul_tile(const TC* __restrict__ In, int64_t ldi
     }
   }
   __syncthreads();
-  // A thread's R rows: H = R / 2 rows from the top half, [H ty, H ty + H), and H from the bottom
-  // half in reverse order, [LP - H (ty + 1), LP - H ty).  With an upper-triangular S (row j needs
-  // p <= j) every thread then does the same work: H (ty + 1) + (LP - H ty) steps over its halves.
-  constexpr int H = R / 2;
-  static_assert(H >= 1 && 2 * H == R, "lmul rows per thread");
-  auto row_of = [&](int v) { return v < H ? H * ty + v : LP - H * (ty + 1) + (v - H); };
   TC acc[R][RI];
 #pragma unroll
   for (int v = 0; v < R; ++v)
 #pragma unroll
     for (int u = 0; u < RI; ++u) acc[v][u] = TC(0);
-  // steps for both halves, then the bottom half alone (bounds taken over the warp's two ty)
-  int pA = l, pB = l;
+  int pend = l;
   if (upper) {
-    pA = H * ((ty | 1) + 1);
-    pB = LP - H * (ty & ~1);
-    pA = pA < l ? pA : l;
-    pB = pB < l ? pB : l;
+    // the warp's rows: ty and ty ^ 1 (both halves of the warp); the larger bounds the loop
+    const int jmax = R * ((ty | 1) + 1);
+    pend = jmax < l ? jmax : l;
   }
 #pragma unroll 2
-  for (int p = 0; p < pA; ++p) {
+  for (int p = 0; p < pend; ++p) {
     TC sv[R], xv[RI];
 #pragma unroll
-    for (int v = 0; v < R; ++v) sv[v] = Ss[p * SP + row_of(v)];
+    for (int v = 0; v < R; ++v) sv[v] = Ss[p * SP + R * ty + v];
 #pragma unroll
     for (int u = 0; u < RI; ++u) xv[u] = Is[p * IP + RI * tx + u];
 #pragma unroll
@@ -807,22 +799,10 @@ __device__ __forceinline__ void lmul_tile(const TC* __restrict__ In, int64_t ldi
 #pragma unroll
       for (int u = 0; u < RI; ++u) acc[v][u] = fma(sv[v], xv[u], acc[v][u]);
   }
-#pragma unroll 2
-  for (int p = pA; p < pB; ++p) {
-    TC sv[H], xv[RI];
-#pragma unroll
-    for (int v = 0; v < H; ++v) sv[v] = Ss[p * SP + row_of(H + v)];
-#pragma unroll
-    for (int u = 0; u < RI; ++u) xv[u] = Is[p * IP + RI * tx + u];
-#pragma unroll
-    for (int v = 0; v < H; ++v)
-#pragma unroll
-      for (int u = 0; u < RI; ++u) acc[H + v][u] = fma(sv[v], xv[u], acc[H + v][u]);
-  }
   if (!out_rowmajor) {
 #pragma unroll
     for (int v = 0; v < R; ++v) {
-      const int j = row_of(v);
+      const int j = R * ty + v;
       if (j >= l) continue;
       const bool repl = defic && defic[j];
 #pragma unroll
@@ -843,7 +823,7 @@ __device__ __forceinline__ void lmul_tile(const TC* __restrict__ In, int64_t ldi
 #pragma unroll
     for (int v = 0; v < R; ++v)
 #pragma unroll
-      for (int u = 0; u < RI; ++u) Os[(RI * tx + u) * (LP + 1) + row_of(v)] = acc[v][u];
+      for (int u = 0; u < RI; ++u) Os[(RI * tx + u) * (LP + 1) + R * ty + v] = acc[v][u];
     __syncthreads();
     for (int e = tid; e < BI * l; e += 256) {
       const int ii = e / l, j = e % l;
