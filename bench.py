@@ -97,6 +97,8 @@ def parse():
                     help="batched / serving workloads: the fixed plan shapes instead of the autotuned ones")
     ap.add_argument("--autotune-cache", default=None,
                     help="JSON cache of tuned batch shapes (default: $CORUTV_AUTOTUNE_CACHE, else none)")
+    ap.add_argument("--fuse-power", action="store_true",
+                    help="batched / serving workloads: fused power steps (A streamed from HBM once per step)")
     ap.add_argument("--count", type=int, default=None,
                     help="batched workloads: the first COUNT problems of the 1024 (a smaller case for profiling)")
     args = ap.parse_args()
@@ -515,7 +517,8 @@ def main_batched(args):
         A = torch.zeros((p.m, -(-p.n * eb // 16) * 16 // eb), dtype=adt, device=dev)[:, :p.n]
         A.copy_(p.content.dense_t(device=dev, dtype=torch.float32))
         phi = W.problem_phi_t(p, p.m if side == "left" else p.n, device=dev).float()
-        items.append(dict(A=A, Phi=phi, k=p.k, l=p.l, q=w["q"], side=side, want_fro2=True))
+        items.append(dict(A=A, Phi=phi, k=p.k, l=p.l, q=w["q"], side=side, want_fro2=True,
+                          fuse_power=args.fuse_power))
     stream = torch.cuda.current_stream()
     h = corutv.handle_for(stream)
     tuning = None
@@ -648,6 +651,8 @@ def main_batched(args):
                "config": {"workload": workload_label(w, "exact"), "count": count,
                           "A_GB": sum(it["A"].numel() for it in items) * eb / 1e9,
                           "passes_per_step": 2 * (w["q"] + 1) + 1,
+                          "hbm_passes_per_step": (w["q"] + 2) if args.fuse_power else 2 * (w["q"] + 1) + 1,
+                          "fused_power_steps": bool(args.fuse_power),
                           "l2": f"inputs larger than L2 ({sum(it['A'].numel() for it in items) * eb / 1e9:.1f} GB "
                                 f"of A per step)",
                           "parallelism": f"replicas x{world}"},
@@ -739,6 +744,7 @@ def main_serving(args):
         p = corutv.Problem()
         p.m, p.n, p.k, p.l, p.q = r.m, r.n, r.k, r.l, r.q
         p.side, p.core, p.orth, p.a_dtype, p.mma, p.want_fro2 = 0, 0, 0, 2, 0, 1
+        p.fuse_power = 1 if args.fuse_power else 0
         p.A, p.lda = A.data_ptr(), A.stride(0)
         p.Phi, p.ldphi = phi.data_ptr(), phi.stride(0)
         p.U, p.ldu, p.T, p.ldt = U.data_ptr(), U.stride(0), T.data_ptr(), T.stride(0)
@@ -825,6 +831,7 @@ def main_serving(args):
                "data": "synthetic",
                "config": {"workload": workload_label(w, "exact"), "requests": len(res),
                           "content": "4 matrices per size class and 4 Psi per (class, k), cycled",
+                          "fused_power_steps": bool(args.fuse_power),
                           "l2": "per-request A of 1-30 MB, many requests in flight",
                           "parallelism": f"replicas x{world}"},
                "p50_ms": p50, "p99_ms": p99, "solves_per_s": len(res) / wall,

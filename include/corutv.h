@@ -39,7 +39,7 @@
 extern "C" {
 #endif
 
-#define CORUTV_ABI_VERSION 6
+#define CORUTV_ABI_VERSION 7
 
 typedef enum {
   CORUTV_OK = 0,
@@ -127,7 +127,10 @@ typedef struct {
   int32_t status;          /* corutv_status of the device work (OK or ERR_TIMEOUT) */
   int32_t passes_over_A;   /* streaming passes over A enqueued by the solve */
   int32_t chol_fallbacks;  /* sketch columns found numerically dependent and replaced */
-  int32_t reserved0;
+  int32_t hbm_passes_over_A; /* of those passes, the ones that stream A from memory (HBM, or host
+                              memory for corutv_solve_host) rather than re-read it from L2: fewer
+                              than passes_over_A when a batched problem fuses its power steps
+                              (corutv_problem.fuse_power), passes_over_A otherwise */
   double chol_shift_rel;   /* shift of the first CholeskyQR pass, relative to trace(C^T C) */
   double fro2_A;           /* ||A||_F^2 if want_fro2, else NaN */
   double fro2_T;           /* ||T||_F^2 */
@@ -286,7 +289,16 @@ typedef struct {
   int32_t a_dtype;       /* F32, BF16 or FP8_E4M3 (Psi, U, V are FP32; T FP64) */
   int32_t mma;           /* AUTO or SIMT: the batched passes run on the CUDA cores */
   int32_t want_fro2;
-  int32_t reserved0;     /* must be zero */
+  int32_t fuse_power;    /* 1: fused power steps (Alg. 3 steps 3-4, read A once per step): the second
+                            product of every power step is formed from the unnormalised first,
+                            W = op2(A) C1, in the launch right after C1's, while A is still in L2
+                            (problems are taken in groups of at most ~80 MB of A), and
+                            C2 = op2(A) Q1 = W R1^-1 follows by applying the R^-1 of each
+                            CholeskyQR pass of orth(C1) to W as well; A then crosses HBM
+                            q + 1 (+ 1 for the exact core) times.  Exact in exact arithmetic;
+                            in floating point W R1^-1 carries the rounding of W amplified by up
+                            to cond(C1), so it suits well-conditioned sketches.  Tensor-core
+                            engines only (ignored for problems on the CUDA cores).  0: off */
   const void* A;
   int64_t lda;
   const float* a_tile_scales;
@@ -315,9 +327,12 @@ int corutv_batch_workspace_size(int count, const corutv_problem* probs, size_t* 
  * can address (16-byte aligned base and row pitch) run every pass as one
  * grouped TF32 tensor-core launch (mma AUTO or TF32; rounded operands, FP32
  * accumulation, problems' (tile, k-block) iterations concatenated and split
- * evenly over the SMs); otherwise, and for mma SIMT or BF16 / FP8 storage, the
- * passes run on the CUDA cores with FP32 accumulation, one CTA per 64 output
- * positions over the whole reduction.  Orthonormalisation and QRCP as in
+ * evenly over the SMs).  BF16 / FP8 problems whose rows TMA can address (mma
+ * AUTO) run theirs as grouped kind::f16 launches of per-problem work units (a
+ * 256-position tile and a K range of at most 2048, each started from zero, tiles
+ * cut into several ranges summed in range order), so each such problem's result
+ * is the same bits in any batch.  The rest (mma SIMT, unaligned rows) run on the
+ * CUDA cores with FP32 accumulation, one CTA per 64 output positions and K range.  Orthonormalisation and QRCP as in
  * corutv_solve.  Limits: l <= 128; a_dtype F64 and the BF16X2 / TF32_TRUNC
  * modes return ERR_UNSUPPORTED (TF32 needs FP32 storage).  The handle keeps a workspace and the tables of the last
  * problem set; calling again with an identical problem array (same shapes,

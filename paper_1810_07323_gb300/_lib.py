@@ -51,7 +51,7 @@ class Problem(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("k", ctypes.c_int32), ("l", ctypes.c_int32),
                 ("q", ctypes.c_int32), ("side", ctypes.c_int32), ("core", ctypes.c_int32),
                 ("orth", ctypes.c_int32), ("a_dtype", ctypes.c_int32), ("mma", ctypes.c_int32),
-                ("want_fro2", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("want_fro2", ctypes.c_int32), ("fuse_power", ctypes.c_int32),
                 ("A", ctypes.c_void_p), ("lda", ctypes.c_int64), ("a_tile_scales", ctypes.c_void_p),
                 ("Phi", ctypes.c_void_p), ("ldphi", ctypes.c_int64), ("U", ctypes.c_void_p),
                 ("ldu", ctypes.c_int64), ("T", ctypes.c_void_p), ("ldt", ctypes.c_int64),
@@ -61,7 +61,7 @@ class Problem(ctypes.Structure):
 
 class Info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("passes_over_A", ctypes.c_int32),
-                ("chol_fallbacks", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("chol_fallbacks", ctypes.c_int32), ("hbm_passes_over_A", ctypes.c_int32),
                 ("chol_shift_rel", ctypes.c_double), ("fro2_A", ctypes.c_double),
                 ("fro2_T", ctypes.c_double), ("fro2_Tk", ctypes.c_double)]
 
@@ -503,6 +503,7 @@ def _fill_problem(p, it):
     p.a_dtype = _dt_code(A)
     p.mma = MMA[it.get("mma", "auto")]
     p.want_fro2 = 1 if it.get("want_fro2", False) else 0
+    p.fuse_power = 1 if it.get("fuse_power", False) else 0
     sc = it.get("a_tile_scales")
     p.A, p.lda = A.data_ptr(), _rowmajor_ld(A)
     p.a_tile_scales = sc.data_ptr() if sc is not None else None
@@ -574,7 +575,7 @@ class Batch:
 
     items: list of dicts with keys A (device float32 / bfloat16 / float8_e4m3fn,
     one dtype for the batch), Phi (float32, n x l for side "right", m x l for
-    "left"), k, l and optionally q, side, core, orth, want_fro2, a_tile_scales.
+    "left"), k, l and optionally q, side, core, orth, want_fro2, a_tile_scales, fuse_power.
     The outputs (U, T, V, perm per problem) are allocated once, so running the
     same Batch again passes an identical problem array and the library replays
     its CUDA graph of the batch."""

@@ -35,6 +35,7 @@ struct PassTable {
   int64_t iters = 0, tiles = 0;
   int lmax = 1;
   bool fro = false;
+  bool keep_a = false;                // the C1 table of a fused group: A stays in L2 for the W launch
   double bytes = 0.0;
   GPassProb* d_gp = nullptr;
   int2* d_rmap = nullptr;
@@ -47,6 +48,8 @@ struct LpTable {
   size_t off_gp = 0, off_cta = 0, off_smap = 0, off_rmap = 0;
   int np = 0, G = 0, nsplit = 0, nred = 0, lmax = 1;
   bool fro = false;
+  bool keep_a = false;                // the C1 table of a fused group: A stays in L2 for the W launch
+  double bytes = 0.0;                 // algorithmic bytes of the pass
   GLpProb* d_gp = nullptr;
   int* d_cta = nullptr;
   int2* d_smap = nullptr;
@@ -91,7 +94,14 @@ struct BatchState {
   bool tc = false;                    // FP32 batch: passes on the tensor cores (grouped TF32)
   std::vector<PassTable> ptabs;       // index 2 * it + which (C1, C2), then the core pass
   bool lpt = false;                   // BF16 / FP8 batch: some problems' passes on the grouped kind::f16 kernel
-  std::vector<LpTable> ltabs;         // index as ptabs
+  std::vector<LpTable> ltabs;
+  // table indices (into ptabs or ltabs) per power step: the non-fused problems' C1 and C2, the
+  // fused problems' (C1, W) groups; then the exact core (-1: no table)
+  std::vector<int> t_c1, t_c2;
+  std::vector<std::vector<std::pair<int, int>>> t_groups;
+  int t_core = -1;
+  bool any_fuse = false;
+  std::vector<int> hbm_passes;        // passes per problem that stream A from HBM
   std::vector<char> multi_pass;       // per power step: some problem runs more than one CholeskyQR pass
   std::vector<double> pass_bytes;     // SIMT passes: algorithmic bytes, [3 * it + which]
   cudaGraphExec_t exec = nullptr;
@@ -118,6 +128,8 @@ size_t align_up(size_t x) { return (x + kBAlign - 1) / kBAlign * kBAlign; }
 
 enum MapKind { kMapT1 = 0, kMapT2, kMapG1, kMapG2, kMapRed, kMapLm1, kMapLm2, kMapS2 };
 constexpr int kClassLP[3] = {32, 64, 128};
+// A of one group of fused problems: small enough to stay in L2 (126 MB) between its C1 and W launches
+constexpr double kFuseGroupBytes = 80.0 * (1 << 20);
 // autotuner candidates (the first of each list is the largest plan: the workspace query sizes for it)
 constexpr int kTuneGramCols[4] = {256, 512, 1024, 2048};
 constexpr int64_t kTuneSplitK[3] = {1024, 2048, 4096};
@@ -125,7 +137,7 @@ int lclass(int l) { return l <= 32 ? 0 : (l <= 64 ? 1 : 2); }
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
 int validate(const corutv_problem& p) {
-  if (p.reserved0) return CORUTV_ERR_INVALID_ARG;
+  if (p.fuse_power != 0 && p.fuse_power != 1) return CORUTV_ERR_INVALID_ARG;
   for (int64_t r : p.reserved)
     if (r) return CORUTV_ERR_INVALID_ARG;
   if (p.a_dtype == CORUTV_F64) return CORUTV_ERR_UNSUPPORTED;
@@ -251,6 +263,10 @@ struct Plan {
   int count = 0, lp = 32, lmax = 1, maxq = 0;
   bool tc = false, lpt = false;
   std::vector<char> eng;              // pass engine per problem
+  std::vector<char> fuse;             // problem fuses its power steps (tensor-core engines)
+  std::vector<int> t_c1, t_c2;
+  std::vector<std::vector<std::pair<int, int>>> t_groups;
+  int t_core = -1;
   std::vector<ProbSizes> sz;
   std::vector<int2> maps[3][8];       // per class and MapKind
   size_t off_maps[3][8] = {};
@@ -258,7 +274,7 @@ struct Plan {
   std::vector<std::vector<int>> pt_probs;     // problems of each pass table
   std::vector<std::vector<int2>> pt_rmaps;
   std::vector<std::vector<int64_t>> pt_fro;   // fro slots per problem of the table (0: none)
-  std::vector<LpTable> ltabs;                 // grouped kind::f16 tables, index as ptabs
+  std::vector<LpTable> ltabs;                 // grouped kind::f16 tables
   std::vector<std::vector<int>> lt_probs;     // problems of each table
   std::vector<std::vector<int>> lt_cta;       // first unit of each CTA (G + 1 entries)
   std::vector<std::vector<int2>> lt_smap, lt_rmap;
@@ -300,135 +316,165 @@ void make_plan(Plan& L, int count, const corutv_problem* probs, int sms, const B
       L.off_maps[c][k] = off;
       off += align_up(sizeof(int2) * std::max<size_t>(1, L.maps[c][k].size()));
     }
-  if (L.tc) {
-    // pass tables: (C1, C2) of every power step, then the exact-core pass
-    for (int t = 0; t < 2 * (L.maxq + 1) + 1; ++t) {
-      PassTable T;
-      T.which = t < 2 * (L.maxq + 1) ? t % 2 : kB_CORE;
-      T.it = t < 2 * (L.maxq + 1) ? t / 2 : 0;
-      std::vector<int> members;
-      std::vector<int2> rmap;
-      for (int i = 0; i < count; ++i) {
-        const corutv_problem& p = probs[i];
-        if (T.which == kB_CORE ? p.core == CORUTV_CORE_EXACT : T.it <= p.q) members.push_back(i);
-      }
-      if (tune.tc_order == 1) {
-        // largest reduction first (ties: larger output, then the given order)
-        auto kk = [&](int i) { return T.which == kB_C2 ? L.sz[i].len1 : L.sz[i].len2; };
-        auto ll = [&](int i) { return T.which == kB_C2 ? L.sz[i].len2 : L.sz[i].len1; };
-        std::stable_sort(members.begin(), members.end(), [&](int a, int b) {
-          return kk(a) != kk(b) ? kk(a) > kk(b) : ll(a) > ll(b);
-        });
-      }
-      for (size_t u = 0; u < members.size(); ++u) {
-        const int i = members[u];
-        const corutv_problem& p = probs[i];
-        const ProbSizes& z = L.sz[i];
-        const int64_t len = T.which == kB_C2 ? z.len2 : z.len1, K = T.which == kB_C2 ? z.len1 : z.len2;
-        T.iters += tc_grouped_tiles(len) * tc_grouped_kblocks(K);
-        T.tiles += tc_grouped_tiles(len);
-        T.lmax = std::max(T.lmax, (int)p.l);
-        const int eb = 4;
-        T.bytes += (double)p.m * p.n * eb + 4.0 * p.l * (double)(len + K);
-        add_blocks(rmap, (int)u, cdiv(K, 128));
-      }
-      T.np = (int)members.size();
-      T.nround = (int)rmap.size();
-      std::vector<int64_t> fro(members.size(), 0);
-      if (T.which == kB_C1 && T.it == 0 && T.np > 0) {
-        const int64_t G = std::min<int64_t>(T.iters, sms);
-        int64_t base = 0;
-        for (size_t u = 0; u < members.size(); ++u) {
-          const int i = members[u];
-          const ProbSizes& z = L.sz[i];
-          const int64_t iters = tc_grouped_tiles(z.len1) * tc_grouped_kblocks(z.len2);
-          if (probs[i].want_fro2) {
-            fro[u] = 4 * (tc_grouped_owner(base + iters - 1, T.iters, G) - tc_grouped_owner(base, T.iters, G) + 1);
-            T.fro = true;
-            L.total_fro += (size_t)fro[u];
-          }
-          base += iters;
-        }
-      }
-      T.off_gp = off;
-      off += align_up(sizeof(GPassProb) * std::max(1, T.np));
-      T.off_rmap = off;
-      off += align_up(sizeof(int2) * std::max(1, T.nround));
-      L.ptabs.push_back(T);
-      L.pt_probs.push_back(members);
-      L.pt_rmaps.push_back(rmap);
-      L.pt_fro.push_back(fro);
-    }
-    L.off_tmaps = off;                              // 4 tensor maps per problem, 128 B each
-    off += align_up(sizeof(CUtensorMap) * 4 * (size_t)count);
-  }
-  if (L.lpt) {
-    // grouped kind::f16 tables: (C1, C2) of every power step, then the exact-core pass
-    for (int t = 0; t < 2 * (L.maxq + 1) + 1; ++t) {
-      LpTable T;
-      T.which = t < 2 * (L.maxq + 1) ? t % 2 : kB_CORE;
-      T.it = t < 2 * (L.maxq + 1) ? t / 2 : 0;
-      std::vector<int> members;
-      for (int i = 0; i < count; ++i) {
-        const corutv_problem& p = probs[i];
-        if (L.eng[i] != kEngF16) continue;
-        if (T.which == kB_CORE ? p.core == CORUTV_CORE_EXACT : T.it <= p.q) members.push_back(i);
-      }
+  // Pass tables (tensor-core engines).  Per power step: one table of the C1 and one of the C2
+  // products of the problems that do not fuse their power steps; for the ones that do, L2-sized
+  // groups, each a C1 table and a W = op2(A) C1 table launched back to back.  Then the exact core.
+  auto make_ptab = [&](int which, int it, std::vector<int> members) -> int {
+    PassTable T;
+    T.which = which;
+    T.it = it;
+    std::vector<int2> rmap;
+    if (tune.tc_order == 1) {
+      // largest reduction first (ties: larger output, then the given order)
       auto kk = [&](int i) { return T.which == kB_C2 ? L.sz[i].len1 : L.sz[i].len2; };
       auto ll = [&](int i) { return T.which == kB_C2 ? L.sz[i].len2 : L.sz[i].len1; };
-      if (tune.tc_order == 1)
-        std::stable_sort(members.begin(), members.end(), [&](int a, int b) {
-          return kk(a) != kk(b) ? kk(a) > kk(b) : ll(a) > ll(b);
-        });
-      // units in table order, weighted by k-blocks (+1 for the epilogue's tile write)
-      std::vector<int> w;
-      std::vector<int2> smap, rmap;
+      std::stable_sort(members.begin(), members.end(), [&](int a, int b) {
+        return kk(a) != kk(b) ? kk(a) > kk(b) : ll(a) > ll(b);
+      });
+    }
+    for (size_t u = 0; u < members.size(); ++u) {
+      const int i = members[u];
+      const corutv_problem& p = probs[i];
+      const ProbSizes& z = L.sz[i];
+      const int64_t len = T.which == kB_C2 ? z.len2 : z.len1, K = T.which == kB_C2 ? z.len1 : z.len2;
+      T.iters += tc_grouped_tiles(len) * tc_grouped_kblocks(K);
+      T.tiles += tc_grouped_tiles(len);
+      T.lmax = std::max(T.lmax, (int)p.l);
+      T.bytes += (double)p.m * p.n * 4 + 4.0 * p.l * (double)(len + K);
+      add_blocks(rmap, (int)u, cdiv(K, 128));
+    }
+    T.np = (int)members.size();
+    T.nround = (int)rmap.size();
+    std::vector<int64_t> fro(members.size(), 0);
+    if (T.which == kB_C1 && T.it == 0 && T.np > 0) {
+      const int64_t G = std::min<int64_t>(T.iters, sms);
+      int64_t base = 0;
       for (size_t u = 0; u < members.size(); ++u) {
         const int i = members[u];
-        const int64_t len = ll(i), K = kk(i);
-        const int64_t tiles = cdiv(len, kLpUnitBN), KB = lp_unit_kblocks(K), kbc = lp_unit_kbc(K);
-        const int S = lp_unit_nsplit(K);
-        for (int s2 = 0; s2 < S; ++s2)
-          for (int64_t t2 = 0; t2 < tiles; ++t2) w.push_back((int)(std::min(KB, (s2 + 1) * kbc) - s2 * kbc) + 1);
-        add_blocks(smap, (int)u, cdiv(K, 256));
-        if (S > 1) add_blocks(rmap, (int)u, tiles);
-        T.lmax = std::max(T.lmax, (int)probs[i].l);
-        T.fro |= T.which == kB_C1 && T.it == 0 && probs[i].want_fro2;
-      }
-      const int64_t U = (int64_t)w.size();
-      T.np = (int)members.size();
-      T.G = (int)std::min<int64_t>(U, sms);
-      std::vector<int> first(T.G + 1, (int)U);
-      if (T.G > 0) {
-        // CTA c runs units [first[c], first[c + 1]): first[c] = first unit whose prefix weight
-        // reaches c / G of the total
-        double total = 0.0, acc = 0.0;
-        for (int x : w) total += x;
-        int c = 1;
-        first[0] = 0;
-        for (int64_t u = 0; u < U; ++u) {
-          while (c < T.G && acc >= total * c / T.G) first[c++] = (int)u;
-          acc += w[u];
+        const ProbSizes& z = L.sz[i];
+        const int64_t iters = tc_grouped_tiles(z.len1) * tc_grouped_kblocks(z.len2);
+        if (probs[i].want_fro2) {
+          fro[u] = 4 * (tc_grouped_owner(base + iters - 1, T.iters, G) - tc_grouped_owner(base, T.iters, G) + 1);
+          T.fro = true;
+          L.total_fro += (size_t)fro[u];
         }
+        base += iters;
       }
-      T.nsplit = (int)smap.size();
-      T.nred = (int)rmap.size();
-      T.off_gp = off;
-      off += align_up(sizeof(GLpProb) * std::max(1, T.np));
-      T.off_cta = off;
-      off += align_up(sizeof(int) * first.size());
-      T.off_smap = off;
-      off += align_up(sizeof(int2) * std::max<size_t>(1, smap.size()));
-      T.off_rmap = off;
-      off += align_up(sizeof(int2) * std::max<size_t>(1, rmap.size()));
-      L.ltabs.push_back(T);
-      L.lt_probs.push_back(members);
-      L.lt_cta.push_back(first);
-      L.lt_smap.push_back(smap);
-      L.lt_rmap.push_back(rmap);
     }
-    L.off_tmaps = off;                              // 6 tensor maps per problem, 128 B each
-    off += align_up(sizeof(CUtensorMap) * 6 * (size_t)count);
+    T.off_gp = off;
+    off += align_up(sizeof(GPassProb) * std::max(1, T.np));
+    T.off_rmap = off;
+    off += align_up(sizeof(int2) * std::max(1, T.nround));
+    L.ptabs.push_back(T);
+    L.pt_probs.push_back(members);
+    L.pt_rmaps.push_back(rmap);
+    L.pt_fro.push_back(fro);
+    return (int)L.ptabs.size() - 1;
+  };
+  auto make_ltab = [&](int which, int it, std::vector<int> members) -> int {
+    LpTable T;
+    T.which = which;
+    T.it = it;
+    auto kk = [&](int i) { return T.which == kB_C2 ? L.sz[i].len1 : L.sz[i].len2; };
+    auto ll = [&](int i) { return T.which == kB_C2 ? L.sz[i].len2 : L.sz[i].len1; };
+    if (tune.tc_order == 1)
+      std::stable_sort(members.begin(), members.end(), [&](int a, int b) {
+        return kk(a) != kk(b) ? kk(a) > kk(b) : ll(a) > ll(b);
+      });
+    // units in table order, weighted by k-blocks (+1 for the epilogue's tile write)
+    std::vector<int> w;
+    std::vector<int2> smap, rmap;
+    for (size_t u = 0; u < members.size(); ++u) {
+      const int i = members[u];
+      const corutv_problem& p = probs[i];
+      const int64_t len = ll(i), K = kk(i);
+      const int64_t tiles = cdiv(len, kLpUnitBN), KB = lp_unit_kblocks(K), kbc = lp_unit_kbc(K);
+      const int S = lp_unit_nsplit(K);
+      for (int s2 = 0; s2 < S; ++s2)
+        for (int64_t t2 = 0; t2 < tiles; ++t2) w.push_back((int)(std::min(KB, (s2 + 1) * kbc) - s2 * kbc) + 1);
+      add_blocks(smap, (int)u, cdiv(K, 256));
+      if (S > 1) add_blocks(rmap, (int)u, tiles);
+      T.lmax = std::max(T.lmax, (int)p.l);
+      T.fro |= T.which == kB_C1 && T.it == 0 && p.want_fro2;
+      const int eb = p.a_dtype == CORUTV_BF16 ? 2 : 1;
+      T.bytes += (double)p.m * p.n * eb + 4.0 * p.l * (double)(len + K);
+    }
+    const int64_t U = (int64_t)w.size();
+    T.np = (int)members.size();
+    T.G = (int)std::min<int64_t>(U, sms);
+    std::vector<int> first(T.G + 1, (int)U);
+    if (T.G > 0) {
+      // CTA c runs units [first[c], first[c + 1]): first[c] = first unit whose prefix weight
+      // reaches c / G of the total
+      double total = 0.0, acc = 0.0;
+      for (int x : w) total += x;
+      int c = 1;
+      first[0] = 0;
+      for (int64_t u = 0; u < U; ++u) {
+        while (c < T.G && acc >= total * c / T.G) first[c++] = (int)u;
+        acc += w[u];
+      }
+    }
+    T.nsplit = (int)smap.size();
+    T.nred = (int)rmap.size();
+    T.off_gp = off;
+    off += align_up(sizeof(GLpProb) * std::max(1, T.np));
+    T.off_cta = off;
+    off += align_up(sizeof(int) * first.size());
+    T.off_smap = off;
+    off += align_up(sizeof(int2) * std::max<size_t>(1, smap.size()));
+    T.off_rmap = off;
+    off += align_up(sizeof(int2) * std::max<size_t>(1, rmap.size()));
+    L.ltabs.push_back(T);
+    L.lt_probs.push_back(members);
+    L.lt_cta.push_back(first);
+    L.lt_smap.push_back(smap);
+    L.lt_rmap.push_back(rmap);
+    return (int)L.ltabs.size() - 1;
+  };
+  L.fuse.assign(count, 0);
+  L.t_c1.assign(L.maxq + 1, -1);
+  L.t_c2.assign(L.maxq + 1, -1);
+  L.t_groups.assign(L.maxq + 1, {});
+  if (L.tc || L.lpt) {
+    auto on_tc = [&](int i) { return L.tc || L.eng[i] == kEngF16; };
+    for (int i = 0; i < count; ++i) L.fuse[i] = probs[i].fuse_power && on_tc(i) ? 1 : 0;
+    auto add = [&](int which, int it, const std::vector<int>& members) {
+      return L.tc ? make_ptab(which, it, members) : make_ltab(which, it, members);
+    };
+    for (int it = 0; it <= L.maxq; ++it) {
+      std::vector<int> plain, fused;
+      for (int i = 0; i < count; ++i)
+        if (on_tc(i) && it <= probs[i].q) (L.fuse[i] ? fused : plain).push_back(i);
+      L.t_c1[it] = add(kB_C1, it, plain);
+      L.t_c2[it] = add(kB_C2, it, plain);
+      // groups of at most kFuseGroupBytes of A (a larger problem alone), in the given order
+      std::vector<int> g;
+      double gb = 0.0;
+      auto flush = [&]() {
+        if (g.empty()) return;
+        const int c1 = add(kB_C1, it, g);
+        if (L.tc) L.ptabs[c1].keep_a = true;
+        else L.ltabs[c1].keep_a = true;
+        L.t_groups[it].push_back(std::make_pair(c1, add(kB_C2, it, g)));
+        g.clear();
+        gb = 0.0;
+      };
+      for (int i : fused) {
+        const corutv_problem& p = probs[i];
+        const double ab = (double)p.m * p.n * (p.a_dtype == CORUTV_F32 ? 4 : (p.a_dtype == CORUTV_BF16 ? 2 : 1));
+        if (!g.empty() && gb + ab > kFuseGroupBytes) flush();
+        g.push_back(i);
+        gb += ab;
+      }
+      flush();
+    }
+    std::vector<int> core;
+    for (int i = 0; i < count; ++i)
+      if (on_tc(i) && probs[i].core == CORUTV_CORE_EXACT) core.push_back(i);
+    L.t_core = add(kB_CORE, 0, core);
+    L.off_tmaps = off;                              // 4 (TF32) or 6 (kind::f16) tensor maps per problem
+    off += align_up(sizeof(CUtensorMap) * (L.tc ? 4 : 6) * (size_t)count);
   }
   L.table_bytes = off;                              // uploaded part
   L.off_fro = off;
@@ -488,6 +534,8 @@ int build(corutv_handle* h, BatchState* B, int count, const corutv_problem* prob
   B->kcount_bytes = std::max<size_t>(sizeof(int), L.kcount_bytes);
   size_t kc_off = 0;
   B->passes.assign(count, 0);
+  B->hbm_passes.assign(count, 0);
+  B->any_fuse = false;
   B->want_fro2.assign(count, 0);
   B->multi_pass.assign(L.maxq + 1, 0);
   B->any_exact = B->any_sketch = B->any_fro2 = false;
@@ -522,6 +570,7 @@ int build(corutv_handle* h, BatchState* B, int count, const corutv_problem* prob
     Q.core = p.core;
     Q.orth = p.orth;
     Q.want_fro2 = p.want_fro2 ? 1 : 0;
+    Q.fuse = L.fuse[i];
     const bool right = p.side == CORUTV_SIDE_RIGHT;
     Q.dir1 = right ? CORUTV_DIR_AX : CORUTV_DIR_ATY;
     Q.dir2 = right ? CORUTV_DIR_ATY : CORUTV_DIR_AX;
@@ -585,6 +634,9 @@ int build(corutv_handle* h, BatchState* B, int count, const corutv_problem* prob
       if (!ok) return CORUTV_ERR_CUDA;
     }
     B->passes[i] = 2 * (p.q + 1) + (p.core == CORUTV_CORE_EXACT ? 1 : 0);
+    // fused power steps: the W launch of each step re-reads A from L2
+    B->hbm_passes[i] = B->passes[i] - (L.fuse[i] ? p.q + 1 : 0);
+    B->any_fuse |= L.fuse[i] != 0;
     B->want_fro2[i] = Q.want_fro2;
     B->any_exact |= p.core == CORUTV_CORE_EXACT;
     B->any_sketch |= p.core == CORUTV_CORE_SKETCH;
@@ -596,6 +648,10 @@ int build(corutv_handle* h, BatchState* B, int count, const corutv_problem* prob
   // pass tables (TF32 tensor cores)
   B->tc = L.tc;
   B->ptabs = L.ptabs;
+  B->t_c1 = L.t_c1;
+  B->t_c2 = L.t_c2;
+  B->t_groups = L.t_groups;
+  B->t_core = L.t_core;
   if (L.tc) {
     const CUtensorMap* dmaps = reinterpret_cast<const CUtensorMap*>(d + L.off_tmaps);
     double* fro_base = reinterpret_cast<double*>(d + L.off_fro);
@@ -712,7 +768,7 @@ int build(corutv_handle* h, BatchState* B, int count, const corutv_problem* prob
     const corutv_problem& p = probs[i];
     const int eb = p.a_dtype == CORUTV_F32 ? 4 : (p.a_dtype == CORUTV_BF16 ? 2 : 1);
     const double a_bytes = (double)p.m * p.n * eb, sk = 4.0 * p.l * (double)(L.sz[i].len1 + L.sz[i].len2);
-    for (int it = 0; it <= p.q; ++it) {
+    for (int it = 0; it <= p.q && !L.fuse[i]; ++it) {      // fused problems: their group tables count
       B->pass_bytes[3 * it + kB_C1] += a_bytes + sk;
       B->pass_bytes[3 * it + kB_C2] += a_bytes + sk;
     }
@@ -748,6 +804,12 @@ int orth_grouped(corutv_handle* h, const BatchState* B, int which, int it) {
     for (int c = 0; c < 3; ++c)
       CUB(launch_lmul_orth_grouped(B->dprobs, B->map[c][second ? kMapLm2 : kMapLm1],
                                    B->nmap[c][second ? kMapLm2 : kMapLm1], kClassLP[c], which, it, pass, h->stream));
+    // fused power steps: the same R^-1 applied to W = op2(A) C1 (in P2), so after the last pass
+    // P2 = W R1^-1 = op2(A) Q1, the sketch C2 of the step
+    if (!second && B->any_fuse)
+      for (int c = 0; c < 3; ++c)
+        CUB(launch_lmul_orth_grouped(B->dprobs, B->map[c][kMapLm2], B->nmap[c][kMapLm2], kClassLP[c], kG_ORTH1_W,
+                                     it, pass, h->stream));
   }
   return CORUTV_OK;
 }
@@ -760,21 +822,41 @@ int gram_core_grouped(corutv_handle* h, const BatchState* B, int which) {
   return CORUTV_OK;
 }
 
-int pass_grouped(corutv_handle* h, const BatchState* B, int which, int it) {
+// one tensor-core pass table (index into ptabs / ltabs; -1: none)
+int launch_table(corutv_handle* h, const BatchState* B, int t) {
+  if (t < 0) return CORUTV_OK;
   if (B->tc) {
-    const PassTable& T = B->ptabs[which == kB_CORE ? B->ptabs.size() - 1 : 2 * it + which];
+    const PassTable& T = B->ptabs[t];
     if (T.np == 0) return CORUTV_OK;
-    PhaseTimer tm(h, kPhPass, T.bytes);
     CUB(launch_pass_tc_grouped(T.d_gp, T.np, T.iters, T.tiles, T.lmax, T.d_rmap, T.nround, B->partials, T.fro,
-                               h->sms, B->bstatus, h->stream));
+                               h->sms, B->bstatus, T.keep_a, h->stream));
     return CORUTV_OK;
   }
+  const LpTable& T = B->ltabs[t];
+  if (T.np == 0) return CORUTV_OK;
+  CUB(launch_pass_lp_grouped(T.d_gp, T.np, B->a_dtype == CORUTV_FP8_E4M3, T.fro, T.d_cta, T.G, T.d_smap,
+                             T.nsplit, T.d_rmap, T.nred, T.lmax, B->bstatus, T.keep_a, h->stream));
+  return CORUTV_OK;
+}
+
+// the same as one traced pass phase
+int run_table(corutv_handle* h, const BatchState* B, int t) {
+  if (t < 0) return CORUTV_OK;
+  const bool empty = B->tc ? B->ptabs[t].np == 0 : B->ltabs[t].np == 0;
+  if (empty) return CORUTV_OK;
+  PhaseTimer tm(h, kPhPass, B->tc ? B->ptabs[t].bytes : B->ltabs[t].bytes);
+  return launch_table(h, B, t);
+}
+
+// the pass `which` of power step `it` for the problems that do not fuse their power steps
+int pass_grouped(corutv_handle* h, const BatchState* B, int which, int it) {
+  const int t = which == kB_CORE ? B->t_core : (which == kB_C1 ? B->t_c1[it] : B->t_c2[it]);
+  if (B->tc) return run_table(h, B, t);
   const double bytes = B->pass_bytes[which == kB_CORE ? 3 * (B->maxq + 1) + kB_CORE : 3 * it + which];
   PhaseTimer tm(h, kPhPass, bytes);
   if (B->lpt) {
-    const LpTable& T = B->ltabs[which == kB_CORE ? B->ltabs.size() - 1 : 2 * it + which];
-    CUB(launch_pass_lp_grouped(T.d_gp, T.np, B->a_dtype == CORUTV_FP8_E4M3, T.fro, T.d_cta, T.G, T.d_smap,
-                               T.nsplit, T.d_rmap, T.nred, T.lmax, B->bstatus, h->stream));
+    const int rc = launch_table(h, B, t);
+    if (rc) return rc;
   }
   const int k = which != kB_C2 ? kMapT1 : kMapT2;
   for (int c = 0; c < 3; ++c)
@@ -794,7 +876,13 @@ int enqueue(corutv_handle* h, const BatchState* B) {
     CUB(launch_stage_grouped(B->dprobs, B->map[0][kMapS2], B->nmap[0][kMapS2], st));    // S0
   }
   for (int it = 0; it <= B->maxq; ++it) {
-    int rc = pass_grouped(h, B, kB_C1, it);                                              // S1
+    int rc = CORUTV_OK;
+    // fused power steps: per L2-sized group, C1 = op1(A) X and then W = op2(A) C1 while A is in L2
+    for (const auto& g : B->t_groups[it]) {
+      if (!rc) rc = run_table(h, B, g.first);
+      if (!rc) rc = run_table(h, B, g.second);
+    }
+    if (!rc) rc = pass_grouped(h, B, kB_C1, it);                                         // S1
     if (!rc) rc = orth_grouped(h, B, kG_ORTH1, it);                                      // S2
     if (!rc) rc = pass_grouped(h, B, kB_C2, it);                                         // S3
     if (rc) return rc;
@@ -835,16 +923,18 @@ int bucket_log2(double x) { return x <= 1.0 ? 0 : (int)floor(log2(x) + 0.5); }
 
 std::string tune_key(int count, const corutv_problem* probs, bool tc) {
   double sm = 0.0, sn = 0.0;
-  int lmax = 1, qmax = 0;
+  int lmax = 1, qmax = 0, fused = 0;
   for (int i = 0; i < count; ++i) {
     sm += (double)probs[i].m;
     sn += (double)probs[i].n;
     lmax = std::max(lmax, (int)probs[i].l);
     qmax = std::max(qmax, (int)probs[i].q);
+    fused |= probs[i].fuse_power;
   }
   char buf[160];
-  snprintf(buf, sizeof(buf), "dtype%d/%s/lclass%d/m%d/n%d/count%d/q%d", (int)probs[0].a_dtype, tc ? "tc" : "simt",
-           lclass(lmax), bucket_log2(sm / count), bucket_log2(sn / count), bucket_log2((double)count), qmax);
+  snprintf(buf, sizeof(buf), "dtype%d/%s/lclass%d/m%d/n%d/count%d/q%d%s", (int)probs[0].a_dtype,
+           tc ? "tc" : "simt", lclass(lmax), bucket_log2(sm / count), bucket_log2(sn / count),
+           bucket_log2((double)count), qmax, fused ? "/fused" : "");
   return std::string(buf);
 }
 
@@ -1167,6 +1257,7 @@ int corutv_batch_info_wait(corutv_handle* h, int count, corutv_info* infos) {
     memset(&o, 0, sizeof(o));
     o.status = ((st[i].flags | bst.flags) & kStatTimeout) ? CORUTV_ERR_TIMEOUT : CORUTV_OK;
     o.passes_over_A = B->passes[i];
+    o.hbm_passes_over_A = B->hbm_passes[i];
     o.chol_fallbacks = st[i].chol_fallbacks;
     o.chol_shift_rel = kShiftRel32;
     o.fro2_A = B->want_fro2[i] ? st[i].fro2_A : NAN;

@@ -861,6 +861,7 @@ int corutv_info_wait(corutv_handle* h, corutv_info* out) {
   if (cudaMemcpy(&st, h->status, sizeof(st), cudaMemcpyDeviceToHost) != cudaSuccess) return CORUTV_ERR_CUDA;
   out->status = (st.flags & kStatTimeout) ? CORUTV_ERR_TIMEOUT : CORUTV_OK;
   out->passes_over_A = h->last_passes;
+  out->hbm_passes_over_A = h->last_passes;
   out->chol_fallbacks = st.chol_fallbacks;
   out->chol_shift_rel = h->last_shift;
   out->fro2_A = h->last.want_fro2 ? st.fro2_A : NAN;

@@ -190,11 +190,13 @@ struct BatchProb {
   int ks1, ks2;         // SIMT passes: K splits of the len1-output (C1, core) and len2-output (C2) passes
   float* kparts;        // their partial products, [split][l][len] (null when neither pass splits)
   int* kcount;          // per output tile: splits finished so far (zero between passes)
+  int fuse;             // fused power steps: P2 holds W = op2(A) C1 during orth(C1)
 };
 
 // Block -> (problem, local block) maps drive every grouped launch.
 enum BatchSketch : int { kB_C1 = 0, kB_C2 = 1, kB_CORE = 2 };          // pass outputs
-enum BatchGram : int { kG_ORTH1 = 0, kG_ORTH2 = 1, kG_CORE_EXACT = 2, kG_CORE_SKETCH = 3 };
+enum BatchGram : int { kG_ORTH1 = 0, kG_ORTH2 = 1, kG_CORE_EXACT = 2, kG_CORE_SKETCH = 3,
+                       kG_ORTH1_W = 4 };   // ORTH1_W: orth(C1)'s R^-1 applied to W (fused power steps)
 
 // batched SIMT pass (pass_simt.cu): one CTA per 64 output positions and K range; a problem
 // whose K exceeds 2 kBatchSplitK is split into ceil(K / kBatchSplitK) ranges (at most
@@ -230,7 +232,7 @@ int64_t tc_grouped_kblocks(int64_t K);
 int64_t tc_grouped_owner(int64_t x, int64_t total, int64_t G);
 cudaError_t launch_pass_tc_grouped(const GPassProb* gp, int np, int64_t total_iters, int64_t total_tiles, int lmax,
                                    const int2* round_map, int nround, float* partials, bool fro, int sms,
-                                   DevStatus* status, cudaStream_t st);
+                                   DevStatus* status, bool keep_a, cudaStream_t st);
 
 // Grouped kind::f16 passes (pass_tc_lp_grouped.cu) for batched BF16 / FP8 problems.  Work is
 // cut into units that depend on the problem alone -- one 256-position output tile and one K range
@@ -279,7 +281,7 @@ inline int lp_unit_nsplit(int64_t K) {
 }
 cudaError_t launch_pass_lp_grouped(const GLpProb* gp, int np, bool fp8, bool fro, const int* cta_first, int G,
                                    const int2* split_map, int nsplit, const int2* red_map, int nred, int lmax,
-                                   DevStatus* status, cudaStream_t st);
+                                   DevStatus* status, bool keep_a, cudaStream_t st);
 
 // grouped small kernels (small.cu)
 constexpr int kBatchGramCols = 512;   // columns per Gram partial block

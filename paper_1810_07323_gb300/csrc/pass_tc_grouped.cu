@@ -54,7 +54,7 @@ __device__ inline int64_t iter_end(const GPassProb& P) { return P.iter_base + P.
 template <bool FRO>
 __global__ void __launch_bounds__(kThreads, 1)
     pass_tc_grouped_kernel(const GPassProb* __restrict__ gp, int np, int64_t total, float* __restrict__ partials,
-                           DevStatus* status) {
+                           DevStatus* status, int keep_a) {
   extern __shared__ uint8_t smem_dyn[];
   uint8_t* smem = smem_dyn + ((1024u - (smem_u32(smem_dyn) & 1023u)) & 1023u);
   uint8_t* a_tiles = smem;
@@ -96,7 +96,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 0) {
     // ---------------------------------------------------------------- TMA producer
     if (lane == 0) {
-      const uint64_t pol_a = policy_evict_first(), pol_x = policy_evict_last();
+      // keep_a: A is read again by the next launch (fused power steps), so it stays in L2
+      const uint64_t pol_a = keep_a ? policy_evict_last() : policy_evict_first(), pol_x = policy_evict_last();
       int64_t n = 0;
       bool ok = true;
       int64_t pend = iter_end(gp[pi]);
@@ -273,48 +274,60 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
-// Ordered sum of the partial slots of split tiles: block (gt, g) handles rows
-// 16 g .. 16 g + 15 of global tile gt.
+// Ordered sum of the partial slots of split tiles.  A tile is split exactly when a CTA's first
+// iteration lies inside it; block (c, g) takes the tile holding CTA c's first iteration if that
+// tile is split and c is the first CTA to start inside it, and sums rows 4 g .. 4 g + 3 (a thread
+// per column) over the CTAs that share the tile, in CTA order.  (One block per CTA boundary and
+// row group, not per tile.)
 __global__ void __launch_bounds__(256) grouped_reduce_kernel(const GPassProb* __restrict__ gp, int np,
                                                              int64_t total, int64_t G,
                                                              const float* __restrict__ partials) {
-  const int64_t gt = blockIdx.x;
-  int lo = 0, hi = np - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (gp[mid].tile_base <= gt) lo = mid;
-    else hi = mid - 1;
-  }
-  const GPassProb& P = gp[lo];
-  const int row0 = blockIdx.y * 16;
-  if (row0 >= P.l) return;
-  const int64_t t = gt - P.tile_base;
+  static_assert(kBN == 256, "a thread per tile column");
+  const int64_t c = blockIdx.x;
+  if (c == 0) return;                                     // CTA 0 starts at a tile start
+  const int64_t x = gstart(c, total, G);
+  if (x >= total) return;
+  const GPassProb& P = gp[find_problem(gp, np, x)];
+  const int64_t t = (x - P.iter_base) / P.KB;
   const int64_t first_it = P.iter_base + t * P.KB, last_it = first_it + P.KB - 1;
+  if (x == first_it) return;                              // c starts a tile: no split at this boundary
+  if (gstart(c - 1, total, G) > first_it) return;         // an earlier CTA also starts inside the tile
+  const int row0 = blockIdx.y * 4;
+  if (row0 >= P.l) return;
   const int64_t cf = gowner(first_it, total, G), cl = gowner(last_it, total, G);
-  if (cf == cl) return;                                   // written directly by its only CTA
+  const int ii = threadIdx.x;
   const int64_t p0 = t * kBN;
-  for (int x = threadIdx.x; x < 16 * kBN; x += blockDim.x) {
-    const int j = row0 + x / kBN, ii = x % kBN;
-    if (j >= P.l || p0 + ii >= P.len) continue;
-    float acc = 0.f;
-    for (int64_t c = cf; c <= cl; ++c) {
-      const int64_t slot = 2 * c + (gstart(c, total, G) >= first_it ? 0 : 1);
-      acc += partials[(slot * kM + j) * kBN + ii];
-    }
-    P.Ct[(int64_t)j * P.ldc + p0 + ii] = acc;
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int64_t cc = cf; cc <= cl; ++cc) {
+    const int64_t slot = 2 * cc + (gstart(cc, total, G) >= first_it ? 0 : 1);
+    const float* src = partials + (slot * kM + row0) * kBN + ii;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) acc[r] += src[r * kBN];
   }
+  if (p0 + ii >= P.len) return;
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+    if (row0 + r < P.l) P.Ct[(int64_t)(row0 + r) * P.ldc + p0 + ii] = acc[r];
 }
 
-// Xr = TF32(X) (round to nearest) for every problem of the table
+// Xr = TF32(X) (round to nearest) for every problem of the table; block (map[b].x, map[b].y)
+// covers 128 columns, four consecutive columns per thread and step (rows are 16-byte aligned)
 __global__ void __launch_bounds__(256) grouped_round_kernel(const GPassProb* __restrict__ gp,
                                                             const int2* __restrict__ map) {
   const int2 pm = map[blockIdx.x];
   const GPassProb& P = gp[pm.x];
   const int64_t i0 = (int64_t)pm.y * 128;
-  for (int e = threadIdx.x; e < P.l * 128; e += blockDim.x) {
-    const int j = e >> 7;
-    const int64_t i = i0 + (e & 127);
-    if (i < P.K) P.Xr[j * P.ldr + i] = to_tf32(P.X[j * P.ldx + i]);
+  for (int e = threadIdx.x; e < P.l * 32; e += blockDim.x) {
+    const int j = e >> 5;
+    const int64_t i = i0 + 4 * (e & 31);
+    if (i >= P.K) continue;
+    if (i + 3 < P.K) {
+      const float4 v = *reinterpret_cast<const float4*>(P.X + j * P.ldx + i);
+      *reinterpret_cast<float4*>(P.Xr + j * P.ldr + i) =
+          make_float4(to_tf32(v.x), to_tf32(v.y), to_tf32(v.z), to_tf32(v.w));
+    } else {
+      for (int q = 0; q < 4 && i + q < P.K; ++q) P.Xr[j * P.ldr + i + q] = to_tf32(P.X[j * P.ldx + i + q]);
+    }
   }
 }
 
@@ -328,7 +341,7 @@ int64_t tc_grouped_owner(int64_t x, int64_t total, int64_t G) { return gowner(x,
 
 cudaError_t launch_pass_tc_grouped(const GPassProb* gp, int np, int64_t total_iters, int64_t total_tiles, int lmax,
                                    const int2* round_map, int nround, float* partials, bool fro, int sms,
-                                   DevStatus* status, cudaStream_t st) {
+                                   DevStatus* status, bool keep_a, cudaStream_t st) {
   if (np <= 0 || total_iters <= 0) return cudaSuccess;
   if (nround > 0) {
     grouped_round_kernel<<<nround, 256, 0, st>>>(gp, round_map);
@@ -346,11 +359,12 @@ cudaError_t launch_pass_tc_grouped(const GPassProb* gp, int np, int64_t total_it
     if (err != cudaSuccess) return err;
     if (dev >= 0 && dev < 64) attr_set[fro ? 1 : 0][dev] = true;
   }
-  kern<<<(unsigned)G, kThreads, kSmem, st>>>(gp, np, total_iters, partials, status);
+  kern<<<(unsigned)G, kThreads, kSmem, st>>>(gp, np, total_iters, partials, status, keep_a ? 1 : 0);
   CORUTV_COUNT_LAUNCH();
   err = cudaGetLastError();
   if (err != cudaSuccess) return err;
-  dim3 rgrid((unsigned)total_tiles, (unsigned)cdiv(lmax, 16));
+  (void)total_tiles;
+  dim3 rgrid((unsigned)G, (unsigned)cdiv(lmax, 4));
   grouped_reduce_kernel<<<rgrid, 256, 0, st>>>(gp, np, total_iters, G, partials);
   CORUTV_COUNT_LAUNCH();
   return cudaGetLastError();

@@ -63,7 +63,7 @@ __device__ inline UnitPos unit_pos(const GLpProb& P, int64_t u) {
 template <bool FP8, bool FRO>
 __global__ void __launch_bounds__(kMaxThreads, 1)
     pass_lp_grouped_kernel(const GLpProb* __restrict__ gp, int np, const int* __restrict__ cta_first,
-                           DevStatus* status) {
+                           DevStatus* status, int keep_a) {
   using Cfg = LpCfg<FP8>;
   constexpr int S = Cfg::kStages;
   constexpr bool kConv = FP8 || FRO;
@@ -115,7 +115,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
   if (warp == 0) {
     // ---------------------------------------------------------------- TMA producer
     if (lane == 0) {
-      const uint64_t pol_a = policy_evict_first(), pol_x = policy_evict_last();
+      // keep_a: A is read again by the next launch (fused power steps), so it stays in L2
+      const uint64_t pol_a = keep_a ? policy_evict_last() : policy_evict_first(), pol_x = policy_evict_last();
       int64_t n = 0;
       bool ok = true;
       for (int64_t u = ub; u < ue && ok; ++u) {
@@ -287,7 +288,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
 }
 
 // X (FP32 ST) -> X_hi = bf16(X), X_lo = bf16(X - X_hi) for every problem of the table; block
-// (map[b].x, map[b].y) covers 256 columns of one problem's sketch operand
+// (map[b].x, map[b].y) covers 256 columns of one problem's sketch operand, four consecutive
+// columns per thread and step (one 16-byte load, two 8-byte stores; rows are 16-byte aligned)
 __global__ void __launch_bounds__(256) lp_grouped_split_kernel(const GLpProb* __restrict__ gp,
                                                                const int2* __restrict__ map) {
   const int2 pm = map[blockIdx.x];
@@ -295,14 +297,35 @@ __global__ void __launch_bounds__(256) lp_grouped_split_kernel(const GLpProb* __
   __nv_bfloat16* Xh = static_cast<__nv_bfloat16*>(P.Xh);
   __nv_bfloat16* Xl = static_cast<__nv_bfloat16*>(P.Xl);
   const int64_t i0 = (int64_t)pm.y * 256;
-  for (int e = threadIdx.x; e < P.l * 256; e += blockDim.x) {
-    const int j = e >> 8;
-    const int64_t i = i0 + (e & 255);
+  for (int e = threadIdx.x; e < P.l * 64; e += blockDim.x) {
+    const int j = e >> 6;
+    const int64_t i = i0 + 4 * (e & 63);
     if (i >= P.K) continue;
-    const float x = P.X[j * P.ldx + i];
-    const __nv_bfloat16 h = __float2bfloat16_rn(x);
-    Xh[j * P.ldxs + i] = h;
-    Xl[j * P.ldxs + i] = __float2bfloat16_rn(x - __bfloat162float(h));
+    float x[4];
+    if (i + 3 < P.K) {
+      const float4 v = *reinterpret_cast<const float4*>(P.X + j * P.ldx + i);
+      x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) x[q] = i + q < P.K ? P.X[j * P.ldx + i + q] : 0.f;
+    }
+    __nv_bfloat16 h[4], lo[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      h[q] = __float2bfloat16_rn(x[q]);
+      lo[q] = __float2bfloat16_rn(x[q] - __bfloat162float(h[q]));
+    }
+    if (i + 3 < P.K) {
+      *reinterpret_cast<uint2*>(Xh + j * P.ldxs + i) = *reinterpret_cast<const uint2*>(h);
+      *reinterpret_cast<uint2*>(Xl + j * P.ldxs + i) = *reinterpret_cast<const uint2*>(lo);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (i + q < P.K) {
+          Xh[j * P.ldxs + i + q] = h[q];
+          Xl[j * P.ldxs + i + q] = lo[q];
+        }
+    }
   }
 }
 
@@ -325,7 +348,7 @@ __global__ void __launch_bounds__(256) lp_grouped_reduce_kernel(const GLpProb* _
 }
 
 template <bool FP8, bool FRO>
-cudaError_t launch_variant(const GLpProb* gp, int np, const int* cta_first, int G, DevStatus* status,
+cudaError_t launch_variant(const GLpProb* gp, int np, const int* cta_first, int G, DevStatus* status, int keep_a,
                            cudaStream_t st) {
   auto kern = pass_lp_grouped_kernel<FP8, FRO>;
   // raised once per device (the first, uncaptured run of a batch)
@@ -339,7 +362,8 @@ cudaError_t launch_variant(const GLpProb* gp, int np, const int* cta_first, int 
     if (dev >= 0 && dev < 64) attr_set[dev] = true;
   }
   constexpr bool conv = FP8 || FRO;
-  kern<<<(unsigned)G, conv ? LpCfg<FP8>::kThreads : 192, LpCfg<FP8>::kSmem, st>>>(gp, np, cta_first, status);
+  kern<<<(unsigned)G, conv ? LpCfg<FP8>::kThreads : 192, LpCfg<FP8>::kSmem, st>>>(gp, np, cta_first, status,
+                                                                                   keep_a);
   CORUTV_COUNT_LAUNCH();
   return cudaGetLastError();
 }
@@ -348,17 +372,18 @@ cudaError_t launch_variant(const GLpProb* gp, int np, const int* cta_first, int 
 
 cudaError_t launch_pass_lp_grouped(const GLpProb* gp, int np, bool fp8, bool fro, const int* cta_first, int G,
                                    const int2* split_map, int nsplit, const int2* red_map, int nred, int lmax,
-                                   DevStatus* status, cudaStream_t st) {
+                                   DevStatus* status, bool keep_a, cudaStream_t st) {
   if (np <= 0 || G <= 0) return cudaSuccess;
   if (nsplit > 0) {
     lp_grouped_split_kernel<<<nsplit, 256, 0, st>>>(gp, split_map);
     CORUTV_COUNT_LAUNCH();
   }
   cudaError_t err;
-  if (fp8) err = fro ? launch_variant<true, true>(gp, np, cta_first, G, status, st)
-                     : launch_variant<true, false>(gp, np, cta_first, G, status, st);
-  else err = fro ? launch_variant<false, true>(gp, np, cta_first, G, status, st)
-                 : launch_variant<false, false>(gp, np, cta_first, G, status, st);
+  const int ka = keep_a ? 1 : 0;
+  if (fp8) err = fro ? launch_variant<true, true>(gp, np, cta_first, G, status, ka, st)
+                     : launch_variant<true, false>(gp, np, cta_first, G, status, ka, st);
+  else err = fro ? launch_variant<false, true>(gp, np, cta_first, G, status, ka, st)
+                 : launch_variant<false, false>(gp, np, cta_first, G, status, ka, st);
   if (err != cudaSuccess) return err;
   if (nred > 0) {
     lp_grouped_reduce_kernel<<<dim3((unsigned)nred, (unsigned)cdiv(lmax, 16)), 256, 0, st>>>(gp, red_map);

@@ -1927,10 +1927,14 @@ __global__ void __launch_bounds__(256, 1) lmul_orth_grouped_kernel(const BatchPr
   const BatchProb& P = probs[pm.x];
   if (!batch_orth_active(P, it, pass)) return;
   if (pass == 2 && P.status->orth_skip) return;
+  // ORTH1_W: orth(C1)'s factor applied to W in P2 (fused power steps), no column replacement
+  const bool w = which == kG_ORTH1_W;
+  if (w && !P.fuse) return;
   float* C = which == kG_ORTH1 ? P.P1 : P.P2;
   const int64_t ldc = which == kG_ORTH1 ? P.ld1 : P.ld2;
   const int64_t len = which == kG_ORTH1 ? P.len1 : P.len2;
-  lmul_body<float, float, LP, kBatchLmulBI>(C, ldc, len, P.l, P.Rinv, P.l, C, ldc, 0, 1, P.defic, pass, pm.y);
+  lmul_body<float, float, LP, kBatchLmulBI>(C, ldc, len, P.l, P.Rinv, P.l, C, ldc, 0, 1, w ? nullptr : P.defic, pass,
+                                            pm.y);
 }
 
 // the last C2 of a problem (power step it == q) is kept in P3 for the sketch core

@@ -385,3 +385,68 @@ def test_autotune_plans_agree_and_cache_round_trip(kind, tmp_path):
         assert O.factor_distance(U1, T1, V1, U0, T0, V0) < 1e-5, i
         ref = O.corutv(Aq, phi.astype(np.float64), k, l, q, side=side)
         assert O.factor_distance(U1, T1, V1, ref["U"], ref["T"], ref["V"]) < TOL, i
+
+
+def _fused_items(kind, seed):
+    """The F16 set (BF16 rows TMA can address) or the MIXED set in FP32 with 16-byte row pitch
+    (grouped TF32 passes), each problem asking for fused power steps."""
+    rows = F16 if kind == "bf16" else MIXED
+    items, refs = [], []
+    for i, (m, n, r, k, l, q, side, core, orth) in enumerate(rows):
+        A = _lowrank_sparse(C.stream_seed(seed, i), m, n, r).astype(np.float32)
+        phi = C.normal_block_np(C.stream_seed(seed + 1, i), l, 0, m if side == "left" else n, 0, l)
+        if kind == "bf16":
+            it, Aq = _item(A, phi, k, l, q, side, core, orth, kind="bf16")
+        else:
+            it = dict(A=_padded(A), Phi=torch.tensor(phi, dtype=torch.float32, device="cuda"), k=k, l=l, q=q,
+                      side=side, core=core, orth=orth, want_fro2=True)
+            Aq = A.astype(np.float64)
+        it["fuse_power"] = True
+        items.append(it)
+        refs.append((Aq, phi, k, l, q, side, core))
+    return rows, items, refs
+
+
+@pytest.mark.parametrize("kind", ["bf16", "f32"])
+def test_batched_fused_power_steps(kind):
+    """Fused power steps (Alg. 3 steps 3-4 with A read once per step): W = op2(A) C1 right after
+    C1 while A is in L2, C2 = W R1^-1.  Parity with the oracle within the batched bounds,
+    A streamed from HBM q + 1 (+ 1) times on the tensor-core engines, replays bit-identical,
+    and (BF16) every problem the same bits alone as in the batch."""
+    rows, items, refs = _fused_items(kind, 95)
+    b = corutv.Batch(items)
+    outs = []
+    for _ in range(3):
+        res = b.run()
+        outs.append([(x.U.clone(), x.T.clone(), x.V.clone()) for x in res])
+    for o in outs[1:]:
+        for a, c in zip(outs[0], o):
+            assert all(torch.equal(x, y) for x, y in zip(a, c))
+    tol = TOL if kind == "bf16" else 1e-3
+    for i, (r, it, (Aq, phi, k, l, q, side, core)) in enumerate(zip(res, items, refs)):
+        assert r.info.status == 0
+        rho = _check(r, Aq, phi, k, l, q, side, core)
+        m, n = Aq.shape
+        tc = kind == "f32" or (n % 8 == 0)                  # rows TMA can address: a tensor-core engine
+        passes = 2 * (q + 1) + (1 if core == "exact" else 0)
+        assert r.info.passes_over_A == passes
+        assert r.info.hbm_passes_over_A == (passes - (q + 1) if tc else passes), (i, r.info.hbm_passes_over_A)
+        print(f"{kind} fused problem {i} {rows[i][:2]} q={q}: rho={rho:.3e}")
+        assert rho < tol, (i, rho)
+        a2 = float(np.sum(Aq ** 2))
+        assert abs(r.info.fro2_A - a2) < 1e-6 * a2
+    if kind == "bf16":
+        for i, (it, r) in enumerate(zip(items, res)):
+            alone = corutv.Batch([it]).run()[0]
+            assert torch.equal(alone.U, r.U) and torch.equal(alone.T, r.T), i
+            assert torch.equal(alone.V, r.V), i
+
+
+def test_batched_fuse_power_flag_is_checked():
+    A = torch.zeros((100, 80), device="cuda")
+    phi = torch.zeros((80, 10), device="cuda")
+    b = corutv.Batch([dict(A=A, Phi=phi, k=5, l=10)])
+    b.arr[0].fuse_power = 2
+    with pytest.raises(corutv.CorutvError) as e:
+        b.run()
+    assert e.value.status == corutv.ERR_INVALID_ARG
