@@ -61,7 +61,15 @@ typedef enum {
   CORUTV_ORTH_STABILISED = 0, /* the last power step's sketches (Q1, Q2) by shifted CholeskyQR3;
                                  earlier sketches by one shifted CholeskyQR pass (a well-conditioned
                                  basis of the same range: the same Q1, Q2 in exact arithmetic) */
-  CORUTV_ORTH_STRICT = 1      /* every sketch by shifted CholeskyQR3 */
+  CORUTV_ORTH_STRICT = 1,     /* every sketch by shifted CholeskyQR3 */
+  CORUTV_ORTH_LITERAL = 2     /* Alg. 3 as printed: the power steps multiply by A and A^T with no
+                                 orthonormalisation in between (C1 = A C2, C2 = A^T C1), and only
+                                 the last C1 and C2 are orthonormalised (shifted CholeskyQR3).  The
+                                 same Q1, Q2 in exact arithmetic; in floating point the columns of
+                                 C1, C2 align with the leading singular vectors as q grows, so
+                                 trailing directions are lost, and the entries grow like
+                                 ||A||^(2q+1) (FP32 range).  corutv_solve / corutv_solve_host with
+                                 core EXACT only (SKETCH: ERR_UNSUPPORTED; batched: ERR_UNSUPPORTED) */
 } corutv_orth;
 typedef enum { CORUTV_F64 = 0, CORUTV_F32 = 1, CORUTV_BF16 = 2, CORUTV_FP8_E4M3 = 3 } corutv_dtype;
 typedef enum {

@@ -22,7 +22,7 @@ ERR_CHOL_BREAKDOWN, ERR_BUSY, PENDING, ERR_UNSUPPORTED = 7, 8, 9, 10
 SIDE = {"right": 0, "left": 1}
 CORE = {"exact": 0, "sketch": 1}
 DTYPE = {"f64": 0, "f32": 1, "bf16": 2, "fp8": 3}
-ORTH = {"stabilised": 0, "strict": 1}
+ORTH = {"stabilised": 0, "strict": 1, "literal": 2}
 MMA = {"auto": 0, "tf32": 1, "tf32x3": 2, "simt": 3, "tf32t": 4, "bf16x2": 5}
 DIR = {"ax": 0, "aty": 1}
 
@@ -305,7 +305,8 @@ def solve(A, Phi, k: int, l: int, q: int = 0, side: str = "right", core: str = "
     A_ref: optional float32 (m, n) matrix for the correction pass of a
     bfloat16 / float8 A (corutv_solve_corrected: the core D from A_ref).
     orth: "stabilised" (one shifted CholeskyQR pass for the sketches of the
-    earlier power steps) or "strict" (shifted CholeskyQR3 for every sketch).
+    earlier power steps), "strict" (shifted CholeskyQR3 for every sketch) or "literal" (Alg. 3 as
+    printed: no orthonormalisation inside the power steps, exact core only).
     factor: "qrcp" (T upper triangular) or "qlp" (T lower triangular, V
     = Q2 P~ Qh; float32-path solves).
     small_f64: float32 / bfloat16 / float8 A with the Gram reductions,

@@ -147,6 +147,7 @@ int validate(const corutv_problem& p) {
     return CORUTV_ERR_UNSUPPORTED;
   if (p.side != CORUTV_SIDE_RIGHT && p.side != CORUTV_SIDE_LEFT) return CORUTV_ERR_INVALID_ARG;
   if (p.core != CORUTV_CORE_EXACT && p.core != CORUTV_CORE_SKETCH) return CORUTV_ERR_INVALID_ARG;
+  if (p.orth == CORUTV_ORTH_LITERAL) return CORUTV_ERR_UNSUPPORTED;
   if (p.orth != CORUTV_ORTH_STABILISED && p.orth != CORUTV_ORTH_STRICT) return CORUTV_ERR_INVALID_ARG;
   if (p.m <= 0 || p.n <= 0) return CORUTV_ERR_SHAPE;
   if (p.k < 1 || p.k > p.l) return CORUTV_ERR_INVALID_ARG;      // 1 <= k <= l (Sec. III)

@@ -145,7 +145,9 @@ int check_params(const corutv_params* p) {
   if (p->a_dtype < CORUTV_F64 || p->a_dtype > CORUTV_FP8_E4M3) return CORUTV_ERR_INVALID_ARG;
   if (p->side != CORUTV_SIDE_RIGHT && p->side != CORUTV_SIDE_LEFT) return CORUTV_ERR_INVALID_ARG;
   if (p->core != CORUTV_CORE_EXACT && p->core != CORUTV_CORE_SKETCH) return CORUTV_ERR_INVALID_ARG;
-  if (p->orth != CORUTV_ORTH_STABILISED && p->orth != CORUTV_ORTH_STRICT) return CORUTV_ERR_INVALID_ARG;
+  if (p->orth != CORUTV_ORTH_STABILISED && p->orth != CORUTV_ORTH_STRICT && p->orth != CORUTV_ORTH_LITERAL)
+    return CORUTV_ERR_INVALID_ARG;
+  if (p->orth == CORUTV_ORTH_LITERAL && p->core != CORUTV_CORE_EXACT) return CORUTV_ERR_UNSUPPORTED;
   if (p->mma < CORUTV_MMA_AUTO || p->mma > CORUTV_MMA_BF16X2) return CORUTV_ERR_INVALID_ARG;
   if (p->m <= 0 || p->n <= 0) return CORUTV_ERR_SHAPE;
   if (p->k < 1 || p->k > p->l) return CORUTV_ERR_INVALID_ARG;      // 1 <= k <= l (Sec. III)
@@ -437,7 +439,10 @@ int solve_impl(corutv_handle* h, const corutv_params* p, const Plan& pl, const v
   // TF32 passes over A: the producers of each sketch operand (the staging of Psi, the last
   // CholeskyQR pass) also write its TF32-rounded copy into Xr for the next pass
   const int eng = pick_mma(p->a_dtype, p->mma, tma_rows_ok(A, lda, p->a_dtype));
-  const bool pre_round = sizeof(TC) == 4 && eng == CORUTV_MMA_TF32;
+  // ORTH_LITERAL (Alg. 3 as printed): no orthonormalisation between the products, so the passes
+  // round their own (raw) sketch operands
+  const bool literal = p->orth == CORUTV_ORTH_LITERAL;
+  const bool pre_round = sizeof(TC) == 4 && eng == CORUTV_MMA_TF32 && !literal;
   float* Xr = static_cast<float*>(pl.Xr);
   float* Xr_out = pre_round ? Xr : nullptr;
   // Gram engine: the 3xTF32 tensor-core partials where the passes themselves run on the tensor cores
@@ -463,10 +468,13 @@ int solve_impl(corutv_handle* h, const corutv_params* p, const Plan& pl, const v
                          pre_round, hs && it == 0 && p->want_fro2);
     if (rc) return rc;
     ++passes;
-    // S2: orth(C1)
-    rc = orth_st<TC>(h, P1, pl.ld1, pl.len1, l, pl, orth_passes(p, it), nullptr, Xr_out, pl.ldr, tc_gram, small64);
-    if (rc) return rc;
-    // S3: C2 = A^T Q1  (Alg. 3 step 4)
+    // S2: orth(C1) (literal: C1 stays as it is)
+    if (!literal) {
+      rc = orth_st<TC>(h, P1, pl.ld1, pl.len1, l, pl, orth_passes(p, it), nullptr, Xr_out, pl.ldr, tc_gram,
+                       small64);
+      if (rc) return rc;
+    }
+    // S3: C2 = A^T Q1  (Alg. 3 step 4; literal: A^T C1)
     rc = do_pass<TC>(h, hs, pl, dir2, p->a_dtype, p->mma, A, lda, p->m, p->n, scales, P1, pl.ld1, l, P2, pl.ld2,
                      Xr, pl.ldr, nullptr, kPhPass, pre_round);
     if (rc) return rc;
@@ -474,8 +482,17 @@ int solve_impl(corutv_handle* h, const corutv_params* p, const Plan& pl, const v
     if (it == p->q && p->core == CORUTV_CORE_SKETCH)
       CU(cudaMemcpy2DAsync(P3, pl.ld3 * sizeof(TC), P2, pl.ld2 * sizeof(TC), pl.len2 * sizeof(TC), l,
                            cudaMemcpyDeviceToDevice, h->stream));
-    // S4: orth(C2)
-    rc = orth_st<TC>(h, P2, pl.ld2, pl.len2, l, pl, orth_passes(p, it), nullptr, Xr_out, pl.ldr, tc_gram, small64);
+    // S4: orth(C2) (literal: only after the last step)
+    if (!literal) {
+      rc = orth_st<TC>(h, P2, pl.ld2, pl.len2, l, pl, orth_passes(p, it), nullptr, Xr_out, pl.ldr, tc_gram,
+                       small64);
+      if (rc) return rc;
+    }
+  }
+  if (literal) {
+    // Alg. 3 step 6: Q1, Q2 from the last C1, C2 (shifted CholeskyQR3)
+    int rc = orth_st<TC>(h, P1, pl.ld1, pl.len1, l, pl, 3, nullptr, nullptr, pl.ldr, tc_gram, small64);
+    if (!rc) rc = orth_st<TC>(h, P2, pl.ld2, pl.len2, l, pl, 3, nullptr, nullptr, pl.ldr, tc_gram, small64);
     if (rc) return rc;
   }
   // S5: core D = Q1^T A Q2 (Alg. 2 step 5); small64: D reduced in FP64

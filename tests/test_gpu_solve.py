@@ -99,6 +99,39 @@ def test_orth_modes_same_factorisation(cfg1, orth):
     _structure(U, T, V, perm, 30, orth_tol=5e-5)
 
 
+@pytest.mark.parametrize("q", [0, 1, 2])
+def test_orth_literal_as_printed(cfg1, q):
+    """orth = literal (Alg. 3 as printed: no orthonormalisation inside the power steps, Q1, Q2 from
+    the last C1, C2).  q = 0: the same factorisation as the oracle's literal loop to FP64 rounding.
+    q >= 1: the unnormalised powers lose the trailing directions in floating point -- the oracle's
+    own literal and stabilised results differ by rho ~5e-5 (q = 1) and ~3e-4 (q = 2) on this
+    matrix -- so the check is the rank-k error (the leading directions), equal to the oracle's,
+    and a distance of the order of that loss."""
+    r, A, phi = _run(cfg1.A, W.phi(1500, 30), 20, 30, q, torch.float64, orth="literal")
+    U, T, V, perm = _np(r)
+    ref = O.corutv(A, phi, 20, 30, q, orth="literal")
+    rho = O.factor_distance(U, T, V, ref["U"], ref["T"], ref["V"])
+    _structure(U, T, V, perm, 30)
+    assert r.info.passes_over_A == 2 * q + 3
+    nA = np.linalg.norm(A)
+    ek = O.fro_residual(A, U, T, V, k=20) / nA
+    ek_ref = O.fro_residual(A, ref["U"], ref["T"], ref["V"], k=20) / nA
+    print(f"literal q={q}: rho={rho:.3e} e_k={ek:.6e} oracle={ek_ref:.6e}")
+    if q == 0:
+        assert rho < TOL["f64"], rho
+    else:
+        assert rho < 2e-3, rho
+        assert ek <= 1.000001 * ek_ref + 1e-12, (ek, ek_ref)
+
+
+def test_orth_literal_needs_exact_core():
+    A = torch.zeros((200, 120), dtype=torch.float64, device="cuda")
+    phi = torch.zeros((120, 10), dtype=torch.float64, device="cuda")
+    with pytest.raises(corutv.CorutvError) as e:
+        corutv.solve(A, phi, 5, 10, 1, core="sketch", orth="literal")
+    assert e.value.status == corutv.ERR_UNSUPPORTED
+
+
 def test_config1_exact_rank_recovery():
     d = W.config1(exact_rank=True)
     r, A, phi = _run(d.A, W.phi(1500, 30), 20, 30, 0, torch.float64)
