@@ -565,22 +565,33 @@ def main_batched(args):
     peak = peak or 6800.0
     avg_pass_ms = tr.pass_ms / max(tr.pass_launches, 1)
     bytes_per_pass = tr.pass_bytes / max(tr.pass_launches, 1)
-    achieved = bytes_per_pass / (avg_pass_ms / 1e3) / 1e9
+    phase_gbs = bytes_per_pass / (avg_pass_ms / 1e3) / 1e9
+    kernel_only = tr.pass_kernel_launches == tr.pass_launches and tr.pass_kernel_launches > 0
+    avg_kernel_ms = tr.pass_kernel_ms / tr.pass_kernel_launches if kernel_only else avg_pass_ms
+    achieved = bytes_per_pass / (avg_kernel_ms / 1e3) / 1e9
     if bf16:
         tkey = f"pass_lp_grouped_kernel/bf16/config4x{count}/src-" + kernel_source_tag(
             "pass_tc_lp_grouped.cu", "tc_lp_common.cuh", "tc_common.cuh")
         kdesc = ("pass_lp_grouped_kernel (all problems' A X or A^T Y in one kind::f16 launch of per-problem "
-                 "units) incl. the sketch operand's BF16 split and the ordered split-K reduction")
+                 "units)" + ("" if kernel_only else
+                             " incl. the sketch operand's BF16 split and the ordered split-K reduction"))
+        pdesc = "the sketch operand's BF16 split, pass kernel, ordered split-K reduction"
     else:
         tkey = f"pass_tc_grouped_kernel/f32/config4x{count}/src-" + kernel_source_tag("pass_tc_grouped.cu",
                                                                                          "tc_common.cuh")
-        kdesc = ("pass_tc_grouped_kernel (all problems' A X or A^T Y in one TF32 launch) incl. operand "
-                 "rounding and split-tile reduce")
+        kdesc = ("pass_tc_grouped_kernel (all problems' A X or A^T Y in one TF32 launch)" +
+                 ("" if kernel_only else " incl. operand rounding and split-tile reduce"))
+        pdesc = "operand rounding, pass kernel, split-tile reduce"
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_source": peak_src,
                 "kernel": kdesc,
-                "bytes_per_launch": bytes_per_pass, "ms_per_launch": avg_pass_ms,
-                "traffic": traffic_from_profiles(tkey), "timing": "two traced, uncaptured runs of the batch"}
+                "bytes_per_launch": bytes_per_pass, "ms_per_launch": avg_kernel_ms,
+                "traffic": traffic_from_profiles(tkey),
+                "timing": "two traced, uncaptured runs of the batch; CUDA events around the pass kernel "
+                          "launches only" if kernel_only else "two traced, uncaptured runs of the batch; "
+                          "CUDA events around the whole pass phase",
+                "pass_phase": {"ms_per_launch": avg_pass_ms, "achieved": phase_gbs, "frac": phase_gbs / peak,
+                               "includes": pdesc}}
 
     # rank-k error of 16 sampled problems (explicit residual on the device)
     idx = list(range(0, count, count // 16))[:16]
@@ -1049,29 +1060,38 @@ def main():
     peak = peaks.get("hbm_gbs")
     peak_src = "measured" if peak else "fallback"
     peak = peak or 6800.0
+    # the pass phase: the sketch operand's split (or rounding), the pass kernel and the split-tile
+    # reduction; the roofline itself is the pass kernel alone (its own event pair in the trace)
     avg_pass_ms = tr.pass_ms / max(tr.pass_launches, 1)
     bytes_per_pass = tr.pass_bytes / max(tr.pass_launches, 1)
-    achieved = bytes_per_pass / (avg_pass_ms / 1e3) / 1e9
+    phase_gbs = bytes_per_pass / (avg_pass_ms / 1e3) / 1e9
+    kernel_only = tr.pass_kernel_launches == tr.pass_launches and tr.pass_kernel_launches > 0
+    avg_kernel_ms = tr.pass_kernel_ms / tr.pass_kernel_launches if kernel_only else avg_pass_ms
+    achieved = bytes_per_pass / (avg_kernel_ms / 1e3) / 1e9
+    incl = "" if kernel_only else " incl. operand split and split-tile reduce"
     if lowp:
         if w["dtype"] == "bf16":
-            kname = "pass_tc_lp_kernel (kind::f16, BF16 A, dir AX / ATY) incl. operand split and split-tile reduce"
+            kname = "pass_tc_lp_kernel (kind::f16, BF16 A, dir AX / ATY)" + incl
             kfn = "pass_tc_lp_kernel"
         else:
             kname = ("pass_tc_lp8_kernel (kind::f16, FP8 A dequantised to BF16 by converter warps through "
-                     "decoupled rings, dir AX / ATY) incl. operand split and split-tile reduce")
+                     "decoupled rings, dir AX / ATY)" + incl)
             kfn = "pass_tc_lp8_kernel"
         tkey = f"{kfn}/{w['dtype']}/{m}x{n}/l{l}/src-" + kernel_source_tag("pass_tc_lp.cu", "tc_lp_common.cuh",
                                                                            "tc_common.cuh")
     elif f32_engine(args.mma) == "tf32x3":
-        kname = "pass_tc3_kernel (dir AX / ATY, split-operand TF32, A in TMEM) incl. operand split and " \
-                "split-tile reduce"
+        kname = "pass_tc3_kernel (dir AX / ATY, split-operand TF32, A in TMEM)" + incl
         tkey = f"pass_tc3_kernel/f32/{m}x{n}/l{l}/src-" + kernel_source_tag("pass_tc3.cu", "tc_common.cuh")
     else:
-        kname = "pass_tc_kernel (dir AX / ATY, TF32) incl. operand rounding and split-tile reduce"
+        kname = "pass_tc_kernel (dir AX / ATY, TF32)" + incl
         tkey = f"pass_tc_kernel/f32/{m}x{n}/l{l}/src-" + kernel_source_tag("pass_tc.cu", "tc_common.cuh")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_source": peak_src, "kernel": kname, "bytes_per_launch": bytes_per_pass,
-                "ms_per_launch": avg_pass_ms, "traffic": traffic_from_profiles(tkey)}
+                "ms_per_launch": avg_kernel_ms, "traffic": traffic_from_profiles(tkey),
+                "timed": "CUDA events around the pass kernel launches only" if kernel_only else
+                         "CUDA events around the whole pass phase",
+                "pass_phase": {"ms_per_launch": avg_pass_ms, "achieved": phase_gbs, "frac": phase_gbs / peak,
+                               "includes": "sketch operand split or rounding, pass kernel, split-tile reduce"}}
     if hosted:
         # the bound is the host -> device link: A crosses it once per pass; its ceiling is the
         # faster of the copy engine and a kernel reading host memory directly (both measured here)

@@ -39,7 +39,7 @@
 extern "C" {
 #endif
 
-#define CORUTV_ABI_VERSION 7
+#define CORUTV_ABI_VERSION 8
 
 typedef enum {
   CORUTV_OK = 0,
@@ -526,6 +526,12 @@ typedef struct {
   double corr_ms;          /* device time inside the correction passes */
   double corr_bytes;       /* algorithmic bytes of those passes */
   double quant_ms;         /* corutv_quantize calls on the handle */
+  int32_t pass_kernel_launches;  /* passes of single-problem solves (the launches counted in
+                                    pass_launches; batched solves record none) timed kernel-only */
+  int32_t reserved2;
+  double pass_kernel_ms;   /* device time of those passes' main kernels alone: without the
+                              sketch-operand split or rounding before them and the split-tile
+                              reduction after them */
 } corutv_trace;
 
 /* Enable (1) or disable (0) tracing on the handle. */

@@ -71,7 +71,9 @@ class Trace(ctypes.Structure):
                 ("pass_ms", ctypes.c_double), ("pass_bytes", ctypes.c_double), ("orth_ms", ctypes.c_double),
                 ("core_ms", ctypes.c_double), ("qrcp_ms", ctypes.c_double), ("assembly_ms", ctypes.c_double),
                 ("fro2_ms", ctypes.c_double), ("corr_launches", ctypes.c_int32), ("reserved1", ctypes.c_int32),
-                ("corr_ms", ctypes.c_double), ("corr_bytes", ctypes.c_double), ("quant_ms", ctypes.c_double)]
+                ("corr_ms", ctypes.c_double), ("corr_bytes", ctypes.c_double), ("quant_ms", ctypes.c_double),
+                ("pass_kernel_launches", ctypes.c_int32), ("reserved2", ctypes.c_int32),
+                ("pass_kernel_ms", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -823,30 +823,57 @@ int gram_core_grouped(corutv_handle* h, const BatchState* B, int which) {
   return CORUTV_OK;
 }
 
-// one tensor-core pass table (index into ptabs / ltabs; -1: none)
-int launch_table(corutv_handle* h, const BatchState* B, int t) {
+// one tensor-core pass table (index into ptabs / ltabs; -1: none); km (tracing, may be null):
+// events around the pass kernel alone
+int launch_table(corutv_handle* h, const BatchState* B, int t, KernelMark* km = nullptr) {
   if (t < 0) return CORUTV_OK;
   if (B->tc) {
     const PassTable& T = B->ptabs[t];
     if (T.np == 0) return CORUTV_OK;
     CUB(launch_pass_tc_grouped(T.d_gp, T.np, T.iters, T.tiles, T.lmax, T.d_rmap, T.nround, B->partials, T.fro,
-                               h->sms, B->bstatus, T.keep_a, h->stream));
+                               h->sms, B->bstatus, T.keep_a, h->stream, km));
     return CORUTV_OK;
   }
   const LpTable& T = B->ltabs[t];
   if (T.np == 0) return CORUTV_OK;
   CUB(launch_pass_lp_grouped(T.d_gp, T.np, B->a_dtype == CORUTV_FP8_E4M3, T.fro, T.d_cta, T.G, T.d_smap,
-                             T.nsplit, T.d_rmap, T.nred, T.lmax, B->bstatus, T.keep_a, h->stream));
+                             T.nsplit, T.d_rmap, T.nred, T.lmax, B->bstatus, T.keep_a, h->stream, km));
   return CORUTV_OK;
 }
+
+// Tracing of a pass phase that is one table launch: a second event pair around its pass
+// kernel alone, recorded as a pass-kernel phase once both events were recorded.
+struct TableMark {
+  corutv_handle* h;
+  double bytes;
+  KernelMark km;
+  TableMark(corutv_handle* h_, double by) : h(h_), bytes(by) {
+    if (h->tracing) {
+      km.a = ev_get(h);
+      km.b = ev_get(h);
+    }
+  }
+  KernelMark* get() { return km.a ? &km : nullptr; }
+  ~TableMark() {
+    if (!km.a) return;
+    if (km.state == 2) {
+      h->recs.push_back(TraceRec{kPhPassKernel, km.a, km.b, bytes});
+    } else {
+      h->ev_pool.push_back(km.a);
+      h->ev_pool.push_back(km.b);
+    }
+  }
+};
 
 // the same as one traced pass phase
 int run_table(corutv_handle* h, const BatchState* B, int t) {
   if (t < 0) return CORUTV_OK;
   const bool empty = B->tc ? B->ptabs[t].np == 0 : B->ltabs[t].np == 0;
   if (empty) return CORUTV_OK;
-  PhaseTimer tm(h, kPhPass, B->tc ? B->ptabs[t].bytes : B->ltabs[t].bytes);
-  return launch_table(h, B, t);
+  const double bytes = B->tc ? B->ptabs[t].bytes : B->ltabs[t].bytes;
+  PhaseTimer tm(h, kPhPass, bytes);
+  TableMark mk(h, bytes);
+  return launch_table(h, B, t, mk.get());
 }
 
 // the pass `which` of power step `it` for the problems that do not fuse their power steps
@@ -855,11 +882,15 @@ int pass_grouped(corutv_handle* h, const BatchState* B, int which, int it) {
   if (B->tc) return run_table(h, B, t);
   const double bytes = B->pass_bytes[which == kB_CORE ? 3 * (B->maxq + 1) + kB_CORE : 3 * it + which];
   PhaseTimer tm(h, kPhPass, bytes);
+  const int k = which != kB_C2 ? kMapT1 : kMapT2;
+  // the kernel-only record when the table's kernel is the phase's only pass kernel
+  bool simt_none = true;
+  for (int c = 0; c < 3; ++c) simt_none = simt_none && B->nmap[c][k] == 0;
+  TableMark mk(h, bytes);
   if (B->lpt) {
-    const int rc = launch_table(h, B, t);
+    const int rc = launch_table(h, B, t, simt_none ? mk.get() : nullptr);
     if (rc) return rc;
   }
-  const int k = which != kB_C2 ? kMapT1 : kMapT2;
   for (int c = 0; c < 3; ++c)
     CUB(launch_pass_simt_grouped(B->dprobs, B->map[c][k], B->nmap[c][k], kClassLP[c], B->a_dtype, which, it,
                                  h->stream));

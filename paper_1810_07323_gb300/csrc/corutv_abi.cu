@@ -232,6 +232,28 @@ int run_pass(corutv_handle* h, int dir, int a_dtype, int mma, const void* A, int
   if (eng != CORUTV_MMA_SIMT && !tma_rows_ok(A, lda, a_dtype)) return CORUTV_ERR_ALIGN;
   const double bytes = (double)m * n * elem_bytes(a_dtype) + (double)l * (a.K + a.len_out) * tc_bytes(a_dtype);
   PhaseTimer tm(h, phase, bytes);
+  // tracing of the resident passes: events around the pass kernel alone as well
+  KernelMark km;
+  if (h->tracing && phase == kPhPass) {
+    km.a = ev_get(h);
+    km.b = ev_get(h);
+    a.kmark = &km;
+  }
+  struct MarkRec {
+    corutv_handle* h;
+    KernelMark* km;
+    double bytes;
+    ~MarkRec() {
+      if (!km->a) return;
+      if (km->state == 2) {
+        h->recs.push_back(TraceRec{kPhPassKernel, km->a, km->b, bytes});
+      } else {
+        // no kernel ran (or the launch failed): the events go back unrecorded
+        h->ev_pool.push_back(km->a);
+        h->ev_pool.push_back(km->b);
+      }
+    }
+  } mark_rec{h, &km, bytes};
   if (eng == CORUTV_MMA_SIMT) {
     if (fro_parts) return CORUTV_ERR_UNSUPPORTED;
     CU(launch_pass_simt(a, dir, a_dtype, h->sms, h->stream));
@@ -909,6 +931,7 @@ int corutv_trace_read(corutv_handle* h, corutv_trace* out) {
       case kPhFro2: t.fro2_ms += ms; break;
       case kPhCorr: t.corr_ms += ms; t.corr_bytes += r.bytes; t.corr_launches += 1; break;
       case kPhQuant: t.quant_ms += ms; break;
+      case kPhPassKernel: t.pass_kernel_ms += ms; t.pass_kernel_launches += 1; break;
       default: break;
     }
     h->ev_pool.push_back(r.a);

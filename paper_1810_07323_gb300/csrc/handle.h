@@ -13,7 +13,7 @@ struct BatchState;                  // batched-solve plan, workspace and graph c
 void batch_state_free(BatchState* b);
 }  // namespace corutv
 
-enum Phase { kPhPass = 0, kPhOrth, kPhCore, kPhQrcp, kPhAsm, kPhFro2, kPhCorr, kPhQuant, kNumPh };
+enum Phase { kPhPass = 0, kPhOrth, kPhCore, kPhQrcp, kPhAsm, kPhFro2, kPhCorr, kPhQuant, kPhPassKernel, kNumPh };
 
 struct TraceRec {
   int phase;

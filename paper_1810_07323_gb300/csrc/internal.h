@@ -26,6 +26,20 @@ int64_t& launch_counter();
 
 // One streaming pass over A: dir 0 (AX): Ct (l x m) = (A X)^T with Xt (l x n);
 // dir 1 (ATY): Ct (l x n) = (A^T Y)^T with Xt (l x m).
+// CUDA events around the main kernel of one pass (tracing): the launchers record `a` right
+// before the pass kernel and `b` right after it, so the pair times that kernel alone (not the
+// operand preparation or the split-tile reduction around it).
+struct KernelMark {
+  cudaEvent_t a = nullptr, b = nullptr;
+  int state = 0;   // 0: nothing recorded, 1: started, 2: both recorded
+  void start(cudaStream_t st) {
+    if (a && state == 0) { cudaEventRecord(a, st); state = 1; }
+  }
+  void stop(cudaStream_t st) {
+    if (b && state == 1) { cudaEventRecord(b, st); state = 2; }
+  }
+};
+
 struct PassArgs {
   const void* A;
   int64_t lda;
@@ -39,6 +53,7 @@ struct PassArgs {
   int64_t ldc;
   void* partials;        // Stream-K partial slots
   int64_t len_out, K;    // AX: (m, n); ATY: (n, m)
+  KernelMark* kmark;     // host-side, may be null: events around the pass kernel
 };
 
 // pass_simt.cu
@@ -232,7 +247,7 @@ int64_t tc_grouped_kblocks(int64_t K);
 int64_t tc_grouped_owner(int64_t x, int64_t total, int64_t G);
 cudaError_t launch_pass_tc_grouped(const GPassProb* gp, int np, int64_t total_iters, int64_t total_tiles, int lmax,
                                    const int2* round_map, int nround, float* partials, bool fro, int sms,
-                                   DevStatus* status, bool keep_a, cudaStream_t st);
+                                   DevStatus* status, bool keep_a, cudaStream_t st, KernelMark* km = nullptr);
 
 // Grouped kind::f16 passes (pass_tc_lp_grouped.cu) for batched BF16 / FP8 problems.  Work is
 // cut into units that depend on the problem alone -- one 256-position output tile and one K range
@@ -281,7 +296,7 @@ inline int lp_unit_nsplit(int64_t K) {
 }
 cudaError_t launch_pass_lp_grouped(const GLpProb* gp, int np, bool fp8, bool fro, const int* cta_first, int G,
                                    const int2* split_map, int nsplit, const int2* red_map, int nred, int lmax,
-                                   DevStatus* status, bool keep_a, cudaStream_t st);
+                                   DevStatus* status, bool keep_a, cudaStream_t st, KernelMark* km = nullptr);
 
 // grouped small kernels (small.cu)
 constexpr int kBatchGramCols = 512;   // columns per Gram partial block

@@ -408,6 +408,7 @@ cudaError_t launch_pass_simt(const PassArgs& a, int dir, int a_dtype, int sms, c
   const int64_t G = simt_pass_grid(a.len_out, a.K, sms);
   if (G <= 0) return cudaSuccess;
   cudaError_t err;
+  if (a.kmark) a.kmark->start(st);
   switch (a_dtype) {
     case 0: err = launch_dir<double>(a, dir, G, st); break;
     case 1: err = launch_dir<float>(a, dir, G, st); break;
@@ -416,6 +417,7 @@ cudaError_t launch_pass_simt(const PassArgs& a, int dir, int a_dtype, int sms, c
     default: return cudaErrorInvalidValue;
   }
   if (err != cudaSuccess) return err;
+  if (a.kmark) a.kmark->stop(st);
   const int LP = a.l <= 32 ? 32 : (a.l <= 64 ? 64 : 128);
   const int64_t tiles = cdiv(a.len_out, kBN), KB = cdiv(a.K, kBK);
   const dim3 rgrid((unsigned)tiles, (unsigned)cdiv(a.l, 16));

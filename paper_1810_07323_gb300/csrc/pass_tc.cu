@@ -290,9 +290,11 @@ cudaError_t launch_pass_tc(const PassArgs& a, int dir, int a_dtype, int mma, int
   TcArgs ta{static_cast<float*>(a.Ct), a.ldc, static_cast<float*>(a.partials), a.len_out, a.K, a.l, status,
             fro_parts};
   const bool conv = (mma == 1), fro = fro_parts != nullptr;
+  if (a.kmark) a.kmark->start(st);
   cudaError_t err = dir == 0 ? launch_dir_tc<0>(mapA, mapX, ta, conv, fro, G, st)
                              : launch_dir_tc<1>(mapA, mapX, ta, conv, fro, G, st);
   if (err != cudaSuccess) return err;
+  if (a.kmark) a.kmark->stop(st);
   // ordered reduction of split tiles
   return launch_streamk_reduce_f32(static_cast<float*>(a.Ct), a.ldc, static_cast<const float*>(a.partials), a.l,
                                    kTcM, kTcBN, a.len_out, cdiv(a.K, kTcBK), G, st);

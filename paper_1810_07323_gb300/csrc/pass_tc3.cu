@@ -527,6 +527,7 @@ cudaError_t launch_pass_tc3(const PassArgs& a, int dir, int sms, DevStatus* stat
   Tc3Args ta{static_cast<float*>(a.Ct), a.ldc, static_cast<float*>(a.partials), a.len_out, a.K, a.l,
              (int)round_up(a.l, 16), status, fro_parts};
   cudaError_t err;
+  if (a.kmark) a.kmark->start(st);
   if (dir == 0)
     err = fro_parts ? launch_variant<0, true>(mapA, mapXh, mapXc, ta, G, st)
                     : launch_variant<0, false>(mapA, mapXh, mapXc, ta, G, st);
@@ -534,6 +535,7 @@ cudaError_t launch_pass_tc3(const PassArgs& a, int dir, int sms, DevStatus* stat
     err = fro_parts ? launch_variant<1, true>(mapA, mapXh, mapXc, ta, G, st)
                     : launch_variant<1, false>(mapA, mapXh, mapXc, ta, G, st);
   if (err != cudaSuccess) return err;
+  if (a.kmark) a.kmark->stop(st);
   return launch_streamk_reduce_f32(static_cast<float*>(a.Ct), a.ldc, static_cast<const float*>(a.partials), a.l,
                                    kNP, kBT, a.len_out, cdiv(a.K, kBK), G, st);
 }

@@ -341,7 +341,7 @@ int64_t tc_grouped_owner(int64_t x, int64_t total, int64_t G) { return gowner(x,
 
 cudaError_t launch_pass_tc_grouped(const GPassProb* gp, int np, int64_t total_iters, int64_t total_tiles, int lmax,
                                    const int2* round_map, int nround, float* partials, bool fro, int sms,
-                                   DevStatus* status, bool keep_a, cudaStream_t st) {
+                                   DevStatus* status, bool keep_a, cudaStream_t st, KernelMark* km) {
   if (np <= 0 || total_iters <= 0) return cudaSuccess;
   if (nround > 0) {
     grouped_round_kernel<<<nround, 256, 0, st>>>(gp, round_map);
@@ -359,10 +359,12 @@ cudaError_t launch_pass_tc_grouped(const GPassProb* gp, int np, int64_t total_it
     if (err != cudaSuccess) return err;
     if (dev >= 0 && dev < 64) attr_set[fro ? 1 : 0][dev] = true;
   }
+  if (km) km->start(st);
   kern<<<(unsigned)G, kThreads, kSmem, st>>>(gp, np, total_iters, partials, status, keep_a ? 1 : 0);
   CORUTV_COUNT_LAUNCH();
   err = cudaGetLastError();
   if (err != cudaSuccess) return err;
+  if (km) km->stop(st);
   (void)total_tiles;
   dim3 rgrid((unsigned)G, (unsigned)cdiv(lmax, 4));
   grouped_reduce_kernel<<<rgrid, 256, 0, st>>>(gp, np, total_iters, G, partials);

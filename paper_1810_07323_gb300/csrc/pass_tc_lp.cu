@@ -533,6 +533,7 @@ cudaError_t launch_pass_tc_lp(const PassArgs& a, int dir, int a_dtype, int sms, 
             fro_parts, a.scales, a.scale_ld, cdiv(a.m, 128), cdiv(a.n, 128)};
   const bool fro = fro_parts != nullptr;
   cudaError_t err;
+  if (a.kmark) a.kmark->start(st);
   if (fp8) {
     if (dir == 0) err = fro ? launch_lp8_variant<0, true>(mA, mH, mL, la, G, st) : launch_lp8_variant<0, false>(mA, mH, mL, la, G, st);
     else err = fro ? launch_lp8_variant<1, true>(mA, mH, mL, la, G, st) : launch_lp8_variant<1, false>(mA, mH, mL, la, G, st);
@@ -541,6 +542,7 @@ cudaError_t launch_pass_tc_lp(const PassArgs& a, int dir, int a_dtype, int sms, 
     err = dir == 0 ? launch_lp_dir<0, false>(mA, mH, mL, la, fro, G, st) : launch_lp_dir<1, false>(mA, mH, mL, la, fro, G, st);
   }
   if (err != cudaSuccess) return err;
+  if (a.kmark) a.kmark->stop(st);
   return launch_streamk_reduce_f32(static_cast<float*>(a.Ct), a.ldc, static_cast<const float*>(a.partials), a.l,
                                    kM, kBN, a.len_out, cdiv(a.K, kBK), G, st);
 }

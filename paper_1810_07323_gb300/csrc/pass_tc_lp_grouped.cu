@@ -372,7 +372,7 @@ cudaError_t launch_variant(const GLpProb* gp, int np, const int* cta_first, int 
 
 cudaError_t launch_pass_lp_grouped(const GLpProb* gp, int np, bool fp8, bool fro, const int* cta_first, int G,
                                    const int2* split_map, int nsplit, const int2* red_map, int nred, int lmax,
-                                   DevStatus* status, bool keep_a, cudaStream_t st) {
+                                   DevStatus* status, bool keep_a, cudaStream_t st, KernelMark* km) {
   if (np <= 0 || G <= 0) return cudaSuccess;
   if (nsplit > 0) {
     lp_grouped_split_kernel<<<nsplit, 256, 0, st>>>(gp, split_map);
@@ -380,11 +380,13 @@ cudaError_t launch_pass_lp_grouped(const GLpProb* gp, int np, bool fp8, bool fro
   }
   cudaError_t err;
   const int ka = keep_a ? 1 : 0;
+  if (km) km->start(st);
   if (fp8) err = fro ? launch_variant<true, true>(gp, np, cta_first, G, status, ka, st)
                      : launch_variant<true, false>(gp, np, cta_first, G, status, ka, st);
   else err = fro ? launch_variant<false, true>(gp, np, cta_first, G, status, ka, st)
                  : launch_variant<false, false>(gp, np, cta_first, G, status, ka, st);
   if (err != cudaSuccess) return err;
+  if (km) km->stop(st);
   if (nred > 0) {
     lp_grouped_reduce_kernel<<<dim3((unsigned)nred, (unsigned)cdiv(lmax, 16)), 256, 0, st>>>(gp, red_map);
     CORUTV_COUNT_LAUNCH();

@@ -450,3 +450,33 @@ def test_batched_fuse_power_flag_is_checked():
     with pytest.raises(corutv.CorutvError) as e:
         b.run()
     assert e.value.status == corutv.ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("kind", ["f32", "bf16"])
+def test_batched_trace_times_the_pass_kernels_alone(kind):
+    """A traced batch of TMA-addressable problems records, for every grouped pass, an event
+    pair around the pass kernel besides the one around its phase (operand preparation and
+    split-tile reduction included)."""
+    shapes = [(700, 304, 6, 6, 14, 1, "right", "exact", "stabilised"),     # rows of 16-byte multiples
+              (512, 1104, 10, 10, 18, 1, "left", "exact", "stabilised"),
+              (1500, 896, 20, 20, 28, 2, "right", "sketch", "stabilised")]
+    items = []
+    for i, (m, n, r, k, l, q, side, core, orth) in enumerate(shapes):
+        A = _lowrank_sparse(C.stream_seed(95, i), m, n, r).astype(np.float32)
+        phi = C.normal_block_np(C.stream_seed(96, i), l, 0, m if side == "left" else n, 0, l)
+        it, _ = _item(A, phi, k, l, q, side, core, orth, kind=kind)
+        items.append(it)
+    h = corutv.Handle()
+    try:
+        b = corutv.Batch(items, handle=h)
+        b.run()
+        h.set_tracing(True)
+        res = b.run()
+        t = h.trace_read()
+        h.set_tracing(False)
+    finally:
+        h.close()
+    assert all(r.info.status == 0 for r in res)
+    assert t.pass_launches > 0
+    assert t.pass_kernel_launches == t.pass_launches
+    assert 0.0 < t.pass_kernel_ms < t.pass_ms

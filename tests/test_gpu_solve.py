@@ -299,3 +299,32 @@ def test_config2_full_size_properties():
     print(f"full size: e_k^2 = {ek2:.4e}, optimal {floor2:.4e}")
     assert ek2 >= floor2 * (1 - 1e-3)
     assert ek2 <= 4.0 * floor2
+
+
+@pytest.mark.parametrize("dt,mma", [(torch.float32, "tf32x3"), (torch.float32, "tf32"), (torch.float32, "simt"),
+                                    (torch.bfloat16, "auto")])
+def test_trace_times_the_pass_kernels_alone(dt, mma):
+    """Tracing records an event pair around every pass kernel besides the one around its whole
+    phase (operand split or rounding, kernel, split-tile reduction): one kernel record per pass,
+    each inside its phase."""
+    rng = np.random.default_rng(7)
+    m, n, k, l, q = 3000, 2000, 20, 40, 1
+    A = rng.standard_normal((m, n))
+    phi = W.phi(n, l)
+    lda = -(-n // 8) * 8 + 8
+    Ad = torch.zeros((m, lda), dtype=dt, device="cuda")[:, :n]
+    Ad.copy_(torch.tensor(A, dtype=torch.float64, device="cuda").to(dt))
+    Pd = torch.tensor(phi, dtype=torch.float32, device="cuda")
+    h = corutv.Handle()
+    try:
+        corutv.solve(Ad, Pd, k, l, q, mma=mma, handle=h)
+        h.set_tracing(True)
+        r = corutv.solve(Ad, Pd, k, l, q, mma=mma, handle=h)
+        t = h.trace_read()
+        h.set_tracing(False)
+    finally:
+        h.close()
+    assert r.info.status == 0
+    assert t.pass_launches == r.info.passes_over_A == 2 * q + 3
+    assert t.pass_kernel_launches == t.pass_launches
+    assert 0.0 < t.pass_kernel_ms < t.pass_ms
