@@ -796,6 +796,7 @@ __device__ __forceinline__ void lmul_tile(const TC* __restrict__ In, int64_t ldi
     const int jmax = R * ((ty | 1) + 1);
     pend = jmax < l ? jmax : l;
   }
+  if (R * (ty & ~1) >= l) pend = 0;               // all rows of the warp are padding (j >= l)
 #pragma unroll 2
   for (int p = 0; p < pend; ++p) {
     TC sv[R], xv[RI];
@@ -1781,31 +1782,53 @@ __device__ __forceinline__ bool batch_gram_sel(const BatchProb& P, int which, in
 }
 
 // FP32 Gram partial of one column range for the grouped launches, with register tiles: a
-// thread owns a TM x TM tile of the LP x LP partial (TM = 4 for LP <= 64, 8 for LP = 128), so
-// each k costs two or four 16-byte shared loads per 16 or 64 FMAs.  For LP = 32 the 64 tiles are
-// computed by four groups of 64 threads, group g taking the columns k = g mod 4 of every staged
+// thread owns a TM x TM tile of the partial (TM = 4 for LP <= 64, 8 for LP = 128), so each k
+// costs two or four 16-byte shared loads per 16 or 64 FMAs.  Only the tiles that hold rows and
+// columns below the problem's own l are formed (TL = ceil(l / TM) per side), and for X X^T only
+// those on or above the diagonal (the rest is their transpose, written as such): the class
+// padding of l to LP costs no FMAs.  The active tiles are taken by G groups of threads (G up to
+// 8, as many as fit in the block), group g forming the columns k = g mod G of every staged
 // block; the group sums are added in group order at the end.  The sums are over this problem's
-// own column range only, so the result does not depend on the other problems of the batch.
+// own column range only and G depends on l alone, so the result does not depend on the other
+// problems of the batch.
 template <int LP>
 __device__ __forceinline__ void gram_tiles_body(const float* __restrict__ Xt, int64_t ldx,
                                                 const float* __restrict__ Yt, int64_t ldy, int64_t len, int l,
                                                 float* __restrict__ parts, int cta, int ncta) {
   constexpr int TM = LP == 128 ? 8 : 4;
-  constexpr int TS = LP / TM, NT = TS * TS, G = 256 / NT;
-  static_assert(G >= 1 && NT * G == 256, "gram tiles");
+  constexpr int TS = LP / TM;
+  constexpr int kMaxG = 8;
   constexpr int BK = 32, LPP = LP + 4;
   constexpr int PER = LP * BK / 4 / 256;        // 16-byte loads of X (and of Y) per thread per stage
-  __shared__ __align__(16) float Xs[BK][LPP];
-  __shared__ __align__(16) float Ys[BK][LPP];
-  __shared__ __align__(16) float red[G > 1 ? NT * TM * TM : 1];
+  static_assert(PER >= 1 && PER * 256 * 4 == LP * BK, "gram stage");
+  static_assert(2 * BK * LPP >= 128 * TM * TM, "group sums reuse the stage buffers");
+  __shared__ __align__(16) float sbuf[2 * BK * LPP];     // X stage, then Y stage
+  float (*Xs)[LPP] = reinterpret_cast<float (*)[LPP]>(sbuf);
+  float (*Ys)[LPP] = reinterpret_cast<float (*)[LPP]>(sbuf + BK * LPP);
   const int tid = threadIdx.x;
-  const int g = tid / NT, t = tid - g * NT, ti = t / TS, tj = t - ti * TS;
   const int64_t chunk = cdiv(cdiv(len, BK), ncta) * BK;
   const int64_t c0 = cta * chunk;
   int64_t c1 = c0 + chunk;
   if (c1 > len) c1 = len;
-  const bool same = Xt == Yt && ldx == ldy;     // X X^T: Y is not staged separately
+  const bool same = Xt == Yt && ldx == ldy;     // X X^T: Y is not staged separately, upper tiles only
   const bool vec = (ldx & 3) == 0 && (ldy & 3) == 0 && ((uintptr_t)Xt & 15) == 0 && ((uintptr_t)Yt & 15) == 0;
+  int TL = (l + TM - 1) / TM;
+  if (TL > TS) TL = TS;
+  const int nact = same ? TL * (TL + 1) / 2 : TL * TL;
+  int G = nact > 0 ? 256 / nact : 1;
+  if (G > kMaxG) G = kMaxG;
+  if (G < 1) G = 1;
+  const int g = tid / (nact > 0 ? nact : 1), t = tid - g * (nact > 0 ? nact : 1);
+  const bool active = nact > 0 && g < G;
+  int ti = 0, tj = 0;
+  if (same) {
+    int rem = t;
+    while (ti < TL && rem >= TL - ti) { rem -= TL - ti; ++ti; }
+    tj = ti + rem;
+  } else if (TL > 0) {
+    ti = t / TL;
+    tj = t - ti * TL;
+  }
   float acc[TM][TM];
 #pragma unroll
   for (int v = 0; v < TM; ++v)
@@ -1844,34 +1867,37 @@ __device__ __forceinline__ void gram_tiles_body(const float* __restrict__ Xt, in
     __syncthreads();
     if (k0 + BK < c1) fetch(k0 + BK);
     const float (*Yv)[LPP] = same ? Xs : Ys;
+    if (active) {
 #pragma unroll 4
-    for (int kk = g; kk < BK; kk += G) {
-      float xa[TM], yb[TM];
+      for (int kk = g; kk < BK; kk += G) {
+        float xa[TM], yb[TM];
 #pragma unroll
-      for (int v = 0; v < TM; v += 4) {
-        const float4 a4 = *reinterpret_cast<const float4*>(&Xs[kk][TM * ti + v]);
-        const float4 b4 = *reinterpret_cast<const float4*>(&Yv[kk][TM * tj + v]);
-        xa[v] = a4.x; xa[v + 1] = a4.y; xa[v + 2] = a4.z; xa[v + 3] = a4.w;
-        yb[v] = b4.x; yb[v + 1] = b4.y; yb[v + 2] = b4.z; yb[v + 3] = b4.w;
+        for (int v = 0; v < TM; v += 4) {
+          const float4 a4 = *reinterpret_cast<const float4*>(&Xs[kk][TM * ti + v]);
+          const float4 b4 = *reinterpret_cast<const float4*>(&Yv[kk][TM * tj + v]);
+          xa[v] = a4.x; xa[v + 1] = a4.y; xa[v + 2] = a4.z; xa[v + 3] = a4.w;
+          yb[v] = b4.x; yb[v + 1] = b4.y; yb[v + 2] = b4.z; yb[v + 3] = b4.w;
+        }
+#pragma unroll
+        for (int v = 0; v < TM; ++v)
+#pragma unroll
+          for (int u = 0; u < TM; ++u) acc[v][u] = fmaf(xa[v], yb[u], acc[v][u]);
       }
-#pragma unroll
-      for (int v = 0; v < TM; ++v)
-#pragma unroll
-        for (int u = 0; u < TM; ++u) acc[v][u] = fmaf(xa[v], yb[u], acc[v][u]);
     }
     __syncthreads();
   }
-  if constexpr (G > 1) {
-    // group sums in group order
+  if (G > 1) {
+    // group sums in group order, through the (now free) stage buffers: nact <= 128 when G > 1
+    float* red = sbuf;
 #pragma unroll 1
     for (int gg = 1; gg < G; ++gg) {
-      if (g == gg)
+      if (active && g == gg)
 #pragma unroll
         for (int v = 0; v < TM; ++v)
 #pragma unroll
           for (int u = 0; u < TM; ++u) red[(t * TM + v) * TM + u] = acc[v][u];
       __syncthreads();
-      if (g == 0)
+      if (active && g == 0)
 #pragma unroll
         for (int v = 0; v < TM; ++v)
 #pragma unroll
@@ -1879,7 +1905,7 @@ __device__ __forceinline__ void gram_tiles_body(const float* __restrict__ Xt, in
       __syncthreads();
     }
   }
-  if (g == 0) {
+  if (active && g == 0) {
     float* out = parts + (int64_t)cta * LP * LP;
 #pragma unroll
     for (int v = 0; v < TM; ++v)
@@ -1887,11 +1913,18 @@ __device__ __forceinline__ void gram_tiles_body(const float* __restrict__ Xt, in
       for (int u = 0; u < TM; u += 4)
         *reinterpret_cast<float4*>(&out[(TM * ti + v) * LP + TM * tj + u]) =
             make_float4(acc[v][u], acc[v][u + 1], acc[v][u + 2], acc[v][u + 3]);
+    if (same && ti != tj)
+#pragma unroll
+      for (int u = 0; u < TM; ++u)
+#pragma unroll
+        for (int v = 0; v < TM; v += 4)
+          *reinterpret_cast<float4*>(&out[(TM * tj + u) * LP + TM * ti + v]) =
+              make_float4(acc[v][u], acc[v + 1][u], acc[v + 2][u], acc[v + 3][u]);
   }
 }
 
 template <int LP>
-__global__ void __launch_bounds__(256) gram_partial_grouped_kernel(const BatchProb* __restrict__ probs,
+__global__ void __launch_bounds__(256, LP == 128 ? 1 : 3) gram_partial_grouped_kernel(const BatchProb* __restrict__ probs,
                                                                    const int2* __restrict__ map, int which, int it,
                                                                    int pass) {
   const int2 pm = map[blockIdx.x];
