@@ -63,6 +63,8 @@ struct BatchTune {
   int tc_order = 0;                   // tensor-core pass tables: 0 problems as given, 1 largest K first
 };
 
+enum MapKind { kMapT1 = 0, kMapT2, kMapG1, kMapG2, kMapRed, kMapLm1, kMapLm2, kMapS2, kMapQ, kNumMaps };
+
 struct BatchState {
   std::vector<unsigned char> key;     // bytes of the problem array the tables were built for
   BatchTune tune;                     // shapes the tables were built with
@@ -86,9 +88,10 @@ struct BatchState {
   // grouped-launch maps (device) and their block counts, per sketch-size class (problems
   // with l <= 32, <= 64, <= 128 run the 32-, 64- and 128-row kernel variants); kinds:
   // kMapT1/T2 SIMT pass tiles, kMapG1/G2 Gram partials, kMapRed Gram reduction, kMapLm1/Lm2
-  // lmul tiles, kMapS2 32-column tiles of the second sketch (class-independent: class 0)
-  int2* map[3][8] = {};
-  int nmap[3][8] = {};
+  // lmul tiles, kMapS2 32-column tiles of the second sketch (class-independent: class 0), kMapQ
+  // one block per problem (QRCP)
+  int2* map[3][kNumMaps] = {};
+  int nmap[3][kNumMaps] = {};
   int lp = 32, lmax = 1, maxq = 0, a_dtype = CORUTV_F32;
   bool any_exact = false, any_sketch = false, any_fro2 = false;
   bool tc = false;                    // FP32 batch: passes on the tensor cores (grouped TF32)
@@ -126,7 +129,6 @@ constexpr size_t kBAlign = 256;
 
 size_t align_up(size_t x) { return (x + kBAlign - 1) / kBAlign * kBAlign; }
 
-enum MapKind { kMapT1 = 0, kMapT2, kMapG1, kMapG2, kMapRed, kMapLm1, kMapLm2, kMapS2 };
 constexpr int kClassLP[3] = {32, 64, 128};
 // A of one group of fused problems: small enough to stay in L2 (126 MB) between its C1 and W launches
 constexpr double kFuseGroupBytes = 80.0 * (1 << 20);
@@ -269,8 +271,8 @@ struct Plan {
   std::vector<std::vector<std::pair<int, int>>> t_groups;
   int t_core = -1;
   std::vector<ProbSizes> sz;
-  std::vector<int2> maps[3][8];       // per class and MapKind
-  size_t off_maps[3][8] = {};
+  std::vector<int2> maps[3][kNumMaps];   // per class and MapKind
+  size_t off_maps[3][kNumMaps] = {};
   std::vector<PassTable> ptabs;
   std::vector<std::vector<int>> pt_probs;     // problems of each pass table
   std::vector<std::vector<int2>> pt_rmaps;
@@ -310,10 +312,11 @@ void make_plan(Plan& L, int count, const corutv_problem* probs, int sms, const B
     add_blocks(mc[kMapLm1], i, cdiv(z.len1, kBatchLmulBI));
     add_blocks(mc[kMapLm2], i, cdiv(z.len2, kBatchLmulBI));
     add_blocks(L.maps[0][kMapS2], i, cdiv(z.len2, kBatchTile32));
+    add_blocks(mc[kMapQ], i, 1);
   }
   size_t off = align_up(sizeof(BatchProb) * count);
   for (int c = 0; c < 3; ++c)
-    for (int k = 0; k < 8; ++k) {
+    for (int k = 0; k < kNumMaps; ++k) {
       L.off_maps[c][k] = off;
       off += align_up(sizeof(int2) * std::max<size_t>(1, L.maps[c][k].size()));
     }
@@ -522,7 +525,7 @@ int build(corutv_handle* h, BatchState* B, int count, const corutv_problem* prob
   memset(hb, 0, L.table_bytes);
   B->dprobs = reinterpret_cast<BatchProb*>(d);
   for (int c = 0; c < 3; ++c)
-    for (int k = 0; k < 8; ++k) {
+    for (int k = 0; k < kNumMaps; ++k) {
       B->map[c][k] = reinterpret_cast<int2*>(d + L.off_maps[c][k]);
       B->nmap[c][k] = (int)L.maps[c][k].size();
       if (!L.maps[c][k].empty())
@@ -936,7 +939,8 @@ int enqueue(corutv_handle* h, const BatchState* B) {
   }
   {
     PhaseTimer tm(h, kPhQrcp);
-    CUB(launch_qrcp_grouped(B->dprobs, B->count, st));                                  // S6
+    for (int c = 0; c < 3; ++c)                                                         // S6
+      CUB(launch_qrcp_grouped(B->dprobs, B->map[c][kMapQ], B->nmap[c][kMapQ], kClassLP[c], st));
   }
   {
     PhaseTimer tm(h, kPhAsm);

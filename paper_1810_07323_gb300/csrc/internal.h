@@ -311,7 +311,7 @@ cudaError_t launch_lmul_orth_grouped(const BatchProb* P, const int2* map, int nb
                                      int pass, cudaStream_t st);
 cudaError_t launch_copy_sketch_grouped(const BatchProb* P, const int2* map32_2, int nblocks, int it,
                                        cudaStream_t st);
-cudaError_t launch_qrcp_grouped(const BatchProb* P, int count, cudaStream_t st);
+cudaError_t launch_qrcp_grouped(const BatchProb* P, const int2* map, int count, int lp, cudaStream_t st);
 cudaError_t launch_assemble_grouped(const BatchProb* P, const int2* map_lmul1, int n1, const int2* map32_2, int n2,
                                     int lp, cudaStream_t st);
 cudaError_t launch_fro2_grouped(const BatchProb* P, int count, cudaStream_t st);

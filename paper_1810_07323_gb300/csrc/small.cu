@@ -739,8 +739,10 @@ __device__ __forceinline__ void lmul_stage_S(const TS* __restrict__ S, int64_t l
   }
 }
 
-// one BI-column tile (index bx) with S already staged in Ss; Is: LP x (BI + 4)
-template <typename TC, int LP, int BI>
+// one BI-column tile (index bx) with S already staged in Ss; Is: LP x (BI + 4).  SKIP_PAD: warps
+// whose rows are all at or beyond l skip the product (the grouped launches, where LP is a class
+// width above the problem's l)
+template <typename TC, int LP, int BI, bool SKIP_PAD = false>
 __device__ __forceinline__ void lmul_tile(const TC* __restrict__ In, int64_t ldi, int64_t len, int l,
                                           const TC* __restrict__ Ss, TC* __restrict__ Is, TC* __restrict__ Out,
                                           int64_t ldo, int out_rowmajor, int upper, const int* __restrict__ defic,
@@ -796,7 +798,7 @@ __device__ __forceinline__ void lmul_tile(const TC* __restrict__ In, int64_t ldi
     const int jmax = R * ((ty | 1) + 1);
     pend = jmax < l ? jmax : l;
   }
-  if (R * (ty & ~1) >= l) pend = 0;               // all rows of the warp are padding (j >= l)
+  if (SKIP_PAD && R * (ty & ~1) >= l) pend = 0;   // all rows of the warp are padding (j >= l)
 #pragma unroll 2
   for (int p = 0; p < pend; ++p) {
     TC sv[R], xv[RI];
@@ -854,7 +856,8 @@ __device__ __forceinline__ void lmul_body(const TC* __restrict__ In, int64_t ldi
   TC* Ss = reinterpret_cast<TC*>(smem_raw);
   TC* Is = Ss + LP * (LP + 4);
   lmul_stage_S<TC, TS, LP>(S, lds, l, Ss);
-  lmul_tile<TC, LP, BI>(In, ldi, len, l, Ss, Is, Out, ldo, out_rowmajor, upper, defic, pass, bx, round_out, ldr);
+  lmul_tile<TC, LP, BI, true>(In, ldi, len, l, Ss, Is, Out, ldo, out_rowmajor, upper, defic, pass, bx, round_out,
+                              ldr);
 }
 
 template <typename TC, typename TS, int LP, int BI>
@@ -1319,30 +1322,32 @@ __global__ void __launch_bounds__(512) qrcp_kernel(const double* __restrict__ Dg
 // physical column exchanges.  The reflector and pivot column are stored with a
 // skew (row i at i + 4 (i / RPT)) so the TPC threads of a column read them
 // without shared-memory bank conflicts.
+// LQ: the capacity (rows and columns, l <= LQ); the grouped launches size it by l's class.
 // PIVOT = false: the unpivoted Householder QR (step j takes the column at position j), the
 // second factorisation of the QLP.  d_transposed: the input is D^T (Dg read column-wise).
 // tk_by_col: the rank-k readout sums the squares of the first k columns of R (the first k
 // rows of the output R^T) instead of its first k rows.
-template <int TPC, typename TD, typename TQ, bool PIVOT = true>
+template <int TPC, typename TD, typename TQ, bool PIVOT = true, int LQ = kMaxL>
 __device__ __forceinline__ void qrcp_reg_body(const TD* __restrict__ Dg, int64_t ldd, int l, int k,
                                               TQ* __restrict__ Qg, int64_t ldq, double* __restrict__ Rg,
                                               int64_t ldr, int r_transposed, int32_t* __restrict__ perm,
                                               double* __restrict__ fro2, DevStatus* status, int d_transposed = 0,
                                               int tk_by_col = 0) {
-  constexpr int RPT = kMaxL / TPC, NWARP = kMaxL * TPC / 32, CPW = 32 / TPC;   // columns per warp
+  constexpr int RPT = LQ / TPC, NWARP = LQ * TPC / 32, CPW = 32 / TPC;   // columns per warp
+  static_assert(RPT % 4 == 0 && NWARP <= 32 && LQ <= kMaxL, "qrcp capacity");
   // row i of the reflector and of the pivot column lives at i + 4 (i / RPT): the RPT-row
   // pieces that the TPC threads of a column read start in different banks
-  constexpr int SKW = kMaxL + 4 * TPC;
+  constexpr int SKW = LQ + 4 * TPC;
   extern __shared__ __align__(16) unsigned char qrcp_smem[];
   float* Vs = reinterpret_cast<float*>(qrcp_smem);   // reflector of step j in row j (zero outside j..l-1)
   __shared__ __align__(16) float pcolv[SKW];         // raw pivot column
-  __shared__ float betas[kMaxL];
+  __shared__ float betas[LQ];
   auto sk = [](int i) { return i + 4 * (i / RPT); };
   __shared__ float cnrm[NWARP];                      // each warp's candidate: trailing norm^2 (-1: none),
   __shared__ int cpos[NWARP], ccol[NWARP];           // its current position and its column
   __shared__ int piv[3];                             // pivot column, -, its position before the swap
-  __shared__ float rdiag[kMaxL];
-  __shared__ int pcol[kMaxL];
+  __shared__ float rdiag[LQ];
+  __shared__ int pcol[LQ];
   __shared__ double red[NWARP][2];
   const int tid = threadIdx.x, c = tid / TPC, h = tid % TPC, lane = tid & 31, warp = tid >> 5;
   const int i0 = RPT * h;
@@ -1408,7 +1413,8 @@ __device__ __forceinline__ void qrcp_reg_body(const TD* __restrict__ Dg, int64_t
         posof = j;
       }
       __syncwarp();
-      const float4 x4 = *reinterpret_cast<const float4*>(pcolv + sk(4 * lane));   // rows 4 lane .. 4 lane + 3
+      const bool rl = 4 * lane < LQ;               // the lane's rows 4 lane .. 4 lane + 3 exist
+      const float4 x4 = rl ? *reinterpret_cast<const float4*>(pcolv + sk(4 * lane)) : make_float4(0.f, 0.f, 0.f, 0.f);
       float xv[4] = {x4.x, x4.y, x4.z, x4.w};
       float ss = 0.f;
 #pragma unroll
@@ -1435,7 +1441,7 @@ __device__ __forceinline__ void qrcp_reg_body(const TD* __restrict__ Dg, int64_t
         const int i = 4 * lane + e;
         vp[e] = (i == j) ? v0 : ((i > j && i < l) ? xv[e] : 0.f);
       }
-      *reinterpret_cast<float4*>(Vs + j * SKW + sk(4 * lane)) = vo;
+      if (rl) *reinterpret_cast<float4*>(Vs + j * SKW + sk(4 * lane)) = vo;
       if (lane == 0) { betas[j] = beta; rdiag[j] = alpha; pcol[j] = cp; }
     }
     __syncthreads();
@@ -1993,11 +1999,13 @@ __global__ void __launch_bounds__(256) copy_sketch_grouped_kernel(const BatchPro
   }
 }
 
-__global__ void __launch_bounds__(kMaxL * kQrcpTPC) qrcp_grouped_kernel(const BatchProb* __restrict__ probs) {
-  const BatchProb& P = probs[blockIdx.x];
-  qrcp_reg_body<kQrcpTPC, float, float>(P.D, P.l, P.l, P.k, P.Qt, P.l, P.T, P.ldt, P.side == 1 ? 1 : 0, P.perm,
-                                         nullptr,
-                          P.status);
+// one problem per block (map: (problem, 0)), the register QRCP sized by the class of l
+template <int LQ>
+__global__ void __launch_bounds__(LQ * kQrcpTPC) qrcp_grouped_kernel(const BatchProb* __restrict__ probs,
+                                                                     const int2* __restrict__ map) {
+  const BatchProb& P = probs[map[blockIdx.x].x];
+  qrcp_reg_body<kQrcpTPC, float, float, true, LQ>(P.D, P.l, P.l, P.k, P.Qt, P.l, P.T, P.ldt, P.side == 1 ? 1 : 0,
+                                                   P.perm, nullptr, P.status);
 }
 
 // U = Q1 Q~ (RIGHT; V for LEFT), row-major out
@@ -2102,14 +2110,22 @@ cudaError_t launch_copy_sketch_grouped(const BatchProb* P, const int2* map32_2, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_qrcp_grouped(const BatchProb* P, int count, cudaStream_t st) {
-  if (count <= 0) return cudaSuccess;
+template <int LQ>
+static cudaError_t qrcp_grouped_lq(const BatchProb* P, const int2* map, int count, cudaStream_t st) {
+  constexpr size_t sm = (size_t)LQ * (LQ + 4 * kQrcpTPC) * sizeof(float);
   static bool attr_set[kAttrDevices] = {};
-  cudaError_t e = raise_smem_once(qrcp_grouped_kernel, kQrcpSmem, attr_set);
+  cudaError_t e = raise_smem_once(qrcp_grouped_kernel<LQ>, sm, attr_set);
   if (e != cudaSuccess) return e;
-  qrcp_grouped_kernel<<<count, kMaxL * kQrcpTPC, kQrcpSmem, st>>>(P);
+  qrcp_grouped_kernel<LQ><<<count, LQ * kQrcpTPC, sm, st>>>(P, map);
   CORUTV_COUNT_LAUNCH();
   return cudaGetLastError();
+}
+
+cudaError_t launch_qrcp_grouped(const BatchProb* P, const int2* map, int count, int lp, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  if (lp <= 32) return qrcp_grouped_lq<32>(P, map, count, st);
+  if (lp <= 64) return qrcp_grouped_lq<64>(P, map, count, st);
+  return qrcp_grouped_lq<kMaxL>(P, map, count, st);
 }
 
 template <int LP>
