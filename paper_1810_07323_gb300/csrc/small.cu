@@ -1715,10 +1715,16 @@ cudaError_t launch_add_st(const TC* src, int64_t lds, int l, int64_t len, TC* ds
 template cudaError_t launch_add_st<float>(const float*, int64_t, int, int64_t, float*, int64_t, cudaStream_t);
 template cudaError_t launch_add_st<double>(const double*, int64_t, int, int64_t, double*, int64_t, cudaStream_t);
 
+// Sum of n FP64 partials by one warp in a fixed order: lane t adds parts t, t + 32, ... in
+// turn, then the 32 lane sums meet in a fixed shuffle tree (the same bits on every run).
 __global__ void sum_parts_kernel(const double* __restrict__ parts, int n, double* out, DevStatus* status) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    double s = 0.0;
-    for (int i = 0; i < n; ++i) s += parts[i];
+  if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+  const int lane = threadIdx.x;
+  double s = 0.0;
+  for (int i = lane; i < n; i += 32) s += parts[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (lane == 0) {
     if (out) *out = s;
     if (status) status->fro2_A = s;
   }
