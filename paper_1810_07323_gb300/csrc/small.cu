@@ -1817,6 +1817,11 @@ __device__ __forceinline__ void gram_tiles_body(const float* __restrict__ Xt, in
   __shared__ __align__(16) float sbuf[2 * BK * LPP];     // X stage, then Y stage
   float (*Xs)[LPP] = reinterpret_cast<float (*)[LPP]>(sbuf);
   float (*Ys)[LPP] = reinterpret_cast<float (*)[LPP]>(sbuf + BK * LPP);
+  // stage row kk keeps its 4-float chunks in the order chunk ^ ((kk / 4) mod 8): the transposing
+  // stores of a warp (eight k, four rows of A's sketch) then fall in 32 different banks, and a
+  // tile's 4 consecutive rows stay one 16-byte vector
+  static_assert(LP >= 32 && LPP % 32 == 4, "gram stage swizzle");
+  auto sw = [](int kk, int col) { return (((col >> 2) ^ ((kk >> 2) & 7)) << 2) | (col & 3); };
   const int tid = threadIdx.x;
   const int64_t chunk = cdiv(cdiv(len, BK), ncta) * BK;
   const int64_t c0 = cta * chunk;
@@ -1871,9 +1876,10 @@ __device__ __forceinline__ void gram_tiles_body(const float* __restrict__ Xt, in
 #pragma unroll
     for (int q = 0; q < PER; ++q) {
       const int x = tid + 256 * q, r = x / (BK / 4), kk = 4 * (x % (BK / 4));
-      Xs[kk][r] = px[q].x; Xs[kk + 1][r] = px[q].y; Xs[kk + 2][r] = px[q].z; Xs[kk + 3][r] = px[q].w;
+      const int rs = sw(kk, r);                  // the same chunk order for rows kk .. kk + 3
+      Xs[kk][rs] = px[q].x; Xs[kk + 1][rs] = px[q].y; Xs[kk + 2][rs] = px[q].z; Xs[kk + 3][rs] = px[q].w;
       if (!same) {
-        Ys[kk][r] = py[q].x; Ys[kk + 1][r] = py[q].y; Ys[kk + 2][r] = py[q].z; Ys[kk + 3][r] = py[q].w;
+        Ys[kk][rs] = py[q].x; Ys[kk + 1][rs] = py[q].y; Ys[kk + 2][rs] = py[q].z; Ys[kk + 3][rs] = py[q].w;
       }
     }
     __syncthreads();
@@ -1885,8 +1891,8 @@ __device__ __forceinline__ void gram_tiles_body(const float* __restrict__ Xt, in
         float xa[TM], yb[TM];
 #pragma unroll
         for (int v = 0; v < TM; v += 4) {
-          const float4 a4 = *reinterpret_cast<const float4*>(&Xs[kk][TM * ti + v]);
-          const float4 b4 = *reinterpret_cast<const float4*>(&Yv[kk][TM * tj + v]);
+          const float4 a4 = *reinterpret_cast<const float4*>(&Xs[kk][sw(kk, TM * ti + v)]);
+          const float4 b4 = *reinterpret_cast<const float4*>(&Yv[kk][sw(kk, TM * tj + v)]);
           xa[v] = a4.x; xa[v + 1] = a4.y; xa[v + 2] = a4.z; xa[v + 3] = a4.w;
           yb[v] = b4.x; yb[v + 1] = b4.y; yb[v + 2] = b4.z; yb[v + 3] = b4.w;
         }
