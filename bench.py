@@ -3,7 +3,8 @@ independent replicas -- a solve does not shard).
 
 Workloads (--workload):
   fp32 (default)  20000 x 20000 FP32 A = G1 diag(i^-1.5) G2^T + 1e-8 noise,
-                  k=100, l=120, q=1, exact core, TF32 tensor-core passes.
+                  k=100, l=120, q=1, sketch core (D = C2^T Q2, 2q+2 passes),
+                  split-operand FP32-class tensor-core passes.
   bf16 / fp8      32768 x 16384 A with sigma_i = exp(-i/30), k=64, l=80, q=2:
                   FP32 A quantised on the device (BF16, or FP8 e4m3 with
                   128 x 128 tile scales), 2q+2 kind::f16 passes over the stored
@@ -359,15 +360,57 @@ def cpu_cores():
         return os.cpu_count()
 
 
-def oracle_solve_time(A64, phi64, w):
+def cpu_model():
+    """The host CPU as /proc/cpuinfo names it ('model name' on x86; implementer and part on Arm)."""
+    import platform
+    import re
+    try:
+        with open("/proc/cpuinfo") as f:
+            txt = f.read()
+    except OSError:
+        return platform.processor() or platform.machine()
+    for key in ("model name", "Model", "Hardware"):
+        mt = re.search(rf"^{key}\s*:\s*(.+)$", txt, re.M)
+        if mt:
+            return mt.group(1).strip()
+    imp = re.search(r"^CPU implementer\s*:\s*(\S+)", txt, re.M)
+    part = re.search(r"^CPU part\s*:\s*(\S+)", txt, re.M)
+    if imp and part:
+        return f"{platform.machine()}, CPU implementer {imp.group(1)}, part {part.group(1)}"
+    return platform.machine()
+
+
+def oracle_single_thread_time(A64, phi64, w, core="exact"):
+    """The same oracle solve in a child process whose BLAS runs one thread (the thread
+    count is fixed before numpy loads); returns seconds, or None if the child failed."""
+    import numpy as np
+    with tempfile.TemporaryDirectory() as d:
+        fa, fp = os.path.join(d, "A.npy"), os.path.join(d, "phi.npy")
+        np.save(fa, A64)
+        np.save(fp, phi64)
+        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+                   BLIS_NUM_THREADS="1")
+        code = ("import json, sys; sys.path.insert(0, %r); import numpy as np; import bench; "
+                "t, _ = bench.oracle_solve_time(np.load(%r), np.load(%r), json.loads(%r), %r); print(t)"
+                % (ROOT, fa, fp, json.dumps({k: w[k] for k in ("dtype", "k", "l", "q")}), core))
+        try:
+            out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                                 timeout=600, check=True).stdout
+            return float(out.strip().splitlines()[-1])
+        except (subprocess.SubprocessError, ValueError, IndexError):
+            return None
+
+
+def oracle_solve_time(A64, phi64, w, core="exact"):
     """One oracle solve (as it stands) on the host cores; returns seconds and the result.
-    For the BF16 / FP8 workloads the oracle's storage conversion of the sample and
-    the correction-pass core are part of the timed solve."""
+    core "sketch": the oracle's core from the last sketch (its D_approx, Sec. IV-B), the form
+    of the GPU's sketch core.  For the BF16 / FP8 workloads the oracle's storage conversion of
+    the sample and the correction-pass core are part of the timed solve."""
     from oracle import corutv_oracle as O
     from oracle import precision as P
     t0 = time.perf_counter()
     if w["dtype"] == "f32":
-        r = O.corutv(A64, phi64, w["k"], w["l"], w["q"])
+        r = O.corutv(A64, phi64, w["k"], w["l"], w["q"], core="approx" if core == "sketch" else "exact")
     else:
         A32 = A64.astype("float32")
         if w["dtype"] == "bf16":
@@ -442,7 +485,8 @@ def run_reference(args):
                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                "data": "synthetic", "config": {"workload": f"Sec. VI-C synthetic robust PCA {w['n']}x{w['n']}"},
-               "cpu_baseline": {"value": ms, "unit": "ms", "cores": cpu_cores(), "kind": "oracle",
+               "cpu_baseline": {"value": ms, "unit": "ms", "cores": cpu_cores(),
+                                "cpu_model": cpu_model(), "kind": "oracle",
                                 "sample": "whole FP64 oracle ALM-CoRUTV runs of the same matrix"},
                "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(out), flush=True)
@@ -462,7 +506,8 @@ def run_reference(args):
                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3,
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                "data": "synthetic", "config": {"workload": workload_label(w, "exact"), "count": len(probs)},
-               "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
+               "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cpu_cores(),
+                                "cpu_model": cpu_model(), "kind": "oracle",
                                 "sample": f"oracle solves of {len(idx)} evenly spaced problems of the batch, "
                                           f"scaled by total m*n"},
                "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -476,23 +521,26 @@ def run_reference(args):
     sm, sn = cpu_sample_shape(w)
     A = g.block(0, sm, 0, sn)
     phi = W.phi(w["n"], w["l"])[:sn]
+    core = args.core if w["dtype"] == "f32" else "exact"
     for _ in range(args.warmup):
-        oracle_solve_time(A, phi, w)
+        oracle_solve_time(A, phi, w, core)
     ts = []
     for _ in range(args.steps):
-        t, _ = oracle_solve_time(A, phi, w)
+        t, _ = oracle_solve_time(A, phi, w, core)
         ts.append(t)
     per = sum(ts) / len(ts)
     scale = (w["m"] * w["n"]) / float(sm * sn)      # passes dominate: cost ~ m n
     value = 1.0 / (per * scale)
-    sample = f"oracle solve of the {sm}x{sn} leading block (same generator, q={w['q']}), scaled by m*n"
+    sample = (f"oracle solve of the {sm}x{sn} leading block (same generator, q={w['q']}, "
+              f"{'core from the last sketch' if core == 'sketch' else 'exact core'}), scaled by m*n")
     out = {"impl": "reference", "metric": "CoR-UTV solves/s", "value": value, "unit": "solves/s",
            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic",
-           "config": {"workload": workload_label(w, "exact"), "m": w["m"], "n": w["n"], "k": w["k"],
-                      "l": w["l"], "q": w["q"]},
-           "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
+           "config": {"workload": workload_label(w, core), "m": w["m"], "n": w["n"], "k": w["k"],
+                      "l": w["l"], "q": w["q"], "core": core},
+           "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cpu_cores(),
+                            "cpu_model": cpu_model(), "kind": "oracle",
                             "sample": sample},
            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -649,7 +697,8 @@ def main_batched(args):
         cidx = idx[:8]
         t = batch_sample_time(probs, cidx)
         scale = sum(p.m * p.n for p in probs) / float(sum(probs[i].m * probs[i].n for i in cidx))
-        cpu = {"value": count / (t * scale), "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
+        cpu = {"value": count / (t * scale), "unit": "solves/s", "cores": cpu_cores(),
+               "cpu_model": cpu_model(), "kind": "oracle",
                "sample": f"FP64 oracle solves of {len(cidx)} evenly spaced problems ({t:.2f} s), scaled by "
                          f"the batch's total m*n"}
 
@@ -832,7 +881,8 @@ def main_serving(args):
                "note": "GPU factors of sampled timed requests (own output buffers) vs the FP64 oracle on the "
                        "same BF16 values and Psi; ratio = GPU rank-k error / oracle's"}
         if not args.no_cpu_baseline:
-            cpu = {"value": len(rows) / tsum, "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
+            cpu = {"value": len(rows) / tsum, "unit": "solves/s", "cores": cpu_cores(),
+                   "cpu_model": cpu_model(), "kind": "oracle",
                    "sample": f"FP64 oracle on the {len(rows)} sampled timed requests (all size classes), "
                              "sequential"}
     if rank == 0:
@@ -952,7 +1002,8 @@ def main_rpca(args):
         ref = R.alm_corutv(M.astype(np.float64), phi.astype(np.float64), r0, l, w["q"], prm["lam"], prm["mu0"],
                            prm["rho"], prm["mu_bar"], 1e-5, 100)
         tc = time.perf_counter() - t0
-        cpu = {"value": tc * 1e3, "unit": "ms", "cores": cpu_cores(), "kind": "oracle",
+        cpu = {"value": tc * 1e3, "unit": "ms", "cores": cpu_cores(),
+               "cpu_model": cpu_model(), "kind": "oracle",
                "sample": f"one FP64 oracle ALM-CoRUTV run of the same {n}x{n} matrix ({ref['iters']} iterations)"}
     paper = PAPER_RPCA_S.get((n, w["sparse"]))
     if rank == 0:
@@ -1193,12 +1244,20 @@ def main():
         sm, sn = cpu_sample_shape(w)
         A64 = A[:sm, :sn].double().cpu().numpy()
         P64 = phi[:sn].double().cpu().numpy()
-        t, r_or = oracle_solve_time(A64, P64, w)
+        _, r_or = oracle_solve_time(A64, P64, w)           # exact core: the error reference
+        ocore = args.core if w["dtype"] == "f32" else "exact"
+        t, _ = oracle_solve_time(A64, P64, w, ocore)       # the timed settings' core form
         scale = (m * n) / float(sm * sn)
         if not args.no_cpu_baseline:
+            t1 = oracle_single_thread_time(A64, P64, w, ocore)
             cpu = {"value": 1.0 / (t * scale), "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
-                   "sample": f"one FP64 oracle solve of the {sm}x{sn} leading block of A (q={q}), {t:.2f} s, "
-                             f"scaled by m*n/({sm}*{sn})"}
+                   "sample": f"one FP64 oracle solve of the {sm}x{sn} leading block of A (q={q}, "
+                             f"{'core from the last sketch' if ocore == 'sketch' else 'exact core'}), {t:.2f} s, "
+                             f"scaled by m*n/({sm}*{sn})",
+                   "cpu_model": cpu_model(), "threads": "numpy's BLAS default (all cores)",
+                   "single_thread": None if t1 is None else
+                   {"value": 1.0 / (t1 * scale), "unit": "solves/s", "seconds": t1,
+                    "sample": "the same block solve with the BLAS limited to one thread"}}
         # the same block solved by the GPU with the timed settings: rank-k errors side by side
         Ab = A[:sm, :sn].contiguous()
         Pb = phi[:sn].contiguous()
