@@ -1980,7 +1980,7 @@ __global__ void __launch_bounds__(kPipeMaxThreads, 1) cholinv_grouped_kernel(con
 }
 
 template <int LP>
-__global__ void __launch_bounds__(256, 1) lmul_orth_grouped_kernel(const BatchProb* __restrict__ probs,
+__global__ void __launch_bounds__(256, LP == 32 ? 8 : (LP == 64 ? 4 : 1)) lmul_orth_grouped_kernel(const BatchProb* __restrict__ probs,
                                                                    const int2* __restrict__ map, int which, int it,
                                                                    int pass) {
   const int2 pm = map[blockIdx.x];
@@ -2022,7 +2022,7 @@ __global__ void __launch_bounds__(LQ * kQrcpTPC) qrcp_grouped_kernel(const Batch
 
 // U = Q1 Q~ (RIGHT; V for LEFT), row-major out
 template <int LP>
-__global__ void __launch_bounds__(256, 1) assemble_lmul_grouped_kernel(const BatchProb* __restrict__ probs,
+__global__ void __launch_bounds__(256, LP == 32 ? 6 : (LP == 64 ? 4 : 1)) assemble_lmul_grouped_kernel(const BatchProb* __restrict__ probs,
                                                                        const int2* __restrict__ map) {
   const int2 pm = map[blockIdx.x];
   const BatchProb& P = probs[pm.x];
