@@ -34,7 +34,8 @@ def test_traffic_lines_of_the_profiles_parse():
             for line in f:
                 mt = re.match(r"\s*traffic_bytes_per_launch\s+(\S+)\s+(\S+)", line)
                 if mt:
-                    assert re.fullmatch(r"[a-z0-9_]+/[a-z0-9]+/[0-9a-z]+(/l[0-9]+)?/src-[0-9a-f]{10}", mt.group(1)), mt.group(1)
+                    pat = r"[a-z0-9_]+/[a-z0-9]+/[0-9a-z]+(/l[0-9]+)?/src-[0-9a-f]{10}"
+                    assert re.fullmatch(pat, mt.group(1)), mt.group(1)
                     assert float(mt.group(2)) > 0
                     keys.append(mt.group(1))
     assert keys
