@@ -704,7 +704,7 @@ int corutv_destroy(corutv_handle* h) {
     cudaEventDestroy(r.b);
   }
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
-  batch_state_free(h->batch);
+  for (BatchState* b : h->batch_pool) batch_state_free(b);
   rpca_free(h);
   ring_free(h);
   resid_free(h);
