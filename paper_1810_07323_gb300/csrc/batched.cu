@@ -67,8 +67,6 @@ enum MapKind { kMapT1 = 0, kMapT2, kMapG1, kMapG2, kMapRed, kMapLm1, kMapLm2, kM
 
 struct BatchState {
   std::vector<unsigned char> key;     // bytes of the problem array the tables were built for
-  std::vector<unsigned char> shape;   // the same without the buffer addresses (shape_key)
-  uint64_t last_use = 0;              // the handle's call counter at its last use
   BatchTune tune;                     // shapes the tables were built with
   bool tuned = false, tune_from_cache = false;
   double tuned_ms = 0.0, default_ms = 0.0;
@@ -499,11 +497,7 @@ void make_plan(Plan& L, int count, const corutv_problem* probs, int sms, const B
 }
 
 // Build tables and buffers for a new problem set (the stream is idle).
-// keep_graph: the problem set has the shape of the one the captured graph was made for (same
-// sizes, flags and alignment; other buffers), so the plan, the workspace layout and every kernel
-// argument are the same and only the tables' buffer addresses and tensor maps change.
-int build(corutv_handle* h, BatchState* B, int count, const corutv_problem* probs, const BatchTune& tune,
-          bool keep_graph = false) {
+int build(corutv_handle* h, BatchState* B, int count, const corutv_problem* probs, const BatchTune& tune) {
   Plan L;
   make_plan(L, count, probs, h->sms, tune);
   if (!B->ws || B->ws_bytes < L.need) {
@@ -794,7 +788,7 @@ int build(corutv_handle* h, BatchState* B, int count, const corutv_problem* prob
   B->key.assign(reinterpret_cast<const unsigned char*>(probs),
                 reinterpret_cast<const unsigned char*>(probs) + sizeof(corutv_problem) * count);
   B->tune = tune;
-  if (B->exec && !keep_graph) {
+  if (B->exec) {
     cudaGraphExecDestroy(B->exec);
     B->exec = nullptr;
   }
@@ -1158,25 +1152,6 @@ bool same_key(const BatchState* B, int count, const corutv_problem* probs) {
          memcmp(B->key.data(), probs, B->key.size()) == 0;
 }
 
-// The problem array without its buffer addresses: what the plan depends on (sizes, flags,
-// leading dimensions, whether A's rows are 16-byte aligned and whether tile scales are given).
-std::vector<unsigned char> shape_key(int count, const corutv_problem* probs) {
-  std::vector<corutv_problem> q(probs, probs + count);
-  for (corutv_problem& p : q) {
-    p.A = reinterpret_cast<const void*>((uintptr_t)(aligned16(p.A) ? 1 : 2));
-    p.a_tile_scales = reinterpret_cast<const float*>((uintptr_t)(p.a_tile_scales ? 1 : 0));
-    p.Phi = nullptr;
-    p.U = nullptr;
-    p.T = nullptr;
-    p.V = nullptr;
-    p.perm = nullptr;
-  }
-  const unsigned char* b = reinterpret_cast<const unsigned char*>(q.data());
-  return std::vector<unsigned char>(b, b + sizeof(corutv_problem) * (size_t)count);
-}
-
-constexpr size_t kBatchPoolMax = 8;   // plans (workspace, tables, graph) kept per handle
-
 }  // namespace
 
 extern "C" {
@@ -1212,81 +1187,13 @@ int corutv_solve_batched(corutv_handle* h, int count, const corutv_problem* prob
     if (rc) return rc;
     if (probs[i].a_dtype != a_dtype) return CORUTV_ERR_UNSUPPORTED;   // one storage dtype per batch
   }
-  // the plan: the one built for this exact problem set, else one built for a set of the same
-  // shape (its tables are rebuilt for the new buffers and its graph is kept), else a new one
-  // (the least recently used plan makes room when the pool is full)
-  BatchState* B = nullptr;
-  bool repoint = false;
-  for (BatchState* e : h->batch_pool)
-    if (same_key(e, count, probs)) B = e;
-  std::vector<unsigned char> shape;
-  if (!B) {
-    shape = shape_key(count, probs);
-    for (BatchState* e : h->batch_pool)
-      if (!e->key.empty() && e->shape == shape) {
-        B = e;
-        repoint = true;
-      }
-  }
-  if (!B) {
-    if (h->batch_pool.size() < kBatchPoolMax) {
-      B = new (std::nothrow) BatchState();
-      if (!B) return CORUTV_ERR_OOM;
-      if (h->batch) B->tuned_keys = h->batch->tuned_keys;
-      h->batch_pool.push_back(B);
-    } else {
-      B = h->batch_pool[0];
-      for (BatchState* e : h->batch_pool)
-        if (e->last_use < B->last_use) B = e;
-      if (h->batch && B != h->batch) B->tuned_keys = h->batch->tuned_keys;
-    }
-  }
-  h->batch = B;
-  B->last_use = ++h->batch_tick;
+  if (!h->batch) h->batch = new (std::nothrow) BatchState();
+  if (!h->batch) return CORUTV_ERR_OOM;
+  BatchState* B = h->batch;
   int64_t l0 = launch_counter();
-  if (repoint) {
-    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return CORUTV_ERR_CUDA;
-    const BatchTune tune = B->tune;
-    int rc = build(h, B, count, probs, tune, true);
-    if (rc) return rc;
-    B->shape = std::move(shape);
-    if (B->exec && !h->tracing) {
-      CUB(cudaGraphLaunch(B->exec, h->stream));
-      launch_counter() += B->launches_per_run;
-    } else if (h->tracing || h->stream == nullptr || h->stream == cudaStreamLegacy) {
-      rc = enqueue(h, B);
-      if (rc) return rc;
-    } else {
-      // second problem set of this shape: capture the sequence once, then replay it
-      cudaGraph_t g = nullptr;
-      CUB(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-      const int64_t c0 = launch_counter();
-      rc = enqueue(h, B);
-      const cudaError_t ce = cudaStreamEndCapture(h->stream, &g);
-      launch_counter() = c0;
-      if (rc || ce != cudaSuccess) {
-        if (g) cudaGraphDestroy(g);
-        cudaGetLastError();
-        return rc ? rc : CORUTV_ERR_CUDA;
-      }
-      if (B->exec) {
-        cudaGraphExecDestroy(B->exec);
-        B->exec = nullptr;
-      }
-      const cudaError_t ie = cudaGraphInstantiate(&B->exec, g, 0);
-      cudaGraphDestroy(g);
-      if (ie != cudaSuccess) {
-        B->exec = nullptr;
-        cudaGetLastError();
-        return CORUTV_ERR_CUDA;
-      }
-      CUB(cudaGraphLaunch(B->exec, h->stream));
-      launch_counter() += B->launches_per_run;
-    }
-  } else if (!same_key(B, count, probs)) {
+  if (!same_key(B, count, probs)) {
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return CORUTV_ERR_CUDA;
     B->key.clear();
-    B->shape.clear();
     BatchTune tune;
     B->tuned = B->tune_from_cache = false;
     B->tuned_ms = B->default_ms = 0.0;
@@ -1299,7 +1206,6 @@ int corutv_solve_batched(corutv_handle* h, int count, const corutv_problem* prob
     }
     int rc = build(h, B, count, probs, tune);
     if (rc) return rc;
-    B->shape = shape.empty() ? shape_key(count, probs) : std::move(shape);
     B->a_dtype = a_dtype;
     rc = enqueue(h, B);                           // first run of a problem set: direct launches
     if (rc) return rc;
@@ -1349,13 +1255,10 @@ int corutv_set_autotune(corutv_handle* h, int mode, const char* cache_path) {
     const char* env = getenv("CORUTV_AUTOTUNE_CACHE");
     h->tune_cache = env ? env : "";
   }
-  if (!h->batch_pool.empty()) {
-    // the next batched calls build new plans with (or without) tuned shapes
+  if (h->batch) {
+    // the next batched call builds a new plan with (or without) tuned shapes
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return CORUTV_ERR_CUDA;
-    for (BatchState* e : h->batch_pool) {
-      e->key.clear();
-      e->shape.clear();
-    }
+    h->batch->key.clear();
   }
   return CORUTV_OK;
 }

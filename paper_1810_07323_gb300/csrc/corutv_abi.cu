@@ -704,7 +704,7 @@ int corutv_destroy(corutv_handle* h) {
     cudaEventDestroy(r.b);
   }
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
-  for (BatchState* b : h->batch_pool) batch_state_free(b);
+  batch_state_free(h->batch);
   rpca_free(h);
   ring_free(h);
   resid_free(h);

@@ -49,9 +49,7 @@ struct corutv_handle {
   int last_passes = 0;
   double last_shift = 0.0;
   bool have_last = false;
-  corutv::BatchState* batch = nullptr;   // the plan of the last batched call (one of batch_pool)
-  std::vector<corutv::BatchState*> batch_pool;   // plans kept per problem-set shape (owned)
-  uint64_t batch_tick = 0;
+  corutv::BatchState* batch = nullptr;
   void* rpca_ws = nullptr;      // factors of the ALM-CoRUTV iterations (rpca.cu), lazily allocated
   size_t rpca_ws_bytes = 0;
   HostRing ring;

@@ -480,46 +480,3 @@ def test_batched_trace_times_the_pass_kernels_alone(kind):
     assert t.pass_launches > 0
     assert t.pass_kernel_launches == t.pass_launches
     assert 0.0 < t.pass_kernel_ms < t.pass_ms
-
-
-@pytest.mark.parametrize("kind", ["f32", "bf16"])
-def test_batched_same_shape_sets_replay_one_graph(kind):
-    """Problem sets of one shape in other buffers reuse the handle's plan: the first runs
-    directly, the second is captured, later ones replay that graph with the tables rebuilt for
-    their buffers.  Every result is the same bits as the set solved on a fresh handle."""
-    shapes = [(700, 304, 6, 6, 14, 1, "right", "exact", "stabilised"),
-              (512, 1104, 10, 10, 18, 1, "left", "exact", "stabilised"),
-              (1500, 896, 20, 20, 28, 2, "right", "sketch", "stabilised"),
-              (333, 128, 4, 4, 12, 0, "right", "exact", "stabilised")]
-
-    def make_set(seed):
-        items = []
-        for i, (m, n, r, k, l, q, side, core, orth) in enumerate(shapes):
-            A = _lowrank_sparse(C.stream_seed(seed, i), m, n, r).astype(np.float32)
-            phi = C.normal_block_np(C.stream_seed(seed + 1, i), l, 0, m if side == "left" else n, 0, l)
-            it, _ = _item(A, phi, k, l, q, side, core, orth, kind=kind)
-            items.append(it)
-        return items
-
-    sets = [make_set(200 + 10 * s) for s in range(3)]
-
-    def factors(res):
-        return [(x.U.clone(), x.T.clone(), x.V.clone(), x.perm.clone(), x.info.status) for x in res]
-
-    alone = []
-    for items in sets:
-        h = corutv.Handle()
-        try:
-            alone.append(factors(corutv.Batch(items, handle=h).run()))
-        finally:
-            h.close()
-    h = corutv.Handle()
-    try:
-        order = [0, 1, 2, 0, 1]         # direct, capture, replay, replay, replay
-        for s in order:
-            got = factors(corutv.Batch(sets[s], handle=h).run())
-            for a, b in zip(alone[s], got):
-                assert a[4] == 0 and b[4] == 0
-                assert all(torch.equal(x, y) for x, y in zip(a[:4], b[:4])), s
-    finally:
-        h.close()
