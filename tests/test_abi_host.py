@@ -104,3 +104,51 @@ def test_host_entry_points_check_their_tensors():
     with pytest.raises(ValueError):
         corutv.residual_norm2(torch.zeros(10, 8), torch.zeros(10, 2), torch.zeros(2, 2, dtype=torch.float64),
                               torch.zeros(8, 2), torch.zeros(8))             # device tensors required
+
+
+def _problem(m=700, n=300, k=6, l=14, q=1, dtype="f32", lda=None, fuse=0, orth="stabilised", scales=True,
+             a_addr=0x10000):
+    """A batched problem descriptor with placeholder (never dereferenced) device addresses."""
+    p = corutv.Problem()
+    p.m, p.n, p.k, p.l, p.q = m, n, k, l, q
+    p.side, p.core, p.orth = corutv.SIDE["right"], corutv.CORE["exact"], corutv.ORTH[orth]
+    p.a_dtype = corutv.DTYPE[dtype]
+    p.mma, p.want_fro2, p.fuse_power = 0, 1, fuse
+    p.A = a_addr
+    p.lda = n if lda is None else lda
+    p.a_tile_scales = 0x20000 if (dtype == "fp8" and scales) else None
+    p.Phi, p.ldphi = 0x30000, l
+    p.U, p.ldu, p.T, p.ldt, p.V, p.ldv, p.perm = 0x40000, l, 0x50000, l, 0x60000, l, 0x70000
+    return p
+
+
+def _batch_ws(probs):
+    arr = (corutv.Problem * len(probs))(*probs)
+    out = ctypes.c_size_t()
+    rc = corutv.load().corutv_batch_workspace_size(len(probs), arr, ctypes.byref(out))
+    return rc, out.value
+
+
+def test_batch_workspace_size_on_the_host():
+    """The batched plan is made on the host (no device needed): its size is deterministic,
+    grows with the problems it holds, and counts every problem of a mixed set."""
+    rc1, one = _batch_ws([_problem()])
+    rc1b, one_b = _batch_ws([_problem()])
+    rc2, two = _batch_ws([_problem(), _problem(m=4096, n=2048, k=30, l=40)])
+    rc3, bf = _batch_ws([_problem(dtype="bf16", n=304), _problem(dtype="fp8", n=304)])
+    assert rc1 == rc1b == rc2 == rc3 == corutv.OK
+    assert one == one_b > 0 and two > one and bf > 0
+
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(k=15, l=14), corutv.ERR_INVALID_ARG),              # k > l
+    (dict(l=300), corutv.ERR_SHAPE),                         # l >= min(m, n)
+    (dict(q=-1), corutv.ERR_INVALID_ARG),
+    (dict(lda=200), corutv.ERR_SHAPE),                       # lda < n
+    (dict(dtype="fp8", scales=False), corutv.ERR_INVALID_ARG),
+    (dict(fuse=2), corutv.ERR_INVALID_ARG),
+    (dict(orth="literal"), corutv.ERR_UNSUPPORTED),          # Alg. 3 as printed: single solves only
+])
+def test_batch_problem_validation_on_the_host(kw, status):
+    rc, _ = _batch_ws([_problem(), _problem(**kw)])
+    assert rc == status
