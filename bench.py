@@ -9,12 +9,15 @@ Workloads (--workload):
                   FP32 A quantised on the device (BF16, or FP8 e4m3 with
                   128 x 128 tile scales), 2q+2 kind::f16 passes over the stored
                   A, then the FP32 correction pass for the core.
-  batched         1024 uneven problems in one batched call per step.
+  batched         1024 uneven problems in one batched call per step (FP32 A,
+                  grouped TF32 tensor-core passes); --count N takes the first N.
+  batched_bf16    the same problems stored in BF16 (grouped kind::f16 passes).
+                  --fuse-power: the fused power steps (A from HBM q + 2 times).
   serving         Poisson request stream through the serving queue (p99 latency).
   rpca            ALM-CoRUTV robust PCA (Alg. 5) of the Sec. VI-C synthetic
                   2000 x 2000 matrix (--n 1000 for the other Table I size):
                   time of one whole run to the stopping rule.
-  fp32c3          the FP32 (TF32-pass) solve of the bf16 / fp8 workload's matrix:
+  fp32c3          the FP32 (split-operand pass) solve of the bf16 / fp8 workload's matrix:
                   the three precisions on one A at the same k, l, q.
   host            the fp32 solve with A in page-locked host memory
                   (corutv_solve_host): every one of the 2q+3 passes streams A
